@@ -1,0 +1,318 @@
+"""FP64 CPU oracle of the hybrid mesh + radiance-field light-transport loop.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
+and by the CPU-baseline leg of ``bench.py``.  The CUDA library never imports,
+links or calls anything in this directory.
+
+The arithmetic lives in ``mrf_oracle.c`` (plain C, double precision, written
+step by step from the paper's Algorithm 1 and Eqs. 3, 10-13).  This module only
+compiles it with gcc and marshals numpy arrays from a ``scenes.Scene`` into the
+C struct ``orc_scene``.
+
+Parity status of each function is stated in the design doc; every function here is
+pinned by a ``-m "not gpu"`` test except the whole-image composition, which the
+paper gives no worked example for ("parity unpinned" beyond its pinned parts).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mrf_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+NO_HIT = 0xFFFFFFFF
+FLAG_EDGE, FLAG_SHADOW, FLAG_FRESNEL, FLAG_TAU, FLAG_BASIS, FLAG_TMIN = 1, 2, 4, 8, 16, 32
+COUNT_NAMES = ("segments", "shadow_rays", "samples_nominal", "samples_supported", "surface_hits", "paths")
+
+_fp = C.POINTER(C.c_float)
+_u32p = C.POINTER(C.c_uint32)
+_u16p = C.POINTER(C.c_uint16)
+_i32p = C.POINTER(C.c_int32)
+_dp = C.POINTER(C.c_double)
+_u64p = C.POINTER(C.c_uint64)
+
+
+class OrcScene(C.Structure):
+    _fields_ = [
+        ("cam_pos", C.c_float * 3), ("cam_look", C.c_float * 3), ("cam_up", C.c_float * 3),
+        ("vfov_deg", C.c_float), ("width", C.c_uint32), ("height", C.c_uint32),
+        ("ray_o", _fp), ("ray_d", _fp), ("n_rays", C.c_uint32),
+        ("field_kind", C.c_int32), ("aabb_min", C.c_float * 3), ("aabb_max", C.c_float * 3),
+        ("const_sigma", C.c_float), ("const_rgb", C.c_float * 3),
+        ("n_blobs", C.c_uint32), ("blob_c", _fp), ("blob_r", _fp), ("blob_peak", _fp), ("blob_e", _fp),
+        ("n_levels", C.c_uint32), ("log2_T", C.c_uint32), ("n_feat", C.c_uint32),
+        ("level_res", _u32p), ("table", _u16p), ("mlp_width", C.c_uint32),
+        ("w1", _fp), ("b1", _fp), ("w2", _fp), ("b2", _fp), ("w3", _fp), ("b3", _fp),
+        ("n_support", C.c_uint32), ("sup_c", _fp), ("sup_r", _fp),
+        ("n_verts", C.c_uint32), ("verts", _fp), ("n_tris", C.c_uint32), ("tris", _u32p), ("tri_mat", _u32p),
+        ("n_mats", C.c_uint32), ("mat_kind", _i32p), ("mat_rgb", _fp), ("mat_ior", _fp),
+        ("n_lights", C.c_uint32), ("light_pos", _fp), ("light_I", _fp),
+        ("max_bounces", C.c_uint32), ("spp", C.c_uint32), ("seed", C.c_uint64),
+        ("steps_per_segment", C.c_uint32), ("dt", C.c_float), ("tau", C.c_float), ("tmin", C.c_float),
+        ("margin_bary", C.c_double), ("margin_t", C.c_double), ("margin_fresnel", C.c_double),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP, strict IEEE double, no contraction)."""
+    with _lock:
+        if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+            tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+            cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                   "-fno-fast-math", "-Wall", "-Wno-unused-function", "-o", tmp, _SRC, "-lm"]
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB_PATH)
+        L.orc_half_to_double.restype = C.c_double
+        L.orc_half_to_double.argtypes = [C.c_uint16]
+        L.orc_philox4x64.argtypes = [_u64p, _u64p, _u64p]
+        L.orc_camera_ray.argtypes = [C.POINTER(OrcScene), C.c_uint32, _dp, _dp]
+        L.orc_hash_encode.argtypes = [C.POINTER(OrcScene), _dp, _dp]
+        L.orc_mlp.argtypes = [C.POINTER(OrcScene), _dp, _dp]
+        L.orc_support.restype = C.c_double
+        L.orc_support.argtypes = [C.POINTER(OrcScene), _dp]
+        L.orc_field_eval.restype = C.c_int
+        L.orc_field_eval.argtypes = [C.POINTER(OrcScene), _dp, _dp, _dp]
+        L.orc_box_interval.restype = C.c_int
+        L.orc_box_interval.argtypes = [C.POINTER(OrcScene), _dp, _dp, _dp, _dp]
+        L.orc_transmittance.restype = C.c_double
+        L.orc_transmittance.argtypes = [C.POINTER(OrcScene), _dp, _dp, C.c_double, C.c_double, _u64p]
+        L.orc_march.argtypes = [C.POINTER(OrcScene), _dp, _dp, C.c_double, C.c_double, _dp, _dp]
+        L.orc_intersect_tri.restype = C.c_int
+        L.orc_intersect_tri.argtypes = [_dp, _dp, _dp, _dp, _dp, C.c_double, _dp, _dp, _dp]
+        L.orc_closest_hit.restype = C.c_uint32
+        L.orc_closest_hit.argtypes = [C.POINTER(OrcScene), _dp, _dp, C.c_uint32, _dp, _u32p]
+        L.orc_reflect.argtypes = [_dp, _dp, _dp]
+        L.orc_fresnel.restype = C.c_double
+        L.orc_fresnel.argtypes = [C.c_double, C.c_double, C.c_double]
+        L.orc_refract.restype = C.c_int
+        L.orc_refract.argtypes = [_dp, _dp, C.c_double, _dp]
+        L.orc_sample_cosine.argtypes = [_dp, C.c_double, C.c_double, _dp]
+        L.orc_render.restype = C.c_int
+        L.orc_render.argtypes = [C.POINTER(OrcScene), _u32p, C.c_uint32, _dp, _u32p, _u32p, _dp, _u32p, _u64p,
+                                 C.c_int]
+        L.orc_num_threads.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(t) if a is not None else None
+
+
+class OracleScene:
+    """A ``scenes.Scene`` marshalled into an ``orc_scene`` (keeps its arrays alive)."""
+
+    def __init__(self, scene, margin_bary=1e-5, margin_t=1e-5, margin_fresnel=1e-5):
+        self.scene = scene
+        keep = []
+
+        def arr(a, dt):
+            if a is None:
+                return None
+            x = np.ascontiguousarray(np.asarray(a).astype(dt, copy=False))
+            keep.append(x)
+            return x
+
+        s = OrcScene()
+        cam = scene.camera
+        s.cam_pos[:] = list(map(float, cam.pos))
+        s.cam_look[:] = list(map(float, cam.look_at))
+        s.cam_up[:] = list(map(float, cam.up))
+        s.vfov_deg = cam.vfov_deg
+        s.width, s.height = cam.width, cam.height
+        if scene.ray_o is not None:
+            s.ray_o = _ptr(arr(scene.ray_o, np.float32), _fp)
+            s.ray_d = _ptr(arr(scene.ray_d, np.float32), _fp)
+            s.n_rays = scene.ray_o.shape[0]
+        f = scene.field
+        s.field_kind = f.kind
+        s.aabb_min[:] = list(map(float, f.aabb_min))
+        s.aabb_max[:] = list(map(float, f.aabb_max))
+        s.const_sigma = f.const_sigma
+        s.const_rgb[:] = list(map(float, f.const_rgb))
+        if f.blob_center is not None:
+            s.n_blobs = f.blob_center.shape[0]
+            s.blob_c = _ptr(arr(f.blob_center, np.float32), _fp)
+            s.blob_r = _ptr(arr(f.blob_radius, np.float32), _fp)
+            s.blob_peak = _ptr(arr(f.blob_peak, np.float32), _fp)
+            s.blob_e = _ptr(arr(f.blob_emission, np.float32), _fp)
+        if f.table is not None:
+            s.n_levels = f.level_res.shape[0]
+            s.log2_T = f.log2_table_size
+            s.n_feat = f.n_features
+            s.level_res = _ptr(arr(f.level_res, np.uint32), _u32p)
+            s.table = _ptr(arr(f.table.view(np.uint16), np.uint16), _u16p)
+            s.mlp_width = f.w1.shape[0]
+            for nm in ("w1", "b1", "w2", "b2", "w3", "b3"):
+                setattr(s, nm, _ptr(arr(getattr(f, nm), np.float32), _fp))
+            s.n_support = f.support_center.shape[0]
+            s.sup_c = _ptr(arr(f.support_center, np.float32), _fp)
+            s.sup_r = _ptr(arr(f.support_radius, np.float32), _fp)
+        m = scene.mesh
+        s.n_verts = m.verts.shape[0]
+        s.verts = _ptr(arr(m.verts, np.float32), _fp)
+        s.n_tris = m.tris.shape[0]
+        s.tris = _ptr(arr(m.tris, np.uint32), _u32p)
+        s.tri_mat = _ptr(arr(m.mat, np.uint32), _u32p)
+        mats = scene.materials or []
+        s.n_mats = len(mats)
+        s.mat_kind = _ptr(arr(np.array([x.kind for x in mats] or [0], np.int32), np.int32), _i32p)
+        s.mat_rgb = _ptr(arr(np.array([x.rgb for x in mats] or [(0, 0, 0)], np.float32), np.float32), _fp)
+        s.mat_ior = _ptr(arr(np.array([x.ior for x in mats] or [1.0], np.float32), np.float32), _fp)
+        lights = scene.lights or []
+        s.n_lights = len(lights)
+        s.light_pos = _ptr(arr(np.array([x.pos for x in lights] or [(0, 0, 0)], np.float32), np.float32), _fp)
+        s.light_I = _ptr(arr(np.array([x.intensity for x in lights] or [(0, 0, 0)], np.float32), np.float32), _fp)
+        o = scene.opts
+        s.max_bounces, s.spp, s.seed = o.max_bounces, o.spp, o.seed
+        s.steps_per_segment, s.dt, s.tau, s.tmin = o.steps_per_segment, o.dt, o.tau, o.tmin
+        s.margin_bary, s.margin_t, s.margin_fresnel = margin_bary, margin_t, margin_fresnel
+        self.s = s
+        self._keep = keep
+
+    @property
+    def ref(self):
+        return C.byref(self.s)
+
+
+def render(scene, ids=None, threads: int = 0, records: bool = True, **margins):
+    """Render ``ids`` (pixel or explicit-ray indices; default all) in FP64.
+
+    Returns a dict: rgba (n,4) f64, segments (n,spp) u32, tri (n,spp,B) u32,
+    t (n,spp,B) f64, flags (n,) u32, counts {name: int}."""
+    L = lib()
+    os_ = OracleScene(scene, **margins)
+    n_all = scene.n_rays
+    ids = np.arange(n_all, dtype=np.uint32) if ids is None else np.ascontiguousarray(np.asarray(ids, np.uint32))
+    n = ids.shape[0]
+    spp, B = scene.opts.spp, scene.opts.max_bounces
+    rgba = np.zeros((n, 4), np.float64)
+    segs = np.zeros((n, spp), np.uint32)
+    tri = np.zeros((n, spp, B), np.uint32) if records else None
+    tt = np.zeros((n, spp, B), np.float64) if records else None
+    flags = np.zeros(n, np.uint32)
+    counts = np.zeros(6, np.uint64)
+    L.orc_render(os_.ref, _ptr(ids, _u32p), n, _ptr(rgba, _dp), _ptr(segs, _u32p), _ptr(tri, _u32p), _ptr(tt, _dp),
+                 _ptr(flags, _u32p), _ptr(counts, _u64p), int(threads))
+    return dict(rgba=rgba, segments=segs, tri=tri, t=tt, flags=flags, ids=ids,
+                counts={k: int(v) for k, v in zip(COUNT_NAMES, counts)})
+
+
+# ---- thin wrappers of the unit functions (used by the pin tests) ----------
+def _d(x, n=3):
+    return np.ascontiguousarray(np.asarray(x, np.float64).reshape(n))
+
+
+def half_to_double(bits: int) -> float:
+    return lib().orc_half_to_double(int(bits))
+
+
+def philox4x64(ctr, key):
+    c = np.ascontiguousarray(np.asarray(ctr, np.uint64))
+    k = np.ascontiguousarray(np.asarray(key, np.uint64))
+    out = np.zeros(4, np.uint64)
+    lib().orc_philox4x64(_ptr(c, _u64p), _ptr(k, _u64p), _ptr(out, _u64p))
+    return out
+
+
+def camera_ray(oscene: OracleScene, pix: int):
+    o, d = np.zeros(3), np.zeros(3)
+    lib().orc_camera_ray(oscene.ref, int(pix), _ptr(o, _dp), _ptr(d, _dp))
+    return o, d
+
+
+def hash_encode(oscene: OracleScene, p):
+    f = oscene.scene.field
+    feat = np.zeros(f.level_res.shape[0] * f.n_features)
+    lib().orc_hash_encode(oscene.ref, _ptr(_d(p), _dp), _ptr(feat, _dp))
+    return feat
+
+
+def mlp(oscene: OracleScene, feat):
+    out = np.zeros(4)
+    lib().orc_mlp(oscene.ref, _ptr(np.ascontiguousarray(np.asarray(feat, np.float64)), _dp), _ptr(out, _dp))
+    return out
+
+
+def support(oscene: OracleScene, p) -> float:
+    return lib().orc_support(oscene.ref, _ptr(_d(p), _dp))
+
+
+def field_eval(oscene: OracleScene, p):
+    sig = np.zeros(1)
+    rgb = np.zeros(3)
+    lib().orc_field_eval(oscene.ref, _ptr(_d(p), _dp), _ptr(sig, _dp), _ptr(rgb, _dp))
+    return float(sig[0]), rgb
+
+
+def box_interval(oscene: OracleScene, o, d):
+    t0, t1 = np.zeros(1), np.zeros(1)
+    ok = lib().orc_box_interval(oscene.ref, _ptr(_d(o), _dp), _ptr(_d(d), _dp), _ptr(t0, _dp), _ptr(t1, _dp))
+    return bool(ok), float(t0[0]), float(t1[0])
+
+
+def transmittance(oscene: OracleScene, o, d, a, b) -> float:
+    return lib().orc_transmittance(oscene.ref, _ptr(_d(o), _dp), _ptr(_d(d), _dp), float(a), float(b), None)
+
+
+def march(oscene: OracleScene, o, d, a, b, T=(1.0, 1.0, 1.0), L=(0.0, 0.0, 0.0)):
+    Tv, Lv = _d(T).copy(), _d(L).copy()
+    lib().orc_march(oscene.ref, _ptr(_d(o), _dp), _ptr(_d(d), _dp), float(a), float(b), _ptr(Tv, _dp), _ptr(Lv, _dp))
+    return Tv, Lv
+
+
+def intersect_tri(o, d, v0, v1, v2, tmin=1e-6):
+    t, b1, b2 = np.zeros(1), np.zeros(1), np.zeros(1)
+    hit = lib().orc_intersect_tri(_ptr(_d(o), _dp), _ptr(_d(d), _dp), _ptr(_d(v0), _dp), _ptr(_d(v1), _dp),
+                                  _ptr(_d(v2), _dp), float(tmin), _ptr(t, _dp), _ptr(b1, _dp), _ptr(b2, _dp))
+    return bool(hit), float(t[0]), float(b1[0]), float(b2[0])
+
+
+def closest_hit(oscene: OracleScene, o, d, skip=NO_HIT):
+    t = np.zeros(1)
+    fl = np.zeros(1, np.uint32)
+    tid = lib().orc_closest_hit(oscene.ref, _ptr(_d(o), _dp), _ptr(_d(d), _dp), int(skip), _ptr(t, _dp),
+                                _ptr(fl, _u32p))
+    return int(tid), float(t[0]), int(fl[0])
+
+
+def reflect(d, n):
+    out = np.zeros(3)
+    lib().orc_reflect(_ptr(_d(d), _dp), _ptr(_d(n), _dp), _ptr(out, _dp))
+    return out
+
+
+def fresnel(cos_i, eta_i, eta_t) -> float:
+    return lib().orc_fresnel(float(cos_i), float(eta_i), float(eta_t))
+
+
+def refract(d, n, eta):
+    out = np.zeros(3)
+    ok = lib().orc_refract(_ptr(_d(d), _dp), _ptr(_d(n), _dp), float(eta), _ptr(out, _dp))
+    return bool(ok), out
+
+
+def sample_cosine(n, u1, u2):
+    out = np.zeros(3)
+    lib().orc_sample_cosine(_ptr(_d(n), _dp), float(u1), float(u2), _ptr(out, _dp))
+    return out
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()

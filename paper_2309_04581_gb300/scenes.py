@@ -1,0 +1,408 @@
+"""Seeded synthetic scenes for the hybrid mesh + radiance-field renderer.
+
+This module only *generates inputs*: cameras, field parameters, meshes,
+materials, lights and render options.  It holds none of the renderer's
+arithmetic (no ray generation, no field evaluation, no intersection, no
+shading); the CUDA library and the FP64 CPU oracle each implement those on
+their own and both consume the arrays produced here.
+
+All floating-point scene values are rounded to FP32 here, so that the FP32
+GPU path and the FP64 oracle start from bit-identical parameters (the oracle
+widens them exactly).
+
+The scene shapes follow the paper's workloads (a bounded radiance field with
+inserted mirror, glass and diffuse meshes, Fig. 1 and Sec. 3.1 of the paper);
+the captured datasets the paper uses are not available, so every scene is
+synthetic and seeded from ``MASTER_SEED`` through SplitMix64 sub-seeds.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field as dc_field
+from typing import List, Optional
+
+import numpy as np
+
+MASTER_SEED = 20230908
+_M64 = (1 << 64) - 1
+
+# material kinds (Sec. 3.3 names refractive, reflective and Lambertian BSDFs)
+MAT_MIRROR = 0
+MAT_GLASS = 1
+MAT_DIFFUSE = 2
+
+# field kinds
+FIELD_CONST = 0
+FIELD_GAUSS = 1
+FIELD_HASH = 2
+
+# light kinds
+LIGHT_POINT = 0
+
+
+def splitmix64(x: int) -> int:
+    """One SplitMix64 output for state ``x`` (Steele, Lea, Flood 2014)."""
+    x = (x + 0x9E3779B97F4A7C15) & _M64
+    z = x
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def subseed(config: int, purpose: int, master: int = MASTER_SEED) -> int:
+    """Sub-seed for (config, purpose), derived from the master seed."""
+    return splitmix64(splitmix64(splitmix64(master) ^ config) ^ (purpose * 0x632BE59BD9B4E019 & _M64))
+
+
+def _rng(config: int, purpose: int) -> np.random.Generator:
+    return np.random.default_rng(subseed(config, purpose))
+
+
+def f32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).astype(np.float32))
+
+
+# ---------------------------------------------------------------------------
+# scene containers
+# ---------------------------------------------------------------------------
+@dataclass
+class Camera:
+    pos: np.ndarray
+    look_at: np.ndarray
+    up: np.ndarray
+    vfov_deg: float
+    width: int
+    height: int
+
+
+@dataclass
+class Field:
+    kind: int
+    aabb_min: np.ndarray
+    aabb_max: np.ndarray
+    # FIELD_CONST
+    const_sigma: float = 0.0
+    const_rgb: np.ndarray = dc_field(default_factory=lambda: f32([0, 0, 0]))
+    # FIELD_GAUSS: sigma(x) = sum_k peak_k exp(-|x-c_k|^2 / (2 r_k^2)); emission-weighted colour
+    blob_center: Optional[np.ndarray] = None   # (K,3) f32
+    blob_radius: Optional[np.ndarray] = None   # (K,)  f32
+    blob_peak: Optional[np.ndarray] = None     # (K,)  f32
+    blob_emission: Optional[np.ndarray] = None  # (K,3) f32
+    # FIELD_HASH: multiresolution hash grid + MLP
+    level_res: Optional[np.ndarray] = None     # (L,) uint32
+    log2_table_size: int = 19
+    n_features: int = 2
+    table: Optional[np.ndarray] = None         # (L, T, F) float16
+    w1: Optional[np.ndarray] = None            # (64, L*F) f32
+    b1: Optional[np.ndarray] = None
+    w2: Optional[np.ndarray] = None            # (64, 64)
+    b2: Optional[np.ndarray] = None
+    w3: Optional[np.ndarray] = None            # (4, 64)
+    b3: Optional[np.ndarray] = None
+    support_center: Optional[np.ndarray] = None  # (S,3) f32: compact support of the density
+    support_radius: Optional[np.ndarray] = None  # (S,)
+    occ_res: int = 0
+    occ_bits: Optional[np.ndarray] = None      # (occ_res^3 / 32,) uint32, cell x + R*(y + R*z)
+
+
+@dataclass
+class Mesh:
+    verts: np.ndarray   # (V,3) f32
+    tris: np.ndarray    # (N,3) uint32
+    mat: np.ndarray     # (N,)  uint32 material index
+
+    @property
+    def n_tris(self) -> int:
+        return int(self.tris.shape[0])
+
+
+@dataclass
+class Material:
+    kind: int
+    rgb: tuple = (1.0, 1.0, 1.0)  # mirror reflectance rho / diffuse albedo
+    ior: float = 1.5              # glass index of refraction
+
+
+@dataclass
+class Light:
+    pos: tuple
+    intensity: tuple
+    kind: int = LIGHT_POINT
+
+
+@dataclass
+class RenderOpts:
+    max_bounces: int = 4          # maximum segments per path (camera segment = 1)
+    spp: int = 1
+    seed: int = 0
+    steps_per_segment: int = 0    # >0: that many midpoint samples per segment
+    dt: float = 0.0               # steps_per_segment == 0: fixed step length
+    tau: float = 0.0              # throughput termination threshold (0 = off)
+    tmin: float = 1e-6            # smallest accepted ray-triangle distance
+
+
+@dataclass
+class Scene:
+    name: str
+    camera: Camera
+    field: Field
+    mesh: Mesh
+    materials: List[Material]
+    lights: List[Light]
+    opts: RenderOpts
+    ray_o: Optional[np.ndarray] = None   # explicit rays (n,3) f32; overrides the camera
+    ray_d: Optional[np.ndarray] = None
+
+    @property
+    def n_rays(self) -> int:
+        if self.ray_o is not None:
+            return int(self.ray_o.shape[0])
+        return self.camera.width * self.camera.height
+
+
+# ---------------------------------------------------------------------------
+# meshes
+# ---------------------------------------------------------------------------
+def empty_mesh() -> Mesh:
+    return Mesh(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.uint32), np.zeros((0,), np.uint32))
+
+
+def merge_meshes(meshes: List[Mesh]) -> Mesh:
+    vs, ts, ms, off = [], [], [], 0
+    for m in meshes:
+        vs.append(m.verts)
+        ts.append(m.tris + off)
+        ms.append(m.mat)
+        off += m.verts.shape[0]
+    return Mesh(f32(np.concatenate(vs)), np.ascontiguousarray(np.concatenate(ts).astype(np.uint32)),
+                np.ascontiguousarray(np.concatenate(ms).astype(np.uint32)))
+
+
+def box_mesh(center, half, mat: int, inward: bool = False) -> Mesh:
+    """Axis-aligned box of 12 triangles; outward-facing winding unless ``inward``."""
+    c = np.asarray(center, np.float64)
+    h = np.broadcast_to(np.asarray(half, np.float64), (3,))
+    corners = np.array([[x, y, z] for z in (-1, 1) for y in (-1, 1) for x in (-1, 1)], np.float64)
+    verts = c + corners * h
+    # vertex index = x + 2y + 4z with x,y,z in {0,1}
+    quads = [(0, 2, 3, 1), (4, 5, 7, 6),   # z-, z+
+             (0, 1, 5, 4), (2, 6, 7, 3),   # y-, y+
+             (0, 4, 6, 2), (1, 3, 7, 5)]   # x-, x+
+    tris = []
+    for a, b, cc, d in quads:
+        t1, t2 = (a, b, cc), (a, cc, d)
+        if inward:
+            t1, t2 = (a, cc, b), (a, d, cc)
+        tris += [t1, t2]
+    return Mesh(f32(verts), np.array(tris, np.uint32), np.full(len(tris), mat, np.uint32))
+
+
+def quad_mesh(p0, p1, p2, p3, mat: int) -> Mesh:
+    verts = np.array([p0, p1, p2, p3], np.float64)
+    return Mesh(f32(verts), np.array([[0, 1, 2], [0, 2, 3]], np.uint32), np.full(2, mat, np.uint32))
+
+
+def icosphere_faces(level: int):
+    """Unit icosphere after ``level`` 1:4 subdivisions (normalised midpoints)."""
+    t = (1.0 + 5.0 ** 0.5) / 2.0
+    v = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t), (0, -1, -t), (0, 1, -t),
+         (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    verts = [np.array(p, np.float64) / np.linalg.norm(p) for p in v]
+    faces = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2),
+             (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5),
+             (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    for _ in range(level):
+        cache = {}
+
+        def mid(a, b):
+            key = (min(a, b), max(a, b))
+            if key not in cache:
+                m = verts[a] + verts[b]
+                verts.append(m / np.linalg.norm(m))
+                cache[key] = len(verts) - 1
+            return cache[key]
+
+        nf = []
+        for a, b, c in faces:
+            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        faces = nf
+    return np.array(verts), np.array(faces, np.int64)
+
+
+def glass_icosphere_10240(center, radius, mat: int) -> Mesh:
+    """10,240-triangle sphere: the level-4 icosphere (5,120 faces) with every face
+    split in two at the midpoint of its longest edge.  The midpoint stays on the
+    chord (it is not pushed onto the sphere), so the surface is exactly the
+    level-4 polyhedron and stays closed where neighbouring faces split
+    different edges."""
+    verts, faces = icosphere_faces(4)
+    verts = list(verts)
+    cache = {}
+    out = []
+    for a, b, c in faces:
+        e = [(np.linalg.norm(verts[a] - verts[b]), 0), (np.linalg.norm(verts[b] - verts[c]), 1),
+             (np.linalg.norm(verts[c] - verts[a]), 2)]
+        k = max(e)[1]
+        tri = (a, b, c)
+        p, q, r = tri[k], tri[(k + 1) % 3], tri[(k + 2) % 3]   # longest edge p-q, opposite r
+        key = (min(p, q), max(p, q))
+        if key not in cache:
+            verts.append(0.5 * (verts[p] + verts[q]))
+            cache[key] = len(verts) - 1
+        m = cache[key]
+        out += [(p, m, r), (m, q, r)]
+    v = np.asarray(center, np.float64) + radius * np.array(verts)
+    tris = np.array(out, np.uint32)
+    assert tris.shape[0] == 10240
+    return Mesh(f32(v), tris, np.full(tris.shape[0], mat, np.uint32))
+
+
+def random_soup(n_tris: int, seed_purpose: int, scale: float = 0.3, tri_size: float = 0.15) -> Mesh:
+    """Random triangle soup inside [-scale, scale]^3 (for intersection tests)."""
+    rng = _rng(900, seed_purpose)
+    c = rng.uniform(-scale, scale, size=(n_tris, 1, 3))
+    v = c + rng.uniform(-tri_size, tri_size, size=(n_tris, 3, 3))
+    verts = v.reshape(-1, 3)
+    tris = np.arange(n_tris * 3, dtype=np.uint32).reshape(-1, 3)
+    return Mesh(f32(verts), tris, np.zeros(n_tris, np.uint32))
+
+
+# ---------------------------------------------------------------------------
+# fields
+# ---------------------------------------------------------------------------
+UNIT_BOX_MIN = f32([-0.5, -0.5, -0.5])
+UNIT_BOX_MAX = f32([0.5, 0.5, 0.5])
+
+
+def const_field(sigma: float, rgb, aabb_min=UNIT_BOX_MIN, aabb_max=UNIT_BOX_MAX) -> Field:
+    return Field(kind=FIELD_CONST, aabb_min=f32(aabb_min), aabb_max=f32(aabb_max),
+                 const_sigma=float(np.float32(sigma)), const_rgb=f32(rgb))
+
+
+def gauss_field(centers, radii, peaks, emission, aabb_min=UNIT_BOX_MIN, aabb_max=UNIT_BOX_MAX) -> Field:
+    return Field(kind=FIELD_GAUSS, aabb_min=f32(aabb_min), aabb_max=f32(aabb_max),
+                 blob_center=f32(np.reshape(centers, (-1, 3))), blob_radius=f32(np.reshape(radii, (-1,))),
+                 blob_peak=f32(np.reshape(peaks, (-1,))), blob_emission=f32(np.reshape(emission, (-1, 3))))
+
+
+def level_resolutions(n_levels: int, n_min: int, n_max: int) -> np.ndarray:
+    """Per-level grid resolution N_l = floor(N_min * b^l), b = exp((ln N_max - ln N_min)/(L-1))
+    (the multiresolution hash encoding the paper takes from Instant-NGP).  Evaluated in
+    FP64 with a 1e-9 guard so that the exact endpoint N_max is not lost to rounding."""
+    b = math.exp((math.log(n_max) - math.log(n_min)) / (n_levels - 1))
+    return np.array([math.floor(n_min * b ** l + 1e-9) for l in range(n_levels)], np.uint32)
+
+
+def occupancy_from_spheres(centers, radii, res: int, aabb_min, aabb_max, margin: float) -> np.ndarray:
+    """Occupancy bitfield: a cell is set when its closed box, grown by ``margin``,
+    meets any sphere.  Bit for cell (x, y, z) is word (i >> 5), bit (i & 31) with
+    i = x + res*(y + res*z)."""
+    lo = np.asarray(aabb_min, np.float64)
+    ext = np.asarray(aabb_max, np.float64) - lo
+    edges = [lo[a] + ext[a] * np.arange(res + 1) / res for a in range(3)]
+    occ = np.zeros((res, res, res), bool)  # [z, y, x]
+    for c, r in zip(np.asarray(centers, np.float64), np.asarray(radii, np.float64)):
+        d = []
+        for a in range(3):
+            cl, ch = edges[a][:-1] - margin, edges[a][1:] + margin
+            d.append(np.maximum(np.maximum(cl - c[a], c[a] - ch), 0.0))
+        d2 = d[2][:, None, None] ** 2 + d[1][None, :, None] ** 2 + d[0][None, None, :] ** 2
+        occ |= d2 <= r * r
+    bits = occ.reshape(-1)  # x fastest
+    words = np.zeros(res ** 3 // 32, np.uint32)
+    idx = np.nonzero(bits)[0]
+    np.bitwise_or.at(words, idx >> 5, (np.uint32(1) << (idx & 31).astype(np.uint32)))
+    return words
+
+
+def hash_field(config: int, n_levels=16, log2_T=19, n_feat=2, n_min=16, n_max=2048, width=64,
+               n_support=8, support_r=(0.1, 0.25), support_c=0.3, occ_res=128, sigma_bias=3.0,
+               aabb_min=UNIT_BOX_MIN, aabb_max=UNIT_BOX_MAX) -> Field:
+    """Hash-grid field of the paper's default Instant-NGP shape: seeded table
+    U(-0.5, 0.5) in FP16, seeded Xavier-uniform MLP 32 -> 64 -> 64 -> 4, and a
+    compact density support made of ``n_support`` seeded spheres whose
+    conservative cover is the occupancy bitfield."""
+    T = 1 << log2_T
+    rng_t = _rng(config, 1)
+    table = rng_t.uniform(-0.5, 0.5, size=(n_levels, T, n_feat)).astype(np.float16)
+    rng_w = _rng(config, 2)
+    d_in = n_levels * n_feat
+
+    def xavier(o, i):
+        a = math.sqrt(6.0 / (i + o))
+        return f32(rng_w.uniform(-a, a, size=(o, i)))
+
+    w1, w2, w3 = xavier(width, d_in), xavier(width, width), xavier(4, width)
+    b3 = f32([sigma_bias, 0, 0, 0])
+    rng_s = _rng(config, 3)
+    sc = f32(rng_s.uniform(-support_c, support_c, size=(n_support, 3)))
+    sr = f32(rng_s.uniform(support_r[0], support_r[1], size=(n_support,)))
+    occ = occupancy_from_spheres(sc, sr, occ_res, aabb_min, aabb_max, margin=1e-4)
+    return Field(kind=FIELD_HASH, aabb_min=f32(aabb_min), aabb_max=f32(aabb_max),
+                 level_res=level_resolutions(n_levels, n_min, n_max), log2_table_size=log2_T,
+                 n_features=n_feat, table=np.ascontiguousarray(table),
+                 w1=w1, b1=f32(np.zeros(width)), w2=w2, b2=f32(np.zeros(width)), w3=w3, b3=b3,
+                 support_center=sc, support_radius=sr, occ_res=occ_res, occ_bits=occ)
+
+
+# ---------------------------------------------------------------------------
+# configurations
+# ---------------------------------------------------------------------------
+def default_camera(width: int, height: int) -> Camera:
+    return Camera(pos=f32([0.0, 0.3, 1.6]), look_at=f32([0, 0, 0]), up=f32([0, 1, 0]),
+                  vfov_deg=45.0, width=width, height=height)
+
+
+def config1(width: int = 64, height: int = 64) -> Scene:
+    """Plain method, analytic field: 8 seeded Gaussian blobs (radius U(0.05,0.15),
+    peak sigma 50, constant linear-HDR emission U(0,4)) in [-1/2,1/2]^3, one
+    12-triangle perfect-mirror cube of half-size 0.2 at the origin, 4 segments per
+    path, 128 midpoint samples per segment."""
+    rng = _rng(1, 0)
+    centers = rng.uniform(-0.35, 0.35, size=(8, 3))
+    radii = rng.uniform(0.05, 0.15, size=8)
+    emission = rng.uniform(0.0, 4.0, size=(8, 3))
+    field = gauss_field(centers, radii, np.full(8, 50.0), emission)
+    mesh = box_mesh([0, 0, 0], 0.2, 0)
+    return Scene(name="c1_gauss_mirror_64", camera=default_camera(width, height), field=field, mesh=mesh,
+                 materials=[Material(MAT_MIRROR, (1.0, 1.0, 1.0))], lights=[],
+                 opts=RenderOpts(max_bounces=4, spp=1, seed=1, steps_per_segment=128, tau=0.0))
+
+
+DT_C2 = float(np.float32(math.sqrt(3.0) / 1024.0))
+
+
+def config2(width: int = 800, height: int = 800, tau: float = 0.0, max_bounces: int = 8) -> Scene:
+    """Hash-grid field (16 levels, 2^19 entries, 2 FP16 features, resolutions 16..2048,
+    MLP 32-64-64-4 with exp density and softplus radiance), 128^3 occupancy, a
+    10,240-triangle glass sphere (IOR 1.5), a mirror cube, a diffuse floor and one
+    point light; up to 8 segments per path, fixed step sqrt(3)/1024."""
+    field = hash_field(2)
+    glass = glass_icosphere_10240([0.2, 0.0, 0.0], 0.15, 1)
+    cube = box_mesh([-0.2, 0.0, 0.0], 0.1, 0)
+    floor = quad_mesh([-0.5, -0.45, -0.5], [-0.5, -0.45, 0.5], [0.5, -0.45, 0.5], [0.5, -0.45, -0.5], 2)
+    mesh = merge_meshes([glass, cube, floor])
+    mats = [Material(MAT_MIRROR, (1.0, 1.0, 1.0)), Material(MAT_GLASS, ior=1.5),
+            Material(MAT_DIFFUSE, (0.5, 0.5, 0.5))]
+    lights = [Light(pos=(0.0, 0.45, 0.3), intensity=(2.0, 2.0, 2.0))]
+    return Scene(name=f"c2_hash_glass_{width}x{height}", camera=default_camera(width, height), field=field,
+                 mesh=mesh, materials=mats, lights=lights,
+                 opts=RenderOpts(max_bounces=max_bounces, spp=1, seed=2, steps_per_segment=0, dt=DT_C2,
+                                 tau=tau))
+
+
+def explicit_rays(scene: Scene, origins, dirs) -> Scene:
+    """Copy of ``scene`` traced along the given rays instead of its camera."""
+    d = np.asarray(dirs, np.float64)
+    d = d / np.linalg.norm(d, axis=1, keepdims=True)
+    return Scene(name=scene.name + "_rays", camera=scene.camera, field=scene.field, mesh=scene.mesh,
+                 materials=scene.materials, lights=scene.lights, opts=scene.opts,
+                 ray_o=f32(np.reshape(origins, (-1, 3))), ray_d=f32(d))
+
+
+def strided_pixels(width: int, height: int, stride: int, offset: int = 0) -> np.ndarray:
+    """Pixel indices (y*width + x) of every ``stride``-th row and column."""
+    ys = np.arange(offset % stride, height, stride)
+    xs = np.arange(offset % stride, width, stride)
+    return np.ascontiguousarray((ys[:, None] * width + xs[None, :]).reshape(-1).astype(np.uint32))

@@ -1,0 +1,221 @@
+"""Closed-form pins of the oracle's march, compositing and whole paths
+(Eqs. 10-13 and Algorithm 1 of the paper)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2309_04581_gb300 import scenes as S
+
+
+def F(v):
+    """The FP32 value the scene stores for v (scenes hold FP32 geometry)."""
+    return np.float64(np.float32(v))
+
+
+def _const_scene(sigma, rgb, **opts):
+    sc = S.config1()
+    sc.field = S.const_field(sigma, rgb)
+    sc.mesh = S.empty_mesh()
+    sc.materials = []
+    for k, v in opts.items():
+        setattr(sc.opts, k, v)
+    return sc
+
+
+@pytest.mark.parametrize("mode", ["steps", "dt"])
+def test_homogeneous_slab(orc, mode):
+    # T = exp(-sigma l), L = e (1 - exp(-sigma l)) exactly, for any step rule
+    sigma, e = 3.7, np.array([0.5, 1.25, 2.0])
+    sc = _const_scene(sigma, e, steps_per_segment=128 if mode == "steps" else 0, dt=0.0137)
+    osc = orc.OracleScene(sc)
+    o, d = np.array([0.1, -0.2, 0.9]), np.array([0.0, 0.0, -1.0])
+    T, L = orc.march(osc, o, d, 0.0, math.inf)
+    l = 1.0   # box z from 0.5 to -0.5
+    assert np.allclose(T, math.exp(-sigma * l), rtol=1e-13)
+    assert np.allclose(L, e * (1 - math.exp(-sigma * l)), rtol=1e-13)
+    # oblique ray, segment cut by a hit at t = 0.7 (ragged last interval)
+    d2 = np.array([0.3, 0.4, -0.866])
+    d2 /= np.linalg.norm(d2)
+    T, L = orc.march(osc, o, d2, 0.0, 0.7)
+    ok, t0, t1 = orc.box_interval(osc, o, d2)
+    lseg = min(0.7, t1) - max(0.0, t0)
+    assert np.allclose(T, math.exp(-sigma * lseg), rtol=1e-13)
+    assert np.allclose(L, e * (1 - math.exp(-sigma * lseg)), rtol=1e-12)
+
+
+def test_throughput_carries_into_segment(orc):
+    # T(t) = T(p_j) exp(-int sigma): an incoming throughput scales the segment's radiance
+    sc = _const_scene(2.0, [1, 1, 1], steps_per_segment=16)
+    osc = orc.OracleScene(sc)
+    Tin = np.array([0.5, 0.25, 1.0])
+    T, L = orc.march(osc, [0, 0, 0.9], [0, 0, -1], 0.0, math.inf, T=Tin, L=[0.1, 0.2, 0.3])
+    q = math.exp(-2.0)
+    assert np.allclose(T, Tin * q, rtol=1e-13)
+    assert np.allclose(L, np.array([0.1, 0.2, 0.3]) + Tin * (1 - q), rtol=1e-13)
+
+
+def _single_blob(center, r, peak=50.0, emission=(1.0, 1.0, 1.0)):
+    sc = S.config1()
+    sc.field = S.gauss_field([center], [r], [peak], [emission])
+    sc.mesh = S.empty_mesh()
+    sc.materials = []
+    return sc
+
+
+def _gauss_depth_closed_form(peak, r, dperp2, s0, s1):
+    # int_{s0}^{s1} peak exp(-(dperp^2 + s^2) / (2 r^2)) ds via erf
+    k = r * math.sqrt(2.0)
+    return peak * math.exp(-dperp2 / (2 * r * r)) * r * math.sqrt(math.pi / 2) * (
+        math.erf(s1 / k) - math.erf(s0 / k))
+
+
+def test_single_gaussian_midpoint_rule_within_error_bound(orc):
+    # The ray starts at the blob's inflection point and runs 0.35 through it.
+    # The 128-sample midpoint rule must agree with the erf closed form within
+    # the midpoint bound (b - a) h^2 / 24 max|f''|; a left-endpoint rule misses
+    # that bound, so a half-step shift of the samples fails this test.
+    r, peak = 0.1, 50.0
+    c = np.array([0.0, 0.05, 0.0])
+    sc = _single_blob(c, r, peak)
+    sc.opts.steps_per_segment = 128
+    osc = orc.OracleScene(sc)
+    o = c + np.array([0.0, 0.0, r])       # distance r from the centre along the ray axis
+    d = np.array([0.0, 0.0, -1.0])
+    a, b = 0.0, 0.35
+    T = orc.transmittance(osc, o, d, a, b)
+    # the ray passes through the centre: s measured from the centre, s = t - r
+    exact = _gauss_depth_closed_form(peak, r, 0.0, a - r, b - r)
+    h = (b - a) / 128
+    f2max = peak / r ** 2          # max |d^2/ds^2 peak exp(-s^2/2r^2)| = peak / r^2 at s = 0
+    bound = (b - a) * h * h / 24 * f2max
+    assert abs(-math.log(T) - exact) <= bound
+    # the discriminating check: a left-endpoint rule is off by more than the bound
+    ts = a + h * np.arange(128)
+    left = sum(peak * math.exp(-((t - r) ** 2) / (2 * r * r)) * h for t in ts)
+    assert abs(left - exact) > 3 * bound
+
+
+def test_constant_colour_telescopes(orc):
+    # For any sigma profile with constant radiance e: L = e (1 - T_final)
+    e = np.array([2.0, 0.5, 1.5])
+    sc = _single_blob([0.05, -0.02, 0.01], 0.12, 40.0, e)
+    sc.opts.steps_per_segment = 77
+    osc = orc.OracleScene(sc)
+    T, L = orc.march(osc, [0.0, 0.0, 0.8], [0.05, -0.03, -1.0], 0.0, math.inf)
+    assert np.allclose(L, e * (1 - T), rtol=1e-13)
+
+
+def test_mirror_box_geometric_series(orc):
+    # Camera inside a closed mirror box (inner half-width 0.4, reflectance rho)
+    # filled with a homogeneous field: the ray runs along z, so segment 1 has
+    # length a = 0.4 - z0 and every later one W = 0.8.  After k segments
+    #   L = e (1 - q_a) + e (1 - q) rho q_a sum_{i<k-1} (rho q)^i,  T = q_a rho^(k-1) q^(k-1).
+    sigma, rho = 1.3, 0.9
+    e = np.array([1.0, 2.0, 0.5])
+    sc = _const_scene(sigma, e, steps_per_segment=64)
+    sc.mesh = S.box_mesh([0, 0, 0], 0.4, 0, inward=True)
+    sc.materials = [S.Material(S.MAT_MIRROR, (rho, rho, rho))]
+    z0 = 0.1
+    for k in (1, 2, 5, 9):
+        sc.opts.max_bounces = k
+        sck = S.explicit_rays(sc, [[0.11, 0.137, z0]], [[0.0, 0.0, 1.0]])
+        res = orc.render(sck)
+        w = F(0.4)
+        qa, q = math.exp(-F(sigma) * (w - F(z0))), math.exp(-F(sigma) * 2 * w)
+        r = F(rho)
+        L = e * (1 - qa) + e * (1 - q) * r * qa * sum((r * q) ** i for i in range(k - 1))
+        assert np.allclose(res["rgba"][0, :3], L, rtol=1e-12)
+        assert res["segments"][0, 0] == k
+        assert res["flags"][0] == 0
+        # hits alternate between the z+ and z- walls
+        tri = res["tri"][0, 0, :k]
+        walls = [int(t) // 2 for t in tri]
+        assert walls == [1 if j % 2 == 0 else 0 for j in range(k)]
+
+
+def _floor_scene(sigma=0.0, occluder=False, albedo=0.5, I=2.0):
+    sc = _const_scene(sigma, [0.0, 0.0, 0.0], steps_per_segment=0, dt=0.01)
+    meshes = [S.quad_mesh([-0.5, -0.45, -0.5], [-0.5, -0.45, 0.5], [0.5, -0.45, 0.5], [0.5, -0.45, -0.5], 0)]
+    if occluder:
+        meshes.append(S.quad_mesh([-0.4, 0.1, -0.15], [-0.4, 0.1, 0.15], [-0.1, 0.1, 0.15], [-0.1, 0.1, -0.15], 0))
+    sc.mesh = S.merge_meshes(meshes)
+    sc.materials = [S.Material(S.MAT_DIFFUSE, (albedo, albedo, albedo))]
+    sc.lights = [S.Light(pos=(0.0, 0.45, 0.0), intensity=(I, I, I))]
+    sc.opts.max_bounces = 1
+    return sc
+
+
+def test_shadow_ray_point_light_closed_form(orc):
+    # Camera ray straight down onto a Lambertian floor, one segment: the only
+    # radiance is the next-event term (albedo/pi) cos I / D^2 * V * exp(-sigma l).
+    x, z = 0.13, -0.07
+    p = np.array([F(x), F(-0.45), F(z)])
+    lp = np.array([0.0, F(0.45), 0.0])
+    D = np.linalg.norm(lp - p)
+    cos = (lp - p)[1] / D
+    for sigma in (0.0, 0.8):
+        sc = S.explicit_rays(_floor_scene(sigma), [[x, 0.3, z]], [[0, -1, 0]])
+        res = orc.render(sc)
+        # field transmittance along the camera segment (0.3 -> -0.45 inside the box)
+        t_cam = math.exp(-F(sigma) * (F(0.3) - F(-0.45)))
+        # the shadow ray runs from the floor to the light; the box ends at y = 0.5 > 0.45
+        expect = t_cam * 0.5 / math.pi * cos * 2.0 / D ** 2 * math.exp(-F(sigma) * D)
+        assert np.allclose(res["rgba"][0, :3], expect, rtol=1e-12)
+        assert res["counts"]["shadow_rays"] == 1
+    # an occluder (x in [-0.4, -0.1], y = 0.1) between floor and light blocks the term
+    sc = S.explicit_rays(_floor_scene(0.0, occluder=True), [[0.3, 0.3, 0.0]], [[0, -1, 0]])
+    assert orc.render(sc)["rgba"][0, :3].max() > 0    # shadow ray passes x = 0.117 at y = 0.1
+    d = np.array([0.0, -0.15, -0.3])
+    sc = S.explicit_rays(_floor_scene(0.0, occluder=True), [[-0.35, -0.3, 0.3]], [d])
+    res = orc.render(sc)
+    hitp = np.array([-0.35, -0.3, 0.3]) + res["t"][0, 0, 0] * d / np.linalg.norm(d)
+    assert np.allclose(hitp, [-0.35, -0.45, 0.0], atol=1e-7)
+    assert np.all(res["rgba"][0, :3] == 0.0)          # shadow ray passes x = -0.136 at y = 0.1
+
+
+def test_glass_plate_normal_incidence(orc):
+    # A glass plate (two inward-facing quads) hit at normal incidence: with the
+    # Fresnel draw above F = 0.04 both times, the ray passes straight through
+    # with its throughput unchanged, so L equals the slab closed form for the
+    # whole box length.  The draw comes from numpy's Philox (the same stream).
+    sigma, e = 0.9, np.array([1.0, 0.5, 0.25])
+    sc = _const_scene(sigma, e, steps_per_segment=32)
+    plate = S.merge_meshes([
+        S.quad_mesh([-0.5, -0.5, 0.1], [0.5, -0.5, 0.1], [0.5, 0.5, 0.1], [-0.5, 0.5, 0.1], 0),
+        S.quad_mesh([-0.5, -0.5, -0.1], [-0.5, 0.5, -0.1], [0.5, 0.5, -0.1], [0.5, -0.5, -0.1], 0)])
+    sc.mesh = plate
+    sc.materials = [S.Material(S.MAT_GLASS, ior=1.5)]
+    sc.opts.max_bounces = 3
+    xs = [[0.1 + 0.01 * i, 0.23, 0.7] for i in range(12)]
+    scr = S.explicit_rays(sc, xs, [[0, 0, -1]] * len(xs))
+    res = orc.render(scr)
+    from tests.test_oracle_units import _numpy_philox_block
+    n_checked = 0
+    for i in range(len(xs)):
+        u1 = int(_numpy_philox_block((i, 0, 1, 0), (sc.opts.seed, 0))[0] >> np.uint64(40)) / 2**24
+        u2 = int(_numpy_philox_block((i, 0, 2, 0), (sc.opts.seed, 0))[0] >> np.uint64(40)) / 2**24
+        if u1 >= 0.04 and u2 >= 0.04:
+            n_checked += 1
+            assert np.allclose(res["rgba"][i, :3], e * (1 - math.exp(-F(sigma) * 1.0)), rtol=1e-12)
+            assert res["segments"][i, 0] == 3
+        elif u1 < 0.04:
+            # reflected straight back out of the box: two segments of length 0.4
+            q = math.exp(-F(sigma) * (0.5 - F(0.1)))
+            assert np.allclose(res["rgba"][i, :3], e * (1 - q) + q * e * (1 - q), rtol=1e-12)
+    assert n_checked >= 8
+
+
+def test_invariants_on_config_scenes(orc):
+    for sc, ids in [(S.config1(), None), (S.config2(96, 96), S.strided_pixels(96, 96, 3))]:
+        res = orc.render(sc, ids)
+        rgb = res["rgba"][:, :3]
+        assert np.all(np.isfinite(rgb)) and np.all(rgb >= 0)
+        assert np.all((res["rgba"][:, 3] >= 0) & (res["rgba"][:, 3] <= 1))
+        assert res["segments"].max() <= sc.opts.max_bounces and res["segments"].min() >= 1
+        assert (res["flags"] != 0).mean() < 0.01
+        # every recorded hit precedes the segment count; unused slots stay empty
+        for i in range(res["segments"].shape[0]):
+            k = res["segments"][i, 0]
+            assert np.all(res["tri"][i, 0, k:] == orc.NO_HIT)
+            assert np.all(res["tri"][i, 0, :k - 1] != orc.NO_HIT)
