@@ -1,0 +1,232 @@
+/*
+ * mrf.h - C ABI of the mesh-aware radiance-field renderer (GB300, sm_103a).
+ *
+ * The library renders the hybrid light-transport loop of "Dynamic Mesh-Aware
+ * Radiance Fields" (Qiao, Gao et al., ICCV 2023), Sec. 3.1 "Hybrid Rendering
+ * Algorithm" and its Algorithm 1: for every pixel a path alternates between
+ * marching a radiance field along a straight segment (Eqs. 10-11) and a
+ * surface event at a triangle mesh (Eqs. 12-13), with shadow rays toward the
+ * lights whose transmittance comes from the same field march.
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an mrf_status; no C++ exception crosses the ABI.
+ *    On failure a human-readable message is kept per thread: mrf_last_error().
+ *  - Array arguments may live in host or device memory unless stated; the
+ *    library finds out with cudaPointerGetAttributes.  Inputs of the create /
+ *    build / set calls are copied into library-owned device memory, so the
+ *    caller may free them as soon as the call returns.
+ *  - Handles belong to the context (and its CUDA device) that made them; they
+ *    are not thread-safe.  Destroy functions accept NULL.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Device work is enqueued on it and the call returns without
+ *    waiting, except where noted (host output buffers, statistics).
+ *  - Asynchronous device faults surface as MRF_ERR_CUDA from the next call.
+ */
+#ifndef MRF_H
+#define MRF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum mrf_status {
+    MRF_OK = 0,
+    MRF_ERR_INVALID_ARG = 1,  /* bad pointer, size, enum value or mismatched handle */
+    MRF_ERR_CUDA = 2,         /* a CUDA runtime call failed (message holds its text) */
+    MRF_ERR_OOM = 3,          /* device allocation failed */
+    MRF_ERR_TIMEOUT = 4,      /* a kernel gave up after its iteration budget */
+    MRF_ERR_NOT_READY = 5,    /* handle not initialised */
+    MRF_ERR_UNSUPPORTED = 6   /* feature not available on this device or build */
+} mrf_status;
+
+typedef struct mrf_context mrf_context;
+typedef struct mrf_field mrf_field;
+typedef struct mrf_bvh mrf_bvh;
+
+/* ---------------------------------------------------------------- context */
+/* Binds the calling thread to CUDA device `device` and creates a context that
+ * owns materials, lights, statistics counters and scratch memory.
+ * MRF_ERR_INVALID_ARG if `out` is NULL or the device does not exist;
+ * MRF_ERR_UNSUPPORTED if the device is not compute capability 10.3. */
+mrf_status mrf_context_create(int device, mrf_context **out);
+void mrf_context_destroy(mrf_context *ctx);
+/* Thread-local text of the last failure (never NULL, "" if none). */
+const char *mrf_last_error(void);
+/* Library version as "major.minor.patch". */
+const char *mrf_version(void);
+
+/* ------------------------------------------------------------------ field */
+/* The radiance field: density sigma(p) and linear-HDR radiance r(p) on the
+ * axis-aligned box [aabb_min, aabb_max] (sigma = 0 outside), the field of
+ * Eq. 7 / Eq. 9 of the paper, trained there with HDR images (Sec. 3.1,
+ * "Unifying color space").  Three kinds:
+ *   CONST    : sigma = const_sigma, r = const_rgb.
+ *   GAUSS    : sigma = sum_k peak_k exp(-|p - c_k|^2 / (2 radius_k^2)),
+ *              r = sum_k sigma_k emission_k / sigma (emission-weighted mix).
+ *   HASHGRID : the Instant-NGP field the paper renders (Sec. 3.3): a
+ *              multiresolution hash encoding (n_levels levels, 2^log2_table_size
+ *              entries of n_features FP16 values per level, per-level grid
+ *              resolution level_res[l]; dense row-major indexing when
+ *              (N_l + 1)^3 fits the table, else the spatial hash
+ *              x ^ y*2654435761 ^ z*805459861 mod T; trilinear interpolation),
+ *              feeding an MLP in -> width -> width -> 4 with ReLU hidden layers:
+ *              sigma = support(p) * exp(min(o0, 15)), r = softplus(o1..3).
+ *              support(p) = max_k max(0, 1 - |p - s_k|^2 / rs_k^2) over the
+ *              support spheres gives the density its compact support.
+ *              occ_bits is a conservative occupancy bitfield (occ_res^3 bits,
+ *              cell x + R*(y + R*z), word i>>5 bit i&31) covering the support;
+ *              the renderer skips samples in empty cells.
+ * Layouts: blob_center (n_blobs x 3), blob_emission (n_blobs x 3), table
+ * [level][entry][feature] as IEEE binary16 bits, w1 (width x in) row-major,
+ * w2 (width x width), w3 (4 x width), in = n_levels * n_features (<= 64),
+ * width = 64.  `precision` selects the MLP arithmetic of the tensor-core
+ * engine (MRF_PREC_FP16 / BF16 operands with FP32 accumulation); FP32 runs the
+ * whole network in FP32 on the CUDA cores. */
+enum { MRF_FIELD_CONST = 0, MRF_FIELD_GAUSS = 1, MRF_FIELD_HASHGRID = 2 };
+enum { MRF_PREC_FP32 = 0, MRF_PREC_FP16 = 1, MRF_PREC_BF16 = 2 };
+
+typedef struct mrf_field_desc {
+    int32_t kind;
+    float aabb_min[3], aabb_max[3];
+    /* CONST */
+    float const_sigma, const_rgb[3];
+    /* GAUSS */
+    uint32_t n_blobs;
+    const float *blob_center, *blob_radius, *blob_peak, *blob_emission;
+    /* HASHGRID */
+    uint32_t n_levels, log2_table_size, n_features;
+    const uint32_t *level_res;
+    const uint16_t *table;
+    uint32_t mlp_width;
+    const float *w1, *b1, *w2, *b2, *w3, *b3;
+    uint32_t n_support;
+    const float *support_center, *support_radius;
+    uint32_t occ_res;              /* 0 = no occupancy grid (every sample evaluated) */
+    const uint32_t *occ_bits;
+    int32_t precision;
+} mrf_field_desc;
+
+/* Copies the description into device memory.  MRF_ERR_INVALID_ARG for an
+ * unknown kind, an empty box, n_levels * n_features > 64, mlp_width != 64,
+ * occ_res not a multiple of 8 or > 1024, or a NULL array the kind needs. */
+mrf_status mrf_field_create(mrf_context *ctx, const mrf_field_desc *desc, mrf_field **out);
+void mrf_field_destroy(mrf_field *field);
+/* Changes the MLP precision of an existing HASHGRID field. */
+mrf_status mrf_field_set_precision(mrf_field *field, int32_t precision);
+
+/* Evaluates sigma and r at n points (n x 3, FP32) into out (n x 4: sigma, r, g, b),
+ * FP32 path.  points and out must be device pointers.  For tests of the field
+ * alone (Eq. 7 / hash encoding / MLP). */
+mrf_status mrf_field_query(mrf_context *ctx, const mrf_field *field, const float *points, uint32_t n, float *out,
+                           void *stream);
+
+/* -------------------------------------------------------------------- BVH */
+/* Builds a bounding-volume hierarchy over a triangle mesh for the ray-casting
+ * function t(p, w) of Eq. 3 (the paper does not name its acceleration
+ * structure; this one is a binned-SAH binary BVH built on the host, 64-byte
+ * nodes holding both children's boxes, leaves of at most 4 triangles).
+ * verts: n_verts x 3 FP32; tris: n_tris x 3 vertex indices; mat_id: n_tris
+ * material indices into the table of mrf_materials_set.  Triangle ids reported
+ * by the renderer are indices into `tris`.  n_tris may be 0 (no meshes).
+ * MRF_ERR_INVALID_ARG for an index >= n_verts or a NULL array with n > 0. */
+mrf_status mrf_bvh_build(mrf_context *ctx, const float *verts, uint32_t n_verts, const uint32_t *tris,
+                         const uint32_t *mat_id, uint32_t n_tris, mrf_bvh **out);
+/* Refits the BVH boxes to moved vertices (same topology; the dynamic meshes of
+ * Sec. 3.2 change their vertices every simulation step).  verts: n_verts x 3,
+ * n_verts must equal the build's (else MRF_ERR_INVALID_ARG).  Runs on `stream`. */
+mrf_status mrf_bvh_refit(mrf_bvh *bvh, const float *verts, uint32_t n_verts, void *stream);
+void mrf_bvh_destroy(mrf_bvh *bvh);
+
+/* Closest hit of n rays (origins, dirs: n x 3 FP32 device arrays; dirs need
+ * not be unit) against the mesh: out_t (FP32, +inf on a miss) and out_tri
+ * (0xFFFFFFFF on a miss), skipping triangle skip[i] if skip is non-NULL, with
+ * t > tmin.  Same traversal as the renderer. */
+mrf_status mrf_cast(mrf_context *ctx, const mrf_bvh *bvh, const float *origins, const float *dirs,
+                    const uint32_t *skip, uint32_t n, float tmin, float *out_t, uint32_t *out_tri, void *stream);
+
+/* -------------------------------------------------------- materials/lights */
+/* BSDFs of the paper's Sec. 3.3: reflective (perfect mirror, T *= rgb),
+ * refractive (smooth dielectric of index `ior`, exact unpolarised Fresnel
+ * choice between reflection and Snell refraction, T unchanged) and Lambertian
+ * (cosine-weighted sampling, T *= rgb albedo). */
+enum { MRF_MAT_MIRROR = 0, MRF_MAT_GLASS = 1, MRF_MAT_DIFFUSE = 2 };
+typedef struct mrf_material {
+    int32_t kind;
+    float rgb[3];
+    float ior;
+} mrf_material;
+/* Point lights with RGB intensity I: a diffuse hit at distance D receives
+ * (albedo / pi) cos I / D^2 times visibility and field transmittance
+ * (the shadow rays of Sec. 3.1, "Shadow rays"). */
+enum { MRF_LIGHT_POINT = 0 };
+typedef struct mrf_light {
+    int32_t kind;
+    float pos[3];
+    float intensity[3];
+} mrf_light;
+/* Replace the context's material / light tables (host or device arrays, n <= 65535). */
+mrf_status mrf_materials_set(mrf_context *ctx, const mrf_material *mats, uint32_t n);
+mrf_status mrf_lights_set(mrf_context *ctx, const mrf_light *lights, uint32_t n);
+
+/* ----------------------------------------------------------------- render */
+/* Pinhole camera: ray from `pos` through the centre of pixel (x, y), row 0 at
+ * the top; vfov_deg is the full vertical field of view. */
+typedef struct mrf_camera {
+    float pos[3], look_at[3], up[3];
+    float vfov_deg;
+    uint32_t width, height;
+} mrf_camera;
+
+/* The primary rays: a camera (count = width * height, ray index = y * width + x)
+ * or explicit FP32 origins / directions (count x 3, host or device). */
+typedef struct mrf_rays {
+    const mrf_camera *camera;
+    const float *origins, *dirs;
+    uint32_t count;
+    uint32_t spp;                  /* paths per ray (>= 1) */
+} mrf_rays;
+
+enum { MRF_ENGINE_AUTO = 0, MRF_ENGINE_MEGAKERNEL = 1, MRF_ENGINE_WAVEFRONT = 2 };
+
+typedef struct mrf_render_opts {
+    uint64_t seed;                 /* Philox4x64-10 key word 0 */
+    uint32_t steps_per_segment;    /* > 0: that many midpoint samples per segment */
+    float dt;                      /* steps_per_segment == 0: fixed step, last interval clipped */
+    float tau;                     /* end a path when max(T) < tau (0 = never) */
+    float tmin;                    /* smallest accepted ray-triangle distance */
+    int32_t engine;                /* MRF_ENGINE_* */
+    /* optional per-path records, device pointers or NULL:
+     * rec_segments[count * spp], rec_tri / rec_t[count * spp * max_bounces] */
+    uint32_t *rec_segments;
+    uint32_t *rec_tri;
+    float *rec_t;
+} mrf_render_opts;
+
+typedef struct mrf_stats {
+    uint64_t paths, segments, surface_hits, shadow_rays;
+    uint64_t samples_nominal;      /* quadrature samples on all marched segments */
+    uint64_t samples_evaluated;    /* samples in occupied cells (field network run) */
+    uint64_t shadow_samples_evaluated;
+    uint64_t fp64_retests;         /* near-edge triangle tests redone in FP64 */
+    uint64_t status;               /* device status word (0 = ok) */
+} mrf_stats;
+
+/* Renders every path of `rays` (Algorithm 1) with at most max_bounces
+ * segments per path (the camera segment counts as the first), writing
+ * out_hdr[4 * i + c] = mean over spp of the linear-HDR radiance L (c < 3) and
+ * the camera segment's field opacity (c = 3).  out_hdr is count x 4 FP32; if
+ * it is host memory the call copies the image back and waits.  If `stats` is
+ * non-NULL the call waits and fills it.  MRF_ERR_INVALID_ARG for NULL
+ * handles, count == 0, spp == 0, max_bounces == 0 or > 64, or records with a
+ * host pointer. */
+mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *bvh, const mrf_rays *rays,
+                      uint32_t max_bounces, const mrf_render_opts *opts, float *out_hdr, void *stream,
+                      mrf_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRF_H */

@@ -57,7 +57,7 @@ class OrcScene(C.Structure):
         ("n_lights", C.c_uint32), ("light_pos", _fp), ("light_I", _fp),
         ("max_bounces", C.c_uint32), ("spp", C.c_uint32), ("seed", C.c_uint64),
         ("steps_per_segment", C.c_uint32), ("dt", C.c_float), ("tau", C.c_float), ("tmin", C.c_float),
-        ("margin_bary", C.c_double), ("margin_t", C.c_double), ("margin_fresnel", C.c_double),
+        ("margin_dist", C.c_double), ("margin_t", C.c_double), ("margin_fresnel", C.c_double),
     ]
 
 
@@ -118,7 +118,7 @@ def _ptr(a, t):
 class OracleScene:
     """A ``scenes.Scene`` marshalled into an ``orc_scene`` (keeps its arrays alive)."""
 
-    def __init__(self, scene, margin_bary=1e-5, margin_t=1e-5, margin_fresnel=1e-5):
+    def __init__(self, scene, margin_dist=1e-6, margin_t=1e-5, margin_fresnel=1e-5):
         self.scene = scene
         keep = []
 
@@ -182,7 +182,7 @@ class OracleScene:
         o = scene.opts
         s.max_bounces, s.spp, s.seed = o.max_bounces, o.spp, o.seed
         s.steps_per_segment, s.dt, s.tau, s.tmin = o.steps_per_segment, o.dt, o.tau, o.tmin
-        s.margin_bary, s.margin_t, s.margin_fresnel = margin_bary, margin_t, margin_fresnel
+        s.margin_dist, s.margin_t, s.margin_fresnel = margin_dist, margin_t, margin_fresnel
         self.s = s
         self._keep = keep
 

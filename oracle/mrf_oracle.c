@@ -32,8 +32,9 @@
  *    (ray, spp, segment, 0), key (seed, 0); uniforms from the top 24 bits.
  *
  * Ambiguity flags mark pixels whose path contains a discrete decision within a
- * small margin of its threshold (a near-edge triangle, a t tie, a Fresnel draw
- * next to F, ...); FP32 and FP64 may legitimately decide those differently.
+ * small margin of its threshold (a hit point within margin_dist world units of
+ * a triangle edge, a t tie, a Fresnel draw next to F, ...); FP32 and FP64 may
+ * legitimately decide those differently.
  */
 #define _DEFAULT_SOURCE
 #include <math.h>
@@ -93,7 +94,7 @@ typedef struct {
     uint32_t steps_per_segment;
     float dt, tau, tmin;
 
-    double margin_bary, margin_t, margin_fresnel;
+    double margin_dist, margin_t, margin_fresnel;
 } orc_scene;
 
 /* per-thread counters: segments, shadow rays, nominal samples, samples with
@@ -406,6 +407,19 @@ static void tri_verts(const orc_scene *sc, uint32_t i, double v0[3], double v1[3
     }
 }
 
+/* Signed distance (world units) from the ray's hit point on the triangle's
+ * plane to the nearest edge line: barycentric b_i times the altitude from
+ * vertex i.  Negative outside the triangle. */
+static double edge_distance(const double v0[3], const double v1[3], const double v2[3], double b1, double b2) {
+    v3 a = fv3(v0), b = fv3(v1), c = fv3(v2);
+    double area2 = sqrt(dot(cross(sub(b, a), sub(c, a)), cross(sub(b, a), sub(c, a))));
+    double l0 = sqrt(dot(sub(c, b), sub(c, b))), l1 = sqrt(dot(sub(c, a), sub(c, a))),
+           l2 = sqrt(dot(sub(b, a), sub(b, a)));
+    double d0 = (1.0 - b1 - b2) * area2 / l0, d1 = b1 * area2 / l1, d2 = b2 * area2 / l2;
+    double m = d0 < d1 ? d0 : d1;
+    return d2 < m ? d2 : m;
+}
+
 /* Closest hit by brute force over every triangle (the ray-casting function of
  * Eq. 3), skipping the triangle the ray leaves.  Ties within 1e-12 relative go
  * to the lower id.  Sets ORC_FLAG_EDGE / ORC_FLAG_TMIN when a triangle whose
@@ -414,17 +428,16 @@ uint32_t orc_closest_hit(const orc_scene *sc, const double o[3], const double d[
                          uint32_t *flags) {
     double best = INFINITY, second = INFINITY, edge_t = INFINITY, tmin_t = INFINITY;
     uint32_t best_id = ORC_NO_HIT;
-    const double mb = sc->margin_bary;
+    const double md = sc->margin_dist;
     for (uint32_t i = 0; i < sc->n_tris; ++i) {
         if (i == skip) continue;
         double v0[3], v1[3], v2[3], t, b1, b2;
         tri_verts(sc, i, v0, v1, v2);
         int hit = orc_intersect_tri(o, d, v0, v1, v2, sc->tmin, &t, &b1, &b2);
         if (!isfinite(t)) continue;
-        double b0 = 1.0 - b1 - b2, bmin = b0 < b1 ? b0 : b1;
-        if (b2 < bmin) bmin = b2;
-        if (bmin >= -mb && bmin <= mb && t > sc->tmin && t < edge_t) edge_t = t;
-        if (bmin >= -mb && fabs(t - sc->tmin) <= 1e-3 * sc->tmin + 1e-9 && t < tmin_t) tmin_t = t;
+        double ed = edge_distance(v0, v1, v2, b1, b2);
+        if (fabs(ed) <= md && t > sc->tmin && t < edge_t) edge_t = t;
+        if (ed >= -md && fabs(t - sc->tmin) <= md && t < tmin_t) tmin_t = t;
         if (!hit) continue;
         if (t < best || (fabs(t - best) <= 1e-12 * best && i < best_id)) {
             if (best_id != ORC_NO_HIT) second = best < second ? best : second;
@@ -445,17 +458,15 @@ uint32_t orc_closest_hit(const orc_scene *sc, const double o[3], const double d[
 static int occluded(const orc_scene *sc, const double o[3], const double d[3], uint32_t skip, double dist,
                     uint32_t *flags) {
     int blocked = 0;
-    const double mb = sc->margin_bary;
+    const double md = sc->margin_dist;
     for (uint32_t i = 0; i < sc->n_tris; ++i) {
         if (i == skip) continue;
         double v0[3], v1[3], v2[3], t, b1, b2;
         tri_verts(sc, i, v0, v1, v2);
         int hit = orc_intersect_tri(o, d, v0, v1, v2, sc->tmin, &t, &b1, &b2);
         if (!isfinite(t)) continue;
-        double b0 = 1.0 - b1 - b2, bmin = b0 < b1 ? b0 : b1;
-        if (b2 < bmin) bmin = b2;
         if (t > sc->tmin && t < dist * (1.0 + sc->margin_t)) {
-            if (bmin >= -mb && bmin <= mb) *flags |= ORC_FLAG_SHADOW;
+            if (fabs(edge_distance(v0, v1, v2, b1, b2)) <= md) *flags |= ORC_FLAG_SHADOW;
             if (hit && fabs(t - dist) <= sc->margin_t * dist) *flags |= ORC_FLAG_SHADOW;
         }
         if (hit && t < dist) blocked = 1;

@@ -1,0 +1,631 @@
+// The C ABI of include/mrf.h: argument checks, device memory ownership and
+// kernel dispatch.  No C++ exception crosses the boundary.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "common.h"
+
+namespace mrf {
+void bvh_build_host(const float *verts, const uint32_t *tris, uint32_t n_tris, std::vector<float> &nodes,
+                    std::vector<uint32_t> &order, std::vector<int> &parent);
+cudaError_t launch_render_wavefront(const RenderParams &P, void *scratch, size_t scratch_bytes, cudaStream_t s);
+size_t wavefront_scratch_bytes(const RenderParams &P);
+bool wavefront_available();
+}  // namespace mrf
+
+using namespace mrf;
+
+static thread_local std::string g_err;
+
+static mrf_status fail(mrf_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+static mrf_status cuda_fail(cudaError_t e, const char *what) {
+    cudaGetLastError();  // clear a sticky-free error so later calls start clean
+    return fail(e == cudaErrorMemoryAllocation ? MRF_ERR_OOM : MRF_ERR_CUDA, "%s: %s (%s)", what,
+                cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+#define CUDA_TRY(expr, what)                         \
+    do {                                             \
+        cudaError_t e_ = (expr);                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+struct mrf_context {
+    int device = 0;
+    MaterialDev *mats = nullptr;
+    int n_mats = 0;
+    LightDev *lights = nullptr;
+    int n_lights = 0;
+    unsigned long long *stats = nullptr;
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+};
+
+struct mrf_field {
+    mrf_context *ctx = nullptr;
+    FieldDev dev{};
+    std::vector<void *> allocs;
+};
+
+struct mrf_bvh {
+    mrf_context *ctx = nullptr;
+    BvhDev dev{};
+    float4 *nodes = nullptr, *tris = nullptr;
+    uint32_t *order = nullptr, *tri_idx = nullptr;
+    float *verts = nullptr;
+    int *parent = nullptr, *counters = nullptr;
+    uint32_t n_verts = 0, n_tris = 0;
+    int n_nodes = 0;
+};
+
+static bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+static mrf_status dev_alloc(T **p, size_t n, const char *what) {
+    *p = nullptr;
+    if (n == 0) return MRF_OK;
+    cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(e, what);
+    }
+    return MRF_OK;
+}
+
+// copy n elements from host or device memory into host vector
+template <class T>
+static mrf_status fetch(std::vector<T> &dst, const T *src, size_t n) {
+    dst.resize(n);
+    if (n == 0) return MRF_OK;
+    CUDA_TRY(cudaMemcpy(dst.data(), src, n * sizeof(T), cudaMemcpyDefault), "copy input");
+    return MRF_OK;
+}
+
+// Entry points keep the C linkage of their declarations in mrf.h.
+const char *mrf_last_error(void) { return g_err.c_str(); }
+const char *mrf_version(void) { return "0.1.0"; }
+
+mrf_status mrf_context_create(int device, mrf_context **out) {
+    if (!out) return fail(MRF_ERR_INVALID_ARG, "mrf_context_create: out is NULL");
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) return cuda_fail(e, "mrf_context_create: cudaGetDeviceCount");
+    if (device < 0 || device >= n) return fail(MRF_ERR_INVALID_ARG, "mrf_context_create: no device %d", device);
+    CUDA_TRY(cudaSetDevice(device), "mrf_context_create: cudaSetDevice");
+    cudaDeviceProp prop;
+    CUDA_TRY(cudaGetDeviceProperties(&prop, device), "mrf_context_create: cudaGetDeviceProperties");
+    if (!(prop.major == 10 && prop.minor == 3))
+        return fail(MRF_ERR_UNSUPPORTED, "mrf_context_create: device %d is sm_%d%d, the library is built for sm_103a",
+                    device, prop.major, prop.minor);
+    mrf_context *c = new (std::nothrow) mrf_context();
+    if (!c) return fail(MRF_ERR_OOM, "mrf_context_create: host allocation");
+    c->device = device;
+    mrf_status st = dev_alloc(&c->stats, ST_COUNT, "mrf_context_create: stats");
+    if (st != MRF_OK) {
+        delete c;
+        return st;
+    }
+    cudaMemset(c->stats, 0, sizeof(unsigned long long) * ST_COUNT);
+    *out = c;
+    return MRF_OK;
+}
+
+void mrf_context_destroy(mrf_context *c) {
+    if (!c) return;
+    cudaFree(c->mats);
+    cudaFree(c->lights);
+    cudaFree(c->stats);
+    cudaFree(c->scratch);
+    delete c;
+}
+
+// ------------------------------------------------------------------ field
+static void field_free(mrf_field *f) {
+    for (void *p : f->allocs) cudaFree(p);
+    f->allocs.clear();
+}
+
+template <class T>
+static mrf_status upload(mrf_field *f, const T *src, size_t n, const T **dst, const char *what) {
+    *dst = nullptr;
+    if (n == 0) return MRF_OK;
+    if (!src) return fail(MRF_ERR_INVALID_ARG, "mrf_field_create: %s is NULL", what);
+    T *d = nullptr;
+    mrf_status st = dev_alloc(&d, n, what);
+    if (st != MRF_OK) return st;
+    f->allocs.push_back(d);
+    CUDA_TRY(cudaMemcpy(d, src, n * sizeof(T), cudaMemcpyDefault), what);
+    *dst = d;
+    return MRF_OK;
+}
+
+static mrf_status field_create_impl(mrf_context *ctx, const mrf_field_desc *D, mrf_field *f) {
+    FieldDev &F = f->dev;
+    F.kind = D->kind;
+    for (int k = 0; k < 3; ++k) {
+        if (!(D->aabb_max[k] > D->aabb_min[k])) return fail(MRF_ERR_INVALID_ARG, "mrf_field_create: empty box");
+        F.lo[k] = D->aabb_min[k];
+        F.hi[k] = D->aabb_max[k];
+        F.ext_inv[k] = (float)(1.0 / ((double)D->aabb_max[k] - (double)D->aabb_min[k]));
+    }
+    F.precision = D->precision;
+    if (D->precision < MRF_PREC_FP32 || D->precision > MRF_PREC_BF16)
+        return fail(MRF_ERR_INVALID_ARG, "mrf_field_create: unknown precision %d", D->precision);
+    if (D->kind == MRF_FIELD_CONST) {
+        F.const_sigma = D->const_sigma;
+        for (int k = 0; k < 3; ++k) F.const_rgb[k] = D->const_rgb[k];
+        return MRF_OK;
+    }
+    if (D->kind == MRF_FIELD_GAUSS) {
+        const uint32_t K = D->n_blobs;
+        if (K > 0 && (!D->blob_center || !D->blob_radius || !D->blob_peak || !D->blob_emission))
+            return fail(MRF_ERR_INVALID_ARG, "mrf_field_create: GAUSS arrays missing");
+        std::vector<float> c, r, pk, em;
+        mrf_status st;
+        if ((st = fetch(c, D->blob_center, 3 * (size_t)K)) || (st = fetch(r, D->blob_radius, K)) ||
+            (st = fetch(pk, D->blob_peak, K)) || (st = fetch(em, D->blob_emission, 3 * (size_t)K)))
+            return st;
+        std::vector<float4> a(K), b(K);
+        for (uint32_t k = 0; k < K; ++k) {
+            a[k] = make_float4(c[3 * k], c[3 * k + 1], c[3 * k + 2], (float)(1.0 / (2.0 * r[k] * (double)r[k])));
+            b[k] = make_float4(pk[k], em[3 * k], em[3 * k + 1], em[3 * k + 2]);
+        }
+        F.n_blobs = (int)K;
+        if ((st = upload(f, a.data(), K, &F.blob_a, "blob params")) || (st = upload(f, b.data(), K, &F.blob_b, "blob params")))
+            return st;
+        return MRF_OK;
+    }
+    if (D->kind != MRF_FIELD_HASHGRID) return fail(MRF_ERR_INVALID_ARG, "mrf_field_create: unknown kind %d", D->kind);
+    if (D->n_levels == 0 || D->n_levels > (uint32_t)kMaxLevels)
+        return fail(MRF_ERR_INVALID_ARG, "mrf_field_create: n_levels %u out of range", D->n_levels);
+    if (D->n_features != 2) return fail(MRF_ERR_UNSUPPORTED, "mrf_field_create: only 2 features per level are supported");
+    if (D->n_levels * D->n_features > (uint32_t)kMaxIn || (D->n_levels * D->n_features) % 16 != 0)
+        return fail(MRF_ERR_INVALID_ARG, "mrf_field_create: n_levels * n_features must be a multiple of 16 and <= 64");
+    if (D->mlp_width != (uint32_t)kMlpWidth) return fail(MRF_ERR_INVALID_ARG, "mrf_field_create: mlp_width must be 64");
+    if (D->log2_table_size < 4 || D->log2_table_size > 24)
+        return fail(MRF_ERR_INVALID_ARG, "mrf_field_create: log2_table_size out of range");
+    if (!D->level_res || !D->table || !D->w1 || !D->b1 || !D->w2 || !D->b2 || !D->w3 || !D->b3)
+        return fail(MRF_ERR_INVALID_ARG, "mrf_field_create: HASHGRID arrays missing");
+    const uint32_t L = D->n_levels, T = 1u << D->log2_table_size, n_in = L * D->n_features;
+    std::vector<uint32_t> res;
+    mrf_status st;
+    if ((st = fetch(res, D->level_res, L))) return st;
+    F.n_levels = (int)L;
+    F.log2T = D->log2_table_size;
+    F.dense_mask = 0;
+    for (uint32_t l = 0; l < L; ++l) {
+        if (res[l] < 1 || res[l] > (1u << 20)) return fail(MRF_ERR_INVALID_ARG, "mrf_field_create: bad level resolution");
+        F.res[l] = res[l];
+        const uint64_t n1 = (uint64_t)res[l] + 1;
+        if (n1 * n1 * n1 <= T) F.dense_mask |= 1u << l;
+    }
+    if ((st = upload(f, reinterpret_cast<const uint32_t *>(D->table), (size_t)L * T, &F.table, "hash table")))
+        return st;
+    // pack the MLP: W1T[in][64], b1, W2[64][64], b2, W3T[64][4], b3
+    std::vector<float> w1, b1, w2, b2, w3, b3;
+    if ((st = fetch(w1, D->w1, 64 * (size_t)n_in)) || (st = fetch(b1, D->b1, 64)) || (st = fetch(w2, D->w2, 64 * 64)) ||
+        (st = fetch(b2, D->b2, 64)) || (st = fetch(w3, D->w3, 4 * 64)) || (st = fetch(b3, D->b3, 4)))
+        return st;
+    std::vector<float> pk(mlp_floats((int)n_in));
+    float *W1T = pk.data(), *B1 = W1T + n_in * 64, *W2 = B1 + 64, *B2 = W2 + 4096, *W3T = B2 + 64, *B3 = W3T + 256;
+    for (uint32_t j = 0; j < 64; ++j)
+        for (uint32_t i = 0; i < n_in; ++i) W1T[i * 64 + j] = w1[j * n_in + i];
+    std::memcpy(B1, b1.data(), 64 * 4);
+    std::memcpy(W2, w2.data(), 4096 * 4);
+    std::memcpy(B2, b2.data(), 64 * 4);
+    for (int j = 0; j < 64; ++j)
+        for (int o = 0; o < 4; ++o) W3T[j * 4 + o] = w3[o * 64 + j];
+    std::memcpy(B3, b3.data(), 4 * 4);
+    F.n_in = (int)n_in;
+    if ((st = upload(f, pk.data(), pk.size(), &F.mlp, "mlp weights"))) return st;
+    // support spheres
+    const uint32_t S = D->n_support;
+    if (S > 0) {
+        if (!D->support_center || !D->support_radius)
+            return fail(MRF_ERR_INVALID_ARG, "mrf_field_create: support arrays missing");
+        std::vector<float> sc, sr;
+        if ((st = fetch(sc, D->support_center, 3 * (size_t)S)) || (st = fetch(sr, D->support_radius, S))) return st;
+        std::vector<float4> sp(S);
+        for (uint32_t k = 0; k < S; ++k)
+            sp[k] = make_float4(sc[3 * k], sc[3 * k + 1], sc[3 * k + 2], (float)(1.0 / ((double)sr[k] * sr[k])));
+        F.n_support = (int)S;
+        if ((st = upload(f, sp.data(), S, &F.support, "support spheres"))) return st;
+    }
+    // occupancy
+    if (D->occ_res) {
+        const uint32_t R = D->occ_res;
+        if (R % 8 != 0 || R > 1024 || !D->occ_bits)
+            return fail(MRF_ERR_INVALID_ARG, "mrf_field_create: occ_res must be a multiple of 8 <= 1024 with occ_bits");
+        const size_t words = (size_t)R * R * R / 32;
+        if ((st = upload(f, D->occ_bits, words, &F.occ, "occupancy"))) return st;
+        F.occ_res = (int)R;
+        for (int k = 0; k < 3; ++k)
+            F.occ_scale[k] = (float)((double)R / ((double)D->aabb_max[k] - (double)D->aabb_min[k]));
+    }
+    (void)ctx;
+    return MRF_OK;
+}
+
+mrf_status mrf_field_create(mrf_context *ctx, const mrf_field_desc *desc, mrf_field **out) {
+    if (!ctx || !desc || !out) return fail(MRF_ERR_INVALID_ARG, "mrf_field_create: NULL argument");
+    *out = nullptr;
+    CUDA_TRY(cudaSetDevice(ctx->device), "mrf_field_create: cudaSetDevice");
+    mrf_field *f = new (std::nothrow) mrf_field();
+    if (!f) return fail(MRF_ERR_OOM, "mrf_field_create: host allocation");
+    f->ctx = ctx;
+    mrf_status st = field_create_impl(ctx, desc, f);
+    if (st != MRF_OK) {
+        field_free(f);
+        delete f;
+        return st;
+    }
+    *out = f;
+    return MRF_OK;
+}
+
+void mrf_field_destroy(mrf_field *f) {
+    if (!f) return;
+    field_free(f);
+    delete f;
+}
+
+mrf_status mrf_field_set_precision(mrf_field *f, int32_t precision) {
+    if (!f) return fail(MRF_ERR_INVALID_ARG, "mrf_field_set_precision: NULL field");
+    if (precision < MRF_PREC_FP32 || precision > MRF_PREC_BF16)
+        return fail(MRF_ERR_INVALID_ARG, "mrf_field_set_precision: unknown precision %d", precision);
+    f->dev.precision = precision;
+    return MRF_OK;
+}
+
+mrf_status mrf_field_query(mrf_context *ctx, const mrf_field *field, const float *points, uint32_t n, float *out,
+                           void *stream) {
+    if (!ctx || !field || (!points && n) || (!out && n)) return fail(MRF_ERR_INVALID_ARG, "mrf_field_query: NULL argument");
+    if (n == 0) return MRF_OK;
+    if (!is_device_ptr(points) || !is_device_ptr(out))
+        return fail(MRF_ERR_INVALID_ARG, "mrf_field_query: points and out must be device memory");
+    CUDA_TRY(launch_field_query(field->dev, points, n, out, (cudaStream_t)stream), "mrf_field_query: launch");
+    return MRF_OK;
+}
+
+// -------------------------------------------------------------------- BVH
+mrf_status mrf_bvh_build(mrf_context *ctx, const float *verts, uint32_t n_verts, const uint32_t *tris,
+                         const uint32_t *mat_id, uint32_t n_tris, mrf_bvh **out) {
+    if (!ctx || !out) return fail(MRF_ERR_INVALID_ARG, "mrf_bvh_build: NULL argument");
+    *out = nullptr;
+    if (n_tris > 0 && (!verts || !tris || !mat_id || n_verts == 0))
+        return fail(MRF_ERR_INVALID_ARG, "mrf_bvh_build: NULL array with n_tris > 0");
+    if (n_tris > (1u << 28)) return fail(MRF_ERR_INVALID_ARG, "mrf_bvh_build: too many triangles");
+    CUDA_TRY(cudaSetDevice(ctx->device), "mrf_bvh_build: cudaSetDevice");
+    std::vector<float> hv;
+    std::vector<uint32_t> ht, hm;
+    mrf_status st;
+    if ((st = fetch(hv, verts, 3 * (size_t)n_verts)) || (st = fetch(ht, tris, 3 * (size_t)n_tris)) ||
+        (st = fetch(hm, mat_id, n_tris)))
+        return st;
+    for (size_t i = 0; i < ht.size(); ++i)
+        if (ht[i] >= n_verts) return fail(MRF_ERR_INVALID_ARG, "mrf_bvh_build: vertex index %u >= n_verts", ht[i]);
+    for (size_t i = 0; i < hv.size(); ++i)
+        if (!std::isfinite(hv[i])) return fail(MRF_ERR_INVALID_ARG, "mrf_bvh_build: non-finite vertex coordinate");
+    std::vector<float> nodes;
+    std::vector<uint32_t> order;
+    std::vector<int> parent;
+    bvh_build_host(hv.data(), ht.data(), n_tris, nodes, order, parent);
+    std::vector<float4> tv(3 * (size_t)n_tris);
+    for (uint32_t s = 0; s < n_tris; ++s) {
+        const uint32_t t = order[s];
+        for (int v = 0; v < 3; ++v) {
+            const float *p = &hv[3 * (size_t)ht[3 * (size_t)t + v]];
+            float w = 0.f;
+            if (v == 0) std::memcpy(&w, &t, 4);
+            if (v == 1) std::memcpy(&w, &hm[t], 4);
+            tv[3 * (size_t)s + v] = make_float4(p[0], p[1], p[2], w);
+        }
+    }
+    mrf_bvh *b = new (std::nothrow) mrf_bvh();
+    if (!b) return fail(MRF_ERR_OOM, "mrf_bvh_build: host allocation");
+    b->ctx = ctx;
+    b->n_verts = n_verts;
+    b->n_tris = n_tris;
+    b->n_nodes = (int)parent.size();
+    auto cleanup = [&](mrf_status s2) {
+        mrf_bvh_destroy(b);
+        return s2;
+    };
+    if ((st = dev_alloc(&b->nodes, 4 * (size_t)b->n_nodes, "bvh nodes")) || (st = dev_alloc(&b->tris, tv.size(), "bvh tris")) ||
+        (st = dev_alloc(&b->order, n_tris, "bvh order")) || (st = dev_alloc(&b->tri_idx, 3 * (size_t)n_tris, "bvh indices")) ||
+        (st = dev_alloc(&b->verts, 3 * (size_t)n_verts, "bvh verts")) || (st = dev_alloc(&b->parent, (size_t)b->n_nodes, "bvh parents")) ||
+        (st = dev_alloc(&b->counters, (size_t)b->n_nodes, "bvh counters")))
+        return cleanup(st);
+    cudaError_t e = cudaSuccess;
+    if (b->n_nodes) {
+        e = cudaMemcpy(b->nodes, nodes.data(), nodes.size() * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(b->parent, parent.data(), parent.size() * 4, cudaMemcpyHostToDevice);
+    }
+    if (n_tris && e == cudaSuccess) {
+        e = cudaMemcpy(b->tris, tv.data(), tv.size() * sizeof(float4), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(b->order, order.data(), order.size() * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(b->tri_idx, ht.data(), ht.size() * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(b->verts, hv.data(), hv.size() * 4, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "mrf_bvh_build: upload"));
+    b->dev.nodes = b->nodes;
+    b->dev.tris = b->tris;
+    b->dev.n_nodes = b->n_nodes;
+    b->dev.n_tris = (int)n_tris;
+    *out = b;
+    return MRF_OK;
+}
+
+mrf_status mrf_bvh_refit(mrf_bvh *b, const float *verts, uint32_t n_verts, void *stream) {
+    if (!b || (!verts && n_verts)) return fail(MRF_ERR_INVALID_ARG, "mrf_bvh_refit: NULL argument");
+    if (n_verts != b->n_verts)
+        return fail(MRF_ERR_INVALID_ARG, "mrf_bvh_refit: %u vertices, the BVH was built with %u", n_verts, b->n_verts);
+    if (b->n_tris == 0) return MRF_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(b->verts, verts, 3 * sizeof(float) * (size_t)n_verts, cudaMemcpyDefault, s),
+             "mrf_bvh_refit: vertex upload");
+    CUDA_TRY(launch_bvh_refit(b->nodes, b->n_nodes, b->tris, (int)b->n_tris, b->order, b->tri_idx, b->verts, b->parent,
+                              b->counters, nullptr, s),
+             "mrf_bvh_refit: launch");
+    return MRF_OK;
+}
+
+void mrf_bvh_destroy(mrf_bvh *b) {
+    if (!b) return;
+    cudaFree(b->nodes);
+    cudaFree(b->tris);
+    cudaFree(b->order);
+    cudaFree(b->tri_idx);
+    cudaFree(b->verts);
+    cudaFree(b->parent);
+    cudaFree(b->counters);
+    delete b;
+}
+
+mrf_status mrf_cast(mrf_context *ctx, const mrf_bvh *bvh, const float *origins, const float *dirs,
+                    const uint32_t *skip, uint32_t n, float tmin, float *out_t, uint32_t *out_tri, void *stream) {
+    if (!ctx || !bvh) return fail(MRF_ERR_INVALID_ARG, "mrf_cast: NULL handle");
+    if (n == 0) return MRF_OK;
+    if (!is_device_ptr(origins) || !is_device_ptr(dirs) || !is_device_ptr(out_t) || !is_device_ptr(out_tri) ||
+        (skip && !is_device_ptr(skip)))
+        return fail(MRF_ERR_INVALID_ARG, "mrf_cast: arrays must be device memory");
+    CUDA_TRY(launch_cast(bvh->dev, origins, dirs, skip, n, tmin, out_t, out_tri, nullptr, (cudaStream_t)stream),
+             "mrf_cast: launch");
+    return MRF_OK;
+}
+
+// -------------------------------------------------------- materials/lights
+mrf_status mrf_materials_set(mrf_context *ctx, const mrf_material *mats, uint32_t n) {
+    if (!ctx || (!mats && n)) return fail(MRF_ERR_INVALID_ARG, "mrf_materials_set: NULL argument");
+    if (n > 65535) return fail(MRF_ERR_INVALID_ARG, "mrf_materials_set: too many materials");
+    std::vector<mrf_material> h;
+    mrf_status st;
+    if ((st = fetch(h, mats, n))) return st;
+    std::vector<MaterialDev> d(n);
+    for (uint32_t i = 0; i < n; ++i) {
+        if (h[i].kind < MRF_MAT_MIRROR || h[i].kind > MRF_MAT_DIFFUSE)
+            return fail(MRF_ERR_INVALID_ARG, "mrf_materials_set: unknown kind %d", h[i].kind);
+        if (h[i].kind == MRF_MAT_GLASS && !(h[i].ior > 0.f))
+            return fail(MRF_ERR_INVALID_ARG, "mrf_materials_set: glass needs ior > 0");
+        d[i].kind = h[i].kind;
+        for (int k = 0; k < 3; ++k) d[i].rgb[k] = h[i].rgb[k];
+        d[i].ior = h[i].ior;
+    }
+    CUDA_TRY(cudaSetDevice(ctx->device), "mrf_materials_set: cudaSetDevice");
+    cudaFree(ctx->mats);
+    ctx->mats = nullptr;
+    ctx->n_mats = 0;
+    if (n) {
+        if ((st = dev_alloc(&ctx->mats, n, "materials"))) return st;
+        CUDA_TRY(cudaMemcpy(ctx->mats, d.data(), n * sizeof(MaterialDev), cudaMemcpyHostToDevice), "materials upload");
+    }
+    ctx->n_mats = (int)n;
+    return MRF_OK;
+}
+
+mrf_status mrf_lights_set(mrf_context *ctx, const mrf_light *lights, uint32_t n) {
+    if (!ctx || (!lights && n)) return fail(MRF_ERR_INVALID_ARG, "mrf_lights_set: NULL argument");
+    if (n > 65535) return fail(MRF_ERR_INVALID_ARG, "mrf_lights_set: too many lights");
+    std::vector<mrf_light> h;
+    mrf_status st;
+    if ((st = fetch(h, lights, n))) return st;
+    std::vector<LightDev> d(n);
+    for (uint32_t i = 0; i < n; ++i) {
+        if (h[i].kind != MRF_LIGHT_POINT) return fail(MRF_ERR_UNSUPPORTED, "mrf_lights_set: only point lights");
+        for (int k = 0; k < 3; ++k) {
+            d[i].pos[k] = h[i].pos[k];
+            d[i].I[k] = h[i].intensity[k];
+        }
+    }
+    CUDA_TRY(cudaSetDevice(ctx->device), "mrf_lights_set: cudaSetDevice");
+    cudaFree(ctx->lights);
+    ctx->lights = nullptr;
+    ctx->n_lights = 0;
+    if (n) {
+        if ((st = dev_alloc(&ctx->lights, n, "lights"))) return st;
+        CUDA_TRY(cudaMemcpy(ctx->lights, d.data(), n * sizeof(LightDev), cudaMemcpyHostToDevice), "lights upload");
+    }
+    ctx->n_lights = (int)n;
+    return MRF_OK;
+}
+
+// ----------------------------------------------------------------- render
+static mrf_status ensure_scratch(mrf_context *ctx, size_t bytes) {
+    if (bytes <= ctx->scratch_bytes) return MRF_OK;
+    cudaFree(ctx->scratch);
+    ctx->scratch = nullptr;
+    ctx->scratch_bytes = 0;
+    size_t want = bytes + bytes / 4;
+    cudaError_t e = cudaMalloc(&ctx->scratch, want);
+    if (e != cudaSuccess) return cuda_fail(e, "render scratch");
+    ctx->scratch_bytes = want;
+    return MRF_OK;
+}
+
+mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *bvh, const mrf_rays *rays,
+                      uint32_t max_bounces, const mrf_render_opts *opts, float *out_hdr, void *stream,
+                      mrf_stats *stats) {
+    if (!ctx || !field || !bvh || !rays || !opts || !out_hdr)
+        return fail(MRF_ERR_INVALID_ARG, "mrf_render: NULL argument");
+    if (field->ctx != ctx || bvh->ctx != ctx) return fail(MRF_ERR_INVALID_ARG, "mrf_render: handle of another context");
+    if (max_bounces == 0 || max_bounces > (uint32_t)kMaxBounces)
+        return fail(MRF_ERR_INVALID_ARG, "mrf_render: max_bounces must be in [1, %d]", kMaxBounces);
+    if (rays->spp == 0) return fail(MRF_ERR_INVALID_ARG, "mrf_render: spp must be >= 1");
+    if (opts->steps_per_segment == 0 && !(opts->dt > 0.f))
+        return fail(MRF_ERR_INVALID_ARG, "mrf_render: need steps_per_segment > 0 or dt > 0");
+    if (!(opts->tau >= 0.f) || !(opts->tmin >= 0.f)) return fail(MRF_ERR_INVALID_ARG, "mrf_render: negative tau or tmin");
+    if (bvh->n_tris && ctx->n_mats == 0) return fail(MRF_ERR_NOT_READY, "mrf_render: no materials set");
+    if (opts->engine < MRF_ENGINE_AUTO || opts->engine > MRF_ENGINE_WAVEFRONT)
+        return fail(MRF_ERR_INVALID_ARG, "mrf_render: unknown engine %d", opts->engine);
+    if (opts->engine == MRF_ENGINE_WAVEFRONT && !wavefront_available())
+        return fail(MRF_ERR_UNSUPPORTED, "mrf_render: wavefront engine not built");
+    CUDA_TRY(cudaSetDevice(ctx->device), "mrf_render: cudaSetDevice");
+    {
+        cudaError_t pending = cudaGetLastError();
+        if (pending != cudaSuccess) return cuda_fail(pending, "mrf_render: earlier asynchronous error");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    RenderParams P{};
+    P.F = field->dev;
+    P.B = bvh->dev;
+    P.mats = ctx->mats;
+    P.n_mats = ctx->n_mats;
+    P.lights = ctx->lights;
+    P.n_lights = ctx->n_lights;
+    uint32_t count;
+    size_t scratch_need = 0;
+    const bool host_rays = !rays->camera && !is_device_ptr(rays->origins);
+    if (rays->camera) {
+        const mrf_camera &c = *rays->camera;
+        if (c.width == 0 || c.height == 0 || !(c.vfov_deg > 0.f && c.vfov_deg < 180.f))
+            return fail(MRF_ERR_INVALID_ARG, "mrf_render: bad camera");
+        const uint64_t cnt = (uint64_t)c.width * c.height;
+        if (cnt > 0xFFFFFFFFull / 4) return fail(MRF_ERR_INVALID_ARG, "mrf_render: image too large");
+        count = (uint32_t)cnt;
+        double f[3], up[3], r[3], u[3];
+        for (int k = 0; k < 3; ++k) { f[k] = (double)c.look_at[k] - c.pos[k]; up[k] = c.up[k]; }
+        double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+        if (!(fl > 0)) return fail(MRF_ERR_INVALID_ARG, "mrf_render: camera looks at itself");
+        for (double &x : f) x /= fl;
+        r[0] = f[1] * up[2] - f[2] * up[1];
+        r[1] = f[2] * up[0] - f[0] * up[2];
+        r[2] = f[0] * up[1] - f[1] * up[0];
+        double rl = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        if (!(rl > 0)) return fail(MRF_ERR_INVALID_ARG, "mrf_render: camera up is parallel to the view direction");
+        for (double &x : r) x /= rl;
+        u[0] = r[1] * f[2] - r[2] * f[1];
+        u[1] = r[2] * f[0] - r[0] * f[2];
+        u[2] = r[0] * f[1] - r[1] * f[0];
+        P.use_camera = 1;
+        for (int k = 0; k < 3; ++k) {
+            P.cam_pos[k] = c.pos[k];
+            P.cam_f[k] = (float)f[k];
+            P.cam_r[k] = (float)r[k];
+            P.cam_u[k] = (float)u[k];
+        }
+        P.tan_half = (float)std::tan(0.5 * (double)c.vfov_deg * M_PI / 180.0);
+        P.aspect = (float)((double)c.width / (double)c.height);
+        P.W = c.width;
+        P.H = c.height;
+    } else {
+        if (!rays->origins || !rays->dirs || rays->count == 0)
+            return fail(MRF_ERR_INVALID_ARG, "mrf_render: explicit rays need origins, dirs and count > 0");
+        count = rays->count;
+        if (host_rays) scratch_need += 2 * 3 * sizeof(float) * (size_t)count;
+    }
+    if ((uint64_t)count * rays->spp > 0xFFFFFFFFull) return fail(MRF_ERR_INVALID_ARG, "mrf_render: too many paths");
+    const bool host_out = !is_device_ptr(out_hdr);
+    const size_t out_off = (scratch_need + 255) & ~(size_t)255;
+    if (host_out) scratch_need = out_off + 4 * sizeof(float) * (size_t)count;
+    if ((opts->rec_segments && !is_device_ptr(opts->rec_segments)) || (opts->rec_tri && !is_device_ptr(opts->rec_tri)) ||
+        (opts->rec_t && !is_device_ptr(opts->rec_t)) || (!opts->rec_tri != !opts->rec_t))
+        return fail(MRF_ERR_INVALID_ARG, "mrf_render: records must be device pointers (rec_tri and rec_t together)");
+    P.count = count;
+    P.spp = rays->spp;
+    P.max_bounces = max_bounces;
+    P.seed = opts->seed;
+    P.steps = opts->steps_per_segment;
+    P.dt = opts->dt;
+    P.tau = opts->tau;
+    P.tmin = opts->tmin;
+    P.rec_seg = opts->rec_segments;
+    P.rec_tri = opts->rec_tri;
+    P.rec_t = opts->rec_t;
+    const int engine = opts->engine == MRF_ENGINE_AUTO ? MRF_ENGINE_MEGAKERNEL : opts->engine;
+    size_t wf_off = 0;
+    if (engine == MRF_ENGINE_WAVEFRONT) {
+        wf_off = (scratch_need + 255) & ~(size_t)255;
+        scratch_need = wf_off + wavefront_scratch_bytes(P);
+    }
+    mrf_status st;
+    if (scratch_need && (st = ensure_scratch(ctx, scratch_need))) return st;
+    char *scr = (char *)ctx->scratch;
+    if (host_rays) {
+        float *o = (float *)scr, *d = o + 3 * (size_t)count;
+        CUDA_TRY(cudaMemcpyAsync(o, rays->origins, 3 * sizeof(float) * (size_t)count, cudaMemcpyDefault, s), "ray upload");
+        CUDA_TRY(cudaMemcpyAsync(d, rays->dirs, 3 * sizeof(float) * (size_t)count, cudaMemcpyDefault, s), "ray upload");
+        P.ray_o = o;
+        P.ray_d = d;
+    } else if (!rays->camera) {
+        P.ray_o = rays->origins;
+        P.ray_d = rays->dirs;
+    }
+    P.out = host_out ? (float *)(scr + out_off) : out_hdr;
+    if (stats) {
+        CUDA_TRY(cudaMemsetAsync(ctx->stats, 0, sizeof(unsigned long long) * ST_COUNT, s), "stats reset");
+        P.stats = ctx->stats;
+    }
+    if (engine == MRF_ENGINE_WAVEFRONT) {
+        CUDA_TRY(launch_render_wavefront(P, scr + wf_off, scratch_need - wf_off, s), "mrf_render: wavefront launch");
+    } else {
+        CUDA_TRY(launch_render_megakernel(P, s), "mrf_render: launch");
+    }
+    if (host_out) {
+        CUDA_TRY(cudaMemcpyAsync(out_hdr, P.out, 4 * sizeof(float) * (size_t)count, cudaMemcpyDeviceToHost, s),
+                 "mrf_render: image download");
+    }
+    if (stats) {
+        unsigned long long h[ST_COUNT];
+        CUDA_TRY(cudaMemcpyAsync(h, ctx->stats, sizeof(h), cudaMemcpyDeviceToHost, s), "stats download");
+        CUDA_TRY(cudaStreamSynchronize(s), "mrf_render: synchronize");
+        stats->paths = h[ST_PATHS];
+        stats->segments = h[ST_SEGMENTS];
+        stats->surface_hits = h[ST_HITS];
+        stats->shadow_rays = h[ST_SHADOW];
+        stats->samples_nominal = h[ST_NOMINAL];
+        stats->samples_evaluated = h[ST_EVALUATED];
+        stats->shadow_samples_evaluated = h[ST_SHADOW_EVALUATED];
+        stats->fp64_retests = h[ST_FP64];
+        stats->status = h[ST_STATUS];
+        if (h[ST_STATUS]) return fail(MRF_ERR_TIMEOUT, "mrf_render: kernel gave up (status %llu)", h[ST_STATUS]);
+    } else if (host_out) {
+        CUDA_TRY(cudaStreamSynchronize(s), "mrf_render: synchronize");
+    }
+    return MRF_OK;
+}
+

@@ -1,0 +1,104 @@
+// Internal structures shared by the host side of the C ABI and the kernels.
+// Everything a kernel reads is reached through plain device pointers held in
+// these structs, which are passed by value as kernel parameters.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/mrf.h"
+
+namespace mrf {
+
+constexpr uint32_t kNoHit = 0xFFFFFFFFu;
+constexpr int kMaxLevels = 32;
+constexpr int kMlpWidth = 64;
+constexpr int kMaxIn = 64;
+constexpr int kMaxBounces = 64;
+constexpr int kStackSize = 64;
+
+// Packed FP32 MLP weights (floats):  W1T[in][64] | b1[64] | W2[64][64] | b2[64] | W3T[64][4] | b3[4]
+constexpr int mlp_floats(int n_in) { return n_in * 64 + 64 + 64 * 64 + 64 + 64 * 4 + 4; }
+
+struct FieldDev {
+    int kind;
+    float lo[3], hi[3], ext_inv[3];
+    float const_sigma, const_rgb[3];
+    // GAUSS: blob_a = (cx, cy, cz, 1 / (2 r^2)), blob_b = (peak, e_r, e_g, e_b)
+    int n_blobs;
+    const float4 *blob_a, *blob_b;
+    // HASHGRID
+    int n_levels;
+    uint32_t log2T;
+    uint32_t res[kMaxLevels];
+    uint32_t dense_mask;        // bit l set: level l indexed densely
+    const uint32_t *table;      // [level][entry] binary16 pairs (feature 0 low half)
+    int n_in;
+    const float *mlp;           // packed FP32, see mlp_floats
+    const uint16_t *mlp_lp;     // packed half / bf16 copies for the tensor-core engine
+    int n_support;
+    const float4 *support;      // (cx, cy, cz, 1 / r^2)
+    int occ_res;
+    const uint32_t *occ;
+    float occ_scale[3];         // occ_res / extent
+    int precision;
+};
+
+// BVH node: 4 x float4 = both children's boxes + (left, right, left_count, right_count).
+// count > 0: leaf child whose triangles are [index, index + count) of `tris`.
+struct BvhDev {
+    const float4 *nodes;
+    const float4 *tris;         // 3 x float4 per triangle: (v0, id) (v1, material) (v2, 0)
+    int n_nodes;
+    int n_tris;
+};
+
+struct MaterialDev {
+    int kind;
+    float rgb[3];
+    float ior;
+};
+
+struct LightDev {
+    float pos[3];
+    float I[3];
+};
+
+// device statistics counters (unsigned long long), in this order
+enum StatIndex {
+    ST_PATHS = 0, ST_SEGMENTS, ST_HITS, ST_SHADOW, ST_NOMINAL, ST_EVALUATED, ST_SHADOW_EVALUATED, ST_FP64,
+    ST_STATUS, ST_COUNT
+};
+
+struct RenderParams {
+    FieldDev F;
+    BvhDev B;
+    const MaterialDev *mats;
+    int n_mats;
+    const LightDev *lights;
+    int n_lights;
+    int use_camera;
+    float cam_pos[3], cam_f[3], cam_r[3], cam_u[3];
+    float tan_half, aspect;
+    uint32_t W, H;
+    const float *ray_o, *ray_d;
+    uint32_t count, spp, max_bounces;
+    uint64_t seed;
+    uint32_t steps;
+    float dt, tau, tmin;
+    float *out;
+    uint32_t *rec_seg, *rec_tri;
+    float *rec_t;
+    unsigned long long *stats;
+};
+
+// launchers (render_mega.cu)
+cudaError_t launch_render_megakernel(const RenderParams &P, cudaStream_t s);
+cudaError_t launch_field_query(const FieldDev &F, const float *pts, uint32_t n, float *out, cudaStream_t s);
+cudaError_t launch_cast(const BvhDev &B, const float *o, const float *d, const uint32_t *skip, uint32_t n, float tmin,
+                        float *out_t, uint32_t *out_tri, unsigned long long *stats, cudaStream_t s);
+// bvh_refit.cu
+cudaError_t launch_bvh_refit(float4 *nodes, int n_nodes, float4 *tris, int n_tris, const uint32_t *tri_order,
+                             const uint32_t *tri_idx, const float *verts, const int *parent, int *counters,
+                             const int *leaf_parent_of_tri, cudaStream_t s);
+
+}  // namespace mrf

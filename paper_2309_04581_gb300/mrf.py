@@ -1,0 +1,344 @@
+"""ctypes binding of the C ABI in include/mrf.h (argument marshalling only).
+
+Every function named ``mrf_*`` here calls the library function of the same
+name; all rendering work runs in the CUDA library ``libmrf.so``.  There is no
+CPU fallback: if the library or a CUDA device is missing, the calls raise.
+
+``Renderer`` is a convenience wrapper that uploads a ``scenes.Scene`` and
+renders it into torch tensors (torch provides device memory and streams).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import scenes as S
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmrf.so")
+_lib = None
+_lock = threading.Lock()
+
+MRF_OK, MRF_ERR_INVALID_ARG, MRF_ERR_CUDA, MRF_ERR_OOM, MRF_ERR_TIMEOUT, MRF_ERR_NOT_READY, MRF_ERR_UNSUPPORTED = range(7)
+MRF_FIELD_CONST, MRF_FIELD_GAUSS, MRF_FIELD_HASHGRID = 0, 1, 2
+MRF_PREC_FP32, MRF_PREC_FP16, MRF_PREC_BF16 = 0, 1, 2
+MRF_MAT_MIRROR, MRF_MAT_GLASS, MRF_MAT_DIFFUSE = 0, 1, 2
+MRF_LIGHT_POINT = 0
+MRF_ENGINE_AUTO, MRF_ENGINE_MEGAKERNEL, MRF_ENGINE_WAVEFRONT = 0, 1, 2
+NO_HIT = 0xFFFFFFFF
+
+# every entry point declared in include/mrf.h
+EXPORTS = ("mrf_context_create", "mrf_context_destroy", "mrf_last_error", "mrf_version", "mrf_field_create",
+           "mrf_field_destroy", "mrf_field_set_precision", "mrf_field_query", "mrf_bvh_build", "mrf_bvh_refit",
+           "mrf_bvh_destroy", "mrf_cast", "mrf_materials_set", "mrf_lights_set", "mrf_render")
+
+_fp = C.POINTER(C.c_float)
+_u32p = C.POINTER(C.c_uint32)
+_u16p = C.POINTER(C.c_uint16)
+_vp = C.c_void_p
+
+
+class mrf_field_desc(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int32), ("aabb_min", C.c_float * 3), ("aabb_max", C.c_float * 3),
+        ("const_sigma", C.c_float), ("const_rgb", C.c_float * 3),
+        ("n_blobs", C.c_uint32), ("blob_center", _fp), ("blob_radius", _fp), ("blob_peak", _fp),
+        ("blob_emission", _fp),
+        ("n_levels", C.c_uint32), ("log2_table_size", C.c_uint32), ("n_features", C.c_uint32),
+        ("level_res", _u32p), ("table", _u16p), ("mlp_width", C.c_uint32),
+        ("w1", _fp), ("b1", _fp), ("w2", _fp), ("b2", _fp), ("w3", _fp), ("b3", _fp),
+        ("n_support", C.c_uint32), ("support_center", _fp), ("support_radius", _fp),
+        ("occ_res", C.c_uint32), ("occ_bits", _u32p), ("precision", C.c_int32),
+    ]
+
+
+class mrf_material(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("rgb", C.c_float * 3), ("ior", C.c_float)]
+
+
+class mrf_light(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pos", C.c_float * 3), ("intensity", C.c_float * 3)]
+
+
+class mrf_camera(C.Structure):
+    _fields_ = [("pos", C.c_float * 3), ("look_at", C.c_float * 3), ("up", C.c_float * 3),
+                ("vfov_deg", C.c_float), ("width", C.c_uint32), ("height", C.c_uint32)]
+
+
+class mrf_rays(C.Structure):
+    _fields_ = [("camera", C.POINTER(mrf_camera)), ("origins", _vp), ("dirs", _vp), ("count", C.c_uint32),
+                ("spp", C.c_uint32)]
+
+
+class mrf_render_opts(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("steps_per_segment", C.c_uint32), ("dt", C.c_float), ("tau", C.c_float),
+                ("tmin", C.c_float), ("engine", C.c_int32), ("rec_segments", _vp), ("rec_tri", _vp),
+                ("rec_t", _vp)]
+
+
+class mrf_stats(C.Structure):
+    _fields_ = [("paths", C.c_uint64), ("segments", C.c_uint64), ("surface_hits", C.c_uint64),
+                ("shadow_rays", C.c_uint64), ("samples_nominal", C.c_uint64), ("samples_evaluated", C.c_uint64),
+                ("shadow_samples_evaluated", C.c_uint64), ("fp64_retests", C.c_uint64), ("status", C.c_uint64)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class MrfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"mrf status {status}: {msg}")
+        self.status = status
+
+
+def lib():
+    """Loads libmrf.so (built in-tree by ``build.py``); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+            L = C.CDLL(LIB_PATH)
+            L.mrf_last_error.restype = C.c_char_p
+            L.mrf_version.restype = C.c_char_p
+            for name in EXPORTS:
+                fn = getattr(L, name)
+                if name not in ("mrf_last_error", "mrf_version"):
+                    fn.restype = C.c_int
+            for name in ("mrf_context_destroy", "mrf_field_destroy", "mrf_bvh_destroy"):
+                getattr(L, name).restype = None
+            L.mrf_context_create.argtypes = [C.c_int, C.POINTER(_vp)]
+            L.mrf_field_create.argtypes = [_vp, C.POINTER(mrf_field_desc), C.POINTER(_vp)]
+            L.mrf_field_set_precision.argtypes = [_vp, C.c_int32]
+            L.mrf_field_query.argtypes = [_vp, _vp, _vp, C.c_uint32, _vp, _vp]
+            L.mrf_bvh_build.argtypes = [_vp, _vp, C.c_uint32, _vp, _vp, C.c_uint32, C.POINTER(_vp)]
+            L.mrf_bvh_refit.argtypes = [_vp, _vp, C.c_uint32, _vp]
+            L.mrf_cast.argtypes = [_vp, _vp, _vp, _vp, _vp, C.c_uint32, C.c_float, _vp, _vp, _vp]
+            L.mrf_materials_set.argtypes = [_vp, C.POINTER(mrf_material), C.c_uint32]
+            L.mrf_lights_set.argtypes = [_vp, C.POINTER(mrf_light), C.c_uint32]
+            L.mrf_render.argtypes = [_vp, _vp, _vp, C.POINTER(mrf_rays), C.c_uint32, C.POINTER(mrf_render_opts), _vp,
+                                     _vp, C.POINTER(mrf_stats)]
+            L.mrf_context_destroy.argtypes = [_vp]
+            L.mrf_field_destroy.argtypes = [_vp]
+            L.mrf_bvh_destroy.argtypes = [_vp]
+            _lib = L
+    return _lib
+
+
+def check(status: int):
+    if status != MRF_OK:
+        raise MrfError(status, lib().mrf_last_error().decode())
+
+
+# ---------------------------------------------------------------- raw ABI
+def mrf_context_create(device: int = 0) -> int:
+    h = _vp()
+    check(lib().mrf_context_create(device, C.byref(h)))
+    return h.value
+
+
+def mrf_context_destroy(ctx: int):
+    lib().mrf_context_destroy(ctx)
+
+
+def mrf_field_create(ctx: int, desc: mrf_field_desc) -> int:
+    h = _vp()
+    check(lib().mrf_field_create(ctx, C.byref(desc), C.byref(h)))
+    return h.value
+
+
+def mrf_field_destroy(f: int):
+    lib().mrf_field_destroy(f)
+
+
+def mrf_field_set_precision(f: int, precision: int):
+    check(lib().mrf_field_set_precision(f, precision))
+
+
+def mrf_field_query(ctx: int, f: int, points_ptr: int, n: int, out_ptr: int, stream: int = 0):
+    check(lib().mrf_field_query(ctx, f, points_ptr, n, out_ptr, stream))
+
+
+def mrf_bvh_build(ctx: int, verts_ptr: int, n_verts: int, tris_ptr: int, mat_ptr: int, n_tris: int) -> int:
+    h = _vp()
+    check(lib().mrf_bvh_build(ctx, verts_ptr, n_verts, tris_ptr, mat_ptr, n_tris, C.byref(h)))
+    return h.value
+
+
+def mrf_bvh_refit(bvh: int, verts_ptr: int, n_verts: int, stream: int = 0):
+    check(lib().mrf_bvh_refit(bvh, verts_ptr, n_verts, stream))
+
+
+def mrf_bvh_destroy(bvh: int):
+    lib().mrf_bvh_destroy(bvh)
+
+
+def mrf_cast(ctx, bvh, o_ptr, d_ptr, skip_ptr, n, tmin, t_ptr, tri_ptr, stream=0):
+    check(lib().mrf_cast(ctx, bvh, o_ptr, d_ptr, skip_ptr, n, tmin, t_ptr, tri_ptr, stream))
+
+
+def mrf_materials_set(ctx: int, mats):
+    arr = (mrf_material * max(1, len(mats)))()
+    for i, m in enumerate(mats):
+        arr[i].kind = m.kind
+        arr[i].rgb[:] = [float(x) for x in m.rgb]
+        arr[i].ior = float(m.ior)
+    check(lib().mrf_materials_set(ctx, arr, len(mats)))
+
+
+def mrf_lights_set(ctx: int, lights):
+    arr = (mrf_light * max(1, len(lights)))()
+    for i, l in enumerate(lights):
+        arr[i].kind = l.kind
+        arr[i].pos[:] = [float(x) for x in l.pos]
+        arr[i].intensity[:] = [float(x) for x in l.intensity]
+    check(lib().mrf_lights_set(ctx, arr, len(lights)))
+
+
+def mrf_render(ctx, field, bvh, rays: mrf_rays, max_bounces: int, opts: mrf_render_opts, out_ptr: int, stream: int = 0,
+               stats: mrf_stats | None = None):
+    check(lib().mrf_render(ctx, field, bvh, C.byref(rays), max_bounces, C.byref(opts), out_ptr, stream,
+                           C.byref(stats) if stats is not None else None))
+
+
+# ---------------------------------------------------------------- helpers
+def _p(a: np.ndarray, t):
+    return a.ctypes.data_as(t)
+
+
+def field_desc(field: S.Field, precision: int = MRF_PREC_FP32):
+    """mrf_field_desc for a scenes.Field (host arrays; returns desc and the arrays it points to)."""
+    d = mrf_field_desc()
+    keep = []
+
+    def arr(a, dt):
+        x = np.ascontiguousarray(np.asarray(a).astype(dt, copy=False))
+        keep.append(x)
+        return x
+
+    d.kind = field.kind
+    d.aabb_min[:] = [float(x) for x in field.aabb_min]
+    d.aabb_max[:] = [float(x) for x in field.aabb_max]
+    d.const_sigma = field.const_sigma
+    d.const_rgb[:] = [float(x) for x in field.const_rgb]
+    d.precision = precision
+    if field.blob_center is not None:
+        d.n_blobs = field.blob_center.shape[0]
+        d.blob_center = _p(arr(field.blob_center, np.float32), _fp)
+        d.blob_radius = _p(arr(field.blob_radius, np.float32), _fp)
+        d.blob_peak = _p(arr(field.blob_peak, np.float32), _fp)
+        d.blob_emission = _p(arr(field.blob_emission, np.float32), _fp)
+    if field.table is not None:
+        d.n_levels = field.level_res.shape[0]
+        d.log2_table_size = field.log2_table_size
+        d.n_features = field.n_features
+        d.level_res = _p(arr(field.level_res, np.uint32), _u32p)
+        d.table = _p(arr(field.table.view(np.uint16), np.uint16), _u16p)
+        d.mlp_width = field.w1.shape[0]
+        for nm in ("w1", "b1", "w2", "b2", "w3", "b3"):
+            setattr(d, nm, _p(arr(getattr(field, nm), np.float32), _fp))
+        if field.support_center is not None:
+            d.n_support = field.support_center.shape[0]
+            d.support_center = _p(arr(field.support_center, np.float32), _fp)
+            d.support_radius = _p(arr(field.support_radius, np.float32), _fp)
+        if field.occ_bits is not None and field.occ_res:
+            d.occ_res = field.occ_res
+            d.occ_bits = _p(arr(field.occ_bits, np.uint32), _u32p)
+    return d, keep
+
+
+def camera_struct(cam: S.Camera) -> mrf_camera:
+    c = mrf_camera()
+    c.pos[:] = [float(x) for x in cam.pos]
+    c.look_at[:] = [float(x) for x in cam.look_at]
+    c.up[:] = [float(x) for x in cam.up]
+    c.vfov_deg = float(cam.vfov_deg)
+    c.width, c.height = cam.width, cam.height
+    return c
+
+
+class Renderer:
+    """Uploads a scenes.Scene once and renders it on ``device`` with torch-owned buffers."""
+
+    def __init__(self, scene: S.Scene, device: int = 0, precision: int = MRF_PREC_FP32):
+        import torch
+        self.torch = torch
+        self.scene = scene
+        self.device = device
+        self.ctx = mrf_context_create(device)
+        desc, keep = field_desc(scene.field, precision)
+        self.field = mrf_field_create(self.ctx, desc)
+        del keep
+        m = scene.mesh
+        v = np.ascontiguousarray(m.verts, np.float32)
+        t = np.ascontiguousarray(m.tris, np.uint32)
+        mt = np.ascontiguousarray(m.mat, np.uint32)
+        self.bvh = mrf_bvh_build(self.ctx, v.ctypes.data, v.shape[0], t.ctypes.data, mt.ctypes.data, t.shape[0])
+        if scene.materials:
+            mrf_materials_set(self.ctx, scene.materials)
+        mrf_lights_set(self.ctx, scene.lights)
+        self.cam = camera_struct(scene.camera)
+        self._rays_dev = None
+        if scene.ray_o is not None:
+            dev = torch.device("cuda", device)
+            self._rays_dev = (torch.from_numpy(scene.ray_o).to(dev), torch.from_numpy(scene.ray_d).to(dev))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            mrf_bvh_destroy(self.bvh)
+            mrf_field_destroy(self.field)
+            mrf_context_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rays_struct(self) -> mrf_rays:
+        r = mrf_rays()
+        if self._rays_dev is None:
+            r.camera = C.pointer(self.cam)
+            r.count = self.scene.n_rays
+        else:
+            r.origins = self._rays_dev[0].data_ptr()
+            r.dirs = self._rays_dev[1].data_ptr()
+            r.count = self._rays_dev[0].shape[0]
+        r.spp = self.scene.opts.spp
+        return r
+
+    def opts_struct(self, engine=MRF_ENGINE_AUTO, records=None) -> mrf_render_opts:
+        o = self.scene.opts
+        s = mrf_render_opts()
+        s.seed, s.steps_per_segment, s.dt, s.tau, s.tmin = o.seed, o.steps_per_segment, o.dt, o.tau, o.tmin
+        s.engine = engine
+        if records is not None:
+            s.rec_segments = records["segments"].data_ptr()
+            s.rec_tri = records["tri"].data_ptr()
+            s.rec_t = records["t"].data_ptr()
+        return s
+
+    def new_records(self):
+        torch = self.torch
+        dev = torch.device("cuda", self.device)
+        n, spp, B = self.scene.n_rays, self.scene.opts.spp, self.scene.opts.max_bounces
+        return {"segments": torch.zeros(n * spp, dtype=torch.int32, device=dev),
+                "tri": torch.zeros(n * spp * B, dtype=torch.int32, device=dev),
+                "t": torch.zeros(n * spp * B, dtype=torch.float32, device=dev)}
+
+    def render(self, out=None, engine=MRF_ENGINE_AUTO, records=None, stats=False, stream=None):
+        """Renders into ``out`` (count x 4 float32 CUDA tensor, allocated if None).
+        Returns (out, stats dict or None)."""
+        torch = self.torch
+        n = self.scene.n_rays
+        if out is None:
+            out = torch.empty((n, 4), dtype=torch.float32, device=torch.device("cuda", self.device))
+        st = mrf_stats() if stats else None
+        s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        mrf_render(self.ctx, self.field, self.bvh, self.rays_struct(), self.scene.opts.max_bounces,
+                   self.opts_struct(engine, records), out.data_ptr(), s, st)
+        return out, (st.as_dict() if st is not None else None)

@@ -320,12 +320,17 @@ def hash_field(config: int, n_levels=16, log2_T=19, n_feat=2, n_min=16, n_max=20
                n_support=8, support_r=(0.1, 0.25), support_c=0.3, occ_res=128, sigma_bias=3.0,
                aabb_min=UNIT_BOX_MIN, aabb_max=UNIT_BOX_MAX) -> Field:
     """Hash-grid field of the paper's default Instant-NGP shape: seeded table
-    U(-0.5, 0.5) in FP16, seeded Xavier-uniform MLP 32 -> 64 -> 64 -> 4, and a
+    U(-a_l, a_l) with a_l = 0.5 * N_0 / N_l in FP16, seeded Xavier-uniform MLP
+    32 -> 64 -> 64 -> 4, and a
     compact density support made of ``n_support`` seeded spheres whose
     conservative cover is the occupancy bitfield."""
     T = 1 << log2_T
     rng_t = _rng(config, 1)
-    table = rng_t.uniform(-0.5, 0.5, size=(n_levels, T, n_feat)).astype(np.float16)
+    res = level_resolutions(n_levels, n_min, n_max)
+    # amplitude 0.5 * N_0 / N_l: every level contributes the same feature gradient
+    # (a 1/f spectrum, like a trained field), instead of white noise at 2048^3
+    amp = 0.5 * n_min / res.astype(np.float64)
+    table = (rng_t.uniform(-1.0, 1.0, size=(n_levels, T, n_feat)) * amp[:, None, None]).astype(np.float16)
     rng_w = _rng(config, 2)
     d_in = n_levels * n_feat
 
@@ -340,7 +345,7 @@ def hash_field(config: int, n_levels=16, log2_T=19, n_feat=2, n_min=16, n_max=20
     sr = f32(rng_s.uniform(support_r[0], support_r[1], size=(n_support,)))
     occ = occupancy_from_spheres(sc, sr, occ_res, aabb_min, aabb_max, margin=1e-4)
     return Field(kind=FIELD_HASH, aabb_min=f32(aabb_min), aabb_max=f32(aabb_max),
-                 level_res=level_resolutions(n_levels, n_min, n_max), log2_table_size=log2_T,
+                 level_res=res, log2_table_size=log2_T,
                  n_features=n_feat, table=np.ascontiguousarray(table),
                  w1=w1, b1=f32(np.zeros(width)), w2=w2, b2=f32(np.zeros(width)), w3=w3, b3=b3,
                  support_center=sc, support_radius=sr, occ_res=occ_res, occ_bits=occ)
