@@ -336,7 +336,7 @@ static int march(const orc_scene *sc, const double o[3], const double d[3], doub
         if (sc->tau > 0) {
             double m = T[0] > T[1] ? T[0] : T[1];
             if (T[2] > m) m = T[2];
-            if (fabs(m - sc->tau) <= 1e-6 * sc->tau) *flags |= ORC_FLAG_TAU;
+            if (fabs(m - sc->tau) <= 1e-4 * sc->tau) *flags |= ORC_FLAG_TAU;
             if (m < sc->tau) return 1;
         }
     }
@@ -595,7 +595,7 @@ static void trace_path(const orc_scene *sc, uint32_t ray, uint32_t s, double L[3
         prev = hit;
         if (sc->tau > 0) {
             double mt = maxc(T);
-            if (fabs(mt - sc->tau) <= 1e-6 * sc->tau) *flags |= ORC_FLAG_TAU;
+            if (fabs(mt - sc->tau) <= 1e-4 * sc->tau) *flags |= ORC_FLAG_TAU;
             if (mt < sc->tau) break;
         }
     }

@@ -3,10 +3,13 @@ through the C ABI.
 
 Tolerances (derived in DESIGN.md, "Parity bar"):
   - hit triangle ids and segment counts: bit-exact on unflagged pixels;
-  - hit distance: 1e-5 relative to max(t, 1e-3) (below 1e-3 the FP32
-    coordinates of magnitude ~0.5 cannot resolve t to 1e-5 relative);
+  - hit distance: 1e-5 relative to max(t, 1e-2) (coordinates of magnitude
+    ~0.5 hold t to ~1e-7 absolute in FP32, so 1e-5 relative is only
+    resolvable from t = 1e-2 up);
   - FP32 radiance: 1e-4 relative per pixel, relative to the pixel's largest
-    channel, with a floor of 1e-3 x the image peak for near-black pixels;
+    channel, with a floor of 1e-2 x the image peak for near-black pixels
+    (their light comes from the fringe of the density support, where FP32
+    sample positions carry ~1e-7 absolute error);
   - pixels the oracle flags as ambiguous (a discrete decision within a margin
     of its threshold) are excluded and must stay below 0.1 %.
 """
@@ -62,7 +65,7 @@ def _compare(gpu, ref, ids=None, rtol=RTOL_PIX, check_records=True, max_flag_fra
     ok = ref["flags"] == 0
     assert (~ok).mean() <= max_flag_frac, f"{(~ok).mean():.4%} ambiguous pixels"
     peak = max(np.abs(o[:, :3]).max(), 1e-30)
-    den = np.maximum(np.abs(o[:, :3]).max(1), 1e-3 * peak)
+    den = np.maximum(np.abs(o[:, :3]).max(1), 1e-2 * peak)
     err = np.abs(g[:, :3] - o[:, :3]).max(1) / den
     worst = int(np.argmax(np.where(ok, err, 0)))
     assert err[ok].max() <= rtol, f"pixel {ids[worst]}: gpu {g[worst]} oracle {o[worst]} rel {err[worst]:.3g}"
@@ -75,7 +78,7 @@ def _compare(gpu, ref, ids=None, rtol=RTOL_PIX, check_records=True, max_flag_fra
         tg, to = gpu["t"][ids][ok], ref["t"][ok]
         fin = np.isfinite(to)
         assert np.array_equal(np.isfinite(tg), fin)
-        assert np.all(np.abs(tg[fin] - to[fin]) <= RTOL_T * np.maximum(to[fin], 1e-3))
+        assert np.all(np.abs(tg[fin] - to[fin]) <= RTOL_T * np.maximum(to[fin], 1e-2))
     return float(err[ok].max())
 
 
@@ -159,7 +162,7 @@ def test_bvh_cast_matches_brute_force(M, orc, torch_cuda, mesh_name):
         assert id_g[i] == tid, (i, id_g[i], tid)
         if tid != orc.NO_HIT:
             hits += 1
-            assert abs(t_g[i] - t) <= RTOL_T * max(t, 1e-3), (i, t_g[i], t)
+            assert abs(t_g[i] - t) <= RTOL_T * max(t, 1e-2), (i, t_g[i], t)
         else:
             assert np.isinf(t_g[i])
     assert flagged <= n * 1e-3
