@@ -223,8 +223,12 @@ def test_spp_and_single_segment_and_no_mesh(M, orc, torch_cuda):
 
 
 def test_throughput_threshold(M, orc, torch_cuda):
+    # Termination at max(T) < tau is a threshold on a continuously falling T:
+    # inside a march T drops by 1-3 % per sample, so ~1e-4 / 0.02 of the
+    # threshold crossings land within the 1e-4 ambiguity margin.  The flagged
+    # fraction here is therefore allowed up to 1 %.
     sc = S.config2(48, 48, tau=0.05)
-    _compare(_render(M, sc), orc.render(sc))
+    _compare(_render(M, sc), orc.render(sc), max_flag_frac=1e-2)
 
 
 def test_mirror_box_series_on_gpu(M, orc, torch_cuda):
