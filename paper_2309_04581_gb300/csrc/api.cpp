@@ -1,5 +1,6 @@
 // The C ABI of include/mrf.h: argument checks, device memory ownership and
 // kernel dispatch.  No C++ exception crosses the boundary.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -53,6 +54,7 @@ struct mrf_context {
     LightDev *lights = nullptr;
     int n_lights = 0;
     unsigned long long *stats = nullptr;
+    unsigned *status = nullptr;  // device status word: non-zero after a kernel gave up
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
 };
@@ -96,6 +98,43 @@ static mrf_status dev_alloc(T **p, size_t n, const char *what) {
     return MRF_OK;
 }
 
+// IEEE binary16 from FP32, round to nearest even (overflow to infinity)
+static uint16_t f32_to_f16(float f) {
+    uint32_t x;
+    std::memcpy(&x, &f, 4);
+    const uint32_t sign = (x >> 16) & 0x8000u, e32 = (x >> 23) & 0xFFu, mant = x & 0x7FFFFFu;
+    if (e32 == 0xFFu) return (uint16_t)(sign | 0x7C00u | (mant ? 0x200u : 0u));
+    const int exp = (int)e32 - 127 + 15;
+    if (exp >= 31) return (uint16_t)(sign | 0x7C00u);
+    if (exp <= 0) {
+        if (exp < -10) return (uint16_t)sign;
+        const uint32_t m = mant | 0x800000u, shift = (uint32_t)(14 - exp);
+        uint32_t h = m >> shift;
+        const uint32_t rem = m & ((1u << shift) - 1u), half = 1u << (shift - 1u);
+        if (rem > half || (rem == half && (h & 1u))) ++h;
+        return (uint16_t)(sign | h);
+    }
+    uint32_t h = sign | ((uint32_t)exp << 10) | (mant >> 13);
+    const uint32_t rem = mant & 0x1FFFu;
+    if (rem > 0x1000u || (rem == 0x1000u && (h & 1u))) ++h;
+    return (uint16_t)h;
+}
+
+// bfloat16 from FP32, round to nearest even
+static uint16_t f32_to_bf16(float f) {
+    uint32_t x;
+    std::memcpy(&x, &f, 4);
+    if ((x & 0x7F800000u) == 0x7F800000u) return (uint16_t)((x >> 16) | ((x & 0xFFFFu) ? 0x40u : 0u));
+    x += 0x7FFFu + ((x >> 16) & 1u);
+    return (uint16_t)(x >> 16);
+}
+
+// byte offset of element (row r, column k) of a K-major operand with K columns
+// in the tensor-core layout without swizzle (8 x 16-byte core matrices)
+static size_t umma_offset(int r, int k, int K) {
+    return (size_t)(r / 8) * (K / 8) * 128 + (size_t)(k / 8) * 128 + (size_t)(r % 8) * 16 + (size_t)(k % 8) * 2;
+}
+
 // copy n elements from host or device memory into host vector
 template <class T>
 static mrf_status fetch(std::vector<T> &dst, const T *src, size_t n) {
@@ -130,7 +169,13 @@ mrf_status mrf_context_create(int device, mrf_context **out) {
         delete c;
         return st;
     }
+    if ((st = dev_alloc(&c->status, 1, "mrf_context_create: status")) != MRF_OK) {
+        cudaFree(c->stats);
+        delete c;
+        return st;
+    }
     cudaMemset(c->stats, 0, sizeof(unsigned long long) * ST_COUNT);
+    cudaMemset(c->status, 0, sizeof(unsigned));
     *out = c;
     return MRF_OK;
 }
@@ -140,6 +185,7 @@ void mrf_context_destroy(mrf_context *c) {
     cudaFree(c->mats);
     cudaFree(c->lights);
     cudaFree(c->stats);
+    cudaFree(c->status);
     cudaFree(c->scratch);
     delete c;
 }
@@ -243,6 +289,28 @@ static mrf_status field_create_impl(mrf_context *ctx, const mrf_field_desc *D, m
     std::memcpy(B3, b3.data(), 4 * 4);
     F.n_in = (int)n_in;
     if ((st = upload(f, pk.data(), pk.size(), &F.mlp, "mlp weights"))) return st;
+    // FP16 and BF16 copies of W1 (64 x in), W2 (64 x 64), W3 (padded to 16 x 64) in the
+    // tensor-core operand layout
+    {
+        const size_t w1b = 64 * (size_t)n_in * 2, per = w1b + 10240;
+        std::vector<uint8_t> lp(2 * per, 0);
+        for (int prec = 0; prec < 2; ++prec) {
+            uint8_t *base = lp.data() + prec * per;
+            auto put = [&](size_t off, float v) {
+                const uint16_t h = prec == 0 ? f32_to_f16(v) : f32_to_bf16(v);
+                std::memcpy(base + off, &h, 2);
+            };
+            for (int j = 0; j < 64; ++j)
+                for (int i = 0; i < (int)n_in; ++i) put(umma_offset(j, i, (int)n_in), w1[j * n_in + i]);
+            for (int j = 0; j < 64; ++j)
+                for (int i = 0; i < 64; ++i) put(w1b + umma_offset(j, i, 64), w2[j * 64 + i]);
+            for (int j = 0; j < 4; ++j)
+                for (int i = 0; i < 64; ++i) put(w1b + 8192 + umma_offset(j, i, 64), w3[j * 64 + i]);
+        }
+        const uint8_t *d = nullptr;
+        if ((st = upload(f, lp.data(), lp.size(), &d, "mlp weights (fp16/bf16)"))) return st;
+        F.mlp_lp = d;
+    }
     // support spheres
     const uint32_t S = D->n_support;
     if (S > 0) {
@@ -308,7 +376,17 @@ mrf_status mrf_field_query(mrf_context *ctx, const mrf_field *field, const float
     if (n == 0) return MRF_OK;
     if (!is_device_ptr(points) || !is_device_ptr(out))
         return fail(MRF_ERR_INVALID_ARG, "mrf_field_query: points and out must be device memory");
-    CUDA_TRY(launch_field_query(field->dev, points, n, out, (cudaStream_t)stream), "mrf_field_query: launch");
+    const FieldDev &F = field->dev;
+    const cudaStream_t s = (cudaStream_t)stream;
+    if (F.kind == MRF_FIELD_HASHGRID && F.precision != MRF_PREC_FP32) {
+        const int grid = (int)std::min<uint32_t>((n + 127) / 128, 152u * (uint32_t)field_tc_blocks_per_sm());
+        CUDA_TRY(launch_field_tc(F, F.precision == MRF_PREC_BF16, points, 3, nullptr, n, reinterpret_cast<float4 *>(out),
+                                 ctx->status, grid, s),
+                 "mrf_field_query: launch");
+    } else {
+        CUDA_TRY(launch_field_simt(F, points, 3, nullptr, n, reinterpret_cast<float4 *>(out), (int)((n + 127) / 128), s),
+                 "mrf_field_query: launch");
+    }
     return MRF_OK;
 }
 
@@ -510,6 +588,14 @@ mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *b
         if (pending != cudaSuccess) return cuda_fail(pending, "mrf_render: earlier asynchronous error");
     }
     cudaStream_t s = (cudaStream_t)stream;
+    {
+        unsigned st_word = 0;
+        CUDA_TRY(cudaMemcpy(&st_word, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost), "mrf_render: status read");
+        if (st_word) {
+            cudaMemset(ctx->status, 0, sizeof(unsigned));
+            return fail(MRF_ERR_TIMEOUT, "mrf_render: an earlier kernel gave up (status 0x%x)", st_word);
+        }
+    }
     RenderParams P{};
     P.F = field->dev;
     P.B = bvh->dev;
@@ -576,7 +662,13 @@ mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *b
     P.rec_seg = opts->rec_segments;
     P.rec_tri = opts->rec_tri;
     P.rec_t = opts->rec_t;
-    const int engine = opts->engine == MRF_ENGINE_AUTO ? MRF_ENGINE_MEGAKERNEL : opts->engine;
+    // AUTO: tensor-core field evaluation needs the wavefront engine's flat sample
+    // tiles; FP32 runs the megakernel
+    const bool lowp = field->dev.kind == MRF_FIELD_HASHGRID && field->dev.precision != MRF_PREC_FP32;
+    const int engine = opts->engine == MRF_ENGINE_AUTO ? (lowp ? MRF_ENGINE_WAVEFRONT : MRF_ENGINE_MEGAKERNEL)
+                                                       : opts->engine;
+    if (engine == MRF_ENGINE_MEGAKERNEL && lowp)
+        return fail(MRF_ERR_UNSUPPORTED, "mrf_render: FP16/BF16 fields run on the wavefront engine");
     size_t wf_off = 0;
     if (engine == MRF_ENGINE_WAVEFRONT) {
         wf_off = (scratch_need + 255) & ~(size_t)255;
@@ -596,6 +688,7 @@ mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *b
         P.ray_d = rays->dirs;
     }
     P.out = host_out ? (float *)(scr + out_off) : out_hdr;
+    P.status = ctx->status;
     if (stats) {
         CUDA_TRY(cudaMemsetAsync(ctx->stats, 0, sizeof(unsigned long long) * ST_COUNT, s), "stats reset");
         P.stats = ctx->stats;
@@ -621,8 +714,13 @@ mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *b
         stats->samples_evaluated = h[ST_EVALUATED];
         stats->shadow_samples_evaluated = h[ST_SHADOW_EVALUATED];
         stats->fp64_retests = h[ST_FP64];
-        stats->status = h[ST_STATUS];
-        if (h[ST_STATUS]) return fail(MRF_ERR_TIMEOUT, "mrf_render: kernel gave up (status %llu)", h[ST_STATUS]);
+        unsigned st_word = 0;
+        CUDA_TRY(cudaMemcpy(&st_word, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost), "mrf_render: status read");
+        stats->status = st_word;
+        if (st_word) {
+            cudaMemset(ctx->status, 0, sizeof(unsigned));
+            return fail(MRF_ERR_TIMEOUT, "mrf_render: a kernel gave up (status 0x%x)", st_word);
+        }
     } else if (host_out) {
         CUDA_TRY(cudaStreamSynchronize(s), "mrf_render: synchronize");
     }

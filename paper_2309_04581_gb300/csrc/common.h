@@ -34,7 +34,8 @@ struct FieldDev {
     const uint32_t *table;      // [level][entry] binary16 pairs (feature 0 low half)
     int n_in;
     const float *mlp;           // packed FP32, see mlp_floats
-    const uint16_t *mlp_lp;     // packed half / bf16 copies for the tensor-core engine
+    const void *mlp_lp;         // [FP16 | BF16] copies of W1, W2, W3 (W3 padded to 16 rows) in the
+                                // tensor-core operand layout, 64 * n_in * 2 + 10240 bytes each
     int n_support;
     const float4 *support;      // (cx, cy, cz, 1 / r^2)
     int occ_res;
@@ -88,12 +89,18 @@ struct RenderParams {
     float *out;
     uint32_t *rec_seg, *rec_tri;
     float *rec_t;
-    unsigned long long *stats;
+    unsigned long long *stats;   // nullable statistics counters
+    unsigned *status;            // context status word: bits set when a kernel gave up
 };
 
 // launchers (render_mega.cu)
 cudaError_t launch_render_megakernel(const RenderParams &P, cudaStream_t s);
-cudaError_t launch_field_query(const FieldDev &F, const float *pts, uint32_t n, float *out, cudaStream_t s);
+cudaError_t launch_field_simt(const FieldDev &F, const float *pts, int stride, const uint32_t *n_dev, uint32_t n_host,
+                              float4 *out, int grid, cudaStream_t s);
+// field_tc.cu
+cudaError_t launch_field_tc(const FieldDev &F, bool bf16, const float *pts, int stride, const uint32_t *n_dev,
+                            uint32_t n_host, float4 *out, unsigned *status, int grid, cudaStream_t s);
+int field_tc_blocks_per_sm();
 cudaError_t launch_cast(const BvhDev &B, const float *o, const float *d, const uint32_t *skip, uint32_t n, float tmin,
                         float *out_t, uint32_t *out_tri, unsigned long long *stats, cudaStream_t s);
 // bvh_refit.cu

@@ -231,7 +231,7 @@ struct Hit {
 };
 
 // Moller-Trumbore in FP64 (edge-inclusive), used to settle near-edge cases.
-__device__ __noinline__ bool mt_fp64(V3 of, V3 df, V3 a, V3 b, V3 c, float tmin, float &t_out) {
+static __device__ __noinline__ bool mt_fp64(V3 of, V3 df, V3 a, V3 b, V3 c, float tmin, float &t_out) {
     D3 o = d3(of), d = d3(df), v0 = d3(a);
     D3 e1 = d3(b) - v0, e2 = d3(c) - v0;
     D3 pv = cross(d, e2);

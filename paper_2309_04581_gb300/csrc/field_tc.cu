@@ -1,0 +1,283 @@
+// Tensor-core evaluation of the hash-grid field (the Instant-NGP field the
+// paper renders, Sec. 3.3): multiresolution hash encoding on the CUDA cores,
+// then the MLP in -> 64 -> 64 -> 4 on the 5th-generation tensor cores
+// (tcgen05.mma, FP16 or BF16 operands, FP32 accumulation in tensor memory).
+//
+// One CTA of 128 threads owns one 128-sample tile at a time (persistent over
+// tiles).  Thread r encodes sample r into row r of the A operand in shared
+// memory; one thread issues the MMAs of a layer and commits them to an
+// mbarrier; every thread then reads its row of the accumulator back from
+// tensor memory (warp w owns lanes 32w..32w+31), applies bias and ReLU in FP32
+// and writes the next layer's A operand.  All operands use the canonical
+// K-major layout without swizzle: 8-row x 16-byte core matrices stored as 128
+// contiguous bytes, K-adjacent core matrices 128 bytes apart (LBO) and
+// 8-row groups (K/8) * 128 bytes apart (SBO).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "path.cuh"
+
+namespace mrf {
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kSmemW1 = 0, kSmemW2 = 8192, kSmemW3 = 16384, kSmemA = 18432, kSmemBias = 34816;
+constexpr int kSmemBar = kSmemBias + 132 * 4, kSmemTmem = kSmemBar + 8, kSmemBytes = kSmemTmem + 8;
+constexpr uint32_t kTmemCols = 64;
+constexpr long long kWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// tcgen05 shared-memory matrix descriptor: start, LBO, SBO (all >> 4),
+// descriptor version 1 at bits 46-47, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: D = F32, A = B = F16 (0) or BF16 (1),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t instr_desc(bool bf16, int m, int n) {
+    return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+}
+
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld_x32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <bool kBF16>
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+    if (kBF16) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
+    } else {
+        __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
+}
+
+// 8 consecutive K values of row `row` into the canonical layout (sbo = (K/8)*128)
+__device__ __forceinline__ void store_chunk(uint8_t *base, int row, int chunk, int sbo, uint4 v) {
+    *reinterpret_cast<uint4 *>(base + (row >> 3) * sbo + chunk * 128 + (row & 7) * 16) = v;
+}
+
+template <bool kBF16>
+__device__ __forceinline__ void relu_bias_store(const uint32_t (&r)[32], const float *bias, uint8_t *A, int row,
+                                                int chunk0) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = 8 * c + 2 * q;
+            w[q] = pack2<kBF16>(fmaxf(__uint_as_float(r[k]) + bias[k], 0.f),
+                                fmaxf(__uint_as_float(r[k + 1]) + bias[k + 1], 0.f));
+        }
+        store_chunk(A, row, chunk0 + c, 1024, make_uint4(w[0], w[1], w[2], w[3]));
+    }
+}
+
+template <bool kBF16>
+__global__ void __launch_bounds__(kThreads, 4)
+    field_tc_kernel(const FieldDev F, const float *__restrict__ pts, int stride, const uint32_t *__restrict__ n_dev,
+                    uint32_t n_host, float4 *__restrict__ out, unsigned *__restrict__ status) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint8_t *sA = smem + kSmemA;
+    float *sBias = reinterpret_cast<float *>(smem + kSmemBias);
+    uint64_t *sBar = reinterpret_cast<uint64_t *>(smem + kSmemBar);
+    uint32_t *sTmem = reinterpret_cast<uint32_t *>(smem + kSmemTmem);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int n_in = F.n_in, kin = n_in / 16, sbo_in = (n_in / 8) * 128;
+
+    // stage the low-precision weights (already in the canonical layout) and FP32 biases
+    {
+        const int w1_bytes = 64 * n_in * 2;
+        const uint8_t *src = reinterpret_cast<const uint8_t *>(F.mlp_lp) + (kBF16 ? w1_bytes + 10240 : 0);
+        for (int o = tid * 16; o < w1_bytes; o += kThreads * 16)
+            *reinterpret_cast<uint4 *>(smem + kSmemW1 + o) = __ldg(reinterpret_cast<const uint4 *>(src + o));
+        for (int o = tid * 16; o < 10240; o += kThreads * 16)
+            *reinterpret_cast<uint4 *>(smem + kSmemW2 + o) = __ldg(reinterpret_cast<const uint4 *>(src + w1_bytes + o));
+        const float *b1 = F.mlp + n_in * 64, *b2 = b1 + 64 + 4096, *b3 = b2 + 64 + 256;
+        if (tid < 64) {
+            sBias[tid] = b1[tid];
+            sBias[64 + tid] = b2[tid];
+        }
+        if (tid < 4) sBias[128 + tid] = b3[tid];
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(sBar)), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(sTmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *sTmem;
+    const uint32_t t_row = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t aA = smem_u32(sA), aW1 = smem_u32(smem + kSmemW1), aW2 = smem_u32(smem + kSmemW2),
+                   aW3 = smem_u32(smem + kSmemW3), bar = smem_u32(sBar);
+    constexpr uint32_t id64 = instr_desc(kBF16, 128, 64), id16 = instr_desc(kBF16, 128, 16);
+    const uint32_t n = n_dev ? min(*n_dev, n_host) : n_host;
+    uint32_t phase = 0;
+    bool ok = true;
+
+    for (uint32_t tile = blockIdx.x; tile * 128u < n; tile += gridDim.x) {
+        const uint32_t i = tile * 128u + tid;
+        const bool valid = i < n;
+        V3 p = v3(0.f, 0.f, 0.f);
+        float s = 0.f;
+        if (valid) {
+            p = v3(pts[(size_t)stride * i], pts[(size_t)stride * i + 1], pts[(size_t)stride * i + 2]);
+            s = F.n_support ? field_support(F, p) : 1.f;
+            if (!inside_field_box(F, p)) s = 0.f;
+        }
+        // hash encoding -> A (K = n_in)
+        for (int c = 0; c < n_in / 8; ++c) {
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+            if (s > 0.f) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float2 f = hash_level(F, 4 * c + q, p);
+                    w[q] = pack2<kBF16>(f.x, f.y);
+                }
+            }
+            store_chunk(sA, tid, c, sbo_in, make_uint4(w[0], w[1], w[2], w[3]));
+        }
+        fence_async_smem();
+        fence_before_sync();
+        if (__syncthreads_or(!ok)) break;
+        if (tid == 0) {
+            fence_after_sync();
+            for (int k = 0; k < kin; ++k)
+                mma_f16(tmem, smem_desc(aA + 256 * k, 128, sbo_in), smem_desc(aW1 + 256 * k, 128, sbo_in), id64, k);
+            mma_commit(bar);
+        }
+        ok &= mbar_wait(bar, phase);
+        phase ^= 1;
+        fence_after_sync();
+        // layer 1 epilogue -> A (K = 64)
+        {
+            uint32_t r[32];
+            tmem_ld_x32(t_row, r);
+            relu_bias_store<kBF16>(r, sBias, sA, tid, 0);
+            tmem_ld_x32(t_row + 32, r);
+            relu_bias_store<kBF16>(r, sBias + 32, sA, tid, 4);
+        }
+        fence_async_smem();
+        fence_before_sync();
+        if (__syncthreads_or(!ok)) break;
+        if (tid == 0) {
+            fence_after_sync();
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                mma_f16(tmem, smem_desc(aA + 256 * k, 128, 1024), smem_desc(aW2 + 256 * k, 128, 1024), id64, k);
+            mma_commit(bar);
+        }
+        ok &= mbar_wait(bar, phase);
+        phase ^= 1;
+        fence_after_sync();
+        // layer 2 epilogue -> A (K = 64)
+        {
+            uint32_t r[32];
+            tmem_ld_x32(t_row, r);
+            relu_bias_store<kBF16>(r, sBias + 64, sA, tid, 0);
+            tmem_ld_x32(t_row + 32, r);
+            relu_bias_store<kBF16>(r, sBias + 96, sA, tid, 4);
+        }
+        fence_async_smem();
+        fence_before_sync();
+        if (__syncthreads_or(!ok)) break;
+        if (tid == 0) {
+            fence_after_sync();
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                mma_f16(tmem, smem_desc(aA + 256 * k, 128, 1024), smem_desc(aW3 + 256 * k, 128, 1024), id16, k);
+            mma_commit(bar);
+        }
+        ok &= mbar_wait(bar, phase);
+        phase ^= 1;
+        fence_after_sync();
+        {
+            uint32_t r[16];
+            tmem_ld_x16(t_row, r);
+            const float o0 = __uint_as_float(r[0]) + sBias[128], o1 = __uint_as_float(r[1]) + sBias[129],
+                        o2 = __uint_as_float(r[2]) + sBias[130], o3 = __uint_as_float(r[3]) + sBias[131];
+            if (valid) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (s > 0.f) v = make_float4(s * expf(fminf(o0, 15.f)), softplusf(o1), softplusf(o2), softplusf(o3));
+                out[i] = v;
+            }
+        }
+        fence_before_sync();
+    }
+    if (!ok && tid == 0 && status) atomicOr(status, 4u);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+}  // namespace
+
+int field_tc_blocks_per_sm() { return 4; }
+
+cudaError_t launch_field_tc(const FieldDev &F, bool bf16, const float *pts, int stride, const uint32_t *n_dev,
+                            uint32_t n_host, float4 *out, unsigned *status, int grid, cudaStream_t s) {
+    auto kern = bf16 ? field_tc_kernel<true> : field_tc_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    if (grid <= 0) grid = 1;
+    kern<<<grid, kThreads, kSmemBytes, s>>>(F, pts, stride, n_dev, n_host, out, status);
+    return cudaGetLastError();
+}
+
+}  // namespace mrf

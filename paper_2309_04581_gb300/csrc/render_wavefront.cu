@@ -1,12 +1,454 @@
-// Wavefront engine (not built yet): the megakernel is the only engine.
+// Wavefront engine: Algorithm 1 run segment by segment over all live paths.
+//
+// Per segment j the host enqueues (no host synchronisation):
+//   1. wf_cast_gen : closest hit, shadow-ray visibility at diffuse hits, and
+//                    generation of every field sample the segment march and
+//                    the shadow-ray marches need (occupancy skip and support
+//                    test), packed contiguously per job in one flat buffer;
+//   2. field       : evaluation of all generated samples, on the tensor cores
+//                    for the hash grid at FP16/BF16 (field_tc.cu), else FP32;
+//   3. wf_shade    : in-order compositing of each job's samples (Eqs. 10-11),
+//                    next-event term, BSDF sample (Eqs. 12-13), termination,
+//                    and compaction of the surviving paths into the next queue.
+// Sample positions, quadrature intervals and every decision are computed with
+// the same FP32 formulas as the megakernel.  Jobs whose samples do not fit the
+// sample buffer are marched in place by wf_shade on the CUDA cores.
+#include <algorithm>
 #include <cuda_runtime.h>
 
-#include "common.h"
+#include "path.cuh"
 
 namespace mrf {
 
-bool wavefront_available() { return false; }
-size_t wavefront_scratch_bytes(const RenderParams &) { return 0; }
-cudaError_t launch_render_wavefront(const RenderParams &, void *, size_t, cudaStream_t) { return cudaErrorNotSupported; }
+namespace {
+
+constexpr uint32_t kOverflow = 0xFFFFFFFFu;
+constexpr int kThreads = 128;
+
+struct WfParams {
+    RenderParams R;
+    uint32_t paths;
+    float4 *acc;                    // per path: L (rgb), camera-segment opacity
+    uint32_t *qpath[2];             // live queues: path ids
+    float4 *qo[2], *qd[2], *qT[2];  // origin (+ previous triangle id bits), direction, throughput
+    float *hit_t;                   // per live slot, current segment
+    int *hit_slot;
+    uint32_t *hit_id;
+    uint32_t *rstart, *rcount;      // radiance samples of the slot's segment
+    uint32_t *sstart, *scount;      // shadow samples, [slot * n_lights + l]
+    float4 *sw;                     // next-event weight (rgb), w = 1 when the light is visible
+    uint32_t *ctr;                  // [0], [1] live counts; [2] generated samples
+    float4 *samp;                   // sample position (xyz) and interval length (w)
+    float4 *fout;                   // sigma, r, g, b per sample
+    uint32_t cap;                   // sample capacity
+};
+
+// exclusive prefix of n over a fully converged warp plus one atomic per warp
+__device__ __forceinline__ uint32_t warp_alloc(uint32_t *ctr, uint32_t n) {
+    const int lane = threadIdx.x & 31;
+    uint32_t x = n;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, x, 31);
+    uint32_t base = 0;
+    if (lane == 31 && total) base = atomicAdd(ctr, total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    return base + x - n;
+}
+
+// Walks the quadrature intervals of [a, b] exactly like march() and counts (or
+// writes) the samples whose density can be non-zero: occupied cell and, for the
+// hash grid, positive support.
+template <bool emit>
+__device__ uint32_t walk_samples(const RenderParams &P, V3 o, V3 d, float a, float b, float4 *out,
+                                 unsigned long long &nominal) {
+    const FieldDev &F = P.F;
+    float tb0, tb1;
+    if (!box_interval(F.lo, F.hi, o, d, tb0, tb1)) return 0;
+    const float t0 = fmaxf(a, tb0), t1 = fminf(b, tb1);
+    if (!(t1 > t0)) return 0;
+    int n;
+    float h;
+    if (P.steps) {
+        n = (int)P.steps;
+        h = (t1 - t0) / (float)n;
+    } else {
+        h = P.dt;
+        const float nf = ceilf((t1 - t0) / h);
+        if (nf > 16777216.f) return 0;
+        n = (int)nf;
+    }
+    if (!emit) nominal += (unsigned long long)n;
+    const V3 inv = v3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+    const bool hash = F.kind == MRF_FIELD_HASHGRID;
+    const bool use_occ = hash && F.occ != nullptr;
+    uint32_t k = 0;
+    for (int i = 0; i < n;) {
+        const float lo = fmaf((float)i, h, t0);
+        const float hi = P.steps ? fmaf((float)(i + 1), h, t0) : fminf(lo + h, t1);
+        const float tm = 0.5f * (lo + hi), delta = hi - lo;
+        const V3 p = fma3(d, tm, o);
+        if (use_occ) {
+            int c[3];
+            if (!occupied(F, p, c)) {
+                const float te = cell_exit(F, c, o, inv);
+                const int j = (int)ceilf((te - t0) / h - 0.5f);
+                i = max(i + 1, j);
+                continue;
+            }
+        }
+        if (hash && !(field_support(F, p) > 0.f)) {
+            ++i;
+            continue;
+        }
+        if (emit) out[k] = make_float4(p.x, p.y, p.z, delta);
+        ++k;
+        ++i;
+    }
+    return k;
+}
+
+__global__ void __launch_bounds__(kThreads) wf_cast_gen(const WfParams W, uint32_t j, int cur) {
+    const RenderParams &P = W.R;
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t live = j == 1 ? W.paths : W.ctr[cur];
+    const bool active = tid < live;
+    const int nl = P.n_lights;
+    Counters C = {};
+    V3 o = v3(0.f, 0.f, 0.f), d = v3(0.f, 0.f, 1.f);
+    uint32_t prev = kNoHit;
+    Hit h;
+    h.t = INFINITY;
+    h.id = kNoHit;
+    h.slot = -1;
+    uint32_t n_r = 0, n_s_total = 0;
+    SurfaceHit S;
+    bool diffuse = false;
+    if (active) {
+        if (j == 1) {
+            const uint32_t path = tid, ray = path / P.spp;
+            primary_ray(P, ray, o, d);
+            W.qpath[cur][tid] = path;
+            W.qo[cur][tid] = make_float4(o.x, o.y, o.z, __uint_as_float(kNoHit));
+            W.qd[cur][tid] = make_float4(d.x, d.y, d.z, 0.f);
+            W.qT[cur][tid] = make_float4(1.f, 1.f, 1.f, 0.f);
+            ++C.paths;
+        } else {
+            const float4 qo = W.qo[cur][tid], qd = W.qd[cur][tid];
+            o = v3(qo.x, qo.y, qo.z);
+            prev = __float_as_uint(qo.w);
+            d = v3(qd.x, qd.y, qd.z);
+        }
+        unsigned rt = 0;
+        bool fault = false;
+        bvh_trace<false>(P.B, o, d, prev, P.tmin, INFINITY, h, rt, fault);
+        C.retests += rt;
+        if (fault) C.fault |= 1;
+        n_r = walk_samples<false>(P, o, d, 0.f, h.t, nullptr, C.nominal);
+        if (h.id != kNoHit) {
+            S = surface_at(P, o, d, h);
+            diffuse = S.mat.kind == MRF_MAT_DIFFUSE;
+        }
+        if (diffuse) {
+            for (int l = 0; l < nl; ++l) {
+                V3 wl;
+                float D, D2, cosl;
+                uint32_t ns = 0;
+                float4 wgt = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (light_geometry(P, S, l, wl, D, D2, cosl)) {
+                    ++C.shadow;
+                    Hit hs;
+                    unsigned rs = 0;
+                    bool f2 = false;
+                    const bool blocked = bvh_trace<true>(P.B, S.p, wl, S.id, P.tmin, D, hs, rs, f2);
+                    C.retests += rs;
+                    if (f2) C.fault |= 1;
+                    if (!blocked) {
+                        float w3[3];
+                        nee_weight(P, S, l, cosl, D2, w3);
+                        wgt = make_float4(w3[0], w3[1], w3[2], 1.f);
+                        ns = walk_samples<false>(P, S.p, wl, 0.f, D, nullptr, C.nominal);
+                    }
+                }
+                W.sw[(size_t)tid * nl + l] = wgt;
+                W.scount[(size_t)tid * nl + l] = ns;
+                n_s_total += ns;
+            }
+        }
+    }
+    const uint32_t n_total = n_r + n_s_total;
+    const uint32_t base = warp_alloc(&W.ctr[2], n_total);
+    if (active) {
+        const bool fits = (uint64_t)base + n_total <= (uint64_t)W.cap;
+        W.hit_t[tid] = h.t;
+        W.hit_slot[tid] = h.slot;
+        W.hit_id[tid] = h.id;
+        uint32_t k = base;
+        if (fits) {
+            walk_samples<true>(P, o, d, 0.f, h.t, W.samp + k, C.nominal);
+            W.rstart[tid] = k;
+            W.rcount[tid] = n_r;
+            k += n_r;
+        } else {
+            W.rcount[tid] = kOverflow;
+        }
+        C.evaluated += n_r;
+        if (diffuse) {
+            for (int l = 0; l < nl; ++l) {
+                const size_t idx = (size_t)tid * nl + l;
+                const uint32_t ns = W.scount[idx];
+                if (W.sw[idx].w == 0.f) continue;
+                if (fits) {
+                    V3 wl;
+                    float D, D2, cosl;
+                    light_geometry(P, S, l, wl, D, D2, cosl);
+                    walk_samples<true>(P, S.p, wl, 0.f, D, W.samp + k, C.nominal);
+                    W.sstart[idx] = k;
+                    k += ns;
+                } else {
+                    W.scount[idx] = kOverflow;
+                }
+                C.shadow_eval += ns;
+            }
+        }
+    }
+    flush_counters(P.stats, C);
+    if (C.fault && P.status) atomicOr(P.status, C.fault);
+}
+
+__global__ void __launch_bounds__(kThreads) wf_shade(const WfParams W, uint32_t j, int cur, int nxt) {
+    const RenderParams &P = W.R;
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t live = W.ctr[cur];
+    const bool active = tid < live;
+    const int nl = P.n_lights;
+    Counters C = {};
+    bool push = false;
+    uint32_t path = 0, prev = kNoHit;
+    V3 o = v3(0.f, 0.f, 0.f), d = v3(0.f, 0.f, 1.f);
+    float T[3] = {1.f, 1.f, 1.f};
+    if (active) {
+        path = W.qpath[cur][tid];
+        const uint32_t ray = path / P.spp, s = path % P.spp;
+        const float4 qo = W.qo[cur][tid], qd = W.qd[cur][tid], qT = W.qT[cur][tid];
+        o = v3(qo.x, qo.y, qo.z);
+        d = v3(qd.x, qd.y, qd.z);
+        T[0] = qT.x; T[1] = qT.y; T[2] = qT.z;
+        float4 acc = j == 1 ? make_float4(0.f, 0.f, 0.f, 0.f) : W.acc[path];
+        float L[3] = {acc.x, acc.y, acc.z};
+        Hit h;
+        h.t = W.hit_t[tid];
+        h.slot = W.hit_slot[tid];
+        h.id = W.hit_id[tid];
+        // Eqs. 10-11 over the segment's samples, in order
+        const float T0 = T[0];
+        bool stop = false;
+        const uint32_t rc = W.rcount[tid];
+        if (rc == kOverflow) {
+            Counters dummy = {};
+            march<true>(P, P.F.mlp, o, d, 0.f, h.t, T, L, stop, dummy);
+        } else {
+            const uint32_t r0 = W.rstart[tid];
+            for (uint32_t k = r0; k < r0 + rc; ++k) {
+                const float4 f = W.fout[k];
+                const float x = f.x * W.samp[k].w;
+                const float att = expf(-x), alpha = -expm1f(-x);
+                L[0] = fmaf(T[0] * alpha, f.y, L[0]);
+                L[1] = fmaf(T[1] * alpha, f.z, L[1]);
+                L[2] = fmaf(T[2] * alpha, f.w, L[2]);
+                T[0] *= att;
+                T[1] *= att;
+                T[2] *= att;
+                if (P.tau > 0.f && fmaxf(T[0], fmaxf(T[1], T[2])) < P.tau) {
+                    stop = true;
+                    break;
+                }
+            }
+        }
+        if (j == 1) acc.w = T0 > 0.f ? 1.f - T[0] / T0 : 0.f;
+        ++C.seg;
+        const uint64_t rbase = (uint64_t)path * P.max_bounces;
+        if (P.rec_tri) {
+            P.rec_tri[rbase + (j - 1)] = h.id;
+            P.rec_t[rbase + (j - 1)] = h.t;
+        }
+        bool end = stop || h.id == kNoHit;
+        if (!end) {
+            ++C.hits;
+            const SurfaceHit S = surface_at(P, o, d, h);
+            float u[3];
+            surface_uniforms(P, ray, s, j, u);
+            if (S.mat.kind == MRF_MAT_DIFFUSE) {
+                for (int l = 0; l < nl; ++l) {
+                    const size_t idx = (size_t)tid * nl + l;
+                    const float4 wgt = W.sw[idx];
+                    if (wgt.w == 0.f) continue;
+                    const uint32_t sc = W.scount[idx];
+                    float depth = 0.f;
+                    if (sc == kOverflow) {
+                        V3 wl;
+                        float D, D2, cosl;
+                        light_geometry(P, S, l, wl, D, D2, cosl);
+                        Counters dummy = {};
+                        bool dstop = false;
+                        depth = march<false>(P, P.F.mlp, S.p, wl, 0.f, D, nullptr, nullptr, dstop, dummy);
+                    } else {
+                        const uint32_t s0 = W.sstart[idx];
+                        for (uint32_t k = s0; k < s0 + sc; ++k) depth = fmaf(W.fout[k].x, W.samp[k].w, depth);
+                    }
+                    const float Tf = expf(-depth);
+                    L[0] = fmaf(T[0] * Tf, wgt.x, L[0]);
+                    L[1] = fmaf(T[1] * Tf, wgt.y, L[1]);
+                    L[2] = fmaf(T[2] * Tf, wgt.z, L[2]);
+                }
+            }
+            const V3 nd = bsdf_sample(S, d, u, T);
+            d = normalize(nd);
+            o = S.p;
+            prev = S.id;
+            if (j == P.max_bounces) end = true;
+            if (P.tau > 0.f && fmaxf(T[0], fmaxf(T[1], T[2])) < P.tau) end = true;
+        }
+        acc.x = L[0];
+        acc.y = L[1];
+        acc.z = L[2];
+        W.acc[path] = acc;
+        if (end) {
+            if (P.rec_seg) P.rec_seg[path] = j;
+            if (P.rec_tri)
+                for (uint32_t q = j; q < P.max_bounces; ++q) {
+                    P.rec_tri[rbase + q] = kNoHit;
+                    P.rec_t[rbase + q] = INFINITY;
+                }
+        }
+        push = !end;
+    }
+    const uint32_t slot = warp_alloc(&W.ctr[nxt], push ? 1u : 0u);
+    if (push) {
+        W.qpath[nxt][slot] = path;
+        W.qo[nxt][slot] = make_float4(o.x, o.y, o.z, __uint_as_float(prev));
+        W.qd[nxt][slot] = make_float4(d.x, d.y, d.z, 0.f);
+        W.qT[nxt][slot] = make_float4(T[0], T[1], T[2], 0.f);
+    }
+    flush_counters(P.stats, C);
+}
+
+__global__ void __launch_bounds__(kThreads) wf_finalize(const float4 *__restrict__ acc, uint32_t count, uint32_t spp,
+                                                        float4 *__restrict__ out) {
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= count) return;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (uint32_t s = 0; s < spp; ++s) {
+        const float4 v = acc[(size_t)r * spp + s];
+        a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
+    }
+    const float inv = 1.f / (float)spp;
+    out[r] = make_float4(a.x * inv, a.y * inv, a.z * inv, a.w * inv);
+}
+
+// scratch layout
+struct Layout {
+    size_t acc, qpath[2], qo[2], qd[2], qT[2], hit_t, hit_slot, hit_id, rstart, rcount, sstart, scount, sw, ctr, samp,
+        fout, total;
+    uint32_t cap;
+};
+
+Layout layout(uint32_t paths, int n_lights) {
+    Layout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t P = paths, nl = (size_t)std::max(n_lights, 1);
+    L.acc = take(16 * P);
+    for (int q = 0; q < 2; ++q) {
+        L.qpath[q] = take(4 * P);
+        L.qo[q] = take(16 * P);
+        L.qd[q] = take(16 * P);
+        L.qT[q] = take(16 * P);
+    }
+    L.hit_t = take(4 * P);
+    L.hit_slot = take(4 * P);
+    L.hit_id = take(4 * P);
+    L.rstart = take(4 * P);
+    L.rcount = take(4 * P);
+    L.sstart = take(4 * P * nl);
+    L.scount = take(4 * P * nl);
+    L.sw = take(16 * P * nl);
+    L.ctr = take(16);
+    // sample capacity: 96 samples per path plus 4M (overflowing jobs are marched in place)
+    const uint64_t cap = std::min<uint64_t>((uint64_t)P * 96 + (4u << 20), 0x7FFFFFFFull);
+    L.cap = (uint32_t)cap;
+    L.samp = take(16 * cap);
+    L.fout = take(16 * cap);
+    L.total = off;
+    return L;
+}
+
+}  // namespace
+
+bool wavefront_available() { return true; }
+
+size_t wavefront_scratch_bytes(const RenderParams &P) {
+    return layout(P.count * P.spp, P.n_lights).total;
+}
+
+cudaError_t launch_render_wavefront(const RenderParams &P, void *scratch, size_t scratch_bytes, cudaStream_t s) {
+    const uint32_t paths = P.count * P.spp;
+    const Layout Lo = layout(paths, P.n_lights);
+    if (scratch_bytes < Lo.total) return cudaErrorInvalidValue;
+    char *b = static_cast<char *>(scratch);
+    WfParams W{};
+    W.R = P;
+    W.paths = paths;
+    W.acc = reinterpret_cast<float4 *>(b + Lo.acc);
+    for (int q = 0; q < 2; ++q) {
+        W.qpath[q] = reinterpret_cast<uint32_t *>(b + Lo.qpath[q]);
+        W.qo[q] = reinterpret_cast<float4 *>(b + Lo.qo[q]);
+        W.qd[q] = reinterpret_cast<float4 *>(b + Lo.qd[q]);
+        W.qT[q] = reinterpret_cast<float4 *>(b + Lo.qT[q]);
+    }
+    W.hit_t = reinterpret_cast<float *>(b + Lo.hit_t);
+    W.hit_slot = reinterpret_cast<int *>(b + Lo.hit_slot);
+    W.hit_id = reinterpret_cast<uint32_t *>(b + Lo.hit_id);
+    W.rstart = reinterpret_cast<uint32_t *>(b + Lo.rstart);
+    W.rcount = reinterpret_cast<uint32_t *>(b + Lo.rcount);
+    W.sstart = reinterpret_cast<uint32_t *>(b + Lo.sstart);
+    W.scount = reinterpret_cast<uint32_t *>(b + Lo.scount);
+    W.sw = reinterpret_cast<float4 *>(b + Lo.sw);
+    W.ctr = reinterpret_cast<uint32_t *>(b + Lo.ctr);
+    W.samp = reinterpret_cast<float4 *>(b + Lo.samp);
+    W.fout = reinterpret_cast<float4 *>(b + Lo.fout);
+    W.cap = Lo.cap;
+    const unsigned grid = (paths + kThreads - 1) / kThreads;
+    const FieldDev &F = P.F;
+    const bool tc = F.kind == MRF_FIELD_HASHGRID && F.precision != MRF_PREC_FP32;
+    const int field_grid = tc ? 152 * field_tc_blocks_per_sm() : 152 * 8;
+    cudaError_t e = cudaMemsetAsync(W.ctr, 0, 16, s);
+    if (e != cudaSuccess) return e;
+    for (uint32_t j = 1; j <= P.max_bounces; ++j) {
+        const int cur = (j - 1) & 1, nxt = j & 1;
+        if ((e = cudaMemsetAsync(W.ctr + 2, 0, 4, s)) != cudaSuccess) return e;
+        wf_cast_gen<<<grid, kThreads, 0, s>>>(W, j, cur);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (tc)
+            e = launch_field_tc(F, F.precision == MRF_PREC_BF16, reinterpret_cast<const float *>(W.samp), 4, W.ctr + 2,
+                                W.cap, W.fout, P.status, field_grid, s);
+        else
+            e = launch_field_simt(F, reinterpret_cast<const float *>(W.samp), 4, W.ctr + 2, W.cap, W.fout, field_grid, s);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(W.ctr + nxt, 0, 4, s)) != cudaSuccess) return e;
+        wf_shade<<<grid, kThreads, 0, s>>>(W, j, cur, nxt);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    wf_finalize<<<(P.count + kThreads - 1) / kThreads, kThreads, 0, s>>>(W.acc, P.count, P.spp,
+                                                                          reinterpret_cast<float4 *>(P.out));
+    return cudaGetLastError();
+}
 
 }  // namespace mrf

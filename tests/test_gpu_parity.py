@@ -328,3 +328,104 @@ def test_invalid_arguments_on_gpu(M, torch_cuda):
     with pytest.raises(M.MrfError):
         M.mrf_field_create(r.ctx, bad)
     r.close()
+
+
+# ----------------------------------------------------------------- tensor-core field
+# (sigma relative, radiance absolute); measured on GB300: fp16 6.7e-5 / 4.6e-5, bf16 5.0e-4 / 3.0e-4
+TC_TOL = {"fp16": (2e-4, 1e-4), "bf16": (2e-3, 1e-3)}
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("n", [1, 4000, 128 * 1300 + 17])
+def test_field_query_tensor_cores(M, orc, torch_cuda, prec, n):
+    """tcgen05 MLP (FP16/BF16 operands, FP32 accumulation) vs the FP64 oracle.
+    n covers a single sample, a ragged tail and more tiles than resident CTAs."""
+    torch = torch_cuda
+    sc = S.config2(8, 8)
+    f = sc.field
+    rng = np.random.default_rng(21)
+    k = rng.integers(0, f.support_center.shape[0], n)
+    pts = f.support_center[k] + rng.uniform(-1, 1, (n, 3)) * f.support_radius[k, None] * 0.6
+    pts = np.clip(pts, -0.5, 0.5).astype(np.float32)
+    check = np.arange(n) if n <= 4000 else rng.choice(n, 3000, replace=False)
+    osc = orc.OracleScene(sc)
+    ref = np.array([[orc.field_eval(osc, p)[0], *orc.field_eval(osc, p)[1]] for p in pts[check].astype(np.float64)])
+    ctx = M.mrf_context_create(0)
+    desc, keep = M.field_desc(f, {"fp16": M.MRF_PREC_FP16, "bf16": M.MRF_PREC_BF16}[prec])
+    fh = M.mrf_field_create(ctx, desc)
+    dp = torch.from_numpy(pts).cuda()
+    out = torch.full((n, 4), float("nan"), dtype=torch.float32, device="cuda")
+    M.mrf_field_query(ctx, fh, dp.data_ptr(), n, out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    got = out.cpu().numpy().astype(np.float64)[check]
+    M.mrf_field_destroy(fh)
+    M.mrf_context_destroy(ctx)
+    assert np.all(np.isfinite(got))
+    pos = ref[:, 0] > 0
+    sig_rel = np.abs(got[pos, 0] - ref[pos, 0]) / ref[pos, 0]
+    rgb_abs = np.abs(got[:, 1:] - ref[:, 1:])
+    print(f"{prec} n={n}: sigma rel max {sig_rel.max():.3g} mean {sig_rel.mean():.3g}; "
+          f"radiance abs max {rgb_abs.max():.3g}")
+    assert np.all(got[~pos] == 0)
+    assert sig_rel.max() <= TC_TOL[prec][0]
+    assert rgb_abs.max() <= TC_TOL[prec][1]
+
+
+# ----------------------------------------------------------------- wavefront engine
+def _psnr(img, ref, ok):
+    peak = np.abs(ref[ok, :3]).max()
+    mse = np.mean((img[ok, :3] - ref[ok, :3]) ** 2)
+    return float("inf") if mse == 0 else 10 * np.log10(peak * peak / mse)
+
+
+@pytest.mark.parametrize("cfg", ["c1", "c2"])
+def test_wavefront_fp32_matches_oracle(M, orc, torch_cuda, cfg):
+    sc = S.config1() if cfg == "c1" else S.config2(64, 64)
+    gpu = _render(M, sc, engine=M.MRF_ENGINE_WAVEFRONT)
+    _compare(gpu, orc.render(sc))
+
+
+def _render_prec(M, sc, prec, records=True):
+    import torch
+    r = M.Renderer(sc, precision={"fp16": M.MRF_PREC_FP16, "bf16": M.MRF_PREC_BF16}[prec])
+    rec = r.new_records() if records else None
+    out, stats = r.render(records=rec, stats=True)
+    torch.cuda.synchronize()
+    res = dict(rgba=out.cpu().numpy().astype(np.float64), stats=stats)
+    if records:
+        res.update(segments=rec["segments"].cpu().numpy().view(np.uint32).reshape(sc.n_rays, sc.opts.spp),
+                   tri=rec["tri"].cpu().numpy().view(np.uint32).reshape(sc.n_rays, sc.opts.spp, sc.opts.max_bounces),
+                   t=rec["t"].cpu().numpy().reshape(sc.n_rays, sc.opts.spp, sc.opts.max_bounces))
+    r.close()
+    return res
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_wavefront_tensor_core_image_quality(M, orc, torch_cuda, prec):
+    """Reduced-precision renders keep every geometric decision of the FP32 path
+    (hit ids, segment counts, distances) and reach >= 45 dB PSNR with <= 1e-2
+    max absolute error in linear HDR against the FP64 oracle."""
+    sc = S.config2(96, 96)
+    gpu = _render_prec(M, sc, prec)
+    ref = orc.render(sc)
+    ok = ref["flags"] == 0
+    psnr = _psnr(gpu["rgba"], ref["rgba"], ok)
+    maxabs = np.abs(gpu["rgba"][ok, :3] - ref["rgba"][ok, :3]).max()
+    print(f"{prec}: PSNR {psnr:.1f} dB, max abs {maxabs:.3g}")
+    assert psnr >= 45.0 and maxabs <= 1e-2
+    assert np.array_equal(gpu["segments"][ok], ref["segments"][ok])
+    assert np.array_equal(gpu["tri"][ok], ref["tri"][ok])
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_wavefront_tensor_core_full_size_sampled(M, orc, torch_cuda, prec):
+    # the 800x800 workload in the benchmark's configuration, oracle on every 16th row/column
+    sc = S.config2(800, 800)
+    gpu = _render_prec(M, sc, prec, records=False)
+    ids = S.strided_pixels(800, 800, 16, offset=3)
+    ref = orc.render(sc, ids)
+    ok = ref["flags"] == 0
+    img = gpu["rgba"][ids]
+    psnr = _psnr(img, ref["rgba"], ok)
+    maxabs = np.abs(img[ok, :3] - ref["rgba"][ok, :3]).max()
+    print(f"{prec} 800x800 sampled: PSNR {psnr:.1f} dB, max abs {maxabs:.3g}")
+    assert psnr >= 45.0 and maxabs <= 1e-2
