@@ -1,12 +1,18 @@
 """Benchmark of the hybrid light-transport loop (one step = one full render).
 
-Workload: the hash-grid scene of the paper-shaped benchmark (800x800, 1 spp,
-16-level hash grid with 2^19 FP16 entries per level, MLP 32-64-64-4, 128^3
-occupancy, 10,240-triangle glass sphere, mirror cube, diffuse floor, one
-point light, up to 8 segments per path, fixed step sqrt(3)/1024).  Inputs are
-synthetic and seeded.  Prints one JSON line.
+Workload: the hash-grid scene at 800x800 (1 spp, up to 8 segments per path):
+16-level hash grid with 2^19 FP16 entries per level (resolutions 16..2048), MLP
+32-64-64-4 with exp density and softplus radiance, 128^3 occupancy, a
+10,240-triangle glass sphere, a mirror cube, a diffuse floor and one point
+light, fixed step sqrt(3)/1024.  Inputs are synthetic and seeded.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp16|bf16]
+The headline runs the mixed-precision renderer (wavefront engine, BF16 MLP on
+the tensor cores, FP32 everywhere else); the same line carries the FP32 GPU
+path (megakernel) measured the same way, the image error of the headline
+against the FP64 oracle on the CPU-baseline pixel sample, the per-kernel
+timings and the dominant kernel's roofline.  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp16|fp32]
     python bench.py --impl reference    # the FP64 CPU oracle on the host cores
 
 Under torchrun (N > 1) every rank renders its own copy of the workload
@@ -30,22 +36,25 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ray-segments/s"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
-FP32_FLOP_PER_SAMPLE = 2 * (32 * 64 + 64 * 64 + 64 * 4)  # MLP multiply-adds x 2
+MLP_FLOP_PER_SAMPLE = 2 * (32 * 64 + 64 * 64 + 64 * 4)   # 12,800
+GATHER_BYTES_PER_SAMPLE = 16 * 8 * 4                       # 16 levels x 8 corners x (2 x FP16)
+SAMPLE_IO_BYTES = 16 + 16                                  # sample record in, (sigma, rgb) out
 SM_COUNT, FP32_LANES_PER_SM = 152, 128
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--engine", default="auto", choices=["auto", "megakernel", "wavefront"])
     ap.add_argument("--width", type=int, default=800)
     ap.add_argument("--height", type=int, default=800)
     ap.add_argument("--cpu-stride", type=int, default=4, help="oracle sample: every n-th row and column")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 comparison run")
     return ap.parse_args()
 
 
@@ -93,9 +102,16 @@ class ClockSampler:
 
     def summary(self):
         if not self.rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [v for v in (num(r[1]) for r in self.rows) if v is not None]
+        mx = [v for v in (num(r[2]) for r in self.rows) if v is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for r in self.rows for k in range(4) if len(r) > 5 + k and r[5 + k] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
@@ -105,7 +121,9 @@ class ClockSampler:
 def workload(args):
     from paper_2309_04581_gb300 import scenes as S
     sc = S.config2(args.width, args.height)
-    name = f"hash-grid field + glass/mirror/diffuse meshes, {args.width}x{args.height}, 1 spp, 8 bounces"
+    name = (f"hash-grid field (16 levels, 2^19 FP16 entries, MLP 32-64-64-4, 128^3 occupancy) + "
+            f"10,240-triangle glass sphere, mirror cube, diffuse floor, 1 point light; "
+            f"{args.width}x{args.height}, 1 spp, up to 8 segments per path")
     return sc, name
 
 
@@ -119,9 +137,11 @@ def cpu_baseline(sc, stride: int):
     res = oracle.render(sc, ids, records=False)
     dt = time.perf_counter() - t
     seg = res["counts"]["segments"]
-    return {"value": seg / dt, "unit": METRIC, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"every {stride}th row and column ({len(ids)} of {sc.n_rays} pixels), {seg} segments in {dt:.1f} s",
-            "samples_per_s": res["counts"]["samples_supported"] / dt}
+    cb = {"value": seg / dt, "unit": METRIC, "cores": oracle.num_threads(), "kind": "oracle",
+          "sample": f"every {stride}th row and column ({len(ids)} of {sc.n_rays} pixels), "
+                    f"{seg} segments in {dt:.1f} s",
+          "field_samples_per_s": res["counts"]["samples_supported"] / dt}
+    return cb, ids, res
 
 
 def run_reference(args):
@@ -129,22 +149,51 @@ def run_reference(args):
     if rank != 0:
         return
     sc, name = workload(args)
-    cb = None
-    vals = []
+    stride = max(args.cpu_stride, 8)
     for _ in range(args.warmup):
-        pass
+        pass  # the oracle has no warm-up state
+    vals, cb = [], None
     for _ in range(max(1, args.steps)):
-        cb = cpu_baseline(sc, max(args.cpu_stride, 8))
+        cb, _, _ = cpu_baseline(sc, stride)
         vals.append(cb["value"])
     v = statistics.mean(vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": name, "precision": "fp64", "l2": "inputs resident; oracle on host"},
+            "config": {"workload": name, "precision": "fp64", "l2": "host oracle"},
             "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"], "value": v,
                              "unit": METRIC},
             "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def time_steps(torch, r, engine, out, stream, steps, warmup, flush, sampler=None):
+    """W untimed steps, then K steps each bracketed by CUDA events on the render
+    stream, with a >L2 buffer written before every step.  Returns per-step ms."""
+    for _ in range(warmup):
+        r.render(out=out, engine=engine, stream=stream.cuda_stream)
+    stream.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    ctx = sampler if sampler is not None else _Null()
+    with ctx:
+        with torch.cuda.stream(stream):
+            for k in range(steps):
+                flush.fill_(float(k))
+                evs[k][0].record(stream)
+                r.render(out=out, engine=engine, stream=stream.cuda_stream)
+                evs[k][1].record(stream)
+        stream.synchronize()
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
 
 
 def run_ours(args):
@@ -164,47 +213,83 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     sc, name = workload(args)
-    prec = {"fp32": M.MRF_PREC_FP32, "fp16": M.MRF_PREC_FP16, "bf16": M.MRF_PREC_BF16}[args.precision]
+    prec_id = {"fp32": M.MRF_PREC_FP32, "fp16": M.MRF_PREC_FP16, "bf16": M.MRF_PREC_BF16}
     engine = {"auto": M.MRF_ENGINE_AUTO, "megakernel": M.MRF_ENGINE_MEGAKERNEL,
               "wavefront": M.MRF_ENGINE_WAVEFRONT}[args.engine]
-    r = M.Renderer(sc, device=local, precision=prec)
+    dev = f"cuda:{local}"
+    r = M.Renderer(sc, device=local, precision=prec_id[args.precision])
     stream = torch.cuda.Stream(local)
-    out = torch.empty((sc.n_rays, 4), dtype=torch.float32, device=f"cuda:{local}")
-    # one untimed run for the deterministic work counts
+    out = torch.empty((sc.n_rays, 4), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+    # untimed: deterministic work counts and the image used for the error check
     with torch.cuda.stream(stream):
         _, st = r.render(out=out, engine=engine, stats=True, stream=stream.cuda_stream)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")  # 256 MB > L2
-    for _ in range(args.warmup):
-        with torch.cuda.stream(stream):
-            r.render(out=out, engine=engine, stream=stream.cuda_stream)
     stream.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    image = out.cpu().numpy().astype(np.float64)
     sampler = ClockSampler(local)
     if world > 1:
         dist.barrier()
-    torch.cuda.synchronize()
-    with sampler:
-        t0 = time.perf_counter()
-        for k in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(float(k))
-                evs[k][0].record(stream)
-                r.render(out=out, engine=engine, stream=stream.cuda_stream)
-                evs[k][1].record(stream)
-        stream.synchronize()
-        wall = time.perf_counter() - t0
-    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    step_ms = time_steps(torch, r, engine, out, stream, args.steps, args.warmup, flush, sampler)
+    wall = time.perf_counter() - t0
     if world > 1:
         dist.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
     ms = sum(step_ms) / len(step_ms)
     if world > 1:
-        t = torch.tensor([ms], device=f"cuda:{local}")
+        t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     segs = st["segments"]
     samples = st["samples_evaluated"] + st["shadow_samples_evaluated"]
     value = world * segs / (ms / 1e3)
+    # per-kernel CUDA-event timing over the same protocol (separate pass: it waits per call)
+    ktimes = {}
+    nk = max(3, args.steps // 2)
+    for k in range(nk):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        tim = {}
+        r.render(out=out, engine=engine, stream=stream.cuda_stream, timing=tim)
+        for name_k, (kms, cnt) in tim.items():
+            a = ktimes.setdefault(name_k, [0.0, 0])
+            a[0] += kms / nk
+            a[1] = cnt
+    kernels = {k: {"ms_per_step": v[0], "launches_per_step": v[1], "share": v[0] / max(ms, 1e-9)}
+               for k, v in ktimes.items() if v[1]}
+    launches = sum(v["launches_per_step"] for v in kernels.values())
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
+    pk, pk_kind = peaks()
+    dom_ms = kernels[dom]["ms_per_step"]
+    if dom == "field" and args.precision != "fp32":
+        nbytes = (GATHER_BYTES_PER_SAMPLE + SAMPLE_IO_BYTES) * samples
+        ach = nbytes / (dom_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
+                "traffic": None, "kernel": "field_tc_kernel",
+                "algorithmic": f"{GATHER_BYTES_PER_SAMPLE + SAMPLE_IO_BYTES} B per evaluated sample "
+                               f"(512 B gathered + 32 B I/O) x {samples} samples",
+                "peak_kind": f"{pk_kind} hbm_gbs",
+                "tensor": {"achieved_tflops": MLP_FLOP_PER_SAMPLE * samples / (dom_ms / 1e3) / 1e12,
+                           "peak_tflops": pk["bf16_tflops"],
+                           "frac": MLP_FLOP_PER_SAMPLE * samples / (dom_ms / 1e3) / 1e12 / pk["bf16_tflops"]}}
+    else:
+        flop = MLP_FLOP_PER_SAMPLE * samples
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        ach = flop / (dom_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel": {"field": "field_simt_kernel"}.get(dom, dom),
+                "algorithmic": f"{MLP_FLOP_PER_SAMPLE} FP32 FLOP per evaluated sample x {samples}",
+                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock"}
+    # FP32 GPU path on the same GPU, same protocol (the comparison the metric names)
+    fp32 = None
+    if not args.no_fp32 and args.precision != "fp32":
+        r32 = M.Renderer(sc, device=local, precision=M.MRF_PREC_FP32)
+        o32 = torch.empty_like(out)
+        ms32 = time_steps(torch, r32, M.MRF_ENGINE_MEGAKERNEL, o32, stream, max(3, args.steps // 2), args.warmup,
+                          flush)
+        m32 = sum(ms32) / len(ms32)
+        fp32 = {"value": world * segs / (m32 / 1e3), "ms_per_step": m32, "engine": "megakernel",
+                "speedup_of_headline": m32 / ms}
+        r32.close()
     # end to end through the C ABI: host output buffer, device->host copy inside the call
     host_out = torch.empty((sc.n_rays, 4), dtype=torch.float32).pin_memory()
     e2e_ms = []
@@ -215,26 +300,14 @@ def run_ours(args):
         r.render(out=host_out, engine=engine, stream=stream.cuda_stream)
         e2e_ms.append((time.perf_counter() - t) * 1e3)
     e2e = world * segs / (statistics.median(e2e_ms) / 1e3)
-    pk, pk_kind = peaks()
-    sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    if args.precision == "fp32":
-        flop = FP32_FLOP_PER_SAMPLE * samples
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": flop / (ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "frac": (flop / (ms / 1e3) / 1e12) / peak, "traffic": None,
-                "kernel": "render_megakernel", "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
-    else:
-        flop = FP32_FLOP_PER_SAMPLE * samples
-        peak = pk["bf16_tflops"]
-        roof = {"bound": "tensor", "achieved": flop / (ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "frac": (flop / (ms / 1e3) / 1e12) / peak, "traffic": None, "kernel": "render",
-                "peak_kind": pk_kind}
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16", "bf16": "bf16"}[args.precision],
             "data": "synthetic",
-            "config": {"workload": name, "precision": args.precision, "engine": args.engine,
-                       "l2": "256 MB buffer written between timed steps", "parallelism": f"replicas x{world}"},
+            "config": {"workload": name, "precision": args.precision,
+                       "engine": args.engine if args.engine != "auto" else
+                       ("wavefront" if args.precision != "fp32" else "megakernel"),
+                       "l2": "256 MB buffer written before every timed step", "parallelism": f"replicas x{world}"},
             "field_samples_per_s": world * samples / (ms / 1e3),
             "work_per_step": {"segments": segs, "samples_evaluated": st["samples_evaluated"],
                               "shadow_samples_evaluated": st["shadow_samples_evaluated"],
@@ -242,13 +315,25 @@ def run_ours(args):
                               "paths": st["paths"], "fp64_retests": st["fp64_retests"]},
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
             "wall_s_timed_region": wall,
+            "kernels": kernels,
             "roofline": roof,
+            "fp32_gpu": fp32,
             "e2e": {"value": e2e, "unit": METRIC, "h2d_bytes_per_step": 48,
-                    "d2h_bytes_per_step": sc.n_rays * 16, "ms_per_step": statistics.median(e2e_ms)},
-            "gpu_launches": args.steps,
+                    "d2h_bytes_per_step": sc.n_rays * 16, "ms_per_step": statistics.median(e2e_ms),
+                    "note": "camera record passed by value; image copied to pinned host memory inside mrf_render"},
+            "gpu_launches": launches * args.steps,
             "clocks": sampler.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(sc, args.cpu_stride)
+        cb, ids, ref = cpu_baseline(sc, args.cpu_stride)
+        line["cpu_baseline"] = cb
+        ok = ref["flags"] == 0
+        g, o = image[ids][ok, :3], ref["rgba"][ok, :3]
+        peak = float(np.abs(o).max())
+        mse = float(np.mean((g - o) ** 2))
+        line["image_error_vs_oracle"] = {
+            "pixels": int(ok.sum()), "psnr_db": (10 * np.log10(peak * peak / mse)) if mse > 0 else None,
+            "max_abs": float(np.abs(g - o).max()), "ambiguous_pixels_excluded": int((~ok).sum()),
+            "peak": peak}
     if rank == 0:
         print(json.dumps(line), flush=True)
     r.close()

@@ -117,9 +117,10 @@ void mrf_field_destroy(mrf_field *field);
 /* Changes the MLP precision of an existing HASHGRID field. */
 mrf_status mrf_field_set_precision(mrf_field *field, int32_t precision);
 
-/* Evaluates sigma and r at n points (n x 3, FP32) into out (n x 4: sigma, r, g, b),
- * FP32 path.  points and out must be device pointers.  For tests of the field
- * alone (Eq. 7 / hash encoding / MLP). */
+/* Evaluates sigma and r at n points (n x 3, FP32) into out (n x 4: sigma, r, g, b)
+ * in the field's precision: FP32 on the CUDA cores, or for FP16/BF16 hash
+ * fields the tensor-core kernel the wavefront engine uses.  points and out must
+ * be device pointers.  For tests of the field alone (Eq. 7 / hash encoding / MLP). */
 mrf_status mrf_field_query(mrf_context *ctx, const mrf_field *field, const float *points, uint32_t n, float *out,
                            void *stream);
 
@@ -189,7 +190,16 @@ typedef struct mrf_rays {
     uint32_t spp;                  /* paths per ray (>= 1) */
 } mrf_rays;
 
+/* MEGAKERNEL: one thread runs a whole path (FP32 field only).  WAVEFRONT: one
+ * launch sequence per segment over all live paths, with every field sample of
+ * the segment evaluated in one flat pass (tensor cores for FP16/BF16 hash
+ * fields).  AUTO picks WAVEFRONT for FP16/BF16 hash fields, else MEGAKERNEL. */
 enum { MRF_ENGINE_AUTO = 0, MRF_ENGINE_MEGAKERNEL = 1, MRF_ENGINE_WAVEFRONT = 2 };
+/* kernel kinds of the per-kernel timing in mrf_render_opts.kernel_ms */
+enum {
+    MRF_KERNEL_MEGAKERNEL = 0, MRF_KERNEL_CAST_GEN = 1, MRF_KERNEL_FIELD = 2, MRF_KERNEL_SHADE = 3,
+    MRF_KERNEL_FINALIZE = 4, MRF_KERNEL_COUNT = 5
+};
 
 typedef struct mrf_render_opts {
     uint64_t seed;                 /* Philox4x64-10 key word 0 */
@@ -203,6 +213,11 @@ typedef struct mrf_render_opts {
     uint32_t *rec_segments;
     uint32_t *rec_tri;
     float *rec_t;
+    /* optional host arrays of MRF_KERNEL_COUNT entries: summed CUDA-event
+     * duration (ms) and launch count of each kernel kind; when set, the call
+     * records events around every launch on `stream` and waits for them */
+    float *kernel_ms;
+    uint32_t *kernel_launches;
 } mrf_render_opts;
 
 typedef struct mrf_stats {

@@ -16,7 +16,8 @@
 namespace mrf {
 void bvh_build_host(const float *verts, const uint32_t *tris, uint32_t n_tris, std::vector<float> &nodes,
                     std::vector<uint32_t> &order, std::vector<int> &parent);
-cudaError_t launch_render_wavefront(const RenderParams &P, void *scratch, size_t scratch_bytes, cudaStream_t s);
+cudaError_t launch_render_wavefront(const RenderParams &P, void *scratch, size_t scratch_bytes, cudaStream_t s,
+                                    KernelTimer *timer);
 size_t wavefront_scratch_bytes(const RenderParams &P);
 bool wavefront_available();
 }  // namespace mrf
@@ -55,6 +56,7 @@ struct mrf_context {
     int n_lights = 0;
     unsigned long long *stats = nullptr;
     unsigned *status = nullptr;  // device status word: non-zero after a kernel gave up
+    KernelTimer *timer = nullptr;
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
 };
@@ -187,6 +189,10 @@ void mrf_context_destroy(mrf_context *c) {
     cudaFree(c->stats);
     cudaFree(c->status);
     cudaFree(c->scratch);
+    if (c->timer) {
+        for (auto &e : c->timer->ev) cudaEventDestroy(e);
+        delete c->timer;
+    }
     delete c;
 }
 
@@ -693,10 +699,34 @@ mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *b
         CUDA_TRY(cudaMemsetAsync(ctx->stats, 0, sizeof(unsigned long long) * ST_COUNT, s), "stats reset");
         P.stats = ctx->stats;
     }
+    KernelTimer *timer = nullptr;
+    if (opts->kernel_ms) {
+        if (!ctx->timer) {
+            ctx->timer = new (std::nothrow) KernelTimer();
+            if (!ctx->timer) return fail(MRF_ERR_OOM, "mrf_render: timer allocation");
+            for (auto &e : ctx->timer->ev) CUDA_TRY(cudaEventCreate(&e), "mrf_render: event create");
+        }
+        timer = ctx->timer;
+        timer->n = 0;
+        timer->ok = true;
+    }
     if (engine == MRF_ENGINE_WAVEFRONT) {
-        CUDA_TRY(launch_render_wavefront(P, scr + wf_off, scratch_need - wf_off, s), "mrf_render: wavefront launch");
+        CUDA_TRY(launch_render_wavefront(P, scr + wf_off, scratch_need - wf_off, s, timer), "mrf_render: wavefront launch");
     } else {
-        CUDA_TRY(launch_render_megakernel(P, s), "mrf_render: launch");
+        CUDA_TRY(launch_render_megakernel(P, s, timer), "mrf_render: launch");
+    }
+    if (timer) {
+        CUDA_TRY(cudaStreamSynchronize(s), "mrf_render: synchronize");
+        for (int k = 0; k < MRF_KERNEL_COUNT; ++k) {
+            opts->kernel_ms[k] = 0.f;
+            if (opts->kernel_launches) opts->kernel_launches[k] = 0;
+        }
+        for (int i = 0; i < timer->n; ++i) {
+            float ms = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&ms, timer->ev[2 * i], timer->ev[2 * i + 1]), "mrf_render: event time");
+            opts->kernel_ms[timer->kind[i]] += ms;
+            if (opts->kernel_launches) opts->kernel_launches[timer->kind[i]] += 1;
+        }
     }
     if (host_out) {
         CUDA_TRY(cudaMemcpyAsync(out_hdr, P.out, 4 * sizeof(float) * (size_t)count, cudaMemcpyDeviceToHost, s),

@@ -93,8 +93,29 @@ struct RenderParams {
     unsigned *status;            // context status word: bits set when a kernel gave up
 };
 
+// Optional per-launch CUDA-event timing of the renderer's kernels (host side).
+struct KernelTimer {
+    static constexpr int kMax = 128;
+    cudaEvent_t ev[2 * kMax];
+    int kind[kMax];
+    int n = 0;
+    bool ok = true;
+    void begin(int k, cudaStream_t s) {
+        if (n >= kMax) { ok = false; return; }
+        kind[n] = k;
+        cudaEventRecord(ev[2 * n], s);
+    }
+    void end(cudaStream_t s) {
+        if (n >= kMax) return;
+        cudaEventRecord(ev[2 * n + 1], s);
+        ++n;
+    }
+};
+inline void timer_begin(KernelTimer *t, int kind, cudaStream_t s) { if (t) t->begin(kind, s); }
+inline void timer_end(KernelTimer *t, cudaStream_t s) { if (t) t->end(s); }
+
 // launchers (render_mega.cu)
-cudaError_t launch_render_megakernel(const RenderParams &P, cudaStream_t s);
+cudaError_t launch_render_megakernel(const RenderParams &P, cudaStream_t s, KernelTimer *timer = nullptr);
 cudaError_t launch_field_simt(const FieldDev &F, const float *pts, int stride, const uint32_t *n_dev, uint32_t n_host,
                               float4 *out, int grid, cudaStream_t s);
 // field_tc.cu

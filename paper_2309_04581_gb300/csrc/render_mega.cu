@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(128) render_megakernel(const RenderParams P) {
     if (C.fault && P.status) atomicOr(P.status, C.fault);
 }
 
-cudaError_t launch_render_megakernel(const RenderParams &P, cudaStream_t s) {
+cudaError_t launch_render_megakernel(const RenderParams &P, cudaStream_t s, KernelTimer *timer) {
     const int threads = 128;
     const size_t smem = P.F.kind == MRF_FIELD_HASHGRID ? (size_t)mlp_floats(P.F.n_in) * sizeof(float) : 0;
     if (smem > 48 * 1024) {
@@ -116,7 +116,9 @@ cudaError_t launch_render_megakernel(const RenderParams &P, cudaStream_t s) {
         if (e != cudaSuccess) return e;
     }
     const unsigned blocks = (P.count + threads - 1) / threads;
+    timer_begin(timer, MRF_KERNEL_MEGAKERNEL, s);
     render_megakernel<<<blocks, threads, smem, s>>>(P);
+    timer_end(timer, s);
     return cudaGetLastError();
 }
 

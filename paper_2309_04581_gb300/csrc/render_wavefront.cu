@@ -127,6 +127,7 @@ __global__ void __launch_bounds__(kThreads) wf_cast_gen(const WfParams W, uint32
     uint32_t n_r = 0, n_s_total = 0;
     SurfaceHit S;
     bool diffuse = false;
+    if (j == 1 && tid == 0) W.ctr[cur] = W.paths;  // every path is live in segment 1
     if (active) {
         if (j == 1) {
             const uint32_t path = tid, ray = path / P.spp;
@@ -398,7 +399,8 @@ size_t wavefront_scratch_bytes(const RenderParams &P) {
     return layout(P.count * P.spp, P.n_lights).total;
 }
 
-cudaError_t launch_render_wavefront(const RenderParams &P, void *scratch, size_t scratch_bytes, cudaStream_t s) {
+cudaError_t launch_render_wavefront(const RenderParams &P, void *scratch, size_t scratch_bytes, cudaStream_t s,
+                                    KernelTimer *timer) {
     const uint32_t paths = P.count * P.spp;
     const Layout Lo = layout(paths, P.n_lights);
     if (scratch_bytes < Lo.total) return cudaErrorInvalidValue;
@@ -434,20 +436,28 @@ cudaError_t launch_render_wavefront(const RenderParams &P, void *scratch, size_t
     for (uint32_t j = 1; j <= P.max_bounces; ++j) {
         const int cur = (j - 1) & 1, nxt = j & 1;
         if ((e = cudaMemsetAsync(W.ctr + 2, 0, 4, s)) != cudaSuccess) return e;
+        timer_begin(timer, MRF_KERNEL_CAST_GEN, s);
         wf_cast_gen<<<grid, kThreads, 0, s>>>(W, j, cur);
+        timer_end(timer, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        timer_begin(timer, MRF_KERNEL_FIELD, s);
         if (tc)
             e = launch_field_tc(F, F.precision == MRF_PREC_BF16, reinterpret_cast<const float *>(W.samp), 4, W.ctr + 2,
                                 W.cap, W.fout, P.status, field_grid, s);
         else
             e = launch_field_simt(F, reinterpret_cast<const float *>(W.samp), 4, W.ctr + 2, W.cap, W.fout, field_grid, s);
+        timer_end(timer, s);
         if (e != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(W.ctr + nxt, 0, 4, s)) != cudaSuccess) return e;
+        timer_begin(timer, MRF_KERNEL_SHADE, s);
         wf_shade<<<grid, kThreads, 0, s>>>(W, j, cur, nxt);
+        timer_end(timer, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    timer_begin(timer, MRF_KERNEL_FINALIZE, s);
     wf_finalize<<<(P.count + kThreads - 1) / kThreads, kThreads, 0, s>>>(W.acc, P.count, P.spp,
                                                                           reinterpret_cast<float4 *>(P.out));
+    timer_end(timer, s);
     return cudaGetLastError();
 }
 

@@ -28,6 +28,7 @@ MRF_PREC_FP32, MRF_PREC_FP16, MRF_PREC_BF16 = 0, 1, 2
 MRF_MAT_MIRROR, MRF_MAT_GLASS, MRF_MAT_DIFFUSE = 0, 1, 2
 MRF_LIGHT_POINT = 0
 MRF_ENGINE_AUTO, MRF_ENGINE_MEGAKERNEL, MRF_ENGINE_WAVEFRONT = 0, 1, 2
+KERNEL_NAMES = ("render_megakernel", "wf_cast_gen", "field", "wf_shade", "wf_finalize")
 NO_HIT = 0xFFFFFFFF
 
 # every entry point declared in include/mrf.h
@@ -76,7 +77,7 @@ class mrf_rays(C.Structure):
 class mrf_render_opts(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("steps_per_segment", C.c_uint32), ("dt", C.c_float), ("tau", C.c_float),
                 ("tmin", C.c_float), ("engine", C.c_int32), ("rec_segments", _vp), ("rec_tri", _vp),
-                ("rec_t", _vp)]
+                ("rec_t", _vp), ("kernel_ms", C.POINTER(C.c_float)), ("kernel_launches", C.POINTER(C.c_uint32))]
 
 
 class mrf_stats(C.Structure):
@@ -330,15 +331,25 @@ class Renderer:
                 "tri": torch.zeros(n * spp * B, dtype=torch.int32, device=dev),
                 "t": torch.zeros(n * spp * B, dtype=torch.float32, device=dev)}
 
-    def render(self, out=None, engine=MRF_ENGINE_AUTO, records=None, stats=False, stream=None):
+    def render(self, out=None, engine=MRF_ENGINE_AUTO, records=None, stats=False, stream=None, timing=None):
         """Renders into ``out`` (count x 4 float32 CUDA tensor, allocated if None).
-        Returns (out, stats dict or None)."""
+        Returns (out, stats dict or None).  If ``timing`` is a dict, it receives
+        per-kernel CUDA-event milliseconds and launch counts of this call."""
         torch = self.torch
         n = self.scene.n_rays
         if out is None:
             out = torch.empty((n, 4), dtype=torch.float32, device=torch.device("cuda", self.device))
         st = mrf_stats() if stats else None
         s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
-        mrf_render(self.ctx, self.field, self.bvh, self.rays_struct(), self.scene.opts.max_bounces,
-                   self.opts_struct(engine, records), out.data_ptr(), s, st)
+        opts = self.opts_struct(engine, records)
+        if timing is not None:
+            ms = (C.c_float * len(KERNEL_NAMES))()
+            cnt = (C.c_uint32 * len(KERNEL_NAMES))()
+            opts.kernel_ms = ms
+            opts.kernel_launches = cnt
+        mrf_render(self.ctx, self.field, self.bvh, self.rays_struct(), self.scene.opts.max_bounces, opts,
+                   out.data_ptr(), s, st)
+        if timing is not None:
+            for k, name in enumerate(KERNEL_NAMES):
+                timing[name] = (float(ms[k]), int(cnt[k]))
         return out, (st.as_dict() if st is not None else None)
