@@ -241,6 +241,30 @@ mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *b
                       uint32_t max_bounces, const mrf_render_opts *opts, float *out_hdr, void *stream,
                       mrf_stats *stats);
 
+/* Allocation-free variant of mrf_render.  The paper has no counterpart: this
+ * entry point exists for embedders that cannot call cudaMalloc while they
+ * render, such as hosts whose device memory belongs to another allocator's
+ * pool, or real-time loops that cannot afford the device-wide synchronisation
+ * an allocation may cause.  It runs the wavefront engine out of a file-scope
+ * device arena of 64 MiB that every GPU loading the library holds until the
+ * process exits, and it allocates no device or pinned memory itself.
+ *  - Limits: rays->count * rays->spp <= 131072 paths and at most 8 lights;
+ *    larger requests return MRF_ERR_INVALID_ARG (use mrf_render).  Samples that
+ *    do not fit the arena's sample buffer are marched in place, so results do
+ *    not depend on the arena size.
+ *  - out_hdr, explicit rays and records must be device memory; per-kernel
+ *    timing (kernel_ms, kernel_launches) is rejected.
+ *  - The first call on a device resolves the arena's address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - All calls share the arena, which keeps the last call's contents; the
+ *    engine clears its counters at the start of every call.  Calls that overlap
+ *    on the GPU (for example on two streams) race on the arena.
+ * Arguments, outputs and statistics otherwise as mrf_render. */
+mrf_status mrf_render_static(mrf_context *ctx, const mrf_field *field, const mrf_bvh *bvh, const mrf_rays *rays,
+                             uint32_t max_bounces, const mrf_render_opts *opts, float *out_hdr, void *stream,
+                             mrf_stats *stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,6 +20,10 @@ cudaError_t launch_render_wavefront(const RenderParams &P, void *scratch, size_t
                                     KernelTimer *timer);
 size_t wavefront_scratch_bytes(const RenderParams &P);
 bool wavefront_available();
+cudaError_t static_arena(int device, void **ptr, size_t *bytes);
+cudaError_t launch_render_wavefront_arena(const RenderParams &P, void *arena, size_t arena_bytes, cudaStream_t s);
+uint32_t static_arena_max_paths();
+int static_arena_max_lights();
 }  // namespace mrf
 
 using namespace mrf;
@@ -757,3 +761,147 @@ mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *b
     return MRF_OK;
 }
 
+
+// Allocation-free render: the wavefront engine on the library's static device
+// arena (render_wavefront.cu).  Nothing here allocates device or pinned memory;
+// the first call on a device resolves the arena's address.
+mrf_status mrf_render_static(mrf_context *ctx, const mrf_field *field, const mrf_bvh *bvh, const mrf_rays *rays,
+                             uint32_t max_bounces, const mrf_render_opts *opts, float *out_hdr, void *stream,
+                             mrf_stats *stats) {
+    if (!ctx || !field || !bvh || !rays || !opts || !out_hdr)
+        return fail(MRF_ERR_INVALID_ARG, "mrf_render_static: NULL argument");
+    if (field->ctx != ctx || bvh->ctx != ctx)
+        return fail(MRF_ERR_INVALID_ARG, "mrf_render_static: handle of another context");
+    if (max_bounces == 0 || max_bounces > (uint32_t)kMaxBounces)
+        return fail(MRF_ERR_INVALID_ARG, "mrf_render_static: max_bounces must be in [1, %d]", kMaxBounces);
+    if (rays->spp == 0) return fail(MRF_ERR_INVALID_ARG, "mrf_render_static: spp must be >= 1");
+    if (opts->steps_per_segment == 0 && !(opts->dt > 0.f))
+        return fail(MRF_ERR_INVALID_ARG, "mrf_render_static: need steps_per_segment > 0 or dt > 0");
+    if (!(opts->tau >= 0.f) || !(opts->tmin >= 0.f))
+        return fail(MRF_ERR_INVALID_ARG, "mrf_render_static: negative tau or tmin");
+    if (opts->kernel_ms || opts->kernel_launches)
+        return fail(MRF_ERR_INVALID_ARG, "mrf_render_static: per-kernel timing is not available here");
+    if (bvh->n_tris && ctx->n_mats == 0) return fail(MRF_ERR_NOT_READY, "mrf_render_static: no materials set");
+    if (ctx->n_lights > static_arena_max_lights())
+        return fail(MRF_ERR_INVALID_ARG, "mrf_render_static: %d lights exceed the arena limit of %d", ctx->n_lights,
+                    static_arena_max_lights());
+    CUDA_TRY(cudaSetDevice(ctx->device), "mrf_render_static: cudaSetDevice");
+    if (!is_device_ptr(out_hdr)) return fail(MRF_ERR_INVALID_ARG, "mrf_render_static: out_hdr must be device memory");
+    if ((opts->rec_segments && !is_device_ptr(opts->rec_segments)) || (opts->rec_tri && !is_device_ptr(opts->rec_tri)) ||
+        (opts->rec_t && !is_device_ptr(opts->rec_t)) || (!opts->rec_tri != !opts->rec_t))
+        return fail(MRF_ERR_INVALID_ARG, "mrf_render_static: records must be device pointers (rec_tri and rec_t together)");
+    {
+        cudaError_t pending = cudaGetLastError();
+        if (pending != cudaSuccess) return cuda_fail(pending, "mrf_render_static: earlier asynchronous error");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    {
+        unsigned st_word = 0;
+        CUDA_TRY(cudaMemcpy(&st_word, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost),
+                 "mrf_render_static: status read");
+        if (st_word) {
+            cudaMemset(ctx->status, 0, sizeof(unsigned));
+            return fail(MRF_ERR_TIMEOUT, "mrf_render_static: an earlier kernel gave up (status 0x%x)", st_word);
+        }
+    }
+    RenderParams P{};
+    P.F = field->dev;
+    P.B = bvh->dev;
+    P.mats = ctx->mats;
+    P.n_mats = ctx->n_mats;
+    P.lights = ctx->lights;
+    P.n_lights = ctx->n_lights;
+    uint32_t count;
+    if (rays->camera) {
+        const mrf_camera &c = *rays->camera;
+        if (c.width == 0 || c.height == 0 || !(c.vfov_deg > 0.f && c.vfov_deg < 180.f))
+            return fail(MRF_ERR_INVALID_ARG, "mrf_render_static: bad camera");
+        const uint64_t cnt = (uint64_t)c.width * c.height;
+        if (cnt > 0xFFFFFFFFull / 4) return fail(MRF_ERR_INVALID_ARG, "mrf_render_static: image too large");
+        count = (uint32_t)cnt;
+        double f[3], up[3], r[3], u[3];
+        for (int k = 0; k < 3; ++k) {
+            f[k] = (double)c.look_at[k] - c.pos[k];
+            up[k] = c.up[k];
+        }
+        const double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+        if (!(fl > 0)) return fail(MRF_ERR_INVALID_ARG, "mrf_render_static: camera looks at itself");
+        for (double &x : f) x /= fl;
+        r[0] = f[1] * up[2] - f[2] * up[1];
+        r[1] = f[2] * up[0] - f[0] * up[2];
+        r[2] = f[0] * up[1] - f[1] * up[0];
+        const double rl = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        if (!(rl > 0)) return fail(MRF_ERR_INVALID_ARG, "mrf_render_static: camera up is parallel to the view direction");
+        for (double &x : r) x /= rl;
+        u[0] = r[1] * f[2] - r[2] * f[1];
+        u[1] = r[2] * f[0] - r[0] * f[2];
+        u[2] = r[0] * f[1] - r[1] * f[0];
+        P.use_camera = 1;
+        for (int k = 0; k < 3; ++k) {
+            P.cam_pos[k] = c.pos[k];
+            P.cam_f[k] = (float)f[k];
+            P.cam_r[k] = (float)r[k];
+            P.cam_u[k] = (float)u[k];
+        }
+        P.tan_half = (float)std::tan(0.5 * (double)c.vfov_deg * M_PI / 180.0);
+        P.aspect = (float)((double)c.width / (double)c.height);
+        P.W = c.width;
+        P.H = c.height;
+    } else {
+        if (!rays->origins || !rays->dirs || rays->count == 0)
+            return fail(MRF_ERR_INVALID_ARG, "mrf_render_static: explicit rays need origins, dirs and count > 0");
+        if (!is_device_ptr(rays->origins) || !is_device_ptr(rays->dirs))
+            return fail(MRF_ERR_INVALID_ARG, "mrf_render_static: explicit rays must be device memory");
+        count = rays->count;
+        P.ray_o = rays->origins;
+        P.ray_d = rays->dirs;
+    }
+    const uint64_t paths = (uint64_t)count * rays->spp;
+    if (paths > static_arena_max_paths())
+        return fail(MRF_ERR_INVALID_ARG,
+                    "mrf_render_static: %llu paths (rays x spp) exceed the static arena limit of %u; use mrf_render",
+                    (unsigned long long)paths, static_arena_max_paths());
+    P.count = count;
+    P.spp = rays->spp;
+    P.max_bounces = max_bounces;
+    P.seed = opts->seed;
+    P.steps = opts->steps_per_segment;
+    P.dt = opts->dt;
+    P.tau = opts->tau;
+    P.tmin = opts->tmin;
+    P.rec_seg = opts->rec_segments;
+    P.rec_tri = opts->rec_tri;
+    P.rec_t = opts->rec_t;
+    P.out = out_hdr;
+    P.status = ctx->status;
+    void *arena = nullptr;
+    size_t arena_bytes = 0;
+    CUDA_TRY(static_arena(ctx->device, &arena, &arena_bytes), "mrf_render_static: arena address (cudaGetSymbolAddress)");
+    if (stats) {
+        CUDA_TRY(cudaMemsetAsync(ctx->stats, 0, sizeof(unsigned long long) * ST_COUNT, s), "stats reset");
+        P.stats = ctx->stats;
+    }
+    CUDA_TRY(launch_render_wavefront_arena(P, arena, arena_bytes, s), "mrf_render_static: launch");
+    if (stats) {
+        unsigned long long h[ST_COUNT];
+        CUDA_TRY(cudaMemcpyAsync(h, ctx->stats, sizeof(h), cudaMemcpyDeviceToHost, s), "stats download");
+        CUDA_TRY(cudaStreamSynchronize(s), "mrf_render_static: synchronize");
+        stats->paths = h[ST_PATHS];
+        stats->segments = h[ST_SEGMENTS];
+        stats->surface_hits = h[ST_HITS];
+        stats->shadow_rays = h[ST_SHADOW];
+        stats->samples_nominal = h[ST_NOMINAL];
+        stats->samples_evaluated = h[ST_EVALUATED];
+        stats->shadow_samples_evaluated = h[ST_SHADOW_EVALUATED];
+        stats->fp64_retests = h[ST_FP64];
+        unsigned st_word = 0;
+        CUDA_TRY(cudaMemcpy(&st_word, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost),
+                 "mrf_render_static: status read");
+        stats->status = st_word;
+        if (st_word) {
+            cudaMemset(ctx->status, 0, sizeof(unsigned));
+            return fail(MRF_ERR_TIMEOUT, "mrf_render_static: a kernel gave up (status 0x%x)", st_word);
+        }
+    }
+    return MRF_OK;
+}

@@ -14,6 +14,8 @@
 // the same FP32 formulas as the megakernel.  Jobs whose samples do not fit the
 // sample buffer are marched in place by wf_shade on the CUDA cores.
 #include <algorithm>
+#include <mutex>
+
 #include <cuda_runtime.h>
 
 #include "path.cuh"
@@ -458,6 +460,115 @@ cudaError_t launch_render_wavefront(const RenderParams &P, void *scratch, size_t
     wf_finalize<<<(P.count + kThreads - 1) / kThreads, kThreads, 0, s>>>(W.acc, P.count, P.spp,
                                                                           reinterpret_cast<float4 *>(P.out));
     timer_end(timer, s);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant.  Some embedders cannot call cudaMalloc while they
+// render: hosts whose device memory is owned by another allocator's pool, and
+// real-time loops that cannot afford the device-wide synchronisation an
+// allocation may cause.  For them the wavefront engine can run out of this
+// file-scope arena instead of library-allocated scratch.  Every GPU that loads
+// the library holds the arena until the process exits.  All calls share it and
+// it keeps the last call's contents; the engine clears what must start at zero
+// (its queue and sample counters), and calls that overlap on the GPU race.
+constexpr size_t kStaticArenaBytes = (size_t)64 << 20;   // 64 MiB
+constexpr uint32_t kStaticMaxPaths = 1u << 17;           // count * spp limit
+constexpr int kStaticMaxLights = 8;
+static __device__ __align__(256) unsigned char g_static_arena[kStaticArenaBytes];
+
+namespace {
+std::mutex g_arena_mu;
+void *g_arena_addr[64] = {};
+
+// per-path state of the wavefront engine plus a sample buffer filling the rest
+Layout layout_in(uint32_t paths, int n_lights, size_t bytes, bool &fits) {
+    Layout L = layout(paths, n_lights);
+    const size_t state = L.samp;   // everything before the sample buffers
+    fits = bytes > state + 2 * 16 * 128 + 512;
+    if (!fits) return L;
+    const uint64_t cap = std::min<uint64_t>((bytes - state - 512) / 32, 0x7FFFFFFFull);
+    L.cap = (uint32_t)cap;
+    L.fout = L.samp + ((16 * cap + 255) & ~(size_t)255);
+    L.total = L.fout + 16 * cap;
+    fits = L.total <= bytes;
+    return L;
+}
+}  // namespace
+
+uint32_t static_arena_max_paths() { return kStaticMaxPaths; }
+int static_arena_max_lights() { return kStaticMaxLights; }
+
+// Resolves the device address of the arena on the current device, once per
+// device (the first call on a device therefore runs cudaGetSymbolAddress).
+cudaError_t static_arena(int device, void **ptr, size_t *bytes) {
+    std::lock_guard<std::mutex> lk(g_arena_mu);
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    if (!g_arena_addr[device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_arena);
+        if (e != cudaSuccess) return e;
+        g_arena_addr[device] = p;
+    }
+    *ptr = g_arena_addr[device];
+    *bytes = kStaticArenaBytes;
+    return cudaSuccess;
+}
+
+// The wavefront launch sequence on a caller-given arena (sample capacity from
+// what the arena leaves after the per-path state; jobs beyond it are marched in
+// place by wf_shade).
+cudaError_t launch_render_wavefront_arena(const RenderParams &P, void *arena, size_t arena_bytes, cudaStream_t s) {
+    const uint32_t paths = P.count * P.spp;
+    bool fits = false;
+    const Layout Lo = layout_in(paths, P.n_lights, arena_bytes, fits);
+    if (!fits) return cudaErrorInvalidValue;
+    char *b = static_cast<char *>(arena);
+    WfParams W{};
+    W.R = P;
+    W.paths = paths;
+    W.acc = reinterpret_cast<float4 *>(b + Lo.acc);
+    for (int q = 0; q < 2; ++q) {
+        W.qpath[q] = reinterpret_cast<uint32_t *>(b + Lo.qpath[q]);
+        W.qo[q] = reinterpret_cast<float4 *>(b + Lo.qo[q]);
+        W.qd[q] = reinterpret_cast<float4 *>(b + Lo.qd[q]);
+        W.qT[q] = reinterpret_cast<float4 *>(b + Lo.qT[q]);
+    }
+    W.hit_t = reinterpret_cast<float *>(b + Lo.hit_t);
+    W.hit_slot = reinterpret_cast<int *>(b + Lo.hit_slot);
+    W.hit_id = reinterpret_cast<uint32_t *>(b + Lo.hit_id);
+    W.rstart = reinterpret_cast<uint32_t *>(b + Lo.rstart);
+    W.rcount = reinterpret_cast<uint32_t *>(b + Lo.rcount);
+    W.sstart = reinterpret_cast<uint32_t *>(b + Lo.sstart);
+    W.scount = reinterpret_cast<uint32_t *>(b + Lo.scount);
+    W.sw = reinterpret_cast<float4 *>(b + Lo.sw);
+    W.ctr = reinterpret_cast<uint32_t *>(b + Lo.ctr);
+    W.samp = reinterpret_cast<float4 *>(b + Lo.samp);
+    W.fout = reinterpret_cast<float4 *>(b + Lo.fout);
+    W.cap = Lo.cap;
+    const unsigned grid = (paths + kThreads - 1) / kThreads;
+    const FieldDev &F = P.F;
+    const bool tc = F.kind == MRF_FIELD_HASHGRID && F.precision != MRF_PREC_FP32;
+    const int field_grid = tc ? 152 * field_tc_blocks_per_sm() : 152 * 8;
+    cudaError_t e = cudaMemsetAsync(W.ctr, 0, 16, s);   // counters left over from the previous call
+    if (e != cudaSuccess) return e;
+    for (uint32_t j = 1; j <= P.max_bounces; ++j) {
+        const int cur = (j - 1) & 1, nxt = j & 1;
+        if ((e = cudaMemsetAsync(W.ctr + 2, 0, 4, s)) != cudaSuccess) return e;
+        wf_cast_gen<<<grid, kThreads, 0, s>>>(W, j, cur);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (tc)
+            e = launch_field_tc(F, F.precision == MRF_PREC_BF16, reinterpret_cast<const float *>(W.samp), 4, W.ctr + 2,
+                                W.cap, W.fout, P.status, field_grid, s);
+        else
+            e = launch_field_simt(F, reinterpret_cast<const float *>(W.samp), 4, W.ctr + 2, W.cap, W.fout, field_grid, s);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(W.ctr + nxt, 0, 4, s)) != cudaSuccess) return e;
+        wf_shade<<<grid, kThreads, 0, s>>>(W, j, cur, nxt);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    wf_finalize<<<(P.count + kThreads - 1) / kThreads, kThreads, 0, s>>>(W.acc, P.count, P.spp,
+                                                                          reinterpret_cast<float4 *>(P.out));
     return cudaGetLastError();
 }
 

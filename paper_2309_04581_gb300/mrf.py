@@ -34,7 +34,7 @@ NO_HIT = 0xFFFFFFFF
 # every entry point declared in include/mrf.h
 EXPORTS = ("mrf_context_create", "mrf_context_destroy", "mrf_last_error", "mrf_version", "mrf_field_create",
            "mrf_field_destroy", "mrf_field_set_precision", "mrf_field_query", "mrf_bvh_build", "mrf_bvh_refit",
-           "mrf_bvh_destroy", "mrf_cast", "mrf_materials_set", "mrf_lights_set", "mrf_render")
+           "mrf_bvh_destroy", "mrf_cast", "mrf_materials_set", "mrf_lights_set", "mrf_render", "mrf_render_static")
 
 _fp = C.POINTER(C.c_float)
 _u32p = C.POINTER(C.c_uint32)
@@ -122,6 +122,8 @@ def lib():
             L.mrf_lights_set.argtypes = [_vp, C.POINTER(mrf_light), C.c_uint32]
             L.mrf_render.argtypes = [_vp, _vp, _vp, C.POINTER(mrf_rays), C.c_uint32, C.POINTER(mrf_render_opts), _vp,
                                      _vp, C.POINTER(mrf_stats)]
+            L.mrf_render_static.argtypes = [_vp, _vp, _vp, C.POINTER(mrf_rays), C.c_uint32, C.POINTER(mrf_render_opts),
+                                            _vp, _vp, C.POINTER(mrf_stats)]
             L.mrf_context_destroy.argtypes = [_vp]
             L.mrf_field_destroy.argtypes = [_vp]
             L.mrf_bvh_destroy.argtypes = [_vp]
