@@ -118,6 +118,22 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """Max of x over all ranks (the timed region is as long as its slowest rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world: int, ms_max: float) -> float:
+    """Whole-job throughput: every rank processed units_per_rank in at most ms_max."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
 def workload(args):
     from paper_2309_04581_gb300 import scenes as S
     sc = S.config2(args.width, args.height)
@@ -234,14 +250,10 @@ def run_ours(args):
     wall = time.perf_counter() - t0
     if world > 1:
         dist.barrier()
-    ms = sum(step_ms) / len(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(step_ms) / len(step_ms), dev)
     segs = st["segments"]
     samples = st["samples_evaluated"] + st["shadow_samples_evaluated"]
-    value = world * segs / (ms / 1e3)
+    value = job_throughput(segs, world, ms)
     # per-kernel CUDA-event timing over the same protocol (separate pass: it waits per call)
     ktimes = {}
     nk = max(3, args.steps // 2)
