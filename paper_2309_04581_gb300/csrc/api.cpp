@@ -344,6 +344,24 @@ static mrf_status field_create_impl(mrf_context *ctx, const mrf_field_desc *D, m
         F.occ_res = (int)R;
         for (int k = 0; k < 3; ++k)
             F.occ_scale[k] = (float)((double)R / ((double)D->aabb_max[k] - (double)D->aabb_min[k]));
+        // coarse level for empty-space skipping: OR over 8^3 blocks
+        std::vector<uint32_t> fine;
+        if ((st = fetch(fine, D->occ_bits, words))) return st;
+        const uint32_t Rc = R / 8;
+        std::vector<uint32_t> coarse(((size_t)Rc * Rc * Rc + 31) / 32, 0u);
+        for (uint32_t z = 0; z < R; ++z)
+            for (uint32_t y = 0; y < R; ++y)
+                for (uint32_t x = 0; x < R; ++x) {
+                    const size_t i = x + (size_t)R * (y + (size_t)R * z);
+                    if ((fine[i >> 5] >> (i & 31)) & 1u) {
+                        const size_t c = x / 8 + (size_t)Rc * (y / 8 + (size_t)Rc * (z / 8));
+                        coarse[c >> 5] |= 1u << (c & 31);
+                    }
+                }
+        if ((st = upload(f, coarse.data(), coarse.size(), &F.occ_coarse, "coarse occupancy"))) return st;
+        F.occ_coarse_res = (int)Rc;
+        for (int k = 0; k < 3; ++k)
+            F.occ_coarse_scale[k] = (float)((double)Rc / ((double)D->aabb_max[k] - (double)D->aabb_min[k]));
     }
     (void)ctx;
     return MRF_OK;

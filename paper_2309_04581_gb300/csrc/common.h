@@ -41,6 +41,10 @@ struct FieldDev {
     int occ_res;
     const uint32_t *occ;
     float occ_scale[3];         // occ_res / extent
+    // coarse occupancy: one bit per 8^3 block of fine cells (bit set if any is occupied)
+    int occ_coarse_res;         // occ_res / 8
+    const uint32_t *occ_coarse;
+    float occ_coarse_scale[3];  // occ_coarse_res / extent
     int precision;
 };
 

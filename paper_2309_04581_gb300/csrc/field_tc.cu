@@ -23,7 +23,9 @@ namespace {
 
 constexpr int kThreads = 128;
 constexpr int kSmemW1 = 0, kSmemW2 = 8192, kSmemW3 = 16384, kSmemA = 18432, kSmemBias = 34816;
-constexpr int kSmemBar = kSmemBias + 132 * 4, kSmemTmem = kSmemBar + 8, kSmemBytes = kSmemTmem + 8;
+constexpr int kSmemBar = kSmemBias + 132 * 4, kSmemTmem = kSmemBar + 8, kSmemSupport = kSmemTmem + 8;
+constexpr int kSupportMax = 64;
+constexpr int kSmemBytes = kSmemSupport + kSupportMax * 16;
 constexpr uint32_t kTmemCols = 64;
 constexpr long long kWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
 
@@ -146,6 +148,11 @@ __global__ void __launch_bounds__(kThreads, 4)
         }
         if (tid < 4) sBias[128 + tid] = b3[tid];
     }
+    float4 *sSup = reinterpret_cast<float4 *>(smem + kSmemSupport);
+    const bool sup_smem = F.n_support <= kSupportMax;
+    if (sup_smem)
+        for (int k = tid; k < F.n_support; k += kThreads) sSup[k] = __ldg(F.support + k);
+    const float4 *sup = sup_smem ? sSup : F.support;
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(sBar)), "r"(1) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -176,7 +183,15 @@ __global__ void __launch_bounds__(kThreads, 4)
         float s = 0.f;
         if (valid) {
             p = v3(pts[(size_t)stride * i], pts[(size_t)stride * i + 1], pts[(size_t)stride * i + 2]);
-            s = F.n_support ? field_support(F, p) : 1.f;
+            if (F.n_support) {
+                for (int k = 0; k < F.n_support; ++k) {
+                    const float4 c = sup[k];
+                    const float dx = p.x - c.x, dy = p.y - c.y, dz = p.z - c.z;
+                    s = fmaxf(s, 1.0f - (dx * dx + dy * dy + dz * dz) * c.w);
+                }
+            } else {
+                s = 1.f;
+            }
             if (!inside_field_box(F, p)) s = 0.f;
         }
         // hash encoding -> A (K = n_in)

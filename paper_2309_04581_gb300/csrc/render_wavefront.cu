@@ -61,64 +61,226 @@ __device__ __forceinline__ uint32_t warp_alloc(uint32_t *ctr, uint32_t n) {
     return base + x - n;
 }
 
-// Walks the quadrature intervals of [a, b] exactly like march() and counts (or
-// writes) the samples whose density can be non-zero: occupied cell and, for the
-// hash grid, positive support.
-template <bool emit>
-__device__ uint32_t walk_samples(const RenderParams &P, V3 o, V3 d, float a, float b, float4 *out,
-                                 unsigned long long &nominal) {
+// Shared-memory copies used by the sample walk: coarse occupancy bits and the
+// density-support spheres.
+constexpr int kCoarseWordsMax = 1024;   // coarse grids up to 32^3 are staged
+constexpr int kSupportMax = 64;
+constexpr int kRuns = 8;                // sample runs remembered per job between the two walks
+
+struct WalkSmem {
+    uint32_t coarse[kCoarseWordsMax];
+    float4 support[kSupportMax];
+};
+
+struct WalkCtx {
+    const uint32_t *coarse;   // shared copy or nullptr
+    const float4 *support;    // shared copy (or the global array when it does not fit)
+};
+
+__device__ __forceinline__ WalkCtx stage_walk(const FieldDev &F, WalkSmem &sm) {
+    const int Rc = F.occ_coarse_res;
+    const int cw = (Rc * Rc * Rc + 31) / 32;
+    const bool coarse_fits = F.occ_coarse && cw <= kCoarseWordsMax;
+    if (coarse_fits)
+        for (int i = threadIdx.x; i < cw; i += blockDim.x) sm.coarse[i] = __ldg(F.occ_coarse + i);
+    const bool sup_fits = F.n_support <= kSupportMax;
+    if (sup_fits)
+        for (int i = threadIdx.x; i < F.n_support; i += blockDim.x) sm.support[i] = __ldg(F.support + i);
+    __syncthreads();
+    return WalkCtx{coarse_fits ? sm.coarse : nullptr, sup_fits ? sm.support : F.support};
+}
+
+__device__ __forceinline__ float support_at(const FieldDev &F, const float4 *sup, V3 p) {
+    float s = 0.f;
+    for (int k = 0; k < F.n_support; ++k) {
+        const float4 c = sup[k];
+        const float dx = p.x - c.x, dy = p.y - c.y, dz = p.z - c.z;
+        s = fmaxf(s, 1.0f - (dx * dx + dy * dy + dz * dz) * c.w);
+    }
+    return s;
+}
+
+// exit parameter of the cell c of a grid with cell size 1/scale along the ray
+__device__ __forceinline__ float grid_cell_exit(const float lo[3], const float scale[3], const int c[3], V3 o, V3 inv) {
+    float t = INFINITY;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float ik = comp(inv, k);
+        if (isinf(ik)) continue;
+        const float edge = lo[k] + (float)(c[k] + (ik > 0.f ? 1 : 0)) / scale[k];
+        t = fminf(t, (edge - comp(o, k)) * ik);
+    }
+    return t;
+}
+
+struct Runs {
+    int n;           // number of runs recorded, kRuns + 1 = too many
+    int b[kRuns], e[kRuns];
+};
+
+struct Segment {
+    float t0, t1, h;
+    int n;
+};
+
+// quadrature intervals of [a, b] clipped to the field box (same FP32 formulas as march())
+__device__ __forceinline__ bool segment_of(const RenderParams &P, V3 o, V3 d, float a, float b, Segment &S) {
     const FieldDev &F = P.F;
     float tb0, tb1;
-    if (!box_interval(F.lo, F.hi, o, d, tb0, tb1)) return 0;
-    const float t0 = fmaxf(a, tb0), t1 = fminf(b, tb1);
-    if (!(t1 > t0)) return 0;
-    int n;
-    float h;
+    if (!box_interval(F.lo, F.hi, o, d, tb0, tb1)) return false;
+    S.t0 = fmaxf(a, tb0);
+    S.t1 = fminf(b, tb1);
+    if (!(S.t1 > S.t0)) return false;
     if (P.steps) {
-        n = (int)P.steps;
-        h = (t1 - t0) / (float)n;
+        S.n = (int)P.steps;
+        S.h = (S.t1 - S.t0) / (float)S.n;
     } else {
-        h = P.dt;
-        const float nf = ceilf((t1 - t0) / h);
-        if (nf > 16777216.f) return 0;
-        n = (int)nf;
+        S.h = P.dt;
+        const float nf = ceilf((S.t1 - S.t0) / S.h);
+        if (nf > 16777216.f) return false;
+        S.n = (int)nf;
     }
-    if (!emit) nominal += (unsigned long long)n;
+    return true;
+}
+
+__device__ __forceinline__ void interval(const RenderParams &P, const Segment &S, int i, float &tm, float &delta) {
+    const float lo = fmaf((float)i, S.h, S.t0);
+    const float hi = P.steps ? fmaf((float)(i + 1), S.h, S.t0) : fminf(lo + S.h, S.t1);
+    tm = 0.5f * (lo + hi);
+    delta = hi - lo;
+}
+
+// Counts the samples of [a, b] whose density can be non-zero (occupied fine
+// cell and, for the hash grid, positive support), skipping empty coarse and
+// fine cells up to their exits, and remembers the runs of consecutive counted
+// samples.  Same intervals, positions and decisions as march().
+__device__ uint32_t count_samples(const RenderParams &P, const WalkCtx &X, V3 o, V3 d, float a, float b,
+                                  unsigned long long &nominal, Runs &R) {
+    R.n = 0;
+    Segment S;
+    if (!segment_of(P, o, d, a, b, S)) return 0;
+    nominal += (unsigned long long)S.n;
+    const FieldDev &F = P.F;
     const V3 inv = v3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
     const bool hash = F.kind == MRF_FIELD_HASHGRID;
     const bool use_occ = hash && F.occ != nullptr;
+    const bool use_coarse = use_occ && X.coarse != nullptr;
+    const int Rc = F.occ_coarse_res;
     uint32_t k = 0;
-    for (int i = 0; i < n;) {
-        const float lo = fmaf((float)i, h, t0);
-        const float hi = P.steps ? fmaf((float)(i + 1), h, t0) : fminf(lo + h, t1);
-        const float tm = 0.5f * (lo + hi), delta = hi - lo;
+    for (int i = 0; i < S.n;) {
+        float tm, delta;
+        interval(P, S, i, tm, delta);
         const V3 p = fma3(d, tm, o);
-        if (use_occ) {
+        if (use_coarse) {
             int c[3];
-            if (!occupied(F, p, c)) {
-                const float te = cell_exit(F, c, o, inv);
-                const int j = (int)ceilf((te - t0) / h - 0.5f);
-                i = max(i + 1, j);
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                c[q] = min(max((int)floorf((comp(p, q) - F.lo[q]) * F.occ_coarse_scale[q]), 0), Rc - 1);
+            const uint32_t ci = (uint32_t)c[0] + (uint32_t)Rc * ((uint32_t)c[1] + (uint32_t)Rc * (uint32_t)c[2]);
+            if (!((X.coarse[ci >> 5] >> (ci & 31)) & 1u)) {
+                const float te = grid_cell_exit(F.lo, F.occ_coarse_scale, c, o, inv);
+                i = max(i + 1, (int)ceilf((te - S.t0) / S.h - 0.5f));
                 continue;
             }
         }
-        if (hash && !(field_support(F, p) > 0.f)) {
+        if (use_occ) {
+            int c[3];
+            if (!occupied(F, p, c)) {
+                const float te = grid_cell_exit(F.lo, F.occ_scale, c, o, inv);
+                i = max(i + 1, (int)ceilf((te - S.t0) / S.h - 0.5f));
+                continue;
+            }
+        }
+        if (hash && !(support_at(F, X.support, p) > 0.f)) {
             ++i;
             continue;
         }
-        if (emit) out[k] = make_float4(p.x, p.y, p.z, delta);
+        if (R.n > 0 && R.n <= kRuns && R.e[R.n - 1] == i) {
+            R.e[R.n - 1] = i + 1;
+        } else if (R.n < kRuns) {
+            R.b[R.n] = i;
+            R.e[R.n] = i + 1;
+            ++R.n;
+        } else {
+            R.n = kRuns + 1;
+        }
         ++k;
         ++i;
     }
     return k;
 }
 
+// Writes the samples counted by count_samples: from the remembered runs, or by
+// walking again when there were more runs than remembered.
+__device__ void emit_samples(const RenderParams &P, const WalkCtx &X, V3 o, V3 d, float a, float b, const Runs &R,
+                             float4 *out) {
+    Segment S;
+    if (!segment_of(P, o, d, a, b, S)) return;
+    if (R.n <= kRuns) {
+        uint32_t k = 0;
+        for (int r = 0; r < R.n; ++r)
+            for (int i = R.b[r]; i < R.e[r]; ++i) {
+                float tm, delta;
+                interval(P, S, i, tm, delta);
+                const V3 p = fma3(d, tm, o);
+                out[k++] = make_float4(p.x, p.y, p.z, delta);
+            }
+        return;
+    }
+    Runs dummy;
+    unsigned long long nom = 0;
+    // more runs than remembered: repeat the walk, writing instead of counting
+    const FieldDev &F = P.F;
+    const V3 inv = v3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+    const bool hash = F.kind == MRF_FIELD_HASHGRID;
+    const bool use_occ = hash && F.occ != nullptr;
+    const bool use_coarse = use_occ && X.coarse != nullptr;
+    const int Rc = F.occ_coarse_res;
+    (void)dummy;
+    (void)nom;
+    uint32_t k = 0;
+    for (int i = 0; i < S.n;) {
+        float tm, delta;
+        interval(P, S, i, tm, delta);
+        const V3 p = fma3(d, tm, o);
+        if (use_coarse) {
+            int c[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                c[q] = min(max((int)floorf((comp(p, q) - F.lo[q]) * F.occ_coarse_scale[q]), 0), Rc - 1);
+            const uint32_t ci = (uint32_t)c[0] + (uint32_t)Rc * ((uint32_t)c[1] + (uint32_t)Rc * (uint32_t)c[2]);
+            if (!((X.coarse[ci >> 5] >> (ci & 31)) & 1u)) {
+                const float te = grid_cell_exit(F.lo, F.occ_coarse_scale, c, o, inv);
+                i = max(i + 1, (int)ceilf((te - S.t0) / S.h - 0.5f));
+                continue;
+            }
+        }
+        if (use_occ) {
+            int c[3];
+            if (!occupied(F, p, c)) {
+                const float te = grid_cell_exit(F.lo, F.occ_scale, c, o, inv);
+                i = max(i + 1, (int)ceilf((te - S.t0) / S.h - 0.5f));
+                continue;
+            }
+        }
+        if (hash && !(support_at(F, X.support, p) > 0.f)) {
+            ++i;
+            continue;
+        }
+        out[k++] = make_float4(p.x, p.y, p.z, delta);
+        ++i;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) wf_cast_gen(const WfParams W, uint32_t j, int cur) {
+    __shared__ WalkSmem wsm;
     const RenderParams &P = W.R;
+    const WalkCtx X = stage_walk(P.F, wsm);
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t live = j == 1 ? W.paths : W.ctr[cur];
     const bool active = tid < live;
     const int nl = P.n_lights;
+    constexpr int kLightRuns = 2;   // lights whose sample runs are remembered between the walks
     Counters C = {};
     V3 o = v3(0.f, 0.f, 0.f), d = v3(0.f, 0.f, 1.f);
     uint32_t prev = kNoHit;
@@ -129,6 +291,8 @@ __global__ void __launch_bounds__(kThreads) wf_cast_gen(const WfParams W, uint32
     uint32_t n_r = 0, n_s_total = 0;
     SurfaceHit S;
     bool diffuse = false;
+    Runs Rr, Rs[kLightRuns];
+    Rr.n = 0;
     if (j == 1 && tid == 0) W.ctr[cur] = W.paths;  // every path is live in segment 1
     if (active) {
         if (j == 1) {
@@ -150,7 +314,7 @@ __global__ void __launch_bounds__(kThreads) wf_cast_gen(const WfParams W, uint32
         bvh_trace<false>(P.B, o, d, prev, P.tmin, INFINITY, h, rt, fault);
         C.retests += rt;
         if (fault) C.fault |= 1;
-        n_r = walk_samples<false>(P, o, d, 0.f, h.t, nullptr, C.nominal);
+        n_r = count_samples(P, X, o, d, 0.f, h.t, C.nominal, Rr);
         if (h.id != kNoHit) {
             S = surface_at(P, o, d, h);
             diffuse = S.mat.kind == MRF_MAT_DIFFUSE;
@@ -173,7 +337,8 @@ __global__ void __launch_bounds__(kThreads) wf_cast_gen(const WfParams W, uint32
                         float w3[3];
                         nee_weight(P, S, l, cosl, D2, w3);
                         wgt = make_float4(w3[0], w3[1], w3[2], 1.f);
-                        ns = walk_samples<false>(P, S.p, wl, 0.f, D, nullptr, C.nominal);
+                        Runs tmp;
+                        ns = count_samples(P, X, S.p, wl, 0.f, D, C.nominal, l < kLightRuns ? Rs[l] : tmp);
                     }
                 }
                 W.sw[(size_t)tid * nl + l] = wgt;
@@ -191,7 +356,7 @@ __global__ void __launch_bounds__(kThreads) wf_cast_gen(const WfParams W, uint32
         W.hit_id[tid] = h.id;
         uint32_t k = base;
         if (fits) {
-            walk_samples<true>(P, o, d, 0.f, h.t, W.samp + k, C.nominal);
+            emit_samples(P, X, o, d, 0.f, h.t, Rr, W.samp + k);
             W.rstart[tid] = k;
             W.rcount[tid] = n_r;
             k += n_r;
@@ -208,7 +373,9 @@ __global__ void __launch_bounds__(kThreads) wf_cast_gen(const WfParams W, uint32
                     V3 wl;
                     float D, D2, cosl;
                     light_geometry(P, S, l, wl, D, D2, cosl);
-                    walk_samples<true>(P, S.p, wl, 0.f, D, W.samp + k, C.nominal);
+                    Runs walk_again;
+                    walk_again.n = kRuns + 1;
+                    emit_samples(P, X, S.p, wl, 0.f, D, l < kLightRuns ? Rs[l] : walk_again, W.samp + k);
                     W.sstart[idx] = k;
                     k += ns;
                 } else {
