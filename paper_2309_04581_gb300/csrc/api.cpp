@@ -360,8 +360,12 @@ static mrf_status field_create_impl(mrf_context *ctx, const mrf_field_desc *D, m
                 }
         if ((st = upload(f, coarse.data(), coarse.size(), &F.occ_coarse, "coarse occupancy"))) return st;
         F.occ_coarse_res = (int)Rc;
-        for (int k = 0; k < 3; ++k)
-            F.occ_coarse_scale[k] = (float)((double)Rc / ((double)D->aabb_max[k] - (double)D->aabb_min[k]));
+        for (int k = 0; k < 3; ++k) {
+            const double ext = (double)D->aabb_max[k] - (double)D->aabb_min[k];
+            F.occ_coarse_scale[k] = (float)((double)Rc / ext);
+            F.occ_cell[k] = (float)(ext / (double)R);
+            F.occ_coarse_cell[k] = (float)(ext / (double)Rc);
+        }
     }
     (void)ctx;
     return MRF_OK;
@@ -697,6 +701,8 @@ mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *b
                                                        : opts->engine;
     if (engine == MRF_ENGINE_MEGAKERNEL && lowp)
         return fail(MRF_ERR_UNSUPPORTED, "mrf_render: FP16/BF16 fields run on the wavefront engine");
+    if (engine == MRF_ENGINE_WAVEFRONT && ctx->n_lights > 8)
+        return fail(MRF_ERR_UNSUPPORTED, "mrf_render: the wavefront engine takes at most 8 point lights");
     size_t wf_off = 0;
     if (engine == MRF_ENGINE_WAVEFRONT) {
         wf_off = (scratch_need + 255) & ~(size_t)255;

@@ -5,7 +5,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/mrf.h"
+#include "mrf.h"
 
 namespace mrf {
 
@@ -45,6 +45,7 @@ struct FieldDev {
     int occ_coarse_res;         // occ_res / 8
     const uint32_t *occ_coarse;
     float occ_coarse_scale[3];  // occ_coarse_res / extent
+    float occ_cell[3], occ_coarse_cell[3];  // cell widths (extent / resolution)
     int precision;
 };
 

@@ -21,12 +21,22 @@
 namespace mrf {
 namespace {
 
-constexpr int kThreads = 128;
-constexpr int kSmemW1 = 0, kSmemW2 = 8192, kSmemW3 = 16384, kSmemA = 18432, kSmemBias = 34816;
-constexpr int kSmemBar = kSmemBias + 132 * 4, kSmemTmem = kSmemBar + 8, kSmemSupport = kSmemTmem + 8;
+// Shared-memory layout of one CTA: weights, biases and support spheres shared
+// by its tile groups, then one mbarrier and one 16 KB A operand per group.
+constexpr int kSmemW1 = 0, kSmemW2 = 8192, kSmemW3 = 16384, kSmemBias = 18432;
+constexpr int kSmemSupport = kSmemBias + 132 * 4;
 constexpr int kSupportMax = 64;
-constexpr int kSmemBytes = kSmemSupport + kSupportMax * 16;
-constexpr uint32_t kTmemCols = 64;
+constexpr int kSmemBars = kSmemSupport + kSupportMax * 16;
+constexpr int kABytes = 16384;
+template <int G>
+struct Layout {
+    static constexpr int bars = kSmemBars;
+    static constexpr int tmem_slot = kSmemBars + 8 * G;
+    static constexpr int a0 = (tmem_slot + 8 + 127) / 128 * 128;
+    static constexpr int bytes = a0 + G * kABytes;
+    static constexpr uint32_t tmem_cols = 64 * G;   // 64 accumulator columns per group
+};
+constexpr int kGroups = 8;   // 128-sample tiles in flight per CTA (one CTA per SM, all 512 TMEM columns)
 constexpr long long kWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -75,6 +85,18 @@ __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fenc
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// barrier over the 128 threads of one tile group (named barrier `id`), OR-reducing `pred`
+__device__ __forceinline__ bool group_sync_or(int id, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "barrier.red.or.pred q, %2, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id)
+        : "memory");
+    return r != 0;
+}
+
 __device__ __forceinline__ void tmem_ld_x32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
@@ -121,25 +143,28 @@ __device__ __forceinline__ void relu_bias_store(const uint32_t (&r)[32], const f
     }
 }
 
-template <bool kBF16>
-__global__ void __launch_bounds__(kThreads, 4)
+// G tile groups of 128 threads per CTA; group g owns TMEM columns [64g, 64g + 64),
+// its own A operand and mbarrier, and synchronises on named barrier 1 + g.
+template <bool kBF16, int G>
+__global__ void __launch_bounds__(128 * G, 1)
     field_tc_kernel(const FieldDev F, const float *__restrict__ pts, int stride, const uint32_t *__restrict__ n_dev,
                     uint32_t n_host, float4 *__restrict__ out, unsigned *__restrict__ status) {
+    using Lo = Layout<G>;
     extern __shared__ __align__(128) uint8_t smem[];
-    uint8_t *sA = smem + kSmemA;
     float *sBias = reinterpret_cast<float *>(smem + kSmemBias);
-    uint64_t *sBar = reinterpret_cast<uint64_t *>(smem + kSmemBar);
-    uint32_t *sTmem = reinterpret_cast<uint32_t *>(smem + kSmemTmem);
+    uint32_t *sTmem = reinterpret_cast<uint32_t *>(smem + Lo::tmem_slot);
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int g = tid >> 7, gt = tid & 127, gw = gt >> 5;
     const int n_in = F.n_in, kin = n_in / 16, sbo_in = (n_in / 8) * 128;
+    constexpr int kThreadsCta = 128 * G;
 
-    // stage the low-precision weights (already in the canonical layout) and FP32 biases
+    // stage the low-precision weights (already in the canonical layout), FP32 biases, support spheres
     {
         const int w1_bytes = 64 * n_in * 2;
         const uint8_t *src = reinterpret_cast<const uint8_t *>(F.mlp_lp) + (kBF16 ? w1_bytes + 10240 : 0);
-        for (int o = tid * 16; o < w1_bytes; o += kThreads * 16)
+        for (int o = tid * 16; o < w1_bytes; o += kThreadsCta * 16)
             *reinterpret_cast<uint4 *>(smem + kSmemW1 + o) = __ldg(reinterpret_cast<const uint4 *>(src + o));
-        for (int o = tid * 16; o < 10240; o += kThreads * 16)
+        for (int o = tid * 16; o < 10240; o += kThreadsCta * 16)
             *reinterpret_cast<uint4 *>(smem + kSmemW2 + o) = __ldg(reinterpret_cast<const uint4 *>(src + w1_bytes + o));
         const float *b1 = F.mlp + n_in * 64, *b2 = b1 + 64 + 4096, *b3 = b2 + 64 + 256;
         if (tid < 64) {
@@ -151,15 +176,16 @@ __global__ void __launch_bounds__(kThreads, 4)
     float4 *sSup = reinterpret_cast<float4 *>(smem + kSmemSupport);
     const bool sup_smem = F.n_support <= kSupportMax;
     if (sup_smem)
-        for (int k = tid; k < F.n_support; k += kThreads) sSup[k] = __ldg(F.support + k);
+        for (int k = tid; k < F.n_support; k += kThreadsCta) sSup[k] = __ldg(F.support + k);
     const float4 *sup = sup_smem ? sSup : F.support;
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(sBar)), "r"(1) : "memory");
+    const uint32_t bar = smem_u32(smem + Lo::bars + 8 * g);
+    if (gt == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(1) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(sTmem)),
-                     "r"(kTmemCols)
+                     "r"(Lo::tmem_cols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -168,16 +194,19 @@ __global__ void __launch_bounds__(kThreads, 4)
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = *sTmem;
-    const uint32_t t_row = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t t_acc = tmem + 64u * (uint32_t)g;                       // this group's columns
+    const uint32_t t_row = t_acc + ((uint32_t)(gw * 32) << 16);            // this warp's lanes
+    uint8_t *sA = smem + Lo::a0 + g * kABytes;
     const uint32_t aA = smem_u32(sA), aW1 = smem_u32(smem + kSmemW1), aW2 = smem_u32(smem + kSmemW2),
-                   aW3 = smem_u32(smem + kSmemW3), bar = smem_u32(sBar);
+                   aW3 = smem_u32(smem + kSmemW3);
     constexpr uint32_t id64 = instr_desc(kBF16, 128, 64), id16 = instr_desc(kBF16, 128, 16);
     const uint32_t n = n_dev ? min(*n_dev, n_host) : n_host;
+    const int bar_id = 1 + g;
     uint32_t phase = 0;
     bool ok = true;
 
-    for (uint32_t tile = blockIdx.x; tile * 128u < n; tile += gridDim.x) {
-        const uint32_t i = tile * 128u + tid;
+    for (uint32_t tile = blockIdx.x * G + g; tile * 128u < n; tile += gridDim.x * G) {
+        const uint32_t i = tile * 128u + gt;
         const bool valid = i < n;
         V3 p = v3(0.f, 0.f, 0.f);
         float s = 0.f;
@@ -204,15 +233,15 @@ __global__ void __launch_bounds__(kThreads, 4)
                     w[q] = pack2<kBF16>(f.x, f.y);
                 }
             }
-            store_chunk(sA, tid, c, sbo_in, make_uint4(w[0], w[1], w[2], w[3]));
+            store_chunk(sA, gt, c, sbo_in, make_uint4(w[0], w[1], w[2], w[3]));
         }
         fence_async_smem();
         fence_before_sync();
-        if (__syncthreads_or(!ok)) break;
-        if (tid == 0) {
+        if (group_sync_or(bar_id, !ok)) break;
+        if (gt == 0) {
             fence_after_sync();
             for (int k = 0; k < kin; ++k)
-                mma_f16(tmem, smem_desc(aA + 256 * k, 128, sbo_in), smem_desc(aW1 + 256 * k, 128, sbo_in), id64, k);
+                mma_f16(t_acc, smem_desc(aA + 256 * k, 128, sbo_in), smem_desc(aW1 + 256 * k, 128, sbo_in), id64, k);
             mma_commit(bar);
         }
         ok &= mbar_wait(bar, phase);
@@ -222,18 +251,18 @@ __global__ void __launch_bounds__(kThreads, 4)
         {
             uint32_t r[32];
             tmem_ld_x32(t_row, r);
-            relu_bias_store<kBF16>(r, sBias, sA, tid, 0);
+            relu_bias_store<kBF16>(r, sBias, sA, gt, 0);
             tmem_ld_x32(t_row + 32, r);
-            relu_bias_store<kBF16>(r, sBias + 32, sA, tid, 4);
+            relu_bias_store<kBF16>(r, sBias + 32, sA, gt, 4);
         }
         fence_async_smem();
         fence_before_sync();
-        if (__syncthreads_or(!ok)) break;
-        if (tid == 0) {
+        if (group_sync_or(bar_id, !ok)) break;
+        if (gt == 0) {
             fence_after_sync();
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                mma_f16(tmem, smem_desc(aA + 256 * k, 128, 1024), smem_desc(aW2 + 256 * k, 128, 1024), id64, k);
+                mma_f16(t_acc, smem_desc(aA + 256 * k, 128, 1024), smem_desc(aW2 + 256 * k, 128, 1024), id64, k);
             mma_commit(bar);
         }
         ok &= mbar_wait(bar, phase);
@@ -243,18 +272,18 @@ __global__ void __launch_bounds__(kThreads, 4)
         {
             uint32_t r[32];
             tmem_ld_x32(t_row, r);
-            relu_bias_store<kBF16>(r, sBias + 64, sA, tid, 0);
+            relu_bias_store<kBF16>(r, sBias + 64, sA, gt, 0);
             tmem_ld_x32(t_row + 32, r);
-            relu_bias_store<kBF16>(r, sBias + 96, sA, tid, 4);
+            relu_bias_store<kBF16>(r, sBias + 96, sA, gt, 4);
         }
         fence_async_smem();
         fence_before_sync();
-        if (__syncthreads_or(!ok)) break;
-        if (tid == 0) {
+        if (group_sync_or(bar_id, !ok)) break;
+        if (gt == 0) {
             fence_after_sync();
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                mma_f16(tmem, smem_desc(aA + 256 * k, 128, 1024), smem_desc(aW3 + 256 * k, 128, 1024), id16, k);
+                mma_f16(t_acc, smem_desc(aA + 256 * k, 128, 1024), smem_desc(aW3 + 256 * k, 128, 1024), id16, k);
             mma_commit(bar);
         }
         ok &= mbar_wait(bar, phase);
@@ -273,25 +302,28 @@ __global__ void __launch_bounds__(kThreads, 4)
         }
         fence_before_sync();
     }
-    if (!ok && tid == 0 && status) atomicOr(status, 4u);
+    if (!ok && gt == 0 && status) atomicOr(status, 4u);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Lo::tmem_cols)
+                     : "memory");
 }
 
 }  // namespace
 
-int field_tc_blocks_per_sm() { return 4; }
+// grid of the persistent launch: one CTA per SM
+int field_tc_blocks_per_sm() { return 1; }
 
 cudaError_t launch_field_tc(const FieldDev &F, bool bf16, const float *pts, int stride, const uint32_t *n_dev,
                             uint32_t n_host, float4 *out, unsigned *status, int grid, cudaStream_t s) {
-    auto kern = bf16 ? field_tc_kernel<true> : field_tc_kernel<false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    auto kern = bf16 ? field_tc_kernel<true, kGroups> : field_tc_kernel<false, kGroups>;
+    constexpr int bytes = Layout<kGroups>::bytes;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     if (grid <= 0) grid = 1;
-    kern<<<grid, kThreads, kSmemBytes, s>>>(F, pts, stride, n_dev, n_host, out, status);
+    kern<<<grid, 128 * kGroups, bytes, s>>>(F, pts, stride, n_dev, n_host, out, status);
     return cudaGetLastError();
 }
 

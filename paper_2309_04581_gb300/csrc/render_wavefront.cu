@@ -1,8 +1,8 @@
 // Wavefront engine: Algorithm 1 run segment by segment over all live paths.
 //
 // Per segment j the host enqueues (no host synchronisation):
-//   1. wf_cast_gen : closest hit, shadow-ray visibility at diffuse hits, and
-//                    generation of every field sample the segment march and
+//   1. wf_cast     : closest hit and shadow-ray visibility at diffuse hits;
+//      wf_gen      : generation of every field sample the segment march and
 //                    the shadow-ray marches need (occupancy skip and support
 //                    test), packed contiguously per job in one flat buffer;
 //   2. field       : evaluation of all generated samples, on the tensor cores
@@ -39,6 +39,8 @@ struct WfParams {
     uint32_t *rstart, *rcount;      // radiance samples of the slot's segment
     uint32_t *sstart, *scount;      // shadow samples, [slot * n_lights + l]
     float4 *sw;                     // next-event weight (rgb), w = 1 when the light is visible
+    float4 *hp;                     // hit point (xyz) and visible-light bits (w) per live slot
+    float4 *sdir;                   // shadow-ray direction (xyz) and light distance (w), [slot * n_lights + l]
     uint32_t *ctr;                  // [0], [1] live counts; [2] generated samples
     float4 *samp;                   // sample position (xyz) and interval length (w)
     float4 *fout;                   // sigma, r, g, b per sample
@@ -65,7 +67,7 @@ __device__ __forceinline__ uint32_t warp_alloc(uint32_t *ctr, uint32_t n) {
 // density-support spheres.
 constexpr int kCoarseWordsMax = 1024;   // coarse grids up to 32^3 are staged
 constexpr int kSupportMax = 64;
-constexpr int kRuns = 8;                // sample runs remembered per job between the two walks
+constexpr int kWfMaxLights = 8;        // point lights the wavefront engine supports
 
 struct WalkSmem {
     uint32_t coarse[kCoarseWordsMax];
@@ -100,23 +102,18 @@ __device__ __forceinline__ float support_at(const FieldDev &F, const float4 *sup
     return s;
 }
 
-// exit parameter of the cell c of a grid with cell size 1/scale along the ray
-__device__ __forceinline__ float grid_cell_exit(const float lo[3], const float scale[3], const int c[3], V3 o, V3 inv) {
+// exit parameter of the cell c of a grid with cell width `cell` along the ray
+__device__ __forceinline__ float grid_cell_exit(const float lo[3], const float cell[3], const int c[3], V3 o, V3 inv) {
     float t = INFINITY;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const float ik = comp(inv, k);
         if (isinf(ik)) continue;
-        const float edge = lo[k] + (float)(c[k] + (ik > 0.f ? 1 : 0)) / scale[k];
+        const float edge = fmaf((float)(c[k] + (ik > 0.f ? 1 : 0)), cell[k], lo[k]);
         t = fminf(t, (edge - comp(o, k)) * ik);
     }
     return t;
 }
-
-struct Runs {
-    int n;           // number of runs recorded, kRuns + 1 = too many
-    int b[kRuns], e[kRuns];
-};
 
 struct Segment {
     float t0, t1, h;
@@ -143,158 +140,175 @@ __device__ __forceinline__ bool segment_of(const RenderParams &P, V3 o, V3 d, fl
     return true;
 }
 
-__device__ __forceinline__ void interval(const RenderParams &P, const Segment &S, int i, float &tm, float &delta) {
-    const float lo = fmaf((float)i, S.h, S.t0);
-    const float hi = P.steps ? fmaf((float)(i + 1), S.h, S.t0) : fminf(lo + S.h, S.t1);
-    tm = 0.5f * (lo + hi);
-    delta = hi - lo;
+// Support spheres a job's ray can enter: lane k tests sphere k (k < 32) against
+// the segment [t0, t1] with a small relative margin; spheres left out have
+// 1 - |p - c|^2 / r^2 < 0 at every point of the segment, so the support (a max
+// clamped at 0) is the same over the kept spheres.  More than 32 spheres: all kept.
+__device__ __forceinline__ uint32_t job_spheres(const FieldDev &F, const WalkCtx &X, V3 o, V3 d, float t0, float t1,
+                                                int lane) {
+    if (F.n_support > 32) return 0xffffffffu;
+    bool hit = false;
+    if (lane < F.n_support) {
+        const float4 c = X.support[lane];
+        const V3 oc = v3(c.x - o.x, c.y - o.y, c.z - o.z);
+        const float dd = dot(d, d), b = dot(oc, d) / dd;   // parameter of the closest approach
+        const float tc = fminf(fmaxf(b, t0), t1);          // clamped to the segment
+        const V3 q = v3(o.x + d.x * tc - c.x, o.y + d.y * tc - c.y, o.z + d.z * tc - c.z);
+        hit = dot(q, q) * c.w < 1.0f + 1e-3f;
+    }
+    return __ballot_sync(0xffffffffu, hit);
 }
 
-// Counts the samples of [a, b] whose density can be non-zero (occupied fine
-// cell and, for the hash grid, positive support), skipping empty coarse and
-// fine cells up to their exits, and remembers the runs of consecutive counted
-// samples.  Same intervals, positions and decisions as march().
-__device__ uint32_t count_samples(const RenderParams &P, const WalkCtx &X, V3 o, V3 d, float a, float b,
-                                  unsigned long long &nominal, Runs &R) {
-    R.n = 0;
+__device__ __forceinline__ float support_masked(const float4 *sup, uint32_t mask, V3 p) {
+    float s = 0.f;
+    while (mask) {
+        const int k = __ffs(mask) - 1;
+        mask &= mask - 1u;
+        const float4 c = sup[k];
+        const float dx = p.x - c.x, dy = p.y - c.y, dz = p.z - c.z;
+        s = fmaxf(s, 1.0f - (dx * dx + dy * dy + dz * dz) * c.w);
+    }
+    return s;
+}
+
+constexpr int kRunsPerJob = 8;
+struct RunList {
+    int n;                 // runs recorded; kRunsPerJob + 1 = more than fit (write pass walks again)
+    int2 r[kRunsPerJob];   // [begin, end) interval indices
+};
+
+// Warp-cooperative walk over the quadrature intervals of one job (every lane
+// holds the same job): lane l takes interval i0 + l of each 32-interval chunk,
+// tests occupancy (coarse, then fine) and the density support exactly as
+// march() does, and the warp advances by 32 or, when the chunk's last interval
+// lies in an empty cell, to that cell's exit.  Counts the samples whose density
+// can be non-zero; records them as runs of consecutive intervals in `runs`
+// (lane 0 writes; may be nullptr) and, if `out` is non-NULL, writes them in
+// order, never more than `limit`.  One compiled copy (noinline) serves the
+// counting and the writing walk, so both take bit-identical decisions.
+__device__ __noinline__ uint32_t warp_walk(const RenderParams &P, const WalkCtx &X, V3 o, V3 d, float a, float b,
+                                           float4 *out, uint32_t limit, unsigned long long &nominal, int lane,
+                                           RunList *runs) {
     Segment S;
+    if (runs && lane == 0) runs->n = 0;
     if (!segment_of(P, o, d, a, b, S)) return 0;
-    nominal += (unsigned long long)S.n;
+    if (!out && lane == 0) nominal += (unsigned long long)S.n;
     const FieldDev &F = P.F;
     const V3 inv = v3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
     const bool hash = F.kind == MRF_FIELD_HASHGRID;
     const bool use_occ = hash && F.occ != nullptr;
     const bool use_coarse = use_occ && X.coarse != nullptr;
     const int Rc = F.occ_coarse_res;
+    const float inv_h = 1.0f / S.h;
+    const uint32_t smask = hash ? job_spheres(F, X, o, d, S.t0, S.t1, lane) : 0u;
+    int nrun = 0, run_end = -1;
     uint32_t k = 0;
-    for (int i = 0; i < S.n;) {
-        float tm, delta;
-        interval(P, S, i, tm, delta);
-        const V3 p = fma3(d, tm, o);
-        if (use_coarse) {
-            int c[3];
+    for (int i0 = 0; i0 < S.n;) {
+        const int i = i0 + lane;
+        bool emit = false;
+        int skip_to = i + 1;
+        float4 rec;
+        if (i < S.n) {
+            const float lo = fmaf((float)i, S.h, S.t0);
+            const float hi = P.steps ? fmaf((float)(i + 1), S.h, S.t0) : fminf(lo + S.h, S.t1);
+            const float tm = 0.5f * (lo + hi), delta = hi - lo;
+            const V3 p = fma3(d, tm, o);
+            bool empty = false;
+            if (use_coarse) {
+                int c[3];
 #pragma unroll
-            for (int q = 0; q < 3; ++q)
-                c[q] = min(max((int)floorf((comp(p, q) - F.lo[q]) * F.occ_coarse_scale[q]), 0), Rc - 1);
-            const uint32_t ci = (uint32_t)c[0] + (uint32_t)Rc * ((uint32_t)c[1] + (uint32_t)Rc * (uint32_t)c[2]);
-            if (!((X.coarse[ci >> 5] >> (ci & 31)) & 1u)) {
-                const float te = grid_cell_exit(F.lo, F.occ_coarse_scale, c, o, inv);
-                i = max(i + 1, (int)ceilf((te - S.t0) / S.h - 0.5f));
-                continue;
+                for (int q = 0; q < 3; ++q)
+                    c[q] = min(max((int)floorf((comp(p, q) - F.lo[q]) * F.occ_coarse_scale[q]), 0), Rc - 1);
+                const uint32_t ci = (uint32_t)c[0] + (uint32_t)Rc * ((uint32_t)c[1] + (uint32_t)Rc * (uint32_t)c[2]);
+                if (!((X.coarse[ci >> 5] >> (ci & 31)) & 1u)) {
+                    const float te = grid_cell_exit(F.lo, F.occ_coarse_cell, c, o, inv);
+                    skip_to = max(i + 1, (int)ceilf((te - S.t0) * inv_h - 0.5f));
+                    empty = true;
+                }
             }
-        }
-        if (use_occ) {
-            int c[3];
-            if (!occupied(F, p, c)) {
-                const float te = grid_cell_exit(F.lo, F.occ_scale, c, o, inv);
-                i = max(i + 1, (int)ceilf((te - S.t0) / S.h - 0.5f));
-                continue;
+            if (!empty && use_occ) {
+                int c[3];
+                if (!occupied(F, p, c)) {
+                    const float te = grid_cell_exit(F.lo, F.occ_cell, c, o, inv);
+                    skip_to = max(i + 1, (int)ceilf((te - S.t0) * inv_h - 0.5f));
+                    empty = true;
+                }
             }
-        }
-        if (hash && !(support_at(F, X.support, p) > 0.f)) {
-            ++i;
-            continue;
-        }
-        if (R.n > 0 && R.n <= kRuns && R.e[R.n - 1] == i) {
-            R.e[R.n - 1] = i + 1;
-        } else if (R.n < kRuns) {
-            R.b[R.n] = i;
-            R.e[R.n] = i + 1;
-            ++R.n;
+            if (!empty) emit = !hash || support_masked(X.support, smask, p) > 0.f;
+            rec = make_float4(p.x, p.y, p.z, delta);
         } else {
-            R.n = kRuns + 1;
+            skip_to = S.n;
         }
-        ++k;
-        ++i;
+        unsigned m = __ballot_sync(0xffffffffu, emit);
+        if (out && emit) {
+            const uint32_t slot = k + __popc(m & ((1u << lane) - 1u));
+            if (slot < limit) out[slot] = rec;
+        }
+        k += __popc(m);
+        if (runs) {
+            // runs of consecutive emitted intervals in this chunk (uniform across lanes)
+            while (m) {
+                const int st = __ffs(m) - 1;
+                const unsigned sh = m >> st;
+                const int len = (~sh == 0u) ? 32 - st : __ffs(~sh) - 1;
+                const int rb = i0 + st, re = rb + len;
+                if (rb == run_end && nrun > 0 && nrun <= kRunsPerJob) {
+                    if (lane == 0) runs->r[nrun - 1].y = re;
+                } else if (nrun < kRunsPerJob) {
+                    if (lane == 0) runs->r[nrun] = make_int2(rb, re);
+                    ++nrun;
+                } else {
+                    nrun = kRunsPerJob + 1;
+                }
+                run_end = re;
+                m = (len == 32) ? 0u : (m & ~(((1u << len) - 1u) << st));
+            }
+        }
+        const int last_skip = __shfl_sync(0xffffffffu, skip_to, 31);
+        i0 = max(i0 + 32, last_skip);
     }
+    if (runs && lane == 0) runs->n = nrun;
     return k;
 }
 
-// Writes the samples counted by count_samples: from the remembered runs, or by
-// walking again when there were more runs than remembered.
-__device__ void emit_samples(const RenderParams &P, const WalkCtx &X, V3 o, V3 d, float a, float b, const Runs &R,
-                             float4 *out) {
+// Writes a job's samples from its recorded runs (lane-parallel over the run's
+// intervals, positions by the same FP32 formulas as the walk).
+__device__ void write_runs(const RenderParams &P, V3 o, V3 d, float a, float b, const RunList &R, float4 *out,
+                           uint32_t limit, int lane) {
     Segment S;
     if (!segment_of(P, o, d, a, b, S)) return;
-    if (R.n <= kRuns) {
-        uint32_t k = 0;
-        for (int r = 0; r < R.n; ++r)
-            for (int i = R.b[r]; i < R.e[r]; ++i) {
-                float tm, delta;
-                interval(P, S, i, tm, delta);
-                const V3 p = fma3(d, tm, o);
-                out[k++] = make_float4(p.x, p.y, p.z, delta);
-            }
-        return;
-    }
-    Runs dummy;
-    unsigned long long nom = 0;
-    // more runs than remembered: repeat the walk, writing instead of counting
-    const FieldDev &F = P.F;
-    const V3 inv = v3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
-    const bool hash = F.kind == MRF_FIELD_HASHGRID;
-    const bool use_occ = hash && F.occ != nullptr;
-    const bool use_coarse = use_occ && X.coarse != nullptr;
-    const int Rc = F.occ_coarse_res;
-    (void)dummy;
-    (void)nom;
     uint32_t k = 0;
-    for (int i = 0; i < S.n;) {
-        float tm, delta;
-        interval(P, S, i, tm, delta);
-        const V3 p = fma3(d, tm, o);
-        if (use_coarse) {
-            int c[3];
-#pragma unroll
-            for (int q = 0; q < 3; ++q)
-                c[q] = min(max((int)floorf((comp(p, q) - F.lo[q]) * F.occ_coarse_scale[q]), 0), Rc - 1);
-            const uint32_t ci = (uint32_t)c[0] + (uint32_t)Rc * ((uint32_t)c[1] + (uint32_t)Rc * (uint32_t)c[2]);
-            if (!((X.coarse[ci >> 5] >> (ci & 31)) & 1u)) {
-                const float te = grid_cell_exit(F.lo, F.occ_coarse_scale, c, o, inv);
-                i = max(i + 1, (int)ceilf((te - S.t0) / S.h - 0.5f));
-                continue;
-            }
+    for (int r = 0; r < R.n; ++r) {
+        const int2 run = R.r[r];
+        for (int i = run.x + lane; i < run.y; i += 32) {
+            const float lo = fmaf((float)i, S.h, S.t0);
+            const float hi = P.steps ? fmaf((float)(i + 1), S.h, S.t0) : fminf(lo + S.h, S.t1);
+            const float tm = 0.5f * (lo + hi), delta = hi - lo;
+            const V3 p = fma3(d, tm, o);
+            const uint32_t slot = k + (uint32_t)(i - run.x);
+            if (slot < limit) out[slot] = make_float4(p.x, p.y, p.z, delta);
         }
-        if (use_occ) {
-            int c[3];
-            if (!occupied(F, p, c)) {
-                const float te = grid_cell_exit(F.lo, F.occ_scale, c, o, inv);
-                i = max(i + 1, (int)ceilf((te - S.t0) / S.h - 0.5f));
-                continue;
-            }
-        }
-        if (hash && !(support_at(F, X.support, p) > 0.f)) {
-            ++i;
-            continue;
-        }
-        out[k++] = make_float4(p.x, p.y, p.z, delta);
-        ++i;
+        k += (uint32_t)(run.y - run.x);
     }
 }
 
-__global__ void __launch_bounds__(kThreads) wf_cast_gen(const WfParams W, uint32_t j, int cur) {
-    __shared__ WalkSmem wsm;
+__device__ __forceinline__ V3 shfl3(V3 v, int src) {
+    return v3(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+              __shfl_sync(0xffffffffu, v.z, src));
+}
+
+// Per lane: primary or queued ray, closest hit (Eq. 3), and at diffuse hits the
+// shadow-ray visibility toward every point light.
+__global__ void __launch_bounds__(kThreads) wf_cast(const WfParams W, uint32_t j, int cur) {
     const RenderParams &P = W.R;
-    const WalkCtx X = stage_walk(P.F, wsm);
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t live = j == 1 ? W.paths : W.ctr[cur];
-    const bool active = tid < live;
     const int nl = P.n_lights;
-    constexpr int kLightRuns = 2;   // lights whose sample runs are remembered between the walks
     Counters C = {};
-    V3 o = v3(0.f, 0.f, 0.f), d = v3(0.f, 0.f, 1.f);
-    uint32_t prev = kNoHit;
-    Hit h;
-    h.t = INFINITY;
-    h.id = kNoHit;
-    h.slot = -1;
-    uint32_t n_r = 0, n_s_total = 0;
-    SurfaceHit S;
-    bool diffuse = false;
-    Runs Rr, Rs[kLightRuns];
-    Rr.n = 0;
     if (j == 1 && tid == 0) W.ctr[cur] = W.paths;  // every path is live in segment 1
-    if (active) {
+    if (tid < live) {
+        V3 o, d;
+        uint32_t prev = kNoHit;
         if (j == 1) {
             const uint32_t path = tid, ray = path / P.spp;
             primary_ray(P, ray, o, d);
@@ -309,89 +323,202 @@ __global__ void __launch_bounds__(kThreads) wf_cast_gen(const WfParams W, uint32
             prev = __float_as_uint(qo.w);
             d = v3(qd.x, qd.y, qd.z);
         }
+        Hit h;
         unsigned rt = 0;
         bool fault = false;
         bvh_trace<false>(P.B, o, d, prev, P.tmin, INFINITY, h, rt, fault);
         C.retests += rt;
         if (fault) C.fault |= 1;
-        n_r = count_samples(P, X, o, d, 0.f, h.t, C.nominal, Rr);
-        if (h.id != kNoHit) {
-            S = surface_at(P, o, d, h);
-            diffuse = S.mat.kind == MRF_MAT_DIFFUSE;
-        }
-        if (diffuse) {
-            for (int l = 0; l < nl; ++l) {
-                V3 wl;
-                float D, D2, cosl;
-                uint32_t ns = 0;
-                float4 wgt = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (light_geometry(P, S, l, wl, D, D2, cosl)) {
-                    ++C.shadow;
-                    Hit hs;
-                    unsigned rs = 0;
-                    bool f2 = false;
-                    const bool blocked = bvh_trace<true>(P.B, S.p, wl, S.id, P.tmin, D, hs, rs, f2);
-                    C.retests += rs;
-                    if (f2) C.fault |= 1;
-                    if (!blocked) {
-                        float w3[3];
-                        nee_weight(P, S, l, cosl, D2, w3);
-                        wgt = make_float4(w3[0], w3[1], w3[2], 1.f);
-                        Runs tmp;
-                        ns = count_samples(P, X, S.p, wl, 0.f, D, C.nominal, l < kLightRuns ? Rs[l] : tmp);
-                    }
-                }
-                W.sw[(size_t)tid * nl + l] = wgt;
-                W.scount[(size_t)tid * nl + l] = ns;
-                n_s_total += ns;
-            }
-        }
-    }
-    const uint32_t n_total = n_r + n_s_total;
-    const uint32_t base = warp_alloc(&W.ctr[2], n_total);
-    if (active) {
-        const bool fits = (uint64_t)base + n_total <= (uint64_t)W.cap;
         W.hit_t[tid] = h.t;
         W.hit_slot[tid] = h.slot;
         W.hit_id[tid] = h.id;
-        uint32_t k = base;
-        if (fits) {
-            emit_samples(P, X, o, d, 0.f, h.t, Rr, W.samp + k);
-            W.rstart[tid] = k;
-            W.rcount[tid] = n_r;
-            k += n_r;
-        } else {
-            W.rcount[tid] = kOverflow;
-        }
-        C.evaluated += n_r;
-        if (diffuse) {
-            for (int l = 0; l < nl; ++l) {
-                const size_t idx = (size_t)tid * nl + l;
-                const uint32_t ns = W.scount[idx];
-                if (W.sw[idx].w == 0.f) continue;
-                if (fits) {
+        uint32_t vis = 0;
+        V3 hp = v3(0.f, 0.f, 0.f);
+        if (h.id != kNoHit) {
+            const SurfaceHit S = surface_at(P, o, d, h);
+            hp = S.p;
+            if (S.mat.kind == MRF_MAT_DIFFUSE) {
+                for (int l = 0; l < nl; ++l) {
                     V3 wl;
                     float D, D2, cosl;
-                    light_geometry(P, S, l, wl, D, D2, cosl);
-                    Runs walk_again;
-                    walk_again.n = kRuns + 1;
-                    emit_samples(P, X, S.p, wl, 0.f, D, l < kLightRuns ? Rs[l] : walk_again, W.samp + k);
-                    W.sstart[idx] = k;
-                    k += ns;
-                } else {
-                    W.scount[idx] = kOverflow;
+                    float4 wgt = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (light_geometry(P, S, l, wl, D, D2, cosl)) {
+                        ++C.shadow;
+                        Hit hs;
+                        unsigned rs = 0;
+                        bool f2 = false;
+                        const bool blocked = bvh_trace<true>(P.B, S.p, wl, S.id, P.tmin, D, hs, rs, f2);
+                        C.retests += rs;
+                        if (f2) C.fault |= 1;
+                        if (!blocked) {
+                            float w3[3];
+                            nee_weight(P, S, l, cosl, D2, w3);
+                            wgt = make_float4(w3[0], w3[1], w3[2], 1.f);
+                            vis |= 1u << l;
+                            W.sdir[(size_t)tid * nl + l] = make_float4(wl.x, wl.y, wl.z, D);
+                        }
+                    }
+                    W.sw[(size_t)tid * nl + l] = wgt;
+                    W.scount[(size_t)tid * nl + l] = 0;
                 }
-                C.shadow_eval += ns;
             }
         }
+        W.hp[tid] = make_float4(hp.x, hp.y, hp.z, __uint_as_float(vis));
     }
     flush_counters(P.stats, C);
     if (C.fault && P.status) atomicOr(P.status, C.fault);
 }
 
+// Warp-cooperative sample generation: counts the samples of every job of the
+// warp's 32 slots (segment march and visible shadow rays), allocates their
+// ranges with one atomic per warp, and writes them in order.
+__global__ void __launch_bounds__(kThreads) wf_gen(const WfParams W, uint32_t j, int cur) {
+    __shared__ WalkSmem wsm;
+    __shared__ RunList runs_sm[kThreads / 32][32][2];   // per warp, per slot: segment job, first shadow job
+    const RenderParams &P = W.R;
+    const WalkCtx X = stage_walk(P.F, wsm);
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const uint32_t live = j == 1 ? W.paths : W.ctr[cur];
+    const bool active = tid < live;
+    const int nl = P.n_lights;
+    Counters C = {};
+    V3 o = v3(0.f, 0.f, 0.f), d = v3(0.f, 0.f, 1.f), hp = v3(0.f, 0.f, 0.f);
+    float th = 0.f;
+    uint32_t vis = 0;
+    if (active) {
+        const float4 qo = W.qo[cur][tid], qd = W.qd[cur][tid], h4 = W.hp[tid];
+        o = v3(qo.x, qo.y, qo.z);
+        d = v3(qd.x, qd.y, qd.z);
+        th = W.hit_t[tid];
+        hp = v3(h4.x, h4.y, h4.z);
+        vis = __float_as_uint(h4.w);
+    }
+    uint32_t my_nr = 0, my_total = 0;
+    for (int src = 0; src < 32; ++src) {
+        if (!__shfl_sync(0xffffffffu, (int)active, src)) continue;
+        const V3 so = shfl3(o, src), sd = shfl3(d, src), sp = shfl3(hp, src);
+        const float st = __shfl_sync(0xffffffffu, th, src);
+        const uint32_t svis = __shfl_sync(0xffffffffu, vis, src);
+        const uint32_t src_tid = tid - lane + src;
+        RunList(&rl)[2] = runs_sm[threadIdx.x >> 5][src];
+        const uint32_t n_r = warp_walk(P, X, so, sd, 0.f, st, nullptr, 0, C.nominal, lane, &rl[0]);
+        uint32_t n_s = 0;
+        for (int l = 0; l < nl; ++l) {
+            if (!((svis >> l) & 1u)) continue;
+            const float4 sh = W.sdir[(size_t)src_tid * nl + l];
+            const uint32_t ns = warp_walk(P, X, sp, v3(sh.x, sh.y, sh.z), 0.f, sh.w, nullptr, 0, C.nominal, lane,
+                                          l == 0 ? &rl[1] : nullptr);
+            if (lane == src) W.scount[(size_t)tid * nl + l] = ns;
+            n_s += ns;
+        }
+        if (lane == src) {
+            W.rcount[tid] = n_r;
+            my_nr = n_r;
+            my_total = n_r + n_s;
+            C.evaluated += n_r;
+            C.shadow_eval += n_s;
+        }
+    }
+    const uint32_t base = warp_alloc(&W.ctr[2], my_total);
+    const bool fits = (uint64_t)base + my_total <= (uint64_t)W.cap;
+    __syncwarp();
+    for (int src = 0; src < 32; ++src) {
+        if (!__shfl_sync(0xffffffffu, (int)active, src)) continue;
+        const bool sfits = __shfl_sync(0xffffffffu, (int)fits, src);
+        const uint32_t sbase = __shfl_sync(0xffffffffu, base, src);
+        const uint32_t svis = __shfl_sync(0xffffffffu, vis, src);
+        const uint32_t src_tid = tid - lane + src;
+        if (!sfits) {
+            if (lane == src) {
+                W.rcount[tid] = kOverflow;
+                for (int l = 0; l < nl; ++l)
+                    if ((vis >> l) & 1u) W.scount[(size_t)tid * nl + l] = kOverflow;
+            }
+            continue;
+        }
+        const V3 so = shfl3(o, src), sd = shfl3(d, src), sp = shfl3(hp, src);
+        const float st = __shfl_sync(0xffffffffu, th, src);
+        unsigned long long dummy = 0;
+        uint32_t k = sbase;
+        const uint32_t nr = __shfl_sync(0xffffffffu, my_nr, src);
+        const RunList(&rl)[2] = runs_sm[threadIdx.x >> 5][src];
+        if (rl[0].n <= kRunsPerJob)
+            write_runs(P, so, sd, 0.f, st, rl[0], W.samp + k, nr, lane);
+        else
+            warp_walk(P, X, so, sd, 0.f, st, W.samp + k, nr, dummy, lane, nullptr);
+        k += nr;
+        if (lane == src) W.rstart[tid] = sbase;
+        for (int l = 0; l < nl; ++l) {
+            if (!((svis >> l) & 1u)) continue;
+            const float4 sh = W.sdir[(size_t)src_tid * nl + l];
+            const uint32_t ns = W.scount[(size_t)src_tid * nl + l];
+            if (lane == src) W.sstart[(size_t)tid * nl + l] = k;
+            if (l == 0 && rl[1].n <= kRunsPerJob)
+                write_runs(P, sp, v3(sh.x, sh.y, sh.z), 0.f, sh.w, rl[1], W.samp + k, ns, lane);
+            else
+                warp_walk(P, X, sp, v3(sh.x, sh.y, sh.z), 0.f, sh.w, W.samp + k, ns, dummy, lane, nullptr);
+            k += ns;
+        }
+    }
+    flush_counters(P.stats, C);
+}
+
+// Warp-cooperative compositing of one job's samples (every lane holds the same
+// job): 32 consecutive samples per step, cumulative optical depth by a warp
+// scan, T(t) = T0 exp(-depth before the sample), L += T(t) alpha r (Eqs. 10-11).
+// Stops after the sample at which max(T) falls below tau.  Each lane returns
+// its partial sums of L; `depth` (the job's optical depth up to the stop) and
+// `stop` are the same in every lane.
+__device__ __forceinline__ void warp_composite(const WfParams &W, uint32_t start, uint32_t count, float tmax0,
+                                               float tau, int lane, float &lr, float &lg, float &lb, float &depth,
+                                               bool &stop) {
+    lr = lg = lb = 0.f;
+    depth = 0.f;
+    stop = false;
+    for (uint32_t i0 = 0; i0 < count; i0 += 32) {
+        const bool v = i0 + lane < count;
+        float x = 0.f;
+        float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (v) {
+            const uint32_t k = start + i0 + lane;
+            f = W.fout[k];
+            x = f.x * W.samp[k].w;
+        }
+        float sc = x;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const float y = __shfl_up_sync(0xffffffffu, sc, off);
+            if (lane >= off) sc += y;
+        }
+        const float before = depth + (sc - x), after = depth + sc;
+        const bool cross = v && tau > 0.f && tmax0 * expf(-after) < tau;
+        const unsigned cm = __ballot_sync(0xffffffffu, cross);
+        const int last = cm ? __ffs(cm) - 1 : 31;
+        if (v && lane <= last) {
+            const float a = -expm1f(-x) * expf(-before);
+            lr = fmaf(a, f.y, lr);
+            lg = fmaf(a, f.z, lg);
+            lb = fmaf(a, f.w, lb);
+        }
+        depth += __shfl_sync(0xffffffffu, sc, last);
+        if (cm) {
+            stop = true;
+            break;
+        }
+    }
+}
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    return x;
+}
+
 __global__ void __launch_bounds__(kThreads) wf_shade(const WfParams W, uint32_t j, int cur, int nxt) {
     const RenderParams &P = W.R;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
     const uint32_t live = W.ctr[cur];
     const bool active = tid < live;
     const int nl = P.n_lights;
@@ -400,43 +527,91 @@ __global__ void __launch_bounds__(kThreads) wf_shade(const WfParams W, uint32_t 
     uint32_t path = 0, prev = kNoHit;
     V3 o = v3(0.f, 0.f, 0.f), d = v3(0.f, 0.f, 1.f);
     float T[3] = {1.f, 1.f, 1.f};
+    Hit h;
+    h.t = INFINITY;
+    h.slot = -1;
+    h.id = kNoHit;
+    uint32_t rc = 0, r0 = 0;
+    bool diffuse = false;
+    SurfaceHit S;
     if (active) {
         path = W.qpath[cur][tid];
-        const uint32_t ray = path / P.spp, s = path % P.spp;
         const float4 qo = W.qo[cur][tid], qd = W.qd[cur][tid], qT = W.qT[cur][tid];
         o = v3(qo.x, qo.y, qo.z);
         d = v3(qd.x, qd.y, qd.z);
-        T[0] = qT.x; T[1] = qT.y; T[2] = qT.z;
-        float4 acc = j == 1 ? make_float4(0.f, 0.f, 0.f, 0.f) : W.acc[path];
-        float L[3] = {acc.x, acc.y, acc.z};
-        Hit h;
+        T[0] = qT.x;
+        T[1] = qT.y;
+        T[2] = qT.z;
         h.t = W.hit_t[tid];
         h.slot = W.hit_slot[tid];
         h.id = W.hit_id[tid];
-        // Eqs. 10-11 over the segment's samples, in order
+        rc = W.rcount[tid];
+        r0 = W.rstart[tid];
+        if (h.id != kNoHit) {
+            S = surface_at(P, o, d, h);
+            diffuse = S.mat.kind == MRF_MAT_DIFFUSE;
+        }
+    }
+    // warp-cooperative compositing of every lane's segment samples and shadow samples
+    float Lseg[3] = {0.f, 0.f, 0.f}, seg_depth = 0.f;
+    bool seg_stop = false;
+    float sh_depth[kWfMaxLights];
+#pragma unroll
+    for (int l = 0; l < kWfMaxLights; ++l) sh_depth[l] = 0.f;
+    for (int src = 0; src < 32; ++src) {
+        const bool sact = __shfl_sync(0xffffffffu, (int)active, src);
+        if (!sact) continue;
+        const uint32_t src_rc = __shfl_sync(0xffffffffu, rc, src);
+        if (src_rc != kOverflow) {
+            const uint32_t src_r0 = __shfl_sync(0xffffffffu, r0, src);
+            const float tmax0 = __shfl_sync(0xffffffffu, fmaxf(T[0], fmaxf(T[1], T[2])), src);
+            float lr, lg, lb, dep;
+            bool stp;
+            warp_composite(W, src_r0, src_rc, tmax0, P.tau, lane, lr, lg, lb, dep, stp);
+            lr = warp_sum(lr);
+            lg = warp_sum(lg);
+            lb = warp_sum(lb);
+            if (lane == src) {
+                Lseg[0] = lr;
+                Lseg[1] = lg;
+                Lseg[2] = lb;
+                seg_depth = dep;
+                seg_stop = stp;
+            }
+        }
+        const bool sdiff = __shfl_sync(0xffffffffu, (int)diffuse, src);
+        if (!sdiff) continue;
+        const uint32_t src_tid = tid - lane + src;
+        for (int l = 0; l < nl; ++l) {
+            const size_t idx = (size_t)src_tid * nl + l;
+            const float4 wgt = W.sw[idx];
+            const uint32_t sc = W.scount[idx];
+            if (wgt.w == 0.f || sc == kOverflow) continue;
+            const uint32_t s0 = W.sstart[idx];
+            float dep = 0.f;
+            for (uint32_t i0 = lane; i0 < sc; i0 += 32) dep = fmaf(W.fout[s0 + i0].x, W.samp[s0 + i0].w, dep);
+            dep = warp_sum(dep);
+            if (lane == src) sh_depth[l] = dep;
+        }
+    }
+    if (active) {
+        const uint32_t ray = path / P.spp, s = path % P.spp;
+        float4 acc = j == 1 ? make_float4(0.f, 0.f, 0.f, 0.f) : W.acc[path];
+        float L[3] = {acc.x, acc.y, acc.z};
         const float T0 = T[0];
         bool stop = false;
-        const uint32_t rc = W.rcount[tid];
         if (rc == kOverflow) {
             Counters dummy = {};
             march<true>(P, P.F.mlp, o, d, 0.f, h.t, T, L, stop, dummy);
         } else {
-            const uint32_t r0 = W.rstart[tid];
-            for (uint32_t k = r0; k < r0 + rc; ++k) {
-                const float4 f = W.fout[k];
-                const float x = f.x * W.samp[k].w;
-                const float att = expf(-x), alpha = -expm1f(-x);
-                L[0] = fmaf(T[0] * alpha, f.y, L[0]);
-                L[1] = fmaf(T[1] * alpha, f.z, L[1]);
-                L[2] = fmaf(T[2] * alpha, f.w, L[2]);
-                T[0] *= att;
-                T[1] *= att;
-                T[2] *= att;
-                if (P.tau > 0.f && fmaxf(T[0], fmaxf(T[1], T[2])) < P.tau) {
-                    stop = true;
-                    break;
-                }
+            // Eqs. 10-11: L += T(p_j) * sum_i T_i alpha_i r_i, T' = T(p_j) exp(-depth)
+            const float att = expf(-seg_depth);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                L[k] = fmaf(T[k], Lseg[k], L[k]);
+                T[k] *= att;
             }
+            stop = seg_stop;
         }
         if (j == 1) acc.w = T0 > 0.f ? 1.f - T[0] / T0 : 0.f;
         ++C.seg;
@@ -448,26 +623,21 @@ __global__ void __launch_bounds__(kThreads) wf_shade(const WfParams W, uint32_t 
         bool end = stop || h.id == kNoHit;
         if (!end) {
             ++C.hits;
-            const SurfaceHit S = surface_at(P, o, d, h);
             float u[3];
             surface_uniforms(P, ray, s, j, u);
-            if (S.mat.kind == MRF_MAT_DIFFUSE) {
+            if (diffuse) {
                 for (int l = 0; l < nl; ++l) {
                     const size_t idx = (size_t)tid * nl + l;
                     const float4 wgt = W.sw[idx];
                     if (wgt.w == 0.f) continue;
-                    const uint32_t sc = W.scount[idx];
-                    float depth = 0.f;
-                    if (sc == kOverflow) {
+                    float depth = sh_depth[l];
+                    if (W.scount[idx] == kOverflow) {
                         V3 wl;
                         float D, D2, cosl;
                         light_geometry(P, S, l, wl, D, D2, cosl);
                         Counters dummy = {};
                         bool dstop = false;
                         depth = march<false>(P, P.F.mlp, S.p, wl, 0.f, D, nullptr, nullptr, dstop, dummy);
-                    } else {
-                        const uint32_t s0 = W.sstart[idx];
-                        for (uint32_t k = s0; k < s0 + sc; ++k) depth = fmaf(W.fout[k].x, W.samp[k].w, depth);
                     }
                     const float Tf = expf(-depth);
                     L[0] = fmaf(T[0] * Tf, wgt.x, L[0]);
@@ -521,8 +691,8 @@ __global__ void __launch_bounds__(kThreads) wf_finalize(const float4 *__restrict
 
 // scratch layout
 struct Layout {
-    size_t acc, qpath[2], qo[2], qd[2], qT[2], hit_t, hit_slot, hit_id, rstart, rcount, sstart, scount, sw, ctr, samp,
-        fout, total;
+    size_t acc, qpath[2], qo[2], qd[2], qT[2], hit_t, hit_slot, hit_id, rstart, rcount, sstart, scount, sw, hp, sdir,
+        ctr, samp, fout, total;
     uint32_t cap;
 };
 
@@ -550,6 +720,8 @@ Layout layout(uint32_t paths, int n_lights) {
     L.sstart = take(4 * P * nl);
     L.scount = take(4 * P * nl);
     L.sw = take(16 * P * nl);
+    L.hp = take(16 * P);
+    L.sdir = take(16 * P * nl);
     L.ctr = take(16);
     // sample capacity: 96 samples per path plus 4M (overflowing jobs are marched in place)
     const uint64_t cap = std::min<uint64_t>((uint64_t)P * 96 + (4u << 20), 0x7FFFFFFFull);
@@ -592,6 +764,8 @@ cudaError_t launch_render_wavefront(const RenderParams &P, void *scratch, size_t
     W.sstart = reinterpret_cast<uint32_t *>(b + Lo.sstart);
     W.scount = reinterpret_cast<uint32_t *>(b + Lo.scount);
     W.sw = reinterpret_cast<float4 *>(b + Lo.sw);
+    W.hp = reinterpret_cast<float4 *>(b + Lo.hp);
+    W.sdir = reinterpret_cast<float4 *>(b + Lo.sdir);
     W.ctr = reinterpret_cast<uint32_t *>(b + Lo.ctr);
     W.samp = reinterpret_cast<float4 *>(b + Lo.samp);
     W.fout = reinterpret_cast<float4 *>(b + Lo.fout);
@@ -606,7 +780,11 @@ cudaError_t launch_render_wavefront(const RenderParams &P, void *scratch, size_t
         const int cur = (j - 1) & 1, nxt = j & 1;
         if ((e = cudaMemsetAsync(W.ctr + 2, 0, 4, s)) != cudaSuccess) return e;
         timer_begin(timer, MRF_KERNEL_CAST_GEN, s);
-        wf_cast_gen<<<grid, kThreads, 0, s>>>(W, j, cur);
+        wf_cast<<<grid, kThreads, 0, s>>>(W, j, cur);
+        timer_end(timer, s);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        timer_begin(timer, MRF_KERNEL_GEN, s);
+        wf_gen<<<grid, kThreads, 0, s>>>(W, j, cur);
         timer_end(timer, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         timer_begin(timer, MRF_KERNEL_FIELD, s);
@@ -709,6 +887,8 @@ cudaError_t launch_render_wavefront_arena(const RenderParams &P, void *arena, si
     W.sstart = reinterpret_cast<uint32_t *>(b + Lo.sstart);
     W.scount = reinterpret_cast<uint32_t *>(b + Lo.scount);
     W.sw = reinterpret_cast<float4 *>(b + Lo.sw);
+    W.hp = reinterpret_cast<float4 *>(b + Lo.hp);
+    W.sdir = reinterpret_cast<float4 *>(b + Lo.sdir);
     W.ctr = reinterpret_cast<uint32_t *>(b + Lo.ctr);
     W.samp = reinterpret_cast<float4 *>(b + Lo.samp);
     W.fout = reinterpret_cast<float4 *>(b + Lo.fout);
@@ -722,7 +902,9 @@ cudaError_t launch_render_wavefront_arena(const RenderParams &P, void *arena, si
     for (uint32_t j = 1; j <= P.max_bounces; ++j) {
         const int cur = (j - 1) & 1, nxt = j & 1;
         if ((e = cudaMemsetAsync(W.ctr + 2, 0, 4, s)) != cudaSuccess) return e;
-        wf_cast_gen<<<grid, kThreads, 0, s>>>(W, j, cur);
+        wf_cast<<<grid, kThreads, 0, s>>>(W, j, cur);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        wf_gen<<<grid, kThreads, 0, s>>>(W, j, cur);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (tc)
             e = launch_field_tc(F, F.precision == MRF_PREC_BF16, reinterpret_cast<const float *>(W.samp), 4, W.ctr + 2,
