@@ -198,7 +198,7 @@ enum { MRF_ENGINE_AUTO = 0, MRF_ENGINE_MEGAKERNEL = 1, MRF_ENGINE_WAVEFRONT = 2 
 /* kernel kinds of the per-kernel timing in mrf_render_opts.kernel_ms */
 enum {
     MRF_KERNEL_MEGAKERNEL = 0, MRF_KERNEL_CAST_GEN = 1, MRF_KERNEL_FIELD = 2, MRF_KERNEL_SHADE = 3,
-    MRF_KERNEL_FINALIZE = 4, MRF_KERNEL_GEN = 5, MRF_KERNEL_COUNT = 6
+    MRF_KERNEL_FINALIZE = 4, MRF_KERNEL_GEN = 5, MRF_KERNEL_COMPOSITE = 6, MRF_KERNEL_COUNT = 7
 };
 
 typedef struct mrf_render_opts {

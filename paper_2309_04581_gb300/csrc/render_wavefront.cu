@@ -7,8 +7,9 @@
 //                    test), packed contiguously per job in one flat buffer;
 //   2. field       : evaluation of all generated samples, on the tensor cores
 //                    for the hash grid at FP16/BF16 (field_tc.cu), else FP32;
-//   3. wf_shade    : in-order compositing of each job's samples (Eqs. 10-11),
-//                    next-event term, BSDF sample (Eqs. 12-13), termination,
+//   3. wf_composite: in-order compositing of each job's samples (Eqs. 10-11),
+//                    one warp per job at a time;
+//      wf_shade    : next-event term, BSDF sample (Eqs. 12-13), termination,
 //                    and compaction of the surviving paths into the next queue.
 // Sample positions, quadrature intervals and every decision are computed with
 // the same FP32 formulas as the megakernel.  Jobs whose samples do not fit the
@@ -41,6 +42,8 @@ struct WfParams {
     float4 *sw;                     // next-event weight (rgb), w = 1 when the light is visible
     float4 *hp;                     // hit point (xyz) and visible-light bits (w) per live slot
     float4 *sdir;                   // shadow-ray direction (xyz) and light distance (w), [slot * n_lights + l]
+    float4 *comp;                   // per slot: segment radiance sum (rgb, times T(p_j)) and optical depth (w)
+    float *sdepth;                  // shadow optical depth, [slot * n_lights + l]
     uint32_t *ctr;                  // [0], [1] live counts; [2] generated samples
     float4 *samp;                   // sample position (xyz) and interval length (w)
     float4 *fout;                   // sigma, r, g, b per sample
@@ -372,7 +375,7 @@ __global__ void __launch_bounds__(kThreads) wf_cast(const WfParams W, uint32_t j
 // Warp-cooperative sample generation: counts the samples of every job of the
 // warp's 32 slots (segment march and visible shadow rays), allocates their
 // ranges with one atomic per warp, and writes them in order.
-__global__ void __launch_bounds__(kThreads) wf_gen(const WfParams W, uint32_t j, int cur) {
+__global__ void __launch_bounds__(kThreads, 8) wf_gen(const WfParams W, uint32_t j, int cur) {
     __shared__ WalkSmem wsm;
     __shared__ RunList runs_sm[kThreads / 32][32][2];   // per warp, per slot: segment job, first shadow job
     const RenderParams &P = W.R;
@@ -515,103 +518,141 @@ __device__ __forceinline__ float warp_sum(float x) {
     return x;
 }
 
-__global__ void __launch_bounds__(kThreads) wf_shade(const WfParams W, uint32_t j, int cur, int nxt) {
+// Warp-cooperative compositing of every live slot's segment samples and
+// shadow samples (Eqs. 10-11).  Writes, per slot, sum_i exp(-depth_i) alpha_i r_i
+// (to be scaled by T(p_j)) and the optical depth up to the stop; a negative
+// depth marks a path that fell below tau inside the segment.  Jobs that did not
+// fit the sample buffer are left to wf_shade.
+__global__ void __launch_bounds__(kThreads, 8) wf_composite(const WfParams W, int cur) {
     const RenderParams &P = W.R;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const uint32_t live = W.ctr[cur];
     const bool active = tid < live;
     const int nl = P.n_lights;
-    Counters C = {};
-    bool push = false;
-    uint32_t path = 0, prev = kNoHit;
-    V3 o = v3(0.f, 0.f, 0.f), d = v3(0.f, 0.f, 1.f);
-    float T[3] = {1.f, 1.f, 1.f};
-    Hit h;
-    h.t = INFINITY;
-    h.slot = -1;
-    h.id = kNoHit;
-    uint32_t rc = 0, r0 = 0;
+    uint32_t rc = kOverflow, r0 = 0;
+    float tmax = 0.f;
     bool diffuse = false;
-    SurfaceHit S;
     if (active) {
-        path = W.qpath[cur][tid];
-        const float4 qo = W.qo[cur][tid], qd = W.qd[cur][tid], qT = W.qT[cur][tid];
-        o = v3(qo.x, qo.y, qo.z);
-        d = v3(qd.x, qd.y, qd.z);
-        T[0] = qT.x;
-        T[1] = qT.y;
-        T[2] = qT.z;
-        h.t = W.hit_t[tid];
-        h.slot = W.hit_slot[tid];
-        h.id = W.hit_id[tid];
         rc = W.rcount[tid];
         r0 = W.rstart[tid];
-        if (h.id != kNoHit) {
-            S = surface_at(P, o, d, h);
-            diffuse = S.mat.kind == MRF_MAT_DIFFUSE;
-        }
+        const float4 qT = W.qT[cur][tid];
+        tmax = fmaxf(qT.x, fmaxf(qT.y, qT.z));
+        diffuse = __float_as_uint(W.hp[tid].w) != 0u;   // some light visible from a diffuse hit
     }
-    // warp-cooperative compositing of every lane's segment samples and shadow samples
-    float Lseg[3] = {0.f, 0.f, 0.f}, seg_depth = 0.f;
-    bool seg_stop = false;
-    float sh_depth[kWfMaxLights];
-#pragma unroll
-    for (int l = 0; l < kWfMaxLights; ++l) sh_depth[l] = 0.f;
     for (int src = 0; src < 32; ++src) {
-        const bool sact = __shfl_sync(0xffffffffu, (int)active, src);
-        if (!sact) continue;
+        if (!__shfl_sync(0xffffffffu, (int)active, src)) continue;
         const uint32_t src_rc = __shfl_sync(0xffffffffu, rc, src);
+        const uint32_t src_tid = tid - lane + src;
         if (src_rc != kOverflow) {
             const uint32_t src_r0 = __shfl_sync(0xffffffffu, r0, src);
-            const float tmax0 = __shfl_sync(0xffffffffu, fmaxf(T[0], fmaxf(T[1], T[2])), src);
+            const float tmax0 = __shfl_sync(0xffffffffu, tmax, src);
             float lr, lg, lb, dep;
             bool stp;
             warp_composite(W, src_r0, src_rc, tmax0, P.tau, lane, lr, lg, lb, dep, stp);
             lr = warp_sum(lr);
             lg = warp_sum(lg);
             lb = warp_sum(lb);
-            if (lane == src) {
-                Lseg[0] = lr;
-                Lseg[1] = lg;
-                Lseg[2] = lb;
-                seg_depth = dep;
-                seg_stop = stp;
-            }
+            if (lane == 0) W.comp[src_tid] = make_float4(lr, lg, lb, stp ? -dep - 1.f : dep);
         }
-        const bool sdiff = __shfl_sync(0xffffffffu, (int)diffuse, src);
-        if (!sdiff) continue;
-        const uint32_t src_tid = tid - lane + src;
+        if (!__shfl_sync(0xffffffffu, (int)diffuse, src)) continue;
         for (int l = 0; l < nl; ++l) {
             const size_t idx = (size_t)src_tid * nl + l;
-            const float4 wgt = W.sw[idx];
             const uint32_t sc = W.scount[idx];
-            if (wgt.w == 0.f || sc == kOverflow) continue;
+            if (W.sw[idx].w == 0.f || sc == kOverflow) continue;
             const uint32_t s0 = W.sstart[idx];
             float dep = 0.f;
             for (uint32_t i0 = lane; i0 < sc; i0 += 32) dep = fmaf(W.fout[s0 + i0].x, W.samp[s0 + i0].w, dep);
             dep = warp_sum(dep);
-            if (lane == src) sh_depth[l] = dep;
+            if (lane == 0) W.sdepth[idx] = dep;
         }
     }
-    if (active) {
+}
+
+// Jobs whose samples did not fit the sample buffer are marched in place here,
+// on the CUDA cores in FP32, producing the same per-slot results as
+// wf_composite (comp, sdepth).  Nothing to do when no job overflowed.
+__global__ void __launch_bounds__(kThreads) wf_overflow(const WfParams W, int cur) {
+    const RenderParams &P = W.R;
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= W.ctr[cur]) return;
+    const int nl = P.n_lights;
+    const bool rad = W.rcount[tid] == kOverflow;
+    bool any_shadow = false;
+    for (int l = 0; l < nl; ++l) any_shadow |= W.scount[(size_t)tid * nl + l] == kOverflow;
+    if (!rad && !any_shadow) return;
+    const float4 qo = W.qo[cur][tid], qd = W.qd[cur][tid], qT = W.qT[cur][tid];
+    const V3 o = v3(qo.x, qo.y, qo.z), d = v3(qd.x, qd.y, qd.z);
+    if (rad) {
+        // march with the path's own throughput so that the tau test is the same
+        float T[3] = {qT.x, qT.y, qT.z}, L[3] = {0.f, 0.f, 0.f};
+        bool stop = false;
+        Counters dummy = {};
+        march<true>(P, P.F.mlp, o, d, 0.f, W.hit_t[tid], T, L, stop, dummy);
+        const int c = (qT.x >= qT.y && qT.x >= qT.z) ? 0 : (qT.y >= qT.z ? 1 : 2);
+        const float T0[3] = {qT.x, qT.y, qT.z};
+        const float dep = T0[c] > 0.f ? logf(T0[c] / fmaxf(T[c], 1e-38f)) : 0.f;
+        W.comp[tid] = make_float4(T0[0] > 0.f ? L[0] / T0[0] : 0.f, T0[1] > 0.f ? L[1] / T0[1] : 0.f,
+                                  T0[2] > 0.f ? L[2] / T0[2] : 0.f, stop ? -dep - 1.f : dep);
+    }
+    if (any_shadow) {
+        Hit h;
+        h.t = W.hit_t[tid];
+        h.slot = W.hit_slot[tid];
+        h.id = W.hit_id[tid];
+        const SurfaceHit S = surface_at(P, o, d, h);
+        for (int l = 0; l < nl; ++l) {
+            const size_t idx = (size_t)tid * nl + l;
+            if (W.scount[idx] != kOverflow) continue;
+            const float4 sh = W.sdir[idx];
+            Counters dummy = {};
+            bool dstop = false;
+            W.sdepth[idx] = march<false>(P, P.F.mlp, S.p, v3(sh.x, sh.y, sh.z), 0.f, sh.w, nullptr, nullptr, dstop,
+                                         dummy);
+        }
+    }
+}
+
+// Per live slot: apply the composited segment (Eq. 11), add the next-event
+// terms, sample the BSDF (Eqs. 12-13), test termination and push survivors.
+__global__ void __launch_bounds__(kThreads) wf_shade(const WfParams W, uint32_t j, int cur, int nxt) {
+    const RenderParams &P = W.R;
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t live = W.ctr[cur];
+    const int nl = P.n_lights;
+    Counters C = {};
+    bool push = false;
+    uint32_t path = 0, prev = kNoHit;
+    V3 o = v3(0.f, 0.f, 0.f), d = v3(0.f, 0.f, 1.f);
+    float T[3] = {1.f, 1.f, 1.f};
+    if (tid < live) {
+        path = W.qpath[cur][tid];
         const uint32_t ray = path / P.spp, s = path % P.spp;
+        const float4 qo = W.qo[cur][tid], qd = W.qd[cur][tid], qT = W.qT[cur][tid];
+        o = v3(qo.x, qo.y, qo.z);
+        d = v3(qd.x, qd.y, qd.z);
+        T[0] = qT.x;
+        T[1] = qT.y;
+        T[2] = qT.z;
+        Hit h;
+        h.t = W.hit_t[tid];
+        h.slot = W.hit_slot[tid];
+        h.id = W.hit_id[tid];
         float4 acc = j == 1 ? make_float4(0.f, 0.f, 0.f, 0.f) : W.acc[path];
         float L[3] = {acc.x, acc.y, acc.z};
         const float T0 = T[0];
         bool stop = false;
-        if (rc == kOverflow) {
-            Counters dummy = {};
-            march<true>(P, P.F.mlp, o, d, 0.f, h.t, T, L, stop, dummy);
-        } else {
-            // Eqs. 10-11: L += T(p_j) * sum_i T_i alpha_i r_i, T' = T(p_j) exp(-depth)
-            const float att = expf(-seg_depth);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                L[k] = fmaf(T[k], Lseg[k], L[k]);
-                T[k] *= att;
-            }
-            stop = seg_stop;
+        {
+            // L += T(p_j) * sum_i T_i alpha_i r_i, T' = T(p_j) exp(-depth)
+            const float4 cp = W.comp[tid];
+            stop = cp.w < 0.f;
+            const float att = expf(-(stop ? -cp.w - 1.f : cp.w));
+            L[0] = fmaf(T[0], cp.x, L[0]);
+            L[1] = fmaf(T[1], cp.y, L[1]);
+            L[2] = fmaf(T[2], cp.z, L[2]);
+            T[0] *= att;
+            T[1] *= att;
+            T[2] *= att;
         }
         if (j == 1) acc.w = T0 > 0.f ? 1.f - T[0] / T0 : 0.f;
         ++C.seg;
@@ -623,23 +664,15 @@ __global__ void __launch_bounds__(kThreads) wf_shade(const WfParams W, uint32_t 
         bool end = stop || h.id == kNoHit;
         if (!end) {
             ++C.hits;
+            const SurfaceHit S = surface_at(P, o, d, h);
             float u[3];
             surface_uniforms(P, ray, s, j, u);
-            if (diffuse) {
+            if (S.mat.kind == MRF_MAT_DIFFUSE) {
                 for (int l = 0; l < nl; ++l) {
                     const size_t idx = (size_t)tid * nl + l;
                     const float4 wgt = W.sw[idx];
                     if (wgt.w == 0.f) continue;
-                    float depth = sh_depth[l];
-                    if (W.scount[idx] == kOverflow) {
-                        V3 wl;
-                        float D, D2, cosl;
-                        light_geometry(P, S, l, wl, D, D2, cosl);
-                        Counters dummy = {};
-                        bool dstop = false;
-                        depth = march<false>(P, P.F.mlp, S.p, wl, 0.f, D, nullptr, nullptr, dstop, dummy);
-                    }
-                    const float Tf = expf(-depth);
+                    const float Tf = expf(-W.sdepth[idx]);
                     L[0] = fmaf(T[0] * Tf, wgt.x, L[0]);
                     L[1] = fmaf(T[1] * Tf, wgt.y, L[1]);
                     L[2] = fmaf(T[2] * Tf, wgt.z, L[2]);
@@ -692,7 +725,7 @@ __global__ void __launch_bounds__(kThreads) wf_finalize(const float4 *__restrict
 // scratch layout
 struct Layout {
     size_t acc, qpath[2], qo[2], qd[2], qT[2], hit_t, hit_slot, hit_id, rstart, rcount, sstart, scount, sw, hp, sdir,
-        ctr, samp, fout, total;
+        comp, sdepth, ctr, samp, fout, total;
     uint32_t cap;
 };
 
@@ -722,6 +755,8 @@ Layout layout(uint32_t paths, int n_lights) {
     L.sw = take(16 * P * nl);
     L.hp = take(16 * P);
     L.sdir = take(16 * P * nl);
+    L.comp = take(16 * P);
+    L.sdepth = take(4 * P * nl);
     L.ctr = take(16);
     // sample capacity: 96 samples per path plus 4M (overflowing jobs are marched in place)
     const uint64_t cap = std::min<uint64_t>((uint64_t)P * 96 + (4u << 20), 0x7FFFFFFFull);
@@ -766,6 +801,8 @@ cudaError_t launch_render_wavefront(const RenderParams &P, void *scratch, size_t
     W.sw = reinterpret_cast<float4 *>(b + Lo.sw);
     W.hp = reinterpret_cast<float4 *>(b + Lo.hp);
     W.sdir = reinterpret_cast<float4 *>(b + Lo.sdir);
+    W.comp = reinterpret_cast<float4 *>(b + Lo.comp);
+    W.sdepth = reinterpret_cast<float *>(b + Lo.sdepth);
     W.ctr = reinterpret_cast<uint32_t *>(b + Lo.ctr);
     W.samp = reinterpret_cast<float4 *>(b + Lo.samp);
     W.fout = reinterpret_cast<float4 *>(b + Lo.fout);
@@ -796,6 +833,12 @@ cudaError_t launch_render_wavefront(const RenderParams &P, void *scratch, size_t
         timer_end(timer, s);
         if (e != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(W.ctr + nxt, 0, 4, s)) != cudaSuccess) return e;
+        timer_begin(timer, MRF_KERNEL_COMPOSITE, s);
+        wf_composite<<<grid, kThreads, 0, s>>>(W, cur);
+        timer_end(timer, s);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        wf_overflow<<<grid, kThreads, 0, s>>>(W, cur);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
         timer_begin(timer, MRF_KERNEL_SHADE, s);
         wf_shade<<<grid, kThreads, 0, s>>>(W, j, cur, nxt);
         timer_end(timer, s);
@@ -889,6 +932,8 @@ cudaError_t launch_render_wavefront_arena(const RenderParams &P, void *arena, si
     W.sw = reinterpret_cast<float4 *>(b + Lo.sw);
     W.hp = reinterpret_cast<float4 *>(b + Lo.hp);
     W.sdir = reinterpret_cast<float4 *>(b + Lo.sdir);
+    W.comp = reinterpret_cast<float4 *>(b + Lo.comp);
+    W.sdepth = reinterpret_cast<float *>(b + Lo.sdepth);
     W.ctr = reinterpret_cast<uint32_t *>(b + Lo.ctr);
     W.samp = reinterpret_cast<float4 *>(b + Lo.samp);
     W.fout = reinterpret_cast<float4 *>(b + Lo.fout);
@@ -913,6 +958,10 @@ cudaError_t launch_render_wavefront_arena(const RenderParams &P, void *arena, si
             e = launch_field_simt(F, reinterpret_cast<const float *>(W.samp), 4, W.ctr + 2, W.cap, W.fout, field_grid, s);
         if (e != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(W.ctr + nxt, 0, 4, s)) != cudaSuccess) return e;
+        wf_composite<<<grid, kThreads, 0, s>>>(W, cur);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        wf_overflow<<<grid, kThreads, 0, s>>>(W, cur);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
         wf_shade<<<grid, kThreads, 0, s>>>(W, j, cur, nxt);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

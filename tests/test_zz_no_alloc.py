@@ -104,3 +104,17 @@ def test_static_arena_rejects_oversize_and_host_output(env):
                                    host.ctypes.data, None, None)
     assert st == M.MRF_ERR_INVALID_ARG
     r.close()
+
+
+def test_static_arena_overflow_is_marched_in_place(env):
+    # 129,600 paths: the arena's sample buffer (~1.3M samples after the per-path
+    # state) is smaller than the first segment's ~7M samples, so most jobs take
+    # the in-place FP32 march; the image must still match mrf_render's.
+    torch, M = env
+    sc = S.config2(360, 360)
+    for prec, tol in ((M.MRF_PREC_FP32, RTOL_PIX), (M.MRF_PREC_BF16, 2e-3)):
+        r, ref, rec_ref, outs = _render_both(torch, M, sc, prec, calls=1)
+        img, rec, _ = outs[0]
+        assert _close(img, ref) <= tol
+        assert torch.equal(rec["segments"], rec_ref["segments"])
+        r.close()
