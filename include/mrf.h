@@ -107,6 +107,12 @@ typedef struct mrf_field_desc {
     uint32_t occ_res;              /* 0 = no occupancy grid (every sample evaluated) */
     const uint32_t *occ_bits;
     int32_t precision;
+    /* Rigid pose of the field: 3x4 row-major local-to-world [R | t] (NULL =
+     * identity).  The paper moves NeRF objects with the simulator's transform
+     * and queries them at t^-1 p (Sec. 3.2); the box, hash grid, occupancy and
+     * support above are given in the field's local frame.  R must be a rotation
+     * (orthonormal within 1e-4), else MRF_ERR_INVALID_ARG. */
+    const float *pose;
 } mrf_field_desc;
 
 /* Copies the description into device memory.  MRF_ERR_INVALID_ARG for an
@@ -117,7 +123,8 @@ void mrf_field_destroy(mrf_field *field);
 /* Changes the MLP precision of an existing HASHGRID field. */
 mrf_status mrf_field_set_precision(mrf_field *field, int32_t precision);
 
-/* Evaluates sigma and r at n points (n x 3, FP32) into out (n x 4: sigma, r, g, b)
+/* Evaluates sigma and r at n points (n x 3, FP32, in the field's local frame)
+ * into out (n x 4: sigma, r, g, b)
  * in the field's precision: FP32 on the CUDA cores, or for FP16/BF16 hash
  * fields the tensor-core kernel the wavefront engine uses.  points and out must
  * be device pointers.  For tests of the field alone (Eq. 7 / hash encoding / MLP). */
@@ -240,6 +247,12 @@ typedef struct mrf_stats {
 mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *bvh, const mrf_rays *rays,
                       uint32_t max_bounces, const mrf_render_opts *opts, float *out_hdr, void *stream,
                       mrf_stats *stats);
+
+/* Tone map psi of the paper (Eq. 14, applied after the path ends): per pixel
+ * and colour channel out = sRGB(clamp(exposure * L, 0, 1)), the transfer
+ * function of IEC 61966-2-1; alpha is copied.  in and out are n x 4 FP32
+ * device arrays (they may alias). */
+mrf_status mrf_tonemap(mrf_context *ctx, const float *in, uint32_t n, float exposure, float *out, void *stream);
 
 /* Allocation-free variant of mrf_render.  The paper has no counterpart: this
  * entry point exists for embedders that cannot call cudaMalloc while they

@@ -58,6 +58,8 @@ class OrcScene(C.Structure):
         ("max_bounces", C.c_uint32), ("spp", C.c_uint32), ("seed", C.c_uint64),
         ("steps_per_segment", C.c_uint32), ("dt", C.c_float), ("tau", C.c_float), ("tmin", C.c_float),
         ("margin_dist", C.c_double), ("margin_t", C.c_double), ("margin_fresnel", C.c_double),
+        ("field_pose", _fp),
+        ("n_views", C.c_uint32), ("view_cam", _fp), ("view_size", _u32p),
     ]
 
 
@@ -107,6 +109,8 @@ def lib():
         L.orc_render.argtypes = [C.POINTER(OrcScene), _u32p, C.c_uint32, _dp, _u32p, _u32p, _dp, _u32p, _u64p,
                                  C.c_int]
         L.orc_num_threads.restype = C.c_int
+        L.orc_tonemap.restype = C.c_double
+        L.orc_tonemap.argtypes = [C.c_double, C.c_double]
         _lib = L
     return _lib
 
@@ -183,6 +187,14 @@ class OracleScene:
         s.max_bounces, s.spp, s.seed = o.max_bounces, o.spp, o.seed
         s.steps_per_segment, s.dt, s.tau, s.tmin = o.steps_per_segment, o.dt, o.tau, o.tmin
         s.margin_dist, s.margin_t, s.margin_fresnel = margin_dist, margin_t, margin_fresnel
+        if getattr(f, "pose", None) is not None:
+            s.field_pose = _ptr(arr(f.pose, np.float32), _fp)
+        views = getattr(scene, "cameras", None)
+        if views:
+            s.n_views = len(views)
+            s.view_cam = _ptr(arr(np.array([[*v.pos, *v.look_at, *v.up, v.vfov_deg] for v in views], np.float32),
+                                  np.float32), _fp)
+            s.view_size = _ptr(arr(np.array([[v.width, v.height] for v in views], np.uint32), np.uint32), _u32p)
         self.s = s
         self._keep = keep
 
@@ -316,3 +328,10 @@ def sample_cosine(n, u1, u2):
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def tonemap(L, exposure=1.0):
+    """psi applied channel-wise to an array of linear radiance values."""
+    f = lib().orc_tonemap
+    a = np.asarray(L, np.float64)
+    return np.vectorize(lambda v: f(float(v), float(exposure)))(a)

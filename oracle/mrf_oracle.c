@@ -95,6 +95,13 @@ typedef struct {
     float dt, tau, tmin;
 
     double margin_dist, margin_t, margin_fresnel;
+    const float *field_pose;   /* 3x4 local-to-world [R | t] of the field (rigid), NULL = identity */
+    /* several pinhole views in one batch: view k has camera view_cam[10k..10k+9]
+     * (pos, look_at, up, vfov) and size view_size[2k], view_size[2k+1]; rays are
+     * numbered view by view, row-major within a view */
+    uint32_t n_views;
+    const float *view_cam;
+    const uint32_t *view_size;
 } orc_scene;
 
 /* per-thread counters: segments, shadow rays, nominal samples, samples with
@@ -160,6 +167,19 @@ static void draw3(const orc_scene *sc, uint64_t ray, uint64_t s, uint64_t seg, d
 /* Pinhole camera (Algorithm 1: p_0 and w_0 from the pixel and the camera
  * centre): the ray leaves the camera centre through the pixel centre.
  * Pixel index = y * width + x, row y = 0 at the top of the image. */
+static void pinhole(const float *cpos, const float *clook, const float *cup, double vfov, uint32_t W, uint32_t H,
+                    uint32_t pix, double o[3], double d[3]) {
+    v3 pos = fv(cpos), f = unit(sub(fv(clook), pos));
+    v3 r = unit(cross(f, fv(cup))), u = cross(r, f);
+    double th = tan(0.5 * vfov * M_PI / 180.0), aspect = (double)W / H;
+    uint32_t px = pix % W, py = pix / W;
+    double sx = (2.0 * (px + 0.5) / W - 1.0) * th * aspect;
+    double sy = (1.0 - 2.0 * (py + 0.5) / H) * th;
+    v3 dir = unit(add(f, add(scl(r, sx), scl(u, sy))));
+    o[0] = pos.x; o[1] = pos.y; o[2] = pos.z;
+    d[0] = dir.x; d[1] = dir.y; d[2] = dir.z;
+}
+
 void orc_camera_ray(const orc_scene *sc, uint32_t pix, double o[3], double d[3]) {
     if (sc->n_rays) {
         for (int i = 0; i < 3; ++i) { o[i] = sc->ray_o[3 * pix + i]; d[i] = sc->ray_d[3 * pix + i]; }
@@ -167,15 +187,17 @@ void orc_camera_ray(const orc_scene *sc, uint32_t pix, double o[3], double d[3])
         d[0] = dd.x; d[1] = dd.y; d[2] = dd.z;
         return;
     }
-    v3 pos = fv(sc->cam_pos), f = unit(sub(fv(sc->cam_look), pos));
-    v3 r = unit(cross(f, fv(sc->cam_up))), u = cross(r, f);
-    double th = tan(0.5 * sc->vfov_deg * M_PI / 180.0), aspect = (double)sc->width / sc->height;
-    uint32_t px = pix % sc->width, py = pix / sc->width;
-    double sx = (2.0 * (px + 0.5) / sc->width - 1.0) * th * aspect;
-    double sy = (1.0 - 2.0 * (py + 0.5) / sc->height) * th;
-    v3 dir = unit(add(f, add(scl(r, sx), scl(u, sy))));
-    o[0] = pos.x; o[1] = pos.y; o[2] = pos.z;
-    d[0] = dir.x; d[1] = dir.y; d[2] = dir.z;
+    if (sc->n_views) {
+        uint32_t k = 0, off = 0;
+        while (k + 1 < sc->n_views && pix >= off + sc->view_size[2 * k] * sc->view_size[2 * k + 1]) {
+            off += sc->view_size[2 * k] * sc->view_size[2 * k + 1];
+            ++k;
+        }
+        const float *c = sc->view_cam + 10 * k;
+        pinhole(c, c + 3, c + 6, c[9], sc->view_size[2 * k], sc->view_size[2 * k + 1], pix - off, o, d);
+        return;
+    }
+    pinhole(sc->cam_pos, sc->cam_look, sc->cam_up, sc->vfov_deg, sc->width, sc->height, pix, o, d);
 }
 
 /* ---------------------------------------------------------------- field */
@@ -308,13 +330,32 @@ int orc_box_interval(const orc_scene *sc, const double o[3], const double d[3], 
     return hi > lo;
 }
 
+/* A field that moves as a rigid body (Sec. 3.2: the simulator's homogeneous
+ * transform t of a NeRF object; queries use t^-1 p).  With the pose [R | t]
+ * (local to world), a world ray (o, d) is the local ray (R^T (o - t), R^T d);
+ * R is orthonormal, so ray parameters and lengths are unchanged. */
+static void to_field_frame(const orc_scene *sc, const double o[3], const double d[3], double lo[3], double ld[3]) {
+    if (!sc->field_pose) {
+        for (int a = 0; a < 3; ++a) { lo[a] = o[a]; ld[a] = d[a]; }
+        return;
+    }
+    const float *M = sc->field_pose;
+    double q[3] = {o[0] - M[3], o[1] - M[7], o[2] - M[11]};
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = M[0 + a] * q[0] + M[4 + a] * q[1] + M[8 + a] * q[2];
+        ld[a] = M[0 + a] * d[0] + M[4 + a] * d[1] + M[8 + a] * d[2];
+    }
+}
+
 /* ---------------------------------------------------------------- march */
 /* Quadrature of Eqs. 10-11 over [a, b] of the ray, with the shadow mask m = 1:
  *   alpha_i = 1 - exp(-sigma_i delta_i); L += T alpha_i r_i; T *= exp(-sigma_i delta_i).
  * T is the RGB path throughput (it carries T(p_j) into the segment).  Returns
  * 1 if the path ended inside the march because max(T) fell below tau. */
-static int march(const orc_scene *sc, const double o[3], const double d[3], double a, double b, double T[3],
+static int march(const orc_scene *sc, const double ow[3], const double dw[3], double a, double b, double T[3],
                  double L[3], uint64_t *cnt, uint32_t *flags) {
+    double o[3], d[3];
+    to_field_frame(sc, ow, dw, o, d);
     double tb0, tb1;
     if (!orc_box_interval(sc, o, d, &tb0, &tb1)) return 0;
     double t0 = a > tb0 ? a : tb0, t1 = b < tb1 ? b : tb1;
@@ -344,8 +385,10 @@ static int march(const orc_scene *sc, const double o[3], const double d[3], doub
 }
 
 /* Field transmittance exp(-int sigma) over [a, b] by the same quadrature. */
-double orc_transmittance(const orc_scene *sc, const double o[3], const double d[3], double a, double b,
+double orc_transmittance(const orc_scene *sc, const double ow[3], const double dw[3], double a, double b,
                          uint64_t *cnt) {
+    double o[3], d[3];
+    to_field_frame(sc, ow, dw, o, d);
     double tb0, tb1;
     uint64_t dummy[C_N] = {0};
     if (!cnt) cnt = dummy;
@@ -642,6 +685,16 @@ int orc_render(const orc_scene *sc, const uint32_t *ids, uint32_t n_ids, double 
     }
     if (out_counts) for (int c = 0; c < C_N; ++c) out_counts[c] = tot[c];
     return 0;
+}
+
+/* Tone map psi (Eq. 14 of the paper: linear radiance to sRGB for display,
+ * applied after the path ends): scale by the exposure, clamp to [0, 1], then
+ * the sRGB transfer function of IEC 61966-2-1. */
+double orc_tonemap(double L, double exposure) {
+    double c = L * exposure;
+    if (c < 0.0) c = 0.0;
+    if (c > 1.0) c = 1.0;
+    return c <= 0.0031308 ? 12.92 * c : 1.055 * pow(c, 1.0 / 2.4) - 0.055;
 }
 
 int orc_num_threads(void) {

@@ -232,6 +232,30 @@ static mrf_status field_create_impl(mrf_context *ctx, const mrf_field_desc *D, m
     F.precision = D->precision;
     if (D->precision < MRF_PREC_FP32 || D->precision > MRF_PREC_BF16)
         return fail(MRF_ERR_INVALID_ARG, "mrf_field_create: unknown precision %d", D->precision);
+    F.has_pose = 0;
+    if (D->pose) {
+        std::vector<float> M;
+        mrf_status st0;
+        if ((st0 = fetch(M, D->pose, 12))) return st0;
+        // R must be orthonormal: R^T R = I within 1e-4
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double dotab = 0.0;
+                for (int k = 0; k < 3; ++k) dotab += (double)M[4 * k + a] * M[4 * k + b];
+                if (std::fabs(dotab - (a == b ? 1.0 : 0.0)) > 1e-4)
+                    return fail(MRF_ERR_INVALID_ARG, "mrf_field_create: pose rotation is not orthonormal");
+            }
+        // world-to-local: [R^T | -R^T t]
+        for (int a = 0; a < 3; ++a) {
+            double tt = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                F.to_local[4 * a + k] = M[4 * k + a];
+                tt += (double)M[4 * k + a] * M[4 * k + 3];
+            }
+            F.to_local[4 * a + 3] = (float)-tt;
+        }
+        F.has_pose = 1;
+    }
     if (D->kind == MRF_FIELD_CONST) {
         F.const_sigma = D->const_sigma;
         for (int k = 0; k < 3; ++k) F.const_rgb[k] = D->const_rgb[k];
@@ -927,5 +951,17 @@ mrf_status mrf_render_static(mrf_context *ctx, const mrf_field *field, const mrf
             return fail(MRF_ERR_TIMEOUT, "mrf_render_static: a kernel gave up (status 0x%x)", st_word);
         }
     }
+    return MRF_OK;
+}
+
+mrf_status mrf_tonemap(mrf_context *ctx, const float *in, uint32_t n, float exposure, float *out, void *stream) {
+    if (!ctx || (n && (!in || !out))) return fail(MRF_ERR_INVALID_ARG, "mrf_tonemap: NULL argument");
+    if (!(exposure >= 0.f)) return fail(MRF_ERR_INVALID_ARG, "mrf_tonemap: exposure must be >= 0");
+    if (n == 0) return MRF_OK;
+    if (!is_device_ptr(in) || !is_device_ptr(out))
+        return fail(MRF_ERR_INVALID_ARG, "mrf_tonemap: in and out must be device memory");
+    CUDA_TRY(launch_tonemap(reinterpret_cast<const float4 *>(in), n, exposure, reinterpret_cast<float4 *>(out),
+                            (cudaStream_t)stream),
+             "mrf_tonemap: launch");
     return MRF_OK;
 }

@@ -47,6 +47,9 @@ struct FieldDev {
     float occ_coarse_scale[3];  // occ_coarse_res / extent
     float occ_cell[3], occ_coarse_cell[3];  // cell widths (extent / resolution)
     int precision;
+    // rigid pose: world-to-local [R^T | -R^T t] applied to every marched ray
+    int has_pose;
+    float to_local[12];
 };
 
 // BVH node: 4 x float4 = both children's boxes + (left, right, left_count, right_count).
@@ -129,6 +132,7 @@ cudaError_t launch_field_tc(const FieldDev &F, bool bf16, const float *pts, int 
 int field_tc_blocks_per_sm();
 cudaError_t launch_cast(const BvhDev &B, const float *o, const float *d, const uint32_t *skip, uint32_t n, float tmin,
                         float *out_t, uint32_t *out_tri, unsigned long long *stats, cudaStream_t s);
+cudaError_t launch_tonemap(const float4 *in, uint32_t n, float exposure, float4 *out, cudaStream_t s);
 // bvh_refit.cu
 cudaError_t launch_bvh_refit(float4 *nodes, int n_nodes, float4 *tris, int n_tris, const uint32_t *tri_order,
                              const uint32_t *tri_idx, const float *verts, const int *parent, int *counters,

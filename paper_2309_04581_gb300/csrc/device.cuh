@@ -73,6 +73,19 @@ __device__ __forceinline__ bool box_interval(const float lo[3], const float hi[3
     return b > a;
 }
 
+// World ray to the field's local frame (rigid pose; identity when absent):
+// o' = R^T (o - t), d' = R^T d.  Ray parameters and lengths are unchanged.
+__device__ __forceinline__ void to_field_frame(const FieldDev &F, V3 &o, V3 &d) {
+    if (!F.has_pose) return;
+    const float *M = F.to_local;
+    const V3 q = o, e = d;
+    o = v3(fmaf(M[0], q.x, fmaf(M[1], q.y, fmaf(M[2], q.z, M[3]))),
+           fmaf(M[4], q.x, fmaf(M[5], q.y, fmaf(M[6], q.z, M[7]))),
+           fmaf(M[8], q.x, fmaf(M[9], q.y, fmaf(M[10], q.z, M[11]))));
+    d = v3(fmaf(M[0], e.x, fmaf(M[1], e.y, M[2] * e.z)), fmaf(M[4], e.x, fmaf(M[5], e.y, M[6] * e.z)),
+           fmaf(M[8], e.x, fmaf(M[9], e.y, M[10] * e.z)));
+}
+
 // ------------------------------------------------------------- field: analytic
 __device__ __forceinline__ bool inside_field_box(const FieldDev &F, V3 p) {
     return p.x >= F.lo[0] && p.x <= F.hi[0] && p.y >= F.lo[1] && p.y <= F.hi[1] && p.z >= F.lo[2] &&

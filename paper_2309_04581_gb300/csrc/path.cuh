@@ -61,6 +61,7 @@ template <bool radiance>
 __device__ float march(const RenderParams &P, const float *w, V3 o, V3 d, float a, float b, float T[3], float L[3],
                        bool &stop, Counters &C) {
     const FieldDev &F = P.F;
+    to_field_frame(F, o, d);
     float tb0, tb1;
     if (!box_interval(F.lo, F.hi, o, d, tb0, tb1)) return 0.f;
     const float t0 = fmaxf(a, tb0), t1 = fminf(b, tb1);

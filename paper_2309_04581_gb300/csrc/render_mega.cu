@@ -159,6 +159,27 @@ cudaError_t launch_field_simt(const FieldDev &F, const float *pts, int stride, c
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------- tone map
+// psi: sRGB transfer function (IEC 61966-2-1) of the clamped, exposed radiance
+__global__ void __launch_bounds__(256) tonemap_kernel(const float4 *__restrict__ in, uint32_t n, float exposure,
+                                                      float4 *__restrict__ out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 v = in[i];
+    float c[3] = {v.x, v.y, v.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float x = fminf(fmaxf(c[k] * exposure, 0.f), 1.f);
+        c[k] = x <= 0.0031308f ? 12.92f * x : 1.055f * powf(x, 1.f / 2.4f) - 0.055f;
+    }
+    out[i] = make_float4(c[0], c[1], c[2], v.w);
+}
+
+cudaError_t launch_tonemap(const float4 *in, uint32_t n, float exposure, float4 *out, cudaStream_t s) {
+    tonemap_kernel<<<(n + 255) / 256, 256, 0, s>>>(in, n, exposure, out);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------- ray cast
 __global__ void __launch_bounds__(128) cast_kernel(const BvhDev B, const float *o, const float *d, const uint32_t *skip,
                                                    uint32_t n, float tmin, float *out_t, uint32_t *out_tri,

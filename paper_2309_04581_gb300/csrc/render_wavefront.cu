@@ -194,6 +194,7 @@ __device__ __noinline__ uint32_t warp_walk(const RenderParams &P, const WalkCtx 
                                            RunList *runs) {
     Segment S;
     if (runs && lane == 0) runs->n = 0;
+    to_field_frame(P.F, o, d);
     if (!segment_of(P, o, d, a, b, S)) return 0;
     if (!out && lane == 0) nominal += (unsigned long long)S.n;
     const FieldDev &F = P.F;
@@ -279,6 +280,7 @@ __device__ __noinline__ uint32_t warp_walk(const RenderParams &P, const WalkCtx 
 __device__ void write_runs(const RenderParams &P, V3 o, V3 d, float a, float b, const RunList &R, float4 *out,
                            uint32_t limit, int lane) {
     Segment S;
+    to_field_frame(P.F, o, d);
     if (!segment_of(P, o, d, a, b, S)) return;
     uint32_t k = 0;
     for (int r = 0; r < R.n; ++r) {

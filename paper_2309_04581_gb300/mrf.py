@@ -34,7 +34,8 @@ NO_HIT = 0xFFFFFFFF
 # every entry point declared in include/mrf.h
 EXPORTS = ("mrf_context_create", "mrf_context_destroy", "mrf_last_error", "mrf_version", "mrf_field_create",
            "mrf_field_destroy", "mrf_field_set_precision", "mrf_field_query", "mrf_bvh_build", "mrf_bvh_refit",
-           "mrf_bvh_destroy", "mrf_cast", "mrf_materials_set", "mrf_lights_set", "mrf_render", "mrf_render_static")
+           "mrf_bvh_destroy", "mrf_cast", "mrf_materials_set", "mrf_lights_set", "mrf_render", "mrf_render_static",
+           "mrf_tonemap")
 
 _fp = C.POINTER(C.c_float)
 _u32p = C.POINTER(C.c_uint32)
@@ -52,7 +53,7 @@ class mrf_field_desc(C.Structure):
         ("level_res", _u32p), ("table", _u16p), ("mlp_width", C.c_uint32),
         ("w1", _fp), ("b1", _fp), ("w2", _fp), ("b2", _fp), ("w3", _fp), ("b3", _fp),
         ("n_support", C.c_uint32), ("support_center", _fp), ("support_radius", _fp),
-        ("occ_res", C.c_uint32), ("occ_bits", _u32p), ("precision", C.c_int32),
+        ("occ_res", C.c_uint32), ("occ_bits", _u32p), ("precision", C.c_int32), ("pose", _fp),
     ]
 
 
@@ -124,6 +125,7 @@ def lib():
                                      _vp, C.POINTER(mrf_stats)]
             L.mrf_render_static.argtypes = [_vp, _vp, _vp, C.POINTER(mrf_rays), C.c_uint32, C.POINTER(mrf_render_opts),
                                             _vp, _vp, C.POINTER(mrf_stats)]
+            L.mrf_tonemap.argtypes = [_vp, _vp, C.c_uint32, C.c_float, _vp, _vp]
             L.mrf_context_destroy.argtypes = [_vp]
             L.mrf_field_destroy.argtypes = [_vp]
             L.mrf_bvh_destroy.argtypes = [_vp]
@@ -228,6 +230,8 @@ def field_desc(field: S.Field, precision: int = MRF_PREC_FP32):
     d.const_sigma = field.const_sigma
     d.const_rgb[:] = [float(x) for x in field.const_rgb]
     d.precision = precision
+    if getattr(field, "pose", None) is not None:
+        d.pose = _p(arr(field.pose, np.float32), _fp)
     if field.blob_center is not None:
         d.n_blobs = field.blob_center.shape[0]
         d.blob_center = _p(arr(field.blob_center, np.float32), _fp)
@@ -355,3 +359,7 @@ class Renderer:
             for k, name in enumerate(KERNEL_NAMES):
                 timing[name] = (float(ms[k]), int(cnt[k]))
         return out, (st.as_dict() if st is not None else None)
+
+
+def mrf_tonemap(ctx: int, in_ptr: int, n: int, exposure: float, out_ptr: int, stream: int = 0):
+    check(lib().mrf_tonemap(ctx, in_ptr, n, exposure, out_ptr, stream))

@@ -103,6 +103,8 @@ class Field:
     support_radius: Optional[np.ndarray] = None  # (S,)
     occ_res: int = 0
     occ_bits: Optional[np.ndarray] = None      # (occ_res^3 / 32,) uint32, cell x + R*(y + R*z)
+    # rigid pose of the field, 3x4 local-to-world [R | t] f32 (None = identity)
+    pose: Optional[np.ndarray] = None
 
 
 @dataclass
@@ -152,11 +154,14 @@ class Scene:
     opts: RenderOpts
     ray_o: Optional[np.ndarray] = None   # explicit rays (n,3) f32; overrides the camera
     ray_d: Optional[np.ndarray] = None
+    cameras: Optional[List[Camera]] = None  # several views in one batch; overrides `camera`
 
     @property
     def n_rays(self) -> int:
         if self.ray_o is not None:
             return int(self.ray_o.shape[0])
+        if self.cameras:
+            return sum(c.width * c.height for c in self.cameras)
         return self.camera.width * self.camera.height
 
 
@@ -411,3 +416,35 @@ def strided_pixels(width: int, height: int, stride: int, offset: int = 0) -> np.
     ys = np.arange(offset % stride, height, stride)
     xs = np.arange(offset % stride, width, stride)
     return np.ascontiguousarray((ys[:, None] * width + xs[None, :]).reshape(-1).astype(np.uint32))
+
+
+def rigid_pose(axis, angle_rad: float, translation) -> np.ndarray:
+    """3x4 local-to-world [R | t] (Rodrigues rotation about `axis`, then translation), in f32."""
+    k = np.asarray(axis, np.float64)
+    k = k / np.linalg.norm(k)
+    K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    R = np.eye(3) + math.sin(angle_rad) * K + (1 - math.cos(angle_rad)) * K @ K
+    return f32(np.concatenate([R, np.asarray(translation, np.float64).reshape(3, 1)], axis=1))
+
+
+def orbit_views(n: int, sizes, radius: float = 1.6, height: float = 0.3, vfov: float = 45.0):
+    """n cameras on a circle around the origin looking at it, with the given (width, height) sizes."""
+    cams = []
+    for k in range(n):
+        a = 2 * math.pi * k / n
+        w, h = sizes[k % len(sizes)]
+        cams.append(Camera(pos=f32([radius * math.sin(a), height, radius * math.cos(a)]), look_at=f32([0, 0, 0]),
+                           up=f32([0, 1, 0]), vfov_deg=vfov, width=int(w), height=int(h)))
+    return cams
+
+
+def seeded_view_sizes(n: int, purpose: int = 0, lo=(256, 256), hi=(1920, 1080)):
+    """n view sizes with log-uniform pixel counts between lo and hi (aspect interpolated)."""
+    rng = _rng(3, purpose)
+    out = []
+    for _ in range(n):
+        t = rng.uniform(0, 1)
+        w = int(round(math.exp(math.log(lo[0]) + t * (math.log(hi[0]) - math.log(lo[0])))))
+        h = int(round(math.exp(math.log(lo[1]) + t * (math.log(hi[1]) - math.log(lo[1])))))
+        out.append((w, h))
+    return out

@@ -219,3 +219,46 @@ def test_invariants_on_config_scenes(orc):
             k = res["segments"][i, 0]
             assert np.all(res["tri"][i, 0, k:] == orc.NO_HIT)
             assert np.all(res["tri"][i, 0, :k - 1] != orc.NO_HIT)
+
+
+def test_tonemap_srgb_transfer(orc):
+    # psi: clamp(exposure * L, 0, 1) then the sRGB transfer function; pinned by its
+    # end points, the continuity of its two branches at 0.0031308 and the inverse
+    # transfer function of the same standard
+    assert orc.tonemap(0.0) == 0.0 and orc.tonemap(1.0) == pytest.approx(1.0, abs=1e-15)
+    assert orc.tonemap(5.0) == pytest.approx(1.0, abs=1e-15) and orc.tonemap(-1.0) == 0.0
+    lo, hi = orc.tonemap(0.0031308), orc.tonemap(0.0031308 * (1 + 1e-9))
+    assert abs(lo - hi) < 1e-6
+    for c in [0.001, 0.01, 0.2, 0.5, 0.9]:
+        v = float(orc.tonemap(c))
+        lin = v / 12.92 if v <= 0.04045 else ((v + 0.055) / 1.055) ** 2.4
+        assert lin == pytest.approx(c, rel=1e-9)
+    assert orc.tonemap(0.25, 2.0) == pytest.approx(float(orc.tonemap(0.5)), rel=1e-15)
+
+
+def test_field_pose_is_a_change_of_frame(orc):
+    # Rendering a field moved by a rigid pose T from camera C equals rendering the
+    # unmoved field from the camera moved by T^-1 (no meshes: only the field moves).
+    base = S.config2(24, 24)
+    base.mesh = S.empty_mesh()
+    base.materials = []
+    T = S.rigid_pose([0.3, 1.0, -0.2], 0.6, [0.05, -0.1, 0.08])
+    R, t = T[:, :3].astype(np.float64), T[:, 3].astype(np.float64)
+    moved = S.config2(24, 24)
+    moved.mesh = S.empty_mesh()
+    moved.materials = []
+    moved.field.pose = T
+    cam = base.camera
+    inv = lambda x: R.T @ (np.asarray(x, np.float64) - t)
+    base.camera = S.Camera(pos=S.f32(inv(cam.pos)), look_at=S.f32(inv(cam.look_at)),
+                           up=S.f32(R.T @ np.asarray(cam.up, np.float64)), vfov_deg=cam.vfov_deg,
+                           width=cam.width, height=cam.height)
+    a = orc.render(moved)["rgba"]
+    b = orc.render(base)["rgba"]
+    peak = np.abs(b[:, :3]).max()
+    assert peak > 0.05
+    assert np.abs(a - b).max() <= 2e-4 * peak + 1e-7
+    # and the pose matters: the same camera without the pose sees something else
+    moved.field.pose = None
+    c = orc.render(moved)["rgba"]
+    assert np.abs(a - c).max() > 0.05 * peak
