@@ -188,13 +188,25 @@ typedef struct mrf_camera {
     uint32_t width, height;
 } mrf_camera;
 
-/* The primary rays: a camera (count = width * height, ray index = y * width + x)
- * or explicit FP32 origins / directions (count x 3, host or device). */
+/* The primary rays: a camera (count = width * height, ray index = y * width + x),
+ * several cameras rendered as one batch, or explicit FP32 origins / directions
+ * (count x 3, host or device).
+ *
+ * Several views (n_cameras > 1): `camera` points to n_cameras host records and
+ * the rays are numbered view by view, each view row-major, so view k starts at
+ * ray sum_{j<k} width_j * height_j and out_hdr holds the images one after the
+ * other.  The views may differ in size, position and field of view; all of
+ * them go through one launch sequence.  Alg. 1 renders every pixel
+ * independently, so batching views changes nothing but the ray index, which is
+ * also the index the random numbers are drawn with.  n_cameras 0 or 1 means
+ * one camera; at most 65,536 views.  mrf_render only: mrf_render_static takes
+ * one camera or explicit rays. */
 typedef struct mrf_rays {
     const mrf_camera *camera;
     const float *origins, *dirs;
     uint32_t count;
     uint32_t spp;                  /* paths per ray (>= 1) */
+    uint32_t n_cameras;            /* records behind `camera` (0 = 1) */
 } mrf_rays;
 
 /* MEGAKERNEL: one thread runs a whole path (FP32 field only).  WAVEFRONT: one

@@ -621,6 +621,42 @@ static mrf_status ensure_scratch(mrf_context *ctx, size_t bytes) {
     return MRF_OK;
 }
 
+// Pinhole basis of one camera, built in FP64 and rounded once to FP32.
+// Returns NULL, or what is wrong with the camera.
+static const char *camera_view(const mrf_camera &c, ViewDev &v) {
+    if (c.width == 0 || c.height == 0 || !(c.vfov_deg > 0.f && c.vfov_deg < 180.f)) return "bad camera";
+    double f[3], up[3], r[3], u[3];
+    for (int k = 0; k < 3; ++k) {
+        f[k] = (double)c.look_at[k] - c.pos[k];
+        up[k] = c.up[k];
+    }
+    const double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    if (!(fl > 0)) return "camera looks at itself";
+    for (double &x : f) x /= fl;
+    r[0] = f[1] * up[2] - f[2] * up[1];
+    r[1] = f[2] * up[0] - f[0] * up[2];
+    r[2] = f[0] * up[1] - f[1] * up[0];
+    const double rl = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    if (!(rl > 0)) return "camera up is parallel to the view direction";
+    for (double &x : r) x /= rl;
+    u[0] = r[1] * f[2] - r[2] * f[1];
+    u[1] = r[2] * f[0] - r[0] * f[2];
+    u[2] = r[0] * f[1] - r[1] * f[0];
+    for (int k = 0; k < 3; ++k) {
+        v.pos[k] = c.pos[k];
+        v.f[k] = (float)f[k];
+        v.r[k] = (float)r[k];
+        v.u[k] = (float)u[k];
+    }
+    v.tan_half = (float)std::tan(0.5 * (double)c.vfov_deg * M_PI / 180.0);
+    v.aspect = (float)((double)c.width / (double)c.height);
+    v.W = c.width;
+    v.H = c.height;
+    v.offset = 0;
+    v.pad = 0;
+    return nullptr;
+}
+
 mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *bvh, const mrf_rays *rays,
                       uint32_t max_bounces, const mrf_render_opts *opts, float *out_hdr, void *stream,
                       mrf_stats *stats) {
@@ -662,38 +698,41 @@ mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *b
     uint32_t count;
     size_t scratch_need = 0;
     const bool host_rays = !rays->camera && !is_device_ptr(rays->origins);
-    if (rays->camera) {
+    const uint32_t n_views = rays->camera && rays->n_cameras > 1 ? rays->n_cameras : 0;
+    std::vector<ViewDev> views;
+    if (n_views) {
+        // several views: a table in device scratch, searched by ray index
+        if (n_views > 65536u) return fail(MRF_ERR_INVALID_ARG, "mrf_render: more than 65536 cameras");
+        if (is_device_ptr(rays->camera)) return fail(MRF_ERR_INVALID_ARG, "mrf_render: camera records must be host memory");
+        views.resize(n_views);
+        uint64_t total = 0;
+        for (uint32_t k = 0; k < n_views; ++k) {
+            if (const char *why = camera_view(rays->camera[k], views[k]))
+                return fail(MRF_ERR_INVALID_ARG, "mrf_render: camera %u: %s", k, why);
+            views[k].offset = (uint32_t)std::min<uint64_t>(total, 0xFFFFFFFFull);
+            total += (uint64_t)views[k].W * views[k].H;
+        }
+        if (total > 0xFFFFFFFFull / 4) return fail(MRF_ERR_INVALID_ARG, "mrf_render: views too large");
+        count = (uint32_t)total;
+        scratch_need = sizeof(ViewDev) * (size_t)n_views;
+    } else if (rays->camera) {
         const mrf_camera &c = *rays->camera;
-        if (c.width == 0 || c.height == 0 || !(c.vfov_deg > 0.f && c.vfov_deg < 180.f))
-            return fail(MRF_ERR_INVALID_ARG, "mrf_render: bad camera");
+        ViewDev v;
+        if (const char *why = camera_view(c, v)) return fail(MRF_ERR_INVALID_ARG, "mrf_render: %s", why);
         const uint64_t cnt = (uint64_t)c.width * c.height;
         if (cnt > 0xFFFFFFFFull / 4) return fail(MRF_ERR_INVALID_ARG, "mrf_render: image too large");
         count = (uint32_t)cnt;
-        double f[3], up[3], r[3], u[3];
-        for (int k = 0; k < 3; ++k) { f[k] = (double)c.look_at[k] - c.pos[k]; up[k] = c.up[k]; }
-        double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
-        if (!(fl > 0)) return fail(MRF_ERR_INVALID_ARG, "mrf_render: camera looks at itself");
-        for (double &x : f) x /= fl;
-        r[0] = f[1] * up[2] - f[2] * up[1];
-        r[1] = f[2] * up[0] - f[0] * up[2];
-        r[2] = f[0] * up[1] - f[1] * up[0];
-        double rl = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-        if (!(rl > 0)) return fail(MRF_ERR_INVALID_ARG, "mrf_render: camera up is parallel to the view direction");
-        for (double &x : r) x /= rl;
-        u[0] = r[1] * f[2] - r[2] * f[1];
-        u[1] = r[2] * f[0] - r[0] * f[2];
-        u[2] = r[0] * f[1] - r[1] * f[0];
         P.use_camera = 1;
         for (int k = 0; k < 3; ++k) {
-            P.cam_pos[k] = c.pos[k];
-            P.cam_f[k] = (float)f[k];
-            P.cam_r[k] = (float)r[k];
-            P.cam_u[k] = (float)u[k];
+            P.cam_pos[k] = v.pos[k];
+            P.cam_f[k] = v.f[k];
+            P.cam_r[k] = v.r[k];
+            P.cam_u[k] = v.u[k];
         }
-        P.tan_half = (float)std::tan(0.5 * (double)c.vfov_deg * M_PI / 180.0);
-        P.aspect = (float)((double)c.width / (double)c.height);
-        P.W = c.width;
-        P.H = c.height;
+        P.tan_half = v.tan_half;
+        P.aspect = v.aspect;
+        P.W = v.W;
+        P.H = v.H;
     } else {
         if (!rays->origins || !rays->dirs || rays->count == 0)
             return fail(MRF_ERR_INVALID_ARG, "mrf_render: explicit rays need origins, dirs and count > 0");
@@ -735,6 +774,12 @@ mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *b
     mrf_status st;
     if (scratch_need && (st = ensure_scratch(ctx, scratch_need))) return st;
     char *scr = (char *)ctx->scratch;
+    if (n_views) {
+        CUDA_TRY(cudaMemcpyAsync(scr, views.data(), sizeof(ViewDev) * (size_t)n_views, cudaMemcpyHostToDevice, s),
+                 "mrf_render: camera table upload");
+        P.views = (const ViewDev *)scr;
+        P.n_views = n_views;
+    }
     if (host_rays) {
         float *o = (float *)scr, *d = o + 3 * (size_t)count;
         CUDA_TRY(cudaMemcpyAsync(o, rays->origins, 3 * sizeof(float) * (size_t)count, cudaMemcpyDefault, s), "ray upload");
@@ -860,6 +905,8 @@ mrf_status mrf_render_static(mrf_context *ctx, const mrf_field *field, const mrf
     P.lights = ctx->lights;
     P.n_lights = ctx->n_lights;
     uint32_t count;
+    if (rays->camera && rays->n_cameras > 1)
+        return fail(MRF_ERR_UNSUPPORTED, "mrf_render_static: one camera or explicit rays; several views go to mrf_render");
     if (rays->camera) {
         const mrf_camera &c = *rays->camera;
         if (c.width == 0 || c.height == 0 || !(c.vfov_deg > 0.f && c.vfov_deg < 180.f))

@@ -78,6 +78,14 @@ enum StatIndex {
     ST_STATUS, ST_COUNT
 };
 
+// One pinhole view of a multi-view batch: orthonormal basis in FP32 (built in
+// FP64 on the host) and the index of its first ray.
+struct ViewDev {
+    float pos[3], f[3], r[3], u[3];
+    float tan_half, aspect;
+    uint32_t W, H, offset, pad;
+};
+
 struct RenderParams {
     FieldDev F;
     BvhDev B;
@@ -89,6 +97,8 @@ struct RenderParams {
     float cam_pos[3], cam_f[3], cam_r[3], cam_u[3];
     float tan_half, aspect;
     uint32_t W, H;
+    const ViewDev *views;        // multi-view batch (device), n_views > 1; else NULL
+    uint32_t n_views;
     const float *ray_o, *ray_d;
     uint32_t count, spp, max_bounces;
     uint64_t seed;

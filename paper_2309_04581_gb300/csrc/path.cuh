@@ -147,8 +147,31 @@ __device__ __forceinline__ V3 sample_cosine(V3 n, float u1, float u2) {
     return t1 * (r * c) + t2 * (r * s) + n * z;
 }
 
+// Pinhole ray through the centre of pixel (px, py) of a W x H image (row 0 at the top).
+__device__ __forceinline__ V3 pinhole_dir(V3 f, V3 r, V3 u, float tan_half, float aspect, uint32_t W, uint32_t H,
+                                          uint32_t px, uint32_t py) {
+    float sx = (2.f * ((float)px + 0.5f) / (float)W - 1.f) * tan_half * aspect;
+    float sy = (1.f - 2.f * ((float)py + 0.5f) / (float)H) * tan_half;
+    return normalize(f + r * sx + u * sy);
+}
+
 __device__ __forceinline__ void primary_ray(const RenderParams &P, uint32_t ray, V3 &o, V3 &d) {
-    if (P.use_camera) {
+    if (P.n_views) {
+        // the view holding this ray: the last one whose first ray is <= ray
+        uint32_t lo = 0, hi = P.n_views - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (__ldg(&P.views[mid].offset) <= ray) lo = mid;
+            else hi = mid - 1;
+        }
+        const ViewDev &v = P.views[lo];
+        const uint32_t pix = ray - __ldg(&v.offset), W = __ldg(&v.W);
+        d = pinhole_dir(v3(__ldg(&v.f[0]), __ldg(&v.f[1]), __ldg(&v.f[2])),
+                        v3(__ldg(&v.r[0]), __ldg(&v.r[1]), __ldg(&v.r[2])),
+                        v3(__ldg(&v.u[0]), __ldg(&v.u[1]), __ldg(&v.u[2])), __ldg(&v.tan_half), __ldg(&v.aspect), W,
+                        __ldg(&v.H), pix % W, pix / W);
+        o = v3(__ldg(&v.pos[0]), __ldg(&v.pos[1]), __ldg(&v.pos[2]));
+    } else if (P.use_camera) {
         uint32_t px = ray % P.W, py = ray / P.W;
         float sx = (2.f * ((float)px + 0.5f) / (float)P.W - 1.f) * P.tan_half * P.aspect;
         float sy = (1.f - 2.f * ((float)py + 0.5f) / (float)P.H) * P.tan_half;

@@ -72,7 +72,7 @@ class mrf_camera(C.Structure):
 
 class mrf_rays(C.Structure):
     _fields_ = [("camera", C.POINTER(mrf_camera)), ("origins", _vp), ("dirs", _vp), ("count", C.c_uint32),
-                ("spp", C.c_uint32)]
+                ("spp", C.c_uint32), ("n_cameras", C.c_uint32)]
 
 
 class mrf_render_opts(C.Structure):
@@ -288,6 +288,9 @@ class Renderer:
             mrf_materials_set(self.ctx, scene.materials)
         mrf_lights_set(self.ctx, scene.lights)
         self.cam = camera_struct(scene.camera)
+        self.views = None
+        if scene.cameras:
+            self.views = (mrf_camera * len(scene.cameras))(*[camera_struct(c) for c in scene.cameras])
         self._rays_dev = None
         if scene.ray_o is not None:
             dev = torch.device("cuda", device)
@@ -308,7 +311,11 @@ class Renderer:
 
     def rays_struct(self) -> mrf_rays:
         r = mrf_rays()
-        if self._rays_dev is None:
+        if self.views is not None:
+            r.camera = C.cast(self.views, C.POINTER(mrf_camera))
+            r.n_cameras = len(self.views)
+            r.count = self.scene.n_rays
+        elif self._rays_dev is None:
             r.camera = C.pointer(self.cam)
             r.count = self.scene.n_rays
         else:

@@ -262,3 +262,51 @@ def test_field_pose_is_a_change_of_frame(orc):
     moved.field.pose = None
     c = orc.render(moved)["rgba"]
     assert np.abs(a - c).max() > 0.05 * peak
+
+
+def test_multi_view_batch_is_the_views_one_after_another(orc):
+    # Alg. 1 treats every pixel alone: a batch of views (rays numbered view by
+    # view) renders each view exactly as that view rendered alone, whenever the
+    # paths draw no random numbers (mirror-only scene); view sizes are uneven
+    # and include a 1x1 view, so a wrong view offset or stride fails.
+    sizes = [(9, 5), (1, 1), (12, 7), (4, 11)]
+    views = S.orbit_views(4, sizes, radius=1.4, height=0.25, vfov=40.0)
+    batch = S.config1()
+    batch.cameras = views
+    got = orc.render(batch)
+    assert batch.n_rays == sum(w * h for w, h in sizes) and got["rgba"].shape[0] == batch.n_rays
+    off = 0
+    images = []
+    for cam in views:
+        one = S.config1()
+        one.camera = cam
+        ref = orc.render(one)
+        n = cam.width * cam.height
+        assert np.array_equal(got["rgba"][off:off + n], ref["rgba"])
+        assert np.array_equal(got["segments"][off:off + n], ref["segments"])
+        images.append(ref["rgba"])
+        off += n
+    # the views see different things (the test would pass vacuously otherwise)
+    assert not np.allclose(images[0][:4], images[2][:4])
+    # a sampled id set indexes the same global numbering
+    ids = np.array([0, 44, 45, 46, batch.n_rays - 1], np.uint32)
+    sub = orc.render(batch, ids)
+    assert np.array_equal(sub["rgba"], got["rgba"][ids])
+
+
+def test_multi_view_random_numbers_follow_the_global_ray_index(orc):
+    # with random draws (glass and diffuse), view 0 of a batch starts at ray 0
+    # and equals its render alone; a later view draws with its global ray index,
+    # so it equals the render alone only where no path drew anything
+    sizes = [(10, 10), (10, 10)]
+    views = S.orbit_views(2, sizes)
+    views[1] = views[0]
+    batch = S.config2(10, 10)
+    batch.cameras = views
+    got = orc.render(batch)
+    one = S.config2(10, 10)
+    one.camera = views[0]
+    ref = orc.render(one)
+    assert np.array_equal(got["rgba"][:100], ref["rgba"])
+    same = np.all(got["rgba"][100:] == ref["rgba"], axis=1)
+    assert not same.all()
