@@ -166,14 +166,35 @@ typedef struct mrf_material {
     float rgb[3];
     float ior;
 } mrf_material;
-/* Point lights with RGB intensity I: a diffuse hit at distance D receives
- * (albedo / pi) cos I / D^2 times visibility and field transmittance
- * (the shadow rays of Sec. 3.1, "Shadow rays"). */
-enum { MRF_LIGHT_POINT = 0 };
+/* Lights for the shadow rays of Sec. 3.1 ("Shadow rays"), cast at diffuse hits.
+ *
+ * POINT: position `pos`, RGB intensity I in `intensity`.  A diffuse hit at
+ * distance D receives (albedo / pi) cos I / D^2 times the mesh visibility and
+ * the field transmittance exp(-int sigma) along the shadow ray (Eq. 10).
+ *
+ * AREA: the triangle (pos, v1, v2) of an estimated emitter mesh (Sec. 3.1,
+ * "Estimating light sources": the faces left after pruning the emission
+ * texture), emitting RGB radiance Le (`intensity`) from its front side, whose
+ * normal is (v1 - pos) x (v2 - pos).  Each diffuse hit casts `samples` shadow
+ * rays (1..64) to points drawn uniformly on the triangle and adds
+ *   (albedo / pi) Le A / samples * sum_s V_s T_s cos_x cos_y / D_s^2,
+ * with A the triangle's area and cos_y the cosine at the emitter.  The points
+ * come from Philox4x64-10 with counter (ray, spp, segment, 1 + q), key
+ * (seed, 0), where q counts the area-light samples of the hit in light order;
+ * uniforms are the top 24 bits of words 0 and 1, and the point has
+ * barycentrics (1 - sqrt(u0), u1 sqrt(u0), rest) (Shirley and Turk's warp).
+ * Emitters are seen only by shadow rays: camera and bounce rays pass through
+ * them (the field already holds the scene's appearance).
+ *
+ * One diffuse hit casts at most 64 shadow rays in all (point lights count
+ * one each) on the wavefront engine. */
+enum { MRF_LIGHT_POINT = 0, MRF_LIGHT_AREA = 1 };
 typedef struct mrf_light {
     int32_t kind;
-    float pos[3];
-    float intensity[3];
+    float pos[3];          /* POINT: position; AREA: vertex v0 */
+    float intensity[3];    /* POINT: intensity I; AREA: radiance Le of the front side */
+    float v1[3], v2[3];    /* AREA only */
+    uint32_t samples;      /* AREA only: shadow rays per diffuse hit */
 } mrf_light;
 /* Replace the context's material / light tables (host or device arrays, n <= 65535). */
 mrf_status mrf_materials_set(mrf_context *ctx, const mrf_material *mats, uint32_t n);
@@ -273,7 +294,7 @@ mrf_status mrf_tonemap(mrf_context *ctx, const float *in, uint32_t n, float expo
  * an allocation may cause.  It runs the wavefront engine out of a file-scope
  * device arena of 64 MiB that every GPU loading the library holds until the
  * process exits, and it allocates no device or pinned memory itself.
- *  - Limits: rays->count * rays->spp <= 131072 paths and at most 8 lights;
+ *  - Limits: rays->count * rays->spp <= 131072 paths and at most 8 shadow rays per hit;
  *    larger requests return MRF_ERR_INVALID_ARG (use mrf_render).  Samples that
  *    do not fit the arena's sample buffer are marched in place, so results do
  *    not depend on the arena size.

@@ -5,9 +5,11 @@ and by the CPU-baseline leg of ``bench.py``.  The CUDA library never imports,
 links or calls anything in this directory.
 
 The arithmetic lives in ``mrf_oracle.c`` (plain C, double precision, written
-step by step from the paper's Algorithm 1 and Eqs. 3, 10-13).  This module only
-compiles it with gcc and marshals numpy arrays from a ``scenes.Scene`` into the
-C struct ``orc_scene``.
+step by step from the paper's Algorithm 1 and Eqs. 3, 10-13) and in
+``shadow_net.c`` (the learned shadow-transmittance surrogate: encoding,
+network, loss, back-propagation and Adam, in FP64).  This module only compiles
+them with gcc and marshals numpy arrays from a ``scenes.Scene`` into the C
+struct ``orc_scene``.
 
 Parity status of each function is stated in the design doc; every function here is
 pinned by a ``-m "not gpu"`` test except the whole-image composition, which the
@@ -24,6 +26,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mrf_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "shadow_net.c")]
 _LIB_PATH = os.path.join(_HERE, "liborc.so")
 _lock = threading.Lock()
 _lib = None
@@ -60,16 +63,18 @@ class OrcScene(C.Structure):
         ("margin_dist", C.c_double), ("margin_t", C.c_double), ("margin_fresnel", C.c_double),
         ("field_pose", _fp),
         ("n_views", C.c_uint32), ("view_cam", _fp), ("view_size", _u32p),
+        ("light_kind", _i32p), ("light_v1", _fp), ("light_v2", _fp), ("light_samples", _u32p),
     ]
 
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (OpenMP, strict IEEE double, no contraction)."""
     with _lock:
-        if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        if force or not os.path.exists(_LIB_PATH) or any(os.path.getmtime(_LIB_PATH) < os.path.getmtime(f)
+                                                         for f in _SRCS):
             tmp = _LIB_PATH + f".{os.getpid()}.tmp"
             cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-                   "-fno-fast-math", "-Wall", "-Wno-unused-function", "-o", tmp, _SRC, "-lm"]
+                   "-fno-fast-math", "-Wall", "-Wno-unused-function", "-o", tmp, *_SRCS, "-lm"]
             subprocess.run(cmd, check=True)
             os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -111,6 +116,17 @@ def lib():
         L.orc_num_threads.restype = C.c_int
         L.orc_tonemap.restype = C.c_double
         L.orc_tonemap.argtypes = [C.c_double, C.c_double]
+        L.orc_shadow_pairs.argtypes = [C.POINTER(OrcScene), C.c_uint64, C.c_uint64, C.c_uint32, _dp]
+        L.orc_sh16.argtypes = [_dp, _dp]
+        L.orc_snet_n_params.restype = C.c_uint64
+        L.orc_snet_n_params.argtypes = [C.POINTER(OrcSnet)]
+        L.orc_snet_encode.argtypes = [C.POINTER(OrcSnet), _dp, _dp, _dp]
+        L.orc_snet_forward.restype = C.c_double
+        L.orc_snet_forward.argtypes = [C.POINTER(OrcSnet), _dp, _dp]
+        L.orc_snet_loss_grad.restype = C.c_double
+        L.orc_snet_loss_grad.argtypes = [C.POINTER(OrcSnet), _dp, _dp, C.c_uint32, _dp]
+        L.orc_adam_step.argtypes = [_dp, _dp, _dp, _dp, C.c_uint64, C.c_uint32, C.c_double, C.c_double, C.c_double,
+                                    C.c_double]
         _lib = L
     return _lib
 
@@ -183,6 +199,13 @@ class OracleScene:
         s.n_lights = len(lights)
         s.light_pos = _ptr(arr(np.array([x.pos for x in lights] or [(0, 0, 0)], np.float32), np.float32), _fp)
         s.light_I = _ptr(arr(np.array([x.intensity for x in lights] or [(0, 0, 0)], np.float32), np.float32), _fp)
+        if any(x.kind != 0 for x in lights):
+            s.light_kind = _ptr(arr(np.array([x.kind for x in lights], np.int32), np.int32), _i32p)
+            s.light_v1 = _ptr(arr(np.array([x.v1 if x.v1 is not None else (0, 0, 0) for x in lights], np.float32),
+                                  np.float32), _fp)
+            s.light_v2 = _ptr(arr(np.array([x.v2 if x.v2 is not None else (0, 0, 0) for x in lights], np.float32),
+                                  np.float32), _fp)
+            s.light_samples = _ptr(arr(np.array([x.samples for x in lights], np.uint32), np.uint32), _u32p)
         o = scene.opts
         s.max_bounces, s.spp, s.seed = o.max_bounces, o.spp, o.seed
         s.steps_per_segment, s.dt, s.tau, s.tmin = o.steps_per_segment, o.dt, o.tau, o.tmin
@@ -335,3 +358,72 @@ def tonemap(L, exposure=1.0):
     f = lib().orc_tonemap
     a = np.asarray(L, np.float64)
     return np.vectorize(lambda v: f(float(v), float(exposure)))(a)
+
+
+# ---- the shadow-transmittance surrogate (shadow_net.c) ----------------------
+class OrcSnet(C.Structure):
+    _fields_ = [("n_levels", C.c_uint32), ("log2_T", C.c_uint32), ("level_res", _u32p),
+                ("aabb_min", C.c_float * 3), ("aabb_max", C.c_float * 3), ("field_pose", _fp), ("params", _dp)]
+
+
+class OracleShadowNet:
+    """The surrogate's hyper-parameters and an FP64 copy of a flat parameter vector."""
+
+    def __init__(self, level_res, log2_T, params, aabb_min=(-0.5, -0.5, -0.5), aabb_max=(0.5, 0.5, 0.5),
+                 pose=None):
+        self.level_res = np.ascontiguousarray(np.asarray(level_res, np.uint32))
+        self.params = np.ascontiguousarray(np.asarray(params, np.float64))
+        self.pose = None if pose is None else np.ascontiguousarray(np.asarray(pose, np.float32))
+        s = OrcSnet()
+        s.n_levels = self.level_res.shape[0]
+        s.log2_T = int(log2_T)
+        s.level_res = _ptr(self.level_res, _u32p)
+        s.aabb_min[:] = [float(x) for x in aabb_min]
+        s.aabb_max[:] = [float(x) for x in aabb_max]
+        s.field_pose = _ptr(self.pose, _fp) if self.pose is not None else None
+        s.params = _ptr(self.params, _dp)
+        self.s = s
+        assert lib().orc_snet_n_params(C.byref(s)) == self.params.shape[0], "parameter count"
+
+    @property
+    def ref(self):
+        return C.byref(self.s)
+
+    def encode(self, p, w):
+        x = np.zeros(32)
+        lib().orc_snet_encode(self.ref, _ptr(_d(p), _dp), _ptr(_d(w), _dp), _ptr(x, _dp))
+        return x
+
+    def forward(self, p, w) -> float:
+        return lib().orc_snet_forward(self.ref, _ptr(_d(p), _dp), _ptr(_d(w), _dp))
+
+    def loss_grad(self, pw, y, grad=True):
+        pw = np.ascontiguousarray(np.asarray(pw, np.float64).reshape(-1, 6))
+        y = np.ascontiguousarray(np.asarray(y, np.float64).reshape(-1))
+        g = np.zeros_like(self.params) if grad else None
+        loss = lib().orc_snet_loss_grad(self.ref, _ptr(pw, _dp), _ptr(y, _dp), pw.shape[0], _ptr(g, _dp))
+        return loss, g
+
+
+def snet_n_params(n_levels: int, log2_T: int, width: int = 64, n_in: int = 32) -> int:
+    return n_levels * (1 << log2_T) * 2 + width * n_in + width + 2 * (width * width + width) + width + 1
+
+
+def sh16(w):
+    out = np.zeros(16)
+    lib().orc_sh16(_ptr(_d(w), _dp), _ptr(out, _dp))
+    return out
+
+
+def adam_step(theta, m, v, g, t, lr, b1=0.9, b2=0.99, eps=1e-15):
+    """In place on the FP64 arrays theta, m, v."""
+    lib().orc_adam_step(_ptr(theta, _dp), _ptr(m, _dp), _ptr(v, _dp), _ptr(np.ascontiguousarray(g, np.float64), _dp),
+                        theta.shape[0], int(t), float(lr), float(b1), float(b2), float(eps))
+
+
+def shadow_pairs(scene, seed: int, first: int, n: int) -> np.ndarray:
+    """n x 8 (point, direction, distance, FP64 marched transmittance)."""
+    os_ = OracleScene(scene)
+    out = np.zeros((n, 8), np.float64)
+    lib().orc_shadow_pairs(os_.ref, int(seed), int(first), int(n), _ptr(out, _dp))
+    return out

@@ -21,8 +21,10 @@
  *    or a fixed step dt whose last interval is clipped at the segment end;
  *    alpha_i = 1 - exp(-sigma_i delta_i), L += T_i alpha_i r_i, T *= exp(-sigma_i delta_i).
  *  - shadow mask m(p_t) = 1 in the march; shadow rays are cast at diffuse hits
- *    toward point lights (next-event estimation), visibility from any mesh and
- *    transmittance exp(-int sigma) from the same field march.
+ *    toward point lights and uniformly drawn points of triangle area lights
+ *    (next-event estimation), visibility from any mesh and transmittance
+ *    exp(-int sigma) from the same field march; area lights emit from their
+ *    front side and are seen by shadow rays only.
  *  - BSDFs: perfect mirror (T *= rho); smooth dielectric with the exact
  *    unpolarised Fresnel term choosing reflection or Snell refraction (T kept);
  *    Lambertian with cosine-weighted sampling (T *= albedo).
@@ -49,6 +51,7 @@
 
 enum { ORC_FIELD_CONST = 0, ORC_FIELD_GAUSS = 1, ORC_FIELD_HASH = 2 };
 enum { ORC_MIRROR = 0, ORC_GLASS = 1, ORC_DIFFUSE = 2 };
+enum { ORC_LIGHT_POINT = 0, ORC_LIGHT_AREA = 1 };
 enum {
     ORC_FLAG_EDGE = 1,      /* near-edge candidate or t tie in a closest-hit cast */
     ORC_FLAG_SHADOW = 2,    /* near-edge candidate in a shadow any-hit test */
@@ -102,6 +105,13 @@ typedef struct {
     uint32_t n_views;
     const float *view_cam;
     const uint32_t *view_size;
+    /* light kinds (NULL = every light is a point light).  An area light l is the
+     * triangle (light_pos[l], light_v1[l], light_v2[l]) emitting radiance
+     * light_I[l] from its front side (normal (v1 - v0) x (v2 - v0)), sampled
+     * light_samples[l] times per diffuse hit */
+    const int32_t *light_kind;
+    const float *light_v1, *light_v2;
+    const uint32_t *light_samples;
 } orc_scene;
 
 /* per-thread counters: segments, shadow rays, nominal samples, samples with
@@ -161,6 +171,14 @@ static void draw3(const orc_scene *sc, uint64_t ray, uint64_t s, uint64_t seg, d
     uint64_t ctr[4] = {ray, s, seg, 0}, key[2] = {sc->seed, 0}, out[4];
     orc_philox4x64(ctr, key, out);
     u[0] = u24(out[0]); u[1] = u24(out[1]); u[2] = u24(out[2]);
+}
+
+/* two uniforms for shadow sample q of the surface event ending segment `seg`
+ * (counter word 3 = 1 + q, so they never meet the surface-event draw) */
+static void draw_shadow(const orc_scene *sc, uint64_t ray, uint64_t s, uint64_t seg, uint64_t q, double u[2]) {
+    uint64_t ctr[4] = {ray, s, seg, 1 + q}, key[2] = {sc->seed, 0}, out[4];
+    orc_philox4x64(ctr, key, out);
+    u[0] = u24(out[0]); u[1] = u24(out[1]);
 }
 
 /* ---------------------------------------------------------------- camera */
@@ -563,6 +581,41 @@ static inline double maxc(const double T[3]) {
     return T[2] > m ? T[2] : m;
 }
 
+/* Next-event estimate of one area light (a triangle of the pruned emissive
+ * mesh, Sec. 3.1 "Estimating light sources"): N points y_s drawn uniformly on
+ * the triangle (square-root barycentric warp of Shirley and Turk), each a
+ * shadow ray; the estimator of the light's reflected radiance is
+ *   (albedo / pi) Le A / N  sum_s V_s T_s cos_x cos_y / |y_s - p|^2,
+ * with cos_x at the surface normal facing the ray, cos_y at the light's front
+ * normal, V the mesh visibility and T the field transmittance of Eq. 10. */
+static void area_light_nee(const orc_scene *sc, uint32_t l, uint32_t ray, uint32_t s, uint32_t j, uint32_t *q,
+                           const double p[3], const double nf[3], uint32_t hit, const float *rgb, const double T[3],
+                           double L[3], uint32_t *flags, uint64_t *cnt) {
+    v3 a = fv(sc->light_pos + 3 * l), b = fv(sc->light_v1 + 3 * l), c = fv(sc->light_v2 + 3 * l);
+    v3 cr = cross(sub(b, a), sub(c, a));
+    double A = 0.5 * sqrt(dot(cr, cr));
+    v3 nl = unit(cr);
+    uint32_t N = sc->light_samples ? sc->light_samples[l] : 1;
+    if (N == 0) N = 1;
+    for (uint32_t k = 0; k < N; ++k, ++*q) {
+        double u[2];
+        draw_shadow(sc, ray, s, j, *q, u);
+        double su = sqrt(u[0]), b0 = 1.0 - su, b1 = u[1] * su, b2 = 1.0 - b0 - b1;
+        v3 y = add(add(scl(a, b0), scl(b, b1)), scl(c, b2));
+        double w[3] = {y.x - p[0], y.y - p[1], y.z - p[2]};
+        double D2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2], D = sqrt(D2);
+        for (int e = 0; e < 3; ++e) w[e] /= D;
+        double cosx = nf[0] * w[0] + nf[1] * w[1] + nf[2] * w[2];
+        double cosy = -(nl.x * w[0] + nl.y * w[1] + nl.z * w[2]);
+        if (cosx <= 0.0 || cosy <= 0.0) continue;
+        cnt[C_SHADOW]++;
+        if (occluded(sc, p, w, hit, D, flags)) continue;
+        double Tf = orc_transmittance(sc, p, w, 0.0, D, cnt);
+        for (int e = 0; e < 3; ++e)
+            L[e] += T[e] * (rgb[e] / M_PI) * sc->light_I[3 * l + e] * A / N * cosx * cosy / D2 * Tf;
+    }
+}
+
 /* ---------------------------------------------------------- one path */
 /* Algorithm 1 for one (ray, spp) pair. */
 static void trace_path(const orc_scene *sc, uint32_t ray, uint32_t s, double L[3], double *alpha0,
@@ -613,9 +666,14 @@ static void trace_path(const orc_scene *sc, uint32_t ray, uint32_t s, double L[3
             if (u[0] < F) orc_reflect(d, n, nd);
             else orc_refract(d, nf, ei / et, nd);
         } else {
-            /* next-event estimation toward each point light (the shadow rays
-             * of Sec. 3.1, "Shadow rays" and Algorithm 1) */
+            /* next-event estimation toward each light (the shadow rays of
+             * Sec. 3.1, "Shadow rays" and Algorithm 1) */
+            uint32_t q = 0;   /* shadow-sample index over all area lights of this hit */
             for (uint32_t l = 0; l < sc->n_lights; ++l) {
+                if (sc->light_kind && sc->light_kind[l] == ORC_LIGHT_AREA) {
+                    area_light_nee(sc, l, ray, s, j, &q, p, nf, hit, rgb, T, L, flags, cnt);
+                    continue;
+                }
                 double w[3], D2 = 0.0;
                 for (int a = 0; a < 3; ++a) { w[a] = sc->light_pos[3 * l + a] - p[a]; D2 += w[a] * w[a]; }
                 double D = sqrt(D2);
@@ -685,6 +743,53 @@ int orc_render(const orc_scene *sc, const uint32_t *ids, uint32_t n_ids, double 
     }
     if (out_counts) for (int c = 0; c < C_N; ++c) out_counts[c] = tot[c];
     return 0;
+}
+
+/* Training pairs of the shadow-transmittance surrogate: pair i is a point p
+ * uniform in the field box (uniforms u0..u2 of Philox4x64-10 with counter
+ * (i, 0, 0, 0) and key (seed, 0x736861646F77), mapped through the field pose),
+ * light l = floor(u3 n_lights) (clamped), a point y on it (the point light's
+ * position, or for an area light the barycentrics (1 - sqrt(a), b sqrt(a),
+ * rest) from the first two uniforms of counter (i, 1, 0, 0)), the direction
+ * w = (y - p)/|y - p|, D = |y - p| and the label exp(-int_0^D sigma), the
+ * transmittance the shadow ray of Sec. 3.1 marches.  out: n x 8 values
+ * (p, w, D, label). */
+void orc_shadow_pairs(const orc_scene *sc, uint64_t seed, uint64_t first, uint32_t n, double *out) {
+    const uint64_t key[2] = {seed, 0x736861646F77ull};
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < (int64_t)n; ++k) {
+        const uint64_t i = first + (uint64_t)k;
+        uint64_t c0[4] = {i, 0, 0, 0}, r0[4], c1[4] = {i, 1, 0, 0}, r1[4];
+        orc_philox4x64(c0, key, r0);
+        orc_philox4x64(c1, key, r1);
+        double pl[3], p[3];
+        for (int a = 0; a < 3; ++a) pl[a] = sc->aabb_min[a] + u24(r0[a]) * ((double)sc->aabb_max[a] - sc->aabb_min[a]);
+        if (sc->field_pose) {
+            const float *M = sc->field_pose;
+            for (int a = 0; a < 3; ++a) p[a] = M[4 * a] * pl[0] + M[4 * a + 1] * pl[1] + M[4 * a + 2] * pl[2] + M[4 * a + 3];
+        } else {
+            for (int a = 0; a < 3; ++a) p[a] = pl[a];
+        }
+        uint32_t l = (uint32_t)(u24(r0[3]) * sc->n_lights);
+        if (l >= sc->n_lights) l = sc->n_lights - 1;
+        v3 y;
+        if (sc->light_kind && sc->light_kind[l] == ORC_LIGHT_AREA) {
+            v3 a = fv(sc->light_pos + 3 * l), b = fv(sc->light_v1 + 3 * l), c = fv(sc->light_v2 + 3 * l);
+            double su = sqrt(u24(r1[0])), b0 = 1.0 - su, b1 = u24(r1[1]) * su, b2 = 1.0 - b0 - b1;
+            y = add(add(scl(a, b0), scl(b, b1)), scl(c, b2));
+        } else {
+            y = fv(sc->light_pos + 3 * l);
+        }
+        double w[3] = {y.x - p[0], y.y - p[1], y.z - p[2]};
+        double D = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+        for (int a = 0; a < 3; ++a) w[a] /= D;
+        uint64_t cnt[C_N] = {0};
+        double T = orc_transmittance(sc, p, w, 0.0, D, cnt);
+        double *o = out + 8 * (uint64_t)k;
+        o[0] = p[0]; o[1] = p[1]; o[2] = p[2];
+        o[3] = w[0]; o[4] = w[1]; o[5] = w[2];
+        o[6] = D; o[7] = T;
+    }
 }
 
 /* Tone map psi (Eq. 14 of the paper: linear radiance to sRGB for display,

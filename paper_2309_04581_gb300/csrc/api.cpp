@@ -58,6 +58,7 @@ struct mrf_context {
     int n_mats = 0;
     LightDev *lights = nullptr;
     int n_lights = 0;
+    int n_shadow = 0;   // shadow rays per diffuse hit over all lights
     unsigned long long *stats = nullptr;
     unsigned *status = nullptr;  // device status word: non-zero after a kernel gave up
     KernelTimer *timer = nullptr;
@@ -589,22 +590,54 @@ mrf_status mrf_lights_set(mrf_context *ctx, const mrf_light *lights, uint32_t n)
     mrf_status st;
     if ((st = fetch(h, lights, n))) return st;
     std::vector<LightDev> d(n);
+    uint32_t q = 0, slots = 0;
     for (uint32_t i = 0; i < n; ++i) {
-        if (h[i].kind != MRF_LIGHT_POINT) return fail(MRF_ERR_UNSUPPORTED, "mrf_lights_set: only point lights");
+        LightDev &L = d[i];
+        std::memset(&L, 0, sizeof(L));
         for (int k = 0; k < 3; ++k) {
-            d[i].pos[k] = h[i].pos[k];
-            d[i].I[k] = h[i].intensity[k];
+            L.pos[k] = h[i].pos[k];
+            L.I[k] = h[i].intensity[k];
         }
+        L.kind = h[i].kind;
+        L.slot0 = slots;
+        if (h[i].kind == MRF_LIGHT_POINT) {
+            L.samples = 1;
+        } else if (h[i].kind == MRF_LIGHT_AREA) {
+            if (h[i].samples < 1 || h[i].samples > 64)
+                return fail(MRF_ERR_INVALID_ARG, "mrf_lights_set: light %u: samples must be 1..64", i);
+            double e1[3], e2[3], c[3];
+            for (int k = 0; k < 3; ++k) {
+                L.v1[k] = h[i].v1[k];
+                L.v2[k] = h[i].v2[k];
+                e1[k] = (double)h[i].v1[k] - h[i].pos[k];
+                e2[k] = (double)h[i].v2[k] - h[i].pos[k];
+            }
+            c[0] = e1[1] * e2[2] - e1[2] * e2[1];
+            c[1] = e1[2] * e2[0] - e1[0] * e2[2];
+            c[2] = e1[0] * e2[1] - e1[1] * e2[0];
+            const double len = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+            if (!(len > 0)) return fail(MRF_ERR_INVALID_ARG, "mrf_lights_set: light %u: degenerate triangle", i);
+            for (int k = 0; k < 3; ++k) L.n[k] = (float)(c[k] / len);
+            L.area = (float)(0.5 * len);
+            L.samples = h[i].samples;
+            L.q0 = q;
+            q += L.samples;
+        } else {
+            return fail(MRF_ERR_INVALID_ARG, "mrf_lights_set: light %u: unknown kind %d", i, h[i].kind);
+        }
+        slots += L.samples;
     }
     CUDA_TRY(cudaSetDevice(ctx->device), "mrf_lights_set: cudaSetDevice");
     cudaFree(ctx->lights);
     ctx->lights = nullptr;
     ctx->n_lights = 0;
+    ctx->n_shadow = 0;
     if (n) {
         if ((st = dev_alloc(&ctx->lights, n, "lights"))) return st;
         CUDA_TRY(cudaMemcpy(ctx->lights, d.data(), n * sizeof(LightDev), cudaMemcpyHostToDevice), "lights upload");
     }
     ctx->n_lights = (int)n;
+    ctx->n_shadow = (int)slots;
     return MRF_OK;
 }
 
@@ -695,6 +728,7 @@ mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *b
     P.n_mats = ctx->n_mats;
     P.lights = ctx->lights;
     P.n_lights = ctx->n_lights;
+    P.n_shadow = ctx->n_shadow;
     uint32_t count;
     size_t scratch_need = 0;
     const bool host_rays = !rays->camera && !is_device_ptr(rays->origins);
@@ -764,8 +798,8 @@ mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *b
                                                        : opts->engine;
     if (engine == MRF_ENGINE_MEGAKERNEL && lowp)
         return fail(MRF_ERR_UNSUPPORTED, "mrf_render: FP16/BF16 fields run on the wavefront engine");
-    if (engine == MRF_ENGINE_WAVEFRONT && ctx->n_lights > 8)
-        return fail(MRF_ERR_UNSUPPORTED, "mrf_render: the wavefront engine takes at most 8 point lights");
+    if (engine == MRF_ENGINE_WAVEFRONT && ctx->n_shadow > 64)
+        return fail(MRF_ERR_UNSUPPORTED, "mrf_render: the wavefront engine takes at most 64 shadow rays per hit");
     size_t wf_off = 0;
     if (engine == MRF_ENGINE_WAVEFRONT) {
         wf_off = (scratch_need + 255) & ~(size_t)255;
@@ -875,9 +909,9 @@ mrf_status mrf_render_static(mrf_context *ctx, const mrf_field *field, const mrf
     if (opts->kernel_ms || opts->kernel_launches)
         return fail(MRF_ERR_INVALID_ARG, "mrf_render_static: per-kernel timing is not available here");
     if (bvh->n_tris && ctx->n_mats == 0) return fail(MRF_ERR_NOT_READY, "mrf_render_static: no materials set");
-    if (ctx->n_lights > static_arena_max_lights())
-        return fail(MRF_ERR_INVALID_ARG, "mrf_render_static: %d lights exceed the arena limit of %d", ctx->n_lights,
-                    static_arena_max_lights());
+    if (ctx->n_shadow > static_arena_max_lights())
+        return fail(MRF_ERR_INVALID_ARG, "mrf_render_static: %d shadow rays per hit exceed the arena limit of %d",
+                    ctx->n_shadow, static_arena_max_lights());
     CUDA_TRY(cudaSetDevice(ctx->device), "mrf_render_static: cudaSetDevice");
     if (!is_device_ptr(out_hdr)) return fail(MRF_ERR_INVALID_ARG, "mrf_render_static: out_hdr must be device memory");
     if ((opts->rec_segments && !is_device_ptr(opts->rec_segments)) || (opts->rec_tri && !is_device_ptr(opts->rec_tri)) ||
@@ -904,6 +938,7 @@ mrf_status mrf_render_static(mrf_context *ctx, const mrf_field *field, const mrf
     P.n_mats = ctx->n_mats;
     P.lights = ctx->lights;
     P.n_lights = ctx->n_lights;
+    P.n_shadow = ctx->n_shadow;
     uint32_t count;
     if (rays->camera && rays->n_cameras > 1)
         return fail(MRF_ERR_UNSUPPORTED, "mrf_render_static: one camera or explicit rays; several views go to mrf_render");

@@ -67,9 +67,19 @@ struct MaterialDev {
     float ior;
 };
 
+// A light: point (pos, I) or triangle emitter (v0 = pos, v1, v2, radiance I,
+// unit front normal n, area A, `samples` shadow rays per hit whose random
+// numbers use counters 1 + q0 .. q0 + samples).
 struct LightDev {
     float pos[3];
     float I[3];
+    float v1[3], v2[3];
+    float n[3];
+    float area;
+    int kind;
+    uint32_t samples;
+    uint32_t q0;
+    uint32_t slot0;     // index of the light's first shadow ray among the hit's rays
 };
 
 // device statistics counters (unsigned long long), in this order
@@ -93,6 +103,7 @@ struct RenderParams {
     int n_mats;
     const LightDev *lights;
     int n_lights;
+    int n_shadow;                // shadow rays per diffuse hit (point lights 1, area lights `samples`)
     int use_camera;
     float cam_pos[3], cam_f[3], cam_r[3], cam_u[3];
     float tan_half, aspect;

@@ -218,26 +218,44 @@ __device__ __forceinline__ void surface_uniforms(const RenderParams &P, uint32_t
     u[2] = u24(ctr[2]);
 }
 
-// Shadow-ray geometry toward point light l: unit direction, distance, cosine
-// at the facing normal; returns false when the light is behind the surface.
-__device__ __forceinline__ bool light_geometry(const RenderParams &P, const SurfaceHit &S, int l, V3 &wl, float &D,
-                                               float &D2, float &cosl) {
-    const LightDev L0 = P.lights[l];
-    wl = v3(L0.pos[0], L0.pos[1], L0.pos[2]) - S.p;
-    D2 = dot(wl, wl);
-    D = sqrtf(D2);
-    wl = wl * (1.f / D);
-    cosl = dot(S.nf, wl);
-    return cosl > 0.f;
-}
-
-// Next-event weight (albedo / pi) cos I / D^2, per channel (times T' and the
-// field transmittance by the caller).
-__device__ __forceinline__ void nee_weight(const RenderParams &P, const SurfaceHit &S, int l, float cosl, float D2,
-                                           float w[3]) {
-    const float g = cosl / D2 * 0.31830988618379067f;
+// Shadow ray k of light l from the diffuse hit S (Sec. 3.1, "Shadow rays"):
+// unit direction wl and distance D to the light point, and the next-event
+// weight w (to be multiplied by T', the visibility and the field
+// transmittance).  Point light: (albedo / pi) cos I / D^2.  Area light: point
+// y drawn uniformly on the triangle from Philox counter (ray, spp, j, 1 + q0 + k)
+// (square-root barycentric warp), weight (albedo / pi) Le A / N cos_x cos_y / D^2.
+// Returns false when the light point is behind the surface or the emitter
+// faces away (no shadow ray is cast).
+__device__ __forceinline__ bool shadow_ray(const RenderParams &P, const SurfaceHit &S, int l, uint32_t k,
+                                           uint32_t ray, uint32_t s, uint32_t j, V3 &wl, float &D, float w[3]) {
+    const LightDev &L0 = P.lights[l];
+    V3 y;
+    float g;
+    if (L0.kind == MRF_LIGHT_AREA) {
+        uint64_t ctr[4] = {(uint64_t)ray, (uint64_t)s, (uint64_t)j, 1ull + L0.q0 + k};
+        philox4x64_10(ctr, P.seed, 0ull);
+        const float su = sqrtf(u24(ctr[0])), b0 = 1.f - su, b1 = u24(ctr[1]) * su, b2 = 1.f - b0 - b1;
+        y = v3(L0.pos[0], L0.pos[1], L0.pos[2]) * b0 + v3(L0.v1[0], L0.v1[1], L0.v1[2]) * b1 +
+            v3(L0.v2[0], L0.v2[1], L0.v2[2]) * b2;
+        wl = y - S.p;
+        const float D2 = dot(wl, wl);
+        D = sqrtf(D2);
+        wl = wl * (1.f / D);
+        const float cosx = dot(S.nf, wl), cosy = -dot(v3(L0.n[0], L0.n[1], L0.n[2]), wl);
+        if (!(cosx > 0.f) || !(cosy > 0.f)) return false;
+        g = cosx * cosy / D2 * (L0.area / (float)L0.samples) * 0.31830988618379067f;
+    } else {
+        wl = v3(L0.pos[0], L0.pos[1], L0.pos[2]) - S.p;
+        const float D2 = dot(wl, wl);
+        D = sqrtf(D2);
+        wl = wl * (1.f / D);
+        const float cosl = dot(S.nf, wl);
+        if (!(cosl > 0.f)) return false;
+        g = cosl / D2 * 0.31830988618379067f;
+    }
 #pragma unroll
-    for (int k = 0; k < 3; ++k) w[k] = S.mat.rgb[k] * g * P.lights[l].I[k];
+    for (int c = 0; c < 3; ++c) w[c] = S.mat.rgb[c] * g * L0.I[c];
+    return true;
 }
 
 // Samples the BSDF (Eq. 13): returns the new (unnormalised) direction and

@@ -43,26 +43,28 @@ __device__ void trace_path(const RenderParams &P, const float *w, uint32_t ray, 
         surface_uniforms(P, ray, s, j, u);
         // Eq. 12 adds T' L_e at the hit; every mesh here has L_e = 0.
         if (S.mat.kind == MRF_MAT_DIFFUSE) {
-            // next-event estimation: shadow rays toward the point lights
+            // next-event estimation: shadow rays toward every light (area
+            // lights: `samples` points each)
             for (int l = 0; l < P.n_lights; ++l) {
-                V3 wl;
-                float D, D2, cosl;
-                if (!light_geometry(P, S, l, wl, D, D2, cosl)) continue;
-                ++C.shadow;
-                Hit hs;
-                unsigned rs = 0;
-                bool f2 = false;
-                const bool blocked = bvh_trace<true>(P.B, S.p, wl, S.id, P.tmin, D, hs, rs, f2);
-                C.retests += rs;
-                if (f2) C.fault |= 1;
-                if (blocked) continue;
-                bool dummy = false;
-                const float depth = march<false>(P, w, S.p, wl, 0.f, D, nullptr, nullptr, dummy, C);
-                const float Tf = expf(-depth);
-                float wt[3];
-                nee_weight(P, S, l, cosl, D2, wt);
+                const uint32_t ns = P.lights[l].samples;
+                for (uint32_t k = 0; k < ns; ++k) {
+                    V3 wl;
+                    float D, wt[3];
+                    if (!shadow_ray(P, S, l, k, ray, s, j, wl, D, wt)) continue;
+                    ++C.shadow;
+                    Hit hs;
+                    unsigned rs = 0;
+                    bool f2 = false;
+                    const bool blocked = bvh_trace<true>(P.B, S.p, wl, S.id, P.tmin, D, hs, rs, f2);
+                    C.retests += rs;
+                    if (f2) C.fault |= 1;
+                    if (blocked) continue;
+                    bool dummy = false;
+                    const float depth = march<false>(P, w, S.p, wl, 0.f, D, nullptr, nullptr, dummy, C);
+                    const float Tf = expf(-depth);
 #pragma unroll
-                for (int k = 0; k < 3; ++k) L[k] = fmaf(T[k] * Tf, wt[k], L[k]);
+                    for (int c = 0; c < 3; ++c) L[c] = fmaf(T[c] * Tf, wt[c], L[c]);
+                }
             }
         }
         const V3 nd = bsdf_sample(S, d, u, T);

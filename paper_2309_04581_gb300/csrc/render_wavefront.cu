@@ -38,12 +38,12 @@ struct WfParams {
     int *hit_slot;
     uint32_t *hit_id;
     uint32_t *rstart, *rcount;      // radiance samples of the slot's segment
-    uint32_t *sstart, *scount;      // shadow samples, [slot * n_lights + l]
-    float4 *sw;                     // next-event weight (rgb), w = 1 when the light is visible
-    float4 *hp;                     // hit point (xyz) and visible-light bits (w) per live slot
-    float4 *sdir;                   // shadow-ray direction (xyz) and light distance (w), [slot * n_lights + l]
+    uint32_t *sstart, *scount;      // shadow samples, [slot * n_shadow + q]
+    float4 *sw;                     // next-event weight (rgb), w = 1 when shadow ray q is unblocked
+    float4 *hp;                     // hit point (xyz) and number of unblocked shadow rays (w) per live slot
+    float4 *sdir;                   // shadow-ray direction (xyz) and light distance (w), [slot * n_shadow + q]
     float4 *comp;                   // per slot: segment radiance sum (rgb, times T(p_j)) and optical depth (w)
-    float *sdepth;                  // shadow optical depth, [slot * n_lights + l]
+    float *sdepth;                  // shadow optical depth, [slot * n_shadow + q]
     uint32_t *ctr;                  // [0], [1] live counts; [2] generated samples
     float4 *samp;                   // sample position (xyz) and interval length (w)
     float4 *fout;                   // sigma, r, g, b per sample
@@ -70,7 +70,6 @@ __device__ __forceinline__ uint32_t warp_alloc(uint32_t *ctr, uint32_t n) {
 // density-support spheres.
 constexpr int kCoarseWordsMax = 1024;   // coarse grids up to 32^3 are staged
 constexpr int kSupportMax = 64;
-constexpr int kWfMaxLights = 8;        // point lights the wavefront engine supports
 
 struct WalkSmem {
     uint32_t coarse[kCoarseWordsMax];
@@ -303,19 +302,20 @@ __device__ __forceinline__ V3 shfl3(V3 v, int src) {
 }
 
 // Per lane: primary or queued ray, closest hit (Eq. 3), and at diffuse hits the
-// shadow-ray visibility toward every point light.
+// visibility of every shadow ray (one per point light, `samples` per area light).
 __global__ void __launch_bounds__(kThreads) wf_cast(const WfParams W, uint32_t j, int cur) {
     const RenderParams &P = W.R;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t live = j == 1 ? W.paths : W.ctr[cur];
-    const int nl = P.n_lights;
+    const int K = P.n_shadow;
     Counters C = {};
     if (j == 1 && tid == 0) W.ctr[cur] = W.paths;  // every path is live in segment 1
     if (tid < live) {
         V3 o, d;
-        uint32_t prev = kNoHit;
+        uint32_t prev = kNoHit, path;
         if (j == 1) {
-            const uint32_t path = tid, ray = path / P.spp;
+            path = tid;
+            const uint32_t ray = path / P.spp;
             primary_ray(P, ray, o, d);
             W.qpath[cur][tid] = path;
             W.qo[cur][tid] = make_float4(o.x, o.y, o.z, __uint_as_float(kNoHit));
@@ -323,6 +323,7 @@ __global__ void __launch_bounds__(kThreads) wf_cast(const WfParams W, uint32_t j
             W.qT[cur][tid] = make_float4(1.f, 1.f, 1.f, 0.f);
             ++C.paths;
         } else {
+            path = W.qpath[cur][tid];
             const float4 qo = W.qo[cur][tid], qd = W.qd[cur][tid];
             o = v3(qo.x, qo.y, qo.z);
             prev = __float_as_uint(qo.w);
@@ -337,38 +338,41 @@ __global__ void __launch_bounds__(kThreads) wf_cast(const WfParams W, uint32_t j
         W.hit_t[tid] = h.t;
         W.hit_slot[tid] = h.slot;
         W.hit_id[tid] = h.id;
-        uint32_t vis = 0;
+        uint32_t nvis = 0;
         V3 hp = v3(0.f, 0.f, 0.f);
         if (h.id != kNoHit) {
             const SurfaceHit S = surface_at(P, o, d, h);
             hp = S.p;
             if (S.mat.kind == MRF_MAT_DIFFUSE) {
-                for (int l = 0; l < nl; ++l) {
-                    V3 wl;
-                    float D, D2, cosl;
-                    float4 wgt = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (light_geometry(P, S, l, wl, D, D2, cosl)) {
-                        ++C.shadow;
-                        Hit hs;
-                        unsigned rs = 0;
-                        bool f2 = false;
-                        const bool blocked = bvh_trace<true>(P.B, S.p, wl, S.id, P.tmin, D, hs, rs, f2);
-                        C.retests += rs;
-                        if (f2) C.fault |= 1;
-                        if (!blocked) {
-                            float w3[3];
-                            nee_weight(P, S, l, cosl, D2, w3);
-                            wgt = make_float4(w3[0], w3[1], w3[2], 1.f);
-                            vis |= 1u << l;
-                            W.sdir[(size_t)tid * nl + l] = make_float4(wl.x, wl.y, wl.z, D);
+                const uint32_t ray = path / P.spp, sp = path % P.spp;
+                for (int l = 0; l < P.n_lights; ++l) {
+                    const uint32_t ns = P.lights[l].samples, q0 = P.lights[l].slot0;
+                    for (uint32_t k = 0; k < ns; ++k) {
+                        const size_t idx = (size_t)tid * K + q0 + k;
+                        V3 wl;
+                        float D, w3[3];
+                        float4 wgt = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (shadow_ray(P, S, l, k, ray, sp, j, wl, D, w3)) {
+                            ++C.shadow;
+                            Hit hs;
+                            unsigned rs = 0;
+                            bool f2 = false;
+                            const bool blocked = bvh_trace<true>(P.B, S.p, wl, S.id, P.tmin, D, hs, rs, f2);
+                            C.retests += rs;
+                            if (f2) C.fault |= 1;
+                            if (!blocked) {
+                                wgt = make_float4(w3[0], w3[1], w3[2], 1.f);
+                                ++nvis;
+                                W.sdir[idx] = make_float4(wl.x, wl.y, wl.z, D);
+                            }
                         }
+                        W.sw[idx] = wgt;
+                        W.scount[idx] = 0;
                     }
-                    W.sw[(size_t)tid * nl + l] = wgt;
-                    W.scount[(size_t)tid * nl + l] = 0;
                 }
             }
         }
-        W.hp[tid] = make_float4(hp.x, hp.y, hp.z, __uint_as_float(vis));
+        W.hp[tid] = make_float4(hp.x, hp.y, hp.z, __uint_as_float(nvis));
     }
     flush_counters(P.stats, C);
     if (C.fault && P.status) atomicOr(P.status, C.fault);
@@ -386,11 +390,11 @@ __global__ void __launch_bounds__(kThreads, 8) wf_gen(const WfParams W, uint32_t
     const int lane = threadIdx.x & 31;
     const uint32_t live = j == 1 ? W.paths : W.ctr[cur];
     const bool active = tid < live;
-    const int nl = P.n_lights;
+    const int K = P.n_shadow;
     Counters C = {};
     V3 o = v3(0.f, 0.f, 0.f), d = v3(0.f, 0.f, 1.f), hp = v3(0.f, 0.f, 0.f);
     float th = 0.f;
-    uint32_t vis = 0;
+    uint32_t vis = 0;   // unblocked shadow rays of the slot
     if (active) {
         const float4 qo = W.qo[cur][tid], qd = W.qd[cur][tid], h4 = W.hp[tid];
         o = v3(qo.x, qo.y, qo.z);
@@ -409,12 +413,15 @@ __global__ void __launch_bounds__(kThreads, 8) wf_gen(const WfParams W, uint32_t
         RunList(&rl)[2] = runs_sm[threadIdx.x >> 5][src];
         const uint32_t n_r = warp_walk(P, X, so, sd, 0.f, st, nullptr, 0, C.nominal, lane, &rl[0]);
         uint32_t n_s = 0;
-        for (int l = 0; l < nl; ++l) {
-            if (!((svis >> l) & 1u)) continue;
-            const float4 sh = W.sdir[(size_t)src_tid * nl + l];
+        bool first = true;   // the first unblocked shadow ray records its runs
+        for (int q = 0; svis && q < K; ++q) {
+            const size_t idx = (size_t)src_tid * K + q;
+            if (W.sw[idx].w == 0.f) continue;
+            const float4 sh = W.sdir[idx];
             const uint32_t ns = warp_walk(P, X, sp, v3(sh.x, sh.y, sh.z), 0.f, sh.w, nullptr, 0, C.nominal, lane,
-                                          l == 0 ? &rl[1] : nullptr);
-            if (lane == src) W.scount[(size_t)tid * nl + l] = ns;
+                                          first ? &rl[1] : nullptr);
+            first = false;
+            if (lane == src) W.scount[idx] = ns;
             n_s += ns;
         }
         if (lane == src) {
@@ -437,8 +444,8 @@ __global__ void __launch_bounds__(kThreads, 8) wf_gen(const WfParams W, uint32_t
         if (!sfits) {
             if (lane == src) {
                 W.rcount[tid] = kOverflow;
-                for (int l = 0; l < nl; ++l)
-                    if ((vis >> l) & 1u) W.scount[(size_t)tid * nl + l] = kOverflow;
+                for (int q = 0; vis && q < K; ++q)
+                    if (W.sw[(size_t)tid * K + q].w != 0.f) W.scount[(size_t)tid * K + q] = kOverflow;
             }
             continue;
         }
@@ -454,15 +461,18 @@ __global__ void __launch_bounds__(kThreads, 8) wf_gen(const WfParams W, uint32_t
             warp_walk(P, X, so, sd, 0.f, st, W.samp + k, nr, dummy, lane, nullptr);
         k += nr;
         if (lane == src) W.rstart[tid] = sbase;
-        for (int l = 0; l < nl; ++l) {
-            if (!((svis >> l) & 1u)) continue;
-            const float4 sh = W.sdir[(size_t)src_tid * nl + l];
-            const uint32_t ns = W.scount[(size_t)src_tid * nl + l];
-            if (lane == src) W.sstart[(size_t)tid * nl + l] = k;
-            if (l == 0 && rl[1].n <= kRunsPerJob)
+        bool first = true;
+        for (int q = 0; svis && q < K; ++q) {
+            const size_t idx = (size_t)src_tid * K + q;
+            if (W.sw[idx].w == 0.f) continue;
+            const float4 sh = W.sdir[idx];
+            const uint32_t ns = W.scount[idx];
+            if (lane == src) W.sstart[idx] = k;
+            if (first && rl[1].n <= kRunsPerJob)
                 write_runs(P, sp, v3(sh.x, sh.y, sh.z), 0.f, sh.w, rl[1], W.samp + k, ns, lane);
             else
                 warp_walk(P, X, sp, v3(sh.x, sh.y, sh.z), 0.f, sh.w, W.samp + k, ns, dummy, lane, nullptr);
+            first = false;
             k += ns;
         }
     }
@@ -531,7 +541,7 @@ __global__ void __launch_bounds__(kThreads, 8) wf_composite(const WfParams W, in
     const int lane = threadIdx.x & 31;
     const uint32_t live = W.ctr[cur];
     const bool active = tid < live;
-    const int nl = P.n_lights;
+    const int K = P.n_shadow;
     uint32_t rc = kOverflow, r0 = 0;
     float tmax = 0.f;
     bool diffuse = false;
@@ -540,7 +550,7 @@ __global__ void __launch_bounds__(kThreads, 8) wf_composite(const WfParams W, in
         r0 = W.rstart[tid];
         const float4 qT = W.qT[cur][tid];
         tmax = fmaxf(qT.x, fmaxf(qT.y, qT.z));
-        diffuse = __float_as_uint(W.hp[tid].w) != 0u;   // some light visible from a diffuse hit
+        diffuse = __float_as_uint(W.hp[tid].w) != 0u;   // some unblocked shadow ray from a diffuse hit
     }
     for (int src = 0; src < 32; ++src) {
         if (!__shfl_sync(0xffffffffu, (int)active, src)) continue;
@@ -558,10 +568,11 @@ __global__ void __launch_bounds__(kThreads, 8) wf_composite(const WfParams W, in
             if (lane == 0) W.comp[src_tid] = make_float4(lr, lg, lb, stp ? -dep - 1.f : dep);
         }
         if (!__shfl_sync(0xffffffffu, (int)diffuse, src)) continue;
-        for (int l = 0; l < nl; ++l) {
-            const size_t idx = (size_t)src_tid * nl + l;
+        for (int q = 0; q < K; ++q) {
+            const size_t idx = (size_t)src_tid * K + q;
+            if (W.sw[idx].w == 0.f) continue;
             const uint32_t sc = W.scount[idx];
-            if (W.sw[idx].w == 0.f || sc == kOverflow) continue;
+            if (sc == kOverflow) continue;
             const uint32_t s0 = W.sstart[idx];
             float dep = 0.f;
             for (uint32_t i0 = lane; i0 < sc; i0 += 32) dep = fmaf(W.fout[s0 + i0].x, W.samp[s0 + i0].w, dep);
@@ -578,10 +589,13 @@ __global__ void __launch_bounds__(kThreads) wf_overflow(const WfParams W, int cu
     const RenderParams &P = W.R;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= W.ctr[cur]) return;
-    const int nl = P.n_lights;
+    const int K = P.n_shadow;
     const bool rad = W.rcount[tid] == kOverflow;
+    const float4 h4 = W.hp[tid];
     bool any_shadow = false;
-    for (int l = 0; l < nl; ++l) any_shadow |= W.scount[(size_t)tid * nl + l] == kOverflow;
+    if (__float_as_uint(h4.w) != 0u)   // unblocked shadow rays (only their counts are current)
+        for (int q = 0; q < K; ++q)
+            any_shadow |= W.sw[(size_t)tid * K + q].w != 0.f && W.scount[(size_t)tid * K + q] == kOverflow;
     if (!rad && !any_shadow) return;
     const float4 qo = W.qo[cur][tid], qd = W.qd[cur][tid], qT = W.qT[cur][tid];
     const V3 o = v3(qo.x, qo.y, qo.z), d = v3(qd.x, qd.y, qd.z);
@@ -598,18 +612,14 @@ __global__ void __launch_bounds__(kThreads) wf_overflow(const WfParams W, int cu
                                   T0[2] > 0.f ? L[2] / T0[2] : 0.f, stop ? -dep - 1.f : dep);
     }
     if (any_shadow) {
-        Hit h;
-        h.t = W.hit_t[tid];
-        h.slot = W.hit_slot[tid];
-        h.id = W.hit_id[tid];
-        const SurfaceHit S = surface_at(P, o, d, h);
-        for (int l = 0; l < nl; ++l) {
-            const size_t idx = (size_t)tid * nl + l;
-            if (W.scount[idx] != kOverflow) continue;
+        const V3 hp = v3(h4.x, h4.y, h4.z);
+        for (int q = 0; q < K; ++q) {
+            const size_t idx = (size_t)tid * K + q;
+            if (W.sw[idx].w == 0.f || W.scount[idx] != kOverflow) continue;
             const float4 sh = W.sdir[idx];
             Counters dummy = {};
             bool dstop = false;
-            W.sdepth[idx] = march<false>(P, P.F.mlp, S.p, v3(sh.x, sh.y, sh.z), 0.f, sh.w, nullptr, nullptr, dstop,
+            W.sdepth[idx] = march<false>(P, P.F.mlp, hp, v3(sh.x, sh.y, sh.z), 0.f, sh.w, nullptr, nullptr, dstop,
                                          dummy);
         }
     }
@@ -621,7 +631,7 @@ __global__ void __launch_bounds__(kThreads) wf_shade(const WfParams W, uint32_t 
     const RenderParams &P = W.R;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t live = W.ctr[cur];
-    const int nl = P.n_lights;
+    const int K = P.n_shadow;
     Counters C = {};
     bool push = false;
     uint32_t path = 0, prev = kNoHit;
@@ -669,9 +679,9 @@ __global__ void __launch_bounds__(kThreads) wf_shade(const WfParams W, uint32_t 
             const SurfaceHit S = surface_at(P, o, d, h);
             float u[3];
             surface_uniforms(P, ray, s, j, u);
-            if (S.mat.kind == MRF_MAT_DIFFUSE) {
-                for (int l = 0; l < nl; ++l) {
-                    const size_t idx = (size_t)tid * nl + l;
+            if (S.mat.kind == MRF_MAT_DIFFUSE && __float_as_uint(W.hp[tid].w) != 0u) {
+                for (int q = 0; q < K; ++q) {
+                    const size_t idx = (size_t)tid * K + q;
                     const float4 wgt = W.sw[idx];
                     if (wgt.w == 0.f) continue;
                     const float Tf = expf(-W.sdepth[idx]);
@@ -731,7 +741,7 @@ struct Layout {
     uint32_t cap;
 };
 
-Layout layout(uint32_t paths, int n_lights) {
+Layout layout(uint32_t paths, int n_shadow) {
     Layout L{};
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -739,7 +749,7 @@ Layout layout(uint32_t paths, int n_lights) {
         off += (bytes + 255) & ~(size_t)255;
         return o;
     };
-    const size_t P = paths, nl = (size_t)std::max(n_lights, 1);
+    const size_t P = paths, nl = (size_t)std::max(n_shadow, 1);
     L.acc = take(16 * P);
     for (int q = 0; q < 2; ++q) {
         L.qpath[q] = take(4 * P);
@@ -774,13 +784,13 @@ Layout layout(uint32_t paths, int n_lights) {
 bool wavefront_available() { return true; }
 
 size_t wavefront_scratch_bytes(const RenderParams &P) {
-    return layout(P.count * P.spp, P.n_lights).total;
+    return layout(P.count * P.spp, P.n_shadow).total;
 }
 
 cudaError_t launch_render_wavefront(const RenderParams &P, void *scratch, size_t scratch_bytes, cudaStream_t s,
                                     KernelTimer *timer) {
     const uint32_t paths = P.count * P.spp;
-    const Layout Lo = layout(paths, P.n_lights);
+    const Layout Lo = layout(paths, P.n_shadow);
     if (scratch_bytes < Lo.total) return cudaErrorInvalidValue;
     char *b = static_cast<char *>(scratch);
     WfParams W{};
@@ -864,7 +874,7 @@ cudaError_t launch_render_wavefront(const RenderParams &P, void *scratch, size_t
 // (its queue and sample counters), and calls that overlap on the GPU race.
 constexpr size_t kStaticArenaBytes = (size_t)64 << 20;   // 64 MiB
 constexpr uint32_t kStaticMaxPaths = 1u << 17;           // count * spp limit
-constexpr int kStaticMaxLights = 8;
+constexpr int kStaticMaxLights = 8;   // shadow rays per diffuse hit
 static __device__ __align__(256) unsigned char g_static_arena[kStaticArenaBytes];
 
 namespace {
@@ -872,8 +882,8 @@ std::mutex g_arena_mu;
 void *g_arena_addr[64] = {};
 
 // per-path state of the wavefront engine plus a sample buffer filling the rest
-Layout layout_in(uint32_t paths, int n_lights, size_t bytes, bool &fits) {
-    Layout L = layout(paths, n_lights);
+Layout layout_in(uint32_t paths, int n_shadow, size_t bytes, bool &fits) {
+    Layout L = layout(paths, n_shadow);
     const size_t state = L.samp;   // everything before the sample buffers
     fits = bytes > state + 2 * 16 * 128 + 512;
     if (!fits) return L;
@@ -911,7 +921,7 @@ cudaError_t static_arena(int device, void **ptr, size_t *bytes) {
 cudaError_t launch_render_wavefront_arena(const RenderParams &P, void *arena, size_t arena_bytes, cudaStream_t s) {
     const uint32_t paths = P.count * P.spp;
     bool fits = false;
-    const Layout Lo = layout_in(paths, P.n_lights, arena_bytes, fits);
+    const Layout Lo = layout_in(paths, P.n_shadow, arena_bytes, fits);
     if (!fits) return cudaErrorInvalidValue;
     char *b = static_cast<char *>(arena);
     WfParams W{};

@@ -26,7 +26,7 @@ MRF_OK, MRF_ERR_INVALID_ARG, MRF_ERR_CUDA, MRF_ERR_OOM, MRF_ERR_TIMEOUT, MRF_ERR
 MRF_FIELD_CONST, MRF_FIELD_GAUSS, MRF_FIELD_HASHGRID = 0, 1, 2
 MRF_PREC_FP32, MRF_PREC_FP16, MRF_PREC_BF16 = 0, 1, 2
 MRF_MAT_MIRROR, MRF_MAT_GLASS, MRF_MAT_DIFFUSE = 0, 1, 2
-MRF_LIGHT_POINT = 0
+MRF_LIGHT_POINT, MRF_LIGHT_AREA = 0, 1
 MRF_ENGINE_AUTO, MRF_ENGINE_MEGAKERNEL, MRF_ENGINE_WAVEFRONT = 0, 1, 2
 KERNEL_NAMES = ("render_megakernel", "wf_cast", "field", "wf_shade", "wf_finalize", "wf_gen", "wf_composite")
 NO_HIT = 0xFFFFFFFF
@@ -62,7 +62,8 @@ class mrf_material(C.Structure):
 
 
 class mrf_light(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("pos", C.c_float * 3), ("intensity", C.c_float * 3)]
+    _fields_ = [("kind", C.c_int32), ("pos", C.c_float * 3), ("intensity", C.c_float * 3), ("v1", C.c_float * 3),
+                ("v2", C.c_float * 3), ("samples", C.c_uint32)]
 
 
 class mrf_camera(C.Structure):
@@ -200,6 +201,10 @@ def mrf_lights_set(ctx: int, lights):
         arr[i].kind = l.kind
         arr[i].pos[:] = [float(x) for x in l.pos]
         arr[i].intensity[:] = [float(x) for x in l.intensity]
+        if getattr(l, "v1", None) is not None:
+            arr[i].v1[:] = [float(x) for x in l.v1]
+            arr[i].v2[:] = [float(x) for x in l.v2]
+        arr[i].samples = int(getattr(l, "samples", 1))
     check(lib().mrf_lights_set(ctx, arr, len(lights)))
 
 

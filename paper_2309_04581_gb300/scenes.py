@@ -38,6 +38,7 @@ FIELD_HASH = 2
 
 # light kinds
 LIGHT_POINT = 0
+LIGHT_AREA = 1
 
 
 def splitmix64(x: int) -> int:
@@ -127,9 +128,17 @@ class Material:
 
 @dataclass
 class Light:
-    pos: tuple
-    intensity: tuple
+    pos: tuple                    # point light: position; area light: vertex v0
+    intensity: tuple              # point light: intensity I; area light: radiance Le of the front side
     kind: int = LIGHT_POINT
+    v1: Optional[tuple] = None    # area light: the other two vertices (front normal (v1-v0) x (v2-v0))
+    v2: Optional[tuple] = None
+    samples: int = 1              # area light: shadow rays per diffuse hit
+
+
+def area_light(v0, v1, v2, radiance, samples: int) -> "Light":
+    return Light(pos=tuple(f32(v0)), intensity=tuple(f32(radiance)), kind=LIGHT_AREA, v1=tuple(f32(v1)),
+                 v2=tuple(f32(v2)), samples=int(samples))
 
 
 @dataclass
@@ -400,6 +409,34 @@ def config2(width: int = 800, height: int = 800, tau: float = 0.0, max_bounces: 
                  mesh=mesh, materials=mats, lights=lights,
                  opts=RenderOpts(max_bounces=max_bounces, spp=1, seed=2, steps_per_segment=0, dt=DT_C2,
                                  tau=tau))
+
+
+def seeded_area_lights(n: int = 4, samples: int = 16, config: int = 4):
+    """n emitter triangles above the field box (y in [0.55, 0.75], outside it),
+    equilateral with circumradius U(0.06, 0.12), random yaw, front side facing
+    down, radiance U(30, 90) per channel (HDR emitters)."""
+    rng = _rng(config, 7)
+    out = []
+    for _ in range(n):
+        c = np.array([rng.uniform(-0.35, 0.35), rng.uniform(0.55, 0.75), rng.uniform(-0.35, 0.35)])
+        r, yaw = rng.uniform(0.06, 0.12), rng.uniform(0, 2 * math.pi)
+        # counter-clockwise seen from below: normal (v1 - v0) x (v2 - v0) points to -y
+        vs = [c + r * np.array([math.cos(yaw - k * 2 * math.pi / 3), 0.0, math.sin(yaw - k * 2 * math.pi / 3)])
+              for k in range(3)]
+        if np.cross(vs[1] - vs[0], vs[2] - vs[0])[1] > 0:
+            vs = [vs[0], vs[2], vs[1]]
+        out.append(area_light(vs[0], vs[1], vs[2], rng.uniform(30.0, 90.0, 3), samples))
+    return out
+
+
+def config4(width: int = 1920, height: int = 1080, samples: int = 16, max_bounces: int = 8) -> Scene:
+    """The hash-grid scene of config2 lit by 4 seeded area-light triangles with
+    `samples` shadow rays each per diffuse hit, 1 spp."""
+    sc = config2(width, height, max_bounces=max_bounces)
+    sc.name = f"c4_area_lights_{width}x{height}"
+    sc.lights = seeded_area_lights(4, samples)
+    sc.opts.seed = 4
+    return sc
 
 
 def explicit_rays(scene: Scene, origins, dirs) -> Scene:

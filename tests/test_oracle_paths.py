@@ -310,3 +310,83 @@ def test_multi_view_random_numbers_follow_the_global_ray_index(orc):
     assert np.array_equal(got["rgba"][:100], ref["rgba"])
     same = np.all(got["rgba"][100:] == ref["rgba"], axis=1)
     assert not same.all()
+
+
+def _polygon_irradiance(p, n, verts, Le):
+    """Irradiance at p (normal n) from a uniformly emitting polygon of radiance
+    Le facing p: Lambert's closed form E = Le/2 |sum_i theta_i (n . unit(R_i x R_i+1))|."""
+    R = [np.asarray(v, np.float64) - p for v in verts]
+    R = [r / np.linalg.norm(r) for r in R]
+    acc = 0.0
+    for i in range(len(R)):
+        a, b = R[i], R[(i + 1) % len(R)]
+        g = np.cross(a, b)
+        acc += math.acos(np.clip(a @ b, -1, 1)) * (g @ n) / np.linalg.norm(g)
+    return 0.5 * Le * abs(acc)
+
+
+def _area_floor_scene(verts, Le, samples, spp, grid=16, half=0.3, y0=0.3):
+    sc = _floor_scene()
+    sc.lights = [S.area_light(*verts, (Le, Le, Le), samples)]
+    sc.opts.spp = spp
+    xs = (np.arange(grid) + 0.5) / grid * 2 * half - half
+    pts = np.array([[x, y0, z] for z in xs for x in xs])
+    return S.explicit_rays(sc, pts, np.tile([0.0, -1.0, 0.0], (pts.shape[0], 1))), pts
+
+
+def test_area_light_estimator_converges_to_lamberts_formula(orc):
+    # A triangle light 0.2 above a Lambertian floor (close, so that cos/D^2
+    # varies strongly over it): the mean of the next-event estimates is
+    # (albedo/pi) E(p) with E from Lambert's polygon formula; a wrong area, a
+    # dropped cosine or non-uniform points on the triangle bias the mean.
+    verts = [[-0.1, -0.25, -0.1], [0.15, -0.25, -0.05], [0.0, -0.25, 0.15]]   # front side faces -y
+    Le = 3.0
+    sc, pts = _area_floor_scene(verts, Le, samples=64, spp=16)
+    res = orc.render(sc)
+    vf = [S.f32(v).astype(np.float64) for v in verts]
+    expect = np.array([0.5 / math.pi * _polygon_irradiance(np.array([F(x), F(-0.45), F(z)]), np.array([0, 1.0, 0]),
+                                                           vf, F(Le)) for x, _, z in pts])
+    got = res["rgba"][:, 0]
+    assert np.all(res["rgba"][:, 0] == res["rgba"][:, 1])
+    ratio = got / expect
+    assert abs(ratio.mean() - 1.0) <= 6e-3, ratio.mean()
+    assert np.abs(ratio - 1.0).max() <= 0.12
+    assert res["counts"]["shadow_rays"] == pts.shape[0] * 16 * 64
+
+
+def test_small_area_light_is_a_point_light(orc):
+    # A 2e-3 triangle at the point light's position, facing down, with Le A = I
+    # at normal emission: its estimate equals the point light's with intensity
+    # I cos(theta_y) (a small Lambertian emitter), cos_y = cos_x for a
+    # horizontal floor.
+    c = np.array([0.0, 0.45, 0.0])
+    h = 1e-3
+    verts = [c + [-h, 0, -h], c + [h, 0, -h * 0.5], c + [0, 0, h]]
+    vf = [S.f32(v).astype(np.float64) for v in verts]
+    A = 0.5 * np.linalg.norm(np.cross(vf[1] - vf[0], vf[2] - vf[0]))
+    assert np.cross(vf[1] - vf[0], vf[2] - vf[0])[1] < 0
+    I = 2.0
+    sc_area, pts = _area_floor_scene(verts, I / A, samples=4, spp=1, grid=6)
+    sc_point = S.explicit_rays(_floor_scene(I=I), pts, np.tile([0.0, -1.0, 0.0], (pts.shape[0], 1)))
+    sc_point.lights = [S.Light(pos=tuple(S.f32(np.mean(vf, axis=0))), intensity=(I, I, I))]
+    a = orc.render(sc_area)["rgba"][:, 0]
+    b = orc.render(sc_point)["rgba"][:, 0]
+    cos_y = np.array([(F(0.45) - F(-0.45)) / np.linalg.norm(np.mean(vf, axis=0) - [F(x), F(-0.45), F(z)])
+                      for x, _, z in pts])
+    assert np.allclose(a, b * cos_y, rtol=5e-3)
+
+
+def test_area_light_back_side_and_occluder(orc):
+    # the same light turned over (front side up) sends nothing down; an occluder
+    # covering the whole light blocks every shadow ray
+    verts = [[-0.1, -0.25, -0.1], [0.0, -0.25, 0.15], [0.15, -0.25, -0.05]]
+    sc, _ = _area_floor_scene(verts, 3.0, samples=8, spp=1, grid=4, half=0.05)
+    res = orc.render(sc)
+    assert np.all(res["rgba"][:, :3] == 0.0) and res["counts"]["shadow_rays"] == 0
+    verts = [[-0.1, 0.25, -0.1], [0.15, 0.25, -0.05], [0.0, 0.25, 0.15]]
+    sc, _ = _area_floor_scene(verts, 3.0, samples=8, spp=1, grid=4, half=0.05, y0=0.0)
+    open_ = orc.render(sc)["rgba"][:, 0]
+    sc.mesh = S.merge_meshes([sc.mesh, S.quad_mesh([-0.3, 0.1, -0.3], [-0.3, 0.1, 0.3], [0.3, 0.1, 0.3],
+                                                   [0.3, 0.1, -0.3], 0)])
+    shut = orc.render(sc)["rgba"][:, 0]
+    assert open_.min() > 0 and np.all(shut == 0.0)
