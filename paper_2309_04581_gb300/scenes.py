@@ -485,3 +485,36 @@ def seeded_view_sizes(n: int, purpose: int = 0, lo=(256, 256), hi=(1920, 1080)):
         h = int(round(math.exp(math.log(lo[1]) + t * (math.log(hi[1]) - math.log(lo[1])))))
         out.append((w, h))
     return out
+
+
+# ---------------------------------------------------------------------------
+# shadow-transmittance surrogate: hyper-parameters and seeded initial values
+# ---------------------------------------------------------------------------
+SNET_LEVELS = 8
+SNET_LOG2_T = 19
+SNET_WIDTH = 64
+SNET_IN = 32
+
+
+def snet_level_resolutions(n_levels: int = SNET_LEVELS, base: int = 16, finest: int = 512) -> np.ndarray:
+    """floor(base * b^l) with b = (finest/base)^(1/(n_levels-1)): 16, 26, 43, 70, 115, 190, 312, 512."""
+    return level_resolutions(n_levels, base, finest)
+
+
+def snet_n_params(log2_T: int = SNET_LOG2_T, n_levels: int = SNET_LEVELS) -> int:
+    W, D = SNET_WIDTH, SNET_IN
+    return n_levels * (1 << log2_T) * 2 + W * D + W + 2 * (W * W + W) + W + 1
+
+
+def snet_init(seed: int = 5, log2_T: int = SNET_LOG2_T, n_levels: int = SNET_LEVELS,
+              table_scale: float = 1e-4) -> np.ndarray:
+    """Flat FP32 parameter vector: table U(-1e-4, 1e-4); W1, W2, W3, W4
+    Xavier-uniform; biases 0 (layout: table, W1, b1, W2, b2, W3, b3, W4, b4)."""
+    rng = _rng(5, seed)
+    W, D = SNET_WIDTH, SNET_IN
+    parts = [rng.uniform(-table_scale, table_scale, n_levels * (1 << log2_T) * 2)]
+    for fan_out, fan_in in ((W, D), (W, W), (W, W), (1, W)):
+        lim = math.sqrt(6.0 / (fan_in + fan_out))
+        parts.append(rng.uniform(-lim, lim, fan_out * fan_in))
+        parts.append(np.zeros(fan_out))
+    return f32(np.concatenate(parts))
