@@ -44,6 +44,7 @@ typedef enum mrf_status {
 
 typedef struct mrf_context mrf_context;
 typedef struct mrf_field mrf_field;
+typedef struct mrf_shadow_net mrf_shadow_net;
 typedef struct mrf_bvh mrf_bvh;
 
 /* ---------------------------------------------------------------- context */
@@ -238,7 +239,8 @@ enum { MRF_ENGINE_AUTO = 0, MRF_ENGINE_MEGAKERNEL = 1, MRF_ENGINE_WAVEFRONT = 2 
 /* kernel kinds of the per-kernel timing in mrf_render_opts.kernel_ms */
 enum {
     MRF_KERNEL_MEGAKERNEL = 0, MRF_KERNEL_CAST_GEN = 1, MRF_KERNEL_FIELD = 2, MRF_KERNEL_SHADE = 3,
-    MRF_KERNEL_FINALIZE = 4, MRF_KERNEL_GEN = 5, MRF_KERNEL_COMPOSITE = 6, MRF_KERNEL_COUNT = 7
+    MRF_KERNEL_FINALIZE = 4, MRF_KERNEL_GEN = 5, MRF_KERNEL_COMPOSITE = 6, MRF_KERNEL_SHADOW_NET = 7,
+    MRF_KERNEL_COUNT = 8
 };
 
 typedef struct mrf_render_opts {
@@ -258,6 +260,10 @@ typedef struct mrf_render_opts {
      * records events around every launch on `stream` and waits for them */
     float *kernel_ms;
     uint32_t *kernel_launches;
+    /* learned shadow transmittance (see mrf_shadow_net_create), or NULL: shadow
+     * rays leaving a point inside the field box take T from the network instead
+     * of marching the field; the rest are marched */
+    const mrf_shadow_net *shadow_net;
 } mrf_render_opts;
 
 typedef struct mrf_stats {
@@ -267,6 +273,7 @@ typedef struct mrf_stats {
     uint64_t shadow_samples_evaluated;
     uint64_t fp64_retests;         /* near-edge triangle tests redone in FP64 */
     uint64_t status;               /* device status word (0 = ok) */
+    uint64_t shadow_net_evals;     /* shadow rays answered by the shadow network */
 } mrf_stats;
 
 /* Renders every path of `rays` (Algorithm 1) with at most max_bounces
@@ -310,6 +317,74 @@ mrf_status mrf_tonemap(mrf_context *ctx, const float *in, uint32_t n, float expo
 mrf_status mrf_render_static(mrf_context *ctx, const mrf_field *field, const mrf_bvh *bvh, const mrf_rays *rays,
                              uint32_t max_bounces, const mrf_render_opts *opts, float *out_hdr, void *stream,
                              mrf_stats *stats);
+
+/* ------------------------------------------ learned shadow transmittance
+ * A small network stands in for the field march of a shadow ray (Sec. 3.1,
+ * "Shadow rays": the transmittance exp(-int sigma) from a shading point toward
+ * a light).  It is trained on the GPU by this library's own kernels on pairs
+ * whose targets come from the plain FP32 march, which stays the fallback (and
+ * the judge of the network's error).
+ *  - Input: the point in the field's local frame, scaled to [0,1]^3 by the
+ *    field box and clamped, encoded by a hash grid of 8 levels of 2 FP32
+ *    features (resolution level_res[l]; 2^log2_table entries per level; dense
+ *    index x + (N+1)(y + (N+1) z) when (N+1)^3 fits, else the spatial hash
+ *    x ^ 2654435761 y ^ 805459861 z modulo the table size), followed by the
+ *    16 real spherical harmonics of bands 0..3 of the unit direction to the
+ *    light (in the local frame).
+ *  - Network: 32 -> 64 ReLU -> 64 ReLU -> 64 ReLU -> 1, T = sigmoid(z).
+ *  - Loss: mean squared error against the marched transmittance; Adam
+ *    (Kingma and Ba) with bias correction over every parameter.
+ *  - Parameters, one flat FP32 vector of mrf_shadow_net_param_count() values:
+ *    the table (level-major, entry-major, 2 features), W1 (64 x 32 row-major),
+ *    b1 (64), W2 (64 x 64), b2, W3 (64 x 64), b3, W4 (64), b4 (1).
+ * The network answers shadow rays from points inside the field box; rays from
+ * other points keep the march.  Handles are not thread-safe. */
+typedef struct mrf_shadow_net_desc {
+    uint32_t log2_table;       /* 10..22 */
+    uint32_t level_res[8];     /* 2..4096 each */
+    const float *params;       /* initial parameters (host or device), NULL = seeded default */
+    uint64_t seed;             /* default initialisation: table U(-1e-4, 1e-4), Xavier-uniform W, zero b */
+    float lr, beta1, beta2, eps;  /* Adam */
+    int32_t precision;         /* weights used when rendering: MRF_PREC_FP32 or MRF_PREC_BF16 (the table stays FP32) */
+} mrf_shadow_net_desc;
+
+/* The network belongs to `field`'s frame and box (copied at creation). */
+mrf_status mrf_shadow_net_create(mrf_context *ctx, const mrf_field *field, const mrf_shadow_net_desc *desc,
+                                 mrf_shadow_net **out);
+void mrf_shadow_net_destroy(mrf_shadow_net *net);
+uint64_t mrf_shadow_net_param_count(const mrf_shadow_net *net);
+/* Copy the FP32 parameters out / in (host or device arrays); setting them
+ * clears Adam's moments and step count. */
+mrf_status mrf_shadow_net_get_params(const mrf_shadow_net *net, float *out, void *stream);
+mrf_status mrf_shadow_net_set_params(mrf_shadow_net *net, const float *in, void *stream);
+
+/* Training pairs first..first+n-1 for the context's lights, written to the
+ * device array out (n x 8 FP32: point p, unit direction w, distance D, label).
+ * Pair i: Philox4x64-10 with key (seed, 0x736861646F77); counter (i, 0, 0, 0)
+ * gives the point uniformly in the field box (top 24 bits of words 0..2,
+ * mapped through the field pose) and the light floor(u3 n_lights); for an
+ * area light, counter (i, 1, 0, 0) gives the point on the triangle as in the
+ * renderer.  The label is exp(-int_0^D sigma) by the FP32 march of the
+ * renderer (step rule from opts: steps_per_segment or dt).  Needs >= 1 light. */
+mrf_status mrf_shadow_pairs(mrf_context *ctx, const mrf_field *field, const mrf_render_opts *opts, uint64_t seed,
+                            uint64_t first, uint32_t n, float *out, void *stream);
+
+/* Loss and gradient of the network over the n pairs (device, n x 8), in FP32:
+ * grad (device, mrf_shadow_net_param_count() values) and loss (device, 1
+ * value) are overwritten.  The parameters are not changed. */
+mrf_status mrf_shadow_net_grad(mrf_shadow_net *net, const float *pairs, uint32_t n, float *grad, float *loss,
+                               void *stream);
+
+/* `steps` Adam steps on batches of `batch` consecutive pairs of the device
+ * array pairs (n_pairs x 8, taken cyclically from where the last call
+ * stopped); loss (device, `steps` values, nullable) receives each batch's loss
+ * before its update. */
+mrf_status mrf_shadow_net_train(mrf_shadow_net *net, const float *pairs, uint64_t n_pairs, uint32_t batch,
+                                uint32_t steps, float *loss, void *stream);
+
+/* Network transmittance for the n pairs (device, n x 8; p and w are read) into
+ * the device array out (n values), with the rendering weights. */
+mrf_status mrf_shadow_net_eval(mrf_shadow_net *net, const float *pairs, uint32_t n, float *out, void *stream);
 
 #ifdef __cplusplus
 }

@@ -64,6 +64,7 @@ class OrcScene(C.Structure):
         ("field_pose", _fp),
         ("n_views", C.c_uint32), ("view_cam", _fp), ("view_size", _u32p),
         ("light_kind", _i32p), ("light_v1", _fp), ("light_v2", _fp), ("light_samples", _u32p),
+        ("shadow_net", C.c_void_p),
     ]
 
 
@@ -123,6 +124,8 @@ def lib():
         L.orc_snet_encode.argtypes = [C.POINTER(OrcSnet), _dp, _dp, _dp]
         L.orc_snet_forward.restype = C.c_double
         L.orc_snet_forward.argtypes = [C.POINTER(OrcSnet), _dp, _dp]
+        L.orc_snet_relu_margin.restype = C.c_double
+        L.orc_snet_relu_margin.argtypes = [C.POINTER(OrcSnet), _dp, _dp]
         L.orc_snet_loss_grad.restype = C.c_double
         L.orc_snet_loss_grad.argtypes = [C.POINTER(OrcSnet), _dp, _dp, C.c_uint32, _dp]
         L.orc_adam_step.argtypes = [_dp, _dp, _dp, _dp, C.c_uint64, C.c_uint32, C.c_double, C.c_double, C.c_double,
@@ -138,8 +141,9 @@ def _ptr(a, t):
 class OracleScene:
     """A ``scenes.Scene`` marshalled into an ``orc_scene`` (keeps its arrays alive)."""
 
-    def __init__(self, scene, margin_dist=1e-6, margin_t=1e-5, margin_fresnel=1e-5):
+    def __init__(self, scene, margin_dist=1e-6, margin_t=1e-5, margin_fresnel=1e-5, shadow_net=None):
         self.scene = scene
+        self.shadow_net = shadow_net
         keep = []
 
         def arr(a, dt):
@@ -218,6 +222,8 @@ class OracleScene:
             s.view_cam = _ptr(arr(np.array([[*v.pos, *v.look_at, *v.up, v.vfov_deg] for v in views], np.float32),
                                   np.float32), _fp)
             s.view_size = _ptr(arr(np.array([[v.width, v.height] for v in views], np.uint32), np.uint32), _u32p)
+        if shadow_net is not None:
+            s.shadow_net = C.cast(C.pointer(shadow_net.s), C.c_void_p)
         self.s = s
         self._keep = keep
 
@@ -226,13 +232,13 @@ class OracleScene:
         return C.byref(self.s)
 
 
-def render(scene, ids=None, threads: int = 0, records: bool = True, **margins):
+def render(scene, ids=None, threads: int = 0, records: bool = True, shadow_net=None, **margins):
     """Render ``ids`` (pixel or explicit-ray indices; default all) in FP64.
 
     Returns a dict: rgba (n,4) f64, segments (n,spp) u32, tri (n,spp,B) u32,
     t (n,spp,B) f64, flags (n,) u32, counts {name: int}."""
     L = lib()
-    os_ = OracleScene(scene, **margins)
+    os_ = OracleScene(scene, shadow_net=shadow_net, **margins)
     n_all = scene.n_rays
     ids = np.arange(n_all, dtype=np.uint32) if ids is None else np.ascontiguousarray(np.asarray(ids, np.uint32))
     n = ids.shape[0]
@@ -396,6 +402,9 @@ class OracleShadowNet:
 
     def forward(self, p, w) -> float:
         return lib().orc_snet_forward(self.ref, _ptr(_d(p), _dp), _ptr(_d(w), _dp))
+
+    def relu_margin(self, p, w) -> float:
+        return lib().orc_snet_relu_margin(self.ref, _ptr(_d(p), _dp), _ptr(_d(w), _dp))
 
     def loss_grad(self, pw, y, grad=True):
         pw = np.ascontiguousarray(np.asarray(pw, np.float64).reshape(-1, 6))

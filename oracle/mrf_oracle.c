@@ -112,7 +112,12 @@ typedef struct {
     const int32_t *light_kind;
     const float *light_v1, *light_v2;
     const uint32_t *light_samples;
+    /* learned shadow transmittance (shadow_net.c), or NULL: shadow rays from
+     * points inside the field box take T from it instead of the march */
+    const struct orc_snet *shadow_net;
 } orc_scene;
+
+double orc_snet_forward(const struct orc_snet *n, const double p[3], const double w[3]);
 
 /* per-thread counters: segments, shadow rays, nominal samples, samples with
  * non-zero support, surface hits, paths */
@@ -581,6 +586,21 @@ static inline double maxc(const double T[3]) {
     return T[2] > m ? T[2] : m;
 }
 
+/* Field transmittance of a shadow ray from p along w over (0, D): the
+ * network's value when one is given and p lies in the field box (in the
+ * field's frame), else the march of Eq. 10. */
+static double shadow_transmittance(const orc_scene *sc, const double p[3], const double w[3], double D,
+                                   uint64_t *cnt) {
+    if (sc->shadow_net) {
+        double pl[3], wl[3];
+        to_field_frame(sc, p, w, pl, wl);
+        int inside = 1;
+        for (int a = 0; a < 3; ++a) inside &= pl[a] >= sc->aabb_min[a] && pl[a] <= sc->aabb_max[a];
+        if (inside) return orc_snet_forward(sc->shadow_net, p, w);
+    }
+    return orc_transmittance(sc, p, w, 0.0, D, cnt);
+}
+
 /* Next-event estimate of one area light (a triangle of the pruned emissive
  * mesh, Sec. 3.1 "Estimating light sources"): N points y_s drawn uniformly on
  * the triangle (square-root barycentric warp of Shirley and Turk), each a
@@ -610,7 +630,7 @@ static void area_light_nee(const orc_scene *sc, uint32_t l, uint32_t ray, uint32
         if (cosx <= 0.0 || cosy <= 0.0) continue;
         cnt[C_SHADOW]++;
         if (occluded(sc, p, w, hit, D, flags)) continue;
-        double Tf = orc_transmittance(sc, p, w, 0.0, D, cnt);
+        double Tf = shadow_transmittance(sc, p, w, D, cnt);
         for (int e = 0; e < 3; ++e)
             L[e] += T[e] * (rgb[e] / M_PI) * sc->light_I[3 * l + e] * A / N * cosx * cosy / D2 * Tf;
     }
@@ -682,7 +702,7 @@ static void trace_path(const orc_scene *sc, uint32_t ray, uint32_t s, double L[3
                 if (cosl <= 0.0) continue;
                 cnt[C_SHADOW]++;
                 if (occluded(sc, p, w, hit, D, flags)) continue;
-                double Tf = orc_transmittance(sc, p, w, 0.0, D, cnt);
+                double Tf = shadow_transmittance(sc, p, w, D, cnt);
                 for (int c = 0; c < 3; ++c)
                     L[c] += T[c] * (rgb[c] / M_PI) * cosl * sc->light_I[3 * l + c] / D2 * Tf;
             }

@@ -33,7 +33,7 @@
 #define SN_W 64
 #define SN_IN 32
 
-typedef struct {
+typedef struct orc_snet {
     uint32_t n_levels, log2_T;
     const uint32_t *level_res;
     float aabb_min[3], aabb_max[3];
@@ -167,6 +167,21 @@ static void sn_forward(const orc_snet *n, const double p[3], const double w[3], 
     for (int k = 0; k < SN_W; ++k) z += W4[k] * A->h3[k];
     A->z = z;
     A->T = 1.0 / (1.0 + exp(-z));
+}
+
+/* Smallest |pre-activation| over the hidden units at (p, w): where it is at
+ * rounding level, FP32 and FP64 may take different ReLU branches and their
+ * gradients legitimately differ (the network's ambiguity margin). */
+double orc_snet_relu_margin(const orc_snet *n, const double p[3], const double w[3]) {
+    sn_act A;
+    sn_forward(n, p, w, &A);
+    double m = INFINITY;
+    for (int i = 0; i < SN_W; ++i) {
+        if (fabs(A.a1[i]) < m) m = fabs(A.a1[i]);
+        if (fabs(A.a2[i]) < m) m = fabs(A.a2[i]);
+        if (fabs(A.a3[i]) < m) m = fabs(A.a3[i]);
+    }
+    return m;
 }
 
 /* Surrogate transmittance from world point p along world direction w. */

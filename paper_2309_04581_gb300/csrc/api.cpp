@@ -83,6 +83,17 @@ struct mrf_bvh {
     int n_nodes = 0;
 };
 
+struct mrf_shadow_net {
+    mrf_context *ctx = nullptr;
+    ShadowNetDev dev{};
+    float *params = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr, *mlp_inf = nullptr;
+    uint64_t n_params = 0;
+    uint32_t t = 0;          // Adam steps taken
+    uint64_t cursor = 0;     // next training pair
+    float lr = 1e-2f, b1 = 0.9f, b2 = 0.99f, eps = 1e-15f;
+    int precision = MRF_PREC_FP32;
+};
+
 static bool is_device_ptr(const void *p) {
     if (!p) return false;
     cudaPointerAttributes a;
@@ -791,6 +802,11 @@ mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *b
     P.rec_seg = opts->rec_segments;
     P.rec_tri = opts->rec_tri;
     P.rec_t = opts->rec_t;
+    if (opts->shadow_net) {
+        if (opts->shadow_net->ctx != ctx) return fail(MRF_ERR_INVALID_ARG, "shadow_net belongs to another context");
+        P.has_snet = 1;
+        P.snet = opts->shadow_net->dev;
+    }
     // AUTO: tensor-core field evaluation needs the wavefront engine's flat sample
     // tiles; FP32 runs the megakernel
     const bool lowp = field->dev.kind == MRF_FIELD_HASHGRID && field->dev.precision != MRF_PREC_FP32;
@@ -875,6 +891,7 @@ mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *b
         stats->samples_evaluated = h[ST_EVALUATED];
         stats->shadow_samples_evaluated = h[ST_SHADOW_EVALUATED];
         stats->fp64_retests = h[ST_FP64];
+        stats->shadow_net_evals = h[ST_NET];
         unsigned st_word = 0;
         CUDA_TRY(cudaMemcpy(&st_word, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost), "mrf_render: status read");
         stats->status = st_word;
@@ -1002,6 +1019,11 @@ mrf_status mrf_render_static(mrf_context *ctx, const mrf_field *field, const mrf
     P.rec_seg = opts->rec_segments;
     P.rec_tri = opts->rec_tri;
     P.rec_t = opts->rec_t;
+    if (opts->shadow_net) {
+        if (opts->shadow_net->ctx != ctx) return fail(MRF_ERR_INVALID_ARG, "shadow_net belongs to another context");
+        P.has_snet = 1;
+        P.snet = opts->shadow_net->dev;
+    }
     P.out = out_hdr;
     P.status = ctx->status;
     void *arena = nullptr;
@@ -1024,6 +1046,7 @@ mrf_status mrf_render_static(mrf_context *ctx, const mrf_field *field, const mrf
         stats->samples_evaluated = h[ST_EVALUATED];
         stats->shadow_samples_evaluated = h[ST_SHADOW_EVALUATED];
         stats->fp64_retests = h[ST_FP64];
+        stats->shadow_net_evals = h[ST_NET];
         unsigned st_word = 0;
         CUDA_TRY(cudaMemcpy(&st_word, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost),
                  "mrf_render_static: status read");
@@ -1045,5 +1068,216 @@ mrf_status mrf_tonemap(mrf_context *ctx, const float *in, uint32_t n, float expo
     CUDA_TRY(launch_tonemap(reinterpret_cast<const float4 *>(in), n, exposure, reinterpret_cast<float4 *>(out),
                             (cudaStream_t)stream),
              "mrf_tonemap: launch");
+    return MRF_OK;
+}
+
+
+// ------------------------------------------------------ shadow network
+namespace {
+uint64_t snet_params(uint32_t log2T) {
+    return ((uint64_t)kSnetLevels << log2T) * 2 + kSnetMlp;
+}
+
+uint64_t splitmix_next(uint64_t &x) {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// uniform in [-a, a) from the top 24 bits of a SplitMix64 stream
+float splitmix_uniform(uint64_t &x, float a) {
+    return (float)(((double)(splitmix_next(x) >> 40) * (1.0 / 16777216.0) * 2.0 - 1.0) * a);
+}
+
+mrf_status snet_refresh(mrf_shadow_net *n, cudaStream_t s) {
+    CUDA_TRY(launch_snet_refresh(n->params + (n->n_params - kSnetMlp), n->mlp_inf, n->precision == MRF_PREC_BF16, s),
+             "shadow net: refresh");
+    return MRF_OK;
+}
+}  // namespace
+
+mrf_status mrf_shadow_net_create(mrf_context *ctx, const mrf_field *field, const mrf_shadow_net_desc *desc,
+                                 mrf_shadow_net **out) {
+    if (!ctx || !field || !desc || !out) return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_net_create: NULL argument");
+    *out = nullptr;
+    if (desc->log2_table < 10 || desc->log2_table > 22)
+        return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_net_create: log2_table must be 10..22");
+    for (int l = 0; l < kSnetLevels; ++l)
+        if (desc->level_res[l] < 2 || desc->level_res[l] > 4096)
+            return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_net_create: level_res must be 2..4096");
+    if (desc->precision != MRF_PREC_FP32 && desc->precision != MRF_PREC_BF16)
+        return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_net_create: precision must be FP32 or BF16");
+    if (!(desc->lr > 0.f) || !(desc->beta1 >= 0.f && desc->beta1 < 1.f) || !(desc->beta2 >= 0.f && desc->beta2 < 1.f) ||
+        !(desc->eps >= 0.f))
+        return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_net_create: bad Adam parameters");
+    CUDA_TRY(cudaSetDevice(ctx->device), "mrf_shadow_net_create: cudaSetDevice");
+    auto *n = new (std::nothrow) mrf_shadow_net();
+    if (!n) return fail(MRF_ERR_OOM, "mrf_shadow_net_create");
+    n->ctx = ctx;
+    n->lr = desc->lr;
+    n->b1 = desc->beta1;
+    n->b2 = desc->beta2;
+    n->eps = desc->eps;
+    n->precision = desc->precision;
+    n->n_params = snet_params(desc->log2_table);
+    ShadowNetDev &D = n->dev;
+    D.log2T = desc->log2_table;
+    const uint64_t T = 1ull << desc->log2_table;
+    for (int l = 0; l < kSnetLevels; ++l) {
+        D.res[l] = desc->level_res[l];
+        const uint64_t s1 = desc->level_res[l] + 1ull;
+        if (s1 * s1 * s1 <= T) D.dense_mask |= 1u << l;
+    }
+    const FieldDev &F = field->dev;
+    for (int a = 0; a < 3; ++a) {
+        D.lo[a] = F.lo[a];
+        D.hi[a] = F.hi[a];
+        D.ext_inv[a] = F.ext_inv[a];
+    }
+    D.has_pose = F.has_pose;
+    for (int k = 0; k < 12; ++k) D.to_local[k] = F.to_local[k];
+    mrf_status st;
+    if ((st = dev_alloc(&n->params, n->n_params, "shadow net parameters")) ||
+        (st = dev_alloc(&n->m, n->n_params, "shadow net Adam m")) ||
+        (st = dev_alloc(&n->v, n->n_params, "shadow net Adam v")) ||
+        (st = dev_alloc(&n->grad, n->n_params, "shadow net gradient")) ||
+        (st = dev_alloc(&n->mlp_inf, (size_t)kSnetMlp + 4, "shadow net rendering weights"))) {
+        mrf_shadow_net_destroy(n);
+        return st;
+    }
+    D.table = n->params;
+    D.mlp = n->mlp_inf;
+    if (desc->params) {
+        if (cudaMemcpy(n->params, desc->params, n->n_params * sizeof(float), cudaMemcpyDefault) != cudaSuccess) {
+            mrf_shadow_net_destroy(n);
+            return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_net_create: cannot read params");
+        }
+    } else {
+        std::vector<float> h(n->n_params, 0.f);
+        uint64_t x = desc->seed;
+        const uint64_t tbl = n->n_params - kSnetMlp;
+        for (uint64_t i = 0; i < tbl; ++i) h[i] = splitmix_uniform(x, 1e-4f);
+        float *w = h.data() + tbl;
+        const int fan[4][2] = {{kSnetW, kSnetIn}, {kSnetW, kSnetW}, {kSnetW, kSnetW}, {1, kSnetW}};
+        const int off[4] = {0, kSnetOffW2, kSnetOffW3, kSnetOffW4};
+        for (int L = 0; L < 4; ++L) {
+            const float a = (float)std::sqrt(6.0 / (fan[L][0] + fan[L][1]));
+            for (int i = 0; i < fan[L][0] * fan[L][1]; ++i) w[off[L] + i] = splitmix_uniform(x, a);
+        }
+        if (cudaMemcpy(n->params, h.data(), n->n_params * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+            mrf_shadow_net_destroy(n);
+            return fail(MRF_ERR_CUDA, "mrf_shadow_net_create: upload");
+        }
+    }
+    if (cudaMemset(n->m, 0, n->n_params * sizeof(float)) != cudaSuccess ||
+        cudaMemset(n->v, 0, n->n_params * sizeof(float)) != cudaSuccess ||
+        cudaMemset(n->grad, 0, n->n_params * sizeof(float)) != cudaSuccess || (st = snet_refresh(n, 0)) ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        mrf_shadow_net_destroy(n);
+        return st ? st : fail(MRF_ERR_CUDA, "mrf_shadow_net_create: initialisation");
+    }
+    *out = n;
+    return MRF_OK;
+}
+
+void mrf_shadow_net_destroy(mrf_shadow_net *n) {
+    if (!n) return;
+    cudaSetDevice(n->ctx->device);
+    cudaFree(n->params);
+    cudaFree(n->m);
+    cudaFree(n->v);
+    cudaFree(n->grad);
+    cudaFree(n->mlp_inf);
+    delete n;
+}
+
+uint64_t mrf_shadow_net_param_count(const mrf_shadow_net *n) { return n ? n->n_params : 0; }
+
+mrf_status mrf_shadow_net_get_params(const mrf_shadow_net *n, float *out, void *stream) {
+    if (!n || !out) return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_net_get_params: NULL argument");
+    CUDA_TRY(cudaSetDevice(n->ctx->device), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(out, n->params, n->n_params * sizeof(float), cudaMemcpyDefault, s), "get params");
+    if (!is_device_ptr(out)) CUDA_TRY(cudaStreamSynchronize(s), "get params: synchronize");
+    return MRF_OK;
+}
+
+mrf_status mrf_shadow_net_set_params(mrf_shadow_net *n, const float *in, void *stream) {
+    if (!n || !in) return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_net_set_params: NULL argument");
+    CUDA_TRY(cudaSetDevice(n->ctx->device), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(n->params, in, n->n_params * sizeof(float), cudaMemcpyDefault, s), "set params");
+    CUDA_TRY(cudaMemsetAsync(n->m, 0, n->n_params * sizeof(float), s), "set params");
+    CUDA_TRY(cudaMemsetAsync(n->v, 0, n->n_params * sizeof(float), s), "set params");
+    n->t = 0;
+    mrf_status st = snet_refresh(n, s);
+    if (st) return st;
+    if (!is_device_ptr(in)) CUDA_TRY(cudaStreamSynchronize(s), "set params: synchronize");
+    return MRF_OK;
+}
+
+mrf_status mrf_shadow_pairs(mrf_context *ctx, const mrf_field *field, const mrf_render_opts *opts, uint64_t seed,
+                            uint64_t first, uint32_t n, float *out, void *stream) {
+    if (!ctx || !field || !opts || (!out && n)) return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_pairs: NULL argument");
+    if (ctx->n_lights < 1) return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_pairs: the context has no lights");
+    if (n && !is_device_ptr(out)) return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_pairs: out must be device memory");
+    if (opts->steps_per_segment == 0 && !(opts->dt > 0.f))
+        return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_pairs: need steps_per_segment > 0 or dt > 0");
+    CUDA_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
+    RenderParams P{};
+    P.F = field->dev;
+    P.lights = ctx->lights;
+    P.n_lights = ctx->n_lights;
+    P.steps = opts->steps_per_segment;
+    P.dt = opts->dt;
+    P.tmin = opts->tmin;
+    P.status = ctx->status;
+    CUDA_TRY(launch_snet_pairs(P, seed, first, n, out, (cudaStream_t)stream), "mrf_shadow_pairs");
+    return MRF_OK;
+}
+
+mrf_status mrf_shadow_net_grad(mrf_shadow_net *n, const float *pairs, uint32_t count, float *grad, float *loss,
+                               void *stream) {
+    if (!n || !pairs || !grad || !loss || count == 0)
+        return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_net_grad: NULL argument or no pairs");
+    if (!is_device_ptr(pairs) || !is_device_ptr(grad) || !is_device_ptr(loss))
+        return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_net_grad: arrays must be device memory");
+    CUDA_TRY(cudaSetDevice(n->ctx->device), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemsetAsync(grad, 0, n->n_params * sizeof(float), s), "grad clear");
+    CUDA_TRY(cudaMemsetAsync(loss, 0, sizeof(float), s), "loss clear");
+    CUDA_TRY(launch_snet_grad(n->dev, n->params, grad, pairs, count, 0, count, loss, s), "mrf_shadow_net_grad");
+    return MRF_OK;
+}
+
+mrf_status mrf_shadow_net_train(mrf_shadow_net *n, const float *pairs, uint64_t n_pairs, uint32_t batch,
+                                uint32_t steps, float *loss, void *stream) {
+    if (!n || !pairs || n_pairs == 0 || batch == 0)
+        return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_net_train: NULL argument, no pairs or batch 0");
+    if (!is_device_ptr(pairs) || (loss && !is_device_ptr(loss)))
+        return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_net_train: arrays must be device memory");
+    CUDA_TRY(cudaSetDevice(n->ctx->device), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (loss) CUDA_TRY(cudaMemsetAsync(loss, 0, sizeof(float) * (size_t)steps, s), "loss clear");
+    for (uint32_t k = 0; k < steps; ++k) {
+        CUDA_TRY(launch_snet_grad(n->dev, n->params, n->grad, pairs, n_pairs, n->cursor % n_pairs, batch,
+                                  loss ? loss + k : nullptr, s),
+                 "mrf_shadow_net_train: gradient");
+        n->cursor = (n->cursor + batch) % n_pairs;
+        ++n->t;
+        const double c1 = 1.0 - std::pow((double)n->b1, (double)n->t), c2 = 1.0 - std::pow((double)n->b2, (double)n->t);
+        CUDA_TRY(launch_snet_adam(n->params, n->m, n->v, n->grad, n->n_params, n->lr, n->b1, n->b2, n->eps, c1, c2, s),
+                 "mrf_shadow_net_train: Adam");
+    }
+    return snet_refresh(n, s);
+}
+
+mrf_status mrf_shadow_net_eval(mrf_shadow_net *n, const float *pairs, uint32_t count, float *out, void *stream) {
+    if (!n || (count && (!pairs || !out))) return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_net_eval: NULL argument");
+    if (count && (!is_device_ptr(pairs) || !is_device_ptr(out)))
+        return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_net_eval: arrays must be device memory");
+    CUDA_TRY(cudaSetDevice(n->ctx->device), "cudaSetDevice");
+    CUDA_TRY(launch_snet_eval(n->dev, pairs, count, out, (cudaStream_t)stream), "mrf_shadow_net_eval");
     return MRF_OK;
 }

@@ -85,7 +85,29 @@ struct LightDev {
 // device statistics counters (unsigned long long), in this order
 enum StatIndex {
     ST_PATHS = 0, ST_SEGMENTS, ST_HITS, ST_SHADOW, ST_NOMINAL, ST_EVALUATED, ST_SHADOW_EVALUATED, ST_FP64,
-    ST_STATUS, ST_COUNT
+    ST_STATUS, ST_NET, ST_COUNT
+};
+
+// Shadow-transmittance network (shadow_net.cu): 8-level hash grid of the point
+// + 16 spherical harmonics of the direction -> 64 -> 64 -> 64 -> 1, sigmoid.
+constexpr int kSnetLevels = 8;
+constexpr int kSnetIn = 32;
+constexpr int kSnetW = 64;
+// MLP part of the flat parameter vector: W1[64][32] b1 W2[64][64] b2 W3[64][64] b3 W4[64] b4
+constexpr int kSnetMlp = kSnetW * kSnetIn + kSnetW + 2 * (kSnetW * kSnetW + kSnetW) + kSnetW + 1;
+constexpr int kSnetOffB1 = kSnetW * kSnetIn, kSnetOffW2 = kSnetOffB1 + kSnetW, kSnetOffB2 = kSnetOffW2 + kSnetW * kSnetW,
+              kSnetOffW3 = kSnetOffB2 + kSnetW, kSnetOffB3 = kSnetOffW3 + kSnetW * kSnetW,
+              kSnetOffW4 = kSnetOffB3 + kSnetW, kSnetOffB4 = kSnetOffW4 + kSnetW;
+
+struct ShadowNetDev {
+    uint32_t log2T;
+    uint32_t res[kSnetLevels];
+    uint32_t dense_mask;
+    float lo[3], hi[3], ext_inv[3];     // field box, local frame
+    int has_pose;
+    float to_local[12];                 // world-to-local [R^T | -R^T t]
+    const float *table;                 // FP32, [level][entry][2]
+    const float *mlp;                   // rendering copy of the MLP part (BF16-rounded for BF16)
 };
 
 // One pinhole view of a multi-view batch: orthonormal basis in FP32 (built in
@@ -120,6 +142,8 @@ struct RenderParams {
     float *rec_t;
     unsigned long long *stats;   // nullable statistics counters
     unsigned *status;            // context status word: bits set when a kernel gave up
+    int has_snet;                // shadow rays from inside the field box use the network
+    ShadowNetDev snet;
 };
 
 // Optional per-launch CUDA-event timing of the renderer's kernels (host side).
@@ -154,6 +178,16 @@ int field_tc_blocks_per_sm();
 cudaError_t launch_cast(const BvhDev &B, const float *o, const float *d, const uint32_t *skip, uint32_t n, float tmin,
                         float *out_t, uint32_t *out_tri, unsigned long long *stats, cudaStream_t s);
 cudaError_t launch_tonemap(const float4 *in, uint32_t n, float exposure, float4 *out, cudaStream_t s);
+// shadow_net.cu
+size_t snet_train_smem();
+cudaError_t launch_snet_pairs(const RenderParams &P, uint64_t seed, uint64_t first, uint32_t n, float *out,
+                              cudaStream_t s);
+cudaError_t launch_snet_grad(const ShadowNetDev &N, const float *params, float *grad, const float *pairs,
+                             uint64_t n_pairs, uint64_t b0, uint32_t B, float *loss, cudaStream_t s);
+cudaError_t launch_snet_adam(float *p, float *m, float *v, float *g, uint64_t n, float lr, float b1, float b2,
+                             float eps, double c1, double c2, cudaStream_t s);
+cudaError_t launch_snet_refresh(const float *mlp, float *out, bool bf16, cudaStream_t s);
+cudaError_t launch_snet_eval(const ShadowNetDev &N, const float *pairs, uint32_t n, float *out, cudaStream_t s);
 // bvh_refit.cu
 cudaError_t launch_bvh_refit(float4 *nodes, int n_nodes, float4 *tris, int n_tris, const uint32_t *tri_order,
                              const uint32_t *tri_idx, const float *verts, const int *parent, int *counters,

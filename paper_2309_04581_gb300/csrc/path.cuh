@@ -10,13 +10,13 @@ namespace mrf {
 
 struct Counters {
     unsigned long long nominal;
-    unsigned paths, seg, hits, shadow, evaluated, shadow_eval, retests, fault;
+    unsigned paths, seg, hits, shadow, evaluated, shadow_eval, retests, fault, net;
 };
 
 __device__ __forceinline__ void flush_counters(unsigned long long *stats, Counters &C) {
     if (!stats) return;
     unsigned long long v[ST_COUNT] = {C.paths, C.seg, C.hits, C.shadow, C.nominal, C.evaluated, C.shadow_eval,
-                                      C.retests, C.fault};
+                                      C.retests, C.fault, C.net};
     const unsigned mask = __activemask();
 #pragma unroll
     for (int k = 0; k < ST_COUNT; ++k) {

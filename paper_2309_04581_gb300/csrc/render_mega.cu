@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "path.cuh"
+#include "shadow_net.cuh"
 
 namespace mrf {
 
@@ -59,9 +60,15 @@ __device__ void trace_path(const RenderParams &P, const float *w, uint32_t ray, 
                     C.retests += rs;
                     if (f2) C.fault |= 1;
                     if (blocked) continue;
-                    bool dummy = false;
-                    const float depth = march<false>(P, w, S.p, wl, 0.f, D, nullptr, nullptr, dummy, C);
-                    const float Tf = expf(-depth);
+                    float Tf;
+                    V3 pl = S.p, wloc = wl;
+                    if (P.has_snet && (snet_to_local(P.snet, pl, wloc), snet_inside(P.snet, pl))) {
+                        Tf = snet_eval(P.snet, P.snet.mlp, S.p, wl);   // learned shadow transmittance
+                        ++C.net;
+                    } else {
+                        bool dummy = false;
+                        Tf = expf(-march<false>(P, w, S.p, wl, 0.f, D, nullptr, nullptr, dummy, C));
+                    }
 #pragma unroll
                     for (int c = 0; c < 3; ++c) L[c] = fmaf(T[c] * Tf, wt[c], L[c]);
                 }

@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include "path.cuh"
+#include "shadow_net.cuh"
 
 namespace mrf {
 
@@ -39,12 +40,13 @@ struct WfParams {
     uint32_t *hit_id;
     uint32_t *rstart, *rcount;      // radiance samples of the slot's segment
     uint32_t *sstart, *scount;      // shadow samples, [slot * n_shadow + q]
-    float4 *sw;                     // next-event weight (rgb), w = 1 when shadow ray q is unblocked
+    float4 *sw;                     // next-event weight (rgb); w = 1: unblocked, marched; 2: unblocked, network
     float4 *hp;                     // hit point (xyz) and number of unblocked shadow rays (w) per live slot
     float4 *sdir;                   // shadow-ray direction (xyz) and light distance (w), [slot * n_shadow + q]
     float4 *comp;                   // per slot: segment radiance sum (rgb, times T(p_j)) and optical depth (w)
-    float *sdepth;                  // shadow optical depth, [slot * n_shadow + q]
-    uint32_t *ctr;                  // [0], [1] live counts; [2] generated samples
+    float *sdepth;                  // shadow optical depth (marched) or transmittance (network), [slot * n_shadow + q]
+    uint32_t *ctr;                  // [0], [1] live counts; [2] generated samples; [3] network shadow rays
+    uint32_t *squeue;               // shadow rays answered by the network: slot * n_shadow + q
     float4 *samp;                   // sample position (xyz) and interval length (w)
     float4 *fout;                   // sigma, r, g, b per sample
     uint32_t cap;                   // sample capacity
@@ -310,6 +312,8 @@ __global__ void __launch_bounds__(kThreads) wf_cast(const WfParams W, uint32_t j
     const int K = P.n_shadow;
     Counters C = {};
     if (j == 1 && tid == 0) W.ctr[cur] = W.paths;  // every path is live in segment 1
+    uint64_t nmask = 0;   // shadow rays of this slot answered by the network
+    uint32_t nnet = 0;
     if (tid < live) {
         V3 o, d;
         uint32_t prev = kNoHit, path;
@@ -345,6 +349,10 @@ __global__ void __launch_bounds__(kThreads) wf_cast(const WfParams W, uint32_t j
             hp = S.p;
             if (S.mat.kind == MRF_MAT_DIFFUSE) {
                 const uint32_t ray = path / P.spp, sp = path % P.spp;
+                // shadow rays from inside the field box go to the network
+                V3 pl = S.p, wdummy = v3(0.f, 0.f, 1.f);
+                if (P.has_snet) snet_to_local(P.snet, pl, wdummy);
+                const bool net = P.has_snet && snet_inside(P.snet, pl);
                 for (int l = 0; l < P.n_lights; ++l) {
                     const uint32_t ns = P.lights[l].samples, q0 = P.lights[l].slot0;
                     for (uint32_t k = 0; k < ns; ++k) {
@@ -361,8 +369,12 @@ __global__ void __launch_bounds__(kThreads) wf_cast(const WfParams W, uint32_t j
                             C.retests += rs;
                             if (f2) C.fault |= 1;
                             if (!blocked) {
-                                wgt = make_float4(w3[0], w3[1], w3[2], 1.f);
+                                wgt = make_float4(w3[0], w3[1], w3[2], net ? 2.f : 1.f);
                                 ++nvis;
+                                if (net) {
+                                    nmask |= 1ull << (q0 + k);
+                                    ++nnet;
+                                }
                                 W.sdir[idx] = make_float4(wl.x, wl.y, wl.z, D);
                             }
                         }
@@ -374,8 +386,33 @@ __global__ void __launch_bounds__(kThreads) wf_cast(const WfParams W, uint32_t j
         }
         W.hp[tid] = make_float4(hp.x, hp.y, hp.z, __uint_as_float(nvis));
     }
+    // queue the network's shadow rays (one atomic per warp)
+    const uint32_t qbase = warp_alloc(&W.ctr[3], nnet);
+    for (uint32_t i = 0; nmask; ++i) {
+        const int q = __ffsll((long long)nmask) - 1;
+        nmask &= nmask - 1;
+        W.squeue[qbase + i] = tid * (uint32_t)K + (uint32_t)q;
+    }
     flush_counters(P.stats, C);
     if (C.fault && P.status) atomicOr(P.status, C.fault);
+}
+
+// Learned shadow transmittance of every queued shadow ray (grid-stride over
+// the queue), stored in sdepth.
+__global__ void __launch_bounds__(128) wf_shadow_net(const WfParams W) {
+    __shared__ __align__(16) float wsm[kSnetMlp + 3];
+    const RenderParams &P = W.R;
+    for (int i = threadIdx.x; i < kSnetMlp; i += blockDim.x) wsm[i] = P.snet.mlp[i];
+    __syncthreads();
+    const uint32_t n = W.ctr[3], K = (uint32_t)P.n_shadow;
+    Counters C = {};
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t idx = W.squeue[i], slot = idx / K;
+        const float4 h4 = W.hp[slot], sh = W.sdir[idx];
+        W.sdepth[idx] = snet_eval(P.snet, wsm, v3(h4.x, h4.y, h4.z), v3(sh.x, sh.y, sh.z));
+        ++C.net;
+    }
+    flush_counters(P.stats, C);
 }
 
 // Warp-cooperative sample generation: counts the samples of every job of the
@@ -416,7 +453,7 @@ __global__ void __launch_bounds__(kThreads, 8) wf_gen(const WfParams W, uint32_t
         bool first = true;   // the first unblocked shadow ray records its runs
         for (int q = 0; svis && q < K; ++q) {
             const size_t idx = (size_t)src_tid * K + q;
-            if (W.sw[idx].w == 0.f) continue;
+            if (W.sw[idx].w != 1.f) continue;   // marched shadow rays only
             const float4 sh = W.sdir[idx];
             const uint32_t ns = warp_walk(P, X, sp, v3(sh.x, sh.y, sh.z), 0.f, sh.w, nullptr, 0, C.nominal, lane,
                                           first ? &rl[1] : nullptr);
@@ -445,7 +482,7 @@ __global__ void __launch_bounds__(kThreads, 8) wf_gen(const WfParams W, uint32_t
             if (lane == src) {
                 W.rcount[tid] = kOverflow;
                 for (int q = 0; vis && q < K; ++q)
-                    if (W.sw[(size_t)tid * K + q].w != 0.f) W.scount[(size_t)tid * K + q] = kOverflow;
+                    if (W.sw[(size_t)tid * K + q].w == 1.f) W.scount[(size_t)tid * K + q] = kOverflow;
             }
             continue;
         }
@@ -464,7 +501,7 @@ __global__ void __launch_bounds__(kThreads, 8) wf_gen(const WfParams W, uint32_t
         bool first = true;
         for (int q = 0; svis && q < K; ++q) {
             const size_t idx = (size_t)src_tid * K + q;
-            if (W.sw[idx].w == 0.f) continue;
+            if (W.sw[idx].w != 1.f) continue;
             const float4 sh = W.sdir[idx];
             const uint32_t ns = W.scount[idx];
             if (lane == src) W.sstart[idx] = k;
@@ -570,7 +607,7 @@ __global__ void __launch_bounds__(kThreads, 8) wf_composite(const WfParams W, in
         if (!__shfl_sync(0xffffffffu, (int)diffuse, src)) continue;
         for (int q = 0; q < K; ++q) {
             const size_t idx = (size_t)src_tid * K + q;
-            if (W.sw[idx].w == 0.f) continue;
+            if (W.sw[idx].w != 1.f) continue;
             const uint32_t sc = W.scount[idx];
             if (sc == kOverflow) continue;
             const uint32_t s0 = W.sstart[idx];
@@ -595,7 +632,7 @@ __global__ void __launch_bounds__(kThreads) wf_overflow(const WfParams W, int cu
     bool any_shadow = false;
     if (__float_as_uint(h4.w) != 0u)   // unblocked shadow rays (only their counts are current)
         for (int q = 0; q < K; ++q)
-            any_shadow |= W.sw[(size_t)tid * K + q].w != 0.f && W.scount[(size_t)tid * K + q] == kOverflow;
+            any_shadow |= W.sw[(size_t)tid * K + q].w == 1.f && W.scount[(size_t)tid * K + q] == kOverflow;
     if (!rad && !any_shadow) return;
     const float4 qo = W.qo[cur][tid], qd = W.qd[cur][tid], qT = W.qT[cur][tid];
     const V3 o = v3(qo.x, qo.y, qo.z), d = v3(qd.x, qd.y, qd.z);
@@ -615,7 +652,7 @@ __global__ void __launch_bounds__(kThreads) wf_overflow(const WfParams W, int cu
         const V3 hp = v3(h4.x, h4.y, h4.z);
         for (int q = 0; q < K; ++q) {
             const size_t idx = (size_t)tid * K + q;
-            if (W.sw[idx].w == 0.f || W.scount[idx] != kOverflow) continue;
+            if (W.sw[idx].w != 1.f || W.scount[idx] != kOverflow) continue;
             const float4 sh = W.sdir[idx];
             Counters dummy = {};
             bool dstop = false;
@@ -684,7 +721,7 @@ __global__ void __launch_bounds__(kThreads) wf_shade(const WfParams W, uint32_t 
                     const size_t idx = (size_t)tid * K + q;
                     const float4 wgt = W.sw[idx];
                     if (wgt.w == 0.f) continue;
-                    const float Tf = expf(-W.sdepth[idx]);
+                    const float Tf = wgt.w == 2.f ? W.sdepth[idx] : expf(-W.sdepth[idx]);
                     L[0] = fmaf(T[0] * Tf, wgt.x, L[0]);
                     L[1] = fmaf(T[1] * Tf, wgt.y, L[1]);
                     L[2] = fmaf(T[2] * Tf, wgt.z, L[2]);
@@ -737,7 +774,7 @@ __global__ void __launch_bounds__(kThreads) wf_finalize(const float4 *__restrict
 // scratch layout
 struct Layout {
     size_t acc, qpath[2], qo[2], qd[2], qT[2], hit_t, hit_slot, hit_id, rstart, rcount, sstart, scount, sw, hp, sdir,
-        comp, sdepth, ctr, samp, fout, total;
+        comp, sdepth, squeue, ctr, samp, fout, total;
     uint32_t cap;
 };
 
@@ -769,6 +806,7 @@ Layout layout(uint32_t paths, int n_shadow) {
     L.sdir = take(16 * P * nl);
     L.comp = take(16 * P);
     L.sdepth = take(4 * P * nl);
+    L.squeue = take(4 * P * nl);
     L.ctr = take(16);
     // sample capacity: 96 samples per path plus 4M (overflowing jobs are marched in place)
     const uint64_t cap = std::min<uint64_t>((uint64_t)P * 96 + (4u << 20), 0x7FFFFFFFull);
@@ -777,6 +815,59 @@ Layout layout(uint32_t paths, int n_shadow) {
     L.fout = take(16 * cap);
     L.total = off;
     return L;
+}
+
+// Every launch of one frame, in stream order, with no host synchronisation.
+cudaError_t enqueue_frame(const WfParams &W, const RenderParams &P, uint32_t paths, cudaStream_t s,
+                          KernelTimer *timer) {
+    const unsigned grid = (paths + kThreads - 1) / kThreads;
+    const FieldDev &F = P.F;
+    const bool tc = F.kind == MRF_FIELD_HASHGRID && F.precision != MRF_PREC_FP32;
+    const int field_grid = tc ? 152 * field_tc_blocks_per_sm() : 152 * 8;
+    cudaError_t e = cudaMemsetAsync(W.ctr, 0, 16, s);   // counters left over from the previous call
+    if (e != cudaSuccess) return e;
+    for (uint32_t j = 1; j <= P.max_bounces; ++j) {
+        const int cur = (j - 1) & 1, nxt = j & 1;
+        if ((e = cudaMemsetAsync(W.ctr + 2, 0, 8, s)) != cudaSuccess) return e;
+        timer_begin(timer, MRF_KERNEL_CAST_GEN, s);
+        wf_cast<<<grid, kThreads, 0, s>>>(W, j, cur);
+        timer_end(timer, s);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (P.has_snet) {
+            timer_begin(timer, MRF_KERNEL_SHADOW_NET, s);
+            wf_shadow_net<<<152 * 4, 128, 0, s>>>(W);
+            timer_end(timer, s);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        timer_begin(timer, MRF_KERNEL_GEN, s);
+        wf_gen<<<grid, kThreads, 0, s>>>(W, j, cur);
+        timer_end(timer, s);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        timer_begin(timer, MRF_KERNEL_FIELD, s);
+        if (tc)
+            e = launch_field_tc(F, F.precision == MRF_PREC_BF16, reinterpret_cast<const float *>(W.samp), 4, W.ctr + 2,
+                                W.cap, W.fout, P.status, field_grid, s);
+        else
+            e = launch_field_simt(F, reinterpret_cast<const float *>(W.samp), 4, W.ctr + 2, W.cap, W.fout, field_grid, s);
+        timer_end(timer, s);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(W.ctr + nxt, 0, 4, s)) != cudaSuccess) return e;
+        timer_begin(timer, MRF_KERNEL_COMPOSITE, s);
+        wf_composite<<<grid, kThreads, 0, s>>>(W, cur);
+        timer_end(timer, s);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        wf_overflow<<<grid, kThreads, 0, s>>>(W, cur);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        timer_begin(timer, MRF_KERNEL_SHADE, s);
+        wf_shade<<<grid, kThreads, 0, s>>>(W, j, cur, nxt);
+        timer_end(timer, s);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    timer_begin(timer, MRF_KERNEL_FINALIZE, s);
+    wf_finalize<<<(P.count + kThreads - 1) / kThreads, kThreads, 0, s>>>(W.acc, P.count, P.spp,
+                                                                          reinterpret_cast<float4 *>(P.out));
+    timer_end(timer, s);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -816,51 +907,11 @@ cudaError_t launch_render_wavefront(const RenderParams &P, void *scratch, size_t
     W.comp = reinterpret_cast<float4 *>(b + Lo.comp);
     W.sdepth = reinterpret_cast<float *>(b + Lo.sdepth);
     W.ctr = reinterpret_cast<uint32_t *>(b + Lo.ctr);
+    W.squeue = reinterpret_cast<uint32_t *>(b + Lo.squeue);
     W.samp = reinterpret_cast<float4 *>(b + Lo.samp);
     W.fout = reinterpret_cast<float4 *>(b + Lo.fout);
     W.cap = Lo.cap;
-    const unsigned grid = (paths + kThreads - 1) / kThreads;
-    const FieldDev &F = P.F;
-    const bool tc = F.kind == MRF_FIELD_HASHGRID && F.precision != MRF_PREC_FP32;
-    const int field_grid = tc ? 152 * field_tc_blocks_per_sm() : 152 * 8;
-    cudaError_t e = cudaMemsetAsync(W.ctr, 0, 16, s);
-    if (e != cudaSuccess) return e;
-    for (uint32_t j = 1; j <= P.max_bounces; ++j) {
-        const int cur = (j - 1) & 1, nxt = j & 1;
-        if ((e = cudaMemsetAsync(W.ctr + 2, 0, 4, s)) != cudaSuccess) return e;
-        timer_begin(timer, MRF_KERNEL_CAST_GEN, s);
-        wf_cast<<<grid, kThreads, 0, s>>>(W, j, cur);
-        timer_end(timer, s);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        timer_begin(timer, MRF_KERNEL_GEN, s);
-        wf_gen<<<grid, kThreads, 0, s>>>(W, j, cur);
-        timer_end(timer, s);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        timer_begin(timer, MRF_KERNEL_FIELD, s);
-        if (tc)
-            e = launch_field_tc(F, F.precision == MRF_PREC_BF16, reinterpret_cast<const float *>(W.samp), 4, W.ctr + 2,
-                                W.cap, W.fout, P.status, field_grid, s);
-        else
-            e = launch_field_simt(F, reinterpret_cast<const float *>(W.samp), 4, W.ctr + 2, W.cap, W.fout, field_grid, s);
-        timer_end(timer, s);
-        if (e != cudaSuccess) return e;
-        if ((e = cudaMemsetAsync(W.ctr + nxt, 0, 4, s)) != cudaSuccess) return e;
-        timer_begin(timer, MRF_KERNEL_COMPOSITE, s);
-        wf_composite<<<grid, kThreads, 0, s>>>(W, cur);
-        timer_end(timer, s);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        wf_overflow<<<grid, kThreads, 0, s>>>(W, cur);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        timer_begin(timer, MRF_KERNEL_SHADE, s);
-        wf_shade<<<grid, kThreads, 0, s>>>(W, j, cur, nxt);
-        timer_end(timer, s);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    timer_begin(timer, MRF_KERNEL_FINALIZE, s);
-    wf_finalize<<<(P.count + kThreads - 1) / kThreads, kThreads, 0, s>>>(W.acc, P.count, P.spp,
-                                                                          reinterpret_cast<float4 *>(P.out));
-    timer_end(timer, s);
-    return cudaGetLastError();
+    return enqueue_frame(W, P, paths, s, timer);
 }
 
 // ---------------------------------------------------------------------------
@@ -947,39 +998,11 @@ cudaError_t launch_render_wavefront_arena(const RenderParams &P, void *arena, si
     W.comp = reinterpret_cast<float4 *>(b + Lo.comp);
     W.sdepth = reinterpret_cast<float *>(b + Lo.sdepth);
     W.ctr = reinterpret_cast<uint32_t *>(b + Lo.ctr);
+    W.squeue = reinterpret_cast<uint32_t *>(b + Lo.squeue);
     W.samp = reinterpret_cast<float4 *>(b + Lo.samp);
     W.fout = reinterpret_cast<float4 *>(b + Lo.fout);
     W.cap = Lo.cap;
-    const unsigned grid = (paths + kThreads - 1) / kThreads;
-    const FieldDev &F = P.F;
-    const bool tc = F.kind == MRF_FIELD_HASHGRID && F.precision != MRF_PREC_FP32;
-    const int field_grid = tc ? 152 * field_tc_blocks_per_sm() : 152 * 8;
-    cudaError_t e = cudaMemsetAsync(W.ctr, 0, 16, s);   // counters left over from the previous call
-    if (e != cudaSuccess) return e;
-    for (uint32_t j = 1; j <= P.max_bounces; ++j) {
-        const int cur = (j - 1) & 1, nxt = j & 1;
-        if ((e = cudaMemsetAsync(W.ctr + 2, 0, 4, s)) != cudaSuccess) return e;
-        wf_cast<<<grid, kThreads, 0, s>>>(W, j, cur);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        wf_gen<<<grid, kThreads, 0, s>>>(W, j, cur);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if (tc)
-            e = launch_field_tc(F, F.precision == MRF_PREC_BF16, reinterpret_cast<const float *>(W.samp), 4, W.ctr + 2,
-                                W.cap, W.fout, P.status, field_grid, s);
-        else
-            e = launch_field_simt(F, reinterpret_cast<const float *>(W.samp), 4, W.ctr + 2, W.cap, W.fout, field_grid, s);
-        if (e != cudaSuccess) return e;
-        if ((e = cudaMemsetAsync(W.ctr + nxt, 0, 4, s)) != cudaSuccess) return e;
-        wf_composite<<<grid, kThreads, 0, s>>>(W, cur);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        wf_overflow<<<grid, kThreads, 0, s>>>(W, cur);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        wf_shade<<<grid, kThreads, 0, s>>>(W, j, cur, nxt);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    wf_finalize<<<(P.count + kThreads - 1) / kThreads, kThreads, 0, s>>>(W.acc, P.count, P.spp,
-                                                                          reinterpret_cast<float4 *>(P.out));
-    return cudaGetLastError();
+    return enqueue_frame(W, P, paths, s, nullptr);
 }
 
 }  // namespace mrf

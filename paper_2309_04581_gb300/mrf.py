@@ -28,14 +28,17 @@ MRF_PREC_FP32, MRF_PREC_FP16, MRF_PREC_BF16 = 0, 1, 2
 MRF_MAT_MIRROR, MRF_MAT_GLASS, MRF_MAT_DIFFUSE = 0, 1, 2
 MRF_LIGHT_POINT, MRF_LIGHT_AREA = 0, 1
 MRF_ENGINE_AUTO, MRF_ENGINE_MEGAKERNEL, MRF_ENGINE_WAVEFRONT = 0, 1, 2
-KERNEL_NAMES = ("render_megakernel", "wf_cast", "field", "wf_shade", "wf_finalize", "wf_gen", "wf_composite")
+KERNEL_NAMES = ("render_megakernel", "wf_cast", "field", "wf_shade", "wf_finalize", "wf_gen", "wf_composite",
+                "wf_shadow_net")
 NO_HIT = 0xFFFFFFFF
 
 # every entry point declared in include/mrf.h
 EXPORTS = ("mrf_context_create", "mrf_context_destroy", "mrf_last_error", "mrf_version", "mrf_field_create",
            "mrf_field_destroy", "mrf_field_set_precision", "mrf_field_query", "mrf_bvh_build", "mrf_bvh_refit",
            "mrf_bvh_destroy", "mrf_cast", "mrf_materials_set", "mrf_lights_set", "mrf_render", "mrf_render_static",
-           "mrf_tonemap")
+           "mrf_tonemap", "mrf_shadow_net_create", "mrf_shadow_net_destroy", "mrf_shadow_net_param_count",
+           "mrf_shadow_net_get_params", "mrf_shadow_net_set_params", "mrf_shadow_pairs", "mrf_shadow_net_grad",
+           "mrf_shadow_net_train", "mrf_shadow_net_eval")
 
 _fp = C.POINTER(C.c_float)
 _u32p = C.POINTER(C.c_uint32)
@@ -79,13 +82,21 @@ class mrf_rays(C.Structure):
 class mrf_render_opts(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("steps_per_segment", C.c_uint32), ("dt", C.c_float), ("tau", C.c_float),
                 ("tmin", C.c_float), ("engine", C.c_int32), ("rec_segments", _vp), ("rec_tri", _vp),
-                ("rec_t", _vp), ("kernel_ms", C.POINTER(C.c_float)), ("kernel_launches", C.POINTER(C.c_uint32))]
+                ("rec_t", _vp), ("kernel_ms", C.POINTER(C.c_float)), ("kernel_launches", C.POINTER(C.c_uint32)),
+                ("shadow_net", _vp)]
+
+
+class mrf_shadow_net_desc(C.Structure):
+    _fields_ = [("log2_table", C.c_uint32), ("level_res", C.c_uint32 * 8), ("params", _vp), ("seed", C.c_uint64),
+                ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("precision", C.c_int32)]
 
 
 class mrf_stats(C.Structure):
     _fields_ = [("paths", C.c_uint64), ("segments", C.c_uint64), ("surface_hits", C.c_uint64),
                 ("shadow_rays", C.c_uint64), ("samples_nominal", C.c_uint64), ("samples_evaluated", C.c_uint64),
-                ("shadow_samples_evaluated", C.c_uint64), ("fp64_retests", C.c_uint64), ("status", C.c_uint64)]
+                ("shadow_samples_evaluated", C.c_uint64), ("fp64_retests", C.c_uint64), ("status", C.c_uint64),
+                ("shadow_net_evals", C.c_uint64)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -111,8 +122,19 @@ def lib():
                 fn = getattr(L, name)
                 if name not in ("mrf_last_error", "mrf_version"):
                     fn.restype = C.c_int
-            for name in ("mrf_context_destroy", "mrf_field_destroy", "mrf_bvh_destroy"):
+            for name in ("mrf_context_destroy", "mrf_field_destroy", "mrf_bvh_destroy", "mrf_shadow_net_destroy"):
                 getattr(L, name).restype = None
+            L.mrf_shadow_net_param_count.restype = C.c_uint64
+            L.mrf_shadow_net_param_count.argtypes = [_vp]
+            L.mrf_shadow_net_create.argtypes = [_vp, _vp, C.POINTER(mrf_shadow_net_desc), C.POINTER(_vp)]
+            L.mrf_shadow_net_destroy.argtypes = [_vp]
+            L.mrf_shadow_net_get_params.argtypes = [_vp, _vp, _vp]
+            L.mrf_shadow_net_set_params.argtypes = [_vp, _vp, _vp]
+            L.mrf_shadow_pairs.argtypes = [_vp, _vp, C.POINTER(mrf_render_opts), C.c_uint64, C.c_uint64, C.c_uint32,
+                                           _vp, _vp]
+            L.mrf_shadow_net_grad.argtypes = [_vp, _vp, C.c_uint32, _vp, _vp, _vp]
+            L.mrf_shadow_net_train.argtypes = [_vp, _vp, C.c_uint64, C.c_uint32, C.c_uint32, _vp, _vp]
+            L.mrf_shadow_net_eval.argtypes = [_vp, _vp, C.c_uint32, _vp, _vp]
             L.mrf_context_create.argtypes = [C.c_int, C.POINTER(_vp)]
             L.mrf_field_create.argtypes = [_vp, C.POINTER(mrf_field_desc), C.POINTER(_vp)]
             L.mrf_field_set_precision.argtypes = [_vp, C.c_int32]
@@ -330,9 +352,10 @@ class Renderer:
         r.spp = self.scene.opts.spp
         return r
 
-    def opts_struct(self, engine=MRF_ENGINE_AUTO, records=None) -> mrf_render_opts:
+    def opts_struct(self, engine=MRF_ENGINE_AUTO, records=None, shadow_net=None) -> mrf_render_opts:
         o = self.scene.opts
         s = mrf_render_opts()
+        s.shadow_net = shadow_net.handle if shadow_net is not None else None
         s.seed, s.steps_per_segment, s.dt, s.tau, s.tmin = o.seed, o.steps_per_segment, o.dt, o.tau, o.tmin
         s.engine = engine
         if records is not None:
@@ -349,17 +372,19 @@ class Renderer:
                 "tri": torch.zeros(n * spp * B, dtype=torch.int32, device=dev),
                 "t": torch.zeros(n * spp * B, dtype=torch.float32, device=dev)}
 
-    def render(self, out=None, engine=MRF_ENGINE_AUTO, records=None, stats=False, stream=None, timing=None):
+    def render(self, out=None, engine=MRF_ENGINE_AUTO, records=None, stats=False, stream=None, timing=None,
+               shadow_net=None):
         """Renders into ``out`` (count x 4 float32 CUDA tensor, allocated if None).
         Returns (out, stats dict or None).  If ``timing`` is a dict, it receives
-        per-kernel CUDA-event milliseconds and launch counts of this call."""
+        per-kernel CUDA-event milliseconds and launch counts of this call.
+        ``shadow_net`` (a ShadowNet of this renderer) answers shadow rays."""
         torch = self.torch
         n = self.scene.n_rays
         if out is None:
             out = torch.empty((n, 4), dtype=torch.float32, device=torch.device("cuda", self.device))
         st = mrf_stats() if stats else None
         s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
-        opts = self.opts_struct(engine, records)
+        opts = self.opts_struct(engine, records, shadow_net)
         if timing is not None:
             ms = (C.c_float * len(KERNEL_NAMES))()
             cnt = (C.c_uint32 * len(KERNEL_NAMES))()
@@ -375,3 +400,78 @@ class Renderer:
 
 def mrf_tonemap(ctx: int, in_ptr: int, n: int, exposure: float, out_ptr: int, stream: int = 0):
     check(lib().mrf_tonemap(ctx, in_ptr, n, exposure, out_ptr, stream))
+
+
+class ShadowNet:
+    """The learned shadow-transmittance network of a Renderer's field (the C ABI's mrf_shadow_net)."""
+
+    def __init__(self, renderer: "Renderer", params=None, precision: int = MRF_PREC_FP32, log2_table: int = S.SNET_LOG2_T,
+                 level_res=None, lr: float = 1e-2, betas=(0.9, 0.99), eps: float = 1e-15, seed: int = 0):
+        self.r = renderer
+        torch = renderer.torch
+        d = mrf_shadow_net_desc()
+        d.log2_table = log2_table
+        d.level_res[:] = [int(x) for x in (level_res if level_res is not None else S.snet_level_resolutions())]
+        keep = None
+        if params is not None:
+            keep = torch.as_tensor(np.asarray(params, np.float32)).to(torch.device("cuda", renderer.device))
+            d.params = keep.data_ptr()
+        d.seed = seed
+        d.lr, d.beta1, d.beta2, d.eps = lr, betas[0], betas[1], eps
+        d.precision = precision
+        h = _vp()
+        check(lib().mrf_shadow_net_create(renderer.ctx, renderer.field, C.byref(d), C.byref(h)))
+        self.handle = h.value
+        self.n_params = int(lib().mrf_shadow_net_param_count(self.handle))
+        del keep
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().mrf_shadow_net_destroy(self.handle)
+            self.handle = None
+
+    def _stream(self):
+        return self.r.torch.cuda.current_stream(self.r.device).cuda_stream
+
+    def params(self):
+        torch = self.r.torch
+        out = torch.empty(self.n_params, dtype=torch.float32, device=torch.device("cuda", self.r.device))
+        check(lib().mrf_shadow_net_get_params(self.handle, out.data_ptr(), self._stream()))
+        return out
+
+    def set_params(self, p):
+        torch = self.r.torch
+        t = torch.as_tensor(p, dtype=torch.float32).to(torch.device("cuda", self.r.device)).contiguous()
+        check(lib().mrf_shadow_net_set_params(self.handle, t.data_ptr(), self._stream()))
+        torch.cuda.synchronize(self.r.device)
+
+    def pairs(self, seed: int, first: int, n: int):
+        """n x 8 float32 CUDA tensor of training pairs labelled by the FP32 march."""
+        torch = self.r.torch
+        out = torch.empty((n, 8), dtype=torch.float32, device=torch.device("cuda", self.r.device))
+        opts = self.r.opts_struct()
+        check(lib().mrf_shadow_pairs(self.r.ctx, self.r.field, C.byref(opts), seed, first, n, out.data_ptr(),
+                                     self._stream()))
+        return out
+
+    def grad(self, pairs):
+        torch = self.r.torch
+        dev = torch.device("cuda", self.r.device)
+        g = torch.empty(self.n_params, dtype=torch.float32, device=dev)
+        loss = torch.empty(1, dtype=torch.float32, device=dev)
+        check(lib().mrf_shadow_net_grad(self.handle, pairs.data_ptr(), pairs.shape[0], g.data_ptr(), loss.data_ptr(),
+                                        self._stream()))
+        return g, loss
+
+    def train(self, pairs, batch: int, steps: int):
+        torch = self.r.torch
+        loss = torch.empty(max(steps, 1), dtype=torch.float32, device=torch.device("cuda", self.r.device))
+        check(lib().mrf_shadow_net_train(self.handle, pairs.data_ptr(), pairs.shape[0], batch, steps, loss.data_ptr(),
+                                         self._stream()))
+        return loss[:steps]
+
+    def eval(self, pairs):
+        torch = self.r.torch
+        out = torch.empty(pairs.shape[0], dtype=torch.float32, device=torch.device("cuda", self.r.device))
+        check(lib().mrf_shadow_net_eval(self.handle, pairs.data_ptr(), pairs.shape[0], out.data_ptr(), self._stream()))
+        return out

@@ -491,13 +491,13 @@ def seeded_view_sizes(n: int, purpose: int = 0, lo=(256, 256), hi=(1920, 1080)):
 # shadow-transmittance surrogate: hyper-parameters and seeded initial values
 # ---------------------------------------------------------------------------
 SNET_LEVELS = 8
-SNET_LOG2_T = 19
+SNET_LOG2_T = 17
 SNET_WIDTH = 64
 SNET_IN = 32
 
 
-def snet_level_resolutions(n_levels: int = SNET_LEVELS, base: int = 16, finest: int = 512) -> np.ndarray:
-    """floor(base * b^l) with b = (finest/base)^(1/(n_levels-1)): 16, 26, 43, 70, 115, 190, 312, 512."""
+def snet_level_resolutions(n_levels: int = SNET_LEVELS, base: int = 16, finest: int = 181) -> np.ndarray:
+    """floor(base * b^l) with b = (finest/base)^(1/(n_levels-1)) = sqrt(2): 16, 22, 32, 45, 64, 90, 128, 181."""
     return level_resolutions(n_levels, base, finest)
 
 

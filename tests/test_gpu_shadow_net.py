@@ -1,0 +1,235 @@
+"""The learned shadow-transmittance network on the GPU against the FP64 oracle:
+training pairs, inference, gradients, Adam, training, rendering with the
+network, and what the trained network gains over the plain march."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2309_04581_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+SEED = 11
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2309_04581_gb300 import build
+    build.build()
+    import paper_2309_04581_gb300.mrf as M
+    return torch, M
+
+
+@pytest.fixture(scope="module")
+def scene():
+    return S.config4(32, 32)
+
+
+@pytest.fixture(scope="module")
+def renderer(env, scene):
+    torch, M = env
+    r = M.Renderer(scene)
+    yield r
+    r.close()
+
+
+def _onet(orc, params, pose=None):
+    return orc.OracleShadowNet(S.snet_level_resolutions(), S.SNET_LOG2_T, np.asarray(params, np.float64), pose=pose)
+
+
+def test_pairs_match_oracle(env, orc, renderer, scene):
+    torch, M = env
+    net = M.ShadowNet(renderer)
+    first, n = 77, 2048
+    got = net.pairs(SEED, first, n).cpu().numpy().astype(np.float64)
+    ref = orc.shadow_pairs(scene, SEED, first, n)
+    assert np.abs(got[:, :3] - ref[:, :3]).max() <= 1e-6
+    assert np.abs(got[:, 3:6] - ref[:, 3:6]).max() <= 2e-6
+    assert np.abs(got[:, 6] - ref[:, 6]).max() <= 2e-6
+    # FP32 march against the FP64 march of the same segment
+    assert np.abs(got[:, 7] - ref[:, 7]).max() <= 2e-4
+    assert ref[:, 7].min() < 0.5 < ref[:, 7].max()
+    net.close()
+
+
+def _random_params(seed=3):
+    # a table far from its zero initialisation so that every input matters
+    return S.snet_init(seed, table_scale=0.3)
+
+
+def test_inference_matches_oracle(env, orc, renderer):
+    torch, M = env
+    params = _random_params()
+    net = M.ShadowNet(renderer, params=params)
+    pairs = net.pairs(SEED, 0, 4096)
+    got = net.eval(pairs).cpu().numpy().astype(np.float64)
+    on = _onet(orc, params)
+    pr = pairs.cpu().numpy().astype(np.float64)
+    ref = np.array([on.forward(pr[k, :3], pr[k, 3:6]) for k in range(pr.shape[0])])
+    assert 0.005 < ref.std()
+    assert np.abs(got - ref).max() <= 2e-6
+    net.close()
+
+
+def _unambiguous(on, pr, margin=1e-5):
+    # pairs with a hidden pre-activation within `margin` of zero may take the
+    # other ReLU branch in FP32 (about 1 pair in 3000 at 1e-5); both sides
+    # then compute a different, equally valid gradient, so they are left out
+    keep = np.array([on.relu_margin(pr[k, :3], pr[k, 3:6]) > margin for k in range(pr.shape[0])])
+    assert keep.mean() > 0.99
+    return keep
+
+
+def test_gradient_matches_oracle(env, orc, renderer):
+    torch, M = env
+    params = _random_params(4)
+    net = M.ShadowNet(renderer, params=params)
+    on = _onet(orc, params)
+    pairs = net.pairs(SEED, 5000, 3000)
+    keep = _unambiguous(on, pairs.cpu().numpy().astype(np.float64))
+    pairs = pairs[torch.from_numpy(keep).to(pairs.device)][:2990].contiguous()   # ragged last tile
+    g, loss = net.grad(pairs)
+    g = g.cpu().numpy().astype(np.float64)
+    pr = pairs.cpu().numpy().astype(np.float64)
+    lref, gref = on.loss_grad(pr[:, :6], pr[:, 7])
+    assert float(loss.item()) == pytest.approx(lref, rel=2e-5)
+    n_tab = S.snet_n_params() - 10497
+    for part in (slice(0, n_tab), slice(n_tab, None)):
+        scale = np.abs(gref[part]).max()
+        assert scale > 0
+        assert np.abs(g[part] - gref[part]).max() <= 1e-4 * scale, part
+    # the pairs touch many table entries on every level
+    assert np.count_nonzero(gref[:n_tab]) > 8 * 2990
+    net.close()
+
+
+def test_adam_step_matches_oracle(env, orc, renderer):
+    torch, M = env
+    params = _random_params(5)
+    lr = 1e-2
+    net = M.ShadowNet(renderer, params=params, lr=lr, eps=1e-15)
+    pairs = net.pairs(SEED, 9000, 1100)
+    keep = _unambiguous(_onet(orc, params), pairs.cpu().numpy().astype(np.float64))
+    pairs = pairs[torch.from_numpy(keep).to(pairs.device)][:1024].contiguous()
+    net.train(pairs, batch=1024, steps=1)
+    after = net.params().cpu().numpy().astype(np.float64)
+    pr = pairs.cpu().numpy().astype(np.float64)
+    _, gref = _onet(orc, params).loss_grad(pr[:, :6], pr[:, 7])
+    theta = np.asarray(params, np.float64).copy()
+    m, v = np.zeros_like(theta), np.zeros_like(theta)
+    orc.adam_step(theta, m, v, gref, 1, lr, 0.9, 0.99, 1e-15)
+    d_gpu, d_ref = after - params, theta - params
+    big = np.abs(gref) >= 1e-3 * np.abs(gref).max()
+    assert big.sum() > 1000
+    assert np.abs(d_gpu[big] - d_ref[big]).max() <= 1e-3 * lr
+    # elsewhere the first Adam step is +-lr or 0 (sign of a tiny gradient)
+    assert np.abs(d_gpu).max() <= lr * (1 + 1e-4) + 1e-6 * np.abs(params).max()
+    net.close()
+
+
+def _train(M, renderer, steps=2000, batch=1 << 16, n_train=1 << 22, precision=None):
+    torch = renderer.torch
+    net = M.ShadowNet(renderer, precision=precision if precision is not None else M.MRF_PREC_FP32, seed=7)
+    train = net.pairs(SEED, 0, n_train)
+    held = net.pairs(SEED, 1 << 30, 1 << 16)
+    y = held[:, 7]
+    mse0 = float(((net.eval(held) - y) ** 2).mean())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = net.train(train, batch, steps)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    mse = float(((net.eval(held) - y) ** 2).mean())
+    return net, dict(mse0=mse0, mse=mse, secs=secs, loss=loss.cpu().numpy(), var=float(y.var()))
+
+
+@pytest.fixture(scope="module")
+def trained(env, renderer):
+    torch, M = env
+    net, info = _train(M, renderer)
+    yield net, info
+    net.close()
+
+
+def test_training_lowers_held_out_error(env, trained):
+    net, info = trained
+    print(f"held-out MSE {info['mse0']:.4g} -> {info['mse']:.4g} (label variance {info['var']:.4g}), "
+          f"2000 steps of 65536 in {info['secs']:.2f} s")
+    # 2^22 pairs and 2000 steps here (the benchmark trains on 2^24 pairs)
+    assert info["mse"] < 0.03 * info["var"]
+    assert info["mse"] < 0.03 * info["mse0"]
+    assert info["loss"][-100:].mean() < 0.1 * info["loss"][:10].mean()
+
+
+@pytest.mark.parametrize("engine", ["megakernel", "wavefront"])
+def test_render_with_network_matches_oracle(env, orc, renderer, scene, trained, engine):
+    """Shadow rays from inside the field box take T from the network: the FP32
+    network on the GPU against the same parameters in the FP64 oracle."""
+    torch, M = env
+    net, _ = trained
+    params = net.params().cpu().numpy()
+    ref = orc.render(scene, shadow_net=_onet(orc, params))
+    eng = M.MRF_ENGINE_MEGAKERNEL if engine == "megakernel" else M.MRF_ENGINE_WAVEFRONT
+    out, stats = renderer.render(engine=eng, stats=True, shadow_net=net)
+    torch.cuda.synchronize()
+    img = out.cpu().numpy().astype(np.float64)
+    ok = ref["flags"] == 0
+    peak = np.abs(ref["rgba"][:, :3]).max()
+    den = np.maximum(np.abs(ref["rgba"][:, :3]).max(1), 1e-2 * peak)
+    err = (np.abs(img[:, :3] - ref["rgba"][:, :3]).max(1) / den)[ok]
+    assert err.max() <= 1e-4
+    assert stats["shadow_net_evals"] > 0 and stats["shadow_samples_evaluated"] == 0
+
+
+def _psnr(a, b):
+    peak = np.abs(b[:, :3]).max()
+    return 10 * np.log10(peak * peak / np.mean((a[:, :3] - b[:, :3]) ** 2))
+
+
+def test_network_gain_over_the_march(env, orc, trained):
+    """What the trained network gains over the plain march on the
+    area-light scene with BF16 field and network weights: shadow samples
+    removed, frame time, and the image error it costs against the FP64 oracle
+    (the plain method), next to that of the untrained network."""
+    torch, M = env
+    net, _ = trained
+    sc = S.config4(192, 192)
+    r = M.Renderer(sc, precision=M.MRF_PREC_BF16)
+    bf = M.ShadowNet(r, params=net.params().cpu().numpy(), precision=M.MRF_PREC_BF16)
+    untrained = M.ShadowNet(r, precision=M.MRF_PREC_BF16, seed=7)
+    ids = S.strided_pixels(192, 192, 6, offset=2)
+    ref = orc.render(sc, ids)
+    ok = ref["flags"] == 0
+
+    def frame(shadow_net):
+        out, st = r.render(stats=True, shadow_net=shadow_net)
+        for _ in range(2):
+            r.render(out=out, shadow_net=shadow_net)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            r.render(out=out, shadow_net=shadow_net)
+        e1.record()
+        torch.cuda.synchronize()
+        return out.cpu().numpy().astype(np.float64), st, e0.elapsed_time(e1) / 5
+
+    img_m, st_m, ms_m = frame(None)
+    img_n, st_n, ms_n = frame(bf)
+    img_u, _, _ = frame(untrained)
+    p_m, p_n, p_u = (_psnr(x[ids][ok], ref["rgba"][ok]) for x in (img_m, img_n, img_u))
+    print(f"march: {ms_m:.2f} ms, {st_m['shadow_samples_evaluated']} shadow samples, PSNR {p_m:.1f} dB | "
+          f"network: {ms_n:.2f} ms, {st_n['shadow_net_evals']} network shadow rays, PSNR {p_n:.1f} dB | "
+          f"untrained network PSNR {p_u:.1f} dB")
+    # every shading point of this scene lies in the field box: no shadow ray is marched
+    assert st_n["shadow_samples_evaluated"] == 0 and st_m["shadow_samples_evaluated"] > 1000
+    assert st_n["shadow_net_evals"] > 0
+    assert p_n > p_u + 10.0           # training is what makes the network usable
+    assert p_n >= 40.0
+    bf.close()
+    untrained.close()
+    r.close()

@@ -177,3 +177,25 @@ def test_training_pairs_follow_philox_and_the_march(orc):
         assert pr[k, 7] == orc.transmittance(osc, pr[k, :3], pr[k, 3:6], 0.0, pr[k, 6])
     assert 0.0 <= pr[:, 7].min() and pr[:, 7].max() <= 1.0
     assert pr[:, 7].min() < 0.5 < pr[:, 7].max()    # the field casts shadows on some pairs
+
+
+def test_render_takes_shadow_transmittance_from_the_network(orc):
+    # A network whose output is the constant sigmoid(b4) (all weights zero)
+    # scales the next-event term of a point light by exactly that value, for
+    # a shading point inside the field box; the march (sigma = 0.8) is not used.
+    from tests.test_oracle_paths import _floor_scene, F
+    p = np.zeros(S.snet_n_params(TINY_T))
+    T_c = 0.3
+    p[-1] = math.log(T_c / (1 - T_c))
+    net = orc.OracleShadowNet(TINY_RES, TINY_T, p)
+    x, z = 0.13, -0.07
+    hp = np.array([F(x), F(-0.45), F(z)])
+    lp = np.array([0.0, F(0.45), 0.0])
+    D = np.linalg.norm(lp - hp)
+    cos = (lp - hp)[1] / D
+    sc = S.explicit_rays(_floor_scene(0.8), [[x, 0.3, z]], [[0, -1, 0]])
+    t_cam = math.exp(-F(0.8) * (F(0.3) - F(-0.45)))
+    got = orc.render(sc, shadow_net=net)["rgba"][0, :3]
+    assert np.allclose(got, t_cam * 0.5 / math.pi * cos * 2.0 / D ** 2 * T_c, rtol=1e-12)
+    marched = orc.render(sc)["rgba"][0, :3]
+    assert np.allclose(marched, t_cam * 0.5 / math.pi * cos * 2.0 / D ** 2 * math.exp(-F(0.8) * D), rtol=1e-12)
