@@ -196,6 +196,7 @@ typedef struct mrf_light {
     float intensity[3];    /* POINT: intensity I; AREA: radiance Le of the front side */
     float v1[3], v2[3];    /* AREA only */
     uint32_t samples;      /* AREA only: shadow rays per diffuse hit */
+    float mask_strength;   /* r_src of the field-sample shadow mask, in [0, 1] (see mrf_render_opts) */
 } mrf_light;
 /* Replace the context's material / light tables (host or device arrays, n <= 65535). */
 mrf_status mrf_materials_set(mrf_context *ctx, const mrf_material *mats, uint32_t n);
@@ -264,6 +265,12 @@ typedef struct mrf_render_opts {
      * rays leaving a point inside the field box take T from the network instead
      * of marching the field; the rest are marched */
     const mrf_shadow_net *shadow_net;
+    /* shadow mask m(p_t) of Sec. 3.1 on the field's samples (0 = off): a ray
+     * from every field sample with sigma > 0 toward each light with
+     * mask_strength r > 0 (a point light's position, an area light's centroid);
+     * each light a mesh blocks scales the sample's radiance by 1 - r, so
+     * L += T alpha m r(p).  The density and throughput are unchanged. */
+    int32_t shadow_mask;
 } mrf_render_opts;
 
 typedef struct mrf_stats {
@@ -317,6 +324,30 @@ mrf_status mrf_tonemap(mrf_context *ctx, const float *in, uint32_t n, float expo
 mrf_status mrf_render_static(mrf_context *ctx, const mrf_field *field, const mrf_bvh *bvh, const mrf_rays *rays,
                              uint32_t max_bounces, const mrf_render_opts *opts, float *out_hdr, void *stream,
                              mrf_stats *stats);
+
+/* --------------------------------------------------------- captured frames
+ * One render call captured once into a CUDA graph and replayed: every launch
+ * of a frame (Algorithm 1 over all paths) goes to the GPU as one graph, with
+ * no per-launch host work.  For sequences whose camera and outputs stay put
+ * while the scene's contents change (a BVH refit per frame for deforming
+ * meshes, new ray origins in the same arrays, a shadow network in training).
+ *  - The graph keeps the device addresses seen at capture: out_hdr, explicit
+ *    ray arrays, records, and the field's, BVH's and shadow network's memory.
+ *    Their contents are read at every replay.
+ *  - Camera records, materials and lights are copied at capture; later
+ *    mrf_materials_set / mrf_lights_set calls do not change the frame.
+ *  - The frame owns its scratch memory and statistics.  Replays of one frame
+ *    must not overlap on the GPU.
+ *  - MRF_ERR_INVALID_ARG for a host out_hdr, host explicit rays or per-kernel
+ *    timing; other arguments as mrf_render.
+ * mrf_frame_stats waits for `stream` and returns the last replay's
+ * statistics. */
+typedef struct mrf_frame mrf_frame;
+mrf_status mrf_frame_capture(mrf_context *ctx, const mrf_field *field, const mrf_bvh *bvh, const mrf_rays *rays,
+                             uint32_t max_bounces, const mrf_render_opts *opts, float *out_hdr, mrf_frame **out);
+mrf_status mrf_frame_replay(mrf_frame *frame, void *stream);
+mrf_status mrf_frame_stats(mrf_frame *frame, void *stream, mrf_stats *stats);
+void mrf_frame_destroy(mrf_frame *frame);
 
 /* ------------------------------------------ learned shadow transmittance
  * A small network stands in for the field march of a shadow ray (Sec. 3.1,

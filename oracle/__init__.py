@@ -64,7 +64,7 @@ class OrcScene(C.Structure):
         ("field_pose", _fp),
         ("n_views", C.c_uint32), ("view_cam", _fp), ("view_size", _u32p),
         ("light_kind", _i32p), ("light_v1", _fp), ("light_v2", _fp), ("light_samples", _u32p),
-        ("shadow_net", C.c_void_p),
+        ("shadow_net", C.c_void_p), ("shadow_mask", C.c_int32), ("light_mask", _fp),
     ]
 
 
@@ -203,6 +203,9 @@ class OracleScene:
         s.n_lights = len(lights)
         s.light_pos = _ptr(arr(np.array([x.pos for x in lights] or [(0, 0, 0)], np.float32), np.float32), _fp)
         s.light_I = _ptr(arr(np.array([x.intensity for x in lights] or [(0, 0, 0)], np.float32), np.float32), _fp)
+        if getattr(scene.opts, "shadow_mask", False):
+            s.shadow_mask = 1
+            s.light_mask = _ptr(arr(np.array([x.mask_strength for x in lights] or [0.0], np.float32), np.float32), _fp)
         if any(x.kind != 0 for x in lights):
             s.light_kind = _ptr(arr(np.array([x.kind for x in lights], np.int32), np.int32), _i32p)
             s.light_v1 = _ptr(arr(np.array([x.v1 if x.v1 is not None else (0, 0, 0) for x in lights], np.float32),

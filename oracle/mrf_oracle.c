@@ -115,6 +115,11 @@ typedef struct {
     /* learned shadow transmittance (shadow_net.c), or NULL: shadow rays from
      * points inside the field box take T from it instead of the march */
     const struct orc_snet *shadow_net;
+    /* shadow mask of Sec. 3.1 on the field's samples: when non-zero, a sample's
+     * radiance is scaled by prod over lights of (1 - light_mask[l]) for every
+     * light whose shadow ray from the sample is blocked by a mesh */
+    int32_t shadow_mask;
+    const float *light_mask;
 } orc_scene;
 
 double orc_snet_forward(const struct orc_snet *n, const double p[3], const double w[3]);
@@ -375,6 +380,8 @@ static void to_field_frame(const orc_scene *sc, const double o[3], const double 
  *   alpha_i = 1 - exp(-sigma_i delta_i); L += T alpha_i r_i; T *= exp(-sigma_i delta_i).
  * T is the RGB path throughput (it carries T(p_j) into the segment).  Returns
  * 1 if the path ended inside the march because max(T) fell below tau. */
+static double shadow_mask(const orc_scene *sc, const double pw[3], uint32_t *flags);
+
 static int march(const orc_scene *sc, const double ow[3], const double dw[3], double a, double b, double T[3],
                  double L[3], uint64_t *cnt, uint32_t *flags) {
     double o[3], d[3];
@@ -395,8 +402,13 @@ static int march(const orc_scene *sc, const double ow[3], const double dw[3], do
         double p[3] = {o[0] + tm * d[0], o[1] + tm * d[1], o[2] + tm * d[2]}, sigma, rgb[3];
         cnt[C_NOMINAL]++;
         cnt[C_SUPPORTED] += orc_field_eval(sc, p, &sigma, rgb);
-        double att = exp(-sigma * delta), alpha = -expm1(-sigma * delta);
-        for (int c = 0; c < 3; ++c) { L[c] += T[c] * alpha * rgb[c]; T[c] *= att; }
+        double att = exp(-sigma * delta), alpha = -expm1(-sigma * delta), m = 1.0;
+        if (sc->shadow_mask && sigma > 0.0) {
+            /* the sample in world space: the pose keeps ray parameters */
+            double pw[3] = {ow[0] + tm * dw[0], ow[1] + tm * dw[1], ow[2] + tm * dw[2]};
+            m = shadow_mask(sc, pw, flags);
+        }
+        for (int c = 0; c < 3; ++c) { L[c] += T[c] * alpha * m * rgb[c]; T[c] *= att; }
         if (sc->tau > 0) {
             double m = T[0] > T[1] ? T[0] : T[1];
             if (T[2] > m) m = T[2];
@@ -520,10 +532,13 @@ uint32_t orc_closest_hit(const orc_scene *sc, const double o[3], const double d[
     return best_id;
 }
 
-/* Any mesh between the shadow-ray origin and the light, t in (tmin, dist). */
+/* Any mesh between the shadow-ray origin and the light, t in (tmin, dist).
+ * The decision is flagged as ambiguous only when it rests on near-edge or
+ * near-endpoint candidates: one triangle hit well inside its edges and well
+ * inside (tmin, dist) settles "blocked" whatever the others do. */
 static int occluded(const orc_scene *sc, const double o[3], const double d[3], uint32_t skip, double dist,
                     uint32_t *flags) {
-    int blocked = 0;
+    int blocked = 0, robust = 0, doubtful = 0;
     const double md = sc->margin_dist;
     for (uint32_t i = 0; i < sc->n_tris; ++i) {
         if (i == skip) continue;
@@ -531,13 +546,40 @@ static int occluded(const orc_scene *sc, const double o[3], const double d[3], u
         tri_verts(sc, i, v0, v1, v2);
         int hit = orc_intersect_tri(o, d, v0, v1, v2, sc->tmin, &t, &b1, &b2);
         if (!isfinite(t)) continue;
+        int near = 0;
         if (t > sc->tmin && t < dist * (1.0 + sc->margin_t)) {
-            if (fabs(edge_distance(v0, v1, v2, b1, b2)) <= md) *flags |= ORC_FLAG_SHADOW;
-            if (hit && fabs(t - dist) <= sc->margin_t * dist) *flags |= ORC_FLAG_SHADOW;
+            if (fabs(edge_distance(v0, v1, v2, b1, b2)) <= md) near = 1;
+            if (hit && fabs(t - dist) <= sc->margin_t * dist) near = 1;
         }
-        if (hit && t < dist) blocked = 1;
+        doubtful |= near;
+        if (hit && t < dist) {
+            blocked = 1;
+            if (!near) robust = 1;
+        }
     }
+    if (doubtful && !robust) *flags |= ORC_FLAG_SHADOW;
     return blocked;
+}
+
+/* Shadow mask m(p_t) of Sec. 3.1 ("Shadow rays" and Algorithm 1, step 3): a
+ * ray from the field sample toward each light (a point light's position, an
+ * area light's centroid); each light that a mesh blocks multiplies m by
+ * 1 - r_src, its mask strength.  Unblocked: m = 1. */
+static double shadow_mask(const orc_scene *sc, const double pw[3], uint32_t *flags) {
+    double m = 1.0;
+    for (uint32_t l = 0; l < sc->n_lights; ++l) {
+        double r = sc->light_mask ? sc->light_mask[l] : 0.0;
+        if (r == 0.0) continue;
+        v3 y = fv(sc->light_pos + 3 * l);
+        if (sc->light_kind && sc->light_kind[l] == ORC_LIGHT_AREA)
+            y = scl(add(add(y, fv(sc->light_v1 + 3 * l)), fv(sc->light_v2 + 3 * l)), 1.0 / 3.0);
+        double w[3] = {y.x - pw[0], y.y - pw[1], y.z - pw[2]};
+        double D = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+        if (!(D > 0)) continue;
+        for (int a = 0; a < 3; ++a) w[a] /= D;
+        if (occluded(sc, pw, w, ORC_NO_HIT, D, flags)) m *= 1.0 - r;
+    }
+    return m;
 }
 
 /* ---------------------------------------------------------------- BSDFs */

@@ -611,6 +611,10 @@ mrf_status mrf_lights_set(mrf_context *ctx, const mrf_light *lights, uint32_t n)
         }
         L.kind = h[i].kind;
         L.slot0 = slots;
+        if (!(h[i].mask_strength >= 0.f && h[i].mask_strength <= 1.f))
+            return fail(MRF_ERR_INVALID_ARG, "mrf_lights_set: light %u: mask_strength must be in [0, 1]", i);
+        L.mask = h[i].mask_strength;
+        for (int k = 0; k < 3; ++k) L.target[k] = h[i].pos[k];
         if (h[i].kind == MRF_LIGHT_POINT) {
             L.samples = 1;
         } else if (h[i].kind == MRF_LIGHT_AREA) {
@@ -629,6 +633,8 @@ mrf_status mrf_lights_set(mrf_context *ctx, const mrf_light *lights, uint32_t n)
             const double len = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
             if (!(len > 0)) return fail(MRF_ERR_INVALID_ARG, "mrf_lights_set: light %u: degenerate triangle", i);
             for (int k = 0; k < 3; ++k) L.n[k] = (float)(c[k] / len);
+            for (int k = 0; k < 3; ++k)
+                L.target[k] = (float)(((double)h[i].pos[k] + h[i].v1[k] + h[i].v2[k]) / 3.0);
             L.area = (float)(0.5 * len);
             L.samples = h[i].samples;
             L.q0 = q;
@@ -701,9 +707,20 @@ static const char *camera_view(const mrf_camera &c, ViewDev &v) {
     return nullptr;
 }
 
-mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *bvh, const mrf_rays *rays,
-                      uint32_t max_bounces, const mrf_render_opts *opts, float *out_hdr, void *stream,
-                      mrf_stats *stats) {
+// A validated render request: kernel parameters, engine and scratch layout.
+struct RenderPlan {
+    RenderParams P{};
+    int engine = MRF_ENGINE_MEGAKERNEL;
+    uint32_t count = 0, n_views = 0;
+    bool host_rays = false, host_out = false;
+    size_t out_off = 0, wf_off = 0, scratch_need = 0;
+    std::vector<ViewDev> views;
+};
+
+// Checks the arguments of a render call and fills the plan; no device work
+// besides pointer queries.
+static mrf_status plan_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *bvh, const mrf_rays *rays,
+                              uint32_t max_bounces, const mrf_render_opts *opts, float *out_hdr, RenderPlan &R) {
     if (!ctx || !field || !bvh || !rays || !opts || !out_hdr)
         return fail(MRF_ERR_INVALID_ARG, "mrf_render: NULL argument");
     if (field->ctx != ctx || bvh->ctx != ctx) return fail(MRF_ERR_INVALID_ARG, "mrf_render: handle of another context");
@@ -718,21 +735,7 @@ mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *b
         return fail(MRF_ERR_INVALID_ARG, "mrf_render: unknown engine %d", opts->engine);
     if (opts->engine == MRF_ENGINE_WAVEFRONT && !wavefront_available())
         return fail(MRF_ERR_UNSUPPORTED, "mrf_render: wavefront engine not built");
-    CUDA_TRY(cudaSetDevice(ctx->device), "mrf_render: cudaSetDevice");
-    {
-        cudaError_t pending = cudaGetLastError();
-        if (pending != cudaSuccess) return cuda_fail(pending, "mrf_render: earlier asynchronous error");
-    }
-    cudaStream_t s = (cudaStream_t)stream;
-    {
-        unsigned st_word = 0;
-        CUDA_TRY(cudaMemcpy(&st_word, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost), "mrf_render: status read");
-        if (st_word) {
-            cudaMemset(ctx->status, 0, sizeof(unsigned));
-            return fail(MRF_ERR_TIMEOUT, "mrf_render: an earlier kernel gave up (status 0x%x)", st_word);
-        }
-    }
-    RenderParams P{};
+    RenderParams &P = R.P;
     P.F = field->dev;
     P.B = bvh->dev;
     P.mats = ctx->mats;
@@ -742,20 +745,19 @@ mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *b
     P.n_shadow = ctx->n_shadow;
     uint32_t count;
     size_t scratch_need = 0;
-    const bool host_rays = !rays->camera && !is_device_ptr(rays->origins);
+    R.host_rays = !rays->camera && !is_device_ptr(rays->origins);
     const uint32_t n_views = rays->camera && rays->n_cameras > 1 ? rays->n_cameras : 0;
-    std::vector<ViewDev> views;
     if (n_views) {
         // several views: a table in device scratch, searched by ray index
         if (n_views > 65536u) return fail(MRF_ERR_INVALID_ARG, "mrf_render: more than 65536 cameras");
         if (is_device_ptr(rays->camera)) return fail(MRF_ERR_INVALID_ARG, "mrf_render: camera records must be host memory");
-        views.resize(n_views);
+        R.views.resize(n_views);
         uint64_t total = 0;
         for (uint32_t k = 0; k < n_views; ++k) {
-            if (const char *why = camera_view(rays->camera[k], views[k]))
+            if (const char *why = camera_view(rays->camera[k], R.views[k]))
                 return fail(MRF_ERR_INVALID_ARG, "mrf_render: camera %u: %s", k, why);
-            views[k].offset = (uint32_t)std::min<uint64_t>(total, 0xFFFFFFFFull);
-            total += (uint64_t)views[k].W * views[k].H;
+            R.views[k].offset = (uint32_t)std::min<uint64_t>(total, 0xFFFFFFFFull);
+            total += (uint64_t)R.views[k].W * R.views[k].H;
         }
         if (total > 0xFFFFFFFFull / 4) return fail(MRF_ERR_INVALID_ARG, "mrf_render: views too large");
         count = (uint32_t)total;
@@ -782,12 +784,17 @@ mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *b
         if (!rays->origins || !rays->dirs || rays->count == 0)
             return fail(MRF_ERR_INVALID_ARG, "mrf_render: explicit rays need origins, dirs and count > 0");
         count = rays->count;
-        if (host_rays) scratch_need += 2 * 3 * sizeof(float) * (size_t)count;
+        if (R.host_rays) scratch_need += 2 * 3 * sizeof(float) * (size_t)count;
+        else {
+            P.ray_o = rays->origins;
+            P.ray_d = rays->dirs;
+        }
     }
+    R.n_views = n_views;
     if ((uint64_t)count * rays->spp > 0xFFFFFFFFull) return fail(MRF_ERR_INVALID_ARG, "mrf_render: too many paths");
-    const bool host_out = !is_device_ptr(out_hdr);
-    const size_t out_off = (scratch_need + 255) & ~(size_t)255;
-    if (host_out) scratch_need = out_off + 4 * sizeof(float) * (size_t)count;
+    R.host_out = !is_device_ptr(out_hdr);
+    R.out_off = (scratch_need + 255) & ~(size_t)255;
+    if (R.host_out) scratch_need = R.out_off + 4 * sizeof(float) * (size_t)count;
     if ((opts->rec_segments && !is_device_ptr(opts->rec_segments)) || (opts->rec_tri && !is_device_ptr(opts->rec_tri)) ||
         (opts->rec_t && !is_device_ptr(opts->rec_t)) || (!opts->rec_tri != !opts->rec_t))
         return fail(MRF_ERR_INVALID_ARG, "mrf_render: records must be device pointers (rec_tri and rec_t together)");
@@ -802,6 +809,7 @@ mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *b
     P.rec_seg = opts->rec_segments;
     P.rec_tri = opts->rec_tri;
     P.rec_t = opts->rec_t;
+    P.shadow_mask = opts->shadow_mask ? 1 : 0;
     if (opts->shadow_net) {
         if (opts->shadow_net->ctx != ctx) return fail(MRF_ERR_INVALID_ARG, "shadow_net belongs to another context");
         P.has_snet = 1;
@@ -810,41 +818,96 @@ mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *b
     // AUTO: tensor-core field evaluation needs the wavefront engine's flat sample
     // tiles; FP32 runs the megakernel
     const bool lowp = field->dev.kind == MRF_FIELD_HASHGRID && field->dev.precision != MRF_PREC_FP32;
-    const int engine = opts->engine == MRF_ENGINE_AUTO ? (lowp ? MRF_ENGINE_WAVEFRONT : MRF_ENGINE_MEGAKERNEL)
-                                                       : opts->engine;
-    if (engine == MRF_ENGINE_MEGAKERNEL && lowp)
+    R.engine = opts->engine == MRF_ENGINE_AUTO ? (lowp ? MRF_ENGINE_WAVEFRONT : MRF_ENGINE_MEGAKERNEL) : opts->engine;
+    if (R.engine == MRF_ENGINE_MEGAKERNEL && lowp)
         return fail(MRF_ERR_UNSUPPORTED, "mrf_render: FP16/BF16 fields run on the wavefront engine");
-    if (engine == MRF_ENGINE_WAVEFRONT && ctx->n_shadow > 64)
+    if (R.engine == MRF_ENGINE_WAVEFRONT && ctx->n_shadow > 64)
         return fail(MRF_ERR_UNSUPPORTED, "mrf_render: the wavefront engine takes at most 64 shadow rays per hit");
-    size_t wf_off = 0;
-    if (engine == MRF_ENGINE_WAVEFRONT) {
-        wf_off = (scratch_need + 255) & ~(size_t)255;
-        scratch_need = wf_off + wavefront_scratch_bytes(P);
+    if (R.engine == MRF_ENGINE_WAVEFRONT) {
+        R.wf_off = (scratch_need + 255) & ~(size_t)255;
+        scratch_need = R.wf_off + wavefront_scratch_bytes(P);
     }
-    mrf_status st;
-    if (scratch_need && (st = ensure_scratch(ctx, scratch_need))) return st;
-    char *scr = (char *)ctx->scratch;
-    if (n_views) {
-        CUDA_TRY(cudaMemcpyAsync(scr, views.data(), sizeof(ViewDev) * (size_t)n_views, cudaMemcpyHostToDevice, s),
-                 "mrf_render: camera table upload");
-        P.views = (const ViewDev *)scr;
-        P.n_views = n_views;
-    }
-    if (host_rays) {
-        float *o = (float *)scr, *d = o + 3 * (size_t)count;
-        CUDA_TRY(cudaMemcpyAsync(o, rays->origins, 3 * sizeof(float) * (size_t)count, cudaMemcpyDefault, s), "ray upload");
-        CUDA_TRY(cudaMemcpyAsync(d, rays->dirs, 3 * sizeof(float) * (size_t)count, cudaMemcpyDefault, s), "ray upload");
-        P.ray_o = o;
-        P.ray_d = d;
-    } else if (!rays->camera) {
-        P.ray_o = rays->origins;
-        P.ray_d = rays->dirs;
-    }
-    P.out = host_out ? (float *)(scr + out_off) : out_hdr;
+    R.count = count;
+    R.scratch_need = scratch_need;
     P.status = ctx->status;
+    return MRF_OK;
+}
+
+// Device pointers of the plan inside the context's scratch (which must hold
+// R.scratch_need bytes).
+static void place_render(mrf_context *ctx, RenderPlan &R, float *out_hdr) {
+    char *scr = (char *)ctx->scratch;
+    if (R.n_views) {
+        R.P.views = (const ViewDev *)scr;
+        R.P.n_views = R.n_views;
+    }
+    if (R.host_rays) {
+        R.P.ray_o = (float *)scr;
+        R.P.ray_d = (float *)scr + 3 * (size_t)R.count;
+    }
+    R.P.out = R.host_out ? (float *)(scr + R.out_off) : out_hdr;
+}
+
+// Every launch of the planned render on stream s.
+static mrf_status launch_render(mrf_context *ctx, const RenderPlan &R, cudaStream_t s, KernelTimer *timer) {
+    char *scr = (char *)ctx->scratch;
+    if (R.engine == MRF_ENGINE_WAVEFRONT) {
+        CUDA_TRY(launch_render_wavefront(R.P, scr + R.wf_off, R.scratch_need - R.wf_off, s, timer),
+                 "mrf_render: wavefront launch");
+    } else {
+        CUDA_TRY(launch_render_megakernel(R.P, s, timer), "mrf_render: launch");
+    }
+    return MRF_OK;
+}
+
+static void stats_from(const unsigned long long *h, unsigned st_word, mrf_stats *stats) {
+    stats->paths = h[ST_PATHS];
+    stats->segments = h[ST_SEGMENTS];
+    stats->surface_hits = h[ST_HITS];
+    stats->shadow_rays = h[ST_SHADOW];
+    stats->samples_nominal = h[ST_NOMINAL];
+    stats->samples_evaluated = h[ST_EVALUATED];
+    stats->shadow_samples_evaluated = h[ST_SHADOW_EVALUATED];
+    stats->fp64_retests = h[ST_FP64];
+    stats->shadow_net_evals = h[ST_NET];
+    stats->status = st_word;
+}
+
+mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *bvh, const mrf_rays *rays,
+                      uint32_t max_bounces, const mrf_render_opts *opts, float *out_hdr, void *stream,
+                      mrf_stats *stats) {
+    RenderPlan R;
+    mrf_status st = plan_render(ctx, field, bvh, rays, max_bounces, opts, out_hdr, R);
+    if (st) return st;
+    CUDA_TRY(cudaSetDevice(ctx->device), "mrf_render: cudaSetDevice");
+    {
+        cudaError_t pending = cudaGetLastError();
+        if (pending != cudaSuccess) return cuda_fail(pending, "mrf_render: earlier asynchronous error");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    {
+        unsigned st_word = 0;
+        CUDA_TRY(cudaMemcpy(&st_word, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost), "mrf_render: status read");
+        if (st_word) {
+            cudaMemset(ctx->status, 0, sizeof(unsigned));
+            return fail(MRF_ERR_TIMEOUT, "mrf_render: an earlier kernel gave up (status 0x%x)", st_word);
+        }
+    }
+    if (R.scratch_need && (st = ensure_scratch(ctx, R.scratch_need))) return st;
+    place_render(ctx, R, out_hdr);
+    if (R.n_views)
+        CUDA_TRY(cudaMemcpyAsync((void *)R.P.views, R.views.data(), sizeof(ViewDev) * (size_t)R.n_views,
+                                 cudaMemcpyHostToDevice, s),
+                 "mrf_render: camera table upload");
+    if (R.host_rays) {
+        CUDA_TRY(cudaMemcpyAsync((void *)R.P.ray_o, rays->origins, 3 * sizeof(float) * (size_t)R.count,
+                                 cudaMemcpyDefault, s), "ray upload");
+        CUDA_TRY(cudaMemcpyAsync((void *)R.P.ray_d, rays->dirs, 3 * sizeof(float) * (size_t)R.count, cudaMemcpyDefault,
+                                 s), "ray upload");
+    }
     if (stats) {
         CUDA_TRY(cudaMemsetAsync(ctx->stats, 0, sizeof(unsigned long long) * ST_COUNT, s), "stats reset");
-        P.stats = ctx->stats;
+        R.P.stats = ctx->stats;
     }
     KernelTimer *timer = nullptr;
     if (opts->kernel_ms) {
@@ -857,11 +920,7 @@ mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *b
         timer->n = 0;
         timer->ok = true;
     }
-    if (engine == MRF_ENGINE_WAVEFRONT) {
-        CUDA_TRY(launch_render_wavefront(P, scr + wf_off, scratch_need - wf_off, s, timer), "mrf_render: wavefront launch");
-    } else {
-        CUDA_TRY(launch_render_megakernel(P, s, timer), "mrf_render: launch");
-    }
+    if ((st = launch_render(ctx, R, s, timer))) return st;
     if (timer) {
         CUDA_TRY(cudaStreamSynchronize(s), "mrf_render: synchronize");
         for (int k = 0; k < MRF_KERNEL_COUNT; ++k) {
@@ -875,36 +934,133 @@ mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *b
             if (opts->kernel_launches) opts->kernel_launches[timer->kind[i]] += 1;
         }
     }
-    if (host_out) {
-        CUDA_TRY(cudaMemcpyAsync(out_hdr, P.out, 4 * sizeof(float) * (size_t)count, cudaMemcpyDeviceToHost, s),
+    if (R.host_out) {
+        CUDA_TRY(cudaMemcpyAsync(out_hdr, R.P.out, 4 * sizeof(float) * (size_t)R.count, cudaMemcpyDeviceToHost, s),
                  "mrf_render: image download");
     }
     if (stats) {
         unsigned long long h[ST_COUNT];
         CUDA_TRY(cudaMemcpyAsync(h, ctx->stats, sizeof(h), cudaMemcpyDeviceToHost, s), "stats download");
         CUDA_TRY(cudaStreamSynchronize(s), "mrf_render: synchronize");
-        stats->paths = h[ST_PATHS];
-        stats->segments = h[ST_SEGMENTS];
-        stats->surface_hits = h[ST_HITS];
-        stats->shadow_rays = h[ST_SHADOW];
-        stats->samples_nominal = h[ST_NOMINAL];
-        stats->samples_evaluated = h[ST_EVALUATED];
-        stats->shadow_samples_evaluated = h[ST_SHADOW_EVALUATED];
-        stats->fp64_retests = h[ST_FP64];
-        stats->shadow_net_evals = h[ST_NET];
         unsigned st_word = 0;
         CUDA_TRY(cudaMemcpy(&st_word, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost), "mrf_render: status read");
-        stats->status = st_word;
+        stats_from(h, st_word, stats);
         if (st_word) {
             cudaMemset(ctx->status, 0, sizeof(unsigned));
             return fail(MRF_ERR_TIMEOUT, "mrf_render: a kernel gave up (status 0x%x)", st_word);
         }
-    } else if (host_out) {
+    } else if (R.host_out) {
         CUDA_TRY(cudaStreamSynchronize(s), "mrf_render: synchronize");
     }
     return MRF_OK;
 }
 
+// ------------------------------------------------------------ captured frames
+struct mrf_frame {
+    mrf_context *parent = nullptr;
+    mrf_context own;             // private scratch, statistics, status, materials and lights
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+void mrf_frame_destroy(mrf_frame *f) {
+    if (!f) return;
+    cudaSetDevice(f->own.device);
+    if (f->exec) cudaGraphExecDestroy(f->exec);
+    if (f->graph) cudaGraphDestroy(f->graph);
+    cudaFree(f->own.scratch);
+    cudaFree(f->own.stats);
+    cudaFree(f->own.status);
+    cudaFree(f->own.mats);
+    cudaFree(f->own.lights);
+    delete f;
+}
+
+mrf_status mrf_frame_capture(mrf_context *ctx, const mrf_field *field, const mrf_bvh *bvh, const mrf_rays *rays,
+                             uint32_t max_bounces, const mrf_render_opts *opts, float *out_hdr, mrf_frame **out) {
+    if (!out) return fail(MRF_ERR_INVALID_ARG, "mrf_frame_capture: NULL argument");
+    *out = nullptr;
+    RenderPlan R;
+    mrf_status st = plan_render(ctx, field, bvh, rays, max_bounces, opts, out_hdr, R);
+    if (st) return st;
+    if (R.host_out || R.host_rays || opts->kernel_ms || opts->kernel_launches)
+        return fail(MRF_ERR_INVALID_ARG, "mrf_frame_capture: outputs and rays must be device memory, no kernel timing");
+    CUDA_TRY(cudaSetDevice(ctx->device), "mrf_frame_capture: cudaSetDevice");
+    auto *f = new (std::nothrow) mrf_frame();
+    if (!f) return fail(MRF_ERR_OOM, "mrf_frame_capture");
+    f->parent = ctx;
+    mrf_context &fc = f->own;
+    fc.device = ctx->device;
+    fc.n_mats = ctx->n_mats;
+    fc.n_lights = ctx->n_lights;
+    fc.n_shadow = ctx->n_shadow;
+    auto bail = [&](mrf_status e) {
+        mrf_frame_destroy(f);
+        return e;
+    };
+    if ((st = dev_alloc(&fc.stats, ST_COUNT, "frame statistics")) || (st = dev_alloc(&fc.status, 1, "frame status")) ||
+        (st = dev_alloc(&fc.mats, (size_t)fc.n_mats, "frame materials")) ||
+        (st = dev_alloc(&fc.lights, (size_t)fc.n_lights, "frame lights")))
+        return bail(st);
+    if (cudaMemset(fc.status, 0, sizeof(unsigned)) != cudaSuccess ||
+        (fc.n_mats && cudaMemcpy(fc.mats, ctx->mats, sizeof(MaterialDev) * fc.n_mats, cudaMemcpyDeviceToDevice)) ||
+        (fc.n_lights && cudaMemcpy(fc.lights, ctx->lights, sizeof(LightDev) * fc.n_lights, cudaMemcpyDeviceToDevice)))
+        return bail(cuda_fail(cudaGetLastError(), "mrf_frame_capture: copies"));
+    if (R.scratch_need && (st = ensure_scratch(&fc, R.scratch_need))) return bail(st);
+    place_render(&fc, R, out_hdr);
+    R.P.mats = fc.mats;
+    R.P.lights = fc.lights;
+    R.P.status = fc.status;
+    R.P.stats = fc.stats;
+    if (R.n_views && cudaMemcpy((void *)R.P.views, R.views.data(), sizeof(ViewDev) * (size_t)R.n_views,
+                                cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "mrf_frame_capture: camera table"));
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "mrf_frame_capture: stream"));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        e = cudaMemsetAsync(fc.stats, 0, sizeof(unsigned long long) * ST_COUNT, cs);
+        mrf_status ls = e == cudaSuccess ? launch_render(&fc, R, cs, nullptr) : MRF_ERR_CUDA;
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (ls != MRF_OK || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaStreamDestroy(cs);
+            return bail(ls != MRF_OK ? ls : cuda_fail(e2, "mrf_frame_capture: capture"));
+        }
+        f->graph = g;
+        e = cudaGraphInstantiate(&f->exec, g, 0);
+    }
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "mrf_frame_capture: graph"));
+    *out = f;
+    return MRF_OK;
+}
+
+mrf_status mrf_frame_replay(mrf_frame *f, void *stream) {
+    if (!f) return fail(MRF_ERR_INVALID_ARG, "mrf_frame_replay: NULL frame");
+    CUDA_TRY(cudaSetDevice(f->own.device), "mrf_frame_replay: cudaSetDevice");
+    CUDA_TRY(cudaGraphLaunch(f->exec, (cudaStream_t)stream), "mrf_frame_replay");
+    return MRF_OK;
+}
+
+mrf_status mrf_frame_stats(mrf_frame *f, void *stream, mrf_stats *stats) {
+    if (!f || !stats) return fail(MRF_ERR_INVALID_ARG, "mrf_frame_stats: NULL argument");
+    CUDA_TRY(cudaSetDevice(f->own.device), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long h[ST_COUNT];
+    unsigned st_word = 0;
+    CUDA_TRY(cudaMemcpyAsync(h, f->own.stats, sizeof(h), cudaMemcpyDeviceToHost, s), "mrf_frame_stats");
+    CUDA_TRY(cudaMemcpyAsync(&st_word, f->own.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "mrf_frame_stats");
+    CUDA_TRY(cudaStreamSynchronize(s), "mrf_frame_stats: synchronize");
+    stats_from(h, st_word, stats);
+    if (st_word) {
+        cudaMemset(f->own.status, 0, sizeof(unsigned));
+        return fail(MRF_ERR_TIMEOUT, "mrf_frame: a kernel gave up (status 0x%x)", st_word);
+    }
+    return MRF_OK;
+}
 
 // Allocation-free render: the wavefront engine on the library's static device
 // arena (render_wavefront.cu).  Nothing here allocates device or pinned memory;
@@ -1019,6 +1175,7 @@ mrf_status mrf_render_static(mrf_context *ctx, const mrf_field *field, const mrf
     P.rec_seg = opts->rec_segments;
     P.rec_tri = opts->rec_tri;
     P.rec_t = opts->rec_t;
+    P.shadow_mask = opts->shadow_mask ? 1 : 0;
     if (opts->shadow_net) {
         if (opts->shadow_net->ctx != ctx) return fail(MRF_ERR_INVALID_ARG, "shadow_net belongs to another context");
         P.has_snet = 1;

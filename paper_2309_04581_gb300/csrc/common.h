@@ -80,6 +80,8 @@ struct LightDev {
     uint32_t samples;
     uint32_t q0;
     uint32_t slot0;     // index of the light's first shadow ray among the hit's rays
+    float mask;         // r_src of the field-sample shadow mask
+    float target[3];    // point the shadow-mask rays aim at (position or centroid)
 };
 
 // device statistics counters (unsigned long long), in this order
@@ -142,6 +144,7 @@ struct RenderParams {
     float *rec_t;
     unsigned long long *stats;   // nullable statistics counters
     unsigned *status;            // context status word: bits set when a kernel gave up
+    int shadow_mask;             // field samples blocked from a light emit (1 - r_src) r
     int has_snet;                // shadow rays from inside the field box use the network
     ShadowNetDev snet;
 };

@@ -86,6 +86,18 @@ __device__ __forceinline__ void to_field_frame(const FieldDev &F, V3 &o, V3 &d) 
            fmaf(M[8], e.x, fmaf(M[9], e.y, M[10] * e.z)));
 }
 
+// Local point of the field back to world space: p = R p' + t, with R and t
+// recovered from the stored world-to-local [R^T | -R^T t].
+__device__ __forceinline__ V3 field_to_world(const FieldDev &F, V3 q) {
+    if (!F.has_pose) return q;
+    const float *M = F.to_local;
+    const V3 t = v3(-(M[0] * M[3] + M[4] * M[7] + M[8] * M[11]), -(M[1] * M[3] + M[5] * M[7] + M[9] * M[11]),
+                    -(M[2] * M[3] + M[6] * M[7] + M[10] * M[11]));
+    return v3(fmaf(M[0], q.x, fmaf(M[4], q.y, fmaf(M[8], q.z, t.x))),
+              fmaf(M[1], q.x, fmaf(M[5], q.y, fmaf(M[9], q.z, t.y))),
+              fmaf(M[2], q.x, fmaf(M[6], q.y, fmaf(M[10], q.z, t.z))));
+}
+
 // ------------------------------------------------------------- field: analytic
 __device__ __forceinline__ bool inside_field_box(const FieldDev &F, V3 p) {
     return p.x >= F.lo[0] && p.x <= F.hi[0] && p.y >= F.lo[1] && p.y <= F.hi[1] && p.z >= F.lo[2] &&

@@ -50,6 +50,26 @@ __device__ __forceinline__ float field_at(const FieldDev &F, const float *w, V3 
     return F.const_sigma;
 }
 
+// Shadow mask m(p_t) of Sec. 3.1 at the world point pw: a ray toward each
+// light with mask strength r > 0 (position, or an area light's centroid); each
+// light a mesh blocks multiplies m by 1 - r.
+static __device__ __noinline__ float sample_mask(const RenderParams &P, V3 pw) {
+    float m = 1.f;
+    for (int l = 0; l < P.n_lights; ++l) {
+        const LightDev &L0 = P.lights[l];
+        if (!(L0.mask > 0.f)) continue;
+        V3 w = v3(L0.target[0], L0.target[1], L0.target[2]) - pw;
+        const float D = sqrtf(dot(w, w));
+        if (!(D > 0.f)) continue;
+        w = w * (1.f / D);
+        Hit hs;
+        unsigned rs = 0;
+        bool fault = false;
+        if (bvh_trace<true>(P.B, pw, w, kNoHit, P.tmin, D, hs, rs, fault)) m *= 1.f - L0.mask;
+    }
+    return m;
+}
+
 // Quadrature of Eqs. 10-11 over [a, b] of the ray (o, d).
 //   radiance: alpha_i = 1 - exp(-sigma_i delta_i); L += T alpha_i r_i; T *= exp(-sigma_i delta_i);
 //             sets `stop` when max(T) falls below tau.
@@ -61,6 +81,7 @@ template <bool radiance>
 __device__ float march(const RenderParams &P, const float *w, V3 o, V3 d, float a, float b, float T[3], float L[3],
                        bool &stop, Counters &C) {
     const FieldDev &F = P.F;
+    const V3 ow = o, dw = d;   // world ray (the shadow mask casts from world points)
     to_field_frame(F, o, d);
     float tb0, tb1;
     if (!box_interval(F.lo, F.hi, o, d, tb0, tb1)) return 0.f;
@@ -104,7 +125,9 @@ __device__ float march(const RenderParams &P, const float *w, V3 o, V3 d, float 
         }
         if (radiance) {
             const float x = sigma * delta;
-            const float att = expf(-x), alpha = -expm1f(-x);
+            const float att = expf(-x);
+            float alpha = -expm1f(-x);
+            if (P.shadow_mask && sigma > 0.f) alpha *= sample_mask(P, fma3(dw, tm, ow));
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 L[k] = fmaf(T[k] * alpha, rgb[k], L[k]);

@@ -619,6 +619,38 @@ __global__ void __launch_bounds__(kThreads, 8) wf_composite(const WfParams W, in
     }
 }
 
+// Shadow mask of Sec. 3.1 on the segment samples (radiance jobs only): the
+// radiance of every sample with sigma > 0 is scaled by m(p_t).  One warp walks
+// the samples of each of its 32 slots' jobs.
+__global__ void __launch_bounds__(kThreads) wf_mask(const WfParams W, int cur) {
+    const RenderParams &P = W.R;
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool active = tid < W.ctr[cur];
+    uint32_t rc = kOverflow, r0 = 0;
+    if (active) {
+        rc = W.rcount[tid];
+        r0 = W.rstart[tid];
+    }
+    for (int src = 0; src < 32; ++src) {
+        const uint32_t src_rc = __shfl_sync(0xffffffffu, rc, src);
+        const uint32_t src_r0 = __shfl_sync(0xffffffffu, r0, src);
+        if (!__shfl_sync(0xffffffffu, (int)active, src) || src_rc == kOverflow) continue;
+        for (uint32_t i = lane; i < src_rc; i += 32) {
+            float4 f = W.fout[src_r0 + i];
+            if (!(f.x > 0.f)) continue;
+            const float4 q = W.samp[src_r0 + i];
+            const float m = sample_mask(P, field_to_world(P.F, v3(q.x, q.y, q.z)));
+            if (m != 1.f) {
+                f.y *= m;
+                f.z *= m;
+                f.w *= m;
+                W.fout[src_r0 + i] = f;
+            }
+        }
+    }
+}
+
 // Jobs whose samples did not fit the sample buffer are marched in place here,
 // on the CUDA cores in FP32, producing the same per-slot results as
 // wf_composite (comp, sdepth).  Nothing to do when no job overflowed.
@@ -851,6 +883,10 @@ cudaError_t enqueue_frame(const WfParams &W, const RenderParams &P, uint32_t pat
             e = launch_field_simt(F, reinterpret_cast<const float *>(W.samp), 4, W.ctr + 2, W.cap, W.fout, field_grid, s);
         timer_end(timer, s);
         if (e != cudaSuccess) return e;
+        if (P.shadow_mask) {
+            wf_mask<<<grid, kThreads, 0, s>>>(W, cur);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
         if ((e = cudaMemsetAsync(W.ctr + nxt, 0, 4, s)) != cudaSuccess) return e;
         timer_begin(timer, MRF_KERNEL_COMPOSITE, s);
         wf_composite<<<grid, kThreads, 0, s>>>(W, cur);

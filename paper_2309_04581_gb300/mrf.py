@@ -38,7 +38,8 @@ EXPORTS = ("mrf_context_create", "mrf_context_destroy", "mrf_last_error", "mrf_v
            "mrf_bvh_destroy", "mrf_cast", "mrf_materials_set", "mrf_lights_set", "mrf_render", "mrf_render_static",
            "mrf_tonemap", "mrf_shadow_net_create", "mrf_shadow_net_destroy", "mrf_shadow_net_param_count",
            "mrf_shadow_net_get_params", "mrf_shadow_net_set_params", "mrf_shadow_pairs", "mrf_shadow_net_grad",
-           "mrf_shadow_net_train", "mrf_shadow_net_eval")
+           "mrf_shadow_net_train", "mrf_shadow_net_eval", "mrf_frame_capture", "mrf_frame_replay", "mrf_frame_stats",
+           "mrf_frame_destroy")
 
 _fp = C.POINTER(C.c_float)
 _u32p = C.POINTER(C.c_uint32)
@@ -66,7 +67,7 @@ class mrf_material(C.Structure):
 
 class mrf_light(C.Structure):
     _fields_ = [("kind", C.c_int32), ("pos", C.c_float * 3), ("intensity", C.c_float * 3), ("v1", C.c_float * 3),
-                ("v2", C.c_float * 3), ("samples", C.c_uint32)]
+                ("v2", C.c_float * 3), ("samples", C.c_uint32), ("mask_strength", C.c_float)]
 
 
 class mrf_camera(C.Structure):
@@ -83,7 +84,7 @@ class mrf_render_opts(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("steps_per_segment", C.c_uint32), ("dt", C.c_float), ("tau", C.c_float),
                 ("tmin", C.c_float), ("engine", C.c_int32), ("rec_segments", _vp), ("rec_tri", _vp),
                 ("rec_t", _vp), ("kernel_ms", C.POINTER(C.c_float)), ("kernel_launches", C.POINTER(C.c_uint32)),
-                ("shadow_net", _vp)]
+                ("shadow_net", _vp), ("shadow_mask", C.c_int32)]
 
 
 class mrf_shadow_net_desc(C.Structure):
@@ -122,8 +123,14 @@ def lib():
                 fn = getattr(L, name)
                 if name not in ("mrf_last_error", "mrf_version"):
                     fn.restype = C.c_int
-            for name in ("mrf_context_destroy", "mrf_field_destroy", "mrf_bvh_destroy", "mrf_shadow_net_destroy"):
+            for name in ("mrf_context_destroy", "mrf_field_destroy", "mrf_bvh_destroy", "mrf_shadow_net_destroy",
+                         "mrf_frame_destroy"):
                 getattr(L, name).restype = None
+            L.mrf_frame_capture.argtypes = [_vp, _vp, _vp, C.POINTER(mrf_rays), C.c_uint32, C.POINTER(mrf_render_opts),
+                                            _vp, C.POINTER(_vp)]
+            L.mrf_frame_replay.argtypes = [_vp, _vp]
+            L.mrf_frame_stats.argtypes = [_vp, _vp, C.POINTER(mrf_stats)]
+            L.mrf_frame_destroy.argtypes = [_vp]
             L.mrf_shadow_net_param_count.restype = C.c_uint64
             L.mrf_shadow_net_param_count.argtypes = [_vp]
             L.mrf_shadow_net_create.argtypes = [_vp, _vp, C.POINTER(mrf_shadow_net_desc), C.POINTER(_vp)]
@@ -227,6 +234,7 @@ def mrf_lights_set(ctx: int, lights):
             arr[i].v1[:] = [float(x) for x in l.v1]
             arr[i].v2[:] = [float(x) for x in l.v2]
         arr[i].samples = int(getattr(l, "samples", 1))
+        arr[i].mask_strength = float(getattr(l, "mask_strength", 0.0))
     check(lib().mrf_lights_set(ctx, arr, len(lights)))
 
 
@@ -323,6 +331,22 @@ class Renderer:
             dev = torch.device("cuda", device)
             self._rays_dev = (torch.from_numpy(scene.ray_o).to(dev), torch.from_numpy(scene.ray_d).to(dev))
 
+    def set_vertices(self, verts, rebuild: bool = False, stream=None):
+        """New vertex positions for the mesh (same topology): a refit of the BVH
+        (mrf_bvh_refit, enqueued on `stream`), or a full rebuild that replaces
+        the BVH handle (captured frames keep the old one)."""
+        v = np.ascontiguousarray(verts, np.float32)
+        if rebuild:
+            m = self.scene.mesh
+            t = np.ascontiguousarray(m.tris, np.uint32)
+            mt = np.ascontiguousarray(m.mat, np.uint32)
+            new = mrf_bvh_build(self.ctx, v.ctypes.data, v.shape[0], t.ctypes.data, mt.ctypes.data, t.shape[0])
+            mrf_bvh_destroy(self.bvh)
+            self.bvh = new
+        else:
+            s = stream if stream is not None else self.torch.cuda.current_stream(self.device).cuda_stream
+            mrf_bvh_refit(self.bvh, v.ctypes.data, v.shape[0], s)
+
     def close(self):
         if getattr(self, "ctx", None):
             mrf_bvh_destroy(self.bvh)
@@ -356,6 +380,7 @@ class Renderer:
         o = self.scene.opts
         s = mrf_render_opts()
         s.shadow_net = shadow_net.handle if shadow_net is not None else None
+        s.shadow_mask = 1 if getattr(o, "shadow_mask", False) else 0
         s.seed, s.steps_per_segment, s.dt, s.tau, s.tmin = o.seed, o.steps_per_segment, o.dt, o.tau, o.tmin
         s.engine = engine
         if records is not None:
@@ -396,6 +421,34 @@ class Renderer:
             for k, name in enumerate(KERNEL_NAMES):
                 timing[name] = (float(ms[k]), int(cnt[k]))
         return out, (st.as_dict() if st is not None else None)
+
+
+class Frame:
+    """A Renderer's render call captured into a CUDA graph (mrf_frame_capture) for replay."""
+
+    def __init__(self, renderer: "Renderer", out, engine=MRF_ENGINE_AUTO, records=None, shadow_net=None):
+        self.r = renderer
+        self.out = out
+        opts = renderer.opts_struct(engine, records, shadow_net)
+        h = _vp()
+        check(lib().mrf_frame_capture(renderer.ctx, renderer.field, renderer.bvh, C.byref(renderer.rays_struct()),
+                                      renderer.scene.opts.max_bounces, C.byref(opts), out.data_ptr(), C.byref(h)))
+        self.handle = h.value
+
+    def replay(self, stream=None):
+        s = stream if stream is not None else self.r.torch.cuda.current_stream(self.r.device).cuda_stream
+        check(lib().mrf_frame_replay(self.handle, s))
+
+    def stats(self, stream=None) -> dict:
+        s = stream if stream is not None else self.r.torch.cuda.current_stream(self.r.device).cuda_stream
+        st = mrf_stats()
+        check(lib().mrf_frame_stats(self.handle, s, C.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().mrf_frame_destroy(self.handle)
+            self.handle = None
 
 
 def mrf_tonemap(ctx: int, in_ptr: int, n: int, exposure: float, out_ptr: int, stream: int = 0):

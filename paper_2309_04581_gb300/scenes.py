@@ -134,6 +134,7 @@ class Light:
     v1: Optional[tuple] = None    # area light: the other two vertices (front normal (v1-v0) x (v2-v0))
     v2: Optional[tuple] = None
     samples: int = 1              # area light: shadow rays per diffuse hit
+    mask_strength: float = 0.0    # r_src of the field-sample shadow mask (0 = casts no mask)
 
 
 def area_light(v0, v1, v2, radiance, samples: int) -> "Light":
@@ -150,6 +151,7 @@ class RenderOpts:
     dt: float = 0.0               # steps_per_segment == 0: fixed step length
     tau: float = 0.0              # throughput termination threshold (0 = off)
     tmin: float = 1e-6            # smallest accepted ray-triangle distance
+    shadow_mask: bool = False     # scale field samples blocked from a light by 1 - r_src
 
 
 @dataclass
@@ -518,3 +520,92 @@ def snet_init(seed: int = 5, log2_T: int = SNET_LOG2_T, n_levels: int = SNET_LEV
         parts.append(rng.uniform(-lim, lim, fan_out * fan_in))
         parts.append(np.zeros(fan_out))
     return f32(np.concatenate(parts))
+
+
+# ---------------------------------------------------------------------------
+# dynamic sequence: a deforming cloth and moving rigid bodies, frame by frame
+# ---------------------------------------------------------------------------
+def cloth_grid(n: int, half: float, y: float, mat: int) -> Mesh:
+    """(n+1)^2 vertices on the square [-half, half]^2 at height y, 2 n^2 triangles."""
+    g = np.linspace(-half, half, n + 1)
+    xx, zz = np.meshgrid(g, g, indexing="xy")
+    verts = np.stack([xx.ravel(), np.full(xx.size, y), zz.ravel()], axis=1)
+    i = np.arange(n)
+    a = (i[None, :] + (n + 1) * i[:, None]).ravel()
+    tris = np.concatenate([np.stack([a, a + n + 1, a + 1], 1), np.stack([a + 1, a + n + 1, a + n + 2], 1)])
+    return Mesh(f32(verts), tris.astype(np.uint32), np.full(tris.shape[0], mat, np.uint32))
+
+
+def torus_mesh(R: float, r: float, nu: int, nv: int, mat: int) -> Mesh:
+    """Torus around the y axis, nu x nv quads split into 2 nu nv triangles."""
+    u = np.arange(nu) * 2 * math.pi / nu
+    v = np.arange(nv) * 2 * math.pi / nv
+    uu, vv = np.meshgrid(u, v, indexing="ij")
+    verts = np.stack([(R + r * np.cos(vv)) * np.cos(uu), r * np.sin(vv), (R + r * np.cos(vv)) * np.sin(uu)], -1)
+    iu, iv = np.meshgrid(np.arange(nu), np.arange(nv), indexing="ij")
+    a = iu * nv + iv
+    b = ((iu + 1) % nu) * nv + iv
+    c = ((iu + 1) % nu) * nv + (iv + 1) % nv
+    d = iu * nv + (iv + 1) % nv
+    tris = np.concatenate([np.stack([a, b, c], -1).reshape(-1, 3), np.stack([a, c, d], -1).reshape(-1, 3)])
+    return Mesh(f32(verts.reshape(-1, 3)), tris.astype(np.uint32), np.full(tris.shape[0], mat, np.uint32))
+
+
+class DynamicSequence:
+    """A cloth grid (n x n quads) with seeded sinusoid-plus-noise motion and
+    `bodies` rigid tori (2,048 triangles each) with seeded rigid motion, inside
+    the config-2 field and its meshes; `vertices(k)` gives frame k's vertex
+    array (topology fixed), `scene` frame 0."""
+
+    def __init__(self, width=1920, height=1080, spp=4, cloth_n=256, bodies=64, lights=4, max_bounces=8):
+        rng = _rng(5, 11)
+        base = config2(width, height, max_bounces=max_bounces)
+        self.static = base.mesh
+        self.cloth = cloth_grid(cloth_n, 0.45, -0.3, 2)
+        self.torus = torus_mesh(0.03, 0.012, 32, 32, 0)
+        self.n_bodies = bodies
+        self.body_center = rng.uniform(-0.35, 0.35, (bodies, 3))
+        self.body_center[:, 1] = rng.uniform(-0.2, 0.35, bodies)
+        self.body_axis = rng.normal(size=(bodies, 3))
+        self.body_axis /= np.linalg.norm(self.body_axis, axis=1, keepdims=True)
+        self.body_spin = rng.uniform(0.5, 2.0, bodies)
+        self.body_orbit = rng.uniform(0.02, 0.08, (bodies, 3))
+        self.body_freq = rng.uniform(0.3, 1.2, (bodies, 3))
+        self.cloth_phase = rng.uniform(0, 2 * math.pi, self.cloth.verts.shape[0])
+        mats = list(base.materials)            # 0 mirror, 1 glass, 2 diffuse
+        body_mat = rng.integers(0, 3, bodies).astype(np.uint32)
+        tris, mat, off = [self.static.tris], [self.static.mat], self.static.verts.shape[0]
+        tris.append(self.cloth.tris + off)
+        mat.append(self.cloth.mat)
+        off += self.cloth.verts.shape[0]
+        nv = self.torus.verts.shape[0]
+        for b in range(bodies):
+            tris.append(self.torus.tris + off + b * nv)
+            mat.append(np.full(self.torus.tris.shape[0], body_mat[b], np.uint32))
+        self.tris = np.ascontiguousarray(np.concatenate(tris).astype(np.uint32))
+        self.mat = np.ascontiguousarray(np.concatenate(mat).astype(np.uint32))
+        lights = [Light(pos=tuple(f32([rng.uniform(-0.4, 0.4), rng.uniform(0.42, 0.48), rng.uniform(-0.4, 0.4)])),
+                        intensity=tuple(f32(rng.uniform(0.5, 1.5, 3)))) for _ in range(lights)]
+        self.scene = Scene(name=f"dynamic_{width}x{height}", camera=default_camera(width, height), field=base.field,
+                           mesh=Mesh(self.vertices(0), self.tris, self.mat), materials=mats, lights=lights,
+                           opts=RenderOpts(max_bounces=max_bounces, spp=spp, seed=5, steps_per_segment=0, dt=DT_C2))
+
+    @property
+    def n_tris(self) -> int:
+        return int(self.tris.shape[0])
+
+    def vertices(self, k: int, fps: float = 30.0) -> np.ndarray:
+        t = k / fps
+        cv = self.cloth.verts.astype(np.float64).copy()
+        cv[:, 1] += 0.04 * np.sin(6.0 * cv[:, 0] + 2.0 * t) * np.cos(5.0 * cv[:, 2] - 1.5 * t) \
+            + 0.004 * np.sin(9.0 * t + self.cloth_phase)
+        tv = self.torus.verts.astype(np.float64)
+        out = [self.static.verts.astype(np.float64), cv]
+        for b in range(self.n_bodies):
+            ang = self.body_spin[b] * t
+            k_ = self.body_axis[b]
+            K = np.array([[0, -k_[2], k_[1]], [k_[2], 0, -k_[0]], [-k_[1], k_[0], 0]])
+            R = np.eye(3) + math.sin(ang) * K + (1 - math.cos(ang)) * K @ K
+            c = self.body_center[b] + self.body_orbit[b] * np.sin(self.body_freq[b] * t * 2 * math.pi)
+            out.append(tv @ R.T + c)
+        return f32(np.concatenate(out))

@@ -1,0 +1,84 @@
+"""Captured frames (mrf_frame_capture / mrf_frame_replay): a render call
+captured once into a CUDA graph replays to the same image as mrf_render, and
+follows the scene's device memory (a BVH refit) between replays."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2309_04581_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2309_04581_gb300 import build
+    build.build()
+    import paper_2309_04581_gb300.mrf as M
+    return torch, M
+
+
+@pytest.mark.parametrize("prec,engine", [("bf16", "wavefront"), ("fp32", "megakernel"), ("fp32", "wavefront")])
+def test_replay_matches_render(env, prec, engine):
+    torch, M = env
+    sc = S.config2(96, 80)
+    sc.cameras = S.orbit_views(3, [(96, 80), (33, 17), (1, 1)])   # a multi-view batch: table copied at capture
+    r = M.Renderer(sc, precision=M.MRF_PREC_BF16 if prec == "bf16" else M.MRF_PREC_FP32)
+    eng = M.MRF_ENGINE_WAVEFRONT if engine == "wavefront" else M.MRF_ENGINE_MEGAKERNEL
+    ref, st_ref = r.render(engine=eng, stats=True)
+    out = torch.full_like(ref, float("nan"))
+    f = M.Frame(r, out, engine=eng)
+    for _ in range(3):
+        f.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+        st = f.stats()
+        for k in ("paths", "segments", "surface_hits", "shadow_rays", "samples_evaluated", "shadow_samples_evaluated"):
+            assert st[k] == st_ref[k], k
+    f.close()
+    r.close()
+
+
+def test_replay_follows_refit_and_keeps_captured_lights(env):
+    torch, M = env
+    sc = S.config2(64, 64)
+    r = M.Renderer(sc, precision=M.MRF_PREC_BF16)
+    out = torch.empty((sc.n_rays, 4), dtype=torch.float32, device="cuda")
+    f = M.Frame(r, out)
+    f.replay()
+    torch.cuda.synchronize()
+    first = out.clone()
+    # deform the meshes: the replay reads the refitted BVH
+    moved = sc.mesh.verts.copy()
+    moved[:, 1] += np.float32(0.05) * np.sin(7.0 * moved[:, 0]).astype(np.float32)
+    moved = np.ascontiguousarray(moved.astype(np.float32))
+    M.mrf_bvh_refit(r.bvh, moved.ctypes.data, moved.shape[0], torch.cuda.current_stream().cuda_stream)
+    ref, _ = r.render()
+    f.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref) and not torch.equal(out, first)
+    # lights were copied at capture: switching them off afterwards changes mrf_render only
+    dark = [S.Light(pos=l.pos, intensity=(0.0, 0.0, 0.0)) for l in sc.lights]
+    M.mrf_lights_set(r.ctx, dark)
+    ref_dark, _ = r.render()
+    f.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref) and not torch.equal(ref_dark, ref)
+    f.close()
+    r.close()
+
+
+def test_capture_rejects_host_outputs(env):
+    torch, M = env
+    sc = S.config1(16, 16)
+    r = M.Renderer(sc)
+    host = np.zeros((sc.n_rays, 4), np.float32)
+    h = C.c_void_p()
+    st = M.lib().mrf_frame_capture(r.ctx, r.field, r.bvh, C.byref(r.rays_struct()), 4, C.byref(r.opts_struct()),
+                                   host.ctypes.data, C.byref(h))
+    assert st == M.MRF_ERR_INVALID_ARG and not h.value
+    r.close()

@@ -390,3 +390,29 @@ def test_area_light_back_side_and_occluder(orc):
                                                    [0.3, 0.1, -0.3], 0)])
     shut = orc.render(sc)["rgba"][:, 0]
     assert open_.min() > 0 and np.all(shut == 0.0)
+
+
+def test_field_sample_shadow_mask_closed_form(orc):
+    # Sec. 3.1's shadow mask: a homogeneous slab seen along +x at y = 0 under a
+    # point light at (0, 0.45, 0); an occluder quad (x in [-0.5, 0], y = 0.3)
+    # blocks the light for exactly the samples with x < 0 (their shadow rays
+    # cross y = 0.3 at x/3).  With mask strength r those samples emit (1 - r) r(p):
+    #   L = e [(1 - r)(1 - exp(-sigma/2)) + exp(-sigma/2)(1 - exp(-sigma/2))].
+    sigma, e, r = 2.3, np.array([0.4, 1.1, 2.0]), 0.75
+    sc = _const_scene(sigma, e, steps_per_segment=128)
+    sc.mesh = S.quad_mesh([-0.5, 0.3, -0.3], [-0.5, 0.3, 0.3], [0.0, 0.3, 0.3], [0.0, 0.3, -0.3], 0)
+    sc.materials = [S.Material(S.MAT_DIFFUSE, (0.5, 0.5, 0.5))]
+    sc.lights = [S.Light(pos=(0.0, 0.45, 0.0), intensity=(1.0, 1.0, 1.0), mask_strength=r)]
+    sc.opts.max_bounces = 1
+    sc.opts.shadow_mask = True
+    sc = S.explicit_rays(sc, [[-0.6, 0.0, 0.0]], [[1.0, 0.0, 0.0]])
+    got = orc.render(sc)["rgba"][0, :3]
+    s2 = F(sigma) * 0.5
+    h = math.exp(-s2)
+    rF = F(r)
+    expect = S.f32(e).astype(np.float64) * ((1 - rF) * (1 - h) + h * (1 - h))
+    assert np.allclose(got, expect, rtol=1e-12)
+    # mask off, or strength 0: the plain slab
+    sc.opts.shadow_mask = False
+    plain = orc.render(sc)["rgba"][0, :3]
+    assert np.allclose(plain, S.f32(e).astype(np.float64) * (1 - h * h), rtol=1e-12)
