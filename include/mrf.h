@@ -325,6 +325,30 @@ mrf_status mrf_render_static(mrf_context *ctx, const mrf_field *field, const mrf
                              uint32_t max_bounces, const mrf_render_opts *opts, float *out_hdr, void *stream,
                              mrf_stats *stats);
 
+/* ------------------------------------------------------------------ tuning
+ * Launch shapes and queue sizes of the wavefront engine, kept per context
+ * and used by every later render call of the context.  The paper names no
+ * such parameters; results do not depend on them (only speed and memory). */
+typedef struct mrf_tuning {
+    uint32_t field_groups;       /* 128-sample tiles in flight per CTA of the tensor-core field kernel:
+                                    8 (one CTA per SM, all TMEM) or 4 (two CTAs per SM); default 8 */
+    uint32_t samples_per_path;   /* sample-buffer capacity per path (plus 4 Mi samples); 16..4096, default 96 */
+    uint32_t rounds;             /* sample-generation rounds per segment, 1..16, default 1: the paths whose
+                                    samples did not fit the buffer go to the next round; those left after
+                                    the last round are marched in place on the CUDA cores in FP32 */
+} mrf_tuning;
+mrf_status mrf_tuning_get(const mrf_context *ctx, mrf_tuning *out);
+mrf_status mrf_tuning_set(mrf_context *ctx, const mrf_tuning *t);
+/* Autotuner: renders the given request (arguments as mrf_render, device
+ * out_hdr) with every candidate, field_groups in {8, 4} x samples_per_path in
+ * {48, 96, 192} x rounds in {1, 8}, times `reps` frames of each with CUDA
+ * events on `stream` after one warm-up frame, keeps the fastest in the
+ * context and returns it in `best` (nullable); `ms` (nullable) receives the
+ * mean frame time of the twelve candidates in that order. */
+mrf_status mrf_autotune(mrf_context *ctx, const mrf_field *field, const mrf_bvh *bvh, const mrf_rays *rays,
+                        uint32_t max_bounces, const mrf_render_opts *opts, float *out_hdr, void *stream, uint32_t reps,
+                        mrf_tuning *best, float *ms);
+
 /* --------------------------------------------------------- captured frames
  * One render call captured once into a CUDA graph and replayed: every launch
  * of a frame (Algorithm 1 over all paths) goes to the GPU as one graph, with

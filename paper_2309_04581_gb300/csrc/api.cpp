@@ -64,6 +64,7 @@ struct mrf_context {
     KernelTimer *timer = nullptr;
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
+    mrf_tuning tuning{8, 96, 1};
 };
 
 struct mrf_field {
@@ -810,6 +811,9 @@ static mrf_status plan_render(mrf_context *ctx, const mrf_field *field, const mr
     P.rec_tri = opts->rec_tri;
     P.rec_t = opts->rec_t;
     P.shadow_mask = opts->shadow_mask ? 1 : 0;
+    P.tc_groups = (int)ctx->tuning.field_groups;
+    P.cap_per_path = ctx->tuning.samples_per_path;
+    P.max_rounds = (int)ctx->tuning.rounds;
     if (opts->shadow_net) {
         if (opts->shadow_net->ctx != ctx) return fail(MRF_ERR_INVALID_ARG, "shadow_net belongs to another context");
         P.has_snet = 1;
@@ -955,6 +959,75 @@ mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *b
     return MRF_OK;
 }
 
+// ------------------------------------------------------------------ tuning
+mrf_status mrf_tuning_get(const mrf_context *ctx, mrf_tuning *out) {
+    if (!ctx || !out) return fail(MRF_ERR_INVALID_ARG, "mrf_tuning_get: NULL argument");
+    *out = ctx->tuning;
+    return MRF_OK;
+}
+
+mrf_status mrf_tuning_set(mrf_context *ctx, const mrf_tuning *t) {
+    if (!ctx || !t) return fail(MRF_ERR_INVALID_ARG, "mrf_tuning_set: NULL argument");
+    if ((t->field_groups != 4 && t->field_groups != 8) || t->samples_per_path < 16 || t->samples_per_path > 4096 ||
+        t->rounds < 1 || t->rounds > 16)
+        return fail(MRF_ERR_INVALID_ARG, "mrf_tuning_set: field_groups 4 or 8, samples_per_path 16..4096, rounds 1..16");
+    ctx->tuning = *t;
+    return MRF_OK;
+}
+
+mrf_status mrf_autotune(mrf_context *ctx, const mrf_field *field, const mrf_bvh *bvh, const mrf_rays *rays,
+                        uint32_t max_bounces, const mrf_render_opts *opts, float *out_hdr, void *stream, uint32_t reps,
+                        mrf_tuning *best, float *ms) {
+    if (!ctx || !opts || reps == 0) return fail(MRF_ERR_INVALID_ARG, "mrf_autotune: NULL argument or reps 0");
+    if (opts->kernel_ms || opts->kernel_launches)
+        return fail(MRF_ERR_INVALID_ARG, "mrf_autotune: per-kernel timing is not allowed here");
+    if (!is_device_ptr(out_hdr)) return fail(MRF_ERR_INVALID_ARG, "mrf_autotune: out_hdr must be device memory");
+    CUDA_TRY(cudaSetDevice(ctx->device), "mrf_autotune: cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    const mrf_tuning keep = ctx->tuning;
+    const uint32_t groups[2] = {8, 4}, caps[3] = {48, 96, 192}, rounds[2] = {1, 8};
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0), "mrf_autotune: event");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(cudaGetLastError(), "mrf_autotune: event");
+    }
+    float best_ms = INFINITY;
+    mrf_tuning win = keep;
+    mrf_status st = MRF_OK;
+    int c = 0;
+    for (uint32_t g : groups) {
+        for (uint32_t cap : caps)
+        for (uint32_t rr : rounds) {
+            ctx->tuning = mrf_tuning{g, cap, rr};
+            float t = INFINITY;
+            if ((st = mrf_render(ctx, field, bvh, rays, max_bounces, opts, out_hdr, stream, nullptr))) break;
+            cudaEventRecord(e0, s);
+            for (uint32_t r = 0; r < reps && !st; ++r)
+                st = mrf_render(ctx, field, bvh, rays, max_bounces, opts, out_hdr, stream, nullptr);
+            if (st) break;
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+                st = cuda_fail(cudaGetLastError(), "mrf_autotune: timing");
+                break;
+            }
+            t /= (float)reps;
+            if (ms) ms[c] = t;
+            ++c;
+            if (t < best_ms) {
+                best_ms = t;
+                win = ctx->tuning;
+            }
+        }
+        if (st) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tuning = st ? keep : win;
+    if (best && !st) *best = win;
+    return st;
+}
+
 // ------------------------------------------------------------ captured frames
 struct mrf_frame {
     mrf_context *parent = nullptr;
@@ -994,6 +1067,7 @@ mrf_status mrf_frame_capture(mrf_context *ctx, const mrf_field *field, const mrf
     fc.n_mats = ctx->n_mats;
     fc.n_lights = ctx->n_lights;
     fc.n_shadow = ctx->n_shadow;
+    fc.tuning = ctx->tuning;
     auto bail = [&](mrf_status e) {
         mrf_frame_destroy(f);
         return e;
@@ -1175,6 +1249,8 @@ mrf_status mrf_render_static(mrf_context *ctx, const mrf_field *field, const mrf
     P.rec_seg = opts->rec_segments;
     P.rec_tri = opts->rec_tri;
     P.rec_t = opts->rec_t;
+    P.tc_groups = (int)ctx->tuning.field_groups;
+    P.max_rounds = (int)ctx->tuning.rounds;
     P.shadow_mask = opts->shadow_mask ? 1 : 0;
     if (opts->shadow_net) {
         if (opts->shadow_net->ctx != ctx) return fail(MRF_ERR_INVALID_ARG, "shadow_net belongs to another context");

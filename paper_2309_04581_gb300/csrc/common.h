@@ -145,6 +145,9 @@ struct RenderParams {
     unsigned long long *stats;   // nullable statistics counters
     unsigned *status;            // context status word: bits set when a kernel gave up
     int shadow_mask;             // field samples blocked from a light emit (1 - r_src) r
+    int tc_groups;               // tuning: tile groups per CTA of the tensor-core field kernel (4 or 8)
+    uint32_t cap_per_path;       // tuning: sample-buffer capacity per path
+    int max_rounds;              // tuning: sample-generation rounds per segment
     int has_snet;                // shadow rays from inside the field box use the network
     ShadowNetDev snet;
 };
@@ -176,8 +179,8 @@ cudaError_t launch_field_simt(const FieldDev &F, const float *pts, int stride, c
                               float4 *out, int grid, cudaStream_t s);
 // field_tc.cu
 cudaError_t launch_field_tc(const FieldDev &F, bool bf16, const float *pts, int stride, const uint32_t *n_dev,
-                            uint32_t n_host, float4 *out, unsigned *status, int grid, cudaStream_t s);
-int field_tc_blocks_per_sm();
+                            uint32_t n_host, float4 *out, unsigned *status, int grid, cudaStream_t s, int groups = 8);
+int field_tc_blocks_per_sm(int groups = 8);
 cudaError_t launch_cast(const BvhDev &B, const float *o, const float *d, const uint32_t *skip, uint32_t n, float tmin,
                         float *out_t, uint32_t *out_tri, unsigned long long *stats, cudaStream_t s);
 cudaError_t launch_tonemap(const float4 *in, uint32_t n, float exposure, float4 *out, cudaStream_t s);

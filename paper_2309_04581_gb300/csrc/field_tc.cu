@@ -292,7 +292,7 @@ __device__ __forceinline__ void relu_bias_store(const uint32_t (&r)[32], const f
 // G tile groups of 128 threads per CTA; group g owns TMEM columns [64g, 64g + 64),
 // its own A operand and mbarrier, and synchronises on named barrier 1 + g.
 template <bool kBF16, int G>
-__global__ void __launch_bounds__(128 * G, 1)
+__global__ void __launch_bounds__(128 * G, 8 / G)
     field_tc_kernel(const FieldDev F, const float *__restrict__ pts, int stride, const uint32_t *__restrict__ n_dev,
                     uint32_t n_host, float4 *__restrict__ out, unsigned *__restrict__ status) {
     using Lo = Layout<G>;
@@ -462,18 +462,26 @@ __global__ void __launch_bounds__(128 * G, 1)
 
 }  // namespace
 
-// grid of the persistent launch: one CTA per SM
-int field_tc_blocks_per_sm() { return 1; }
+// CTAs per SM of the persistent launch: 8 groups take all 512 TMEM columns
+// (one CTA), 4 groups half of them (two CTAs)
+int field_tc_blocks_per_sm(int groups) { return groups == 4 ? 2 : 1; }
 
-cudaError_t launch_field_tc(const FieldDev &F, bool bf16, const float *pts, int stride, const uint32_t *n_dev,
-                            uint32_t n_host, float4 *out, unsigned *status, int grid, cudaStream_t s) {
-    auto kern = bf16 ? field_tc_kernel<true, kGroups> : field_tc_kernel<false, kGroups>;
-    constexpr int bytes = Layout<kGroups>::bytes;
+template <int G>
+static cudaError_t launch_groups(bool bf16, const FieldDev &F, const float *pts, int stride, const uint32_t *n_dev,
+                                 uint32_t n_host, float4 *out, unsigned *status, int grid, cudaStream_t s) {
+    auto kern = bf16 ? field_tc_kernel<true, G> : field_tc_kernel<false, G>;
+    constexpr int bytes = Layout<G>::bytes;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     if (grid <= 0) grid = 1;
-    kern<<<grid, 128 * kGroups, bytes, s>>>(F, pts, stride, n_dev, n_host, out, status);
+    kern<<<grid, 128 * G, bytes, s>>>(F, pts, stride, n_dev, n_host, out, status);
     return cudaGetLastError();
+}
+
+cudaError_t launch_field_tc(const FieldDev &F, bool bf16, const float *pts, int stride, const uint32_t *n_dev,
+                            uint32_t n_host, float4 *out, unsigned *status, int grid, cudaStream_t s, int groups) {
+    if (groups == 4) return launch_groups<4>(bf16, F, pts, stride, n_dev, n_host, out, status, grid, s);
+    return launch_groups<kGroups>(bf16, F, pts, stride, n_dev, n_host, out, status, grid, s);
 }
 
 }  // namespace mrf

@@ -26,7 +26,9 @@ namespace mrf {
 
 namespace {
 
-constexpr uint32_t kOverflow = 0xFFFFFFFFu;
+constexpr uint32_t kOverflow = 0xFFFFFFFFu;   // slot whose samples did not fit (pending)
+constexpr uint32_t kDone = 0xFFFFFFFEu;       // slot composited in an earlier round of the segment
+constexpr int kMaxRounds = 16;
 constexpr int kThreads = 128;
 
 struct WfParams {
@@ -45,7 +47,8 @@ struct WfParams {
     float4 *sdir;                   // shadow-ray direction (xyz) and light distance (w), [slot * n_shadow + q]
     float4 *comp;                   // per slot: segment radiance sum (rgb, times T(p_j)) and optical depth (w)
     float *sdepth;                  // shadow optical depth (marched) or transmittance (network), [slot * n_shadow + q]
-    uint32_t *ctr;                  // [0], [1] live counts; [2] generated samples; [3] network shadow rays
+    uint32_t *ctr;                  // [0], [1] live counts; [2] generated samples; [3] network shadow rays;
+                                    // [4 + r] slots left pending by generation round r
     uint32_t *squeue;               // shadow rays answered by the network: slot * n_shadow + q
     float4 *samp;                   // sample position (xyz) and interval length (w)
     float4 *fout;                   // sigma, r, g, b per sample
@@ -418,15 +421,18 @@ __global__ void __launch_bounds__(128) wf_shadow_net(const WfParams W) {
 // Warp-cooperative sample generation: counts the samples of every job of the
 // warp's 32 slots (segment march and visible shadow rays), allocates their
 // ranges with one atomic per warp, and writes them in order.
-__global__ void __launch_bounds__(kThreads, 8) wf_gen(const WfParams W, uint32_t j, int cur) {
+// Round r > 0 regenerates only the slots that round r - 1 left pending (their
+// samples did not fit the buffer), into the emptied buffer.
+__global__ void __launch_bounds__(kThreads, 8) wf_gen(const WfParams W, uint32_t j, int cur, int round) {
     __shared__ WalkSmem wsm;
     __shared__ RunList runs_sm[kThreads / 32][32][2];   // per warp, per slot: segment job, first shadow job
     const RenderParams &P = W.R;
+    if (round > 0 && W.ctr[4 + round - 1] == 0) return;   // nothing pending: the whole grid leaves
     const WalkCtx X = stage_walk(P.F, wsm);
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const uint32_t live = j == 1 ? W.paths : W.ctr[cur];
-    const bool active = tid < live;
+    const bool active = tid < live && (round == 0 || W.rcount[tid] == kOverflow);
     const int K = P.n_shadow;
     Counters C = {};
     V3 o = v3(0.f, 0.f, 0.f), d = v3(0.f, 0.f, 1.f), hp = v3(0.f, 0.f, 0.f);
@@ -483,6 +489,7 @@ __global__ void __launch_bounds__(kThreads, 8) wf_gen(const WfParams W, uint32_t
                 W.rcount[tid] = kOverflow;
                 for (int q = 0; vis && q < K; ++q)
                     if (W.sw[(size_t)tid * K + q].w == 1.f) W.scount[(size_t)tid * K + q] = kOverflow;
+                atomicAdd(&W.ctr[4 + round], 1u);
             }
             continue;
         }
@@ -513,6 +520,7 @@ __global__ void __launch_bounds__(kThreads, 8) wf_gen(const WfParams W, uint32_t
             k += ns;
         }
     }
+    if (round > 0) C.evaluated = C.shadow_eval = 0, C.nominal = 0;   // counted by round 0
     flush_counters(P.stats, C);
 }
 
@@ -571,29 +579,33 @@ __device__ __forceinline__ float warp_sum(float x) {
 // shadow samples (Eqs. 10-11).  Writes, per slot, sum_i exp(-depth_i) alpha_i r_i
 // (to be scaled by T(p_j)) and the optical depth up to the stop; a negative
 // depth marks a path that fell below tau inside the segment.  Jobs that did not
-// fit the sample buffer are left to wf_shade.
-__global__ void __launch_bounds__(kThreads, 8) wf_composite(const WfParams W, int cur) {
+// fit the sample buffer stay pending for the next round (or wf_overflow);
+// composited slots are marked done so that later rounds pass them by.
+__global__ void __launch_bounds__(kThreads, 8) wf_composite(const WfParams W, int cur, int round) {
     const RenderParams &P = W.R;
+    if (round > 0 && W.ctr[4 + round - 1] == 0) return;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const uint32_t live = W.ctr[cur];
-    const bool active = tid < live;
+    bool active = tid < live;
     const int K = P.n_shadow;
     uint32_t rc = kOverflow, r0 = 0;
     float tmax = 0.f;
     bool diffuse = false;
     if (active) {
         rc = W.rcount[tid];
+        active = rc != kOverflow && rc != kDone;   // generated in this round
         r0 = W.rstart[tid];
         const float4 qT = W.qT[cur][tid];
         tmax = fmaxf(qT.x, fmaxf(qT.y, qT.z));
         diffuse = __float_as_uint(W.hp[tid].w) != 0u;   // some unblocked shadow ray from a diffuse hit
+        if (active) W.rcount[tid] = kDone;   // read below from the registers only
     }
     for (int src = 0; src < 32; ++src) {
         if (!__shfl_sync(0xffffffffu, (int)active, src)) continue;
         const uint32_t src_rc = __shfl_sync(0xffffffffu, rc, src);
         const uint32_t src_tid = tid - lane + src;
-        if (src_rc != kOverflow) {
+        {
             const uint32_t src_r0 = __shfl_sync(0xffffffffu, r0, src);
             const float tmax0 = __shfl_sync(0xffffffffu, tmax, src);
             float lr, lg, lb, dep;
@@ -622,8 +634,9 @@ __global__ void __launch_bounds__(kThreads, 8) wf_composite(const WfParams W, in
 // Shadow mask of Sec. 3.1 on the segment samples (radiance jobs only): the
 // radiance of every sample with sigma > 0 is scaled by m(p_t).  One warp walks
 // the samples of each of its 32 slots' jobs.
-__global__ void __launch_bounds__(kThreads) wf_mask(const WfParams W, int cur) {
+__global__ void __launch_bounds__(kThreads) wf_mask(const WfParams W, int cur, int round) {
     const RenderParams &P = W.R;
+    if (round > 0 && W.ctr[4 + round - 1] == 0) return;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const bool active = tid < W.ctr[cur];
@@ -635,7 +648,7 @@ __global__ void __launch_bounds__(kThreads) wf_mask(const WfParams W, int cur) {
     for (int src = 0; src < 32; ++src) {
         const uint32_t src_rc = __shfl_sync(0xffffffffu, rc, src);
         const uint32_t src_r0 = __shfl_sync(0xffffffffu, r0, src);
-        if (!__shfl_sync(0xffffffffu, (int)active, src) || src_rc == kOverflow) continue;
+        if (!__shfl_sync(0xffffffffu, (int)active, src) || src_rc == kOverflow || src_rc == kDone) continue;
         for (uint32_t i = lane; i < src_rc; i += 32) {
             float4 f = W.fout[src_r0 + i];
             if (!(f.x > 0.f)) continue;
@@ -810,7 +823,7 @@ struct Layout {
     uint32_t cap;
 };
 
-Layout layout(uint32_t paths, int n_shadow) {
+Layout layout(uint32_t paths, int n_shadow, uint32_t cap_per_path = 96) {
     Layout L{};
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -839,9 +852,10 @@ Layout layout(uint32_t paths, int n_shadow) {
     L.comp = take(16 * P);
     L.sdepth = take(4 * P * nl);
     L.squeue = take(4 * P * nl);
-    L.ctr = take(16);
-    // sample capacity: 96 samples per path plus 4M (overflowing jobs are marched in place)
-    const uint64_t cap = std::min<uint64_t>((uint64_t)P * 96 + (4u << 20), 0x7FFFFFFFull);
+    L.ctr = take(4 * (4 + kMaxRounds));
+    // sample capacity: cap_per_path samples per path plus 4M (overflowing jobs are marched in place)
+    const uint64_t cap = std::min<uint64_t>((uint64_t)P * (cap_per_path ? cap_per_path : 96) + (4u << 20),
+                                            0x7FFFFFFFull);
     L.cap = (uint32_t)cap;
     L.samp = take(16 * cap);
     L.fout = take(16 * cap);
@@ -855,12 +869,14 @@ cudaError_t enqueue_frame(const WfParams &W, const RenderParams &P, uint32_t pat
     const unsigned grid = (paths + kThreads - 1) / kThreads;
     const FieldDev &F = P.F;
     const bool tc = F.kind == MRF_FIELD_HASHGRID && F.precision != MRF_PREC_FP32;
-    const int field_grid = tc ? 152 * field_tc_blocks_per_sm() : 152 * 8;
-    cudaError_t e = cudaMemsetAsync(W.ctr, 0, 16, s);   // counters left over from the previous call
+    const int groups = P.tc_groups == 4 ? 4 : 8;
+    const int field_grid = tc ? 152 * field_tc_blocks_per_sm(groups) : 152 * 8;
+    const int rounds = std::min(std::max(P.max_rounds, 1), kMaxRounds);
+    cudaError_t e = cudaMemsetAsync(W.ctr, 0, 4 * (4 + kMaxRounds), s);   // counters left over from the previous call
     if (e != cudaSuccess) return e;
     for (uint32_t j = 1; j <= P.max_bounces; ++j) {
         const int cur = (j - 1) & 1, nxt = j & 1;
-        if ((e = cudaMemsetAsync(W.ctr + 2, 0, 8, s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(W.ctr + 2, 0, 4 * (2 + rounds), s)) != cudaSuccess) return e;
         timer_begin(timer, MRF_KERNEL_CAST_GEN, s);
         wf_cast<<<grid, kThreads, 0, s>>>(W, j, cur);
         timer_end(timer, s);
@@ -871,27 +887,34 @@ cudaError_t enqueue_frame(const WfParams &W, const RenderParams &P, uint32_t pat
             timer_end(timer, s);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
-        timer_begin(timer, MRF_KERNEL_GEN, s);
-        wf_gen<<<grid, kThreads, 0, s>>>(W, j, cur);
-        timer_end(timer, s);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        timer_begin(timer, MRF_KERNEL_FIELD, s);
-        if (tc)
-            e = launch_field_tc(F, F.precision == MRF_PREC_BF16, reinterpret_cast<const float *>(W.samp), 4, W.ctr + 2,
-                                W.cap, W.fout, P.status, field_grid, s);
-        else
-            e = launch_field_simt(F, reinterpret_cast<const float *>(W.samp), 4, W.ctr + 2, W.cap, W.fout, field_grid, s);
-        timer_end(timer, s);
-        if (e != cudaSuccess) return e;
-        if (P.shadow_mask) {
-            wf_mask<<<grid, kThreads, 0, s>>>(W, cur);
+        // generation rounds: each evaluates and composites what fits the sample
+        // buffer; slots left over wait for the next round (the last leftovers
+        // are marched in place by wf_overflow)
+        for (int r = 0; r < rounds; ++r) {
+            if (r > 0 && (e = cudaMemsetAsync(W.ctr + 2, 0, 4, s)) != cudaSuccess) return e;
+            timer_begin(timer, MRF_KERNEL_GEN, s);
+            wf_gen<<<grid, kThreads, 0, s>>>(W, j, cur, r);
+            timer_end(timer, s);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            timer_begin(timer, MRF_KERNEL_FIELD, s);
+            if (tc)
+                e = launch_field_tc(F, F.precision == MRF_PREC_BF16, reinterpret_cast<const float *>(W.samp), 4,
+                                    W.ctr + 2, W.cap, W.fout, P.status, field_grid, s, groups);
+            else
+                e = launch_field_simt(F, reinterpret_cast<const float *>(W.samp), 4, W.ctr + 2, W.cap, W.fout,
+                                      field_grid, s);
+            timer_end(timer, s);
+            if (e != cudaSuccess) return e;
+            if (P.shadow_mask) {
+                wf_mask<<<grid, kThreads, 0, s>>>(W, cur, r);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            }
+            timer_begin(timer, MRF_KERNEL_COMPOSITE, s);
+            wf_composite<<<grid, kThreads, 0, s>>>(W, cur, r);
+            timer_end(timer, s);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
         if ((e = cudaMemsetAsync(W.ctr + nxt, 0, 4, s)) != cudaSuccess) return e;
-        timer_begin(timer, MRF_KERNEL_COMPOSITE, s);
-        wf_composite<<<grid, kThreads, 0, s>>>(W, cur);
-        timer_end(timer, s);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
         wf_overflow<<<grid, kThreads, 0, s>>>(W, cur);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         timer_begin(timer, MRF_KERNEL_SHADE, s);
@@ -911,13 +934,13 @@ cudaError_t enqueue_frame(const WfParams &W, const RenderParams &P, uint32_t pat
 bool wavefront_available() { return true; }
 
 size_t wavefront_scratch_bytes(const RenderParams &P) {
-    return layout(P.count * P.spp, P.n_shadow).total;
+    return layout(P.count * P.spp, P.n_shadow, P.cap_per_path).total;
 }
 
 cudaError_t launch_render_wavefront(const RenderParams &P, void *scratch, size_t scratch_bytes, cudaStream_t s,
                                     KernelTimer *timer) {
     const uint32_t paths = P.count * P.spp;
-    const Layout Lo = layout(paths, P.n_shadow);
+    const Layout Lo = layout(paths, P.n_shadow, P.cap_per_path);
     if (scratch_bytes < Lo.total) return cudaErrorInvalidValue;
     char *b = static_cast<char *>(scratch);
     WfParams W{};

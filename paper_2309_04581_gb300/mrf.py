@@ -39,7 +39,7 @@ EXPORTS = ("mrf_context_create", "mrf_context_destroy", "mrf_last_error", "mrf_v
            "mrf_tonemap", "mrf_shadow_net_create", "mrf_shadow_net_destroy", "mrf_shadow_net_param_count",
            "mrf_shadow_net_get_params", "mrf_shadow_net_set_params", "mrf_shadow_pairs", "mrf_shadow_net_grad",
            "mrf_shadow_net_train", "mrf_shadow_net_eval", "mrf_frame_capture", "mrf_frame_replay", "mrf_frame_stats",
-           "mrf_frame_destroy")
+           "mrf_frame_destroy", "mrf_tuning_get", "mrf_tuning_set", "mrf_autotune")
 
 _fp = C.POINTER(C.c_float)
 _u32p = C.POINTER(C.c_uint32)
@@ -93,6 +93,13 @@ class mrf_shadow_net_desc(C.Structure):
                 ("precision", C.c_int32)]
 
 
+class mrf_tuning(C.Structure):
+    _fields_ = [("field_groups", C.c_uint32), ("samples_per_path", C.c_uint32), ("rounds", C.c_uint32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 class mrf_stats(C.Structure):
     _fields_ = [("paths", C.c_uint64), ("segments", C.c_uint64), ("surface_hits", C.c_uint64),
                 ("shadow_rays", C.c_uint64), ("samples_nominal", C.c_uint64), ("samples_evaluated", C.c_uint64),
@@ -129,6 +136,10 @@ def lib():
             L.mrf_frame_capture.argtypes = [_vp, _vp, _vp, C.POINTER(mrf_rays), C.c_uint32, C.POINTER(mrf_render_opts),
                                             _vp, C.POINTER(_vp)]
             L.mrf_frame_replay.argtypes = [_vp, _vp]
+            L.mrf_tuning_get.argtypes = [_vp, C.POINTER(mrf_tuning)]
+            L.mrf_tuning_set.argtypes = [_vp, C.POINTER(mrf_tuning)]
+            L.mrf_autotune.argtypes = [_vp, _vp, _vp, C.POINTER(mrf_rays), C.c_uint32, C.POINTER(mrf_render_opts),
+                                       _vp, _vp, C.c_uint32, C.POINTER(mrf_tuning), C.POINTER(C.c_float)]
             L.mrf_frame_stats.argtypes = [_vp, _vp, C.POINTER(mrf_stats)]
             L.mrf_frame_destroy.argtypes = [_vp]
             L.mrf_shadow_net_param_count.restype = C.c_uint64
@@ -330,6 +341,28 @@ class Renderer:
         if scene.ray_o is not None:
             dev = torch.device("cuda", device)
             self._rays_dev = (torch.from_numpy(scene.ray_o).to(dev), torch.from_numpy(scene.ray_d).to(dev))
+
+    def tuning(self) -> dict:
+        t = mrf_tuning()
+        check(lib().mrf_tuning_get(self.ctx, C.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, field_groups: int, samples_per_path: int, rounds: int = 1):
+        t = mrf_tuning(field_groups, samples_per_path, rounds)
+        check(lib().mrf_tuning_set(self.ctx, C.byref(t)))
+
+    def autotune(self, out=None, reps: int = 2, engine=MRF_ENGINE_AUTO, shadow_net=None):
+        """Runs the autotuner on this renderer's request; returns (best tuning, [12 frame times in ms])."""
+        torch = self.torch
+        if out is None:
+            out = torch.empty((self.scene.n_rays, 4), dtype=torch.float32, device=torch.device("cuda", self.device))
+        best = mrf_tuning()
+        ms = (C.c_float * 12)()
+        opts = self.opts_struct(engine, None, shadow_net)
+        check(lib().mrf_autotune(self.ctx, self.field, self.bvh, C.byref(self.rays_struct()),
+                                 self.scene.opts.max_bounces, C.byref(opts), out.data_ptr(),
+                                 torch.cuda.current_stream(self.device).cuda_stream, reps, C.byref(best), ms))
+        return best.as_dict(), [float(x) for x in ms]
 
     def set_vertices(self, verts, rebuild: bool = False, stream=None):
         """New vertex positions for the mesh (same topology): a refit of the BVH

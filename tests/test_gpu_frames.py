@@ -82,3 +82,30 @@ def test_capture_rejects_host_outputs(env):
                                    host.ctypes.data, C.byref(h))
     assert st == M.MRF_ERR_INVALID_ARG and not h.value
     r.close()
+
+
+def test_autotuner_picks_a_candidate_and_keeps_results(env):
+    """The autotuner times the six launch-shape / queue-size candidates on the
+    request and keeps the fastest; none of them changes the image."""
+    torch, M = env
+    sc = S.config2(256, 256)
+    r = M.Renderer(sc, precision=M.MRF_PREC_BF16)
+    assert r.tuning() == {"field_groups": 8, "samples_per_path": 96, "rounds": 1}
+    before, st0 = r.render(stats=True)
+    best, ms = r.autotune(reps=2)
+    assert best == r.tuning()
+    cands = [(g, c, k) for g in (8, 4) for c in (48, 96, 192) for k in (1, 8)]
+    assert (best["field_groups"], best["samples_per_path"], best["rounds"]) in cands
+    assert all(x > 0 for x in ms) and min(ms) == pytest.approx(
+        ms[cands.index((best["field_groups"], best["samples_per_path"], best["rounds"]))])
+    print("autotune ms", ms, "best", best)
+    for g in (4, 8):
+        for c in (48, 192):
+            r.set_tuning(g, c, 8)
+            img, st = r.render(stats=True)
+            torch.cuda.synchronize()
+            assert torch.equal(img, before), (g, c)
+            assert st["samples_evaluated"] == st0["samples_evaluated"]
+    with pytest.raises(M.MrfError):
+        r.set_tuning(5, 96)
+    r.close()

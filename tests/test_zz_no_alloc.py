@@ -118,3 +118,24 @@ def test_static_arena_overflow_is_marched_in_place(env):
         assert _close(img, ref) <= tol
         assert torch.equal(rec["segments"], rec_ref["segments"])
         r.close()
+
+
+def test_static_arena_rounds_match_mrf_render_exactly(env):
+    # with enough generation rounds every job of the 129,600 paths is evaluated
+    # from the arena's small sample buffer in turns, none is marched in place:
+    # the image is mrf_render's bit for bit
+    torch, M = env
+    sc = S.config2(360, 360)
+    for prec in (M.MRF_PREC_BF16, M.MRF_PREC_FP32):
+        r = M.Renderer(sc, precision=prec)
+        r.set_tuning(8, 96, 16)
+        ref = torch.empty((sc.n_rays, 4), dtype=torch.float32, device="cuda")
+        M.mrf_render(r.ctx, r.field, r.bvh, r.rays_struct(), 8, r.opts_struct(M.MRF_ENGINE_WAVEFRONT), ref.data_ptr(),
+                     0)
+        out = torch.full_like(ref, float("nan"))
+        st = M.mrf_stats()
+        assert M.lib().mrf_render_static(r.ctx, r.field, r.bvh, C.byref(r.rays_struct()), 8, C.byref(r.opts_struct()),
+                                         out.data_ptr(), None, C.byref(st)) == M.MRF_OK
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+        r.close()
