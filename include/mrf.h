@@ -147,6 +147,14 @@ mrf_status mrf_bvh_build(mrf_context *ctx, const float *verts, uint32_t n_verts,
  * Sec. 3.2 change their vertices every simulation step).  verts: n_verts x 3,
  * n_verts must equal the build's (else MRF_ERR_INVALID_ARG).  Runs on `stream`. */
 mrf_status mrf_bvh_refit(mrf_bvh *bvh, const float *verts, uint32_t n_verts, void *stream);
+/* Rebuild of the hierarchy on the GPU for new vertex positions (same
+ * triangles, n_verts as at build; host or device array): a linear BVH over the
+ * 30-bit Morton order of the triangle centroids (Karras, HPG 2012), one
+ * triangle per leaf, enqueued on `stream` without host synchronisation (the
+ * first call allocates room for n - 1 nodes and the sort buffers and waits).
+ * For deforming meshes whose refitted boxes have grown loose: casts give the
+ * same closest hits as with the original tree. */
+mrf_status mrf_bvh_rebuild(mrf_bvh *bvh, const float *verts, uint32_t n_verts, void *stream);
 void mrf_bvh_destroy(mrf_bvh *bvh);
 
 /* Closest hit of n rays (origins, dirs: n x 3 FP32 device arrays; dirs need
@@ -401,6 +409,7 @@ typedef struct mrf_shadow_net_desc {
     uint64_t seed;             /* default initialisation: table U(-1e-4, 1e-4), Xavier-uniform W, zero b */
     float lr, beta1, beta2, eps;  /* Adam */
     int32_t precision;         /* weights used when rendering: MRF_PREC_FP32 or MRF_PREC_BF16 (the table stays FP32) */
+    float lr_decay;            /* step t (from 1) uses lr * lr_decay^(t-1); 0 means 1 (constant) */
 } mrf_shadow_net_desc;
 
 /* The network belongs to `field`'s frame and box (copied at creation). */

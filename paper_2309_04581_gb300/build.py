@@ -17,7 +17,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmrf.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cpp", "bvh_build.cpp", "render_mega.cu", "render_wavefront.cu", "bvh_refit.cu", "field_tc.cu", "shadow_net.cu"]
+SOURCES = ["api.cpp", "bvh_build.cpp", "render_mega.cu", "render_wavefront.cu", "bvh_refit.cu", "field_tc.cu", "shadow_net.cu",
+           "bvh_lbvh.cu"]
 
 
 def _nvcc() -> str:

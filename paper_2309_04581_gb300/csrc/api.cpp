@@ -80,8 +80,10 @@ struct mrf_bvh {
     uint32_t *order = nullptr, *tri_idx = nullptr;
     float *verts = nullptr;
     int *parent = nullptr, *counters = nullptr;
+    uint32_t *mat = nullptr;             // material per original triangle (for rebuilds)
+    uint32_t *rebuild_scratch = nullptr; // sort buffers of the GPU rebuild, allocated at the first one
     uint32_t n_verts = 0, n_tris = 0;
-    int n_nodes = 0;
+    int n_nodes = 0, node_cap = 0;
 };
 
 struct mrf_shadow_net {
@@ -91,7 +93,7 @@ struct mrf_shadow_net {
     uint64_t n_params = 0;
     uint32_t t = 0;          // Adam steps taken
     uint64_t cursor = 0;     // next training pair
-    float lr = 1e-2f, b1 = 0.9f, b2 = 0.99f, eps = 1e-15f;
+    float lr = 1e-2f, b1 = 0.9f, b2 = 0.99f, eps = 1e-15f, decay = 1.f;
     int precision = MRF_PREC_FP32;
 };
 
@@ -506,8 +508,10 @@ mrf_status mrf_bvh_build(mrf_context *ctx, const float *verts, uint32_t n_verts,
     if ((st = dev_alloc(&b->nodes, 4 * (size_t)b->n_nodes, "bvh nodes")) || (st = dev_alloc(&b->tris, tv.size(), "bvh tris")) ||
         (st = dev_alloc(&b->order, n_tris, "bvh order")) || (st = dev_alloc(&b->tri_idx, 3 * (size_t)n_tris, "bvh indices")) ||
         (st = dev_alloc(&b->verts, 3 * (size_t)n_verts, "bvh verts")) || (st = dev_alloc(&b->parent, (size_t)b->n_nodes, "bvh parents")) ||
-        (st = dev_alloc(&b->counters, (size_t)b->n_nodes, "bvh counters")))
+        (st = dev_alloc(&b->counters, (size_t)b->n_nodes, "bvh counters")) ||
+        (st = dev_alloc(&b->mat, n_tris, "bvh materials")))
         return cleanup(st);
+    b->node_cap = b->n_nodes;
     cudaError_t e = cudaSuccess;
     if (b->n_nodes) {
         e = cudaMemcpy(b->nodes, nodes.data(), nodes.size() * 4, cudaMemcpyHostToDevice);
@@ -518,6 +522,7 @@ mrf_status mrf_bvh_build(mrf_context *ctx, const float *verts, uint32_t n_verts,
         if (e == cudaSuccess) e = cudaMemcpy(b->order, order.data(), order.size() * 4, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(b->tri_idx, ht.data(), ht.size() * 4, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(b->verts, hv.data(), hv.size() * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(b->mat, hm.data(), hm.size() * 4, cudaMemcpyHostToDevice);
     }
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "mrf_bvh_build: upload"));
     b->dev.nodes = b->nodes;
@@ -525,6 +530,52 @@ mrf_status mrf_bvh_build(mrf_context *ctx, const float *verts, uint32_t n_verts,
     b->dev.n_nodes = b->n_nodes;
     b->dev.n_tris = (int)n_tris;
     *out = b;
+    return MRF_OK;
+}
+
+mrf_status mrf_bvh_rebuild(mrf_bvh *b, const float *verts, uint32_t n_verts, void *stream) {
+    if (!b || (!verts && n_verts)) return fail(MRF_ERR_INVALID_ARG, "mrf_bvh_rebuild: NULL argument");
+    if (n_verts != b->n_verts)
+        return fail(MRF_ERR_INVALID_ARG, "mrf_bvh_rebuild: %u vertices, the BVH was built with %u", n_verts, b->n_verts);
+    if (b->n_tris == 0) return MRF_OK;
+    CUDA_TRY(cudaSetDevice(b->ctx->device), "mrf_bvh_rebuild: cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int need = b->n_tris > 1 ? (int)b->n_tris - 1 : 1;
+    if (b->node_cap < need || !b->rebuild_scratch) {
+        // first rebuild: room for n - 1 internal nodes and the sort buffers
+        CUDA_TRY(cudaStreamSynchronize(s), "mrf_bvh_rebuild: synchronize");
+        float4 *nodes = nullptr;
+        int *parent = nullptr, *counters = nullptr;
+        uint32_t *scr = nullptr;
+        mrf_status st;
+        if ((st = dev_alloc(&nodes, 4 * (size_t)need, "bvh nodes")) || (st = dev_alloc(&parent, (size_t)need, "bvh parents")) ||
+            (st = dev_alloc(&counters, (size_t)need, "bvh counters")) ||
+            (st = dev_alloc(&scr, bvh_rebuild_scratch_words(b->n_tris), "bvh rebuild scratch"))) {
+            cudaFree(nodes);
+            cudaFree(parent);
+            cudaFree(counters);
+            cudaFree(scr);
+            return st;
+        }
+        cudaFree(b->nodes);
+        cudaFree(b->parent);
+        cudaFree(b->counters);
+        cudaFree(b->rebuild_scratch);
+        b->nodes = nodes;
+        b->parent = parent;
+        b->counters = counters;
+        b->rebuild_scratch = scr;
+        b->node_cap = need;
+        b->dev.nodes = b->nodes;
+    }
+    CUDA_TRY(cudaMemcpyAsync(b->verts, verts, 3 * sizeof(float) * (size_t)n_verts, cudaMemcpyDefault, s),
+             "mrf_bvh_rebuild: vertex upload");
+    CUDA_TRY(launch_bvh_rebuild(b->nodes, b->parent, b->counters, b->tris, b->order, b->tri_idx, b->mat, b->verts,
+                                b->n_tris, b->rebuild_scratch, s),
+             "mrf_bvh_rebuild");
+    b->n_nodes = need;
+    b->dev.n_nodes = need;
+    if (!is_device_ptr(verts)) CUDA_TRY(cudaStreamSynchronize(s), "mrf_bvh_rebuild: synchronize");
     return MRF_OK;
 }
 
@@ -551,6 +602,8 @@ void mrf_bvh_destroy(mrf_bvh *b) {
     cudaFree(b->verts);
     cudaFree(b->parent);
     cudaFree(b->counters);
+    cudaFree(b->mat);
+    cudaFree(b->rebuild_scratch);
     delete b;
 }
 
@@ -1352,6 +1405,11 @@ mrf_status mrf_shadow_net_create(mrf_context *ctx, const mrf_field *field, const
     n->b1 = desc->beta1;
     n->b2 = desc->beta2;
     n->eps = desc->eps;
+    n->decay = desc->lr_decay > 0.f ? desc->lr_decay : 1.f;
+    if (!(n->decay <= 1.f)) {
+        delete n;
+        return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_net_create: lr_decay must be in (0, 1]");
+    }
     n->precision = desc->precision;
     n->n_params = snet_params(desc->log2_table);
     ShadowNetDev &D = n->dev;
@@ -1500,7 +1558,8 @@ mrf_status mrf_shadow_net_train(mrf_shadow_net *n, const float *pairs, uint64_t 
         n->cursor = (n->cursor + batch) % n_pairs;
         ++n->t;
         const double c1 = 1.0 - std::pow((double)n->b1, (double)n->t), c2 = 1.0 - std::pow((double)n->b2, (double)n->t);
-        CUDA_TRY(launch_snet_adam(n->params, n->m, n->v, n->grad, n->n_params, n->lr, n->b1, n->b2, n->eps, c1, c2, s),
+        const float lr_t = (float)((double)n->lr * std::pow((double)n->decay, (double)(n->t - 1)));
+        CUDA_TRY(launch_snet_adam(n->params, n->m, n->v, n->grad, n->n_params, lr_t, n->b1, n->b2, n->eps, c1, c2, s),
                  "mrf_shadow_net_train: Adam");
     }
     return snet_refresh(n, s);

@@ -194,6 +194,11 @@ cudaError_t launch_snet_adam(float *p, float *m, float *v, float *g, uint64_t n,
                              float eps, double c1, double c2, cudaStream_t s);
 cudaError_t launch_snet_refresh(const float *mlp, float *out, bool bf16, cudaStream_t s);
 cudaError_t launch_snet_eval(const ShadowNetDev &N, const float *pairs, uint32_t n, float *out, cudaStream_t s);
+// bvh_lbvh.cu
+size_t bvh_rebuild_scratch_words(uint32_t n);
+cudaError_t launch_bvh_rebuild(float4 *nodes, int *parent, int *counters, float4 *tris, uint32_t *order,
+                               const uint32_t *tri_idx, const uint32_t *mat, const float *verts, uint32_t n,
+                               uint32_t *scratch, cudaStream_t s);
 // bvh_refit.cu
 cudaError_t launch_bvh_refit(float4 *nodes, int n_nodes, float4 *tris, int n_tris, const uint32_t *tri_order,
                              const uint32_t *tri_idx, const float *verts, const int *parent, int *counters,

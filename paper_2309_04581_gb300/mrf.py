@@ -35,7 +35,7 @@ NO_HIT = 0xFFFFFFFF
 # every entry point declared in include/mrf.h
 EXPORTS = ("mrf_context_create", "mrf_context_destroy", "mrf_last_error", "mrf_version", "mrf_field_create",
            "mrf_field_destroy", "mrf_field_set_precision", "mrf_field_query", "mrf_bvh_build", "mrf_bvh_refit",
-           "mrf_bvh_destroy", "mrf_cast", "mrf_materials_set", "mrf_lights_set", "mrf_render", "mrf_render_static",
+           "mrf_bvh_destroy", "mrf_bvh_rebuild", "mrf_cast", "mrf_materials_set", "mrf_lights_set", "mrf_render", "mrf_render_static",
            "mrf_tonemap", "mrf_shadow_net_create", "mrf_shadow_net_destroy", "mrf_shadow_net_param_count",
            "mrf_shadow_net_get_params", "mrf_shadow_net_set_params", "mrf_shadow_pairs", "mrf_shadow_net_grad",
            "mrf_shadow_net_train", "mrf_shadow_net_eval", "mrf_frame_capture", "mrf_frame_replay", "mrf_frame_stats",
@@ -90,7 +90,7 @@ class mrf_render_opts(C.Structure):
 class mrf_shadow_net_desc(C.Structure):
     _fields_ = [("log2_table", C.c_uint32), ("level_res", C.c_uint32 * 8), ("params", _vp), ("seed", C.c_uint64),
                 ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
-                ("precision", C.c_int32)]
+                ("precision", C.c_int32), ("lr_decay", C.c_float)]
 
 
 class mrf_tuning(C.Structure):
@@ -159,6 +159,7 @@ def lib():
             L.mrf_field_query.argtypes = [_vp, _vp, _vp, C.c_uint32, _vp, _vp]
             L.mrf_bvh_build.argtypes = [_vp, _vp, C.c_uint32, _vp, _vp, C.c_uint32, C.POINTER(_vp)]
             L.mrf_bvh_refit.argtypes = [_vp, _vp, C.c_uint32, _vp]
+            L.mrf_bvh_rebuild.argtypes = [_vp, _vp, C.c_uint32, _vp]
             L.mrf_cast.argtypes = [_vp, _vp, _vp, _vp, _vp, C.c_uint32, C.c_float, _vp, _vp, _vp]
             L.mrf_materials_set.argtypes = [_vp, C.POINTER(mrf_material), C.c_uint32]
             L.mrf_lights_set.argtypes = [_vp, C.POINTER(mrf_light), C.c_uint32]
@@ -364,12 +365,16 @@ class Renderer:
                                  torch.cuda.current_stream(self.device).cuda_stream, reps, C.byref(best), ms))
         return best.as_dict(), [float(x) for x in ms]
 
-    def set_vertices(self, verts, rebuild: bool = False, stream=None):
+    def set_vertices(self, verts, rebuild=False, stream=None):
         """New vertex positions for the mesh (same topology): a refit of the BVH
-        (mrf_bvh_refit, enqueued on `stream`), or a full rebuild that replaces
-        the BVH handle (captured frames keep the old one)."""
+        (mrf_bvh_refit), rebuild="gpu" a GPU rebuild in place (mrf_bvh_rebuild),
+        both enqueued on `stream`, or rebuild="host" (or True) a host SAH build
+        that replaces the BVH handle (captured frames keep the old one)."""
         v = np.ascontiguousarray(verts, np.float32)
-        if rebuild:
+        s = stream if stream is not None else self.torch.cuda.current_stream(self.device).cuda_stream
+        if rebuild == "gpu":
+            check(lib().mrf_bvh_rebuild(self.bvh, v.ctypes.data, v.shape[0], s))
+        elif rebuild:
             m = self.scene.mesh
             t = np.ascontiguousarray(m.tris, np.uint32)
             mt = np.ascontiguousarray(m.mat, np.uint32)
@@ -377,7 +382,6 @@ class Renderer:
             mrf_bvh_destroy(self.bvh)
             self.bvh = new
         else:
-            s = stream if stream is not None else self.torch.cuda.current_stream(self.device).cuda_stream
             mrf_bvh_refit(self.bvh, v.ctypes.data, v.shape[0], s)
 
     def close(self):
@@ -492,7 +496,8 @@ class ShadowNet:
     """The learned shadow-transmittance network of a Renderer's field (the C ABI's mrf_shadow_net)."""
 
     def __init__(self, renderer: "Renderer", params=None, precision: int = MRF_PREC_FP32, log2_table: int = S.SNET_LOG2_T,
-                 level_res=None, lr: float = 1e-2, betas=(0.9, 0.99), eps: float = 1e-15, seed: int = 0):
+                 level_res=None, lr: float = 1e-2, betas=(0.9, 0.99), eps: float = 1e-15, seed: int = 0,
+                 lr_decay: float = 1.0):
         self.r = renderer
         torch = renderer.torch
         d = mrf_shadow_net_desc()
@@ -505,6 +510,7 @@ class ShadowNet:
         d.seed = seed
         d.lr, d.beta1, d.beta2, d.eps = lr, betas[0], betas[1], eps
         d.precision = precision
+        d.lr_decay = lr_decay
         h = _vp()
         check(lib().mrf_shadow_net_create(renderer.ctx, renderer.field, C.byref(d), C.byref(h)))
         self.handle = h.value

@@ -23,16 +23,21 @@ def test_refit_sequence_matches_rebuild_and_oracle(env, orc):
     torch, M = env
     seq = S.DynamicSequence(48, 40, spp=1, cloth_n=24, bodies=3, lights=2)
     a = M.Renderer(seq.scene)      # refitted every frame
-    b = M.Renderer(seq.scene)      # rebuilt every frame
+    b = M.Renderer(seq.scene)      # rebuilt on the host every frame
+    c = M.Renderer(seq.scene)      # rebuilt on the GPU every frame
     for k in range(1, 5):
         v = seq.vertices(k, fps=4.0)   # large steps: the boxes move a lot between frames
         a.set_vertices(v)
-        b.set_vertices(v, rebuild=True)
+        b.set_vertices(v, rebuild="host")
+        c.set_vertices(v, rebuild="gpu")
         ia, _ = a.render()
         ib, _ = b.render()
+        ic, _ = c.render()
         torch.cuda.synchronize()
         # same closest hits whichever tree finds them: identical images
         assert torch.equal(ia, ib), k
+        assert torch.equal(ia, ic), k
+    c.close()
     sc = S.Scene(name="frame4", camera=seq.scene.camera, field=seq.scene.field,
                  mesh=S.Mesh(seq.vertices(4, fps=4.0), seq.tris, seq.mat), materials=seq.scene.materials,
                  lights=seq.scene.lights, opts=seq.scene.opts)

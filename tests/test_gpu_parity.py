@@ -129,14 +129,19 @@ def _cast(M, torch, ctx, bvh, o, d, skip=None, tmin=1e-6):
     return ot.cpu().numpy(), oi.cpu().numpy().view(np.uint32)
 
 
-@pytest.mark.parametrize("mesh_name", ["c2", "soup", "tiny"])
-def test_bvh_cast_matches_brute_force(M, orc, torch_cuda, mesh_name):
+@pytest.mark.parametrize("builder", ["host", "gpu"])
+@pytest.mark.parametrize("mesh_name", ["c2", "soup", "tiny", "one"])
+def test_bvh_cast_matches_brute_force(M, orc, torch_cuda, mesh_name, builder):
+    """Closest hits through the BVH equal the brute-force oracle's, for the
+    host SAH tree and for the GPU-rebuilt linear BVH."""
     torch = torch_cuda
     sc = S.config2(8, 8)
     if mesh_name == "soup":
         sc.mesh = S.random_soup(2000, 1)
     elif mesh_name == "tiny":
         sc.mesh = S.random_soup(3, 2)
+    elif mesh_name == "one":
+        sc.mesh = S.random_soup(1, 3)
     rng = np.random.default_rng(5)
     n = 6000
     o = rng.uniform(-0.6, 0.6, (n, 3)).astype(np.float32)
@@ -148,6 +153,9 @@ def test_bvh_cast_matches_brute_force(M, orc, torch_cuda, mesh_name):
     ctx = M.mrf_context_create(0)
     m = sc.mesh
     bvh = M.mrf_bvh_build(ctx, m.verts.ctypes.data, m.verts.shape[0], m.tris.ctypes.data, m.mat.ctypes.data, m.n_tris)
+    if builder == "gpu":
+        v = np.ascontiguousarray(m.verts)
+        M.check(M.lib().mrf_bvh_rebuild(bvh, v.ctypes.data, v.shape[0], None))
     t_g, id_g = _cast(M, torch, ctx, bvh, o, d, skip)
     M.mrf_bvh_destroy(bvh)
     M.mrf_context_destroy(ctx)
@@ -166,7 +174,7 @@ def test_bvh_cast_matches_brute_force(M, orc, torch_cuda, mesh_name):
         else:
             assert np.isinf(t_g[i])
     assert flagged <= n * 1e-3
-    if mesh_name != "tiny":
+    if mesh_name not in ("tiny", "one"):
         assert hits > n // 10
 
 
