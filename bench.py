@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--frames", type=int, default=300)
     ap.add_argument("--rebuild", type=int, default=30)
     ap.add_argument("--spp", type=int, default=4)
+    ap.add_argument("--train-steps", type=int, default=6000, help="area: Adam steps of the shadow network")
+    ap.add_argument("--train-pairs-log2", type=int, default=24, help="area: log2 of the training pairs")
     return ap.parse_args()
 
 
@@ -140,13 +142,24 @@ def job_throughput(units_per_rank: int, world: int, ms_max: float) -> float:
     return world * units_per_rank / (ms_max / 1e3)
 
 
-def measured_traffic(kernel_file: str, summary: str):
-    """DRAM bytes per launch from a committed ncu summary, or None when the
-    kernel's source has changed since the counters were taken."""
+def source_hash(files) -> str:
+    """sha256 over the concatenated kernel source files."""
     import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()
+
+
+FIELD_TC_SOURCES = ("paper_2309_04581_gb300/csrc/field_tc.cu", "paper_2309_04581_gb300/csrc/tc.cuh")
+
+
+def measured_traffic(kernel_files, summary: str):
+    """DRAM bytes per launch from a committed ncu summary, or None when the
+    kernel's sources have changed since the counters were taken."""
     import re
     try:
-        src = hashlib.sha256(open(os.path.join(ROOT, kernel_file), "rb").read()).hexdigest()
+        src = source_hash(kernel_files)
         text = open(os.path.join(ROOT, "profiles", summary)).read()
     except OSError:
         return None
@@ -299,7 +312,7 @@ def run_ours(args):
         f_ms = kernels["field"]["ms_per_step"]
         nbytes = (GATHER_BYTES_PER_SAMPLE + SAMPLE_IO_BYTES) * samples
         ach = nbytes / (f_ms / 1e3) / 1e9
-        traffic = measured_traffic("paper_2309_04581_gb300/csrc/field_tc.cu",
+        traffic = measured_traffic(FIELD_TC_SOURCES,
                                    "field_tc_dram_traffic_hashgrid_800x800_bf16.md") \
             if (args.width, args.height, args.precision) == (800, 800, "bf16") else None
         tfl = MLP_FLOP_PER_SAMPLE * samples / (f_ms / 1e3) / 1e12
@@ -444,7 +457,8 @@ def run_area(args):
     with 16 shadow rays each per diffuse hit, 1 spp, --width x --height
     (default 1920x1080), BF16 field.  Times the frame with the shadow rays
     marched (512 samples per path, up to 16 generation rounds) and with the learned
-    transmittance (BF16 weights, trained here on 2^24 pairs), and the image
+    transmittance (BF16 weights on the tensor cores, trained here on 2^24
+    pairs), and the image
     error of both against the FP64 oracle on every 32nd row and column."""
     import torch
     from paper_2309_04581_gb300 import scenes as S
@@ -459,14 +473,14 @@ def run_area(args):
     # buffer evaluated in up to 16 rounds per segment
     r.set_tuning(8, 512, 16)
     best = r.tuning()
-    net = M.ShadowNet(r, seed=7)
+    net = M.ShadowNet(r, seed=7, lr_decay=0.9995)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    pairs = net.pairs(11, 0, 1 << 24)
+    pairs = net.pairs(11, 0, 1 << args.train_pairs_log2)
     torch.cuda.synchronize()
     t_pairs = time.perf_counter() - t0
     t0 = time.perf_counter()
-    net.train(pairs, 1 << 16, 3000)
+    net.train(pairs, 1 << 16, args.train_steps)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del pairs
@@ -510,7 +524,8 @@ def run_area(args):
                   "shadow_samples_evaluated": st_m["shadow_samples_evaluated"], "image_error_vs_oracle": err(img_m)},
         "network": {"ms_per_step": ms_n, "kernels_ms": k_n, "shadow_net_evals": st_n["shadow_net_evals"],
                     "image_error_vs_oracle": err(img_n), "pairs_s": t_pairs, "train_s": t_train,
-                    "train": "2^24 pairs (FP32 march labels), 3000 Adam steps of 65536"},
+                    "train": f"2^{args.train_pairs_log2} pairs (FP32 march labels), {args.train_steps} Adam steps "
+                             "of 65536, lr 1e-2 x 0.9995^t"},
         "speedup_vs_march": ms_m / ms_n, "oracle_pixels": int(ok.sum()),
     }
     print(json.dumps(line))

@@ -90,6 +90,7 @@ struct mrf_shadow_net {
     mrf_context *ctx = nullptr;
     ShadowNetDev dev{};
     float *params = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr, *mlp_inf = nullptr;
+    uint8_t *lp = nullptr;   // BF16 tensor-core weights (BF16 networks)
     uint64_t n_params = 0;
     uint32_t t = 0;          // Adam steps taken
     uint64_t cursor = 0;     // next training pair
@@ -1379,6 +1380,7 @@ float splitmix_uniform(uint64_t &x, float a) {
 mrf_status snet_refresh(mrf_shadow_net *n, cudaStream_t s) {
     CUDA_TRY(launch_snet_refresh(n->params + (n->n_params - kSnetMlp), n->mlp_inf, n->precision == MRF_PREC_BF16, s),
              "shadow net: refresh");
+    if (n->lp) CUDA_TRY(launch_snet_pack_lp(n->params + (n->n_params - kSnetMlp), n->lp, s), "shadow net: pack");
     return MRF_OK;
 }
 }  // namespace
@@ -1433,12 +1435,14 @@ mrf_status mrf_shadow_net_create(mrf_context *ctx, const mrf_field *field, const
         (st = dev_alloc(&n->m, n->n_params, "shadow net Adam m")) ||
         (st = dev_alloc(&n->v, n->n_params, "shadow net Adam v")) ||
         (st = dev_alloc(&n->grad, n->n_params, "shadow net gradient")) ||
-        (st = dev_alloc(&n->mlp_inf, (size_t)kSnetMlp + 4, "shadow net rendering weights"))) {
+        (st = dev_alloc(&n->mlp_inf, (size_t)kSnetMlp + 4, "shadow net rendering weights")) ||
+        (desc->precision == MRF_PREC_BF16 && (st = dev_alloc(&n->lp, snet_lp_bytes(), "shadow net BF16 weights")))) {
         mrf_shadow_net_destroy(n);
         return st;
     }
     D.table = n->params;
     D.mlp = n->mlp_inf;
+    D.lp = n->lp;
     if (desc->params) {
         if (cudaMemcpy(n->params, desc->params, n->n_params * sizeof(float), cudaMemcpyDefault) != cudaSuccess) {
             mrf_shadow_net_destroy(n);
@@ -1480,6 +1484,7 @@ void mrf_shadow_net_destroy(mrf_shadow_net *n) {
     cudaFree(n->v);
     cudaFree(n->grad);
     cudaFree(n->mlp_inf);
+    cudaFree(n->lp);
     delete n;
 }
 

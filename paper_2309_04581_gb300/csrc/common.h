@@ -110,6 +110,7 @@ struct ShadowNetDev {
     float to_local[12];                 // world-to-local [R^T | -R^T t]
     const float *table;                 // FP32, [level][entry][2]
     const float *mlp;                   // rendering copy of the MLP part (BF16-rounded for BF16)
+    const uint8_t *lp;                  // BF16 weights in the tensor-core operand layout (BF16 networks), or NULL
 };
 
 // One pinhole view of a multi-view batch: orthonormal basis in FP32 (built in
@@ -194,6 +195,11 @@ cudaError_t launch_snet_adam(float *p, float *m, float *v, float *g, uint64_t n,
                              float eps, double c1, double c2, cudaStream_t s);
 cudaError_t launch_snet_refresh(const float *mlp, float *out, bool bf16, cudaStream_t s);
 cudaError_t launch_snet_eval(const ShadowNetDev &N, const float *pairs, uint32_t n, float *out, cudaStream_t s);
+size_t snet_lp_bytes();
+cudaError_t launch_snet_pack_lp(const float *mlp, uint8_t *lp, cudaStream_t s);
+cudaError_t launch_snet_tc(const ShadowNetDev &N, const uint8_t *lp, const float *mlp, const uint32_t *queue,
+                           const float4 *hp, const float4 *sdir, int K, const float *pairs, const uint32_t *n_dev,
+                           uint32_t n_host, float *out, unsigned *status, unsigned long long *stats, cudaStream_t s);
 // bvh_lbvh.cu
 size_t bvh_rebuild_scratch_words(uint32_t n);
 cudaError_t launch_bvh_rebuild(float4 *nodes, int *parent, int *counters, float4 *tris, uint32_t *order,

@@ -883,9 +883,15 @@ cudaError_t enqueue_frame(const WfParams &W, const RenderParams &P, uint32_t pat
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (P.has_snet) {
             timer_begin(timer, MRF_KERNEL_SHADOW_NET, s);
-            wf_shadow_net<<<152 * 4, 128, 0, s>>>(W);
+            if (P.snet.lp)   // BF16 network: tensor cores
+                e = launch_snet_tc(P.snet, P.snet.lp, P.snet.mlp, W.squeue, W.hp, W.sdir, P.n_shadow, nullptr,
+                                   W.ctr + 3, paths * (uint32_t)P.n_shadow, W.sdepth, P.status, P.stats, s);
+            else {
+                wf_shadow_net<<<152 * 4, 128, 0, s>>>(W);
+                e = cudaGetLastError();
+            }
             timer_end(timer, s);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if (e != cudaSuccess) return e;
         }
         // generation rounds: each evaluates and composites what fits the sample
         // buffer; slots left over wait for the next round (the last leftovers

@@ -22,6 +22,7 @@
 
 #include "path.cuh"
 #include "shadow_net.cuh"
+#include "tc.cuh"
 
 namespace mrf {
 
@@ -436,7 +437,219 @@ __global__ void __launch_bounds__(128) snet_pairs_kernel(const RenderParams P, u
     o[1] = make_float4(w.y, w.z, D, expf(-depth));
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core inference (BF16 weights and activations, FP32 accumulators in
+// TMEM): four chained tcgen05 MMAs per tile of 128 shadow rays, M = 128 and
+// N = 64 (the last layer padded to N = 16), like the field kernel.
+constexpr int kLpW1 = 0, kLpW2 = 4096, kLpW3 = 12288, kLpW4 = 20480, kLpBytes = 22528;
+constexpr int kTcGroups = 4;   // 128-ray tiles in flight per CTA (256 TMEM columns: two CTAs per SM)
+constexpr int kTcBias = kLpBytes, kTcBars = kTcBias + (3 * kSnetW + 4) * 4, kTcSlot = kTcBars + 8 * kTcGroups,
+              kTcA = (kTcSlot + 8 + 127) / 128 * 128, kTcBytes = kTcA + kTcGroups * 16384;
+
+// byte offset of element (r, k) of an R x K operand in the canonical K-major layout
+__device__ __forceinline__ uint32_t umma_off(int r, int k, int K) {
+    return (uint32_t)((r >> 3) * (K >> 3) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// BF16 copies of W1 (64 x 32), W2, W3 (64 x 64) and W4 (1 x 64, padded to 16
+// rows) in the MMA operand layout, from the FP32 MLP part.
+__global__ void snet_pack_lp(const float *__restrict__ mlp, uint8_t *__restrict__ lp) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    auto put = [&](uint32_t off, float v) {
+        *reinterpret_cast<__nv_bfloat16 *>(lp + off) = __float2bfloat16_rn(v);
+    };
+    if (i < kSnetW * kSnetIn) put(kLpW1 + umma_off(i / kSnetIn, i % kSnetIn, kSnetIn), mlp[i]);
+    if (i < kSnetW * kSnetW) {
+        put(kLpW2 + umma_off(i / kSnetW, i % kSnetW, kSnetW), mlp[kSnetOffW2 + i]);
+        put(kLpW3 + umma_off(i / kSnetW, i % kSnetW, kSnetW), mlp[kSnetOffW3 + i]);
+    }
+    if (i < 16 * kSnetW) {
+        const int r = i / kSnetW, k = i % kSnetW;
+        put(kLpW4 + umma_off(r, k, kSnetW), r == 0 ? mlp[kSnetOffW4 + k] : 0.f);
+    }
+}
+
+// Network transmittance on the tensor cores.  Queue mode (queue != NULL): ray
+// i is queue[i] = slot * K + q with point hp[slot] and direction sdir[idx],
+// result to out[idx]; pairs mode: ray i is pairs[8 i ..], result to out[i].
+// n = min(*n_dev, n_host) rays (n_dev nullable).
+__global__ void __launch_bounds__(128 * kTcGroups, 2)
+    snet_tc_kernel(const ShadowNetDev N, const uint8_t *__restrict__ lp, const float *__restrict__ mlp,
+                   const uint32_t *__restrict__ queue, const float4 *__restrict__ hp, const float4 *__restrict__ sdir,
+                   int K, const float *__restrict__ pairs, const uint32_t *__restrict__ n_dev, uint32_t n_host,
+                   float *__restrict__ out, unsigned *__restrict__ status, unsigned long long *stats) {
+    using namespace tc;
+    extern __shared__ __align__(128) uint8_t smem[];
+    float *sBias = reinterpret_cast<float *>(smem + kTcBias);
+    uint32_t *sTmem = reinterpret_cast<uint32_t *>(smem + kTcSlot);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int g = tid >> 7, gt = tid & 127, gw = gt >> 5;
+    for (int o = tid * 16; o < kLpBytes; o += 128 * kTcGroups * 16)
+        *reinterpret_cast<uint4 *>(smem + o) = __ldg(reinterpret_cast<const uint4 *>(lp + o));
+    if (tid < kSnetW) {
+        sBias[tid] = mlp[kSnetOffB1 + tid];
+        sBias[kSnetW + tid] = mlp[kSnetOffB2 + tid];
+        sBias[2 * kSnetW + tid] = mlp[kSnetOffB3 + tid];
+    }
+    if (tid == 0) sBias[3 * kSnetW] = mlp[kSnetOffB4];
+    const uint32_t bar = smem_u32(smem + kTcBars + 8 * g);
+    if (gt == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(sTmem)),
+                     "r"(64 * kTcGroups)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *sTmem;
+    const uint32_t t_acc = tmem + 64u * (uint32_t)g;
+    const uint32_t t_row = t_acc + ((uint32_t)(gw * 32) << 16);
+    uint8_t *sA = smem + kTcA + g * 16384;
+    const uint32_t aA = smem_u32(sA), aW1 = smem_u32(smem + kLpW1), aW2 = smem_u32(smem + kLpW2),
+                   aW3 = smem_u32(smem + kLpW3), aW4 = smem_u32(smem + kLpW4);
+    constexpr uint32_t id64 = instr_desc(true, 128, 64), id16 = instr_desc(true, 128, 16);
+    const uint32_t n = n_dev ? min(*n_dev, n_host) : n_host;
+    const int bar_id = 1 + g;
+    uint32_t phase = 0, evals = 0;
+    bool ok = true;
+    for (uint32_t tile = blockIdx.x * kTcGroups + g; tile * 128u < n; tile += gridDim.x * kTcGroups) {
+        const uint32_t i = tile * 128u + gt;
+        const bool valid = i < n;
+        uint32_t dst = i;
+        V3 p = v3(0.f, 0.f, 0.f), w = v3(0.f, 0.f, 1.f);
+        if (valid) {
+            if (queue) {
+                dst = queue[i];
+                const float4 h4 = hp[dst / (uint32_t)K], sh = sdir[dst];
+                p = v3(h4.x, h4.y, h4.z);
+                w = v3(sh.x, sh.y, sh.z);
+            } else {
+                const float4 *q = reinterpret_cast<const float4 *>(pairs + 8 * (size_t)i);
+                const float4 a = __ldg(q), b = __ldg(q + 1);
+                p = v3(a.x, a.y, a.z);
+                w = v3(a.w, b.x, b.y);
+            }
+            ++evals;
+        }
+        snet_to_local(N, p, w);
+        {
+            float x[kSnetIn];
+            snet_encode(N, p, w, x);
+#pragma unroll
+            for (int c = 0; c < kSnetIn / 8; ++c) {
+                uint32_t v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] = valid ? pack2<true>(x[8 * c + 2 * q], x[8 * c + 2 * q + 1]) : 0u;
+                store_chunk(sA, gt, c, (kSnetIn / 8) * 128, make_uint4(v[0], v[1], v[2], v[3]));
+            }
+        }
+        // layer 1: K = 32
+        fence_async_smem();
+        fence_before_sync();
+        if (group_sync_or(bar_id, !ok)) break;
+        if (gt == 0) {
+            fence_after_sync();
+#pragma unroll
+            for (int k = 0; k < kSnetIn / 16; ++k)
+                mma_f16(t_acc, smem_desc(aA + 256 * k, 128, 512), smem_desc(aW1 + 256 * k, 128, 512), id64, k);
+            mma_commit(bar);
+        }
+        ok &= mbar_wait(bar, phase);
+        phase ^= 1;
+        fence_after_sync();
+        // layers 2 and 3: K = 64, each fed by the previous epilogue
+        const uint32_t wl[2] = {aW2, aW3};
+#pragma unroll
+        for (int L = 0; L < 2; ++L) {
+            {
+                uint32_t r[32];
+                tmem_ld_x32(t_row, r);
+                relu_bias_store<true>(r, sBias + 64 * L, sA, gt, 0);
+                tmem_ld_x32(t_row + 32, r);
+                relu_bias_store<true>(r, sBias + 64 * L + 32, sA, gt, 4);
+            }
+            fence_async_smem();
+            fence_before_sync();
+            if (group_sync_or(bar_id, !ok)) { ok = false; break; }
+            if (gt == 0) {
+                fence_after_sync();
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    mma_f16(t_acc, smem_desc(aA + 256 * k, 128, 1024), smem_desc(wl[L] + 256 * k, 128, 1024), id64, k);
+                mma_commit(bar);
+            }
+            ok &= mbar_wait(bar, phase);
+            phase ^= 1;
+            fence_after_sync();
+        }
+        if (!ok) break;
+        // layer 4: N = 16 (row 0 is W4)
+        {
+            uint32_t r[32];
+            tmem_ld_x32(t_row, r);
+            relu_bias_store<true>(r, sBias + 128, sA, gt, 0);
+            tmem_ld_x32(t_row + 32, r);
+            relu_bias_store<true>(r, sBias + 160, sA, gt, 4);
+        }
+        fence_async_smem();
+        fence_before_sync();
+        if (group_sync_or(bar_id, !ok)) break;
+        if (gt == 0) {
+            fence_after_sync();
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                mma_f16(t_acc, smem_desc(aA + 256 * k, 128, 1024), smem_desc(aW4 + 256 * k, 128, 1024), id16, k);
+            mma_commit(bar);
+        }
+        ok &= mbar_wait(bar, phase);
+        phase ^= 1;
+        fence_after_sync();
+        {
+            uint32_t r[16];
+            tmem_ld_x16(t_row, r);
+            const float z = __uint_as_float(r[0]) + sBias[3 * kSnetW];
+            if (valid) out[dst] = 1.f / (1.f + expf(-z));
+        }
+        fence_before_sync();
+    }
+    if (!ok && gt == 0 && status) atomicOr(status, 4u);
+    if (stats) {
+        Counters C = {};
+        C.net = evals;
+        flush_counters(stats, C);
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64 * kTcGroups)
+                     : "memory");
+}
+
 }  // namespace
+
+size_t snet_lp_bytes() { return kLpBytes; }
+
+cudaError_t launch_snet_pack_lp(const float *mlp, uint8_t *lp, cudaStream_t s) {
+    snet_pack_lp<<<(kSnetW * kSnetW + 255) / 256, 256, 0, s>>>(mlp, lp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_snet_tc(const ShadowNetDev &N, const uint8_t *lp, const float *mlp, const uint32_t *queue,
+                           const float4 *hp, const float4 *sdir, int K, const float *pairs, const uint32_t *n_dev,
+                           uint32_t n_host, float *out, unsigned *status, unsigned long long *stats, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(snet_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcBytes);
+    if (e != cudaSuccess) return e;
+    snet_tc_kernel<<<152 * 2, 128 * kTcGroups, kTcBytes, s>>>(N, lp, mlp, queue, hp, sdir, K, pairs, n_dev, n_host,
+                                                              out, status, stats);
+    return cudaGetLastError();
+}
 
 size_t snet_train_smem() { return sizeof(TrainSmem); }
 
@@ -475,6 +688,7 @@ cudaError_t launch_snet_refresh(const float *mlp, float *out, bool bf16, cudaStr
 
 cudaError_t launch_snet_eval(const ShadowNetDev &N, const float *pairs, uint32_t n, float *out, cudaStream_t s) {
     if (!n) return cudaSuccess;
+    if (N.lp) return launch_snet_tc(N, N.lp, N.mlp, nullptr, nullptr, nullptr, 1, pairs, nullptr, n, out, nullptr, nullptr, s);
     snet_eval_kernel<<<(n + 127) / 128, 128, 0, s>>>(N, pairs, n, out);
     return cudaGetLastError();
 }

@@ -84,6 +84,23 @@ def _unambiguous(on, pr, margin=1e-5):
     return keep
 
 
+def test_tensor_core_inference_matches_oracle(env, orc, renderer):
+    """BF16 networks run on the tensor cores (BF16 weights, inputs and
+    activations, FP32 accumulation): their error against the FP64 network."""
+    torch, M = env
+    params = _random_params(6)
+    net = M.ShadowNet(renderer, params=params, precision=M.MRF_PREC_BF16)
+    pairs = net.pairs(SEED, 100, 128 * 37 + 5)      # many tiles and a ragged one
+    got = net.eval(pairs).cpu().numpy().astype(np.float64)
+    on = _onet(orc, params)
+    pr = pairs.cpu().numpy().astype(np.float64)
+    ref = np.array([on.forward(pr[k, :3], pr[k, 3:6]) for k in range(pr.shape[0])])
+    err = np.abs(got - ref)
+    print(f"BF16 tensor-core network: max |dT| {err.max():.3g}, mean {err.mean():.3g}")
+    assert err.max() <= 2e-2 and err.mean() <= 2e-3
+    net.close()
+
+
 def test_gradient_matches_oracle(env, orc, renderer):
     torch, M = env
     params = _random_params(4)
