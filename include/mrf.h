@@ -114,6 +114,18 @@ typedef struct mrf_field_desc {
      * support above are given in the field's local frame.  R must be a rotation
      * (orthonormal within 1e-4), else MRF_ERR_INVALID_ARG. */
     const float *pose;
+    /* View-dependent radiance (the network layout of Instant-NGP, which the
+     * paper renders with, Sec. 3.3): when non-zero, layer 1 (w1, b1) feeds a
+     * density head wd2 (16 x 64), bd2 whose output 0 gives sigma, and a colour
+     * network takes the 16 head outputs and the 16 real spherical harmonics of
+     * the unit view direction in the field's frame (bands 0..3):
+     * 32 -> 64 (wc1: 64 x 32, bc1) -> 64 (wc2, bc2) -> 3 (wc3: 3 x 64, bc3),
+     * r = softplus.  w2, b2, w3, b3 may then be NULL.  Such fields are
+     * evaluated in FP32 on the CUDA cores by both engines (the tensor-core
+     * field kernel serves the view-independent layout only); mrf_field_query
+     * evaluates them for the view direction +z. */
+    int32_t view_dependent;
+    const float *wd2, *bd2, *wc1, *bc1, *wc2, *bc2, *wc3, *bc3;
 } mrf_field_desc;
 
 /* Copies the description into device memory.  MRF_ERR_INVALID_ARG for an

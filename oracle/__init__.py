@@ -65,6 +65,8 @@ class OrcScene(C.Structure):
         ("n_views", C.c_uint32), ("view_cam", _fp), ("view_size", _u32p),
         ("light_kind", _i32p), ("light_v1", _fp), ("light_v2", _fp), ("light_samples", _u32p),
         ("shadow_net", C.c_void_p), ("shadow_mask", C.c_int32), ("light_mask", _fp),
+        ("view_dep", C.c_int32), ("wd2", _fp), ("bd2", _fp), ("wc1", _fp), ("bc1", _fp), ("wc2", _fp), ("bc2", _fp),
+        ("wc3", _fp), ("bc3", _fp),
     ]
 
 
@@ -96,6 +98,9 @@ def lib():
         L.orc_support.argtypes = [C.POINTER(OrcScene), _dp]
         L.orc_field_eval.restype = C.c_int
         L.orc_field_eval.argtypes = [C.POINTER(OrcScene), _dp, _dp, _dp]
+        L.orc_field_eval_dir.restype = C.c_int
+        L.orc_field_eval_dir.argtypes = [C.POINTER(OrcScene), _dp, _dp, _dp, _dp]
+        L.orc_mlp_view.argtypes = [C.POINTER(OrcScene), _dp, _dp, _dp, _dp]
         L.orc_box_interval.restype = C.c_int
         L.orc_box_interval.argtypes = [C.POINTER(OrcScene), _dp, _dp, _dp, _dp]
         L.orc_transmittance.restype = C.c_double
@@ -188,6 +193,10 @@ class OracleScene:
             s.n_support = f.support_center.shape[0]
             s.sup_c = _ptr(arr(f.support_center, np.float32), _fp)
             s.sup_r = _ptr(arr(f.support_radius, np.float32), _fp)
+            if getattr(f, "view", None) is not None:
+                s.view_dep = 1
+                for nm in ("wd2", "bd2", "wc1", "bc1", "wc2", "bc2", "wc3", "bc3"):
+                    setattr(s, nm, _ptr(arr(f.view[nm], np.float32), _fp))
         m = scene.mesh
         s.n_verts = m.verts.shape[0]
         s.verts = _ptr(arr(m.verts, np.float32), _fp)
@@ -303,6 +312,21 @@ def field_eval(oscene: OracleScene, p):
     rgb = np.zeros(3)
     lib().orc_field_eval(oscene.ref, _ptr(_d(p), _dp), _ptr(sig, _dp), _ptr(rgb, _dp))
     return float(sig[0]), rgb
+
+
+def field_eval_dir(oscene: OracleScene, p, d):
+    sig = np.zeros(1)
+    rgb = np.zeros(3)
+    lib().orc_field_eval_dir(oscene.ref, _ptr(_d(p), _dp), _ptr(_d(d), _dp), _ptr(sig, _dp), _ptr(rgb, _dp))
+    return float(sig[0]), rgb
+
+
+def mlp_view(oscene: OracleScene, feat, d):
+    """View-dependent networks on given encoder features: (sigma logit, rgb)."""
+    f = np.ascontiguousarray(np.asarray(feat, np.float64))
+    lg, rgb = np.zeros(1), np.zeros(3)
+    lib().orc_mlp_view(oscene.ref, _ptr(f, _dp), _ptr(_d(d), _dp), _ptr(lg, _dp), _ptr(rgb, _dp))
+    return float(lg[0]), rgb
 
 
 def box_interval(oscene: OracleScene, o, d):

@@ -120,7 +120,17 @@ typedef struct {
      * light whose shadow ray from the sample is blocked by a mesh */
     int32_t shadow_mask;
     const float *light_mask;
+    /* view-dependent radiance (the network layout of Instant-NGP): when
+     * non-zero the hash field's density network is 32 -> 64 (w1, b1) -> 16
+     * (wd2: 16 x 64, bd2), sigma from its output 0, and a colour network takes
+     * those 16 outputs and the 16 spherical harmonics of the view direction
+     * (in the field's frame): 32 -> 64 (wc1, bc1) -> 64 (wc2, bc2) -> 3
+     * (wc3: 3 x 64, bc3), rgb = softplus; w2, b2, w3, b3 are unused */
+    int32_t view_dep;
+    const float *wd2, *bd2, *wc1, *bc1, *wc2, *bc2, *wc3, *bc3;
 } orc_scene;
+
+void orc_sh16(const double w[3], double Y[16]);
 
 double orc_snet_forward(const struct orc_snet *n, const double p[3], const double w[3]);
 
@@ -308,7 +318,56 @@ static int inside_box(const orc_scene *sc, const double p[3]) {
 /* Density sigma(p) and linear-HDR radiance r(p) (Eq. 7 and the HDR radiance of
  * Sec. 3.1).  Returns 1 when the sample needed a network evaluation (non-zero
  * support), for the sample counters. */
+/* View-dependent hash field: density network, then the colour network of
+ * the density outputs and SH16 of the unit view direction d (field frame). */
+void orc_mlp_view(const orc_scene *sc, const double *feat, const double d[3], double *sigma_logit, double rgb[3]) {
+    const uint32_t W = sc->mlp_width, D = sc->n_levels * sc->n_feat;
+    double h1[256], dn[16], x[32], c1[256], c2[256];
+    for (uint32_t j = 0; j < W; ++j) {
+        double a = sc->b1[j];
+        for (uint32_t i = 0; i < D; ++i) a += (double)sc->w1[j * D + i] * feat[i];
+        h1[j] = a > 0 ? a : 0;
+    }
+    for (uint32_t j = 0; j < 16; ++j) {
+        double a = sc->bd2[j];
+        for (uint32_t i = 0; i < W; ++i) a += (double)sc->wd2[j * W + i] * h1[i];
+        dn[j] = a;
+    }
+    *sigma_logit = dn[0];
+    double n = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    double u[3] = {d[0] / n, d[1] / n, d[2] / n};
+    for (int j = 0; j < 16; ++j) x[j] = dn[j];
+    orc_sh16(u, x + 16);
+    for (uint32_t j = 0; j < W; ++j) {
+        double a = sc->bc1[j];
+        for (int i = 0; i < 32; ++i) a += (double)sc->wc1[j * 32 + i] * x[i];
+        c1[j] = a > 0 ? a : 0;
+    }
+    for (uint32_t j = 0; j < W; ++j) {
+        double a = sc->bc2[j];
+        for (uint32_t i = 0; i < W; ++i) a += (double)sc->wc2[j * W + i] * c1[i];
+        c2[j] = a > 0 ? a : 0;
+    }
+    for (int c = 0; c < 3; ++c) {
+        double a = sc->bc3[c];
+        for (uint32_t i = 0; i < W; ++i) a += (double)sc->wc3[c * W + i] * c2[i];
+        rgb[c] = log1p(exp(a));   /* softplus */
+    }
+}
+
+static int field_eval_dir(const orc_scene *sc, const double p[3], const double d[3], double *sigma, double rgb[3]);
+
 int orc_field_eval(const orc_scene *sc, const double p[3], double *sigma, double rgb[3]) {
+    const double d[3] = {0.0, 0.0, 1.0};
+    return field_eval_dir(sc, p, d, sigma, rgb);
+}
+
+/* Field at p seen along d (d only matters for view-dependent radiance). */
+int orc_field_eval_dir(const orc_scene *sc, const double p[3], const double d[3], double *sigma, double rgb[3]) {
+    return field_eval_dir(sc, p, d, sigma, rgb);
+}
+
+static int field_eval_dir(const orc_scene *sc, const double p[3], const double d[3], double *sigma, double rgb[3]) {
     *sigma = 0.0; rgb[0] = rgb[1] = rgb[2] = 0.0;
     if (!inside_box(sc, p)) return 0;
     if (sc->field_kind == ORC_FIELD_CONST) {
@@ -334,6 +393,12 @@ int orc_field_eval(const orc_scene *sc, const double p[3], double *sigma, double
     if (sup <= 0.0) return 0;   /* sigma = 0 * exp(...) exactly */
     double feat[64], o[4];
     orc_hash_encode(sc, p, feat);
+    if (sc->view_dep) {
+        double logit;
+        orc_mlp_view(sc, feat, d, &logit, rgb);
+        *sigma = sup * exp(logit < 15.0 ? logit : 15.0);
+        return 1;
+    }
     orc_mlp(sc, feat, o);
     *sigma = sup * exp(o[0] < 15.0 ? o[0] : 15.0);
     for (int c = 0; c < 3; ++c) rgb[c] = log1p(exp(o[1 + c]));   /* softplus */
@@ -401,7 +466,7 @@ static int march(const orc_scene *sc, const double ow[3], const double dw[3], do
         if (delta <= 0) continue;
         double p[3] = {o[0] + tm * d[0], o[1] + tm * d[1], o[2] + tm * d[2]}, sigma, rgb[3];
         cnt[C_NOMINAL]++;
-        cnt[C_SUPPORTED] += orc_field_eval(sc, p, &sigma, rgb);
+        cnt[C_SUPPORTED] += field_eval_dir(sc, p, d, &sigma, rgb);
         double att = exp(-sigma * delta), alpha = -expm1(-sigma * delta), m = 1.0;
         if (sc->shadow_mask && sigma > 0.0) {
             /* the sample in world space: the pose keeps ray parameters */

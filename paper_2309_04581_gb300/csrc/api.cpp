@@ -322,12 +322,18 @@ static mrf_status field_create_impl(mrf_context *ctx, const mrf_field_desc *D, m
     }
     if ((st = upload(f, reinterpret_cast<const uint32_t *>(D->table), (size_t)L * T, &F.table, "hash table")))
         return st;
-    // pack the MLP: W1T[in][64], b1, W2[64][64], b2, W3T[64][4], b3
-    std::vector<float> w1, b1, w2, b2, w3, b3;
-    if ((st = fetch(w1, D->w1, 64 * (size_t)n_in)) || (st = fetch(b1, D->b1, 64)) || (st = fetch(w2, D->w2, 64 * 64)) ||
-        (st = fetch(b2, D->b2, 64)) || (st = fetch(w3, D->w3, 4 * 64)) || (st = fetch(b3, D->b3, 4)))
-        return st;
-    std::vector<float> pk(mlp_floats((int)n_in));
+    // pack the MLP: W1T[in][64], b1, W2[64][64], b2, W3T[64][4], b3 (+ the view-dependent heads)
+    const bool vd = D->view_dependent != 0;
+    if (vd && n_in != 32) return fail(MRF_ERR_INVALID_ARG, "mrf_field_create: view-dependent fields need 32 inputs");
+    std::vector<float> w1, b1, w2(64 * 64, 0.f), b2(64, 0.f), w3(4 * 64, 0.f), b3(4, 0.f);
+    if ((st = fetch(w1, D->w1, 64 * (size_t)n_in)) || (st = fetch(b1, D->b1, 64))) return st;
+    if (!vd || D->w2) {
+        if (!D->w2 || !D->b2 || !D->w3 || !D->b3) return fail(MRF_ERR_INVALID_ARG, "mrf_field_create: MLP arrays missing");
+        if ((st = fetch(w2, D->w2, 64 * 64)) || (st = fetch(b2, D->b2, 64)) || (st = fetch(w3, D->w3, 4 * 64)) ||
+            (st = fetch(b3, D->b3, 4)))
+            return st;
+    }
+    std::vector<float> pk(mlp_floats((int)n_in) + (vd ? kViewFloats : 0));
     float *W1T = pk.data(), *B1 = W1T + n_in * 64, *W2 = B1 + 64, *B2 = W2 + 4096, *W3T = B2 + 64, *B3 = W3T + 256;
     for (uint32_t j = 0; j < 64; ++j)
         for (uint32_t i = 0; i < n_in; ++i) W1T[i * 64 + j] = w1[j * n_in + i];
@@ -337,6 +343,29 @@ static mrf_status field_create_impl(mrf_context *ctx, const mrf_field_desc *D, m
     for (int j = 0; j < 64; ++j)
         for (int o = 0; o < 4; ++o) W3T[j * 4 + o] = w3[o * 64 + j];
     std::memcpy(B3, b3.data(), 4 * 4);
+    if (vd) {
+        if (!D->wd2 || !D->bd2 || !D->wc1 || !D->bc1 || !D->wc2 || !D->bc2 || !D->wc3 || !D->bc3)
+            return fail(MRF_ERR_INVALID_ARG, "mrf_field_create: view-dependent heads missing");
+        std::vector<float> wd2, bd2, wc1, bc1, wc2, bc2, wc3, bc3;
+        if ((st = fetch(wd2, D->wd2, 16 * 64)) || (st = fetch(bd2, D->bd2, 16)) || (st = fetch(wc1, D->wc1, 64 * 32)) ||
+            (st = fetch(bc1, D->bc1, 64)) || (st = fetch(wc2, D->wc2, 64 * 64)) || (st = fetch(bc2, D->bc2, 64)) ||
+            (st = fetch(wc3, D->wc3, 3 * 64)) || (st = fetch(bc3, D->bc3, 3)))
+            return st;
+        float *WdT = pk.data() + mlp_floats((int)n_in), *BD = WdT + 64 * 16, *Wc1T = BD + 16, *BC1 = Wc1T + 32 * 64,
+              *WC2 = BC1 + 64, *BC2 = WC2 + 64 * 64, *Wc3T = BC2 + 64, *BC3 = Wc3T + 256;
+        for (int j = 0; j < 64; ++j)
+            for (int o = 0; o < 16; ++o) WdT[j * 16 + o] = wd2[o * 64 + j];
+        std::memcpy(BD, bd2.data(), 16 * 4);
+        for (int j = 0; j < 64; ++j)
+            for (int i = 0; i < 32; ++i) Wc1T[i * 64 + j] = wc1[j * 32 + i];
+        std::memcpy(BC1, bc1.data(), 64 * 4);
+        std::memcpy(WC2, wc2.data(), 4096 * 4);
+        std::memcpy(BC2, bc2.data(), 64 * 4);
+        for (int j = 0; j < 64; ++j)
+            for (int o = 0; o < 3; ++o) Wc3T[j * 4 + o] = wc3[o * 64 + j];
+        for (int o = 0; o < 3; ++o) BC3[o] = bc3[o];
+        F.view_dep = 1;
+    }
     F.n_in = (int)n_in;
     if ((st = upload(f, pk.data(), pk.size(), &F.mlp, "mlp weights"))) return st;
     // FP16 and BF16 copies of W1 (64 x in), W2 (64 x 64), W3 (padded to 16 x 64) in the
@@ -450,7 +479,7 @@ mrf_status mrf_field_query(mrf_context *ctx, const mrf_field *field, const float
         return fail(MRF_ERR_INVALID_ARG, "mrf_field_query: points and out must be device memory");
     const FieldDev &F = field->dev;
     const cudaStream_t s = (cudaStream_t)stream;
-    if (F.kind == MRF_FIELD_HASHGRID && F.precision != MRF_PREC_FP32) {
+    if (F.kind == MRF_FIELD_HASHGRID && F.precision != MRF_PREC_FP32 && !F.view_dep) {
         const int grid = (int)std::min<uint32_t>((n + 127) / 128, 152u * (uint32_t)field_tc_blocks_per_sm());
         CUDA_TRY(launch_field_tc(F, F.precision == MRF_PREC_BF16, points, 3, nullptr, n, reinterpret_cast<float4 *>(out),
                                  ctx->status, grid, s),
@@ -875,7 +904,7 @@ static mrf_status plan_render(mrf_context *ctx, const mrf_field *field, const mr
     }
     // AUTO: tensor-core field evaluation needs the wavefront engine's flat sample
     // tiles; FP32 runs the megakernel
-    const bool lowp = field->dev.kind == MRF_FIELD_HASHGRID && field->dev.precision != MRF_PREC_FP32;
+    const bool lowp = field->dev.kind == MRF_FIELD_HASHGRID && field->dev.precision != MRF_PREC_FP32 && !field->dev.view_dep;
     R.engine = opts->engine == MRF_ENGINE_AUTO ? (lowp ? MRF_ENGINE_WAVEFRONT : MRF_ENGINE_MEGAKERNEL) : opts->engine;
     if (R.engine == MRF_ENGINE_MEGAKERNEL && lowp)
         return fail(MRF_ERR_UNSUPPORTED, "mrf_render: FP16/BF16 fields run on the wavefront engine");
@@ -1243,6 +1272,8 @@ mrf_status mrf_render_static(mrf_context *ctx, const mrf_field *field, const mrf
     uint32_t count;
     if (rays->camera && rays->n_cameras > 1)
         return fail(MRF_ERR_UNSUPPORTED, "mrf_render_static: one camera or explicit rays; several views go to mrf_render");
+    if (field && field->dev.view_dep)
+        return fail(MRF_ERR_UNSUPPORTED, "mrf_render_static: view-dependent fields go to mrf_render");
     if (rays->camera) {
         const mrf_camera &c = *rays->camera;
         if (c.width == 0 || c.height == 0 || !(c.vfov_deg > 0.f && c.vfov_deg < 180.f))

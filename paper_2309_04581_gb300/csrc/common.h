@@ -18,6 +18,9 @@ constexpr int kStackSize = 64;
 
 // Packed FP32 MLP weights (floats):  W1T[in][64] | b1[64] | W2[64][64] | b2[64] | W3T[64][4] | b3[4]
 constexpr int mlp_floats(int n_in) { return n_in * 64 + 64 + 64 * 64 + 64 + 64 * 4 + 4; }
+// View-dependent heads appended after it (floats): WdT[64][16] bd[16] | Wc1T[32][64] bc1[64] |
+// Wc2[64][64] bc2[64] | Wc3T[64][4] bc3[4]
+constexpr int kViewFloats = 64 * 16 + 16 + 32 * 64 + 64 + 64 * 64 + 64 + 64 * 4 + 4;
 
 struct FieldDev {
     int kind;
@@ -33,7 +36,8 @@ struct FieldDev {
     uint32_t dense_mask;        // bit l set: level l indexed densely
     const uint32_t *table;      // [level][entry] binary16 pairs (feature 0 low half)
     int n_in;
-    const float *mlp;           // packed FP32, see mlp_floats
+    const float *mlp;           // packed FP32, see mlp_floats (+ kViewFloats when view_dep)
+    int view_dep;               // view-dependent radiance (colour network of the view direction)
     const void *mlp_lp;         // [FP16 | BF16] copies of W1, W2, W3 (W3 padded to 16 rows) in the
                                 // tensor-core operand layout, 64 * n_in * 2 + 10240 bytes each
     int n_support;
@@ -83,6 +87,11 @@ struct LightDev {
     float mask;         // r_src of the field-sample shadow mask
     float target[3];    // point the shadow-mask rays aim at (position or centroid)
 };
+
+// FP32 weights the CUDA-core field kernels stage in shared memory
+inline __host__ __device__ int field_mlp_floats(const FieldDev &F) {
+    return mlp_floats(F.n_in) + (F.view_dep ? kViewFloats : 0);
+}
 
 // device statistics counters (unsigned long long), in this order
 enum StatIndex {
@@ -177,7 +186,7 @@ inline void timer_end(KernelTimer *t, cudaStream_t s) { if (t) t->end(s); }
 // launchers (render_mega.cu)
 cudaError_t launch_render_megakernel(const RenderParams &P, cudaStream_t s, KernelTimer *timer = nullptr);
 cudaError_t launch_field_simt(const FieldDev &F, const float *pts, int stride, const uint32_t *n_dev, uint32_t n_host,
-                              float4 *out, int grid, cudaStream_t s);
+                              float4 *out, int grid, cudaStream_t s, const float4 *dirs = nullptr);
 // field_tc.cu
 cudaError_t launch_field_tc(const FieldDev &F, bool bf16, const float *pts, int stride, const uint32_t *n_dev,
                             uint32_t n_host, float4 *out, unsigned *status, int grid, cudaStream_t s, int groups = 8);

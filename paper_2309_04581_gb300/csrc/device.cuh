@@ -195,6 +195,30 @@ __device__ __forceinline__ float2 hash_level(const FieldDev &F, int l, V3 p) {
 
 __device__ __forceinline__ float softplusf(float x) { return fmaxf(x, 0.f) + log1pf(expf(-fabsf(x))); }
 
+// Real spherical harmonics of bands 0..3 at the unit direction w, orthonormal
+// on the sphere, ordered (l, m = -l..l).  Constants: 1/(2 sqrt(pi)),
+// sqrt(3/(4 pi)), sqrt(15/pi)/2, sqrt(5/pi)/4, sqrt(15/pi)/4, sqrt(35/(2 pi))/4,
+// sqrt(105/pi)/2, sqrt(21/(2 pi))/4, sqrt(7/pi)/4, sqrt(105/pi)/4.
+__device__ __forceinline__ void sh16(V3 w, float *Y) {
+    const float x = w.x, y = w.y, z = w.z;
+    Y[0] = 0.28209479177387814f;
+    Y[1] = 0.4886025119029199f * y;
+    Y[2] = 0.4886025119029199f * z;
+    Y[3] = 0.4886025119029199f * x;
+    Y[4] = 1.0925484305920792f * x * y;
+    Y[5] = 1.0925484305920792f * y * z;
+    Y[6] = 0.31539156525252005f * (3.f * z * z - 1.f);
+    Y[7] = 1.0925484305920792f * x * z;
+    Y[8] = 0.5462742152960396f * (x * x - y * y);
+    Y[9] = 0.5900435899266435f * y * (3.f * x * x - y * y);
+    Y[10] = 2.890611442640554f * x * y * z;
+    Y[11] = 0.4570457994644658f * y * (5.f * z * z - 1.f);
+    Y[12] = 0.3731763325901154f * z * (5.f * z * z - 3.f);
+    Y[13] = 0.4570457994644658f * x * (5.f * z * z - 1.f);
+    Y[14] = 1.445305721320277f * z * (x * x - y * y);
+    Y[15] = 0.5900435899266435f * x * (x * x - 3.f * y * y);
+}
+
 // Hash-grid field in FP32: encoding + MLP (weights `w` packed as in mlp_floats,
 // normally staged in shared memory).  Returns sigma; fills rgb when want_rgb.
 template <bool want_rgb>
@@ -246,6 +270,95 @@ __device__ __forceinline__ float hash_field_fp32(const FieldDev &F, const float 
         rgb[2] = softplusf(o3);
     }
     return s * expf(fminf(o0, 15.f));
+}
+
+// View-dependent hash field in FP32: layer 1 as above, a 16-output density
+// head (sigma from output 0), and when want_rgb a colour network of those 16
+// outputs and sh16 of the unit view direction d (field frame): 32 -> 64 ->
+// 64 -> 3, r = softplus.  Weights: mlp_floats(n_in) floats, then kViewFloats.
+template <bool want_rgb>
+__device__ __noinline__ float hash_field_view(const FieldDev &F, const float *__restrict__ w, V3 p, V3 d, float s,
+                                              float rgb[3]) {
+    const int n_in = F.n_in;
+    const float *W1T = w, *b1 = w + n_in * 64;
+    const float *WdT = w + mlp_floats(n_in), *bd = WdT + 64 * 16, *Wc1T = bd + 16, *bc1 = Wc1T + 32 * 64,
+                *Wc2 = bc1 + 64, *bc2 = Wc2 + 64 * 64, *Wc3T = bc2 + 64, *bc3 = Wc3T + 256;
+    float h1[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) h1[j] = b1[j];
+    for (int l = 0; l < F.n_levels; ++l) {
+        float2 f = hash_level(F, l, p);
+        const float4 *ra = reinterpret_cast<const float4 *>(W1T + (2 * l) * 64);
+        const float4 *rb = reinterpret_cast<const float4 *>(W1T + (2 * l + 1) * 64);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            float4 a = ra[j], b = rb[j];
+            h1[4 * j + 0] = fmaf(a.x, f.x, fmaf(b.x, f.y, h1[4 * j + 0]));
+            h1[4 * j + 1] = fmaf(a.y, f.x, fmaf(b.y, f.y, h1[4 * j + 1]));
+            h1[4 * j + 2] = fmaf(a.z, f.x, fmaf(b.z, f.y, h1[4 * j + 2]));
+            h1[4 * j + 3] = fmaf(a.w, f.x, fmaf(b.w, f.y, h1[4 * j + 3]));
+        }
+    }
+    float x[32];
+#pragma unroll
+    for (int o = 0; o < 16; ++o) x[o] = bd[o];
+#pragma unroll 4
+    for (int j = 0; j < 64; ++j) {
+        const float h = fmaxf(h1[j], 0.f);
+        const float4 *r = reinterpret_cast<const float4 *>(WdT + 16 * j);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 a = r[q];
+            x[4 * q + 0] = fmaf(a.x, h, x[4 * q + 0]);
+            x[4 * q + 1] = fmaf(a.y, h, x[4 * q + 1]);
+            x[4 * q + 2] = fmaf(a.z, h, x[4 * q + 2]);
+            x[4 * q + 3] = fmaf(a.w, h, x[4 * q + 3]);
+        }
+    }
+    const float sigma = s * expf(fminf(x[0], 15.f));
+    if (!want_rgb) return sigma;
+    sh16(normalize(d), x + 16);
+    float c1[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) c1[j] = bc1[j];
+#pragma unroll 4
+    for (int i = 0; i < 32; ++i) {
+        const float4 *r = reinterpret_cast<const float4 *>(Wc1T + 64 * i);
+        const float xi = x[i];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const float4 a = r[q];
+            c1[4 * q + 0] = fmaf(a.x, xi, c1[4 * q + 0]);
+            c1[4 * q + 1] = fmaf(a.y, xi, c1[4 * q + 1]);
+            c1[4 * q + 2] = fmaf(a.z, xi, c1[4 * q + 2]);
+            c1[4 * q + 3] = fmaf(a.w, xi, c1[4 * q + 3]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 64; ++j) c1[j] = fmaxf(c1[j], 0.f);
+    float o0 = bc3[0], o1 = bc3[1], o2 = bc3[2];
+#pragma unroll 4
+    for (int j = 0; j < 64; ++j) {
+        const float4 *row = reinterpret_cast<const float4 *>(Wc2 + j * 64);
+        float a = bc2[j];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            float4 r = row[i];
+            a = fmaf(r.x, c1[4 * i + 0], a);
+            a = fmaf(r.y, c1[4 * i + 1], a);
+            a = fmaf(r.z, c1[4 * i + 2], a);
+            a = fmaf(r.w, c1[4 * i + 3], a);
+        }
+        a = fmaxf(a, 0.f);
+        const float4 w3 = *reinterpret_cast<const float4 *>(Wc3T + 4 * j);
+        o0 = fmaf(w3.x, a, o0);
+        o1 = fmaf(w3.y, a, o1);
+        o2 = fmaf(w3.z, a, o2);
+    }
+    rgb[0] = softplusf(o0);
+    rgb[1] = softplusf(o1);
+    rgb[2] = softplusf(o2);
+    return sigma;
 }
 
 // ------------------------------------------------------------- intersection

@@ -34,7 +34,8 @@ __device__ __forceinline__ void flush_counters(unsigned long long *stats, Counte
 // Field sample at p: returns sigma (and radiance if want_rgb).  Sets `evaluated`
 // when the field's network (or analytic formula) had to run.
 template <bool want_rgb>
-__device__ __forceinline__ float field_at(const FieldDev &F, const float *w, V3 p, float rgb[3], bool &evaluated) {
+__device__ __forceinline__ float field_at(const FieldDev &F, const float *w, V3 p, V3 d, float rgb[3],
+                                          bool &evaluated) {
     evaluated = true;
     if (F.kind == MRF_FIELD_HASHGRID) {
         float s = field_support(F, p);
@@ -43,6 +44,7 @@ __device__ __forceinline__ float field_at(const FieldDev &F, const float *w, V3 
             if (want_rgb) rgb[0] = rgb[1] = rgb[2] = 0.f;
             return 0.f;
         }
+        if (F.view_dep) return hash_field_view<want_rgb>(F, w, p, d, s, rgb);
         return hash_field_fp32<want_rgb>(F, w, p, s, rgb);
     }
     if (F.kind == MRF_FIELD_GAUSS) return gauss_field(F, p, rgb);
@@ -118,7 +120,7 @@ __device__ float march(const RenderParams &P, const float *w, V3 o, V3 d, float 
         }
         float rgb[3];
         bool ev;
-        float sigma = field_at<radiance>(F, w, p, rgb, ev);
+        float sigma = field_at<radiance>(F, w, p, d, rgb, ev);
         if (ev) {
             if (radiance) ++C.evaluated;
             else ++C.shadow_eval;

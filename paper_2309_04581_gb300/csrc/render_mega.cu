@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(128) render_megakernel(const RenderParams P) {
     const FieldDev &F = P.F;
     const float *w = nullptr;
     if (F.kind == MRF_FIELD_HASHGRID) {
-        const int nw = mlp_floats(F.n_in);
+        const int nw = field_mlp_floats(F);
         for (int i = threadIdx.x; i < nw; i += blockDim.x) smem_w[i] = F.mlp[i];
         __syncthreads();
         w = smem_w;
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(128) render_megakernel(const RenderParams P) {
 
 cudaError_t launch_render_megakernel(const RenderParams &P, cudaStream_t s, KernelTimer *timer) {
     const int threads = 128;
-    const size_t smem = P.F.kind == MRF_FIELD_HASHGRID ? (size_t)mlp_floats(P.F.n_in) * sizeof(float) : 0;
+    const size_t smem = P.F.kind == MRF_FIELD_HASHGRID ? (size_t)field_mlp_floats(P.F) * sizeof(float) : 0;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(render_megakernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -135,11 +135,12 @@ cudaError_t launch_render_megakernel(const RenderParams &P, cudaStream_t s, Kern
 // FP32 evaluation of the field at n points (stride floats apart): sigma, r, g, b.
 // n is read from n_dev when it is non-NULL (device-side counts).
 __global__ void __launch_bounds__(128) field_simt_kernel(const FieldDev F, const float *pts, int stride,
-                                                         const uint32_t *n_dev, uint32_t n_host, float4 *out) {
+                                                         const uint32_t *n_dev, uint32_t n_host, float4 *out,
+                                                         const float4 *dirs) {
     extern __shared__ float smem_w[];
     const float *w = nullptr;
     if (F.kind == MRF_FIELD_HASHGRID) {
-        const int nw = mlp_floats(F.n_in);
+        const int nw = field_mlp_floats(F);
         for (int i = threadIdx.x; i < nw; i += blockDim.x) smem_w[i] = F.mlp[i];
         __syncthreads();
         w = smem_w;
@@ -150,21 +151,22 @@ __global__ void __launch_bounds__(128) field_simt_kernel(const FieldDev F, const
         float rgb[3] = {0.f, 0.f, 0.f}, sigma = 0.f;
         if (inside_field_box(F, p)) {
             bool ev;
-            sigma = field_at<true>(F, w, p, rgb, ev);
+            const float4 dv = dirs ? dirs[i] : make_float4(0.f, 0.f, 1.f, 0.f);
+            sigma = field_at<true>(F, w, p, v3(dv.x, dv.y, dv.z), rgb, ev);
         }
         out[i] = make_float4(sigma, rgb[0], rgb[1], rgb[2]);
     }
 }
 
 cudaError_t launch_field_simt(const FieldDev &F, const float *pts, int stride, const uint32_t *n_dev, uint32_t n_host,
-                              float4 *out, int grid, cudaStream_t s) {
-    const size_t smem = F.kind == MRF_FIELD_HASHGRID ? (size_t)mlp_floats(F.n_in) * sizeof(float) : 0;
+                              float4 *out, int grid, cudaStream_t s, const float4 *dirs) {
+    const size_t smem = F.kind == MRF_FIELD_HASHGRID ? (size_t)field_mlp_floats(F) * sizeof(float) : 0;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(field_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     if (grid <= 0) grid = 1;
-    field_simt_kernel<<<grid, 128, smem, s>>>(F, pts, stride, n_dev, n_host, out);
+    field_simt_kernel<<<grid, 128, smem, s>>>(F, pts, stride, n_dev, n_host, out, dirs);
     return cudaGetLastError();
 }
 

@@ -51,6 +51,7 @@ struct WfParams {
                                     // [4 + r] slots left pending by generation round r
     uint32_t *squeue;               // shadow rays answered by the network: slot * n_shadow + q
     float4 *samp;                   // sample position (xyz) and interval length (w)
+    float4 *sview;                  // view direction (field frame) of each radiance sample (view-dependent fields)
     float4 *fout;                   // sigma, r, g, b per sample
     uint32_t cap;                   // sample capacity
 };
@@ -503,6 +504,11 @@ __global__ void __launch_bounds__(kThreads, 8) wf_gen(const WfParams W, uint32_t
             write_runs(P, so, sd, 0.f, st, rl[0], W.samp + k, nr, lane);
         else
             warp_walk(P, X, so, sd, 0.f, st, W.samp + k, nr, dummy, lane, nullptr);
+        if (P.F.view_dep) {   // the colour network needs each radiance sample's view direction
+            V3 ol = so, dl = sd;
+            to_field_frame(P.F, ol, dl);
+            for (uint32_t i = lane; i < nr; i += 32) W.sview[k + i] = make_float4(dl.x, dl.y, dl.z, 0.f);
+        }
         k += nr;
         if (lane == src) W.rstart[tid] = sbase;
         bool first = true;
@@ -819,11 +825,11 @@ __global__ void __launch_bounds__(kThreads) wf_finalize(const float4 *__restrict
 // scratch layout
 struct Layout {
     size_t acc, qpath[2], qo[2], qd[2], qT[2], hit_t, hit_slot, hit_id, rstart, rcount, sstart, scount, sw, hp, sdir,
-        comp, sdepth, squeue, ctr, samp, fout, total;
+        comp, sdepth, squeue, ctr, samp, fout, sview, total;
     uint32_t cap;
 };
 
-Layout layout(uint32_t paths, int n_shadow, uint32_t cap_per_path = 96) {
+Layout layout(uint32_t paths, int n_shadow, uint32_t cap_per_path = 96, bool view_dep = false) {
     Layout L{};
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -859,6 +865,7 @@ Layout layout(uint32_t paths, int n_shadow, uint32_t cap_per_path = 96) {
     L.cap = (uint32_t)cap;
     L.samp = take(16 * cap);
     L.fout = take(16 * cap);
+    L.sview = view_dep ? take(16 * cap) : 0;
     L.total = off;
     return L;
 }
@@ -868,7 +875,7 @@ cudaError_t enqueue_frame(const WfParams &W, const RenderParams &P, uint32_t pat
                           KernelTimer *timer) {
     const unsigned grid = (paths + kThreads - 1) / kThreads;
     const FieldDev &F = P.F;
-    const bool tc = F.kind == MRF_FIELD_HASHGRID && F.precision != MRF_PREC_FP32;
+    const bool tc = F.kind == MRF_FIELD_HASHGRID && F.precision != MRF_PREC_FP32 && !F.view_dep;
     const int groups = P.tc_groups == 4 ? 4 : 8;
     const int field_grid = tc ? 152 * field_tc_blocks_per_sm(groups) : 152 * 8;
     const int rounds = std::min(std::max(P.max_rounds, 1), kMaxRounds);
@@ -908,7 +915,7 @@ cudaError_t enqueue_frame(const WfParams &W, const RenderParams &P, uint32_t pat
                                     W.ctr + 2, W.cap, W.fout, P.status, field_grid, s, groups);
             else
                 e = launch_field_simt(F, reinterpret_cast<const float *>(W.samp), 4, W.ctr + 2, W.cap, W.fout,
-                                      field_grid, s);
+                                      field_grid, s, F.view_dep ? W.sview : nullptr);
             timer_end(timer, s);
             if (e != cudaSuccess) return e;
             if (P.shadow_mask) {
@@ -940,13 +947,13 @@ cudaError_t enqueue_frame(const WfParams &W, const RenderParams &P, uint32_t pat
 bool wavefront_available() { return true; }
 
 size_t wavefront_scratch_bytes(const RenderParams &P) {
-    return layout(P.count * P.spp, P.n_shadow, P.cap_per_path).total;
+    return layout(P.count * P.spp, P.n_shadow, P.cap_per_path, P.F.view_dep != 0).total;
 }
 
 cudaError_t launch_render_wavefront(const RenderParams &P, void *scratch, size_t scratch_bytes, cudaStream_t s,
                                     KernelTimer *timer) {
     const uint32_t paths = P.count * P.spp;
-    const Layout Lo = layout(paths, P.n_shadow, P.cap_per_path);
+    const Layout Lo = layout(paths, P.n_shadow, P.cap_per_path, P.F.view_dep != 0);
     if (scratch_bytes < Lo.total) return cudaErrorInvalidValue;
     char *b = static_cast<char *>(scratch);
     WfParams W{};
@@ -975,6 +982,7 @@ cudaError_t launch_render_wavefront(const RenderParams &P, void *scratch, size_t
     W.squeue = reinterpret_cast<uint32_t *>(b + Lo.squeue);
     W.samp = reinterpret_cast<float4 *>(b + Lo.samp);
     W.fout = reinterpret_cast<float4 *>(b + Lo.fout);
+    W.sview = Lo.sview ? reinterpret_cast<float4 *>(b + Lo.sview) : nullptr;
     W.cap = Lo.cap;
     return enqueue_frame(W, P, paths, s, timer);
 }

@@ -9,29 +9,8 @@
 
 namespace mrf {
 
-// Real spherical harmonics of bands 0..3 at the unit direction w, orthonormal
-// on the sphere, ordered (l, m = -l..l).  Constants: 1/(2 sqrt(pi)),
-// sqrt(3/(4 pi)), sqrt(15/pi)/2, sqrt(5/pi)/4, sqrt(15/pi)/4, sqrt(35/(2 pi))/4,
-// sqrt(105/pi)/2, sqrt(21/(2 pi))/4, sqrt(7/pi)/4, sqrt(105/pi)/4.
-__device__ __forceinline__ void snet_sh16(V3 w, float *Y) {
-    const float x = w.x, y = w.y, z = w.z;
-    Y[0] = 0.28209479177387814f;
-    Y[1] = 0.4886025119029199f * y;
-    Y[2] = 0.4886025119029199f * z;
-    Y[3] = 0.4886025119029199f * x;
-    Y[4] = 1.0925484305920792f * x * y;
-    Y[5] = 1.0925484305920792f * y * z;
-    Y[6] = 0.31539156525252005f * (3.f * z * z - 1.f);
-    Y[7] = 1.0925484305920792f * x * z;
-    Y[8] = 0.5462742152960396f * (x * x - y * y);
-    Y[9] = 0.5900435899266435f * y * (3.f * x * x - y * y);
-    Y[10] = 2.890611442640554f * x * y * z;
-    Y[11] = 0.4570457994644658f * y * (5.f * z * z - 1.f);
-    Y[12] = 0.3731763325901154f * z * (5.f * z * z - 3.f);
-    Y[13] = 0.4570457994644658f * x * (5.f * z * z - 1.f);
-    Y[14] = 1.445305721320277f * z * (x * x - y * y);
-    Y[15] = 0.5900435899266435f * x * (x * x - 3.f * y * y);
-}
+// Spherical harmonics of the direction input: sh16 (device.cuh).
+__device__ __forceinline__ void snet_sh16(V3 w, float *Y) { sh16(w, Y); }
 
 // World point and direction to the field's local frame.
 __device__ __forceinline__ void snet_to_local(const ShadowNetDev &N, V3 &p, V3 &w) {

@@ -58,6 +58,8 @@ class mrf_field_desc(C.Structure):
         ("w1", _fp), ("b1", _fp), ("w2", _fp), ("b2", _fp), ("w3", _fp), ("b3", _fp),
         ("n_support", C.c_uint32), ("support_center", _fp), ("support_radius", _fp),
         ("occ_res", C.c_uint32), ("occ_bits", _u32p), ("precision", C.c_int32), ("pose", _fp),
+        ("view_dependent", C.c_int32), ("wd2", _fp), ("bd2", _fp), ("wc1", _fp), ("bc1", _fp), ("wc2", _fp),
+        ("bc2", _fp), ("wc3", _fp), ("bc3", _fp),
     ]
 
 
@@ -279,6 +281,10 @@ def field_desc(field: S.Field, precision: int = MRF_PREC_FP32):
     d.precision = precision
     if getattr(field, "pose", None) is not None:
         d.pose = _p(arr(field.pose, np.float32), _fp)
+    if getattr(field, "view", None) is not None:
+        d.view_dependent = 1
+        for nm in ("wd2", "bd2", "wc1", "bc1", "wc2", "bc2", "wc3", "bc3"):
+            setattr(d, nm, _p(arr(field.view[nm], np.float32), _fp))
     if field.blob_center is not None:
         d.n_blobs = field.blob_center.shape[0]
         d.blob_center = _p(arr(field.blob_center, np.float32), _fp)

@@ -106,6 +106,9 @@ class Field:
     occ_bits: Optional[np.ndarray] = None      # (occ_res^3 / 32,) uint32, cell x + R*(y + R*z)
     # rigid pose of the field, 3x4 local-to-world [R | t] f32 (None = identity)
     pose: Optional[np.ndarray] = None
+    # view-dependent radiance: dict of the density head wd2 (16x64), bd2 and the
+    # colour network wc1 (64x32), bc1, wc2 (64x64), bc2, wc3 (3x64), bc3 (None = off)
+    view: Optional[dict] = None
 
 
 @dataclass
@@ -609,3 +612,28 @@ class DynamicSequence:
             c = self.body_center[b] + self.body_orbit[b] * np.sin(self.body_freq[b] * t * 2 * math.pi)
             out.append(tv @ R.T + c)
         return f32(np.concatenate(out))
+
+
+def view_networks(seed: int = 9, width: int = 64, sigma_bias: float = 3.0) -> dict:
+    """Seeded Xavier-uniform weights of the view-dependent heads (density head
+    16 x 64 with bias[0] = sigma_bias, colour network 32 -> 64 -> 64 -> 3)."""
+    rng = _rng(6, seed)
+
+    def xavier(fo, fi):
+        lim = math.sqrt(6.0 / (fi + fo))
+        return f32(rng.uniform(-lim, lim, (fo, fi)))
+
+    bd2 = np.zeros(16)
+    bd2[0] = sigma_bias
+    return {"wd2": xavier(16, width), "bd2": f32(bd2), "wc1": xavier(width, 32), "bc1": f32(np.zeros(width)),
+            "wc2": xavier(width, width), "bc2": f32(np.zeros(width)), "wc3": xavier(3, width), "bc3": f32(np.zeros(3))}
+
+
+def config2_view(width: int = 800, height: int = 800, max_bounces: int = 8) -> Scene:
+    """config2 with view-dependent radiance: the hash grid and first layer of
+    config2 feed a 16-output density head and a colour network of those outputs
+    and the view direction's spherical harmonics (the Instant-NGP layout)."""
+    sc = config2(width, height, max_bounces=max_bounces)
+    sc.field.view = view_networks()
+    sc.name = f"c2_view_{width}x{height}"
+    return sc

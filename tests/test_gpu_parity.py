@@ -578,3 +578,44 @@ def test_field_sample_shadow_mask_matches_oracle(M, orc, torch_cuda, engine):
         # hundreds of mask rays per pixel sample the hard shadow boundary: about 1 %
         # of pixels hold one that grazes an edge (flagged, legitimately decided either way)
         _compare(_render(M, sc, engine=eng), ref, max_flag_frac=1.5e-2)
+
+
+# ----------------------------------------------------------------- view-dependent radiance
+@pytest.mark.parametrize("engine", ["megakernel", "wavefront"])
+def test_view_dependent_field_matches_oracle(M, orc, torch_cuda, engine):
+    """Instant-NGP network layout: a density head and a colour network of the
+    view direction's spherical harmonics (field frame), posed field included."""
+    sc = S.config2_view(48, 48)
+    sc.field.pose = S.rigid_pose([0.2, 1.0, 0.1], 0.4, [0.03, -0.02, 0.05])
+    ref = orc.render(sc)
+    eng = M.MRF_ENGINE_MEGAKERNEL if engine == "megakernel" else M.MRF_ENGINE_WAVEFRONT
+    gpu = _render(M, sc, engine=eng)
+    _compare(gpu, ref)
+    # the direction matters: the same scene without its colour network's SH inputs differs
+    flat = S.config2_view(48, 48)
+    flat.field.pose = sc.field.pose
+    flat.field.view = dict(flat.field.view, wc1=flat.field.view["wc1"].copy())
+    flat.field.view["wc1"][:, 16:] = 0
+    assert np.abs(_render(M, flat, engine=eng)["rgba"] - gpu["rgba"]).max() > 1e-3
+
+
+def test_view_dependent_field_query(M, orc, torch_cuda):
+    torch = torch_cuda
+    sc = S.config2_view(8, 8)
+    rng = np.random.default_rng(21)
+    pts = rng.uniform(-0.45, 0.45, (5000, 3)).astype(np.float32)
+    ctx = M.mrf_context_create(0)
+    desc, keep = M.field_desc(sc.field)
+    f = M.mrf_field_create(ctx, desc)
+    dp = torch.from_numpy(pts).cuda()
+    out = torch.empty((pts.shape[0], 4), dtype=torch.float32, device="cuda")
+    M.mrf_field_query(ctx, f, dp.data_ptr(), pts.shape[0], out.data_ptr())
+    got = out.cpu().numpy().astype(np.float64)
+    osc = orc.OracleScene(sc)
+    ref = np.array([[*orc.field_eval_dir(osc, p.astype(np.float64), [0, 0, 1])[0:1],
+                     *orc.field_eval_dir(osc, p.astype(np.float64), [0, 0, 1])[1]] for p in pts])
+    assert (ref[:, 0] > 0).sum() > 100
+    scale = np.maximum(np.abs(ref).max(0), 1e-6)
+    assert np.all(np.abs(got - ref) <= 1e-4 * np.abs(ref) + 1e-6 * scale)
+    M.mrf_field_destroy(f)
+    M.mrf_context_destroy(ctx)

@@ -416,3 +416,28 @@ def test_field_sample_shadow_mask_closed_form(orc):
     sc.opts.shadow_mask = False
     plain = orc.render(sc)["rgba"][0, :3]
     assert np.allclose(plain, S.f32(e).astype(np.float64) * (1 - h * h), rtol=1e-12)
+
+
+def test_view_dependent_field_pose_uses_the_field_frame(orc):
+    # the colour network sees the view direction in the field's own frame: a
+    # posed view-dependent field seen from a camera equals the unposed field
+    # seen from the inversely moved camera
+    T = S.rigid_pose([0.3, 1.0, -0.2], 0.6, [0.05, -0.1, 0.08])
+    R, t = T[:, :3].astype(np.float64), T[:, 3].astype(np.float64)
+    moved = S.config2_view(24, 24)
+    moved.mesh = S.empty_mesh()
+    moved.materials = []
+    moved.field.pose = T
+    base = S.config2_view(24, 24)
+    base.mesh = S.empty_mesh()
+    base.materials = []
+    cam = base.camera
+    inv = lambda x: R.T @ (np.asarray(x, np.float64) - t)
+    base.camera = S.Camera(pos=S.f32(inv(cam.pos)), look_at=S.f32(inv(cam.look_at)),
+                           up=S.f32(R.T @ np.asarray(cam.up, np.float64)), vfov_deg=cam.vfov_deg,
+                           width=cam.width, height=cam.height)
+    a = orc.render(moved)["rgba"]
+    b = orc.render(base)["rgba"]
+    peak = np.abs(b[:, :3]).max()
+    assert peak > 0.05
+    assert np.abs(a - b).max() <= 2e-4 * peak + 1e-7

@@ -322,3 +322,50 @@ def test_cosine_hemisphere_sampling(orc, n):
     assert abs(cos.mean() - 2 / 3) < 2e-3
     hist, _ = np.histogram(cos ** 2, bins=8, range=(0, 1))
     assert np.all(np.abs(hist - cos.size / 8) <= 1)
+
+
+# --------------------------------------------------------------- view-dependent radiance
+def test_view_networks_match_torch_layers(orc):
+    torch = pytest.importorskip("torch")
+    sc = S.config2_view(8, 8)
+    osc = orc.OracleScene(sc)
+    f, v = sc.field, sc.field.view
+    rng = np.random.default_rng(12)
+    F = torch.nn.functional
+    T = lambda a: torch.tensor(np.asarray(a, np.float64))
+    for _ in range(8):
+        feat = rng.uniform(-0.5, 0.5, 32)
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        lg, rgb = orc.mlp_view(osc, feat, d)
+        h = F.relu(F.linear(T(feat), T(f.w1), T(f.b1)))
+        dn = F.linear(h, T(v["wd2"]), T(v["bd2"]))
+        x = torch.cat([dn, T(orc.sh16(d))])
+        c = F.relu(F.linear(x, T(v["wc1"]), T(v["bc1"])))
+        c = F.relu(F.linear(c, T(v["wc2"]), T(v["bc2"])))
+        out = F.softplus(F.linear(c, T(v["wc3"]), T(v["bc3"])))
+        assert lg == pytest.approx(float(dn[0]), rel=1e-13, abs=1e-13)
+        assert np.allclose(rgb, out.numpy(), rtol=1e-13, atol=1e-14)
+
+
+def test_view_dependence_is_only_in_the_colour(orc):
+    sc = S.config2_view(8, 8)
+    osc = orc.OracleScene(sc)
+    p = None
+    rng = np.random.default_rng(13)
+    for _ in range(200):   # a point with density
+        q = rng.uniform(-0.4, 0.4, 3)
+        if orc.field_eval_dir(osc, q, [0, 0, 1])[0] > 1.0:
+            p = q
+            break
+    assert p is not None
+    s1, c1 = orc.field_eval_dir(osc, p, [0, 0, 1])
+    s2, c2 = orc.field_eval_dir(osc, p, [1, 0, 0])
+    assert s1 == s2 and np.abs(c1 - c2).max() > 1e-3
+    # zero SH columns of the colour network: no view dependence at all
+    sc.field.view["wc1"] = sc.field.view["wc1"].copy()
+    sc.field.view["wc1"][:, 16:] = 0
+    osc = orc.OracleScene(sc)
+    _, c1 = orc.field_eval_dir(osc, p, [0, 0, 1])
+    _, c2 = orc.field_eval_dir(osc, p, [0.6, -0.8, 0])
+    assert np.array_equal(c1, c2)
