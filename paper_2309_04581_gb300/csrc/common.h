@@ -17,7 +17,7 @@ constexpr int kMaxBounces = 64;
 constexpr int kStackSize = 64;
 
 // Packed FP32 MLP weights (floats):  W1T[in][64] | b1[64] | W2[64][64] | b2[64] | W3T[64][4] | b3[4]
-constexpr int mlp_floats(int n_in) { return n_in * 64 + 64 + 64 * 64 + 64 + 64 * 4 + 4; }
+__host__ __device__ constexpr int mlp_floats(int n_in) { return n_in * 64 + 64 + 64 * 64 + 64 + 64 * 4 + 4; }
 // View-dependent heads appended after it (floats): WdT[64][16] bd[16] | Wc1T[32][64] bc1[64] |
 // Wc2[64][64] bc2[64] | Wc3T[64][4] bc3[4]
 constexpr int kViewFloats = 64 * 16 + 16 + 32 * 64 + 64 + 64 * 64 + 64 + 64 * 4 + 4;

@@ -637,3 +637,55 @@ def config2_view(width: int = 800, height: int = 800, max_bounces: int = 8) -> S
     sc.field.view = view_networks()
     sc.name = f"c2_view_{width}x{height}"
     return sc
+
+
+# ---------------------------------------------------------------------------
+# batched views in a mirror room
+# ---------------------------------------------------------------------------
+def displaced_sphere(center, radius: float, level: int, mat: int, seed_purpose: int, amp: float = 0.1) -> Mesh:
+    """Icosphere whose vertices move radially by amp * radius * n(x), n a seeded
+    smooth noise (a sum of 6 random plane waves, values in [-1, 1])."""
+    rng = _rng(7, seed_purpose)
+    verts, faces = icosphere_faces(level)
+    k = rng.normal(size=(6, 3)) * 3.0
+    ph = rng.uniform(0, 2 * math.pi, 6)
+    noise = np.sin(verts @ k.T + ph).sum(1) / 6.0
+    v = np.asarray(center, np.float64) + verts * (radius * (1.0 + amp * noise))[:, None]
+    return Mesh(f32(v), np.ascontiguousarray(faces, np.uint32), np.full(faces.shape[0], mat, np.uint32))
+
+
+class MultiViewScene:
+    """32 seeded views (log-uniform sizes from 256x256 to 1920x1080) inside a
+    mirror room around the hash-grid field, with 13 noise-displaced spheres
+    (5,120 triangles each, mixed materials) and a 128 x 128 cloth grid whose
+    vertices move every frame; up to 16 segments per path."""
+
+    def __init__(self, n_views: int = 32, scale: float = 1.0, max_bounces: int = 16, spheres: int = 13):
+        rng = _rng(3, 21)
+        base = config2(8, 8, max_bounces=max_bounces)
+        room = box_mesh([0.0, 0.0, 0.0], 0.62, 0, inward=True)
+        meshes = [room]
+        for i in range(spheres):
+            c = rng.uniform(-0.38, 0.38, 3)
+            meshes.append(displaced_sphere(c, rng.uniform(0.05, 0.1), 4, int(rng.integers(0, 3)), i))
+        self.static = merge_meshes(meshes)
+        self.cloth = cloth_grid(128, 0.45, -0.4, 2)
+        self.cloth_phase = rng.uniform(0, 2 * math.pi, self.cloth.verts.shape[0])
+        mesh = merge_meshes([self.static, self.cloth])
+        sizes = seeded_view_sizes(n_views, 4)
+        sizes = [(max(1, int(round(w * scale))), max(1, int(round(h * scale)))) for w, h in sizes]
+        views = orbit_views(n_views, sizes, radius=0.58, height=0.1, vfov=60.0)
+        self.scene = Scene(name=f"views{n_views}", camera=views[0], field=base.field, mesh=mesh,
+                           materials=base.materials, lights=base.lights, cameras=views,
+                           opts=RenderOpts(max_bounces=max_bounces, spp=1, seed=3, steps_per_segment=0, dt=DT_C2))
+
+    @property
+    def n_tris(self) -> int:
+        return int(self.scene.mesh.tris.shape[0])
+
+    def vertices(self, k: int, fps: float = 30.0) -> np.ndarray:
+        t = k / fps
+        cv = self.cloth.verts.astype(np.float64).copy()
+        cv[:, 1] += 0.03 * np.sin(7.0 * cv[:, 0] + 2.0 * t) * np.cos(6.0 * cv[:, 2] - 1.3 * t) \
+            + 0.003 * np.sin(8.0 * t + self.cloth_phase)
+        return f32(np.concatenate([self.static.verts.astype(np.float64), cv]))
