@@ -458,9 +458,31 @@ mrf_status mrf_shadow_net_grad(mrf_shadow_net *net, const float *pairs, uint32_t
 mrf_status mrf_shadow_net_train(mrf_shadow_net *net, const float *pairs, uint64_t n_pairs, uint32_t batch,
                                 uint32_t steps, float *loss, void *stream);
 
+/* Checkpoint of a network in training: parameters, Adam's moments and step
+ * count, the training-pair cursor and the optimiser settings, to a binary
+ * file (a header then three arrays of mrf_shadow_net_param_count() FP32
+ * values); loading requires the same table size and level resolutions and
+ * resumes training where the saved network stopped.  Both wait for the
+ * device. */
+mrf_status mrf_shadow_net_save(const mrf_shadow_net *net, const char *path);
+mrf_status mrf_shadow_net_load(mrf_shadow_net *net, const char *path);
+
 /* Network transmittance for the n pairs (device, n x 8; p and w are read) into
  * the device array out (n values), with the rendering weights. */
 mrf_status mrf_shadow_net_eval(mrf_shadow_net *net, const float *pairs, uint32_t n, float *out, void *stream);
+
+/* ------------------------------------------------------------ self tests
+ * Failure paths exercised without faulting the GPU.  Every wait of the
+ * library's kernels (mbarrier waits on tensor-core work) is bounded; a wait
+ * that gives up sets a bit of the context's status word and its kernel
+ * returns, and the next call reports MRF_ERR_TIMEOUT.
+ * mrf_selftest_timeout runs one such wait on a barrier that nothing arrives
+ * at, with a budget of `cycles` SM cycles (at most 2^32): it returns
+ * MRF_ERR_TIMEOUT, clears the status word, and leaves the context usable.
+ * mrf_debug_fail_allocations makes the library's next n device allocations
+ * fail as if the device were out of memory (MRF_ERR_OOM); 0 turns it off. */
+mrf_status mrf_selftest_timeout(mrf_context *ctx, uint64_t cycles);
+void mrf_debug_fail_allocations(uint32_t n);
 
 #ifdef __cplusplus
 }

@@ -1,6 +1,7 @@
 // The C ABI of include/mrf.h: argument checks, device memory ownership and
 // kernel dispatch.  No C++ exception crosses the boundary.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -108,10 +109,15 @@ static bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+static std::atomic<uint32_t> g_fail_allocs{0};   // allocations still to fail (mrf_debug_fail_allocations)
+
 template <class T>
 static mrf_status dev_alloc(T **p, size_t n, const char *what) {
     *p = nullptr;
     if (n == 0) return MRF_OK;
+    for (uint32_t k = g_fail_allocs.load(); k > 0;)
+        if (g_fail_allocs.compare_exchange_weak(k, k - 1))
+            return fail(MRF_ERR_OOM, "%s: injected allocation failure", what);
     cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
     if (e != cudaSuccess) {
         *p = nullptr;
@@ -1607,5 +1613,112 @@ mrf_status mrf_shadow_net_eval(mrf_shadow_net *n, const float *pairs, uint32_t c
         return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_net_eval: arrays must be device memory");
     CUDA_TRY(cudaSetDevice(n->ctx->device), "cudaSetDevice");
     CUDA_TRY(launch_snet_eval(n->dev, pairs, count, out, (cudaStream_t)stream), "mrf_shadow_net_eval");
+    return MRF_OK;
+}
+
+
+// ------------------------------------------------------------ self tests
+void mrf_debug_fail_allocations(uint32_t n) { g_fail_allocs.store(n); }
+
+mrf_status mrf_selftest_timeout(mrf_context *ctx, uint64_t cycles) {
+    if (!ctx) return fail(MRF_ERR_INVALID_ARG, "mrf_selftest_timeout: NULL context");
+    if (cycles > (1ull << 32)) return fail(MRF_ERR_INVALID_ARG, "mrf_selftest_timeout: budget above 2^32 cycles");
+    CUDA_TRY(cudaSetDevice(ctx->device), "mrf_selftest_timeout: cudaSetDevice");
+    CUDA_TRY(launch_selftest_timeout((long long)cycles, ctx->status, 0), "mrf_selftest_timeout: launch");
+    CUDA_TRY(cudaDeviceSynchronize(), "mrf_selftest_timeout: synchronize");
+    unsigned st_word = 0;
+    CUDA_TRY(cudaMemcpy(&st_word, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost), "mrf_selftest_timeout: status");
+    if (st_word) {
+        cudaMemset(ctx->status, 0, sizeof(unsigned));
+        return fail(MRF_ERR_TIMEOUT, "mrf_selftest_timeout: the wait gave up (status 0x%x)", st_word);
+    }
+    return MRF_OK;
+}
+
+
+// ------------------------------------------------------------ shadow network checkpoints
+namespace {
+constexpr char kSnetMagic[8] = {'M', 'R', 'F', 'S', 'N', 'E', 'T', '1'};
+struct SnetHeader {
+    char magic[8];
+    uint32_t log2T, res[kSnetLevels];
+    uint64_t n_params;
+    uint32_t t;
+    uint64_t cursor;
+    float lr, b1, b2, eps, decay;
+    int32_t precision;
+};
+}  // namespace
+
+mrf_status mrf_shadow_net_save(const mrf_shadow_net *n, const char *path) {
+    if (!n || !path) return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_net_save: NULL argument");
+    CUDA_TRY(cudaSetDevice(n->ctx->device), "cudaSetDevice");
+    CUDA_TRY(cudaDeviceSynchronize(), "mrf_shadow_net_save: synchronize");
+    SnetHeader h{};
+    std::memcpy(h.magic, kSnetMagic, 8);
+    h.log2T = n->dev.log2T;
+    for (int l = 0; l < kSnetLevels; ++l) h.res[l] = n->dev.res[l];
+    h.n_params = n->n_params;
+    h.t = n->t;
+    h.cursor = n->cursor;
+    h.lr = n->lr;
+    h.b1 = n->b1;
+    h.b2 = n->b2;
+    h.eps = n->eps;
+    h.decay = n->decay;
+    h.precision = n->precision;
+    std::vector<float> buf(n->n_params);
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_net_save: cannot open %s", path);
+    bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1;
+    const float *arrays[3] = {n->params, n->m, n->v};
+    for (const float *a : arrays) {
+        if (!ok) break;
+        if (cudaMemcpy(buf.data(), a, n->n_params * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            std::fclose(f);
+            return cuda_fail(cudaGetLastError(), "mrf_shadow_net_save: download");
+        }
+        ok = std::fwrite(buf.data(), sizeof(float), n->n_params, f) == n->n_params;
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? MRF_OK : fail(MRF_ERR_INVALID_ARG, "mrf_shadow_net_save: write to %s failed", path);
+}
+
+mrf_status mrf_shadow_net_load(mrf_shadow_net *n, const char *path) {
+    if (!n || !path) return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_net_load: NULL argument");
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_net_load: cannot open %s", path);
+    SnetHeader h{};
+    bool ok = std::fread(&h, sizeof(h), 1, f) == 1 && std::memcmp(h.magic, kSnetMagic, 8) == 0;
+    ok = ok && h.log2T == n->dev.log2T && h.n_params == n->n_params;
+    for (int l = 0; ok && l < kSnetLevels; ++l) ok = h.res[l] == n->dev.res[l];
+    if (!ok) {
+        std::fclose(f);
+        return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_net_load: %s is not a checkpoint of this network shape", path);
+    }
+    std::vector<float> buf(n->n_params);
+    float *arrays[3] = {n->params, n->m, n->v};
+    mrf_status st = MRF_OK;
+    for (float *a : arrays) {
+        if (std::fread(buf.data(), sizeof(float), n->n_params, f) != n->n_params) {
+            st = fail(MRF_ERR_INVALID_ARG, "mrf_shadow_net_load: %s is truncated", path);
+            break;
+        }
+        if (cudaMemcpy(a, buf.data(), n->n_params * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+            st = cuda_fail(cudaGetLastError(), "mrf_shadow_net_load: upload");
+            break;
+        }
+    }
+    std::fclose(f);
+    if (st) return st;
+    n->t = h.t;
+    n->cursor = h.cursor;
+    n->lr = h.lr;
+    n->b1 = h.b1;
+    n->b2 = h.b2;
+    n->eps = h.eps;
+    n->decay = h.decay;
+    if ((st = snet_refresh(n, 0))) return st;
+    CUDA_TRY(cudaDeviceSynchronize(), "mrf_shadow_net_load: synchronize");
     return MRF_OK;
 }

@@ -194,6 +194,7 @@ int field_tc_blocks_per_sm(int groups = 8);
 cudaError_t launch_cast(const BvhDev &B, const float *o, const float *d, const uint32_t *skip, uint32_t n, float tmin,
                         float *out_t, uint32_t *out_tri, unsigned long long *stats, cudaStream_t s);
 cudaError_t launch_tonemap(const float4 *in, uint32_t n, float exposure, float4 *out, cudaStream_t s);
+cudaError_t launch_selftest_timeout(long long cycles, unsigned *status, cudaStream_t s);
 // shadow_net.cu
 size_t snet_train_smem();
 cudaError_t launch_snet_pairs(const RenderParams &P, uint64_t seed, uint64_t first, uint32_t n, float *out,

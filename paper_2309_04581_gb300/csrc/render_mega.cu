@@ -6,6 +6,7 @@
 
 #include "path.cuh"
 #include "shadow_net.cuh"
+#include "tc.cuh"
 
 namespace mrf {
 
@@ -167,6 +168,23 @@ cudaError_t launch_field_simt(const FieldDev &F, const float *pts, int stride, c
     }
     if (grid <= 0) grid = 1;
     field_simt_kernel<<<grid, 128, smem, s>>>(F, pts, stride, n_dev, n_host, out, dirs);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- self test
+// One thread waits on a fresh shared-memory mbarrier that nothing arrives at,
+// with a budget of `cycles`; the bounded wait gives up and the kernel records
+// the time-out in the status word (bit 8) and returns, as every bounded wait
+// of the library does.
+__global__ void selftest_timeout_kernel(long long cycles, unsigned *status) {
+    __shared__ __align__(8) unsigned long long bar;
+    const uint32_t a = tc::smem_u32(&bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(1) : "memory");
+    if (!tc::mbar_wait_budget(a, 0, cycles)) atomicOr(status, 8u);
+}
+
+cudaError_t launch_selftest_timeout(long long cycles, unsigned *status, cudaStream_t s) {
+    selftest_timeout_kernel<<<1, 1, 0, s>>>(cycles, status);
     return cudaGetLastError();
 }
 

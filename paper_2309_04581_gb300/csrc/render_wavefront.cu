@@ -210,9 +210,32 @@ __device__ __noinline__ uint32_t warp_walk(const RenderParams &P, const WalkCtx 
     const int Rc = F.occ_coarse_res;
     const float inv_h = 1.0f / S.h;
     const uint32_t smask = hash ? job_spheres(F, X, o, d, S.t0, S.t1, lane) : 0u;
+    // Interval-index range of this lane's support sphere along the job: only
+    // samples inside some sphere can have non-zero density, so the walk jumps
+    // over the gaps between the ranges (conservative by two intervals).
+    const bool jump = hash && F.n_support > 0 && F.n_support <= 32;
+    int jb = 0x7fffffff, je = -1;
+    if (jump && ((smask >> lane) & 1u)) {
+        const float4 c = X.support[lane];
+        const V3 oc = v3(c.x - o.x, c.y - o.y, c.z - o.z);
+        const float dd = dot(d, d), tcl = dot(oc, d) / dd;
+        const V3 q = v3(o.x + d.x * tcl - c.x, o.y + d.y * tcl - c.y, o.z + d.z * tcl - c.z);
+        const float disc = ((1.0f + 1e-3f) / c.w - dot(q, q)) / dd;
+        if (disc > 0.f) {
+            const float w = sqrtf(disc);
+            jb = max((int)floorf((tcl - w - S.t0) * inv_h - 0.5f) - 2, 0);
+            je = min((int)ceilf((tcl + w - S.t0) * inv_h - 0.5f) + 2, S.n);
+        }
+    }
+    auto next_start = [&](int from) {
+        int v = je > from ? max(jb, from) : 0x7fffffff;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, off));
+        return v;
+    };
     int nrun = 0, run_end = -1;
     uint32_t k = 0;
-    for (int i0 = 0; i0 < S.n;) {
+    for (int i0 = jump ? next_start(0) : 0; i0 < S.n;) {
         const int i = i0 + lane;
         bool emit = false;
         int skip_to = i + 1;
@@ -275,6 +298,7 @@ __device__ __noinline__ uint32_t warp_walk(const RenderParams &P, const WalkCtx 
         }
         const int last_skip = __shfl_sync(0xffffffffu, skip_to, 31);
         i0 = max(i0 + 32, last_skip);
+        if (jump) i0 = next_start(i0);
     }
     if (runs && lane == 0) runs->n = nrun;
     return k;

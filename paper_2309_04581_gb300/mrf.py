@@ -39,7 +39,8 @@ EXPORTS = ("mrf_context_create", "mrf_context_destroy", "mrf_last_error", "mrf_v
            "mrf_tonemap", "mrf_shadow_net_create", "mrf_shadow_net_destroy", "mrf_shadow_net_param_count",
            "mrf_shadow_net_get_params", "mrf_shadow_net_set_params", "mrf_shadow_pairs", "mrf_shadow_net_grad",
            "mrf_shadow_net_train", "mrf_shadow_net_eval", "mrf_frame_capture", "mrf_frame_replay", "mrf_frame_stats",
-           "mrf_frame_destroy", "mrf_tuning_get", "mrf_tuning_set", "mrf_autotune")
+           "mrf_frame_destroy", "mrf_tuning_get", "mrf_tuning_set", "mrf_autotune", "mrf_selftest_timeout",
+           "mrf_debug_fail_allocations", "mrf_shadow_net_save", "mrf_shadow_net_load")
 
 _fp = C.POINTER(C.c_float)
 _u32p = C.POINTER(C.c_uint32)
@@ -133,8 +134,12 @@ def lib():
                 if name not in ("mrf_last_error", "mrf_version"):
                     fn.restype = C.c_int
             for name in ("mrf_context_destroy", "mrf_field_destroy", "mrf_bvh_destroy", "mrf_shadow_net_destroy",
-                         "mrf_frame_destroy"):
+                         "mrf_frame_destroy", "mrf_debug_fail_allocations"):
                 getattr(L, name).restype = None
+            L.mrf_selftest_timeout.argtypes = [_vp, C.c_uint64]
+            L.mrf_shadow_net_save.argtypes = [_vp, C.c_char_p]
+            L.mrf_shadow_net_load.argtypes = [_vp, C.c_char_p]
+            L.mrf_debug_fail_allocations.argtypes = [C.c_uint32]
             L.mrf_frame_capture.argtypes = [_vp, _vp, _vp, C.POINTER(mrf_rays), C.c_uint32, C.POINTER(mrf_render_opts),
                                             _vp, C.POINTER(_vp)]
             L.mrf_frame_replay.argtypes = [_vp, _vp]
@@ -567,6 +572,12 @@ class ShadowNet:
         check(lib().mrf_shadow_net_train(self.handle, pairs.data_ptr(), pairs.shape[0], batch, steps, loss.data_ptr(),
                                          self._stream()))
         return loss[:steps]
+
+    def save(self, path: str):
+        check(lib().mrf_shadow_net_save(self.handle, os.fsencode(path)))
+
+    def load(self, path: str):
+        check(lib().mrf_shadow_net_load(self.handle, os.fsencode(path)))
 
     def eval(self, pairs):
         torch = self.r.torch

@@ -146,3 +146,33 @@ def test_mirror_room_views_match_oracle(env, orc):
     assert ref["segments"].mean() > 8     # long mirror-room paths
     f.close()
     r.close()
+
+
+def test_bounded_wait_gives_up_cleanly(env):
+    """A wait on a barrier nothing arrives at runs out of its budget, the
+    status word reports it as MRF_ERR_TIMEOUT, and the context renders on."""
+    torch, M = env
+    sc = S.config1(16, 16)
+    r = M.Renderer(sc)
+    before, _ = r.render()
+    st = M.lib().mrf_selftest_timeout(r.ctx, 20000)
+    assert st == M.MRF_ERR_TIMEOUT and b"gave up" in M.lib().mrf_last_error()
+    after, stats = r.render(stats=True)
+    torch.cuda.synchronize()
+    assert stats["status"] == 0 and torch.equal(before, after)
+    r.close()
+
+
+def test_injected_allocation_failure(env):
+    torch, M = env
+    sc = S.config2(8, 8)
+    ctx = M.mrf_context_create(0)
+    desc, keep = M.field_desc(sc.field)
+    M.lib().mrf_debug_fail_allocations(1)
+    with pytest.raises(M.MrfError) as ei:
+        M.mrf_field_create(ctx, desc)
+    assert ei.value.status == M.MRF_ERR_OOM and "injected" in str(ei.value)
+    f = M.mrf_field_create(ctx, desc)          # the next one succeeds
+    M.mrf_field_destroy(f)
+    M.lib().mrf_debug_fail_allocations(0)
+    M.mrf_context_destroy(ctx)

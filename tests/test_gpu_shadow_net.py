@@ -250,3 +250,36 @@ def test_network_gain_over_the_march(env, orc, trained):
     bf.close()
     untrained.close()
     r.close()
+
+
+def test_checkpoint_resume(env, renderer, tmp_path):
+    """Training stopped at a checkpoint and resumed in a fresh network ends
+    where uninterrupted training ends (up to the order of the FP32 gradient
+    atomics); loading restores the parameters bit for bit."""
+    torch, M = env
+    a = M.ShadowNet(renderer, seed=3, lr_decay=0.999)
+    pairs = a.pairs(SEED, 0, 1 << 18)
+    a.train(pairs, 1 << 14, 40)
+    ck = str(tmp_path / "snet.ckpt")
+    a.save(ck)
+    saved = a.params().clone()
+    a.train(pairs, 1 << 14, 40)
+    b = M.ShadowNet(renderer, seed=99)          # different initial values, overwritten by the checkpoint
+    b.load(ck)
+    assert torch.equal(b.params(), saved)
+    b.train(pairs, 1 << 14, 40)
+    pa, pb = a.params(), b.params()
+    # Adam with eps 1e-15 turns a gradient of rounding size into a full step of
+    # either sign, so a few entries may differ by a step; the rest agree closely
+    close = (pa - pb).abs() <= 1e-5 * float(pa.abs().max())
+    assert float(close.float().mean()) >= 0.99
+    held = a.pairs(SEED, 1 << 28, 1 << 14)
+    ea = float(((a.eval(held) - held[:, 7]) ** 2).mean())
+    eb = float(((b.eval(held) - held[:, 7]) ** 2).mean())
+    assert abs(ea - eb) <= 0.05 * ea
+    # a checkpoint of another shape is refused
+    c = M.ShadowNet(renderer, log2_table=12)
+    with pytest.raises(M.MrfError):
+        c.load(ck)
+    for n in (a, b, c):
+        n.close()
