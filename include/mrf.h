@@ -120,10 +120,10 @@ typedef struct mrf_field_desc {
      * network takes the 16 head outputs and the 16 real spherical harmonics of
      * the unit view direction in the field's frame (bands 0..3):
      * 32 -> 64 (wc1: 64 x 32, bc1) -> 64 (wc2, bc2) -> 3 (wc3: 3 x 64, bc3),
-     * r = softplus.  w2, b2, w3, b3 may then be NULL.  Such fields are
-     * evaluated in FP32 on the CUDA cores by both engines (the tensor-core
-     * field kernel serves the view-independent layout only); mrf_field_query
-     * evaluates them for the view direction +z. */
+     * r = softplus.  w2, b2, w3, b3 may then be NULL; n_levels * n_features
+     * must be 32.  FP32 runs on the CUDA cores (both engines); FP16/BF16 on the
+     * tensor cores in the wavefront engine (five chained MMAs per tile).
+     * mrf_field_query evaluates them for the view direction +z. */
     int32_t view_dependent;
     const float *wd2, *bd2, *wc1, *bc1, *wc2, *bc2, *wc3, *bc3;
 } mrf_field_desc;

@@ -15,6 +15,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmrf.so")
+# bounds-checked variant (every table, node and triangle index tested before use)
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libmrf_checked.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cpp", "bvh_build.cpp", "render_mega.cu", "render_wavefront.cu", "bvh_refit.cu", "field_tc.cu", "shadow_net.cu",
@@ -26,9 +29,11 @@ def _nvcc() -> str:
     return cand if os.path.exists(cand) else "nvcc"
 
 
-def _flags(verbose_ptxas: bool):
+def _flags(verbose_ptxas: bool, checked: bool = False):
     f = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
                 "--expt-relaxed-constexpr", "-Xcompiler", "-Wall"]
+    if checked:
+        f += ["-DMRF_BOUNDS_CHECK"]
     if verbose_ptxas:
         f += ["-Xptxas", "-v"]
     return f
@@ -43,17 +48,19 @@ def _stale(obj: str, src: str) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = None, checked: bool = False) -> str:
+    """Builds libmrf.so (or with checked=True the bounds-checked libmrf_checked.so)."""
+    bdir, lib_path = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
     objs, cmds = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src + ".o")
+        o = os.path.join(bdir, src + ".o")
         objs.append(o)
         if force or _stale(o, s):
             lang = ["-x", "cu"] if src.endswith(".cu") else ["-x", "c++"]
-            cmds.append([nvcc] + _flags(verbose_ptxas) + lang + ["-c", s, "-o", o])
+            cmds.append([nvcc] + _flags(verbose_ptxas, checked) + lang + ["-c", s, "-o", o])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -67,14 +74,14 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
                     raise RuntimeError("nvcc failed: " + " ".join(cmd))
                 if verbose_ptxas and r.stderr:
                     sys.stderr.write(r.stderr)
-    if cmds or not os.path.exists(LIB):
-        tmp = LIB + f".{os.getpid()}.tmp"
+    if cmds or not os.path.exists(lib_path):
+        tmp = lib_path + f".{os.getpid()}.tmp"
         r = subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"], capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError("link failed")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -245,6 +245,7 @@ static mrf_status upload(mrf_field *f, const T *src, size_t n, const T **dst, co
 static mrf_status field_create_impl(mrf_context *ctx, const mrf_field_desc *D, mrf_field *f) {
     FieldDev &F = f->dev;
     F.kind = D->kind;
+    F.status = ctx->status;
     for (int k = 0; k < 3; ++k) {
         if (!(D->aabb_max[k] > D->aabb_min[k])) return fail(MRF_ERR_INVALID_ARG, "mrf_field_create: empty box");
         F.lo[k] = D->aabb_min[k];
@@ -349,10 +350,10 @@ static mrf_status field_create_impl(mrf_context *ctx, const mrf_field_desc *D, m
     for (int j = 0; j < 64; ++j)
         for (int o = 0; o < 4; ++o) W3T[j * 4 + o] = w3[o * 64 + j];
     std::memcpy(B3, b3.data(), 4 * 4);
+    std::vector<float> wd2, bd2, wc1, bc1, wc2, bc2, wc3, bc3;
     if (vd) {
         if (!D->wd2 || !D->bd2 || !D->wc1 || !D->bc1 || !D->wc2 || !D->bc2 || !D->wc3 || !D->bc3)
             return fail(MRF_ERR_INVALID_ARG, "mrf_field_create: view-dependent heads missing");
-        std::vector<float> wd2, bd2, wc1, bc1, wc2, bc2, wc3, bc3;
         if ((st = fetch(wd2, D->wd2, 16 * 64)) || (st = fetch(bd2, D->bd2, 16)) || (st = fetch(wc1, D->wc1, 64 * 32)) ||
             (st = fetch(bc1, D->bc1, 64)) || (st = fetch(wc2, D->wc2, 64 * 64)) || (st = fetch(bc2, D->bc2, 64)) ||
             (st = fetch(wc3, D->wc3, 3 * 64)) || (st = fetch(bc3, D->bc3, 3)))
@@ -376,8 +377,10 @@ static mrf_status field_create_impl(mrf_context *ctx, const mrf_field_desc *D, m
     if ((st = upload(f, pk.data(), pk.size(), &F.mlp, "mlp weights"))) return st;
     // FP16 and BF16 copies of W1 (64 x in), W2 (64 x 64), W3 (padded to 16 x 64) in the
     // tensor-core operand layout
+    // (view-dependent fields: W1 (64 x 32) at 0, Wd (16 x 64) at 4096, Wc1 (64 x 32) at 6144,
+    // Wc2 (64 x 64) at 10240, Wc3 (padded to 16 x 64) at 18432; 20480 bytes per precision)
     {
-        const size_t w1b = 64 * (size_t)n_in * 2, per = w1b + 10240;
+        const size_t w1b = 64 * (size_t)n_in * 2, per = vd ? 20480 : w1b + 10240;
         std::vector<uint8_t> lp(2 * per, 0);
         for (int prec = 0; prec < 2; ++prec) {
             uint8_t *base = lp.data() + prec * per;
@@ -387,6 +390,17 @@ static mrf_status field_create_impl(mrf_context *ctx, const mrf_field_desc *D, m
             };
             for (int j = 0; j < 64; ++j)
                 for (int i = 0; i < (int)n_in; ++i) put(umma_offset(j, i, (int)n_in), w1[j * n_in + i]);
+            if (vd) {
+                for (int j = 0; j < 16; ++j)
+                    for (int i = 0; i < 64; ++i) put(4096 + umma_offset(j, i, 64), wd2[j * 64 + i]);
+                for (int j = 0; j < 64; ++j)
+                    for (int i = 0; i < 32; ++i) put(6144 + umma_offset(j, i, 32), wc1[j * 32 + i]);
+                for (int j = 0; j < 64; ++j)
+                    for (int i = 0; i < 64; ++i) put(10240 + umma_offset(j, i, 64), wc2[j * 64 + i]);
+                for (int j = 0; j < 3; ++j)
+                    for (int i = 0; i < 64; ++i) put(18432 + umma_offset(j, i, 64), wc3[j * 64 + i]);
+                continue;
+            }
             for (int j = 0; j < 64; ++j)
                 for (int i = 0; i < 64; ++i) put(w1b + umma_offset(j, i, 64), w2[j * 64 + i]);
             for (int j = 0; j < 4; ++j)
@@ -485,7 +499,12 @@ mrf_status mrf_field_query(mrf_context *ctx, const mrf_field *field, const float
         return fail(MRF_ERR_INVALID_ARG, "mrf_field_query: points and out must be device memory");
     const FieldDev &F = field->dev;
     const cudaStream_t s = (cudaStream_t)stream;
-    if (F.kind == MRF_FIELD_HASHGRID && F.precision != MRF_PREC_FP32 && !F.view_dep) {
+    if (F.kind == MRF_FIELD_HASHGRID && F.precision != MRF_PREC_FP32 && F.view_dep) {
+        const int grid = (int)std::min<uint32_t>((n + 127) / 128, 152u * (uint32_t)field_tc_blocks_per_sm());
+        CUDA_TRY(launch_field_tc_view(F, F.precision == MRF_PREC_BF16, points, 3, nullptr, nullptr, n,
+                                      reinterpret_cast<float4 *>(out), ctx->status, grid, s),
+                 "mrf_field_query: tensor-core launch");
+    } else if (F.kind == MRF_FIELD_HASHGRID && F.precision != MRF_PREC_FP32) {
         const int grid = (int)std::min<uint32_t>((n + 127) / 128, 152u * (uint32_t)field_tc_blocks_per_sm());
         CUDA_TRY(launch_field_tc(F, F.precision == MRF_PREC_BF16, points, 3, nullptr, n, reinterpret_cast<float4 *>(out),
                                  ctx->status, grid, s),
@@ -565,6 +584,7 @@ mrf_status mrf_bvh_build(mrf_context *ctx, const float *verts, uint32_t n_verts,
     b->dev.tris = b->tris;
     b->dev.n_nodes = b->n_nodes;
     b->dev.n_tris = (int)n_tris;
+    b->dev.status = ctx->status;
     *out = b;
     return MRF_OK;
 }
@@ -910,7 +930,7 @@ static mrf_status plan_render(mrf_context *ctx, const mrf_field *field, const mr
     }
     // AUTO: tensor-core field evaluation needs the wavefront engine's flat sample
     // tiles; FP32 runs the megakernel
-    const bool lowp = field->dev.kind == MRF_FIELD_HASHGRID && field->dev.precision != MRF_PREC_FP32 && !field->dev.view_dep;
+    const bool lowp = field->dev.kind == MRF_FIELD_HASHGRID && field->dev.precision != MRF_PREC_FP32;
     R.engine = opts->engine == MRF_ENGINE_AUTO ? (lowp ? MRF_ENGINE_WAVEFRONT : MRF_ENGINE_MEGAKERNEL) : opts->engine;
     if (R.engine == MRF_ENGINE_MEGAKERNEL && lowp)
         return fail(MRF_ERR_UNSUPPORTED, "mrf_render: FP16/BF16 fields run on the wavefront engine");

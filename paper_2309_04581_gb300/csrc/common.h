@@ -54,6 +54,7 @@ struct FieldDev {
     // rigid pose: world-to-local [R^T | -R^T t] applied to every marched ray
     int has_pose;
     float to_local[12];
+    unsigned *status;           // the context's status word (bounds-checked builds report here)
 };
 
 // BVH node: 4 x float4 = both children's boxes + (left, right, left_count, right_count).
@@ -63,7 +64,29 @@ struct BvhDev {
     const float4 *tris;         // 3 x float4 per triangle: (v0, id) (v1, material) (v2, 0)
     int n_nodes;
     int n_tris;
+    unsigned *status;           // the context's status word (bounds-checked builds report here)
 };
+
+// Bounds-checked builds (-DMRF_BOUNDS_CHECK, libmrf_checked.so) test every
+// table, node and triangle index before the access; a bad index sets `bit` in
+// the status word and is replaced by 0, so the access stays in bounds and the
+// next call reports MRF_ERR_TIMEOUT-class status.  Release builds compile the
+// check away.
+constexpr unsigned kStatusBadIndex = 0x100u;
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t checked_index(uint32_t i, uint64_t n, unsigned *status) {
+#ifdef MRF_BOUNDS_CHECK
+    if ((uint64_t)i >= n) {
+        if (status) atomicOr(status, kStatusBadIndex);
+        return 0u;
+    }
+#else
+    (void)n;
+    (void)status;
+#endif
+    return i;
+}
+#endif
 
 struct MaterialDev {
     int kind;
@@ -191,6 +214,9 @@ cudaError_t launch_field_simt(const FieldDev &F, const float *pts, int stride, c
 cudaError_t launch_field_tc(const FieldDev &F, bool bf16, const float *pts, int stride, const uint32_t *n_dev,
                             uint32_t n_host, float4 *out, unsigned *status, int grid, cudaStream_t s, int groups = 8);
 int field_tc_blocks_per_sm(int groups = 8);
+cudaError_t launch_field_tc_view(const FieldDev &F, bool bf16, const float *pts, int stride, const float4 *dirs,
+                                 const uint32_t *n_dev, uint32_t n_host, float4 *out, unsigned *status, int grid,
+                                 cudaStream_t s, int groups = 8);
 cudaError_t launch_cast(const BvhDev &B, const float *o, const float *d, const uint32_t *skip, uint32_t n, float tmin,
                         float *out_t, uint32_t *out_tri, unsigned long long *stats, cudaStream_t s);
 cudaError_t launch_tonemap(const float4 *in, uint32_t n, float exposure, float4 *out, cudaStream_t s);

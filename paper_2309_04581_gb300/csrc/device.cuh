@@ -184,7 +184,7 @@ __device__ __forceinline__ float2 hash_level(const FieldDev &F, int l, V3 p) {
         uint32_t idx = dense ? x + (N + 1) * (y + (N + 1) * z) : ((x ^ (y * 2654435761u) ^ (z * 805459861u)) & (T - 1));
         float wt = ((k & 1) ? w[0] : 1.f - w[0]) * (((k >> 1) & 1) ? w[1] : 1.f - w[1]) *
                    (((k >> 2) & 1) ? w[2] : 1.f - w[2]);
-        uint32_t e = __ldg(tab + idx);
+        uint32_t e = __ldg(tab + checked_index(idx, T, F.status));
         __half2 h = *reinterpret_cast<__half2 *>(&e);
         float2 v = __half22float2(h);
         f0 = fmaf(wt, v.x, f0);
@@ -465,7 +465,7 @@ __device__ bool bvh_trace(const BvhDev &B, V3 o, V3 d, uint32_t skip, float tmin
     int guard = 4 * B.n_nodes + 64;
     while (true) {
         if (--guard < 0) { fault = true; return found; }
-        const float4 *nd = B.nodes + 4 * node;
+        const float4 *nd = B.nodes + 4 * checked_index((uint32_t)node, (uint64_t)B.n_nodes, B.status);
         float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
         int ci[2] = {__float_as_int(n3.x), __float_as_int(n3.y)};
         int cc[2] = {__float_as_int(n3.z), __float_as_int(n3.w)};
@@ -483,7 +483,7 @@ __device__ bool bvh_trace(const BvhDev &B, V3 o, V3 d, uint32_t skip, float tmin
                 for (int k = ci[s]; k < ci[s] + cc[s]; ++k) {
                     V3 a, b, c;
                     uint32_t id, mat;
-                    load_tri(B, k, a, b, c, id, mat);
+                    load_tri(B, (int)checked_index((uint32_t)k, (uint64_t)B.n_tris, B.status), a, b, c, id, mat);
                     if (id == skip) continue;
                     float t;
                     if (tri_test(o, d, a, b, c, tmin, h.t, t, retests)) {

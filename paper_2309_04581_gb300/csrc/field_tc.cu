@@ -170,6 +170,8 @@ __device__ __forceinline__ float2 encode_level_pairs(const FieldDev &F, int l, V
     const uint32_t *tab = F.table + ((size_t)l << F.log2T);
     uint32_t e[8];
 #pragma unroll
+    for (int k = 0; k < 8; ++k) idx[k] = checked_index(idx[k], 1ull << F.log2T, F.status);
+#pragma unroll
     for (int k = 0; k < 4; ++k) load_pair(tab, idx[2 * k], idx[2 * k + 1], e[2 * k], e[2 * k + 1]);
     float2 v[8];
 #pragma unroll
@@ -358,6 +360,199 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
                      : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// View-dependent fields: five chained MMAs per 128-sample tile.  Layer 1
+// (in -> 64), the density head (64 -> 16, N = 16), then the colour network on
+// [head outputs | sh16(view direction)] (32 -> 64 -> 64 -> 3, the last padded
+// to N = 16).  Operand block of each precision (bytes): W1 (64 x 32) at 0,
+// Wd (16 x 64) at 4096, Wc1 (64 x 32) at 6144, Wc2 (64 x 64) at 10240,
+// Wc3 (16 x 64, rows 3.. zero) at 18432; 20,480 bytes.
+constexpr int kVW1 = 0, kVWd = 4096, kVWc1 = 6144, kVWc2 = 10240, kVWc3 = 18432, kVWBytes = 20480;
+constexpr int kVBias = kVWBytes;                       // b1[64] bd[16] bc1[64] bc2[64] bc3[4]
+constexpr int kVSupport = kVBias + 212 * 4;
+constexpr int kVBars = kVSupport + kSupportMax * 16;
+template <int G>
+struct LayoutV {
+    static constexpr int bars = kVBars;
+    static constexpr int tmem_slot = kVBars + 8 * G;
+    static constexpr int a0 = (tmem_slot + 8 + 127) / 128 * 128;
+    static constexpr int bytes = a0 + G * kABytes;
+    static constexpr uint32_t tmem_cols = 64 * G;
+};
+
+template <bool kBF16, int G>
+__global__ void __launch_bounds__(128 * G, 8 / G)
+    field_tc_view_kernel(const FieldDev F, const float *__restrict__ pts, int stride, const float4 *__restrict__ dirs,
+                         const uint32_t *__restrict__ n_dev, uint32_t n_host, float4 *__restrict__ out,
+                         unsigned *__restrict__ status) {
+    using Lo = LayoutV<G>;
+    extern __shared__ __align__(128) uint8_t smem[];
+    float *sBias = reinterpret_cast<float *>(smem + kVBias);
+    uint32_t *sTmem = reinterpret_cast<uint32_t *>(smem + Lo::tmem_slot);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int g = tid >> 7, gt = tid & 127, gw = gt >> 5;
+    constexpr int kThreadsCta = 128 * G;
+    {
+        const uint8_t *src = reinterpret_cast<const uint8_t *>(F.mlp_lp) + (kBF16 ? kVWBytes : 0);
+        for (int o = tid * 16; o < kVWBytes; o += kThreadsCta * 16)
+            *reinterpret_cast<uint4 *>(smem + o) = __ldg(reinterpret_cast<const uint4 *>(src + o));
+        const float *b1 = F.mlp + 32 * 64, *v = F.mlp + mlp_floats(32);
+        const float *bd = v + 64 * 16, *bc1 = bd + 16 + 32 * 64, *bc2 = bc1 + 64 + 64 * 64, *bc3 = bc2 + 64 + 256;
+        if (tid < 64) {
+            sBias[tid] = b1[tid];
+            sBias[80 + tid] = bc1[tid];
+            sBias[144 + tid] = bc2[tid];
+        }
+        if (tid < 16) sBias[64 + tid] = bd[tid];
+        if (tid < 4) sBias[208 + tid] = tid < 3 ? bc3[tid] : 0.f;
+    }
+    float4 *sSup = reinterpret_cast<float4 *>(smem + kVSupport);
+    const bool sup_smem = F.n_support <= kSupportMax;
+    if (sup_smem)
+        for (int k = tid; k < F.n_support; k += kThreadsCta) sSup[k] = __ldg(F.support + k);
+    const float4 *sup = sup_smem ? sSup : F.support;
+    const uint32_t bar = smem_u32(smem + Lo::bars + 8 * g);
+    if (gt == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(sTmem)),
+                     "r"(Lo::tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *sTmem;
+    const uint32_t t_acc = tmem + 64u * (uint32_t)g;
+    const uint32_t t_row = t_acc + ((uint32_t)(gw * 32) << 16);
+    uint8_t *sA = smem + Lo::a0 + g * kABytes;
+    const uint32_t aA = smem_u32(sA), aW1 = smem_u32(smem + kVW1), aWd = smem_u32(smem + kVWd),
+                   aWc1 = smem_u32(smem + kVWc1), aWc2 = smem_u32(smem + kVWc2), aWc3 = smem_u32(smem + kVWc3);
+    constexpr uint32_t id64 = instr_desc(kBF16, 128, 64), id16 = instr_desc(kBF16, 128, 16);
+    const uint32_t n = n_dev ? min(*n_dev, n_host) : n_host;
+    const int bar_id = 1 + g;
+    uint32_t phase = 0;
+    bool ok = true;
+
+    // issue the K steps of one layer from a K-major A (sbo) against weights w
+    auto layer = [&](uint32_t w, int ksteps, int sbo, uint32_t idesc) {
+        fence_async_smem();
+        fence_before_sync();
+        if (group_sync_or(bar_id, !ok)) return false;
+        if (gt == 0) {
+            fence_after_sync();
+            for (int k = 0; k < ksteps; ++k)
+                mma_f16(t_acc, smem_desc(aA + 256 * k, 128, sbo), smem_desc(w + 256 * k, 128, sbo), idesc, k);
+            mma_commit(bar);
+        }
+        ok &= mbar_wait(bar, phase);
+        phase ^= 1;
+        fence_after_sync();
+        return true;
+    };
+
+    for (uint32_t tile = blockIdx.x * G + g; tile * 128u < n; tile += gridDim.x * G) {
+        const uint32_t i = tile * 128u + gt;
+        const bool valid = i < n;
+        V3 p = v3(0.f, 0.f, 0.f), dv = v3(0.f, 0.f, 1.f);
+        float s = 0.f;
+        if (valid) {
+            p = v3(pts[(size_t)stride * i], pts[(size_t)stride * i + 1], pts[(size_t)stride * i + 2]);
+            if (dirs) {
+                const float4 q = dirs[i];
+                dv = v3(q.x, q.y, q.z);
+            }
+            if (F.n_support) {
+                for (int k = 0; k < F.n_support; ++k) {
+                    const float4 c = sup[k];
+                    const float dx = p.x - c.x, dy = p.y - c.y, dz = p.z - c.z;
+                    s = fmaxf(s, 1.0f - (dx * dx + dy * dy + dz * dz) * c.w);
+                }
+            } else {
+                s = 1.f;
+            }
+            if (!inside_field_box(F, p)) s = 0.f;
+        }
+        for (int c = 0; c < 4; ++c) {
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+            if (s > 0.f) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float2 f = encode_level_pairs(F, 4 * c + q, p);
+                    w[q] = pack2<kBF16>(f.x, f.y);
+                }
+            }
+            store_chunk(sA, gt, c, 512, make_uint4(w[0], w[1], w[2], w[3]));
+        }
+        if (!layer(aW1, 2, 512, id64)) break;
+        {   // layer 1 epilogue -> A (K = 64)
+            uint32_t r[32];
+            tmem_ld_x32(t_row, r);
+            relu_bias_store<kBF16>(r, sBias, sA, gt, 0);
+            tmem_ld_x32(t_row + 32, r);
+            relu_bias_store<kBF16>(r, sBias + 32, sA, gt, 4);
+        }
+        if (!layer(aWd, 4, 1024, id16)) break;
+        float sigma;
+        {   // density head: sigma, and A (K = 32) = [head outputs | sh16(view)]
+            uint32_t r[16];
+            tmem_ld_x16(t_row, r);
+            float x[32];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) x[k] = __uint_as_float(r[k]) + sBias[64 + k];
+            sigma = s * expf(fminf(x[0], 15.f));
+            sh16(normalize(dv), x + 16);
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                store_chunk(sA, gt, c, 512,
+                            make_uint4(pack2<kBF16>(x[8 * c], x[8 * c + 1]), pack2<kBF16>(x[8 * c + 2], x[8 * c + 3]),
+                                       pack2<kBF16>(x[8 * c + 4], x[8 * c + 5]),
+                                       pack2<kBF16>(x[8 * c + 6], x[8 * c + 7])));
+        }
+        if (!layer(aWc1, 2, 512, id64)) break;
+        {
+            uint32_t r[32];
+            tmem_ld_x32(t_row, r);
+            relu_bias_store<kBF16>(r, sBias + 80, sA, gt, 0);
+            tmem_ld_x32(t_row + 32, r);
+            relu_bias_store<kBF16>(r, sBias + 112, sA, gt, 4);
+        }
+        if (!layer(aWc2, 4, 1024, id64)) break;
+        {
+            uint32_t r[32];
+            tmem_ld_x32(t_row, r);
+            relu_bias_store<kBF16>(r, sBias + 144, sA, gt, 0);
+            tmem_ld_x32(t_row + 32, r);
+            relu_bias_store<kBF16>(r, sBias + 176, sA, gt, 4);
+        }
+        if (!layer(aWc3, 4, 1024, id16)) break;
+        {
+            uint32_t r[16];
+            tmem_ld_x16(t_row, r);
+            if (valid) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (s > 0.f)
+                    v = make_float4(sigma, softplusf(__uint_as_float(r[0]) + sBias[208]),
+                                    softplusf(__uint_as_float(r[1]) + sBias[209]),
+                                    softplusf(__uint_as_float(r[2]) + sBias[210]));
+                out[i] = v;
+            }
+        }
+        fence_before_sync();
+    }
+    if (!ok && gt == 0 && status) atomicOr(status, 4u);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Lo::tmem_cols)
+                     : "memory");
+}
+
 }  // namespace
 
 // CTAs per SM of the persistent launch: 8 groups take all 512 TMEM columns
@@ -374,6 +569,26 @@ static cudaError_t launch_groups(bool bf16, const FieldDev &F, const float *pts,
     if (grid <= 0) grid = 1;
     kern<<<grid, 128 * G, bytes, s>>>(F, pts, stride, n_dev, n_host, out, status);
     return cudaGetLastError();
+}
+
+template <int G>
+static cudaError_t launch_view_groups(bool bf16, const FieldDev &F, const float *pts, int stride, const float4 *dirs,
+                                      const uint32_t *n_dev, uint32_t n_host, float4 *out, unsigned *status, int grid,
+                                      cudaStream_t s) {
+    auto kern = bf16 ? field_tc_view_kernel<true, G> : field_tc_view_kernel<false, G>;
+    constexpr int bytes = LayoutV<G>::bytes;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    if (grid <= 0) grid = 1;
+    kern<<<grid, 128 * G, bytes, s>>>(F, pts, stride, dirs, n_dev, n_host, out, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_tc_view(const FieldDev &F, bool bf16, const float *pts, int stride, const float4 *dirs,
+                                 const uint32_t *n_dev, uint32_t n_host, float4 *out, unsigned *status, int grid,
+                                 cudaStream_t s, int groups) {
+    if (groups == 4) return launch_view_groups<4>(bf16, F, pts, stride, dirs, n_dev, n_host, out, status, grid, s);
+    return launch_view_groups<kGroups>(bf16, F, pts, stride, dirs, n_dev, n_host, out, status, grid, s);
 }
 
 cudaError_t launch_field_tc(const FieldDev &F, bool bf16, const float *pts, int stride, const uint32_t *n_dev,

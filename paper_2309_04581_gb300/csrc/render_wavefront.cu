@@ -18,6 +18,7 @@
 #include <mutex>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "path.cuh"
 #include "shadow_net.cuh"
@@ -419,7 +420,7 @@ __global__ void __launch_bounds__(kThreads) wf_cast(const WfParams W, uint32_t j
     for (uint32_t i = 0; nmask; ++i) {
         const int q = __ffsll((long long)nmask) - 1;
         nmask &= nmask - 1;
-        W.squeue[qbase + i] = tid * (uint32_t)K + (uint32_t)q;
+        W.squeue[checked_index(qbase + i, (uint64_t)W.paths * (uint64_t)K, P.status)] = tid * (uint32_t)K + (uint32_t)q;
     }
     flush_counters(P.stats, C);
     if (C.fault && P.status) atomicOr(P.status, C.fault);
@@ -823,8 +824,9 @@ __global__ void __launch_bounds__(kThreads) wf_shade(const WfParams W, uint32_t 
         }
         push = !end;
     }
-    const uint32_t slot = warp_alloc(&W.ctr[nxt], push ? 1u : 0u);
+    uint32_t slot = warp_alloc(&W.ctr[nxt], push ? 1u : 0u);
     if (push) {
+        slot = checked_index(slot, W.paths, P.status);
         W.qpath[nxt][slot] = path;
         W.qo[nxt][slot] = make_float4(o.x, o.y, o.z, __uint_as_float(prev));
         W.qd[nxt][slot] = make_float4(d.x, d.y, d.z, 0.f);
@@ -899,14 +901,20 @@ cudaError_t enqueue_frame(const WfParams &W, const RenderParams &P, uint32_t pat
                           KernelTimer *timer) {
     const unsigned grid = (paths + kThreads - 1) / kThreads;
     const FieldDev &F = P.F;
-    const bool tc = F.kind == MRF_FIELD_HASHGRID && F.precision != MRF_PREC_FP32 && !F.view_dep;
+    const bool tc = F.kind == MRF_FIELD_HASHGRID && F.precision != MRF_PREC_FP32;
     const int groups = P.tc_groups == 4 ? 4 : 8;
     const int field_grid = tc ? 152 * field_tc_blocks_per_sm(groups) : 152 * 8;
     const int rounds = std::min(std::max(P.max_rounds, 1), kMaxRounds);
     cudaError_t e = cudaMemsetAsync(W.ctr, 0, 4 * (4 + kMaxRounds), s);   // counters left over from the previous call
     if (e != cudaSuccess) return e;
+    // NVTX ranges mark the host-side enqueue of the frame and of each segment
+    struct Range {
+        explicit Range(const char *n) { nvtxRangePushA(n); }
+        ~Range() { nvtxRangePop(); }
+    } frame_range("mrf wavefront frame");
     for (uint32_t j = 1; j <= P.max_bounces; ++j) {
         const int cur = (j - 1) & 1, nxt = j & 1;
+        Range seg_range("mrf segment");
         if ((e = cudaMemsetAsync(W.ctr + 2, 0, 4 * (2 + rounds), s)) != cudaSuccess) return e;
         timer_begin(timer, MRF_KERNEL_CAST_GEN, s);
         wf_cast<<<grid, kThreads, 0, s>>>(W, j, cur);
@@ -934,7 +942,10 @@ cudaError_t enqueue_frame(const WfParams &W, const RenderParams &P, uint32_t pat
             timer_end(timer, s);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             timer_begin(timer, MRF_KERNEL_FIELD, s);
-            if (tc)
+            if (tc && F.view_dep)
+                e = launch_field_tc_view(F, F.precision == MRF_PREC_BF16, reinterpret_cast<const float *>(W.samp), 4,
+                                         W.sview, W.ctr + 2, W.cap, W.fout, P.status, field_grid, s, groups);
+            else if (tc)
                 e = launch_field_tc(F, F.precision == MRF_PREC_BF16, reinterpret_cast<const float *>(W.samp), 4,
                                     W.ctr + 2, W.cap, W.fout, P.status, field_grid, s, groups);
             else

@@ -69,7 +69,8 @@ __device__ __forceinline__ void snet_encode(const ShadowNetDev &N, V3 pl, V3 wl,
             const uint32_t i = snet_index(N, l, c[0] + (k & 1), c[1] + ((k >> 1) & 1), c[2] + ((k >> 2) & 1));
             const float wt = ((k & 1) ? f[0] : 1.f - f[0]) * (((k >> 1) & 1) ? f[1] : 1.f - f[1]) *
                              (((k >> 2) & 1) ? f[2] : 1.f - f[2]);
-            const float2 e = __ldg(reinterpret_cast<const float2 *>(N.table) + i);
+            const float2 e = __ldg(reinterpret_cast<const float2 *>(N.table) +
+                                   checked_index(i, (uint64_t)kSnetLevels << N.log2T, nullptr));
             a0 = fmaf(wt, e.x, a0);
             a1 = fmaf(wt, e.y, a1);
         }

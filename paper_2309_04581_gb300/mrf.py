@@ -18,7 +18,8 @@ import numpy as np
 from . import scenes as S
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libmrf.so")
+# MRF_LIB selects another in-tree build (the bounds-checked libmrf_checked.so)
+LIB_PATH = os.environ.get("MRF_LIB") or os.path.join(_HERE, "libmrf.so")
 _lib = None
 _lock = threading.Lock()
 

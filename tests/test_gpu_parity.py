@@ -581,13 +581,22 @@ def test_field_sample_shadow_mask_matches_oracle(M, orc, torch_cuda, engine):
 
 
 # ----------------------------------------------------------------- view-dependent radiance
-@pytest.mark.parametrize("engine", ["megakernel", "wavefront"])
+@pytest.mark.parametrize("engine", ["megakernel", "wavefront", "wavefront_bf16"])
 def test_view_dependent_field_matches_oracle(M, orc, torch_cuda, engine):
     """Instant-NGP network layout: a density head and a colour network of the
-    view direction's spherical harmonics (field frame), posed field included."""
+    view direction's spherical harmonics (field frame), posed field included;
+    BF16 runs the five-MMA tensor-core kernel."""
     sc = S.config2_view(48, 48)
     sc.field.pose = S.rigid_pose([0.2, 1.0, 0.1], 0.4, [0.03, -0.02, 0.05])
     ref = orc.render(sc)
+    if engine == "wavefront_bf16":
+        gpu = _render_prec(M, sc, "bf16")
+        ok = ref["flags"] == 0
+        psnr = _psnr(gpu["rgba"], ref["rgba"], ok)
+        print(f"view-dependent BF16 tensor cores: PSNR {psnr:.1f} dB")
+        assert psnr >= 45.0 and np.abs(gpu["rgba"][ok, :3] - ref["rgba"][ok, :3]).max() <= 1e-2
+        assert np.array_equal(gpu["tri"][ok], ref["tri"][ok])
+        return
     eng = M.MRF_ENGINE_MEGAKERNEL if engine == "megakernel" else M.MRF_ENGINE_WAVEFRONT
     gpu = _render(M, sc, engine=eng)
     _compare(gpu, ref)
@@ -599,13 +608,14 @@ def test_view_dependent_field_matches_oracle(M, orc, torch_cuda, engine):
     assert np.abs(_render(M, flat, engine=eng)["rgba"] - gpu["rgba"]).max() > 1e-3
 
 
-def test_view_dependent_field_query(M, orc, torch_cuda):
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_view_dependent_field_query(M, orc, torch_cuda, prec):
     torch = torch_cuda
     sc = S.config2_view(8, 8)
     rng = np.random.default_rng(21)
     pts = rng.uniform(-0.45, 0.45, (5000, 3)).astype(np.float32)
     ctx = M.mrf_context_create(0)
-    desc, keep = M.field_desc(sc.field)
+    desc, keep = M.field_desc(sc.field, M.MRF_PREC_BF16 if prec == "bf16" else M.MRF_PREC_FP32)
     f = M.mrf_field_create(ctx, desc)
     dp = torch.from_numpy(pts).cuda()
     out = torch.empty((pts.shape[0], 4), dtype=torch.float32, device="cuda")
@@ -616,6 +626,9 @@ def test_view_dependent_field_query(M, orc, torch_cuda):
                      *orc.field_eval_dir(osc, p.astype(np.float64), [0, 0, 1])[1]] for p in pts])
     assert (ref[:, 0] > 0).sum() > 100
     scale = np.maximum(np.abs(ref).max(0), 1e-6)
-    assert np.all(np.abs(got - ref) <= 1e-4 * np.abs(ref) + 1e-6 * scale)
+    if prec == "fp32":
+        assert np.all(np.abs(got - ref) <= 1e-4 * np.abs(ref) + 1e-6 * scale)
+    else:   # BF16 operands through five layers: a few 1e-2 relative
+        assert np.all(np.abs(got - ref) <= 5e-2 * np.abs(ref) + 5e-3 * scale)
     M.mrf_field_destroy(f)
     M.mrf_context_destroy(ctx)
