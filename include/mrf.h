@@ -301,6 +301,8 @@ typedef struct mrf_stats {
     uint64_t fp64_retests;         /* near-edge triangle tests redone in FP64 */
     uint64_t status;               /* device status word (0 = ok) */
     uint64_t shadow_net_evals;     /* shadow rays answered by the shadow network */
+    uint64_t ended_miss, ended_tau, ended_cap;   /* paths that left the scene, fell below tau, hit the bounce cap */
+    uint64_t bvh_nodes;            /* BVH nodes visited (closest-hit, shadow and mask rays) */
 } mrf_stats;
 
 /* Renders every path of `rays` (Algorithm 1) with at most max_bounces

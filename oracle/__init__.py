@@ -33,7 +33,8 @@ _lib = None
 
 NO_HIT = 0xFFFFFFFF
 FLAG_EDGE, FLAG_SHADOW, FLAG_FRESNEL, FLAG_TAU, FLAG_BASIS, FLAG_TMIN = 1, 2, 4, 8, 16, 32
-COUNT_NAMES = ("segments", "shadow_rays", "samples_nominal", "samples_supported", "surface_hits", "paths")
+COUNT_NAMES = ("segments", "shadow_rays", "samples_nominal", "samples_supported", "surface_hits", "paths",
+               "ended_miss", "ended_tau", "ended_cap")
 
 _fp = C.POINTER(C.c_float)
 _u32p = C.POINTER(C.c_uint32)
@@ -260,7 +261,7 @@ def render(scene, ids=None, threads: int = 0, records: bool = True, shadow_net=N
     tri = np.zeros((n, spp, B), np.uint32) if records else None
     tt = np.zeros((n, spp, B), np.float64) if records else None
     flags = np.zeros(n, np.uint32)
-    counts = np.zeros(6, np.uint64)
+    counts = np.zeros(len(COUNT_NAMES), np.uint64)
     L.orc_render(os_.ref, _ptr(ids, _u32p), n, _ptr(rgba, _dp), _ptr(segs, _u32p), _ptr(tri, _u32p), _ptr(tt, _dp),
                  _ptr(flags, _u32p), _ptr(counts, _u64p), int(threads))
     return dict(rgba=rgba, segments=segs, tri=tri, t=tt, flags=flags, ids=ids,

@@ -136,7 +136,7 @@ double orc_snet_forward(const struct orc_snet *n, const double p[3], const doubl
 
 /* per-thread counters: segments, shadow rays, nominal samples, samples with
  * non-zero support, surface hits, paths */
-enum { C_SEG = 0, C_SHADOW, C_NOMINAL, C_SUPPORTED, C_HITS, C_PATHS, C_N };
+enum { C_SEG = 0, C_SHADOW, C_NOMINAL, C_SUPPORTED, C_HITS, C_PATHS, C_END_MISS, C_END_TAU, C_END_CAP, C_N };
 
 /* ---------------------------------------------------------------- vectors */
 typedef struct { double x, y, z; } v3;
@@ -763,7 +763,8 @@ static void trace_path(const orc_scene *sc, uint32_t ray, uint32_t s, double L[3
         segs = j;
         cnt[C_SEG]++;
         if (tri_rec) { tri_rec[j - 1] = hit; t_rec[j - 1] = th; }
-        if (stop || hit == ORC_NO_HIT) break;
+        if (stop) { cnt[C_END_TAU]++; break; }
+        if (hit == ORC_NO_HIT) { cnt[C_END_MISS]++; break; }
         cnt[C_HITS]++;
         double p[3] = {o[0] + th * d[0], o[1] + th * d[1], o[2] + th * d[2]};
         double v0[3], v1[3], v2[3];
@@ -824,8 +825,9 @@ static void trace_path(const orc_scene *sc, uint32_t ray, uint32_t s, double L[3
         if (sc->tau > 0) {
             double mt = maxc(T);
             if (fabs(mt - sc->tau) <= 1e-4 * sc->tau) *flags |= ORC_FLAG_TAU;
-            if (mt < sc->tau) break;
+            if (mt < sc->tau) { cnt[C_END_TAU]++; break; }
         }
+        if (j == sc->max_bounces) cnt[C_END_CAP]++;   /* the loop ends after this surface event */
     }
     *segs_out = segs;
 }

@@ -983,6 +983,10 @@ static void stats_from(const unsigned long long *h, unsigned st_word, mrf_stats 
     stats->shadow_samples_evaluated = h[ST_SHADOW_EVALUATED];
     stats->fp64_retests = h[ST_FP64];
     stats->shadow_net_evals = h[ST_NET];
+    stats->ended_miss = h[ST_END_MISS];
+    stats->ended_tau = h[ST_END_TAU];
+    stats->ended_cap = h[ST_END_CAP];
+    stats->bvh_nodes = h[ST_NODES];
     stats->status = st_word;
 }
 
@@ -1382,19 +1386,10 @@ mrf_status mrf_render_static(mrf_context *ctx, const mrf_field *field, const mrf
         unsigned long long h[ST_COUNT];
         CUDA_TRY(cudaMemcpyAsync(h, ctx->stats, sizeof(h), cudaMemcpyDeviceToHost, s), "stats download");
         CUDA_TRY(cudaStreamSynchronize(s), "mrf_render_static: synchronize");
-        stats->paths = h[ST_PATHS];
-        stats->segments = h[ST_SEGMENTS];
-        stats->surface_hits = h[ST_HITS];
-        stats->shadow_rays = h[ST_SHADOW];
-        stats->samples_nominal = h[ST_NOMINAL];
-        stats->samples_evaluated = h[ST_EVALUATED];
-        stats->shadow_samples_evaluated = h[ST_SHADOW_EVALUATED];
-        stats->fp64_retests = h[ST_FP64];
-        stats->shadow_net_evals = h[ST_NET];
         unsigned st_word = 0;
         CUDA_TRY(cudaMemcpy(&st_word, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost),
                  "mrf_render_static: status read");
-        stats->status = st_word;
+        stats_from(h, st_word, stats);
         if (st_word) {
             cudaMemset(ctx->status, 0, sizeof(unsigned));
             return fail(MRF_ERR_TIMEOUT, "mrf_render_static: a kernel gave up (status 0x%x)", st_word);

@@ -451,7 +451,7 @@ __device__ __forceinline__ bool child_hit(float lx, float ly, float lz, float hx
 // `fault` if the traversal stack overflows.
 template <bool any_hit>
 __device__ bool bvh_trace(const BvhDev &B, V3 o, V3 d, uint32_t skip, float tmin, float tmax, Hit &h,
-                          unsigned &retests, bool &fault) {
+                          unsigned &retests, unsigned &visits, bool &fault) {
     h.t = tmax;
     h.id = kNoHit;
     h.slot = -1;
@@ -465,6 +465,7 @@ __device__ bool bvh_trace(const BvhDev &B, V3 o, V3 d, uint32_t skip, float tmin
     int guard = 4 * B.n_nodes + 64;
     while (true) {
         if (--guard < 0) { fault = true; return found; }
+        ++visits;
         const float4 *nd = B.nodes + 4 * checked_index((uint32_t)node, (uint64_t)B.n_nodes, B.status);
         float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
         int ci[2] = {__float_as_int(n3.x), __float_as_int(n3.y)};

@@ -11,12 +11,14 @@ namespace mrf {
 struct Counters {
     unsigned long long nominal;
     unsigned paths, seg, hits, shadow, evaluated, shadow_eval, retests, fault, net;
+    unsigned end_miss, end_tau, end_cap;   // how paths ended: left the scene, throughput below tau, bounce cap
+    unsigned nodes;                        // BVH nodes visited
 };
 
 __device__ __forceinline__ void flush_counters(unsigned long long *stats, Counters &C) {
     if (!stats) return;
     unsigned long long v[ST_COUNT] = {C.paths, C.seg, C.hits, C.shadow, C.nominal, C.evaluated, C.shadow_eval,
-                                      C.retests, C.fault, C.net};
+                                      C.retests, C.fault, C.net, C.end_miss, C.end_tau, C.end_cap, C.nodes};
     const unsigned mask = __activemask();
 #pragma unroll
     for (int k = 0; k < ST_COUNT; ++k) {
@@ -65,9 +67,9 @@ static __device__ __noinline__ float sample_mask(const RenderParams &P, V3 pw) {
         if (!(D > 0.f)) continue;
         w = w * (1.f / D);
         Hit hs;
-        unsigned rs = 0;
+        unsigned rs = 0, nv = 0;
         bool fault = false;
-        if (bvh_trace<true>(P.B, pw, w, kNoHit, P.tmin, D, hs, rs, fault)) m *= 1.f - L0.mask;
+        if (bvh_trace<true>(P.B, pw, w, kNoHit, P.tmin, D, hs, rs, nv, fault)) m *= 1.f - L0.mask;
     }
     return m;
 }

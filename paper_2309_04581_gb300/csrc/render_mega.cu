@@ -25,7 +25,7 @@ __device__ void trace_path(const RenderParams &P, const float *w, uint32_t ray, 
         Hit h;
         unsigned rt = 0;
         bool fault = false;
-        bvh_trace<false>(P.B, o, d, prev, P.tmin, INFINITY, h, rt, fault);
+        bvh_trace<false>(P.B, o, d, prev, P.tmin, INFINITY, h, rt, C.nodes, fault);
         C.retests += rt;
         if (fault) C.fault |= 1;
         const float T0 = T[0];
@@ -38,7 +38,8 @@ __device__ void trace_path(const RenderParams &P, const float *w, uint32_t ray, 
             P.rec_tri[path * P.max_bounces + (j - 1)] = h.id;
             P.rec_t[path * P.max_bounces + (j - 1)] = h.t;
         }
-        if (stop || h.id == kNoHit) break;
+        if (stop) { ++C.end_tau; break; }
+        if (h.id == kNoHit) { ++C.end_miss; break; }
         ++C.hits;
         const SurfaceHit S = surface_at(P, o, d, h);
         float u[3];
@@ -57,7 +58,7 @@ __device__ void trace_path(const RenderParams &P, const float *w, uint32_t ray, 
                     Hit hs;
                     unsigned rs = 0;
                     bool f2 = false;
-                    const bool blocked = bvh_trace<true>(P.B, S.p, wl, S.id, P.tmin, D, hs, rs, f2);
+                    const bool blocked = bvh_trace<true>(P.B, S.p, wl, S.id, P.tmin, D, hs, rs, C.nodes, f2);
                     C.retests += rs;
                     if (f2) C.fault |= 1;
                     if (blocked) continue;
@@ -81,7 +82,8 @@ __device__ void trace_path(const RenderParams &P, const float *w, uint32_t ray, 
         d = normalize(nd);
         o = p;
         prev = id;
-        if (P.tau > 0.f && fmaxf(T[0], fmaxf(T[1], T[2])) < P.tau) break;
+        if (P.tau > 0.f && fmaxf(T[0], fmaxf(T[1], T[2])) < P.tau) { ++C.end_tau; break; }
+        if (j == P.max_bounces) ++C.end_cap;
     }
     if (P.rec_seg) P.rec_seg[path] = segs;
     if (P.rec_tri) {
@@ -220,7 +222,7 @@ __global__ void __launch_bounds__(128) cast_kernel(const BvhDev B, const float *
         unsigned rt = 0;
         bool fault = false;
         bvh_trace<false>(B, v3(o[3 * i], o[3 * i + 1], o[3 * i + 2]), v3(d[3 * i], d[3 * i + 1], d[3 * i + 2]),
-                         skip ? skip[i] : kNoHit, tmin, INFINITY, h, rt, fault);
+                         skip ? skip[i] : kNoHit, tmin, INFINITY, h, rt, C.nodes, fault);
         out_t[i] = h.t;
         out_tri[i] = h.id;
         C.retests = rt;

@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(kThreads) wf_cast(const WfParams W, uint32_t j
         Hit h;
         unsigned rt = 0;
         bool fault = false;
-        bvh_trace<false>(P.B, o, d, prev, P.tmin, INFINITY, h, rt, fault);
+        bvh_trace<false>(P.B, o, d, prev, P.tmin, INFINITY, h, rt, C.nodes, fault);
         C.retests += rt;
         if (fault) C.fault |= 1;
         W.hit_t[tid] = h.t;
@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(kThreads) wf_cast(const WfParams W, uint32_t j
                             Hit hs;
                             unsigned rs = 0;
                             bool f2 = false;
-                            const bool blocked = bvh_trace<true>(P.B, S.p, wl, S.id, P.tmin, D, hs, rs, f2);
+                            const bool blocked = bvh_trace<true>(P.B, S.p, wl, S.id, P.tmin, D, hs, rs, C.nodes, f2);
                             C.retests += rs;
                             if (f2) C.fault |= 1;
                             if (!blocked) {
@@ -787,6 +787,7 @@ __global__ void __launch_bounds__(kThreads) wf_shade(const WfParams W, uint32_t 
             P.rec_t[rbase + (j - 1)] = h.t;
         }
         bool end = stop || h.id == kNoHit;
+        int cause = stop ? 2 : (h.id == kNoHit ? 1 : 0);   // 1 left the scene, 2 throughput below tau, 3 bounce cap
         if (!end) {
             ++C.hits;
             const SurfaceHit S = surface_at(P, o, d, h);
@@ -807,14 +808,22 @@ __global__ void __launch_bounds__(kThreads) wf_shade(const WfParams W, uint32_t 
             d = normalize(nd);
             o = S.p;
             prev = S.id;
-            if (j == P.max_bounces) end = true;
-            if (P.tau > 0.f && fmaxf(T[0], fmaxf(T[1], T[2])) < P.tau) end = true;
+            if (P.tau > 0.f && fmaxf(T[0], fmaxf(T[1], T[2])) < P.tau) {
+                end = true;
+                cause = 2;
+            } else if (j == P.max_bounces) {
+                end = true;
+                cause = 3;
+            }
         }
         acc.x = L[0];
         acc.y = L[1];
         acc.z = L[2];
         W.acc[path] = acc;
         if (end) {
+            C.end_miss += cause == 1;
+            C.end_tau += cause == 2;
+            C.end_cap += cause == 3;
             if (P.rec_seg) P.rec_seg[path] = j;
             if (P.rec_tri)
                 for (uint32_t q = j; q < P.max_bounces; ++q) {

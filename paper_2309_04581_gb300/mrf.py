@@ -108,7 +108,8 @@ class mrf_stats(C.Structure):
     _fields_ = [("paths", C.c_uint64), ("segments", C.c_uint64), ("surface_hits", C.c_uint64),
                 ("shadow_rays", C.c_uint64), ("samples_nominal", C.c_uint64), ("samples_evaluated", C.c_uint64),
                 ("shadow_samples_evaluated", C.c_uint64), ("fp64_retests", C.c_uint64), ("status", C.c_uint64),
-                ("shadow_net_evals", C.c_uint64)]
+                ("shadow_net_evals", C.c_uint64), ("ended_miss", C.c_uint64), ("ended_tau", C.c_uint64),
+                ("ended_cap", C.c_uint64), ("bvh_nodes", C.c_uint64)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

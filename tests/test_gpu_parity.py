@@ -194,6 +194,12 @@ def test_config2_small_full_image(M, orc, torch_cuda):
     ref = orc.render(sc)
     _compare(gpu, ref)
     st = gpu["stats"]
+    # every path ends by exactly one cause; the causes match the oracle's up to flagged pixels
+    assert st["ended_miss"] + st["ended_tau"] + st["ended_cap"] == st["paths"]
+    nflag = int((ref["flags"] != 0).sum())
+    for k in ("ended_miss", "ended_tau", "ended_cap"):
+        assert abs(st[k] - ref["counts"][k]) <= nflag, k
+    assert st["bvh_nodes"] >= st["segments"]
     assert st["shadow_rays"] > 0 and st["samples_evaluated"] > 0
     assert st["samples_nominal"] >= st["samples_evaluated"]
     ok = ref["flags"] == 0

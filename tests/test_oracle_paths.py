@@ -206,6 +206,14 @@ def test_glass_plate_normal_incidence(orc):
     assert n_checked >= 8
 
 
+def test_every_path_ends_by_one_cause(orc):
+    for sc in (S.config1(24, 24), S.config2(24, 24, tau=0.05), S.config2(16, 16, max_bounces=2)):
+        c = orc.render(sc)["counts"]
+        assert c["ended_miss"] + c["ended_tau"] + c["ended_cap"] == c["paths"]
+    c = orc.render(S.config2(16, 16, max_bounces=2))["counts"]
+    assert c["ended_cap"] > 0 and c["ended_tau"] == 0
+
+
 def test_invariants_on_config_scenes(orc):
     for sc, ids in [(S.config1(), None), (S.config2(96, 96), S.strided_pixels(96, 96, 3))]:
         res = orc.render(sc, ids)
