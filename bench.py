@@ -8,7 +8,8 @@ light, fixed step sqrt(3)/1024.  Inputs are synthetic and seeded.
 
 The headline runs the mixed-precision renderer (wavefront engine, BF16 MLP on
 the tensor cores, FP32 everywhere else); the same line carries the FP32 GPU
-path (megakernel) measured the same way, the image error of the headline
+path (megakernel) measured the same way, the same scene at 1920x1080 (BF16
+and FP32, same protocol) under "at_1920x1080", the image error of the headline
 against the FP64 oracle on the CPU-baseline pixel sample, the per-kernel
 timings and the dominant kernel's roofline.  Prints one JSON line.
 
@@ -55,6 +56,7 @@ def parse():
     ap.add_argument("--cpu-stride", type=int, default=4, help="oracle sample: every n-th row and column")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 comparison run")
+    ap.add_argument("--no-1080p", action="store_true", help="skip the 1920x1080 run of the same scene")
     ap.add_argument("--workload", default="hashgrid", choices=["hashgrid", "dynamic", "area", "views"],
                     help="dynamic: the deforming-mesh sequence (per-frame refit, rebuild every --rebuild frames); "
                          "area: 4 area lights x 16 shadow rays, marched against the learned transmittance")
@@ -179,8 +181,10 @@ def workload(args):
     return sc, name
 
 
-def cpu_baseline(sc, stride: int):
-    """The FP64 oracle, as it stands, on a strided pixel sample of the workload."""
+def cpu_baseline(sc, stride: int, single_core_stride: int = 0):
+    """The FP64 oracle, as it stands, on a strided pixel sample of the workload
+    (all host cores); with single_core_stride, also on one core on a sparser
+    sample."""
     import oracle
     from paper_2309_04581_gb300 import scenes as S
     oracle.build()
@@ -193,6 +197,15 @@ def cpu_baseline(sc, stride: int):
           "sample": f"every {stride}th row and column ({len(ids)} of {sc.n_rays} pixels), "
                     f"{seg} segments in {dt:.1f} s",
           "field_samples_per_s": res["counts"]["samples_supported"] / dt}
+    if single_core_stride:
+        ids1 = S.strided_pixels(sc.camera.width, sc.camera.height, single_core_stride)
+        t = time.perf_counter()
+        r1 = oracle.render(sc, ids1, threads=1, records=False)
+        dt1 = time.perf_counter() - t
+        s1 = r1["counts"]["segments"]
+        cb["single_core"] = {"value": s1 / dt1, "unit": METRIC, "cores": 1,
+                             "sample": f"every {single_core_stride}th row and column ({len(ids1)} pixels), "
+                                       f"{s1} segments in {dt1:.1f} s"}
     return cb, ids, res
 
 
@@ -349,6 +362,55 @@ def run_ours(args):
         fp32 = {"value": world * segs / (m32 / 1e3), "ms_per_step": m32, "engine": "megakernel",
                 "speedup_of_headline": m32 / ms}
         r32.close()
+    # BVH traversal of the cast kernel: nodes (64 B) and triangles (48 B) fetched
+    cast = None
+    if "wf_cast" in kernels:
+        c_ms = kernels["wf_cast"]["ms_per_step"]
+        cb_bytes = 64 * st["bvh_nodes"] + 48 * st["bvh_tri_tests"]
+        cast = {"kernel": "wf_cast", "bvh_nodes": st["bvh_nodes"], "tri_tests": st["bvh_tri_tests"],
+                "worst_traversal_nodes": st["bvh_worst_nodes"],
+                "rays": segs + st["shadow_rays"], "algorithmic_bytes": cb_bytes,
+                "achieved_gbs": cb_bytes / (c_ms / 1e3) / 1e9, "ms_per_step": c_ms,
+                "note": "64 B per node visited + 48 B per triangle tested; the BVH is on-chip (L1/L2) resident, "
+                        "so this is not DRAM traffic"}
+    # render time against pixel count (the same scene at 200^2, 400^2, 800^2)
+    scaling = None
+    if not args.no_1080p and (args.width, args.height) == (800, 800):
+        from paper_2309_04581_gb300 import scenes as S
+        scaling = []
+        for n_px in (200, 400):
+            sc_s = S.config2(n_px, n_px)
+            r_s = M.Renderer(sc_s, device=local, precision=prec_id[args.precision])
+            o_s = torch.empty((sc_s.n_rays, 4), dtype=torch.float32, device=dev)
+            ms_s = time_steps(torch, r_s, engine, o_s, stream, 5, args.warmup, flush)
+            scaling.append({"pixels": n_px * n_px, "ms_per_step": statistics.median(ms_s)})
+            r_s.close()
+        scaling.append({"pixels": 640000, "ms_per_step": statistics.median(step_ms)})
+        for e in scaling:
+            e["ns_per_pixel"] = e["ms_per_step"] * 1e6 / e["pixels"]
+    # the same scene at 1920x1080, same protocol (the metric's frame size)
+    hd = None
+    if not args.no_1080p and (args.width, args.height) != (1920, 1080):
+        from paper_2309_04581_gb300 import scenes as S
+        sc_hd = S.config2(1920, 1080)
+        r_hd = M.Renderer(sc_hd, device=local, precision=prec_id[args.precision])
+        o_hd = torch.empty((sc_hd.n_rays, 4), dtype=torch.float32, device=dev)
+        _, st_hd = r_hd.render(out=o_hd, engine=engine, stats=True, stream=stream.cuda_stream)
+        ms_hd = time_steps(torch, r_hd, engine, o_hd, stream, max(3, args.steps // 2), args.warmup, flush)
+        m_hd = max_over_ranks(sum(ms_hd) / len(ms_hd), dev)
+        s_hd = st_hd["samples_evaluated"] + st_hd["shadow_samples_evaluated"]
+        hd = {"value": job_throughput(st_hd["segments"], world, m_hd), "unit": METRIC, "ms_per_step": m_hd,
+              "field_samples_per_s": world * s_hd / (m_hd / 1e3), "segments": st_hd["segments"],
+              "samples_evaluated": s_hd, "steps": len(ms_hd)}
+        if not args.no_fp32 and args.precision != "fp32":
+            r32 = M.Renderer(sc_hd, device=local, precision=M.MRF_PREC_FP32)
+            ms32 = time_steps(torch, r32, M.MRF_ENGINE_MEGAKERNEL, o_hd, stream, 3, 1, flush)
+            m32 = max_over_ranks(sum(ms32) / len(ms32), dev)
+            hd["fp32_gpu"] = {"value": job_throughput(st_hd["segments"], world, m32), "ms_per_step": m32,
+                              "engine": "megakernel", "speedup_of_bf16": m32 / m_hd}
+            r32.close()
+        r_hd.close()
+        del o_hd
     # end to end through the C ABI: host output buffer, device->host copy inside the call
     host_out = torch.empty((sc.n_rays, 4), dtype=torch.float32).pin_memory()
     e2e_ms = []
@@ -377,13 +439,16 @@ def run_ours(args):
             "kernels": kernels,
             "roofline": roof,
             "fp32_gpu": fp32,
+            "at_1920x1080": hd,
+            "bvh_traversal": cast,
+            "time_vs_pixels": scaling,
             "e2e": {"value": e2e, "unit": METRIC, "h2d_bytes_per_step": 48,
                     "d2h_bytes_per_step": sc.n_rays * 16, "ms_per_step": statistics.median(e2e_ms),
                     "note": "camera record passed by value; image copied to pinned host memory inside mrf_render"},
             "gpu_launches": launches * args.steps,
             "clocks": sampler.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb, ids, ref = cpu_baseline(sc, args.cpu_stride)
+        cb, ids, ref = cpu_baseline(sc, args.cpu_stride, 4 * args.cpu_stride)
         line["cpu_baseline"] = cb
         ok = ref["flags"] == 0
         g, o = image[ids][ok, :3], ref["rgba"][ok, :3]

@@ -303,6 +303,9 @@ typedef struct mrf_stats {
     uint64_t shadow_net_evals;     /* shadow rays answered by the shadow network */
     uint64_t ended_miss, ended_tau, ended_cap;   /* paths that left the scene, fell below tau, hit the bounce cap */
     uint64_t bvh_nodes;            /* BVH nodes visited (closest-hit, shadow and mask rays) */
+    uint64_t bvh_tri_tests;        /* ray-triangle tests made by those traversals */
+    uint64_t bvh_worst_nodes;      /* nodes visited by the longest closest-hit traversal */
+    uint64_t bvh_worst_path;       /* the path (ray * spp + sample) that made it */
 } mrf_stats;
 
 /* Renders every path of `rays` (Algorithm 1) with at most max_bounces

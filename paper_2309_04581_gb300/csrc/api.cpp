@@ -987,6 +987,9 @@ static void stats_from(const unsigned long long *h, unsigned st_word, mrf_stats 
     stats->ended_tau = h[ST_END_TAU];
     stats->ended_cap = h[ST_END_CAP];
     stats->bvh_nodes = h[ST_NODES];
+    stats->bvh_tri_tests = h[ST_TRIS];
+    stats->bvh_worst_nodes = h[ST_WORST] >> 32;
+    stats->bvh_worst_path = h[ST_WORST] & 0xffffffffull;
     stats->status = st_word;
 }
 

@@ -119,7 +119,7 @@ inline __host__ __device__ int field_mlp_floats(const FieldDev &F) {
 // device statistics counters (unsigned long long), in this order
 enum StatIndex {
     ST_PATHS = 0, ST_SEGMENTS, ST_HITS, ST_SHADOW, ST_NOMINAL, ST_EVALUATED, ST_SHADOW_EVALUATED, ST_FP64,
-    ST_STATUS, ST_NET, ST_END_MISS, ST_END_TAU, ST_END_CAP, ST_NODES, ST_COUNT
+    ST_STATUS, ST_NET, ST_END_MISS, ST_END_TAU, ST_END_CAP, ST_NODES, ST_TRIS, ST_WORST, ST_COUNT
 };
 
 // Shadow-transmittance network (shadow_net.cu): 8-level hash grid of the point

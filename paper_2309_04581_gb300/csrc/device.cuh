@@ -447,11 +447,12 @@ __device__ __forceinline__ bool child_hit(float lx, float ly, float lz, float hx
 }
 
 // Closest hit (any_hit = false) or first hit in (tmin, tmax) (any_hit = true),
-// skipping the triangle with original id `skip`.  Returns false and sets
+// skipping the triangle with original id `skip`.  Adds the nodes visited to
+// `visits` and the ray-triangle tests made to `tests`.  Returns false and sets
 // `fault` if the traversal stack overflows.
 template <bool any_hit>
 __device__ bool bvh_trace(const BvhDev &B, V3 o, V3 d, uint32_t skip, float tmin, float tmax, Hit &h,
-                          unsigned &retests, unsigned &visits, bool &fault) {
+                          unsigned &retests, unsigned &visits, unsigned &tests, bool &fault) {
     h.t = tmax;
     h.id = kNoHit;
     h.slot = -1;
@@ -486,6 +487,7 @@ __device__ bool bvh_trace(const BvhDev &B, V3 o, V3 d, uint32_t skip, float tmin
                     uint32_t id, mat;
                     load_tri(B, (int)checked_index((uint32_t)k, (uint64_t)B.n_tris, B.status), a, b, c, id, mat);
                     if (id == skip) continue;
+                    ++tests;
                     float t;
                     if (tri_test(o, d, a, b, c, tmin, h.t, t, retests)) {
                         if (t < h.t || (t == h.t && id < h.id)) {

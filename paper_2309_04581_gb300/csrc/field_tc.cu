@@ -28,6 +28,7 @@ using namespace tc;
 // by its tile groups, then one mbarrier and one 16 KB A operand per group.
 constexpr int kSmemW1 = 0, kSmemW2 = 8192, kSmemW3 = 16384, kSmemBias = 18432;
 constexpr int kSmemSupport = kSmemBias + 132 * 4;
+static_assert(kSmemBias % 16 == 0, "biases are read as float4");
 constexpr int kSupportMax = 64;
 constexpr int kSmemBars = kSmemSupport + kSupportMax * 16;
 constexpr int kABytes = 16384;
@@ -341,8 +342,9 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
         {
             uint32_t r[16];
             tmem_ld_x16(t_row, r);
-            const float o0 = __uint_as_float(r[0]) + sBias[128], o1 = __uint_as_float(r[1]) + sBias[129],
-                        o2 = __uint_as_float(r[2]) + sBias[130], o3 = __uint_as_float(r[3]) + sBias[131];
+            const float4 b3 = *reinterpret_cast<const float4 *>(sBias + 128);
+            const float o0 = __uint_as_float(r[0]) + b3.x, o1 = __uint_as_float(r[1]) + b3.y,
+                        o2 = __uint_as_float(r[2]) + b3.z, o3 = __uint_as_float(r[3]) + b3.w;
             if (valid) {
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (s > 0.f) v = make_float4(s * expf(fminf(o0, 15.f)), softplusf(o1), softplusf(o2), softplusf(o3));
@@ -370,6 +372,7 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
 constexpr int kVW1 = 0, kVWd = 4096, kVWc1 = 6144, kVWc2 = 10240, kVWc3 = 18432, kVWBytes = 20480;
 constexpr int kVBias = kVWBytes;                       // b1[64] bd[16] bc1[64] bc2[64] bc3[4]
 constexpr int kVSupport = kVBias + 212 * 4;
+static_assert(kVBias % 16 == 0, "biases are read as float4");
 constexpr int kVBars = kVSupport + kSupportMax * 16;
 template <int G>
 struct LayoutV {
@@ -503,7 +506,13 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
             tmem_ld_x16(t_row, r);
             float x[32];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) x[k] = __uint_as_float(r[k]) + sBias[64 + k];
+            for (int k = 0; k < 4; ++k) {
+                const float4 b = reinterpret_cast<const float4 *>(sBias + 64)[k];
+                x[4 * k] = __uint_as_float(r[4 * k]) + b.x;
+                x[4 * k + 1] = __uint_as_float(r[4 * k + 1]) + b.y;
+                x[4 * k + 2] = __uint_as_float(r[4 * k + 2]) + b.z;
+                x[4 * k + 3] = __uint_as_float(r[4 * k + 3]) + b.w;
+            }
             sigma = s * expf(fminf(x[0], 15.f));
             sh16(normalize(dv), x + 16);
 #pragma unroll
@@ -535,10 +544,11 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
             tmem_ld_x16(t_row, r);
             if (valid) {
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (s > 0.f)
-                    v = make_float4(sigma, softplusf(__uint_as_float(r[0]) + sBias[208]),
-                                    softplusf(__uint_as_float(r[1]) + sBias[209]),
-                                    softplusf(__uint_as_float(r[2]) + sBias[210]));
+                if (s > 0.f) {
+                    const float4 bc = *reinterpret_cast<const float4 *>(sBias + 208);
+                    v = make_float4(sigma, softplusf(__uint_as_float(r[0]) + bc.x),
+                                    softplusf(__uint_as_float(r[1]) + bc.y), softplusf(__uint_as_float(r[2]) + bc.z));
+                }
                 out[i] = v;
             }
         }

@@ -12,13 +12,20 @@ struct Counters {
     unsigned long long nominal;
     unsigned paths, seg, hits, shadow, evaluated, shadow_eval, retests, fault, net;
     unsigned end_miss, end_tau, end_cap;   // how paths ended: left the scene, throughput below tau, bounce cap
-    unsigned nodes;                        // BVH nodes visited
+    unsigned nodes, tris;                  // BVH nodes visited, ray-triangle tests
+    unsigned long long worst;              // (nodes << 32) | path of this thread's longest closest-hit traversal
 };
+
+// Records a closest-hit traversal of `nodes` nodes made for `path`.
+__device__ __forceinline__ void note_traversal(Counters &C, unsigned nodes, uint32_t path) {
+    const unsigned long long key = ((unsigned long long)nodes << 32) | path;
+    if (key > C.worst) C.worst = key;
+}
 
 __device__ __forceinline__ void flush_counters(unsigned long long *stats, Counters &C) {
     if (!stats) return;
     unsigned long long v[ST_COUNT] = {C.paths, C.seg, C.hits, C.shadow, C.nominal, C.evaluated, C.shadow_eval,
-                                      C.retests, C.fault, C.net, C.end_miss, C.end_tau, C.end_cap, C.nodes};
+                                      C.retests, C.fault, C.net, C.end_miss, C.end_tau, C.end_cap, C.nodes, C.tris, 0ull};
     const unsigned mask = __activemask();
 #pragma unroll
     for (int k = 0; k < ST_COUNT; ++k) {
@@ -26,10 +33,16 @@ __device__ __forceinline__ void flush_counters(unsigned long long *stats, Counte
         for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(mask, x, off);
         v[k] = x;
     }
+    unsigned long long worst = C.worst;
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(mask, worst, off);
+        if (y > worst) worst = y;
+    }
     if ((threadIdx.x & 31) == __ffs(mask) - 1) {
 #pragma unroll
         for (int k = 0; k < ST_COUNT; ++k)
-            if (v[k]) atomicAdd(stats + k, v[k]);
+            if (v[k] && k != ST_WORST) atomicAdd(stats + k, v[k]);
+        if (worst) atomicMax(stats + ST_WORST, worst);
     }
 }
 
@@ -67,9 +80,9 @@ static __device__ __noinline__ float sample_mask(const RenderParams &P, V3 pw) {
         if (!(D > 0.f)) continue;
         w = w * (1.f / D);
         Hit hs;
-        unsigned rs = 0, nv = 0;
+        unsigned rs = 0, nv = 0, nt = 0;
         bool fault = false;
-        if (bvh_trace<true>(P.B, pw, w, kNoHit, P.tmin, D, hs, rs, nv, fault)) m *= 1.f - L0.mask;
+        if (bvh_trace<true>(P.B, pw, w, kNoHit, P.tmin, D, hs, rs, nv, nt, fault)) m *= 1.f - L0.mask;
     }
     return m;
 }

@@ -25,7 +25,9 @@ __device__ void trace_path(const RenderParams &P, const float *w, uint32_t ray, 
         Hit h;
         unsigned rt = 0;
         bool fault = false;
-        bvh_trace<false>(P.B, o, d, prev, P.tmin, INFINITY, h, rt, C.nodes, fault);
+        const unsigned nodes0 = C.nodes;
+        bvh_trace<false>(P.B, o, d, prev, P.tmin, INFINITY, h, rt, C.nodes, C.tris, fault);
+        note_traversal(C, C.nodes - nodes0, (uint32_t)path);
         C.retests += rt;
         if (fault) C.fault |= 1;
         const float T0 = T[0];
@@ -58,7 +60,7 @@ __device__ void trace_path(const RenderParams &P, const float *w, uint32_t ray, 
                     Hit hs;
                     unsigned rs = 0;
                     bool f2 = false;
-                    const bool blocked = bvh_trace<true>(P.B, S.p, wl, S.id, P.tmin, D, hs, rs, C.nodes, f2);
+                    const bool blocked = bvh_trace<true>(P.B, S.p, wl, S.id, P.tmin, D, hs, rs, C.nodes, C.tris, f2);
                     C.retests += rs;
                     if (f2) C.fault |= 1;
                     if (blocked) continue;
@@ -222,7 +224,7 @@ __global__ void __launch_bounds__(128) cast_kernel(const BvhDev B, const float *
         unsigned rt = 0;
         bool fault = false;
         bvh_trace<false>(B, v3(o[3 * i], o[3 * i + 1], o[3 * i + 2]), v3(d[3 * i], d[3 * i + 1], d[3 * i + 2]),
-                         skip ? skip[i] : kNoHit, tmin, INFINITY, h, rt, C.nodes, fault);
+                         skip ? skip[i] : kNoHit, tmin, INFINITY, h, rt, C.nodes, C.tris, fault);
         out_t[i] = h.t;
         out_tri[i] = h.id;
         C.retests = rt;

@@ -73,6 +73,18 @@ __device__ __forceinline__ uint32_t warp_alloc(uint32_t *ctr, uint32_t n) {
     return base + x - n;
 }
 
+// Slots per warp of the warp-cooperative kernels (wf_gen, wf_composite,
+// wf_mask): 32 while the live slots fill every warp of the grid, fewer (a power
+// of two, down to 1) when they do not, so that each warp's serial loop over its
+// slots' jobs stays short in the late segments, where few paths are live and
+// the grid would otherwise wait on a few warps with 32 long jobs each.  Warp w
+// takes slots [w * S, w * S + S); lane l < S holds slot w * S + l.
+__device__ __forceinline__ int slots_per_warp(uint32_t live) {
+    const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+    const uint32_t need = (live + warps - 1) / warps;
+    return need <= 1 ? 1 : (int)min(32u, 1u << (32 - __clz(need - 1)));
+}
+
 // Shared-memory copies used by the sample walk: coarse occupancy bits and the
 // density-support spheres.
 constexpr int kCoarseWordsMax = 1024;   // coarse grids up to 32^3 are staged
@@ -365,7 +377,9 @@ __global__ void __launch_bounds__(kThreads) wf_cast(const WfParams W, uint32_t j
         Hit h;
         unsigned rt = 0;
         bool fault = false;
-        bvh_trace<false>(P.B, o, d, prev, P.tmin, INFINITY, h, rt, C.nodes, fault);
+        const unsigned nodes0 = C.nodes;
+        bvh_trace<false>(P.B, o, d, prev, P.tmin, INFINITY, h, rt, C.nodes, C.tris, fault);
+        note_traversal(C, C.nodes - nodes0, path);
         C.retests += rt;
         if (fault) C.fault |= 1;
         W.hit_t[tid] = h.t;
@@ -394,7 +408,8 @@ __global__ void __launch_bounds__(kThreads) wf_cast(const WfParams W, uint32_t j
                             Hit hs;
                             unsigned rs = 0;
                             bool f2 = false;
-                            const bool blocked = bvh_trace<true>(P.B, S.p, wl, S.id, P.tmin, D, hs, rs, C.nodes, f2);
+                            const bool blocked =
+                                bvh_trace<true>(P.B, S.p, wl, S.id, P.tmin, D, hs, rs, C.nodes, C.tris, f2);
                             C.retests += rs;
                             if (f2) C.fault |= 1;
                             if (!blocked) {
@@ -445,7 +460,7 @@ __global__ void __launch_bounds__(128) wf_shadow_net(const WfParams W) {
 }
 
 // Warp-cooperative sample generation: counts the samples of every job of the
-// warp's 32 slots (segment march and visible shadow rays), allocates their
+// warp's slots (segment march and visible shadow rays), allocates their
 // ranges with one atomic per warp, and writes them in order.
 // Round r > 0 regenerates only the slots that round r - 1 left pending (their
 // samples did not fit the buffer), into the emptied buffer.
@@ -455,10 +470,12 @@ __global__ void __launch_bounds__(kThreads, 8) wf_gen(const WfParams W, uint32_t
     const RenderParams &P = W.R;
     if (round > 0 && W.ctr[4 + round - 1] == 0) return;   // nothing pending: the whole grid leaves
     const WalkCtx X = stage_walk(P.F, wsm);
-    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const uint32_t live = j == 1 ? W.paths : W.ctr[cur];
-    const bool active = tid < live && (round == 0 || W.rcount[tid] == kOverflow);
+    const int S = slots_per_warp(live);
+    const uint32_t wbase = (blockIdx.x * blockDim.x + threadIdx.x) / 32u * (uint32_t)S;
+    const uint32_t tid = wbase + (uint32_t)lane;   // this lane's slot (lane < S)
+    const bool active = lane < S && tid < live && (round == 0 || W.rcount[tid] == kOverflow);
     const int K = P.n_shadow;
     Counters C = {};
     V3 o = v3(0.f, 0.f, 0.f), d = v3(0.f, 0.f, 1.f), hp = v3(0.f, 0.f, 0.f);
@@ -473,12 +490,12 @@ __global__ void __launch_bounds__(kThreads, 8) wf_gen(const WfParams W, uint32_t
         vis = __float_as_uint(h4.w);
     }
     uint32_t my_nr = 0, my_total = 0;
-    for (int src = 0; src < 32; ++src) {
+    for (int src = 0; src < S; ++src) {
         if (!__shfl_sync(0xffffffffu, (int)active, src)) continue;
         const V3 so = shfl3(o, src), sd = shfl3(d, src), sp = shfl3(hp, src);
         const float st = __shfl_sync(0xffffffffu, th, src);
         const uint32_t svis = __shfl_sync(0xffffffffu, vis, src);
-        const uint32_t src_tid = tid - lane + src;
+        const uint32_t src_tid = wbase + src;
         RunList(&rl)[2] = runs_sm[threadIdx.x >> 5][src];
         const uint32_t n_r = warp_walk(P, X, so, sd, 0.f, st, nullptr, 0, C.nominal, lane, &rl[0]);
         uint32_t n_s = 0;
@@ -504,12 +521,12 @@ __global__ void __launch_bounds__(kThreads, 8) wf_gen(const WfParams W, uint32_t
     const uint32_t base = warp_alloc(&W.ctr[2], my_total);
     const bool fits = (uint64_t)base + my_total <= (uint64_t)W.cap;
     __syncwarp();
-    for (int src = 0; src < 32; ++src) {
+    for (int src = 0; src < S; ++src) {
         if (!__shfl_sync(0xffffffffu, (int)active, src)) continue;
         const bool sfits = __shfl_sync(0xffffffffu, (int)fits, src);
         const uint32_t sbase = __shfl_sync(0xffffffffu, base, src);
         const uint32_t svis = __shfl_sync(0xffffffffu, vis, src);
-        const uint32_t src_tid = tid - lane + src;
+        const uint32_t src_tid = wbase + src;
         if (!sfits) {
             if (lane == src) {
                 W.rcount[tid] = kOverflow;
@@ -615,10 +632,12 @@ __device__ __forceinline__ float warp_sum(float x) {
 __global__ void __launch_bounds__(kThreads, 8) wf_composite(const WfParams W, int cur, int round) {
     const RenderParams &P = W.R;
     if (round > 0 && W.ctr[4 + round - 1] == 0) return;
-    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const uint32_t live = W.ctr[cur];
-    bool active = tid < live;
+    const int S = slots_per_warp(live);
+    const uint32_t wbase = (blockIdx.x * blockDim.x + threadIdx.x) / 32u * (uint32_t)S;
+    const uint32_t tid = wbase + (uint32_t)lane;   // this lane's slot (lane < S)
+    bool active = lane < S && tid < live;
     const int K = P.n_shadow;
     uint32_t rc = kOverflow, r0 = 0;
     float tmax = 0.f;
@@ -632,10 +651,10 @@ __global__ void __launch_bounds__(kThreads, 8) wf_composite(const WfParams W, in
         diffuse = __float_as_uint(W.hp[tid].w) != 0u;   // some unblocked shadow ray from a diffuse hit
         if (active) W.rcount[tid] = kDone;   // read below from the registers only
     }
-    for (int src = 0; src < 32; ++src) {
+    for (int src = 0; src < S; ++src) {
         if (!__shfl_sync(0xffffffffu, (int)active, src)) continue;
         const uint32_t src_rc = __shfl_sync(0xffffffffu, rc, src);
-        const uint32_t src_tid = tid - lane + src;
+        const uint32_t src_tid = wbase + src;
         {
             const uint32_t src_r0 = __shfl_sync(0xffffffffu, r0, src);
             const float tmax0 = __shfl_sync(0xffffffffu, tmax, src);
@@ -664,19 +683,21 @@ __global__ void __launch_bounds__(kThreads, 8) wf_composite(const WfParams W, in
 
 // Shadow mask of Sec. 3.1 on the segment samples (radiance jobs only): the
 // radiance of every sample with sigma > 0 is scaled by m(p_t).  One warp walks
-// the samples of each of its 32 slots' jobs.
+// the samples of each of its slots' jobs.
 __global__ void __launch_bounds__(kThreads) wf_mask(const WfParams W, int cur, int round) {
     const RenderParams &P = W.R;
     if (round > 0 && W.ctr[4 + round - 1] == 0) return;
-    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    const bool active = tid < W.ctr[cur];
+    const uint32_t live = W.ctr[cur];
+    const int S = slots_per_warp(live);
+    const uint32_t tid = (blockIdx.x * blockDim.x + threadIdx.x) / 32u * (uint32_t)S + (uint32_t)lane;
+    const bool active = lane < S && tid < live;
     uint32_t rc = kOverflow, r0 = 0;
     if (active) {
         rc = W.rcount[tid];
         r0 = W.rstart[tid];
     }
-    for (int src = 0; src < 32; ++src) {
+    for (int src = 0; src < S; ++src) {
         const uint32_t src_rc = __shfl_sync(0xffffffffu, rc, src);
         const uint32_t src_r0 = __shfl_sync(0xffffffffu, r0, src);
         if (!__shfl_sync(0xffffffffu, (int)active, src) || src_rc == kOverflow || src_rc == kDone) continue;

@@ -445,6 +445,7 @@ constexpr int kLpW1 = 0, kLpW2 = 4096, kLpW3 = 12288, kLpW4 = 20480, kLpBytes = 
 constexpr int kTcGroups = 4;   // 128-ray tiles in flight per CTA (256 TMEM columns: two CTAs per SM)
 constexpr int kTcBias = kLpBytes, kTcBars = kTcBias + (3 * kSnetW + 4) * 4, kTcSlot = kTcBars + 8 * kTcGroups,
               kTcA = (kTcSlot + 8 + 127) / 128 * 128, kTcBytes = kTcA + kTcGroups * 16384;
+static_assert(kTcBias % 16 == 0, "biases are read as float4");
 
 // byte offset of element (r, k) of an R x K operand in the canonical K-major layout
 __device__ __forceinline__ uint32_t umma_off(int r, int k, int K) {

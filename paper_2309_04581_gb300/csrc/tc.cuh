@@ -121,17 +121,23 @@ __device__ __forceinline__ void store_chunk(uint8_t *base, int row, int chunk, i
     *reinterpret_cast<uint4 *>(base + (row >> 3) * sbo + chunk * 128 + (row & 7) * 16) = v;
 }
 
+// ReLU(accumulator + bias) of 32 columns to four 16-byte chunks of A.  `bias`
+// is a 16-byte aligned shared-memory array: every lane reads the same
+// addresses, as 128-bit loads (8 instead of 32 shared-memory wavefronts).
 template <bool kBF16>
 __device__ __forceinline__ void relu_bias_store(const uint32_t (&r)[32], const float *bias, uint8_t *A, int row,
                                                 int chunk0) {
+    const float4 *b4 = reinterpret_cast<const float4 *>(bias);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
+        const float4 bl = b4[2 * c], bh = b4[2 * c + 1];
+        const float b[8] = {bl.x, bl.y, bl.z, bl.w, bh.x, bh.y, bh.z, bh.w};
         uint32_t w[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int k = 8 * c + 2 * q;
-            w[q] = pack2<kBF16>(fmaxf(__uint_as_float(r[k]) + bias[k], 0.f),
-                                fmaxf(__uint_as_float(r[k + 1]) + bias[k + 1], 0.f));
+            w[q] = pack2<kBF16>(fmaxf(__uint_as_float(r[k]) + b[2 * q], 0.f),
+                                fmaxf(__uint_as_float(r[k + 1]) + b[2 * q + 1], 0.f));
         }
         store_chunk(A, row, chunk0 + c, 1024, make_uint4(w[0], w[1], w[2], w[3]));
     }

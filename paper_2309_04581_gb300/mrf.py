@@ -109,7 +109,8 @@ class mrf_stats(C.Structure):
                 ("shadow_rays", C.c_uint64), ("samples_nominal", C.c_uint64), ("samples_evaluated", C.c_uint64),
                 ("shadow_samples_evaluated", C.c_uint64), ("fp64_retests", C.c_uint64), ("status", C.c_uint64),
                 ("shadow_net_evals", C.c_uint64), ("ended_miss", C.c_uint64), ("ended_tau", C.c_uint64),
-                ("ended_cap", C.c_uint64), ("bvh_nodes", C.c_uint64)]
+                ("ended_cap", C.c_uint64), ("bvh_nodes", C.c_uint64),
+                ("bvh_tri_tests", C.c_uint64), ("bvh_worst_nodes", C.c_uint64), ("bvh_worst_path", C.c_uint64)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

@@ -206,6 +206,21 @@ def test_config2_small_full_image(M, orc, torch_cuda):
     assert abs(st["shadow_rays"] - ref["counts"]["shadow_rays"]) <= (~ok).sum() * sc.opts.max_bounces
 
 
+def test_traversal_counts_agree_between_engines(M, torch_cuda):
+    """The megakernel and the wavefront engine trace the same closest-hit and
+    shadow rays with the same FP32 arithmetic, so they visit the same BVH nodes
+    and make the same ray-triangle tests; every surface hit needs a test, and a
+    visited node holds at most two leaves of at most 4 triangles."""
+    sc = S.config2(48, 40)
+    a = _render(M, sc, engine=M.MRF_ENGINE_MEGAKERNEL)["stats"]
+    b = _render(M, sc, engine=M.MRF_ENGINE_WAVEFRONT)["stats"]
+    for k in ("bvh_nodes", "bvh_tri_tests", "segments", "surface_hits", "shadow_rays", "bvh_worst_nodes",
+              "bvh_worst_path"):
+        assert a[k] == b[k], (k, a[k], b[k])
+    assert a["surface_hits"] <= a["bvh_tri_tests"] <= 8 * a["bvh_nodes"]
+    assert 1 <= a["bvh_worst_nodes"] <= a["bvh_nodes"] and a["bvh_worst_path"] < a["paths"]
+
+
 def test_config2_full_size_sampled_pixels(M, orc, torch_cuda):
     # the 800x800 benchmark workload, rendered whole on the GPU in the bench's
     # launch configuration; every 16th row and column is recomputed by the oracle
