@@ -165,7 +165,7 @@ def measured_traffic(kernel_files, summary: str):
         text = open(os.path.join(ROOT, "profiles", summary)).read()
     except OSError:
         return None
-    m = re.search(r"sha256 ([0-9a-f]{64})", text)
+    m = re.search(r"sha256\D*?([0-9a-f]{64})", text)
     v = re.search(r"traffic_bytes_per_launch: (\d+)", text)
     if not m or not v or m.group(1) != src:
         return None

@@ -208,6 +208,10 @@ inline void timer_end(KernelTimer *t, cudaStream_t s) { if (t) t->end(s); }
 
 // launchers (render_mega.cu)
 cudaError_t launch_render_megakernel(const RenderParams &P, cudaStream_t s, KernelTimer *timer = nullptr);
+// Field kernels: point i is pts[stride * i .. + 2].  With stride 4 the fourth
+// float is the quadrature interval delta of the sample and out[i].x is its
+// optical depth sigma * delta (FP32 product); with stride 3, out[i].x is sigma.
+// out[i].yzw is the radiance.
 cudaError_t launch_field_simt(const FieldDev &F, const float *pts, int stride, const uint32_t *n_dev, uint32_t n_host,
                               float4 *out, int grid, cudaStream_t s, const float4 *dirs = nullptr);
 // field_tc.cu

@@ -256,9 +256,15 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
         const uint32_t i = tile * 128u + gt;
         const bool valid = i < n;
         V3 p = v3(0.f, 0.f, 0.f);
-        float s = 0.f;
+        float s = 0.f, dl = 1.f;   // support, interval length (stride 4)
         if (valid) {
-            p = v3(pts[(size_t)stride * i], pts[(size_t)stride * i + 1], pts[(size_t)stride * i + 2]);
+            if (stride == 4) {
+                const float4 q = reinterpret_cast<const float4 *>(pts)[i];
+                p = v3(q.x, q.y, q.z);
+                dl = q.w;
+            } else {
+                p = v3(pts[(size_t)stride * i], pts[(size_t)stride * i + 1], pts[(size_t)stride * i + 2]);
+            }
             if (F.n_support) {
                 for (int k = 0; k < F.n_support; ++k) {
                     const float4 c = sup[k];
@@ -347,7 +353,8 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
                         o2 = __uint_as_float(r[2]) + b3.z, o3 = __uint_as_float(r[3]) + b3.w;
             if (valid) {
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (s > 0.f) v = make_float4(s * expf(fminf(o0, 15.f)), softplusf(o1), softplusf(o2), softplusf(o3));
+                if (s > 0.f)
+                    v = make_float4(s * expf(fminf(o0, 15.f)) * dl, softplusf(o1), softplusf(o2), softplusf(o3));
                 out[i] = v;
             }
         }
@@ -462,9 +469,15 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
         const uint32_t i = tile * 128u + gt;
         const bool valid = i < n;
         V3 p = v3(0.f, 0.f, 0.f), dv = v3(0.f, 0.f, 1.f);
-        float s = 0.f;
+        float s = 0.f, dl = 1.f;   // support, interval length (stride 4)
         if (valid) {
-            p = v3(pts[(size_t)stride * i], pts[(size_t)stride * i + 1], pts[(size_t)stride * i + 2]);
+            if (stride == 4) {
+                const float4 q = reinterpret_cast<const float4 *>(pts)[i];
+                p = v3(q.x, q.y, q.z);
+                dl = q.w;
+            } else {
+                p = v3(pts[(size_t)stride * i], pts[(size_t)stride * i + 1], pts[(size_t)stride * i + 2]);
+            }
             if (dirs) {
                 const float4 q = dirs[i];
                 dv = v3(q.x, q.y, q.z);
@@ -546,7 +559,7 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (s > 0.f) {
                     const float4 bc = *reinterpret_cast<const float4 *>(sBias + 208);
-                    v = make_float4(sigma, softplusf(__uint_as_float(r[0]) + bc.x),
+                    v = make_float4(sigma * dl, softplusf(__uint_as_float(r[0]) + bc.x),
                                     softplusf(__uint_as_float(r[1]) + bc.y), softplusf(__uint_as_float(r[2]) + bc.z));
                 }
                 out[i] = v;

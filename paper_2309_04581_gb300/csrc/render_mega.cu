@@ -153,13 +153,14 @@ __global__ void __launch_bounds__(128) field_simt_kernel(const FieldDev F, const
     const uint32_t n = n_dev ? min(*n_dev, n_host) : n_host;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const V3 p = v3(pts[(size_t)stride * i], pts[(size_t)stride * i + 1], pts[(size_t)stride * i + 2]);
+        const float dl = stride == 4 ? pts[(size_t)stride * i + 3] : 1.f;
         float rgb[3] = {0.f, 0.f, 0.f}, sigma = 0.f;
         if (inside_field_box(F, p)) {
             bool ev;
             const float4 dv = dirs ? dirs[i] : make_float4(0.f, 0.f, 1.f, 0.f);
             sigma = field_at<true>(F, w, p, v3(dv.x, dv.y, dv.z), rgb, ev);
         }
-        out[i] = make_float4(sigma, rgb[0], rgb[1], rgb[2]);
+        out[i] = make_float4(sigma * dl, rgb[0], rgb[1], rgb[2]);
     }
 }
 

@@ -53,7 +53,7 @@ struct WfParams {
     uint32_t *squeue;               // shadow rays answered by the network: slot * n_shadow + q
     float4 *samp;                   // sample position (xyz) and interval length (w)
     float4 *sview;                  // view direction (field frame) of each radiance sample (view-dependent fields)
-    float4 *fout;                   // sigma, r, g, b per sample
+    float4 *fout;                   // sigma * delta, r, g, b per sample
     uint32_t cap;                   // sample capacity
 };
 
@@ -73,17 +73,33 @@ __device__ __forceinline__ uint32_t warp_alloc(uint32_t *ctr, uint32_t n) {
     return base + x - n;
 }
 
-// Slots per warp of the warp-cooperative kernels (wf_gen, wf_composite,
-// wf_mask): 32 while the live slots fill every warp of the grid, fewer (a power
-// of two, down to 1) when they do not, so that each warp's serial loop over its
-// slots' jobs stays short in the late segments, where few paths are live and
-// the grid would otherwise wait on a few warps with 32 long jobs each.  Warp w
-// takes slots [w * S, w * S + S); lane l < S holds slot w * S + l.
-__device__ __forceinline__ int slots_per_warp(uint32_t live) {
-    const uint32_t warps = gridDim.x * (blockDim.x >> 5);
-    const uint32_t need = (live + warps - 1) / warps;
+// Work distribution of the warp-cooperative kernels (wf_gen, wf_mask,
+// wf_composite): a warp takes a chunk of S consecutive slots from a per-round
+// work counter, walks their jobs one after another (lane l < S holds slot
+// base + l) and takes the next chunk until none is left.  S is a power of two,
+// at most 32, sized for about four chunks per resident warp: job lengths vary
+// by orders of magnitude (a ray through the field against one that hits the
+// floor at once), and a static split left SMs idle for half of the first
+// segment and waiting on a few warps with 32 long jobs in the late ones.
+__device__ __forceinline__ int chunk_slots(uint32_t live) {
+    const uint32_t warps = min(gridDim.x * (blockDim.x >> 5), 152u * 32u);
+    const uint32_t need = (live + 4u * warps - 1u) / (4u * warps);
     return need <= 1 ? 1 : (int)min(32u, 1u << (32 - __clz(need - 1)));
 }
+
+// First slot of the warp's next chunk (>= live: no work left).
+__device__ __forceinline__ uint32_t next_chunk(uint32_t *work, int S, int lane) {
+    uint32_t b = 0;
+    if (lane == 0) b = atomicAdd(work, (uint32_t)S);
+    return __shfl_sync(0xffffffffu, b, 0);
+}
+
+// Counters of the engine (W.ctr): [0], [1] live slots of the two queues,
+// [2] generated samples, [3] network shadow rays, then per generation round r
+// a block of four: slots left pending, and the work counters of wf_gen,
+// wf_mask and wf_composite.  One memset per segment clears [2, 4 + 4 * rounds).
+__device__ __forceinline__ uint32_t *pending_ctr(const WfParams &W, int r) { return W.ctr + 4 + 4 * r; }
+__device__ __forceinline__ uint32_t *work_ctr(const WfParams &W, int r, int k) { return W.ctr + 5 + 4 * r + k; }
 
 // Shared-memory copies used by the sample walk: coarse occupancy bits and the
 // density-support spheres.
@@ -111,16 +127,6 @@ __device__ __forceinline__ WalkCtx stage_walk(const FieldDev &F, WalkSmem &sm) {
         for (int i = threadIdx.x; i < F.n_support; i += blockDim.x) sm.support[i] = __ldg(F.support + i);
     __syncthreads();
     return WalkCtx{coarse_fits ? sm.coarse : nullptr, sup_fits ? sm.support : F.support};
-}
-
-__device__ __forceinline__ float support_at(const FieldDev &F, const float4 *sup, V3 p) {
-    float s = 0.f;
-    for (int k = 0; k < F.n_support; ++k) {
-        const float4 c = sup[k];
-        const float dx = p.x - c.x, dy = p.y - c.y, dz = p.z - c.z;
-        s = fmaxf(s, 1.0f - (dx * dx + dy * dy + dz * dz) * c.w);
-    }
-    return s;
 }
 
 // exit parameter of the cell c of a grid with cell width `cell` along the ray
@@ -468,105 +474,107 @@ __global__ void __launch_bounds__(kThreads, 8) wf_gen(const WfParams W, uint32_t
     __shared__ WalkSmem wsm;
     __shared__ RunList runs_sm[kThreads / 32][32][2];   // per warp, per slot: segment job, first shadow job
     const RenderParams &P = W.R;
-    if (round > 0 && W.ctr[4 + round - 1] == 0) return;   // nothing pending: the whole grid leaves
+    if (round > 0 && *pending_ctr(W, round - 1) == 0) return;   // nothing pending: the whole grid leaves
     const WalkCtx X = stage_walk(P.F, wsm);
     const int lane = threadIdx.x & 31;
     const uint32_t live = j == 1 ? W.paths : W.ctr[cur];
-    const int S = slots_per_warp(live);
-    const uint32_t wbase = (blockIdx.x * blockDim.x + threadIdx.x) / 32u * (uint32_t)S;
-    const uint32_t tid = wbase + (uint32_t)lane;   // this lane's slot (lane < S)
-    const bool active = lane < S && tid < live && (round == 0 || W.rcount[tid] == kOverflow);
+    const int S = chunk_slots(live);
     const int K = P.n_shadow;
     Counters C = {};
-    V3 o = v3(0.f, 0.f, 0.f), d = v3(0.f, 0.f, 1.f), hp = v3(0.f, 0.f, 0.f);
-    float th = 0.f;
-    uint32_t vis = 0;   // unblocked shadow rays of the slot
-    if (active) {
-        const float4 qo = W.qo[cur][tid], qd = W.qd[cur][tid], h4 = W.hp[tid];
-        o = v3(qo.x, qo.y, qo.z);
-        d = v3(qd.x, qd.y, qd.z);
-        th = W.hit_t[tid];
-        hp = v3(h4.x, h4.y, h4.z);
-        vis = __float_as_uint(h4.w);
-    }
-    uint32_t my_nr = 0, my_total = 0;
-    for (int src = 0; src < S; ++src) {
-        if (!__shfl_sync(0xffffffffu, (int)active, src)) continue;
-        const V3 so = shfl3(o, src), sd = shfl3(d, src), sp = shfl3(hp, src);
-        const float st = __shfl_sync(0xffffffffu, th, src);
-        const uint32_t svis = __shfl_sync(0xffffffffu, vis, src);
-        const uint32_t src_tid = wbase + src;
-        RunList(&rl)[2] = runs_sm[threadIdx.x >> 5][src];
-        const uint32_t n_r = warp_walk(P, X, so, sd, 0.f, st, nullptr, 0, C.nominal, lane, &rl[0]);
-        uint32_t n_s = 0;
-        bool first = true;   // the first unblocked shadow ray records its runs
-        for (int q = 0; svis && q < K; ++q) {
-            const size_t idx = (size_t)src_tid * K + q;
-            if (W.sw[idx].w != 1.f) continue;   // marched shadow rays only
-            const float4 sh = W.sdir[idx];
-            const uint32_t ns = warp_walk(P, X, sp, v3(sh.x, sh.y, sh.z), 0.f, sh.w, nullptr, 0, C.nominal, lane,
-                                          first ? &rl[1] : nullptr);
-            first = false;
-            if (lane == src) W.scount[idx] = ns;
-            n_s += ns;
+    for (uint32_t wbase; (wbase = next_chunk(work_ctr(W, round, 0), S, lane)) < live;) {
+        const uint32_t tid = wbase + (uint32_t)lane;   // this lane's slot (lane < S)
+        const bool active = lane < S && tid < live && (round == 0 || W.rcount[tid] == kOverflow);
+        V3 o = v3(0.f, 0.f, 0.f), d = v3(0.f, 0.f, 1.f), hp = v3(0.f, 0.f, 0.f);
+        float th = 0.f;
+        uint32_t vis = 0;   // unblocked shadow rays of the slot
+        if (active) {
+            const float4 qo = W.qo[cur][tid], qd = W.qd[cur][tid], h4 = W.hp[tid];
+            o = v3(qo.x, qo.y, qo.z);
+            d = v3(qd.x, qd.y, qd.z);
+            th = W.hit_t[tid];
+            hp = v3(h4.x, h4.y, h4.z);
+            vis = __float_as_uint(h4.w);
         }
-        if (lane == src) {
-            W.rcount[tid] = n_r;
-            my_nr = n_r;
-            my_total = n_r + n_s;
-            C.evaluated += n_r;
-            C.shadow_eval += n_s;
-        }
-    }
-    const uint32_t base = warp_alloc(&W.ctr[2], my_total);
-    const bool fits = (uint64_t)base + my_total <= (uint64_t)W.cap;
-    __syncwarp();
-    for (int src = 0; src < S; ++src) {
-        if (!__shfl_sync(0xffffffffu, (int)active, src)) continue;
-        const bool sfits = __shfl_sync(0xffffffffu, (int)fits, src);
-        const uint32_t sbase = __shfl_sync(0xffffffffu, base, src);
-        const uint32_t svis = __shfl_sync(0xffffffffu, vis, src);
-        const uint32_t src_tid = wbase + src;
-        if (!sfits) {
-            if (lane == src) {
-                W.rcount[tid] = kOverflow;
-                for (int q = 0; vis && q < K; ++q)
-                    if (W.sw[(size_t)tid * K + q].w == 1.f) W.scount[(size_t)tid * K + q] = kOverflow;
-                atomicAdd(&W.ctr[4 + round], 1u);
+        uint32_t my_nr = 0, my_total = 0;
+        for (int src = 0; src < S; ++src) {
+            if (!__shfl_sync(0xffffffffu, (int)active, src)) continue;
+            const V3 so = shfl3(o, src), sd = shfl3(d, src), sp = shfl3(hp, src);
+            const float st = __shfl_sync(0xffffffffu, th, src);
+            const uint32_t svis = __shfl_sync(0xffffffffu, vis, src);
+            const uint32_t src_tid = wbase + src;
+            RunList(&rl)[2] = runs_sm[threadIdx.x >> 5][src];
+            const uint32_t n_r = warp_walk(P, X, so, sd, 0.f, st, nullptr, 0, C.nominal, lane, &rl[0]);
+            uint32_t n_s = 0;
+            bool first = true;   // the first unblocked shadow ray records its runs
+            for (int q = 0; svis && q < K; ++q) {
+                const size_t idx = (size_t)src_tid * K + q;
+                if (W.sw[idx].w != 1.f) continue;   // marched shadow rays only
+                const float4 sh = W.sdir[idx];
+                const uint32_t ns = warp_walk(P, X, sp, v3(sh.x, sh.y, sh.z), 0.f, sh.w, nullptr, 0, C.nominal, lane,
+                                              first ? &rl[1] : nullptr);
+                first = false;
+                if (lane == src) W.scount[idx] = ns;
+                n_s += ns;
             }
-            continue;
+            if (lane == src) {
+                W.rcount[tid] = n_r;
+                my_nr = n_r;
+                my_total = n_r + n_s;
+                C.evaluated += n_r;
+                C.shadow_eval += n_s;
+            }
         }
-        const V3 so = shfl3(o, src), sd = shfl3(d, src), sp = shfl3(hp, src);
-        const float st = __shfl_sync(0xffffffffu, th, src);
-        unsigned long long dummy = 0;
-        uint32_t k = sbase;
-        const uint32_t nr = __shfl_sync(0xffffffffu, my_nr, src);
-        const RunList(&rl)[2] = runs_sm[threadIdx.x >> 5][src];
-        if (rl[0].n <= kRunsPerJob)
-            write_runs(P, so, sd, 0.f, st, rl[0], W.samp + k, nr, lane);
-        else
-            warp_walk(P, X, so, sd, 0.f, st, W.samp + k, nr, dummy, lane, nullptr);
-        if (P.F.view_dep) {   // the colour network needs each radiance sample's view direction
-            V3 ol = so, dl = sd;
-            to_field_frame(P.F, ol, dl);
-            for (uint32_t i = lane; i < nr; i += 32) W.sview[k + i] = make_float4(dl.x, dl.y, dl.z, 0.f);
-        }
-        k += nr;
-        if (lane == src) W.rstart[tid] = sbase;
-        bool first = true;
-        for (int q = 0; svis && q < K; ++q) {
-            const size_t idx = (size_t)src_tid * K + q;
-            if (W.sw[idx].w != 1.f) continue;
-            const float4 sh = W.sdir[idx];
-            const uint32_t ns = W.scount[idx];
-            if (lane == src) W.sstart[idx] = k;
-            if (first && rl[1].n <= kRunsPerJob)
-                write_runs(P, sp, v3(sh.x, sh.y, sh.z), 0.f, sh.w, rl[1], W.samp + k, ns, lane);
+        const uint32_t base = warp_alloc(&W.ctr[2], my_total);
+        const bool fits = (uint64_t)base + my_total <= (uint64_t)W.cap;
+        __syncwarp();
+        for (int src = 0; src < S; ++src) {
+            if (!__shfl_sync(0xffffffffu, (int)active, src)) continue;
+            const bool sfits = __shfl_sync(0xffffffffu, (int)fits, src);
+            const uint32_t sbase = __shfl_sync(0xffffffffu, base, src);
+            const uint32_t svis = __shfl_sync(0xffffffffu, vis, src);
+            const uint32_t src_tid = wbase + src;
+            if (!sfits) {
+                if (lane == src) {
+                    W.rcount[tid] = kOverflow;
+                    for (int q = 0; vis && q < K; ++q)
+                        if (W.sw[(size_t)tid * K + q].w == 1.f) W.scount[(size_t)tid * K + q] = kOverflow;
+                    atomicAdd(pending_ctr(W, round), 1u);
+                }
+                continue;
+            }
+            const V3 so = shfl3(o, src), sd = shfl3(d, src), sp = shfl3(hp, src);
+            const float st = __shfl_sync(0xffffffffu, th, src);
+            unsigned long long dummy = 0;
+            uint32_t k = sbase;
+            const uint32_t nr = __shfl_sync(0xffffffffu, my_nr, src);
+            const RunList(&rl)[2] = runs_sm[threadIdx.x >> 5][src];
+            if (rl[0].n <= kRunsPerJob)
+                write_runs(P, so, sd, 0.f, st, rl[0], W.samp + k, nr, lane);
             else
-                warp_walk(P, X, sp, v3(sh.x, sh.y, sh.z), 0.f, sh.w, W.samp + k, ns, dummy, lane, nullptr);
-            first = false;
-            k += ns;
+                warp_walk(P, X, so, sd, 0.f, st, W.samp + k, nr, dummy, lane, nullptr);
+            if (P.F.view_dep) {   // the colour network needs each radiance sample's view direction
+                V3 ol = so, dl = sd;
+                to_field_frame(P.F, ol, dl);
+                for (uint32_t i = lane; i < nr; i += 32) W.sview[k + i] = make_float4(dl.x, dl.y, dl.z, 0.f);
+            }
+            k += nr;
+            if (lane == src) W.rstart[tid] = sbase;
+            bool first = true;
+            for (int q = 0; svis && q < K; ++q) {
+                const size_t idx = (size_t)src_tid * K + q;
+                if (W.sw[idx].w != 1.f) continue;
+                const float4 sh = W.sdir[idx];
+                const uint32_t ns = W.scount[idx];
+                if (lane == src) W.sstart[idx] = k;
+                if (first && rl[1].n <= kRunsPerJob)
+                    write_runs(P, sp, v3(sh.x, sh.y, sh.z), 0.f, sh.w, rl[1], W.samp + k, ns, lane);
+                else
+                    warp_walk(P, X, sp, v3(sh.x, sh.y, sh.z), 0.f, sh.w, W.samp + k, ns, dummy, lane, nullptr);
+                first = false;
+                k += ns;
+            }
         }
+        __syncwarp();   // runs_sm is rewritten by the next chunk
     }
     if (round > 0) C.evaluated = C.shadow_eval = 0, C.nominal = 0;   // counted by round 0
     flush_counters(P.stats, C);
@@ -591,7 +599,7 @@ __device__ __forceinline__ void warp_composite(const WfParams &W, uint32_t start
         if (v) {
             const uint32_t k = start + i0 + lane;
             f = W.fout[k];
-            x = f.x * W.samp[k].w;
+            x = f.x;   // sigma * delta, from the field kernel
         }
         float sc = x;
 #pragma unroll
@@ -631,52 +639,53 @@ __device__ __forceinline__ float warp_sum(float x) {
 // composited slots are marked done so that later rounds pass them by.
 __global__ void __launch_bounds__(kThreads, 8) wf_composite(const WfParams W, int cur, int round) {
     const RenderParams &P = W.R;
-    if (round > 0 && W.ctr[4 + round - 1] == 0) return;
+    if (round > 0 && *pending_ctr(W, round - 1) == 0) return;
     const int lane = threadIdx.x & 31;
     const uint32_t live = W.ctr[cur];
-    const int S = slots_per_warp(live);
-    const uint32_t wbase = (blockIdx.x * blockDim.x + threadIdx.x) / 32u * (uint32_t)S;
-    const uint32_t tid = wbase + (uint32_t)lane;   // this lane's slot (lane < S)
-    bool active = lane < S && tid < live;
-    const int K = P.n_shadow;
-    uint32_t rc = kOverflow, r0 = 0;
-    float tmax = 0.f;
-    bool diffuse = false;
-    if (active) {
-        rc = W.rcount[tid];
-        active = rc != kOverflow && rc != kDone;   // generated in this round
-        r0 = W.rstart[tid];
-        const float4 qT = W.qT[cur][tid];
-        tmax = fmaxf(qT.x, fmaxf(qT.y, qT.z));
-        diffuse = __float_as_uint(W.hp[tid].w) != 0u;   // some unblocked shadow ray from a diffuse hit
-        if (active) W.rcount[tid] = kDone;   // read below from the registers only
-    }
-    for (int src = 0; src < S; ++src) {
-        if (!__shfl_sync(0xffffffffu, (int)active, src)) continue;
-        const uint32_t src_rc = __shfl_sync(0xffffffffu, rc, src);
-        const uint32_t src_tid = wbase + src;
-        {
-            const uint32_t src_r0 = __shfl_sync(0xffffffffu, r0, src);
-            const float tmax0 = __shfl_sync(0xffffffffu, tmax, src);
-            float lr, lg, lb, dep;
-            bool stp;
-            warp_composite(W, src_r0, src_rc, tmax0, P.tau, lane, lr, lg, lb, dep, stp);
-            lr = warp_sum(lr);
-            lg = warp_sum(lg);
-            lb = warp_sum(lb);
-            if (lane == 0) W.comp[src_tid] = make_float4(lr, lg, lb, stp ? -dep - 1.f : dep);
+    const int S = chunk_slots(live);
+    for (uint32_t wbase; (wbase = next_chunk(work_ctr(W, round, 2), S, lane)) < live;) {
+        const uint32_t tid = wbase + (uint32_t)lane;   // this lane's slot (lane < S)
+        bool active = lane < S && tid < live;
+        const int K = P.n_shadow;
+        uint32_t rc = kOverflow, r0 = 0;
+        float tmax = 0.f;
+        bool diffuse = false;
+        if (active) {
+            rc = W.rcount[tid];
+            active = rc != kOverflow && rc != kDone;   // generated in this round
+            r0 = W.rstart[tid];
+            const float4 qT = W.qT[cur][tid];
+            tmax = fmaxf(qT.x, fmaxf(qT.y, qT.z));
+            diffuse = __float_as_uint(W.hp[tid].w) != 0u;   // some unblocked shadow ray from a diffuse hit
+            if (active) W.rcount[tid] = kDone;   // read below from the registers only
         }
-        if (!__shfl_sync(0xffffffffu, (int)diffuse, src)) continue;
-        for (int q = 0; q < K; ++q) {
-            const size_t idx = (size_t)src_tid * K + q;
-            if (W.sw[idx].w != 1.f) continue;
-            const uint32_t sc = W.scount[idx];
-            if (sc == kOverflow) continue;
-            const uint32_t s0 = W.sstart[idx];
-            float dep = 0.f;
-            for (uint32_t i0 = lane; i0 < sc; i0 += 32) dep = fmaf(W.fout[s0 + i0].x, W.samp[s0 + i0].w, dep);
-            dep = warp_sum(dep);
-            if (lane == 0) W.sdepth[idx] = dep;
+        for (int src = 0; src < S; ++src) {
+            if (!__shfl_sync(0xffffffffu, (int)active, src)) continue;
+            const uint32_t src_rc = __shfl_sync(0xffffffffu, rc, src);
+            const uint32_t src_tid = wbase + src;
+            {
+                const uint32_t src_r0 = __shfl_sync(0xffffffffu, r0, src);
+                const float tmax0 = __shfl_sync(0xffffffffu, tmax, src);
+                float lr, lg, lb, dep;
+                bool stp;
+                warp_composite(W, src_r0, src_rc, tmax0, P.tau, lane, lr, lg, lb, dep, stp);
+                lr = warp_sum(lr);
+                lg = warp_sum(lg);
+                lb = warp_sum(lb);
+                if (lane == 0) W.comp[src_tid] = make_float4(lr, lg, lb, stp ? -dep - 1.f : dep);
+            }
+            if (!__shfl_sync(0xffffffffu, (int)diffuse, src)) continue;
+            for (int q = 0; q < K; ++q) {
+                const size_t idx = (size_t)src_tid * K + q;
+                if (W.sw[idx].w != 1.f) continue;
+                const uint32_t sc = W.scount[idx];
+                if (sc == kOverflow) continue;
+                const uint32_t s0 = W.sstart[idx];
+                float dep = 0.f;
+                for (uint32_t i0 = lane; i0 < sc; i0 += 32) dep += W.fout[s0 + i0].x;
+                dep = warp_sum(dep);
+                if (lane == 0) W.sdepth[idx] = dep;
+            }
         }
     }
 }
@@ -686,31 +695,33 @@ __global__ void __launch_bounds__(kThreads, 8) wf_composite(const WfParams W, in
 // the samples of each of its slots' jobs.
 __global__ void __launch_bounds__(kThreads) wf_mask(const WfParams W, int cur, int round) {
     const RenderParams &P = W.R;
-    if (round > 0 && W.ctr[4 + round - 1] == 0) return;
+    if (round > 0 && *pending_ctr(W, round - 1) == 0) return;
     const int lane = threadIdx.x & 31;
     const uint32_t live = W.ctr[cur];
-    const int S = slots_per_warp(live);
-    const uint32_t tid = (blockIdx.x * blockDim.x + threadIdx.x) / 32u * (uint32_t)S + (uint32_t)lane;
-    const bool active = lane < S && tid < live;
-    uint32_t rc = kOverflow, r0 = 0;
-    if (active) {
-        rc = W.rcount[tid];
-        r0 = W.rstart[tid];
-    }
-    for (int src = 0; src < S; ++src) {
-        const uint32_t src_rc = __shfl_sync(0xffffffffu, rc, src);
-        const uint32_t src_r0 = __shfl_sync(0xffffffffu, r0, src);
-        if (!__shfl_sync(0xffffffffu, (int)active, src) || src_rc == kOverflow || src_rc == kDone) continue;
-        for (uint32_t i = lane; i < src_rc; i += 32) {
-            float4 f = W.fout[src_r0 + i];
-            if (!(f.x > 0.f)) continue;
-            const float4 q = W.samp[src_r0 + i];
-            const float m = sample_mask(P, field_to_world(P.F, v3(q.x, q.y, q.z)));
-            if (m != 1.f) {
-                f.y *= m;
-                f.z *= m;
-                f.w *= m;
-                W.fout[src_r0 + i] = f;
+    const int S = chunk_slots(live);
+    for (uint32_t wbase; (wbase = next_chunk(work_ctr(W, round, 1), S, lane)) < live;) {
+        const uint32_t tid = wbase + (uint32_t)lane;   // this lane's slot (lane < S)
+        const bool active = lane < S && tid < live;
+        uint32_t rc = kOverflow, r0 = 0;
+        if (active) {
+            rc = W.rcount[tid];
+            r0 = W.rstart[tid];
+        }
+        for (int src = 0; src < S; ++src) {
+            const uint32_t src_rc = __shfl_sync(0xffffffffu, rc, src);
+            const uint32_t src_r0 = __shfl_sync(0xffffffffu, r0, src);
+            if (!__shfl_sync(0xffffffffu, (int)active, src) || src_rc == kOverflow || src_rc == kDone) continue;
+            for (uint32_t i = lane; i < src_rc; i += 32) {
+                float4 f = W.fout[src_r0 + i];
+                if (!(f.x > 0.f)) continue;
+                const float4 q = W.samp[src_r0 + i];
+                const float m = sample_mask(P, field_to_world(P.F, v3(q.x, q.y, q.z)));
+                if (m != 1.f) {
+                    f.y *= m;
+                    f.z *= m;
+                    f.w *= m;
+                    W.fout[src_r0 + i] = f;
+                }
             }
         }
     }
@@ -914,7 +925,7 @@ Layout layout(uint32_t paths, int n_shadow, uint32_t cap_per_path = 96, bool vie
     L.comp = take(16 * P);
     L.sdepth = take(4 * P * nl);
     L.squeue = take(4 * P * nl);
-    L.ctr = take(4 * (4 + kMaxRounds));
+    L.ctr = take(4 * (4 + 4 * kMaxRounds));
     // sample capacity: cap_per_path samples per path plus 4M (overflowing jobs are marched in place)
     const uint64_t cap = std::min<uint64_t>((uint64_t)P * (cap_per_path ? cap_per_path : 96) + (4u << 20),
                                             0x7FFFFFFFull);
@@ -935,7 +946,8 @@ cudaError_t enqueue_frame(const WfParams &W, const RenderParams &P, uint32_t pat
     const int groups = P.tc_groups == 4 ? 4 : 8;
     const int field_grid = tc ? 152 * field_tc_blocks_per_sm(groups) : 152 * 8;
     const int rounds = std::min(std::max(P.max_rounds, 1), kMaxRounds);
-    cudaError_t e = cudaMemsetAsync(W.ctr, 0, 4 * (4 + kMaxRounds), s);   // counters left over from the previous call
+    // counters left over from the previous call
+    cudaError_t e = cudaMemsetAsync(W.ctr, 0, 4 * (4 + 4 * kMaxRounds), s);
     if (e != cudaSuccess) return e;
     // NVTX ranges mark the host-side enqueue of the frame and of each segment
     struct Range {
@@ -945,7 +957,7 @@ cudaError_t enqueue_frame(const WfParams &W, const RenderParams &P, uint32_t pat
     for (uint32_t j = 1; j <= P.max_bounces; ++j) {
         const int cur = (j - 1) & 1, nxt = j & 1;
         Range seg_range("mrf segment");
-        if ((e = cudaMemsetAsync(W.ctr + 2, 0, 4 * (2 + rounds), s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(W.ctr + 2, 0, 4 * (2 + 4 * rounds), s)) != cudaSuccess) return e;
         timer_begin(timer, MRF_KERNEL_CAST_GEN, s);
         wf_cast<<<grid, kThreads, 0, s>>>(W, j, cur);
         timer_end(timer, s);
