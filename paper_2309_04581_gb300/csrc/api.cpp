@@ -372,6 +372,15 @@ static mrf_status field_create_impl(mrf_context *ctx, const mrf_field_desc *D, m
             for (int o = 0; o < 3; ++o) Wc3T[j * 4 + o] = wc3[o * 64 + j];
         for (int o = 0; o < 3; ++o) BC3[o] = bc3[o];
         F.view_dep = 1;
+        std::memcpy(F.bias_c, b1.data(), 64 * 4);
+        std::memcpy(F.bias_c + 64, bd2.data(), 16 * 4);
+        std::memcpy(F.bias_c + 80, bc1.data(), 64 * 4);
+        std::memcpy(F.bias_c + 144, bc2.data(), 64 * 4);
+        for (int o = 0; o < 3; ++o) F.bias_c[208 + o] = bc3[o];
+    } else {
+        std::memcpy(F.bias_c, b1.data(), 64 * 4);
+        std::memcpy(F.bias_c + 64, b2.data(), 64 * 4);
+        std::memcpy(F.bias_c + 128, b3.data(), 4 * 4);
     }
     F.n_in = (int)n_in;
     if ((st = upload(f, pk.data(), pk.size(), &F.mlp, "mlp weights"))) return st;

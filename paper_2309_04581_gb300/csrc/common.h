@@ -38,6 +38,11 @@ struct FieldDev {
     int n_in;
     const float *mlp;           // packed FP32, see mlp_floats (+ kViewFloats when view_dep)
     int view_dep;               // view-dependent radiance (colour network of the view direction)
+    // FP32 biases for the tensor-core kernels, read from the kernel-parameter
+    // constant bank (uniform across the warp: no shared-memory loads).  Plain
+    // network: b1[64] b2[64] b3[4]; view-dependent: b1[64] bd[16] bc1[64]
+    // bc2[64] bc3[3] 0.
+    float bias_c[212];
     const void *mlp_lp;         // [FP16 | BF16] copies of W1, W2, W3 (W3 padded to 16 rows) in the
                                 // tensor-core operand layout, 64 * n_in * 2 + 10240 bytes each
     int n_support;

@@ -24,6 +24,24 @@ namespace {
 
 using namespace tc;
 
+// relu_bias_store with the bias taken from the field's kernel-parameter copy
+// (F.bias_c[kOff .. kOff + 32)): constant-bank operands instead of shared loads.
+template <bool kBF16, int kOff>
+__device__ __forceinline__ void relu_bias_store_c(const uint32_t (&r)[32], const FieldDev &F, uint8_t *A, int row,
+                                                  int chunk0) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = 8 * c + 2 * q;
+            w[q] = pack2<kBF16>(fmaxf(__uint_as_float(r[k]) + F.bias_c[kOff + k], 0.f),
+                                fmaxf(__uint_as_float(r[k + 1]) + F.bias_c[kOff + k + 1], 0.f));
+        }
+        store_chunk(A, row, chunk0 + c, 1024, make_uint4(w[0], w[1], w[2], w[3]));
+    }
+}
+
 // Shared-memory layout of one CTA: weights, biases and support spheres shared
 // by its tile groups, then one mbarrier and one 16 KB A operand per group.
 constexpr int kSmemW1 = 0, kSmemW2 = 8192, kSmemW3 = 16384, kSmemBias = 18432;
@@ -198,14 +216,13 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
                     uint32_t n_host, float4 *__restrict__ out, unsigned *__restrict__ status) {
     using Lo = Layout<G>;
     extern __shared__ __align__(128) uint8_t smem[];
-    float *sBias = reinterpret_cast<float *>(smem + kSmemBias);
     uint32_t *sTmem = reinterpret_cast<uint32_t *>(smem + Lo::tmem_slot);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int g = tid >> 7, gt = tid & 127, gw = gt >> 5;
     const int n_in = F.n_in, kin = n_in / 16, sbo_in = (n_in / 8) * 128;
     constexpr int kThreadsCta = 128 * G;
 
-    // stage the low-precision weights (already in the canonical layout), FP32 biases, support spheres
+    // stage the low-precision weights (already in the canonical layout) and the support spheres
     {
         const int w1_bytes = 64 * n_in * 2;
         const uint8_t *src = reinterpret_cast<const uint8_t *>(F.mlp_lp) + (kBF16 ? w1_bytes + 10240 : 0);
@@ -213,12 +230,6 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
             *reinterpret_cast<uint4 *>(smem + kSmemW1 + o) = __ldg(reinterpret_cast<const uint4 *>(src + o));
         for (int o = tid * 16; o < 10240; o += kThreadsCta * 16)
             *reinterpret_cast<uint4 *>(smem + kSmemW2 + o) = __ldg(reinterpret_cast<const uint4 *>(src + w1_bytes + o));
-        const float *b1 = F.mlp + n_in * 64, *b2 = b1 + 64 + 4096, *b3 = b2 + 64 + 256;
-        if (tid < 64) {
-            sBias[tid] = b1[tid];
-            sBias[64 + tid] = b2[tid];
-        }
-        if (tid < 4) sBias[128 + tid] = b3[tid];
     }
     float4 *sSup = reinterpret_cast<float4 *>(smem + kSmemSupport);
     const bool sup_smem = F.n_support <= kSupportMax;
@@ -252,6 +263,18 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
     uint32_t phase = 0;
     bool ok = true;
 
+    // One warp of the group polls the MMA's mbarrier; the other three wait at the
+    // group's named barrier, which also carries the give-up flag, so that the
+    // wait costs no shared-memory polls next to the table gathers.  False: the
+    // group leaves its loop.
+    auto wait_mma = [&]() -> bool {
+        if (gw == 0) ok &= mbar_wait(bar, phase);
+        phase ^= 1;
+        fence_before_sync();
+        const bool bad = group_sync_or(bar_id, !ok);
+        fence_after_sync();
+        return !bad;
+    };
     for (uint32_t tile = blockIdx.x * G + g; tile * 128u < n; tile += gridDim.x * G) {
         const uint32_t i = tile * 128u + gt;
         const bool valid = i < n;
@@ -300,16 +323,14 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
                 mma_f16(t_acc, smem_desc(aA + 256 * k, 128, sbo_in), smem_desc(aW1 + 256 * k, 128, sbo_in), id64, k);
             mma_commit(bar);
         }
-        ok &= mbar_wait(bar, phase);
-        phase ^= 1;
-        fence_after_sync();
+        if (!wait_mma()) break;
         // layer 1 epilogue -> A (K = 64)
         {
             uint32_t r[32];
             tmem_ld_x32(t_row, r);
-            relu_bias_store<kBF16>(r, sBias, sA, gt, 0);
+            relu_bias_store_c<kBF16, 0>(r, F, sA, gt, 0);
             tmem_ld_x32(t_row + 32, r);
-            relu_bias_store<kBF16>(r, sBias + 32, sA, gt, 4);
+            relu_bias_store_c<kBF16, 32>(r, F, sA, gt, 4);
         }
         fence_async_smem();
         fence_before_sync();
@@ -321,16 +342,14 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
                 mma_f16(t_acc, smem_desc(aA + 256 * k, 128, 1024), smem_desc(aW2 + 256 * k, 128, 1024), id64, k);
             mma_commit(bar);
         }
-        ok &= mbar_wait(bar, phase);
-        phase ^= 1;
-        fence_after_sync();
+        if (!wait_mma()) break;
         // layer 2 epilogue -> A (K = 64)
         {
             uint32_t r[32];
             tmem_ld_x32(t_row, r);
-            relu_bias_store<kBF16>(r, sBias + 64, sA, gt, 0);
+            relu_bias_store_c<kBF16, 64>(r, F, sA, gt, 0);
             tmem_ld_x32(t_row + 32, r);
-            relu_bias_store<kBF16>(r, sBias + 96, sA, gt, 4);
+            relu_bias_store_c<kBF16, 96>(r, F, sA, gt, 4);
         }
         fence_async_smem();
         fence_before_sync();
@@ -342,15 +361,12 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
                 mma_f16(t_acc, smem_desc(aA + 256 * k, 128, 1024), smem_desc(aW3 + 256 * k, 128, 1024), id16, k);
             mma_commit(bar);
         }
-        ok &= mbar_wait(bar, phase);
-        phase ^= 1;
-        fence_after_sync();
+        if (!wait_mma()) break;
         {
             uint32_t r[16];
             tmem_ld_x16(t_row, r);
-            const float4 b3 = *reinterpret_cast<const float4 *>(sBias + 128);
-            const float o0 = __uint_as_float(r[0]) + b3.x, o1 = __uint_as_float(r[1]) + b3.y,
-                        o2 = __uint_as_float(r[2]) + b3.z, o3 = __uint_as_float(r[3]) + b3.w;
+            const float o0 = __uint_as_float(r[0]) + F.bias_c[128], o1 = __uint_as_float(r[1]) + F.bias_c[129],
+                        o2 = __uint_as_float(r[2]) + F.bias_c[130], o3 = __uint_as_float(r[3]) + F.bias_c[131];
             if (valid) {
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (s > 0.f)
@@ -397,7 +413,6 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
                          unsigned *__restrict__ status) {
     using Lo = LayoutV<G>;
     extern __shared__ __align__(128) uint8_t smem[];
-    float *sBias = reinterpret_cast<float *>(smem + kVBias);
     uint32_t *sTmem = reinterpret_cast<uint32_t *>(smem + Lo::tmem_slot);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int g = tid >> 7, gt = tid & 127, gw = gt >> 5;
@@ -406,15 +421,6 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
         const uint8_t *src = reinterpret_cast<const uint8_t *>(F.mlp_lp) + (kBF16 ? kVWBytes : 0);
         for (int o = tid * 16; o < kVWBytes; o += kThreadsCta * 16)
             *reinterpret_cast<uint4 *>(smem + o) = __ldg(reinterpret_cast<const uint4 *>(src + o));
-        const float *b1 = F.mlp + 32 * 64, *v = F.mlp + mlp_floats(32);
-        const float *bd = v + 64 * 16, *bc1 = bd + 16 + 32 * 64, *bc2 = bc1 + 64 + 64 * 64, *bc3 = bc2 + 64 + 256;
-        if (tid < 64) {
-            sBias[tid] = b1[tid];
-            sBias[80 + tid] = bc1[tid];
-            sBias[144 + tid] = bc2[tid];
-        }
-        if (tid < 16) sBias[64 + tid] = bd[tid];
-        if (tid < 4) sBias[208 + tid] = tid < 3 ? bc3[tid] : 0.f;
     }
     float4 *sSup = reinterpret_cast<float4 *>(smem + kVSupport);
     const bool sup_smem = F.n_support <= kSupportMax;
@@ -508,9 +514,9 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
         {   // layer 1 epilogue -> A (K = 64)
             uint32_t r[32];
             tmem_ld_x32(t_row, r);
-            relu_bias_store<kBF16>(r, sBias, sA, gt, 0);
+            relu_bias_store_c<kBF16, 0>(r, F, sA, gt, 0);
             tmem_ld_x32(t_row + 32, r);
-            relu_bias_store<kBF16>(r, sBias + 32, sA, gt, 4);
+            relu_bias_store_c<kBF16, 32>(r, F, sA, gt, 4);
         }
         if (!layer(aWd, 4, 1024, id16)) break;
         float sigma;
@@ -519,13 +525,7 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
             tmem_ld_x16(t_row, r);
             float x[32];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float4 b = reinterpret_cast<const float4 *>(sBias + 64)[k];
-                x[4 * k] = __uint_as_float(r[4 * k]) + b.x;
-                x[4 * k + 1] = __uint_as_float(r[4 * k + 1]) + b.y;
-                x[4 * k + 2] = __uint_as_float(r[4 * k + 2]) + b.z;
-                x[4 * k + 3] = __uint_as_float(r[4 * k + 3]) + b.w;
-            }
+            for (int k = 0; k < 16; ++k) x[k] = __uint_as_float(r[k]) + F.bias_c[64 + k];
             sigma = s * expf(fminf(x[0], 15.f));
             sh16(normalize(dv), x + 16);
 #pragma unroll
@@ -539,17 +539,17 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
         {
             uint32_t r[32];
             tmem_ld_x32(t_row, r);
-            relu_bias_store<kBF16>(r, sBias + 80, sA, gt, 0);
+            relu_bias_store_c<kBF16, 80>(r, F, sA, gt, 0);
             tmem_ld_x32(t_row + 32, r);
-            relu_bias_store<kBF16>(r, sBias + 112, sA, gt, 4);
+            relu_bias_store_c<kBF16, 112>(r, F, sA, gt, 4);
         }
         if (!layer(aWc2, 4, 1024, id64)) break;
         {
             uint32_t r[32];
             tmem_ld_x32(t_row, r);
-            relu_bias_store<kBF16>(r, sBias + 144, sA, gt, 0);
+            relu_bias_store_c<kBF16, 144>(r, F, sA, gt, 0);
             tmem_ld_x32(t_row + 32, r);
-            relu_bias_store<kBF16>(r, sBias + 176, sA, gt, 4);
+            relu_bias_store_c<kBF16, 176>(r, F, sA, gt, 4);
         }
         if (!layer(aWc3, 4, 1024, id16)) break;
         {
@@ -558,9 +558,9 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
             if (valid) {
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (s > 0.f) {
-                    const float4 bc = *reinterpret_cast<const float4 *>(sBias + 208);
-                    v = make_float4(sigma * dl, softplusf(__uint_as_float(r[0]) + bc.x),
-                                    softplusf(__uint_as_float(r[1]) + bc.y), softplusf(__uint_as_float(r[2]) + bc.z));
+                    v = make_float4(sigma * dl, softplusf(__uint_as_float(r[0]) + F.bias_c[208]),
+                                    softplusf(__uint_as_float(r[1]) + F.bias_c[209]),
+                                    softplusf(__uint_as_float(r[2]) + F.bias_c[210]));
                 }
                 out[i] = v;
             }

@@ -264,8 +264,12 @@ __device__ __noinline__ uint32_t warp_walk(const RenderParams &P, const WalkCtx 
             const float hi = P.steps ? fmaf((float)(i + 1), S.h, S.t0) : fminf(lo + S.h, S.t1);
             const float tm = 0.5f * (lo + hi), delta = hi - lo;
             const V3 p = fma3(d, tm, o);
-            bool empty = false;
-            if (use_coarse) {
+            // With the range jumps the support test (arithmetic only) goes first
+            // and the coarse grid is left out: the fine grid alone takes the same
+            // decisions, and the coarse one only sped up skipping, which the
+            // jumps between sphere ranges now do.
+            bool empty = jump && !(support_masked(X.support, smask, p) > 0.f);
+            if (!empty && use_coarse && !jump) {
                 int c[3];
 #pragma unroll
                 for (int q = 0; q < 3; ++q)
@@ -285,7 +289,7 @@ __device__ __noinline__ uint32_t warp_walk(const RenderParams &P, const WalkCtx 
                     empty = true;
                 }
             }
-            if (!empty) emit = !hash || support_masked(X.support, smask, p) > 0.f;
+            if (!empty) emit = !hash || jump || support_masked(X.support, smask, p) > 0.f;
             rec = make_float4(p.x, p.y, p.z, delta);
         } else {
             skip_to = S.n;

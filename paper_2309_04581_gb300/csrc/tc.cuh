@@ -44,36 +44,28 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 }
 
 // Waits for phase `parity` of the mbarrier for at most `budget` SM cycles;
-// false when it gave up.
+// false when it gave up.  Each try_wait may suspend the thread for up to
+// kSuspendNs (it resumes as soon as the phase completes), so a wait on an MMA
+// costs a few polls of the barrier instead of one per scheduling round: the
+// polls are shared-memory accesses that compete with the table gathers for the
+// L1 data pipe.
+constexpr uint32_t kSuspendNs = 20000;
 __device__ __forceinline__ bool mbar_wait_budget(uint32_t bar, uint32_t parity, long long budget) {
     const long long t0 = clock64();
     while (true) {
         uint32_t done;
         asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}\n"
             : "=r"(done)
-            : "r"(bar), "r"(parity)
+            : "r"(bar), "r"(parity), "r"(kSuspendNs)
             : "memory");
         if (done) return true;
         if (clock64() - t0 > budget) return false;
     }
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    const long long t0 = clock64();
-    while (true) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if (clock64() - t0 > kWaitCycles) return false;
-    }
-}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) { return mbar_wait_budget(bar, parity, kWaitCycles); }
 
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
