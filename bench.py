@@ -361,6 +361,12 @@ def run_ours(args):
         m32 = sum(ms32) / len(ms32)
         fp32 = {"value": world * segs / (m32 / 1e3), "ms_per_step": m32, "engine": "megakernel",
                 "speedup_of_headline": m32 / ms}
+        # the same FP32 arithmetic through the wavefront engine (FP32 field on the CUDA cores)
+        ms32w = time_steps(torch, r32, M.MRF_ENGINE_WAVEFRONT, o32, stream, max(3, args.steps // 2), args.warmup,
+                           flush)
+        m32w = sum(ms32w) / len(ms32w)
+        fp32["wavefront"] = {"value": world * segs / (m32w / 1e3), "ms_per_step": m32w,
+                             "speedup_of_headline": m32w / ms}
         r32.close()
     # BVH traversal of the cast kernel: nodes (64 B) and triangles (48 B) fetched
     cast = None

@@ -79,7 +79,10 @@ const char *mrf_version(void);
  *              support spheres gives the density its compact support.
  *              occ_bits is a conservative occupancy bitfield (occ_res^3 bits,
  *              cell x + R*(y + R*z), word i>>5 bit i&31) covering the support;
- *              the renderer skips samples in empty cells.
+ *              the renderer skips samples in empty cells.  mrf_field_create
+ *              checks the cover (every cell a support sphere reaches is set);
+ *              when it holds, the wavefront sample walk tests the support
+ *              only, otherwise it also tests every sample's cell.
  * Layouts: blob_center (n_blobs x 3), blob_emission (n_blobs x 3), table
  * [level][entry][feature] as IEEE binary16 bits, w1 (width x in) row-major,
  * w2 (width x width), w3 (4 x width), in = n_levels * n_features (<= 64),

@@ -242,6 +242,40 @@ static mrf_status upload(mrf_field *f, const T *src, size_t n, const T **dst, co
     return MRF_OK;
 }
 
+// True when every occupancy cell that a support sphere can reach is marked, so
+// that no sample with positive support is ever rejected by the occupancy test.
+// The sphere is grown by 1e-5 relative and by 1e-5 of the box, and cells are
+// tested as closed boxes: this absorbs the FP32 rounding of the walk's support
+// test and of its cell index (a few ulps of the coordinates).
+static bool occupancy_covers_support(const std::vector<uint32_t> &bits, uint32_t R, const double lo[3],
+                                     const double ext[3], const std::vector<float> &sc, const std::vector<float> &sr) {
+    const double m = 1e-5 * std::max(ext[0], std::max(ext[1], ext[2]));
+    for (size_t k = 0; k < sr.size(); ++k) {
+        const double r = (double)sr[k] * (1.0 + 1e-5) + m;
+        const double c[3] = {sc[3 * k], sc[3 * k + 1], sc[3 * k + 2]};
+        int a[3], b[3];
+        for (int q = 0; q < 3; ++q) {
+            const double cell = ext[q] / R;
+            a[q] = std::max(0, (int)std::floor((c[q] - r - lo[q]) / cell) - 1);
+            b[q] = std::min((int)R - 1, (int)std::floor((c[q] + r - lo[q]) / cell) + 1);
+        }
+        for (int z = a[2]; z <= b[2]; ++z)
+            for (int y = a[1]; y <= b[1]; ++y)
+                for (int x = a[0]; x <= b[0]; ++x) {
+                    const int ii[3] = {x, y, z};
+                    double d2 = 0.0;
+                    for (int q = 0; q < 3; ++q) {
+                        const double cell = ext[q] / R, e0 = lo[q] + ii[q] * cell, e1 = e0 + cell;
+                        const double g = std::max(0.0, std::max(e0 - c[q], c[q] - e1));
+                        d2 += g * g;
+                    }
+                    const size_t i = (size_t)x + (size_t)R * ((size_t)y + (size_t)R * (size_t)z);
+                    if (d2 <= r * r && !((bits[i >> 5] >> (i & 31)) & 1u)) return false;
+                }
+    }
+    return true;
+}
+
 static mrf_status field_create_impl(mrf_context *ctx, const mrf_field_desc *D, mrf_field *f) {
     FieldDev &F = f->dev;
     F.kind = D->kind;
@@ -421,10 +455,10 @@ static mrf_status field_create_impl(mrf_context *ctx, const mrf_field_desc *D, m
     }
     // support spheres
     const uint32_t S = D->n_support;
+    std::vector<float> sc, sr;
     if (S > 0) {
         if (!D->support_center || !D->support_radius)
             return fail(MRF_ERR_INVALID_ARG, "mrf_field_create: support arrays missing");
-        std::vector<float> sc, sr;
         if ((st = fetch(sc, D->support_center, 3 * (size_t)S)) || (st = fetch(sr, D->support_radius, S))) return st;
         std::vector<float4> sp(S);
         for (uint32_t k = 0; k < S; ++k)
@@ -458,12 +492,15 @@ static mrf_status field_create_impl(mrf_context *ctx, const mrf_field_desc *D, m
                 }
         if ((st = upload(f, coarse.data(), coarse.size(), &F.occ_coarse, "coarse occupancy"))) return st;
         F.occ_coarse_res = (int)Rc;
+        double lo[3], ext[3];
         for (int k = 0; k < 3; ++k) {
-            const double ext = (double)D->aabb_max[k] - (double)D->aabb_min[k];
-            F.occ_coarse_scale[k] = (float)((double)Rc / ext);
-            F.occ_cell[k] = (float)(ext / (double)R);
-            F.occ_coarse_cell[k] = (float)(ext / (double)Rc);
+            lo[k] = D->aabb_min[k];
+            ext[k] = (double)D->aabb_max[k] - (double)D->aabb_min[k];
+            F.occ_coarse_scale[k] = (float)((double)Rc / ext[k]);
+            F.occ_cell[k] = (float)(ext[k] / (double)R);
+            F.occ_coarse_cell[k] = (float)(ext[k] / (double)Rc);
         }
+        F.occ_covers_support = S > 0 && occupancy_covers_support(fine, R, lo, ext, sc, sr) ? 1 : 0;
     }
     (void)ctx;
     return MRF_OK;

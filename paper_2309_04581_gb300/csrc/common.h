@@ -55,6 +55,10 @@ struct FieldDev {
     const uint32_t *occ_coarse;
     float occ_coarse_scale[3];  // occ_coarse_res / extent
     float occ_cell[3], occ_coarse_cell[3];  // cell widths (extent / resolution)
+    // 1 when every occupancy cell a support sphere reaches is marked (checked on
+    // the host at creation): a sample with positive support then always lies in
+    // an occupied cell, and walks that test the support may skip the grid.
+    int occ_covers_support;
     int precision;
     // rigid pose: world-to-local [R^T | -R^T t] applied to every marched ray
     int has_pose;

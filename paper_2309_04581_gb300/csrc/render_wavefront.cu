@@ -224,8 +224,8 @@ __device__ __noinline__ uint32_t warp_walk(const RenderParams &P, const WalkCtx 
     const FieldDev &F = P.F;
     const V3 inv = v3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
     const bool hash = F.kind == MRF_FIELD_HASHGRID;
-    const bool use_occ = hash && F.occ != nullptr;
-    const bool use_coarse = use_occ && X.coarse != nullptr;
+    const bool use_occ0 = hash && F.occ != nullptr;
+    const bool use_coarse = use_occ0 && X.coarse != nullptr;
     const int Rc = F.occ_coarse_res;
     const float inv_h = 1.0f / S.h;
     const uint32_t smask = hash ? job_spheres(F, X, o, d, S.t0, S.t1, lane) : 0u;
@@ -233,6 +233,9 @@ __device__ __noinline__ uint32_t warp_walk(const RenderParams &P, const WalkCtx 
     // samples inside some sphere can have non-zero density, so the walk jumps
     // over the gaps between the ranges (conservative by two intervals).
     const bool jump = hash && F.n_support > 0 && F.n_support <= 32;
+    // with range jumps the support test comes first; when the grid covers the
+    // support it can no longer reject anything, and is left out
+    const bool use_occ = use_occ0 && !(jump && F.occ_covers_support);
     int jb = 0x7fffffff, je = -1;
     if (jump && ((smask >> lane) & 1u)) {
         const float4 c = X.support[lane];

@@ -188,6 +188,30 @@ def test_config1_full_image(M, orc, torch_cuda):
     assert gpu["stats"]["paths"] == sc.n_rays
 
 
+def test_occupancy_that_does_not_cover_the_support(M, torch_cuda):
+    """Occupancy is an acceleration structure that must cover the density
+    support; the library checks the cover when the field is created and lets
+    the sample walk skip the grid only then.  With a grid that leaves a slab of
+    supported cells empty, the wavefront walk must keep testing it: its image
+    then agrees with the megakernel's march (which always tests the grid) and
+    differs from the render of the covering grid."""
+    import dataclasses
+    sc = S.config2(48, 40)
+    R = sc.field.occ_res
+    i = np.arange(R ** 3, dtype=np.int64)
+    clear = ((i % R) >= 56) & ((i % R) < 72)
+    bits = sc.field.occ_bits.copy()
+    np.bitwise_and.at(bits, i[clear] >> 5, ~(np.uint32(1) << (i[clear] & 31).astype(np.uint32)))
+    holes = dataclasses.replace(sc, field=dataclasses.replace(sc.field, occ_bits=bits))
+    wf = _render(M, holes, engine=M.MRF_ENGINE_WAVEFRONT)
+    mk = _render(M, holes, engine=M.MRF_ENGINE_MEGAKERNEL)
+    full = _render(M, sc, engine=M.MRF_ENGINE_WAVEFRONT)
+    assert np.abs(wf["rgba"] - full["rgba"]).max() > 1e-2          # the empty slab removes density
+    peak = np.abs(mk["rgba"][:, :3]).max()
+    assert np.abs(wf["rgba"][:, :3] - mk["rgba"][:, :3]).max() <= 1e-4 * peak
+    assert wf["stats"]["samples_evaluated"] == mk["stats"]["samples_evaluated"]
+
+
 def test_config2_small_full_image(M, orc, torch_cuda):
     sc = S.config2(64, 64)
     gpu = _render(M, sc)
