@@ -446,6 +446,8 @@ __device__ __forceinline__ bool child_hit(float lx, float ly, float lz, float hx
     return a <= b;
 }
 
+constexpr int kTriBatch = 4;   // the host SAH builder's largest leaf
+
 // Closest hit (any_hit = false) or first hit in (tmin, tmax) (any_hit = true),
 // skipping the triangle with original id `skip`.  Adds the nodes visited to
 // `visits` and the ray-triangle tests made to `tests`.  Returns false and sets
@@ -482,20 +484,39 @@ __device__ bool bvh_trace(const BvhDev &B, V3 o, V3 d, uint32_t skip, float tmin
             bool hs = s == 0 ? hl : hr;
             if (!hs) continue;
             if (cc[s] > 0) {
-                for (int k = ci[s]; k < ci[s] + cc[s]; ++k) {
-                    V3 a, b, c;
-                    uint32_t id, mat;
-                    load_tri(B, (int)checked_index((uint32_t)k, (uint64_t)B.n_tris, B.status), a, b, c, id, mat);
-                    if (id == skip) continue;
-                    ++tests;
-                    float t;
-                    if (tri_test(o, d, a, b, c, tmin, h.t, t, retests)) {
-                        if (t < h.t || (t == h.t && id < h.id)) {
-                            h.t = t;
-                            h.id = id;
-                            h.slot = k;
-                            found = true;
-                            if (any_hit) return true;
+                // the leaf's triangles in batches of kTriBatch: all loads of a
+                // batch are issued before the first test, so a leaf costs one
+                // memory round trip instead of one per triangle (the slowest
+                // rays, inside the glass, are chains of such round trips)
+                for (int k0 = ci[s]; k0 < ci[s] + cc[s]; k0 += kTriBatch) {
+                    const int nb = min(kTriBatch, ci[s] + cc[s] - k0);
+                    float4 tv[kTriBatch][3];
+#pragma unroll
+                    for (int q = 0; q < kTriBatch; ++q)
+                        if (q < nb) {
+                            const float4 *tp =
+                                B.tris + 3 * checked_index((uint32_t)(k0 + q), (uint64_t)B.n_tris, B.status);
+                            tv[q][0] = __ldg(tp);
+                            tv[q][1] = __ldg(tp + 1);
+                            tv[q][2] = __ldg(tp + 2);
+                        }
+#pragma unroll
+                    for (int q = 0; q < kTriBatch; ++q) {
+                        if (q >= nb) break;
+                        const uint32_t id = __float_as_uint(tv[q][0].w);
+                        if (id == skip) continue;
+                        ++tests;
+                        float t;
+                        const V3 a = v3(tv[q][0].x, tv[q][0].y, tv[q][0].z), b = v3(tv[q][1].x, tv[q][1].y, tv[q][1].z),
+                                 c = v3(tv[q][2].x, tv[q][2].y, tv[q][2].z);
+                        if (tri_test(o, d, a, b, c, tmin, h.t, t, retests)) {
+                            if (t < h.t || (t == h.t && id < h.id)) {
+                                h.t = t;
+                                h.id = id;
+                                h.slot = k0 + q;
+                                found = true;
+                                if (any_hit) return true;
+                            }
                         }
                     }
                 }
