@@ -446,13 +446,15 @@ __device__ __forceinline__ bool child_hit(float lx, float ly, float lz, float hx
     return a <= b;
 }
 
-constexpr int kTriBatch = 4;   // the host SAH builder's largest leaf
-
 // Closest hit (any_hit = false) or first hit in (tmin, tmax) (any_hit = true),
-// skipping the triangle with original id `skip`.  Adds the nodes visited to
+// skipping the triangle with original id `skip`.  A leaf's triangles are
+// loaded in batches of kTriBatch before they are tested: 4 (the host SAH
+// builder's largest leaf) makes a leaf one memory round trip, which shortens
+// the slowest rays' dependent chains in the wavefront cast kernel; the
+// register-bound megakernel keeps 1.  Adds the nodes visited to
 // `visits` and the ray-triangle tests made to `tests`.  Returns false and sets
 // `fault` if the traversal stack overflows.
-template <bool any_hit>
+template <bool any_hit, int kTriBatch = 1>
 __device__ bool bvh_trace(const BvhDev &B, V3 o, V3 d, uint32_t skip, float tmin, float tmax, Hit &h,
                           unsigned &retests, unsigned &visits, unsigned &tests, bool &fault) {
     h.t = tmax;
@@ -484,10 +486,6 @@ __device__ bool bvh_trace(const BvhDev &B, V3 o, V3 d, uint32_t skip, float tmin
             bool hs = s == 0 ? hl : hr;
             if (!hs) continue;
             if (cc[s] > 0) {
-                // the leaf's triangles in batches of kTriBatch: all loads of a
-                // batch are issued before the first test, so a leaf costs one
-                // memory round trip instead of one per triangle (the slowest
-                // rays, inside the glass, are chains of such round trips)
                 for (int k0 = ci[s]; k0 < ci[s] + cc[s]; k0 += kTriBatch) {
                     const int nb = min(kTriBatch, ci[s] + cc[s] - k0);
                     float4 tv[kTriBatch][3];

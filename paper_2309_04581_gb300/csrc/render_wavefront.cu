@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(kThreads) wf_cast(const WfParams W, uint32_t j
         unsigned rt = 0;
         bool fault = false;
         const unsigned nodes0 = C.nodes;
-        bvh_trace<false>(P.B, o, d, prev, P.tmin, INFINITY, h, rt, C.nodes, C.tris, fault);
+        bvh_trace<false, 4>(P.B, o, d, prev, P.tmin, INFINITY, h, rt, C.nodes, C.tris, fault);
         note_traversal(C, C.nodes - nodes0, path);
         C.retests += rt;
         if (fault) C.fault |= 1;
@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(kThreads) wf_cast(const WfParams W, uint32_t j
                             unsigned rs = 0;
                             bool f2 = false;
                             const bool blocked =
-                                bvh_trace<true>(P.B, S.p, wl, S.id, P.tmin, D, hs, rs, C.nodes, C.tris, f2);
+                                bvh_trace<true, 4>(P.B, S.p, wl, S.id, P.tmin, D, hs, rs, C.nodes, C.tris, f2);
                             C.retests += rs;
                             if (f2) C.fault |= 1;
                             if (!blocked) {
