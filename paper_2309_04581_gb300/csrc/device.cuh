@@ -448,10 +448,11 @@ __device__ __forceinline__ bool child_hit(float lx, float ly, float lz, float hx
 
 // Closest hit (any_hit = false) or first hit in (tmin, tmax) (any_hit = true),
 // skipping the triangle with original id `skip`.  A leaf's triangles are
-// loaded in batches of kTriBatch before they are tested: 4 (the host SAH
-// builder's largest leaf) makes a leaf one memory round trip, which shortens
-// the slowest rays' dependent chains in the wavefront cast kernel; the
-// register-bound megakernel keeps 1.  Adds the nodes visited to
+// loaded in batches of kTriBatch before they are tested.  4 (the host SAH
+// builder's largest leaf) makes a leaf one memory round trip, which shortens a
+// lone slow ray's chain of dependent loads, but the extra registers cost more
+// occupancy than that gains wherever many rays are in flight, so every caller
+// uses 1.  Adds the nodes visited to
 // `visits` and the ray-triangle tests made to `tests`.  Returns false and sets
 // `fault` if the traversal stack overflows.
 template <bool any_hit, int kTriBatch = 1>

@@ -206,21 +206,22 @@ struct RunList {
 
 // Warp-cooperative walk over the quadrature intervals of one job (every lane
 // holds the same job): lane l takes interval i0 + l of each 32-interval chunk,
-// tests occupancy (coarse, then fine) and the density support exactly as
-// march() does, and the warp advances by 32 or, when the chunk's last interval
-// lies in an empty cell, to that cell's exit.  Counts the samples whose density
-// can be non-zero; records them as runs of consecutive intervals in `runs`
-// (lane 0 writes; may be nullptr) and, if `out` is non-NULL, writes them in
-// order, never more than `limit`.  One compiled copy (noinline) serves the
-// counting and the writing walk, so both take bit-identical decisions.
-__device__ __noinline__ uint32_t warp_walk(const RenderParams &P, const WalkCtx &X, V3 o, V3 d, float a, float b,
-                                           float4 *out, uint32_t limit, unsigned long long &nominal, int lane,
-                                           RunList *runs) {
+// tests the density support and the occupancy grid, taking the decisions
+// march() takes, and the warp advances by 32, to the exit of an empty cell
+// that holds the chunk's last interval, or to the next support sphere's range.
+// Returns the number of samples whose density can be non-zero (x) and the
+// job's nominal interval count (y); records the samples as runs of consecutive
+// intervals in `runs` (lane 0 writes; may be nullptr) and, if `out` is
+// non-NULL, writes them in order, never more than `limit`.  One compiled copy
+// (noinline) serves the counting and the writing walk, so both take
+// bit-identical decisions; the counts come back in registers (a reference
+// argument would put the caller's counters in local memory).
+__device__ __noinline__ uint2 warp_walk(const RenderParams &P, const WalkCtx &X, V3 o, V3 d, float a, float b,
+                                        float4 *out, uint32_t limit, int lane, RunList *runs) {
     Segment S;
     if (runs && lane == 0) runs->n = 0;
     to_field_frame(P.F, o, d);
-    if (!segment_of(P, o, d, a, b, S)) return 0;
-    if (!out && lane == 0) nominal += (unsigned long long)S.n;
+    if (!segment_of(P, o, d, a, b, S)) return make_uint2(0u, 0u);
     const FieldDev &F = P.F;
     const V3 inv = v3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
     const bool hash = F.kind == MRF_FIELD_HASHGRID;
@@ -327,7 +328,7 @@ __device__ __noinline__ uint32_t warp_walk(const RenderParams &P, const WalkCtx 
         if (jump) i0 = next_start(i0);
     }
     if (runs && lane == 0) runs->n = nrun;
-    return k;
+    return make_uint2(k, (uint32_t)S.n);
 }
 
 // Writes a job's samples from its recorded runs (lane-parallel over the run's
@@ -391,7 +392,7 @@ __global__ void __launch_bounds__(kThreads) wf_cast(const WfParams W, uint32_t j
         unsigned rt = 0;
         bool fault = false;
         const unsigned nodes0 = C.nodes;
-        bvh_trace<false, 4>(P.B, o, d, prev, P.tmin, INFINITY, h, rt, C.nodes, C.tris, fault);
+        bvh_trace<false>(P.B, o, d, prev, P.tmin, INFINITY, h, rt, C.nodes, C.tris, fault);
         note_traversal(C, C.nodes - nodes0, path);
         C.retests += rt;
         if (fault) C.fault |= 1;
@@ -422,7 +423,7 @@ __global__ void __launch_bounds__(kThreads) wf_cast(const WfParams W, uint32_t j
                             unsigned rs = 0;
                             bool f2 = false;
                             const bool blocked =
-                                bvh_trace<true, 4>(P.B, S.p, wl, S.id, P.tmin, D, hs, rs, C.nodes, C.tris, f2);
+                                bvh_trace<true>(P.B, S.p, wl, S.id, P.tmin, D, hs, rs, C.nodes, C.tris, f2);
                             C.retests += rs;
                             if (f2) C.fault |= 1;
                             if (!blocked) {
@@ -477,7 +478,7 @@ __global__ void __launch_bounds__(128) wf_shadow_net(const WfParams W) {
 // ranges with one atomic per warp, and writes them in order.
 // Round r > 0 regenerates only the slots that round r - 1 left pending (their
 // samples did not fit the buffer), into the emptied buffer.
-__global__ void __launch_bounds__(kThreads, 8) wf_gen(const WfParams W, uint32_t j, int cur, int round) {
+__global__ void __launch_bounds__(kThreads, 6) wf_gen(const WfParams W, uint32_t j, int cur, int round) {
     __shared__ WalkSmem wsm;
     __shared__ RunList runs_sm[kThreads / 32][32][2];   // per warp, per slot: segment job, first shadow job
     const RenderParams &P = W.R;
@@ -510,15 +511,19 @@ __global__ void __launch_bounds__(kThreads, 8) wf_gen(const WfParams W, uint32_t
             const uint32_t svis = __shfl_sync(0xffffffffu, vis, src);
             const uint32_t src_tid = wbase + src;
             RunList(&rl)[2] = runs_sm[threadIdx.x >> 5][src];
-            const uint32_t n_r = warp_walk(P, X, so, sd, 0.f, st, nullptr, 0, C.nominal, lane, &rl[0]);
+            const uint2 wr = warp_walk(P, X, so, sd, 0.f, st, nullptr, 0, lane, &rl[0]);
+            const uint32_t n_r = wr.x;
+            if (lane == 0) C.nominal += wr.y;
             uint32_t n_s = 0;
             bool first = true;   // the first unblocked shadow ray records its runs
             for (int q = 0; svis && q < K; ++q) {
                 const size_t idx = (size_t)src_tid * K + q;
                 if (W.sw[idx].w != 1.f) continue;   // marched shadow rays only
                 const float4 sh = W.sdir[idx];
-                const uint32_t ns = warp_walk(P, X, sp, v3(sh.x, sh.y, sh.z), 0.f, sh.w, nullptr, 0, C.nominal, lane,
-                                              first ? &rl[1] : nullptr);
+                const uint2 ws = warp_walk(P, X, sp, v3(sh.x, sh.y, sh.z), 0.f, sh.w, nullptr, 0, lane,
+                                           first ? &rl[1] : nullptr);
+                const uint32_t ns = ws.x;
+                if (lane == 0) C.nominal += ws.y;
                 first = false;
                 if (lane == src) W.scount[idx] = ns;
                 n_s += ns;
@@ -551,14 +556,13 @@ __global__ void __launch_bounds__(kThreads, 8) wf_gen(const WfParams W, uint32_t
             }
             const V3 so = shfl3(o, src), sd = shfl3(d, src), sp = shfl3(hp, src);
             const float st = __shfl_sync(0xffffffffu, th, src);
-            unsigned long long dummy = 0;
             uint32_t k = sbase;
             const uint32_t nr = __shfl_sync(0xffffffffu, my_nr, src);
             const RunList(&rl)[2] = runs_sm[threadIdx.x >> 5][src];
             if (rl[0].n <= kRunsPerJob)
                 write_runs(P, so, sd, 0.f, st, rl[0], W.samp + k, nr, lane);
             else
-                warp_walk(P, X, so, sd, 0.f, st, W.samp + k, nr, dummy, lane, nullptr);
+                warp_walk(P, X, so, sd, 0.f, st, W.samp + k, nr, lane, nullptr);
             if (P.F.view_dep) {   // the colour network needs each radiance sample's view direction
                 V3 ol = so, dl = sd;
                 to_field_frame(P.F, ol, dl);
@@ -576,7 +580,7 @@ __global__ void __launch_bounds__(kThreads, 8) wf_gen(const WfParams W, uint32_t
                 if (first && rl[1].n <= kRunsPerJob)
                     write_runs(P, sp, v3(sh.x, sh.y, sh.z), 0.f, sh.w, rl[1], W.samp + k, ns, lane);
                 else
-                    warp_walk(P, X, sp, v3(sh.x, sh.y, sh.z), 0.f, sh.w, W.samp + k, ns, dummy, lane, nullptr);
+                    warp_walk(P, X, sp, v3(sh.x, sh.y, sh.z), 0.f, sh.w, W.samp + k, ns, lane, nullptr);
                 first = false;
                 k += ns;
             }
