@@ -603,35 +603,44 @@ __device__ __forceinline__ void warp_composite(const WfParams &W, uint32_t start
     lr = lg = lb = 0.f;
     depth = 0.f;
     stop = false;
-    for (uint32_t i0 = 0; i0 < count; i0 += 32) {
-        const bool v = i0 + lane < count;
-        float x = 0.f;
-        float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (v) {
-            const uint32_t k = start + i0 + lane;
-            f = W.fout[k];
-            x = f.x;   // sigma * delta, from the field kernel
-        }
-        float sc = x;
+    // four 32-sample chunks are loaded before the first is composited, so that a
+    // job costs one memory round trip per 128 samples (loads past the stop are
+    // inside the job's range and harmless)
+    constexpr int kChunks = 4;
+    for (uint32_t i0 = 0; i0 < count; i0 += 32 * kChunks) {
+        float4 fc[kChunks];
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const float y = __shfl_up_sync(0xffffffffu, sc, off);
-            if (lane >= off) sc += y;
+        for (int u = 0; u < kChunks; ++u) {
+            const uint32_t i = i0 + 32u * u + lane;
+            fc[u] = i < count ? W.fout[start + i] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        const float before = depth + (sc - x), after = depth + sc;
-        const bool cross = v && tau > 0.f && tmax0 * expf(-after) < tau;
-        const unsigned cm = __ballot_sync(0xffffffffu, cross);
-        const int last = cm ? __ffs(cm) - 1 : 31;
-        if (v && lane <= last) {
-            const float a = -expm1f(-x) * expf(-before);
-            lr = fmaf(a, f.y, lr);
-            lg = fmaf(a, f.z, lg);
-            lb = fmaf(a, f.w, lb);
-        }
-        depth += __shfl_sync(0xffffffffu, sc, last);
-        if (cm) {
-            stop = true;
-            break;
+#pragma unroll
+        for (int u = 0; u < kChunks; ++u) {
+            if (i0 + 32u * u >= count) break;
+            const bool v = i0 + 32u * u + lane < count;
+            const float4 f = fc[u];
+            const float x = f.x;   // sigma * delta, from the field kernel (0 past the job)
+            float sc = x;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const float y = __shfl_up_sync(0xffffffffu, sc, off);
+                if (lane >= off) sc += y;
+            }
+            const float before = depth + (sc - x), after = depth + sc;
+            const bool cross = v && tau > 0.f && tmax0 * expf(-after) < tau;
+            const unsigned cm = __ballot_sync(0xffffffffu, cross);
+            const int last = cm ? __ffs(cm) - 1 : 31;
+            if (v && lane <= last) {
+                const float a = -expm1f(-x) * expf(-before);
+                lr = fmaf(a, f.y, lr);
+                lg = fmaf(a, f.z, lg);
+                lb = fmaf(a, f.w, lb);
+            }
+            depth += __shfl_sync(0xffffffffu, sc, last);
+            if (cm) {
+                stop = true;
+                return;
+            }
         }
     }
 }
@@ -693,6 +702,7 @@ __global__ void __launch_bounds__(kThreads, 8) wf_composite(const WfParams W, in
                 if (sc == kOverflow) continue;
                 const uint32_t s0 = W.sstart[idx];
                 float dep = 0.f;
+#pragma unroll 4
                 for (uint32_t i0 = lane; i0 < sc; i0 += 32) dep += W.fout[s0 + i0].x;
                 dep = warp_sum(dep);
                 if (lane == 0) W.sdepth[idx] = dep;
