@@ -60,78 +60,6 @@ struct Layout {
 };
 constexpr int kGroups = 8;   // 128-sample tiles in flight per CTA (one CTA per SM, all 512 TMEM columns)
 
-// Level l features at p with the corner indices built incrementally: dense
-// levels from one base index and the two strides, hashed levels from the four
-// (y, z) hash partials XORed with x and x + 1 (the same indices as hash_level).
-// kHalf2 interpolates the FP16 feature pairs with half2 arithmetic (the result
-// feeds an FP16 or BF16 MMA operand); otherwise in FP32.
-template <bool kHalf2>
-__device__ __forceinline__ float2 encode_level(const FieldDev &F, int l, V3 p) {
-    const uint32_t N = F.res[l];
-    int c[3];
-    float w[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float u = (comp(p, k) - F.lo[k]) * F.ext_inv[k] * (float)N;
-        float fl = floorf(u);
-        fl = fminf(fmaxf(fl, 0.f), (float)(N - 1));
-        c[k] = (int)fl;
-        w[k] = u - fl;
-    }
-    uint32_t idx[8];
-    if ((F.dense_mask >> l) & 1u) {
-        const uint32_t sy = N + 1, sz = sy * sy;
-        const uint32_t b = (uint32_t)c[0] + sy * (uint32_t)c[1] + sz * (uint32_t)c[2];
-        idx[0] = b;
-        idx[1] = b + 1;
-        idx[2] = b + sy;
-        idx[3] = b + sy + 1;
-        idx[4] = b + sz;
-        idx[5] = b + sz + 1;
-        idx[6] = b + sy + sz;
-        idx[7] = b + sy + sz + 1;
-    } else {
-        const uint32_t mask = (1u << F.log2T) - 1u;
-        const uint32_t x0 = (uint32_t)c[0], x1 = x0 + 1u;
-        const uint32_t hy0 = (uint32_t)c[1] * 2654435761u, hy1 = hy0 + 2654435761u;
-        const uint32_t hz0 = (uint32_t)c[2] * 805459861u, hz1 = hz0 + 805459861u;
-        const uint32_t a00 = hy0 ^ hz0, a10 = hy1 ^ hz0, a01 = hy0 ^ hz1, a11 = hy1 ^ hz1;
-        idx[0] = (x0 ^ a00) & mask;
-        idx[1] = (x1 ^ a00) & mask;
-        idx[2] = (x0 ^ a10) & mask;
-        idx[3] = (x1 ^ a10) & mask;
-        idx[4] = (x0 ^ a01) & mask;
-        idx[5] = (x1 ^ a01) & mask;
-        idx[6] = (x0 ^ a11) & mask;
-        idx[7] = (x1 ^ a11) & mask;
-    }
-    const uint32_t *tab = F.table + ((size_t)l << F.log2T);
-    uint32_t e[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) e[k] = __ldg(tab + idx[k]);
-    if (kHalf2) {
-        const __half2 wx = __float2half2_rn(w[0]), wy = __float2half2_rn(w[1]), wz = __float2half2_rn(w[2]);
-        __half2 v[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = *reinterpret_cast<const __half2 *>(&e[k]);
-        const __half2 a0 = __hfma2(wx, __hsub2(v[1], v[0]), v[0]), a1 = __hfma2(wx, __hsub2(v[3], v[2]), v[2]);
-        const __half2 a2 = __hfma2(wx, __hsub2(v[5], v[4]), v[4]), a3 = __hfma2(wx, __hsub2(v[7], v[6]), v[6]);
-        const __half2 b0 = __hfma2(wy, __hsub2(a1, a0), a0), b1 = __hfma2(wy, __hsub2(a3, a2), a2);
-        return __half22float2(__hfma2(wz, __hsub2(b1, b0), b0));
-    }
-    float2 v[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = __half22float2(*reinterpret_cast<const __half2 *>(&e[k]));
-    float2 a[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-        a[k] = make_float2(fmaf(w[0], v[2 * k + 1].x - v[2 * k].x, v[2 * k].x),
-                           fmaf(w[0], v[2 * k + 1].y - v[2 * k].y, v[2 * k].y));
-    const float2 b0 = make_float2(fmaf(w[1], a[1].x - a[0].x, a[0].x), fmaf(w[1], a[1].y - a[0].y, a[0].y));
-    const float2 b1 = make_float2(fmaf(w[1], a[3].x - a[2].x, a[2].x), fmaf(w[1], a[3].y - a[2].y, a[2].y));
-    return make_float2(fmaf(w[2], b1.x - b0.x, b0.x), fmaf(w[2], b1.y - b0.y, b0.y));
-}
-
 // Loads the FP16 pair of corner i0 and of its x-neighbour i1 with one 16-byte
 // load of the aligned 4-entry chunk holding i0; i1 shares that chunk for 3 of 4
 // cells (dense: i1 = i0 + 1; hashed: i1 = i0 ^ 1 or ^ 3 unless x = 3 mod 4) and
@@ -153,9 +81,10 @@ __device__ __forceinline__ float2 encode_level_pairs(const FieldDev &F, int l, V
     float w[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
+        // p lies in the field box (callers encode only samples with support,
+        // which is zero outside it), so u >= 0 and only u = N needs clamping
         const float u = (comp(p, k) - F.lo[k]) * F.ext_inv[k] * (float)N;
-        float fl = floorf(u);
-        fl = fminf(fmaxf(fl, 0.f), (float)(N - 1));
+        const float fl = fminf(floorf(u), (float)(N - 1));
         c[k] = (int)fl;
         w[k] = u - fl;
     }
@@ -204,9 +133,6 @@ __device__ __forceinline__ float2 encode_level_pairs(const FieldDev &F, int l, V
     const float2 b1 = make_float2(fmaf(w[1], a[3].x - a[2].x, a[2].x), fmaf(w[1], a[3].y - a[2].y, a[2].y));
     return make_float2(fmaf(w[2], b1.x - b0.x, b0.x), fmaf(w[2], b1.y - b0.y, b0.y));
 }
-
-// 0: hash_level (device.cuh), 1: incremental indices FP32, 2: incremental + half2, 3: paired 16-byte loads
-constexpr int kEncode = 3;
 
 // G tile groups of 128 threads per CTA; group g owns TMEM columns [64g, 64g + 64),
 // its own A operand and mbarrier, and synchronises on named barrier 1 + g.
@@ -305,10 +231,7 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
             if (s > 0.f) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const float2 f = kEncode == 0   ? hash_level(F, 4 * c + q, p)
-                                     : kEncode == 1 ? encode_level<false>(F, 4 * c + q, p)
-                                     : kEncode == 2 ? encode_level<true>(F, 4 * c + q, p)
-                                                    : encode_level_pairs(F, 4 * c + q, p);
+                    const float2 f = encode_level_pairs(F, 4 * c + q, p);
                     w[q] = pack2<kBF16>(f.x, f.y);
                 }
             }
