@@ -35,8 +35,8 @@ __device__ __forceinline__ void relu_bias_store_c(const uint32_t (&r)[32], const
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int k = 8 * c + 2 * q;
-            w[q] = pack2<kBF16>(fmaxf(__uint_as_float(r[k]) + F.bias_c[kOff + k], 0.f),
-                                fmaxf(__uint_as_float(r[k + 1]) + F.bias_c[kOff + k + 1], 0.f));
+            w[q] = pack2_relu<kBF16>(__uint_as_float(r[k]) + F.bias_c[kOff + k],
+                                     __uint_as_float(r[k + 1]) + F.bias_c[kOff + k + 1]);
         }
         store_chunk(A, row, chunk0 + c, 1024, make_uint4(w[0], w[1], w[2], w[3]));
     }

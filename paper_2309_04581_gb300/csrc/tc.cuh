@@ -108,6 +108,18 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
     }
 }
 
+// pack2 of (max(a, 0), max(b, 0)) in one conversion with ReLU (cvt.rn.relu
+// rounds like pack2 and takes negative inputs to zero); a goes to the low half.
+template <bool kBF16>
+__device__ __forceinline__ uint32_t pack2_relu(float a, float b) {
+    uint32_t d;
+    if (kBF16)
+        asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+    else
+        asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+    return d;
+}
+
 // 8 consecutive K values of row `row` into the canonical layout (sbo = (K/8)*128)
 __device__ __forceinline__ void store_chunk(uint8_t *base, int row, int chunk, int sbo, uint4 v) {
     *reinterpret_cast<uint4 *>(base + (row >> 3) * sbo + chunk * 128 + (row & 7) * 16) = v;
@@ -128,8 +140,7 @@ __device__ __forceinline__ void relu_bias_store(const uint32_t (&r)[32], const f
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int k = 8 * c + 2 * q;
-            w[q] = pack2<kBF16>(fmaxf(__uint_as_float(r[k]) + b[2 * q], 0.f),
-                                fmaxf(__uint_as_float(r[k + 1]) + b[2 * q + 1], 0.f));
+            w[q] = pack2_relu<kBF16>(__uint_as_float(r[k]) + b[2 * q], __uint_as_float(r[k + 1]) + b[2 * q + 1]);
         }
         store_chunk(A, row, chunk0 + c, 1024, make_uint4(w[0], w[1], w[2], w[3]));
     }
