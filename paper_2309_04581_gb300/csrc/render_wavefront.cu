@@ -28,6 +28,7 @@ namespace mrf {
 namespace {
 
 constexpr uint32_t kOverflow = 0xFFFFFFFFu;   // slot whose samples did not fit (pending)
+constexpr uint32_t kDeferred = 0x80000000u;   // hp.w bit: the slot's shadow rays are traced by wf_vis
 constexpr uint32_t kDone = 0xFFFFFFFEu;       // slot composited in an earlier round of the segment
 constexpr int kMaxRounds = 16;
 constexpr int kThreads = 128;
@@ -359,7 +360,10 @@ __device__ __forceinline__ V3 shfl3(V3 v, int src) {
 }
 
 // Per lane: primary or queued ray, closest hit (Eq. 3), and at diffuse hits the
-// visibility of every shadow ray (one per point light, `samples` per area light).
+// shadow rays (one per point light, `samples` per area light).  With one shadow
+// ray per hit its visibility is traced here; with more, the rays are stored
+// with sw.w = -1 (marched) or -2 (network) and wf_vis traces them, one thread
+// per ray, instead of one thread tracing up to 64 of them in turn.
 __global__ void __launch_bounds__(kThreads) wf_cast(const WfParams W, uint32_t j, int cur) {
     const RenderParams &P = W.R;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -399,12 +403,13 @@ __global__ void __launch_bounds__(kThreads) wf_cast(const WfParams W, uint32_t j
         W.hit_t[tid] = h.t;
         W.hit_slot[tid] = h.slot;
         W.hit_id[tid] = h.id;
-        uint32_t nvis = 0;
+        uint32_t nvis = 0;   // unblocked shadow rays; kDeferred marks a slot whose rays wf_vis traces
         V3 hp = v3(0.f, 0.f, 0.f);
         if (h.id != kNoHit) {
             const SurfaceHit S = surface_at(P, o, d, h);
             hp = S.p;
             if (S.mat.kind == MRF_MAT_DIFFUSE) {
+                if (K > 1) nvis = kDeferred;
                 const uint32_t ray = path / P.spp, sp = path % P.spp;
                 // shadow rays from inside the field box go to the network
                 V3 pl = S.p, wdummy = v3(0.f, 0.f, 1.f);
@@ -417,7 +422,11 @@ __global__ void __launch_bounds__(kThreads) wf_cast(const WfParams W, uint32_t j
                         V3 wl;
                         float D, w3[3];
                         float4 wgt = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (shadow_ray(P, S, l, k, ray, sp, j, wl, D, w3)) {
+                        const bool valid = shadow_ray(P, S, l, k, ray, sp, j, wl, D, w3);
+                        if (valid && K > 1) {
+                            wgt = make_float4(w3[0], w3[1], w3[2], net ? -2.f : -1.f);   // wf_vis decides
+                            W.sdir[idx] = make_float4(wl.x, wl.y, wl.z, D);
+                        } else if (valid) {
                             ++C.shadow;
                             Hit hs;
                             unsigned rs = 0;
@@ -450,6 +459,51 @@ __global__ void __launch_bounds__(kThreads) wf_cast(const WfParams W, uint32_t j
         const int q = __ffsll((long long)nmask) - 1;
         nmask &= nmask - 1;
         W.squeue[checked_index(qbase + i, (uint64_t)W.paths * (uint64_t)K, P.status)] = tid * (uint32_t)K + (uint32_t)q;
+    }
+    flush_counters(P.stats, C);
+    if (C.fault && P.status) atomicOr(P.status, C.fault);
+}
+
+// Visibility of the shadow rays that wf_cast deferred (more than one per
+// diffuse hit): one thread per ray, grid-stride over live slots x K.  An
+// unblocked ray keeps its weight with sw.w = 1 (marched) or 2 (network: queued
+// for wf_shadow_net) and counts in its slot's hp.w; a blocked one gets sw = 0.
+// hp.w keeps the kDeferred bit, so the slot reads as having shadow rays and the
+// later kernels look at each ray's sw.w.
+__global__ void __launch_bounds__(kThreads) wf_vis(const WfParams W, int cur) {
+    const RenderParams &P = W.R;
+    const uint32_t K = (uint32_t)P.n_shadow;
+    const uint64_t total = (uint64_t)W.ctr[cur] * K;
+    Counters C = {};
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < total; base += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t idx = base + threadIdx.x;
+        bool to_net = false;
+        const uint32_t slot = (uint32_t)(idx / K);
+        // only slots wf_cast marked hold current shadow-ray entries
+        if (idx < total && (__float_as_uint(W.hp[slot].w) & kDeferred)) {
+            float4 wgt = W.sw[idx];
+            if (wgt.w < 0.f) {
+                const float4 h4 = W.hp[slot], sd = W.sdir[idx];
+                ++C.shadow;
+                Hit hs;
+                unsigned rs = 0;
+                bool f2 = false;
+                const bool blocked = bvh_trace<true>(P.B, v3(h4.x, h4.y, h4.z), v3(sd.x, sd.y, sd.z), W.hit_id[slot],
+                                                     P.tmin, sd.w, hs, rs, C.nodes, C.tris, f2);
+                C.retests += rs;
+                if (f2) C.fault |= 1;
+                if (blocked) {
+                    wgt = make_float4(0.f, 0.f, 0.f, 0.f);
+                } else {
+                    wgt.w = -wgt.w;
+                    to_net = wgt.w == 2.f;
+                    atomicAdd(reinterpret_cast<unsigned *>(&W.hp[slot]) + 3, 1u);
+                }
+                W.sw[idx] = wgt;
+            }
+        }
+        const uint32_t qi = warp_alloc(&W.ctr[3], to_net ? 1u : 0u);
+        if (to_net) W.squeue[checked_index(qi, (uint64_t)W.paths * K, P.status)] = (uint32_t)idx;
     }
     flush_counters(P.stats, C);
     if (C.fault && P.status) atomicOr(P.status, C.fault);
@@ -983,6 +1037,14 @@ cudaError_t enqueue_frame(const WfParams &W, const RenderParams &P, uint32_t pat
         wf_cast<<<grid, kThreads, 0, s>>>(W, j, cur);
         timer_end(timer, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (P.n_shadow > 1) {
+            const uint64_t rays = (uint64_t)paths * (uint64_t)P.n_shadow;
+            const unsigned vgrid = (unsigned)std::min<uint64_t>((rays + kThreads - 1) / kThreads, 152u * 16u);
+            timer_begin(timer, MRF_KERNEL_SHADOW_VIS, s);
+            wf_vis<<<vgrid, kThreads, 0, s>>>(W, cur);
+            timer_end(timer, s);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
         if (P.has_snet) {
             timer_begin(timer, MRF_KERNEL_SHADOW_NET, s);
             if (P.snet.lp)   // BF16 network: tensor cores
