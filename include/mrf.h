@@ -405,8 +405,8 @@ void mrf_frame_destroy(mrf_frame *frame);
  * A small network stands in for the field march of a shadow ray (Sec. 3.1,
  * "Shadow rays": the transmittance exp(-int sigma) from a shading point toward
  * a light).  It is trained on the GPU by this library's own kernels on pairs
- * whose targets come from the plain FP32 march, which stays the fallback (and
- * the judge of the network's error).
+ * whose targets come from the plain FP32 march, which stays the fallback and
+ * the reference the network's error is measured against.
  *  - Input: the point in the field's local frame, scaled to [0,1]^3 by the
  *    field box and clamped, encoded by a hash grid of 8 levels of 2 FP32
  *    features (resolution level_res[l]; 2^log2_table entries per level; dense

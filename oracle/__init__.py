@@ -11,9 +11,10 @@ network, loss, back-propagation and Adam, in FP64).  This module only compiles
 them with gcc and marshals numpy arrays from a ``scenes.Scene`` into the C
 struct ``orc_scene``.
 
-Parity status of each function is stated in the design doc; every function here is
-pinned by a ``-m "not gpu"`` test except the whole-image composition, which the
-paper gives no worked example for ("parity unpinned" beyond its pinned parts).
+Every function here is pinned by a ``-m "not gpu"`` test (closed forms,
+invariants, brute force, library routines) except the whole-image composition,
+for which the paper gives no worked example: "parity unpinned" beyond its
+pinned parts.
 """
 from __future__ import annotations
 

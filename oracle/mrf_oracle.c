@@ -16,7 +16,7 @@
  *   L (Eq. 12) and T (Eq. 13, T = T' f |cos| / P), then test termination
  *   (leaves the scene, throughput below tau, bounce limit).
  *
- * Readings of passages the paper leaves open (each is listed in the design doc):
+ * Readings of passages the paper leaves open (the CUDA path takes the same ones):
  *  - quadrature: midpoint rule; either a fixed number of samples per segment,
  *    or a fixed step dt whose last interval is clipped at the segment end;
  *    alpha_i = 1 - exp(-sigma_i delta_i), L += T_i alpha_i r_i, T *= exp(-sigma_i delta_i).

@@ -128,7 +128,7 @@ def lib():
     with _lock:
         if _lib is None:
             if not os.path.exists(LIB_PATH):
-                raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+                raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run paper_2309_04581_gb300.build.build())")
             L = C.CDLL(LIB_PATH)
             L.mrf_last_error.restype = C.c_char_p
             L.mrf_version.restype = C.c_char_p

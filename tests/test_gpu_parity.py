@@ -1,7 +1,7 @@
 """CUDA path vs the FP64 oracle, element by element on the same seeded inputs,
 through the C ABI.
 
-Tolerances (derived in DESIGN.md, "Parity bar"):
+Tolerances (derived from the FP32 arithmetic of each step):
   - hit triangle ids and segment counts: bit-exact on unflagged pixels;
   - hit distance: 1e-5 relative to max(t, 1e-2) (coordinates of magnitude
     ~0.5 hold t to ~1e-7 absolute in FP32, so 1e-5 relative is only
