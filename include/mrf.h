@@ -264,7 +264,7 @@ enum { MRF_ENGINE_AUTO = 0, MRF_ENGINE_MEGAKERNEL = 1, MRF_ENGINE_WAVEFRONT = 2 
 enum {
     MRF_KERNEL_MEGAKERNEL = 0, MRF_KERNEL_CAST_GEN = 1, MRF_KERNEL_FIELD = 2, MRF_KERNEL_SHADE = 3,
     MRF_KERNEL_FINALIZE = 4, MRF_KERNEL_GEN = 5, MRF_KERNEL_COMPOSITE = 6, MRF_KERNEL_SHADOW_NET = 7,
-    MRF_KERNEL_SHADOW_VIS = 8, MRF_KERNEL_COUNT = 9
+    MRF_KERNEL_SHADOW_VIS = 8, MRF_KERNEL_OVERFLOW = 9, MRF_KERNEL_MASK = 10, MRF_KERNEL_COUNT = 11
 };
 
 typedef struct mrf_render_opts {

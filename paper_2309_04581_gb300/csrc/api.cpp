@@ -1089,6 +1089,9 @@ mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *b
     if ((st = launch_render(ctx, R, s, timer))) return st;
     if (timer) {
         CUDA_TRY(cudaStreamSynchronize(s), "mrf_render: synchronize");
+        if (!timer->ok)
+            return fail(MRF_ERR_UNSUPPORTED, "mrf_render: kernel timing holds at most %d launches per call",
+                        KernelTimer::kMax);
         for (int k = 0; k < MRF_KERNEL_COUNT; ++k) {
             opts->kernel_ms[k] = 0.f;
             if (opts->kernel_launches) opts->kernel_launches[k] = 0;

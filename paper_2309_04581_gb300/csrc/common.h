@@ -196,7 +196,7 @@ struct RenderParams {
 
 // Optional per-launch CUDA-event timing of the renderer's kernels (host side).
 struct KernelTimer {
-    static constexpr int kMax = 128;
+    static constexpr int kMax = 4096;   // launches of one call (16 segments x 16 rounds fit)
     cudaEvent_t ev[2 * kMax];
     int kind[kMax];
     int n = 0;

@@ -1079,7 +1079,9 @@ cudaError_t enqueue_frame(const WfParams &W, const RenderParams &P, uint32_t pat
             timer_end(timer, s);
             if (e != cudaSuccess) return e;
             if (P.shadow_mask) {
+                timer_begin(timer, MRF_KERNEL_MASK, s);
                 wf_mask<<<grid, kThreads, 0, s>>>(W, cur, r);
+                timer_end(timer, s);
                 if ((e = cudaGetLastError()) != cudaSuccess) return e;
             }
             timer_begin(timer, MRF_KERNEL_COMPOSITE, s);
@@ -1088,7 +1090,9 @@ cudaError_t enqueue_frame(const WfParams &W, const RenderParams &P, uint32_t pat
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
         if ((e = cudaMemsetAsync(W.ctr + nxt, 0, 4, s)) != cudaSuccess) return e;
+        timer_begin(timer, MRF_KERNEL_OVERFLOW, s);
         wf_overflow<<<grid, kThreads, 0, s>>>(W, cur);
+        timer_end(timer, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         timer_begin(timer, MRF_KERNEL_SHADE, s);
         wf_shade<<<grid, kThreads, 0, s>>>(W, j, cur, nxt);

@@ -30,7 +30,7 @@ MRF_MAT_MIRROR, MRF_MAT_GLASS, MRF_MAT_DIFFUSE = 0, 1, 2
 MRF_LIGHT_POINT, MRF_LIGHT_AREA = 0, 1
 MRF_ENGINE_AUTO, MRF_ENGINE_MEGAKERNEL, MRF_ENGINE_WAVEFRONT = 0, 1, 2
 KERNEL_NAMES = ("render_megakernel", "wf_cast", "field", "wf_shade", "wf_finalize", "wf_gen", "wf_composite",
-                "wf_shadow_net", "wf_vis")
+                "wf_shadow_net", "wf_vis", "wf_overflow", "wf_mask")
 NO_HIT = 0xFFFFFFFF
 
 # every entry point declared in include/mrf.h
