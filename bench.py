@@ -8,8 +8,9 @@ light, fixed step sqrt(3)/1024.  Inputs are synthetic and seeded.
 
 The headline runs the mixed-precision renderer (wavefront engine, BF16 MLP on
 the tensor cores, FP32 everywhere else); the same line carries the FP32 GPU
-path (megakernel) measured the same way, the same scene at 1920x1080 (BF16
-and FP32, same protocol) under "at_1920x1080", the image error of the headline
+path (megakernel, and the FP32 wavefront engine) and the FP16 tensor-core form
+measured the same way, the same scene at 1920x1080 (BF16 and FP32, same
+protocol) under "at_1920x1080", the image error of the headline
 against the FP64 oracle on the CPU-baseline pixel sample, the per-kernel
 timings and the dominant kernel's roofline.  Prints one JSON line.
 
@@ -417,6 +418,19 @@ def run_ours(args):
             r32.close()
         r_hd.close()
         del o_hd
+    # the other tensor-core form (FP16 operands when the headline is BF16), same protocol
+    other = None
+    img_other = None
+    if not args.no_fp32 and args.precision == "bf16":
+        r16 = M.Renderer(sc, device=local, precision=M.MRF_PREC_FP16)
+        o16 = torch.empty_like(out)
+        ms16 = time_steps(torch, r16, engine, o16, stream, max(3, args.steps // 2), args.warmup, flush)
+        m16 = max_over_ranks(sum(ms16) / len(ms16), dev)
+        r16.render(out=o16, engine=engine, stream=stream.cuda_stream)
+        stream.synchronize()
+        img_other = o16.cpu().numpy().astype(np.float64)
+        other = {"precision": "fp16", "value": job_throughput(segs, world, m16), "ms_per_step": m16}
+        r16.close()
     # end to end through the C ABI: host output buffer, device->host copy inside the call
     host_out = torch.empty((sc.n_rays, 4), dtype=torch.float32).pin_memory()
     e2e_ms = []
@@ -445,6 +459,7 @@ def run_ours(args):
             "kernels": kernels,
             "roofline": roof,
             "fp32_gpu": fp32,
+            "fp16_tensor_cores": other,
             "at_1920x1080": hd,
             "bvh_traversal": cast,
             "time_vs_pixels": scaling,
@@ -464,6 +479,11 @@ def run_ours(args):
             "pixels": int(ok.sum()), "psnr_db": (10 * np.log10(peak * peak / mse)) if mse > 0 else None,
             "max_abs": float(np.abs(g - o).max()), "ambiguous_pixels_excluded": int((~ok).sum()),
             "peak": peak}
+        if img_other is not None:
+            g16 = img_other[ids][ok, :3]
+            mse16 = float(np.mean((g16 - o) ** 2))
+            other["image_error_vs_oracle"] = {"psnr_db": (10 * np.log10(peak * peak / mse16)) if mse16 > 0 else None,
+                                              "max_abs": float(np.abs(g16 - o).max())}
     if rank == 0:
         print(json.dumps(line), flush=True)
     r.close()
