@@ -431,6 +431,24 @@ def run_ours(args):
         img_other = o16.cpu().numpy().astype(np.float64)
         other = {"precision": "fp16", "value": job_throughput(segs, world, m16), "ms_per_step": m16}
         r16.close()
+    # view-dependent radiance (Instant-NGP layout: density head + colour network of
+    # the view direction's SH) on the same scene: five tensor-core layers per sample
+    vd = None
+    img_vd = None
+    if not args.no_1080p and args.precision != "fp32":
+        from paper_2309_04581_gb300 import scenes as S
+        sc_vd = S.config2_view(args.width, args.height)
+        r_vd = M.Renderer(sc_vd, device=local, precision=prec_id[args.precision])
+        o_vd = torch.empty_like(out)
+        _, st_vd = r_vd.render(out=o_vd, engine=engine, stats=True, stream=stream.cuda_stream)
+        stream.synchronize()
+        img_vd = o_vd.cpu().numpy().astype(np.float64)
+        ms_vd = time_steps(torch, r_vd, engine, o_vd, stream, max(3, args.steps // 2), args.warmup, flush)
+        m_vd = max_over_ranks(sum(ms_vd) / len(ms_vd), dev)
+        vd = {"value": job_throughput(st_vd["segments"], world, m_vd), "unit": METRIC, "ms_per_step": m_vd,
+              "field_samples_per_s": world * (st_vd["samples_evaluated"] + st_vd["shadow_samples_evaluated"]) /
+              (m_vd / 1e3), "scene": sc_vd}
+        r_vd.close()
     # end to end through the C ABI: host output buffer, device->host copy inside the call
     host_out = torch.empty((sc.n_rays, 4), dtype=torch.float32).pin_memory()
     e2e_ms = []
@@ -460,6 +478,7 @@ def run_ours(args):
             "roofline": roof,
             "fp32_gpu": fp32,
             "fp16_tensor_cores": other,
+            "view_dependent_field": vd,
             "at_1920x1080": hd,
             "bvh_traversal": cast,
             "time_vs_pixels": scaling,
@@ -479,11 +498,26 @@ def run_ours(args):
             "pixels": int(ok.sum()), "psnr_db": (10 * np.log10(peak * peak / mse)) if mse > 0 else None,
             "max_abs": float(np.abs(g - o).max()), "ambiguous_pixels_excluded": int((~ok).sum()),
             "peak": peak}
+        if vd is not None:
+            # the oracle on a sparser sample of the view-dependent scene
+            import oracle
+            from paper_2309_04581_gb300 import scenes as S
+            ids_vd = S.strided_pixels(sc.camera.width, sc.camera.height, 4 * args.cpu_stride)
+            ref_vd = oracle.render(vd["scene"], ids_vd, records=False)
+            okv = ref_vd["flags"] == 0
+            gv, ov = img_vd[ids_vd][okv, :3], ref_vd["rgba"][okv, :3]
+            pv = float(np.abs(ov).max())
+            msev = float(np.mean((gv - ov) ** 2))
+            vd["image_error_vs_oracle"] = {"pixels": int(okv.sum()),
+                                           "psnr_db": (10 * np.log10(pv * pv / msev)) if msev > 0 else None,
+                                           "max_abs": float(np.abs(gv - ov).max())}
         if img_other is not None:
             g16 = img_other[ids][ok, :3]
             mse16 = float(np.mean((g16 - o) ** 2))
             other["image_error_vs_oracle"] = {"psnr_db": (10 * np.log10(peak * peak / mse16)) if mse16 > 0 else None,
                                               "max_abs": float(np.abs(g16 - o).max())}
+    if vd is not None:
+        vd.pop("scene", None)
     if rank == 0:
         print(json.dumps(line), flush=True)
     r.close()
