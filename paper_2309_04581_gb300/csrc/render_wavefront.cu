@@ -364,7 +364,7 @@ __device__ __forceinline__ V3 shfl3(V3 v, int src) {
 // ray per hit its visibility is traced here; with more, the rays are stored
 // with sw.w = -1 (marched) or -2 (network) and wf_vis traces them, one thread
 // per ray, instead of one thread tracing up to 64 of them in turn.
-__global__ void __launch_bounds__(kThreads) wf_cast(const WfParams W, uint32_t j, int cur) {
+__global__ void __launch_bounds__(kThreads, 5) wf_cast(const WfParams W, uint32_t j, int cur) {
     const RenderParams &P = W.R;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t live = j == 1 ? W.paths : W.ctr[cur];
@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(kThreads) wf_cast(const WfParams W, uint32_t j
 // for wf_shadow_net) and counts in its slot's hp.w; a blocked one gets sw = 0.
 // hp.w keeps the kDeferred bit, so the slot reads as having shadow rays and the
 // later kernels look at each ray's sw.w.
-__global__ void __launch_bounds__(kThreads) wf_vis(const WfParams W, int cur) {
+__global__ void __launch_bounds__(kThreads, 5) wf_vis(const WfParams W, int cur) {
     const RenderParams &P = W.R;
     const uint32_t K = (uint32_t)P.n_shadow;
     const uint64_t total = (uint64_t)W.ctr[cur] * K;
