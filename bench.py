@@ -10,9 +10,11 @@ The headline runs the mixed-precision renderer (wavefront engine, BF16 MLP on
 the tensor cores, FP32 everywhere else); the same line carries the FP32 GPU
 path (megakernel, and the FP32 wavefront engine) and the FP16 tensor-core form
 measured the same way, the same scene at 1920x1080 (BF16 and FP32, same
-protocol) under "at_1920x1080", the image error of the headline
-against the FP64 oracle on the CPU-baseline pixel sample, the per-kernel
-timings and the dominant kernel's roofline.  Prints one JSON line.
+protocol) under "at_1920x1080", the render time at 200^2, 400^2 and 800^2
+pixels, the view-dependent field on the same scene, the BVH traversal counts,
+the image error of the headline against the FP64 oracle on the CPU-baseline
+pixel sample, the per-kernel timings and the dominant kernel's roofline.
+Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp16|fp32]
     python bench.py --impl reference    # the FP64 CPU oracle on the host cores
@@ -57,7 +59,9 @@ def parse():
     ap.add_argument("--cpu-stride", type=int, default=4, help="oracle sample: every n-th row and column")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 comparison run")
-    ap.add_argument("--no-1080p", action="store_true", help="skip the 1920x1080 run of the same scene")
+    ap.add_argument("--no-1080p", action="store_true",
+                    help="skip the extra measurements: the scene at 1920x1080, time against pixel count and the "
+                         "view-dependent field")
     ap.add_argument("--workload", default="hashgrid", choices=["hashgrid", "dynamic", "area", "views"],
                     help="dynamic: the deforming-mesh sequence (per-frame refit, rebuild every --rebuild frames); "
                          "area: 4 area lights x 16 shadow rays, marched against the learned transmittance")
