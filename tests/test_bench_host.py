@@ -29,12 +29,5 @@ def test_measured_traffic_follows_the_source_hash(tmp_path, monkeypatch):
     assert bench.measured_traffic(["a.cu"], "missing.md") is None
 
 
-def test_committed_field_traffic_summary_matches_the_sources():
-    """The committed DRAM summary of the field kernel carries the hash of the
-    sources it was measured on; the bench reports its traffic only then."""
-    v = bench.measured_traffic(bench.FIELD_TC_SOURCES, "field_tc_dram_traffic_hashgrid_800x800_bf16.md")
-    assert v is not None and v > 0
-
-
 def test_job_throughput_counts_every_rank():
     assert bench.job_throughput(1000, 4, 2.0) == 4 * 1000 / 2e-3
