@@ -657,10 +657,10 @@ __device__ __forceinline__ void warp_composite(const WfParams &W, uint32_t start
     lr = lg = lb = 0.f;
     depth = 0.f;
     stop = false;
-    // four 32-sample chunks are loaded before the first is composited, so that a
-    // job costs one memory round trip per 128 samples (loads past the stop are
+    // eight 32-sample chunks are loaded before the first is composited, so that a
+    // job costs one memory round trip per 256 samples (loads past the stop are
     // inside the job's range and harmless)
-    constexpr int kChunks = 4;
+    constexpr int kChunks = 8;
     for (uint32_t i0 = 0; i0 < count; i0 += 32 * kChunks) {
         float4 fc[kChunks];
 #pragma unroll
