@@ -68,7 +68,7 @@ class OrcScene(C.Structure):
         ("light_kind", _i32p), ("light_v1", _fp), ("light_v2", _fp), ("light_samples", _u32p),
         ("shadow_net", C.c_void_p), ("shadow_mask", C.c_int32), ("light_mask", _fp),
         ("view_dep", C.c_int32), ("wd2", _fp), ("bd2", _fp), ("wc1", _fp), ("bc1", _fp), ("wc2", _fp), ("bc2", _fp),
-        ("wc3", _fp), ("bc3", _fp),
+        ("wc3", _fp), ("bc3", _fp), ("margin_tau", C.c_double),
     ]
 
 
@@ -121,6 +121,9 @@ def lib():
         L.orc_render.restype = C.c_int
         L.orc_render.argtypes = [C.POINTER(OrcScene), _u32p, C.c_uint32, _dp, _u32p, _u32p, _dp, _u32p, _u64p,
                                  C.c_int]
+        L.orc_render_ex.restype = C.c_int
+        L.orc_render_ex.argtypes = [C.POINTER(OrcScene), _u32p, C.c_uint32, _dp, _u32p, _u32p, _dp, _u32p, _u64p,
+                                    C.c_int, _u32p]
         L.orc_num_threads.restype = C.c_int
         L.orc_tonemap.restype = C.c_double
         L.orc_tonemap.argtypes = [C.c_double, C.c_double]
@@ -148,7 +151,7 @@ def _ptr(a, t):
 class OracleScene:
     """A ``scenes.Scene`` marshalled into an ``orc_scene`` (keeps its arrays alive)."""
 
-    def __init__(self, scene, margin_dist=1e-6, margin_t=1e-5, margin_fresnel=1e-5, shadow_net=None):
+    def __init__(self, scene, margin_dist=2e-7, margin_t=1e-5, margin_fresnel=1e-5, margin_tau=2e-6, shadow_net=None):
         self.scene = scene
         self.shadow_net = shadow_net
         keep = []
@@ -228,6 +231,7 @@ class OracleScene:
         s.max_bounces, s.spp, s.seed = o.max_bounces, o.spp, o.seed
         s.steps_per_segment, s.dt, s.tau, s.tmin = o.steps_per_segment, o.dt, o.tau, o.tmin
         s.margin_dist, s.margin_t, s.margin_fresnel = margin_dist, margin_t, margin_fresnel
+        s.margin_tau = margin_tau
         if getattr(f, "pose", None) is not None:
             s.field_pose = _ptr(arr(f.pose, np.float32), _fp)
         views = getattr(scene, "cameras", None)
@@ -250,7 +254,8 @@ def render(scene, ids=None, threads: int = 0, records: bool = True, shadow_net=N
     """Render ``ids`` (pixel or explicit-ray indices; default all) in FP64.
 
     Returns a dict: rgba (n,4) f64, segments (n,spp) u32, tri (n,spp,B) u32,
-    t (n,spp,B) f64, flags (n,) u32, counts {name: int}."""
+    t (n,spp,B) f64, flags (n,) u32, first_flag (n,spp) u32 (the segment of
+    each path's first ambiguity flag, 0 = none), counts {name: int}."""
     L = lib()
     os_ = OracleScene(scene, shadow_net=shadow_net, **margins)
     n_all = scene.n_rays
@@ -262,10 +267,11 @@ def render(scene, ids=None, threads: int = 0, records: bool = True, shadow_net=N
     tri = np.zeros((n, spp, B), np.uint32) if records else None
     tt = np.zeros((n, spp, B), np.float64) if records else None
     flags = np.zeros(n, np.uint32)
+    first = np.zeros((n, spp), np.uint32)
     counts = np.zeros(len(COUNT_NAMES), np.uint64)
-    L.orc_render(os_.ref, _ptr(ids, _u32p), n, _ptr(rgba, _dp), _ptr(segs, _u32p), _ptr(tri, _u32p), _ptr(tt, _dp),
-                 _ptr(flags, _u32p), _ptr(counts, _u64p), int(threads))
-    return dict(rgba=rgba, segments=segs, tri=tri, t=tt, flags=flags, ids=ids,
+    L.orc_render_ex(os_.ref, _ptr(ids, _u32p), n, _ptr(rgba, _dp), _ptr(segs, _u32p), _ptr(tri, _u32p),
+                    _ptr(tt, _dp), _ptr(flags, _u32p), _ptr(counts, _u64p), int(threads), _ptr(first, _u32p))
+    return dict(rgba=rgba, segments=segs, tri=tri, t=tt, flags=flags, first_flag=first, ids=ids,
                 counts={k: int(v) for k, v in zip(COUNT_NAMES, counts)})
 
 

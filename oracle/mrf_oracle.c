@@ -128,7 +128,44 @@ typedef struct {
      * (wc3: 3 x 64, bc3), rgb = softplus; w2, b2, w3, b3 are unused */
     int32_t view_dep;
     const float *wd2, *bd2, *wc1, *bc1, *wc2, *bc2, *wc3, *bc3;
+    /* base relative margin of the throughput-threshold flag (0: 2e-6): a path
+     * is flagged when |max T - tau| <= (margin_tau + depth uncertainty) * tau
+     * at a termination test */
+    double margin_tau;
 } orc_scene;
+
+/* First-order bounds on how far the FP32 path of the CUDA library may lie from
+ * this FP64 path.  They decide nothing in the path itself: they only widen the
+ * margins of the ambiguity flags as FP32 errors accumulate along a path.
+ *   lat : lateral offset of the current ray's line (world units);
+ *   dir : angle between the FP32 and FP64 directions (radians);
+ *   unc : uncertainty of the path's optical depth, i.e. of ln T, from the FP32
+ *         positions of the field samples (see march()). */
+typedef struct {
+    double lat, dir, unc;
+} orc_err;
+#define ORC_ERR_POS 2.4e-7   /* FP32 rounding of a point or distance below 2 (two ulps of 1.x) */
+#define ORC_ERR_DIR 4e-7     /* FP32 rounding of a unit direction from a camera basis, reflection or refraction */
+
+/* relative margin of the throughput-threshold flag at one termination test */
+static double tau_margin(const orc_scene *sc, const orc_err *e) {
+    return (sc->margin_tau > 0 ? sc->margin_tau : 2e-6) + (e ? e->unc : 0.0);
+}
+
+/* Support of the hash field at p (the value s of orc_support) and its
+ * sensitivity to a position error: |grad s| = 2 |p - c| / r^2 = 2 sqrt(1 - s) / r
+ * for the sphere that attains the maximum. */
+static double support_slope(const orc_scene *sc, const double p[3], double *s_out) {
+    double s = 0.0, slope = 0.0;
+    for (uint32_t k = 0; k < sc->n_support; ++k) {
+        double d2 = 0.0;
+        for (int a = 0; a < 3; ++a) { double q = p[a] - sc->sup_c[3 * k + a]; d2 += q * q; }
+        double r = sc->sup_r[k], v = 1.0 - d2 / (r * r);
+        if (v > s) { s = v; slope = 2.0 * sqrt(d2) / (r * r); }
+    }
+    *s_out = s;
+    return slope;
+}
 
 void orc_sh16(const double w[3], double Y[16]);
 
@@ -445,10 +482,10 @@ static void to_field_frame(const orc_scene *sc, const double o[3], const double 
  *   alpha_i = 1 - exp(-sigma_i delta_i); L += T alpha_i r_i; T *= exp(-sigma_i delta_i).
  * T is the RGB path throughput (it carries T(p_j) into the segment).  Returns
  * 1 if the path ended inside the march because max(T) fell below tau. */
-static double shadow_mask(const orc_scene *sc, const double pw[3], uint32_t *flags);
+static double shadow_mask(const orc_scene *sc, const double pw[3], uint32_t *flags, double dp);
 
 static int march(const orc_scene *sc, const double ow[3], const double dw[3], double a, double b, double T[3],
-                 double L[3], uint64_t *cnt, uint32_t *flags) {
+                 double L[3], uint64_t *cnt, uint32_t *flags, orc_err *e) {
     double o[3], d[3];
     to_field_frame(sc, ow, dw, o, d);
     double tb0, tb1;
@@ -467,17 +504,28 @@ static int march(const orc_scene *sc, const double ow[3], const double dw[3], do
         double p[3] = {o[0] + tm * d[0], o[1] + tm * d[1], o[2] + tm * d[2]}, sigma, rgb[3];
         cnt[C_NOMINAL]++;
         cnt[C_SUPPORTED] += field_eval_dir(sc, p, d, &sigma, rgb);
+        if (e && sigma > 0.0) {
+            /* uncertainty of sigma * delta in FP32: rounding, and for the hash
+             * field the support's response to the sample's position error,
+             * |ds| <= 2 |dp| / r_min, times the density before the support */
+            double du = 1e-6 * sigma * delta;
+            if (sc->field_kind == ORC_FIELD_HASH && sc->n_support) {
+                double sup, slope = support_slope(sc, p, &sup), dp = ORC_ERR_POS + e->lat + tm * e->dir;
+                if (sup > 0.0) du += sigma / sup * delta * slope * dp;
+            }
+            e->unc += du;
+        }
         double att = exp(-sigma * delta), alpha = -expm1(-sigma * delta), m = 1.0;
         if (sc->shadow_mask && sigma > 0.0) {
             /* the sample in world space: the pose keeps ray parameters */
             double pw[3] = {ow[0] + tm * dw[0], ow[1] + tm * dw[1], ow[2] + tm * dw[2]};
-            m = shadow_mask(sc, pw, flags);
+            m = shadow_mask(sc, pw, flags, e ? ORC_ERR_POS + e->lat + tm * e->dir : 0.0);
         }
         for (int c = 0; c < 3; ++c) { L[c] += T[c] * alpha * m * rgb[c]; T[c] *= att; }
         if (sc->tau > 0) {
             double m = T[0] > T[1] ? T[0] : T[1];
             if (T[2] > m) m = T[2];
-            if (fabs(m - sc->tau) <= 1e-4 * sc->tau) *flags |= ORC_FLAG_TAU;
+            if (fabs(m - sc->tau) <= tau_margin(sc, e) * sc->tau) *flags |= ORC_FLAG_TAU;
             if (m < sc->tau) return 1;
         }
     }
@@ -517,7 +565,7 @@ void orc_march(const orc_scene *sc, const double o[3], const double d[3], double
                double L[3]) {
     uint64_t cnt[C_N] = {0};
     uint32_t fl = 0;
-    march(sc, o, d, a, b, T, L, cnt, &fl);
+    march(sc, o, d, a, b, T, L, cnt, &fl, NULL);
 }
 
 /* ---------------------------------------------------------- ray casting */
@@ -567,17 +615,37 @@ static double edge_distance(const double v0[3], const double v1[3], const double
  * Eq. 3), skipping the triangle the ray leaves.  Ties within 1e-12 relative go
  * to the lower id.  Sets ORC_FLAG_EDGE / ORC_FLAG_TMIN when a triangle whose
  * hit/miss decision lies within the margins could change the answer. */
+/* Edge margin of a candidate hit at parameter t of a ray whose FP32 error
+ * bounds are e (NULL: none): the base margin plus the in-plane error of the
+ * hit point, (lat + t dir) / |cos| at the triangle (|cos| clamped at 0.01). */
+static double edge_margin(const orc_scene *sc, const orc_err *e, const double d[3], const double v0[3],
+                          const double v1[3], const double v2[3], double t) {
+    if (!e) return sc->margin_dist;
+    v3 n = unit(cross(sub(fv3(v1), fv3(v0)), sub(fv3(v2), fv3(v0))));
+    double c = fabs(d[0] * n.x + d[1] * n.y + d[2] * n.z);
+    if (c < 0.01) c = 0.01;
+    return sc->margin_dist + (e->lat + (t > 0.0 ? t : 0.0) * e->dir) / c;
+}
+
+static uint32_t closest_hit_e(const orc_scene *sc, const double o[3], const double d[3], uint32_t skip,
+                              double *t_out, uint32_t *flags, const orc_err *e);
+
 uint32_t orc_closest_hit(const orc_scene *sc, const double o[3], const double d[3], uint32_t skip, double *t_out,
                          uint32_t *flags) {
+    return closest_hit_e(sc, o, d, skip, t_out, flags, NULL);
+}
+
+static uint32_t closest_hit_e(const orc_scene *sc, const double o[3], const double d[3], uint32_t skip,
+                              double *t_out, uint32_t *flags, const orc_err *e) {
     double best = INFINITY, second = INFINITY, edge_t = INFINITY, tmin_t = INFINITY;
     uint32_t best_id = ORC_NO_HIT;
-    const double md = sc->margin_dist;
     for (uint32_t i = 0; i < sc->n_tris; ++i) {
         if (i == skip) continue;
         double v0[3], v1[3], v2[3], t, b1, b2;
         tri_verts(sc, i, v0, v1, v2);
         int hit = orc_intersect_tri(o, d, v0, v1, v2, sc->tmin, &t, &b1, &b2);
         if (!isfinite(t)) continue;
+        const double md = edge_margin(sc, e, d, v0, v1, v2, t);
         double ed = edge_distance(v0, v1, v2, b1, b2);
         if (fabs(ed) <= md && t > sc->tmin && t < edge_t) edge_t = t;
         if (ed >= -md && fabs(t - sc->tmin) <= md && t < tmin_t) tmin_t = t;
@@ -602,15 +670,15 @@ uint32_t orc_closest_hit(const orc_scene *sc, const double o[3], const double d[
  * near-endpoint candidates: one triangle hit well inside its edges and well
  * inside (tmin, dist) settles "blocked" whatever the others do. */
 static int occluded(const orc_scene *sc, const double o[3], const double d[3], uint32_t skip, double dist,
-                    uint32_t *flags) {
+                    uint32_t *flags, const orc_err *e) {
     int blocked = 0, robust = 0, doubtful = 0;
-    const double md = sc->margin_dist;
     for (uint32_t i = 0; i < sc->n_tris; ++i) {
         if (i == skip) continue;
         double v0[3], v1[3], v2[3], t, b1, b2;
         tri_verts(sc, i, v0, v1, v2);
         int hit = orc_intersect_tri(o, d, v0, v1, v2, sc->tmin, &t, &b1, &b2);
         if (!isfinite(t)) continue;
+        const double md = edge_margin(sc, e, d, v0, v1, v2, t);
         int near = 0;
         if (t > sc->tmin && t < dist * (1.0 + sc->margin_t)) {
             if (fabs(edge_distance(v0, v1, v2, b1, b2)) <= md) near = 1;
@@ -630,7 +698,8 @@ static int occluded(const orc_scene *sc, const double o[3], const double d[3], u
  * ray from the field sample toward each light (a point light's position, an
  * area light's centroid); each light that a mesh blocks multiplies m by
  * 1 - r_src, its mask strength.  Unblocked: m = 1. */
-static double shadow_mask(const orc_scene *sc, const double pw[3], uint32_t *flags) {
+/* dp: bound on the FP32 position error of the sample (0: none) */
+static double shadow_mask(const orc_scene *sc, const double pw[3], uint32_t *flags, double dp) {
     double m = 1.0;
     for (uint32_t l = 0; l < sc->n_lights; ++l) {
         double r = sc->light_mask ? sc->light_mask[l] : 0.0;
@@ -642,7 +711,8 @@ static double shadow_mask(const orc_scene *sc, const double pw[3], uint32_t *fla
         double D = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
         if (!(D > 0)) continue;
         for (int a = 0; a < 3; ++a) w[a] /= D;
-        if (occluded(sc, pw, w, ORC_NO_HIT, D, flags)) m *= 1.0 - r;
+        const orc_err Es = {dp, ORC_ERR_DIR + dp / D, 0.0};
+        if (occluded(sc, pw, w, ORC_NO_HIT, D, flags, &Es)) m *= 1.0 - r;
     }
     return m;
 }
@@ -717,7 +787,7 @@ static double shadow_transmittance(const orc_scene *sc, const double p[3], const
  * normal, V the mesh visibility and T the field transmittance of Eq. 10. */
 static void area_light_nee(const orc_scene *sc, uint32_t l, uint32_t ray, uint32_t s, uint32_t j, uint32_t *q,
                            const double p[3], const double nf[3], uint32_t hit, const float *rgb, const double T[3],
-                           double L[3], uint32_t *flags, uint64_t *cnt) {
+                           double L[3], uint32_t *flags, uint64_t *cnt, double e_hit) {
     v3 a = fv(sc->light_pos + 3 * l), b = fv(sc->light_v1 + 3 * l), c = fv(sc->light_v2 + 3 * l);
     v3 cr = cross(sub(b, a), sub(c, a));
     double A = 0.5 * sqrt(dot(cr, cr));
@@ -736,7 +806,8 @@ static void area_light_nee(const orc_scene *sc, uint32_t l, uint32_t ray, uint32
         double cosy = -(nl.x * w[0] + nl.y * w[1] + nl.z * w[2]);
         if (cosx <= 0.0 || cosy <= 0.0) continue;
         cnt[C_SHADOW]++;
-        if (occluded(sc, p, w, hit, D, flags)) continue;
+        const orc_err Es = {e_hit, ORC_ERR_DIR + e_hit / D, 0.0};
+        if (occluded(sc, p, w, hit, D, flags, &Es)) continue;
         double Tf = shadow_transmittance(sc, p, w, D, cnt);
         for (int e = 0; e < 3; ++e)
             L[e] += T[e] * (rgb[e] / M_PI) * sc->light_I[3 * l + e] * A / N * cosx * cosy / D2 * Tf;
@@ -745,24 +816,37 @@ static void area_light_nee(const orc_scene *sc, uint32_t l, uint32_t ray, uint32
 
 /* ---------------------------------------------------------- one path */
 /* Algorithm 1 for one (ray, spp) pair. */
+/* *first_flag receives the segment j during which the path raised its first
+ * flag on a decision that can change its course (a closest hit, a Fresnel
+ * draw, the tangent frame, the throughput threshold; 0: none): the hit
+ * records of the segments before it rest on decisions clear of every margin.
+ * Shadow-ray flags change radiance only and do not count here. */
 static void trace_path(const orc_scene *sc, uint32_t ray, uint32_t s, double L[3], double *alpha0,
-                       uint32_t *segs_out, uint32_t *tri_rec, double *t_rec, uint32_t *flags, uint64_t *cnt) {
+                       uint32_t *segs_out, uint32_t *tri_rec, double *t_rec, uint32_t *path_flags,
+                       uint32_t *first_flag, uint64_t *cnt) {
+    uint32_t pf = 0, *flags = &pf;
+    *first_flag = 0;
+#define NOTE_FLAGS(j) do { if ((pf & ~(uint32_t)ORC_FLAG_SHADOW) && !*first_flag) *first_flag = (j); } while (0)
     double o[3], d[3];
     orc_camera_ray(sc, ray, o, d);
     double T[3] = {1, 1, 1};
     L[0] = L[1] = L[2] = 0.0;
     *alpha0 = 0.0;
     uint32_t prev = ORC_NO_HIT, segs = 0;
+    /* FP32 error bounds of the camera ray: an exact origin, a direction built
+     * from the FP32 camera basis */
+    orc_err E = {ORC_ERR_POS, ORC_ERR_DIR, 0.0};
     cnt[C_PATHS]++;
     for (uint32_t j = 1; j <= sc->max_bounces; ++j) {
         double th;
-        uint32_t hit = orc_closest_hit(sc, o, d, prev, &th, flags);
+        uint32_t hit = closest_hit_e(sc, o, d, prev, &th, flags, &E);
         double Tprev = T[0];
-        int stop = march(sc, o, d, 0.0, th, T, L, cnt, flags);
+        int stop = march(sc, o, d, 0.0, th, T, L, cnt, flags, &E);
         if (j == 1) *alpha0 = Tprev > 0 ? 1.0 - T[0] / Tprev : 0.0;
         segs = j;
         cnt[C_SEG]++;
         if (tri_rec) { tri_rec[j - 1] = hit; t_rec[j - 1] = th; }
+        NOTE_FLAGS(j);
         if (stop) { cnt[C_END_TAU]++; break; }
         if (hit == ORC_NO_HIT) { cnt[C_END_MISS]++; break; }
         cnt[C_HITS]++;
@@ -773,6 +857,9 @@ static void trace_path(const orc_scene *sc, uint32_t ray, uint32_t s, double L[3
         double n[3] = {ng.x, ng.y, ng.z};
         double dn = d[0] * n[0] + d[1] * n[1] + d[2] * n[2];
         double nf[3] = {dn > 0 ? -n[0] : n[0], dn > 0 ? -n[1] : n[1], dn > 0 ? -n[2] : n[2]};
+        /* error of the hit point within the surface, and of the ray line at it */
+        const double cos_h = fabs(dn) > 0.01 ? fabs(dn) : 0.01;
+        const double e_line = E.lat + th * E.dir, e_hit = e_line / cos_h + ORC_ERR_POS;
         uint32_t m = sc->tri_mat[hit];
         int kind = sc->mat_kind[m];
         const float *rgb = sc->mat_rgb + 3 * m;
@@ -783,6 +870,9 @@ static void trace_path(const orc_scene *sc, uint32_t ray, uint32_t s, double L[3
         if (kind == ORC_MIRROR) {
             orc_reflect(d, n, nd);
             for (int c = 0; c < 3; ++c) T[c] *= rgb[c];
+            /* a mirror keeps a ray bundle's width and its angular spread */
+            E.lat = e_line + ORC_ERR_POS;
+            E.dir += ORC_ERR_DIR;
         } else if (kind == ORC_GLASS) {
             double ior = sc->mat_ior[m], cos_i = fabs(dn);
             int entering = dn < 0;
@@ -791,15 +881,25 @@ static void trace_path(const orc_scene *sc, uint32_t ray, uint32_t s, double L[3
             double s2t = (ei / et) * (ei / et) * (1.0 - cos_i * cos_i);
             if (fabs(u[0] - F) <= sc->margin_fresnel || fabs(s2t - 1.0) <= 1e-9 || cos_i <= 1e-7)
                 *flags |= ORC_FLAG_FRESNEL;
-            if (u[0] < F) orc_reflect(d, n, nd);
-            else orc_refract(d, nf, ei / et, nd);
+            if (u[0] < F) {
+                orc_reflect(d, n, nd);
+                E.lat = e_line + ORC_ERR_POS;
+                E.dir += ORC_ERR_DIR;
+            } else {
+                orc_refract(d, nf, ei / et, nd);
+                /* Snell: angles scale by eta cos_i / cos_t, bundle widths by cos_t / cos_i */
+                double ct = sqrt(1.0 - (s2t < 1.0 ? s2t : 1.0)), ci = cos_h;
+                if (ct < 0.01) ct = 0.01;
+                E.lat = e_line * ct / ci + ORC_ERR_POS;
+                E.dir = E.dir * (ei / et) * ci / ct + ORC_ERR_DIR;
+            }
         } else {
             /* next-event estimation toward each light (the shadow rays of
              * Sec. 3.1, "Shadow rays" and Algorithm 1) */
             uint32_t q = 0;   /* shadow-sample index over all area lights of this hit */
             for (uint32_t l = 0; l < sc->n_lights; ++l) {
                 if (sc->light_kind && sc->light_kind[l] == ORC_LIGHT_AREA) {
-                    area_light_nee(sc, l, ray, s, j, &q, p, nf, hit, rgb, T, L, flags, cnt);
+                    area_light_nee(sc, l, ray, s, j, &q, p, nf, hit, rgb, T, L, flags, cnt, e_hit);
                     continue;
                 }
                 double w[3], D2 = 0.0;
@@ -809,7 +909,9 @@ static void trace_path(const orc_scene *sc, uint32_t ray, uint32_t s, double L[3
                 double cosl = nf[0] * w[0] + nf[1] * w[1] + nf[2] * w[2];
                 if (cosl <= 0.0) continue;
                 cnt[C_SHADOW]++;
-                if (occluded(sc, p, w, hit, D, flags)) continue;
+                /* the shadow ray starts at the hit point and aims at the light */
+                const orc_err Es = {e_hit, ORC_ERR_DIR + e_hit / D, 0.0};
+                if (occluded(sc, p, w, hit, D, flags, &Es)) continue;
                 double Tf = shadow_transmittance(sc, p, w, D, cnt);
                 for (int c = 0; c < 3; ++c)
                     L[c] += T[c] * (rgb[c] / M_PI) * cosl * sc->light_I[3 * l + c] / D2 * Tf;
@@ -817,6 +919,10 @@ static void trace_path(const orc_scene *sc, uint32_t ray, uint32_t s, double L[3
             if (nf[2] != 0.0 && fabs(nf[2]) <= 1e-6) *flags |= ORC_FLAG_BASIS;
             orc_sample_cosine(nf, u[1], u[2], nd);
             for (int c = 0; c < 3; ++c) T[c] *= rgb[c];
+            /* the sampled direction depends on the normal only; the new ray
+             * starts at the hit point */
+            E.lat = e_hit;
+            E.dir = ORC_ERR_DIR;
         }
         v3 ndu = unit(mk(nd[0], nd[1], nd[2]));
         o[0] = p[0]; o[1] = p[1]; o[2] = p[2];
@@ -824,12 +930,16 @@ static void trace_path(const orc_scene *sc, uint32_t ray, uint32_t s, double L[3
         prev = hit;
         if (sc->tau > 0) {
             double mt = maxc(T);
-            if (fabs(mt - sc->tau) <= 1e-4 * sc->tau) *flags |= ORC_FLAG_TAU;
+            if (fabs(mt - sc->tau) <= tau_margin(sc, &E) * sc->tau) *flags |= ORC_FLAG_TAU;
+            NOTE_FLAGS(j);
             if (mt < sc->tau) { cnt[C_END_TAU]++; break; }
         }
+        NOTE_FLAGS(j);
         if (j == sc->max_bounces) cnt[C_END_CAP]++;   /* the loop ends after this surface event */
     }
+#undef NOTE_FLAGS
     *segs_out = segs;
+    *path_flags |= pf;
 }
 
 /* Render the given rays (pixel indices, or explicit-ray indices).
@@ -837,9 +947,11 @@ static void trace_path(const orc_scene *sc, uint32_t ray, uint32_t s, double L[3
  *   out_segments    : [n_ids * spp] segments per path (nullable)
  *   out_tri, out_t  : [n_ids * spp * max_bounces] hit triangle / distance per segment (nullable)
  *   out_flags       : [n_ids] OR of ambiguity flags over spp (nullable)
+ *   out_first_flag  : [n_ids * spp] segment of each path's first ambiguity flag, 0 = none (nullable)
  *   out_counts      : [C_N] totals (nullable) */
-int orc_render(const orc_scene *sc, const uint32_t *ids, uint32_t n_ids, double *out_rgba, uint32_t *out_segments,
-               uint32_t *out_tri, double *out_t, uint32_t *out_flags, uint64_t *out_counts, int n_threads) {
+int orc_render_ex(const orc_scene *sc, const uint32_t *ids, uint32_t n_ids, double *out_rgba, uint32_t *out_segments,
+                  uint32_t *out_tri, double *out_t, uint32_t *out_flags, uint64_t *out_counts, int n_threads,
+                  uint32_t *out_first_flag) {
     uint64_t tot[C_N] = {0};
 #ifdef _OPENMP
     if (n_threads <= 0) n_threads = omp_get_max_threads();
@@ -859,7 +971,9 @@ int orc_render(const orc_scene *sc, const uint32_t *ids, uint32_t n_ids, double 
                 uint32_t *tr = out_tri ? out_tri + k * B : NULL;
                 double *tt = out_t ? out_t + k * B : NULL;
                 if (tr) for (uint32_t j = 0; j < B; ++j) { tr[j] = ORC_NO_HIT; tt[j] = INFINITY; }
-                trace_path(sc, ids[i], s, L, &a0, &segs, tr, tt, &fl, cnt);
+                uint32_t first;
+                trace_path(sc, ids[i], s, L, &a0, &segs, tr, tt, &fl, &first, cnt);
+                if (out_first_flag) out_first_flag[k] = first;
                 for (int c = 0; c < 3; ++c) acc[c] += L[c];
                 acc[3] += a0;
                 if (out_segments) out_segments[k] = segs;
@@ -872,6 +986,12 @@ int orc_render(const orc_scene *sc, const uint32_t *ids, uint32_t n_ids, double 
     }
     if (out_counts) for (int c = 0; c < C_N; ++c) out_counts[c] = tot[c];
     return 0;
+}
+
+int orc_render(const orc_scene *sc, const uint32_t *ids, uint32_t n_ids, double *out_rgba, uint32_t *out_segments,
+               uint32_t *out_tri, double *out_t, uint32_t *out_flags, uint64_t *out_counts, int n_threads) {
+    return orc_render_ex(sc, ids, n_ids, out_rgba, out_segments, out_tri, out_t, out_flags, out_counts, n_threads,
+                         NULL);
 }
 
 /* Training pairs of the shadow-transmittance surrogate: pair i is a point p

@@ -90,7 +90,7 @@ def test_autotuner_picks_a_candidate_and_keeps_results(env):
     torch, M = env
     sc = S.config2(256, 256)
     r = M.Renderer(sc, precision=M.MRF_PREC_BF16)
-    assert r.tuning() == {"field_groups": 8, "samples_per_path": 96, "rounds": 1}
+    assert r.tuning() == {"field_groups": 8, "samples_per_path": 96, "rounds": 1, "tail_paths": 0}
     before, st0 = r.render(stats=True)
     best, ms = r.autotune(reps=2)
     assert best == r.tuning()
@@ -111,14 +111,24 @@ def test_autotuner_picks_a_candidate_and_keeps_results(env):
     r.close()
 
 
-def test_mirror_room_views_match_oracle(env, orc):
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_mirror_room_views_match_oracle(env, orc, prec):
     """The batched-view workload at a tiny scale: five views of uneven size in a
     mirror room with displaced spheres and a cloth, 16 segments per path,
-    through a captured frame after a cloth refit, against the oracle."""
+    through a captured frame after a cloth refit, against the oracle.
+
+    Every segment of a 16-bounce mirror path carries the FP32 error of all
+    the bounces before it (the angular error grows by every reflection, the
+    lateral one by the distance travelled times the angular one), so the
+    oracle's error bound reaches the edges of the spheres' small facets on a
+    fifth of the paths, mostly in their late segments.  Hence: on every pixel
+    the hit ids of all segments before the path's first flagged decision; on
+    unflagged pixels every segment's hit id, the segment counts and the
+    radiance (FP32: 1e-4 per pixel; BF16: >= 45 dB and <= 1e-2 max abs)."""
     torch, M = env
-    from tests.test_gpu_parity import _compare, RTOL_PIX
+    from tests.test_gpu_parity import _compare, _trusted
     mv = S.MultiViewScene(n_views=5, scale=0.02)   # 25x16, 25x16, 23x15, 17x12, 8x7
-    r = M.Renderer(mv.scene)
+    r = M.Renderer(mv.scene, precision=M.MRF_PREC_FP32 if prec == "fp32" else M.MRF_PREC_BF16)
     v = mv.vertices(5)
     r.set_vertices(v)
     out = torch.empty((mv.scene.n_rays, 4), dtype=torch.float32, device="cuda")
@@ -135,15 +145,36 @@ def test_mirror_room_views_match_oracle(env, orc):
                segments=rec["segments"].cpu().numpy().view(np.uint32).reshape(-1, 1),
                tri=rec["tri"].cpu().numpy().view(np.uint32).reshape(-1, 1, B),
                t=rec["t"].cpu().numpy().reshape(-1, 1, B))
-    # The image at the FP32 bar.  Hit records are compared over the first 4
-    # segments: after many mirror bounces off curved, finely tessellated spheres
-    # the FP32 and FP64 paths drift apart by more than the oracle's 1e-6 edge
-    # margin, and a late hit may land on the neighbouring triangle of the same
-    # surface (same radiance, different id).
-    _compare(gpu, ref, max_flag_frac=2e-2, check_records=False)
     ok = ref["flags"] == 0
-    assert np.array_equal(gpu["tri"][ok][:, :, :4], ref["tri"][ok][:, :, :4])
+    frac = float((~ok).mean())
+    print(f"{prec}: {frac:.1%} of the pixels flagged; first flagged segment histogram "
+          f"{np.bincount(ref['first_flag'][:, 0], minlength=B + 1).tolist()}")
+    assert frac <= 0.3
     assert ref["segments"].mean() > 8     # long mirror-room paths
+    tr = _trusted(ref)
+    assert tr.mean() > 0.8
+    assert np.array_equal(np.where(tr, gpu["tri"], 0), np.where(tr, ref["tri"], 0))
+    assert np.array_equal(gpu["tri"][ok], ref["tri"][ok])
+    assert np.array_equal(gpu["segments"][ok], ref["segments"][ok])
+    if prec == "fp32":
+        # hit distances: the 1e-5 relative bar on the camera segment; later ones
+        # carry the FP32 error of every bounce before them (the hit point's
+        # bound reaches about 5e-5 world units after 16 mirror bounces) and are
+        # held to 1e-4 absolute
+        _compare(gpu, ref, max_flag_frac=0.3, t_segments=1)
+        tg, to = gpu["t"][ok], ref["t"][ok]
+        fin = np.isfinite(to)
+        assert np.array_equal(np.isfinite(tg), fin)
+        dt = np.where(fin, np.abs(np.where(fin, tg, 0) - np.where(fin, to, 0)), 0)
+        print("fp32 mirror room: largest hit-distance difference per segment",
+              [f"{x:.2g}" for x in dt.max(axis=(0, 1))])
+        assert dt.max() <= 1e-4
+    else:
+        a, b = gpu["rgba"][ok, :3], ref["rgba"][ok, :3]
+        peak = np.abs(b).max()
+        psnr = 10 * np.log10(peak * peak / np.mean((a - b) ** 2))
+        print(f"bf16 mirror room: PSNR {psnr:.1f} dB, max abs {np.abs(a - b).max():.3g}")
+        assert psnr >= 45.0 and np.abs(a - b).max() <= 1e-2
     f.close()
     r.close()
 
@@ -155,11 +186,48 @@ def test_bounded_wait_gives_up_cleanly(env):
     sc = S.config1(16, 16)
     r = M.Renderer(sc)
     before, _ = r.render()
-    st = M.lib().mrf_selftest_timeout(r.ctx, 20000)
+    st = M.lib().mrf_selftest_timeout(r.ctx, 20000, 1)
     assert st == M.MRF_ERR_TIMEOUT and b"gave up" in M.lib().mrf_last_error()
     after, stats = r.render(stats=True)
     torch.cuda.synchronize()
     assert stats["status"] == 0 and torch.equal(before, after)
+    r.close()
+
+
+def test_sync_status_reports_a_wait_that_gave_up(env):
+    """Without waiting, a kernel that gave up is reported later: by
+    mrf_sync_status, which waits for the device, or by the next render call
+    once the status copy that the earlier call enqueued has landed; either
+    clears the word and the context renders on."""
+    torch, M = env
+    sc = S.config1(16, 16)
+    r = M.Renderer(sc)
+    before, _ = r.render()
+    torch.cuda.synchronize()
+    w = C.c_uint32(0)
+    assert M.lib().mrf_sync_status(r.ctx, C.byref(w)) == M.MRF_OK and w.value == 0
+    # reported by mrf_sync_status
+    assert M.lib().mrf_selftest_timeout(r.ctx, 20000, 0) == M.MRF_OK
+    assert M.lib().mrf_sync_status(r.ctx, C.byref(w)) == M.MRF_ERR_TIMEOUT and w.value != 0
+    assert b"gave up" in M.lib().mrf_last_error()
+    assert M.lib().mrf_sync_status(r.ctx, C.byref(w)) == M.MRF_OK and w.value == 0
+    # reported by the next render call, without a host wait in that call
+    assert M.lib().mrf_selftest_timeout(r.ctx, 20000, 0) == M.MRF_OK
+    torch.cuda.synchronize()
+    out = torch.empty_like(before)
+    st = M.lib().mrf_render(r.ctx, r.field, r.bvh, C.byref(r.rays_struct()), sc.opts.max_bounces,
+                            C.byref(r.opts_struct()), out.data_ptr(), None, None)
+    assert st == M.MRF_ERR_TIMEOUT and b"earlier kernel gave up" in M.lib().mrf_last_error()
+    after, stats = r.render(stats=True)
+    torch.cuda.synchronize()
+    assert stats["status"] == 0 and torch.equal(before, after)
+    # the same through the allocation-free entry point
+    assert M.lib().mrf_selftest_timeout(r.ctx, 20000, 0) == M.MRF_OK
+    torch.cuda.synchronize()
+    st = M.lib().mrf_render_static(r.ctx, r.field, r.bvh, C.byref(r.rays_struct()), sc.opts.max_bounces,
+                                   C.byref(r.opts_struct()), out.data_ptr(), None, None)
+    assert st == M.MRF_ERR_TIMEOUT
+    assert M.lib().mrf_sync_status(r.ctx, C.byref(w)) == M.MRF_OK
     r.close()
 
 

@@ -2,16 +2,23 @@
 through the C ABI.
 
 Tolerances (derived from the FP32 arithmetic of each step):
-  - hit triangle ids and segment counts: bit-exact on unflagged pixels;
+  - hit triangle ids and segment counts: bit-exact on unflagged pixels, and
+    on every pixel the hit ids of the segments before the path's first
+    flagged decision (the oracle's first_flag);
   - hit distance: 1e-5 relative to max(t, 1e-2) (coordinates of magnitude
     ~0.5 hold t to ~1e-7 absolute in FP32, so 1e-5 relative is only
     resolvable from t = 1e-2 up);
   - FP32 radiance: 1e-4 relative per pixel, relative to the pixel's largest
-    channel, with a floor of 1e-2 x the image peak for near-black pixels
-    (their light comes from the fringe of the density support, where FP32
-    sample positions carry ~1e-7 absolute error);
-  - pixels the oracle flags as ambiguous (a discrete decision within a margin
-    of its threshold) are excluded and must stay below 0.1 %.
+    channel, with a floor of 1e-2 x the image peak.  The floor is the FP32
+    position error at the fringe of the density support: a sample position
+    off by |dp| <= ~5e-7 moves the support s = 1 - |p - c|^2 / r^2 by up to
+    2 |dp| / r ~ 1e-5 (r >= 0.1), so a pixel lit by fringe samples carries an
+    absolute error up to ~1e-6 x the radiance of the unsupported field,
+    about 1e-4 x (1e-2 x the image peak);
+  - pixels the oracle flags as ambiguous (a discrete decision within the
+    FP32 error bound of its threshold, the bound growing along the path) are
+    excluded and must stay below 0.1 % of an image, except in the scenes
+    whose own test says why not.
 """
 import ctypes as C
 
@@ -56,8 +63,18 @@ def _render(M, sc, engine=None, spp=None):
     return res
 
 
-def _compare(gpu, ref, ids=None, rtol=RTOL_PIX, check_records=True, max_flag_frac=1e-3):
-    """Element-wise comparison of a GPU render with the oracle's on the pixels `ids`."""
+def _trusted(ref):
+    """Per path and segment: True where the hit record comes before the path's
+    first flagged decision (all segments of paths without one)."""
+    ff = ref["first_flag"]
+    jj = np.arange(1, ref["tri"].shape[2] + 1)
+    return (ff[:, :, None] == 0) | (jj[None, None, :] < ff[:, :, None])
+
+
+def _compare(gpu, ref, ids=None, rtol=RTOL_PIX, check_records=True, max_flag_frac=1e-3, t_segments=None):
+    """Element-wise comparison of a GPU render with the oracle's on the pixels
+    `ids`; hit distances are held to RTOL_T on the first `t_segments` segments
+    (default: all)."""
     if ids is None:
         ids = np.arange(gpu["rgba"].shape[0])
     g = gpu["rgba"][ids]
@@ -75,7 +92,12 @@ def _compare(gpu, ref, ids=None, rtol=RTOL_PIX, check_records=True, max_flag_fra
         assert np.array_equal(seg_g[ok], ref["segments"][ok]), "segment counts differ"
         tri_g = gpu["tri"][ids]
         assert np.array_equal(tri_g[ok], ref["tri"][ok]), "hit triangle ids differ"
-        tg, to = gpu["t"][ids][ok], ref["t"][ok]
+        tr = _trusted(ref)
+        assert np.array_equal(np.where(tr, tri_g, 0), np.where(tr, ref["tri"], 0)), \
+            "hit ids differ before a path's first flagged decision"
+        clear = ref["first_flag"] == 0
+        assert np.array_equal(seg_g[clear], ref["segments"][clear]), "segment counts differ on unflagged paths"
+        tg, to = gpu["t"][ids][ok][:, :, :t_segments], ref["t"][ok][:, :, :t_segments]
         fin = np.isfinite(to)
         assert np.array_equal(np.isfinite(tg), fin)
         assert np.all(np.abs(tg[fin] - to[fin]) <= RTOL_T * np.maximum(to[fin], 1e-2))
@@ -275,13 +297,19 @@ def test_spp_and_single_segment_and_no_mesh(M, orc, torch_cuda):
     assert np.all(gpu["segments"] == 1)
 
 
-def test_throughput_threshold(M, orc, torch_cuda):
-    # Termination at max(T) < tau is a threshold on a continuously falling T:
-    # inside a march T drops by 1-3 % per sample, so ~1e-4 / 0.02 of the
-    # threshold crossings land within the 1e-4 ambiguity margin.  The flagged
-    # fraction here is therefore allowed up to 1 %.
+@pytest.mark.parametrize("engine", ["megakernel", "wavefront"])
+def test_throughput_threshold(M, orc, torch_cuda, engine):
+    # Termination at max(T) < tau: the oracle flags a crossing only where T
+    # lies within the FP32 uncertainty of the path's optical depth (which the
+    # support's response to FP32 sample positions dominates); that flags
+    # fewer than 0.1 % of the pixels, and every other path must stop at the
+    # same sample, segment and hit.
     sc = S.config2(48, 48, tau=0.05)
-    _compare(_render(M, sc), orc.render(sc), max_flag_frac=1e-2)
+    eng = M.MRF_ENGINE_MEGAKERNEL if engine == "megakernel" else M.MRF_ENGINE_WAVEFRONT
+    gpu = _render(M, sc, engine=eng)
+    ref = orc.render(sc)
+    _compare(gpu, ref)
+    assert gpu["stats"]["ended_tau"] > 200          # many paths end at the threshold
 
 
 def test_mirror_box_series_on_gpu(M, orc, torch_cuda):
@@ -620,9 +648,12 @@ def test_field_sample_shadow_mask_matches_oracle(M, orc, torch_cuda, engine):
         assert np.array_equal(gpu["tri"][ok], ref["tri"][ok])
     else:
         eng = M.MRF_ENGINE_MEGAKERNEL if engine == "megakernel" else M.MRF_ENGINE_WAVEFRONT
-        # hundreds of mask rays per pixel sample the hard shadow boundary: about 1 %
-        # of pixels hold one that grazes an edge (flagged, legitimately decided either way)
-        _compare(_render(M, sc, engine=eng), ref, max_flag_frac=1.5e-2)
+        # every field sample with sigma > 0 casts a mask ray, hundreds per
+        # pixel, each from an FP32 position: about 2 % of the pixels hold one
+        # whose error bound reaches a mesh edge (flagged: a decision the FP32
+        # ray can take either way).  The mask changes radiance only, so hit
+        # ids and segment counts are compared on every unflagged path.
+        _compare(_render(M, sc, engine=eng), ref, max_flag_frac=3e-2)
 
 
 # ----------------------------------------------------------------- view-dependent radiance
@@ -677,3 +708,53 @@ def test_view_dependent_field_query(M, orc, torch_cuda, prec):
         assert np.all(np.abs(got - ref) <= 5e-2 * np.abs(ref) + 5e-3 * scale)
     M.mrf_field_destroy(f)
     M.mrf_context_destroy(ctx)
+
+
+# ----------------------------------------------------------------- persistent tail
+def _render_tuned(M, sc, prec, tail_paths, engine):
+    import torch
+    r = M.Renderer(sc, precision=prec)
+    r.set_tuning(8, 96, 1, tail_paths)
+    rec = r.new_records()
+    out, stats = r.render(records=rec, stats=True, engine=engine)
+    torch.cuda.synchronize()
+    res = dict(rgba=out.cpu().numpy().astype(np.float64), stats=stats, img=out.clone(),
+               segments=rec["segments"].cpu().numpy().view(np.uint32).reshape(sc.n_rays, sc.opts.spp),
+               tri=rec["tri"].cpu().numpy().view(np.uint32).reshape(sc.n_rays, sc.opts.spp, sc.opts.max_bounces),
+               t=rec["t"].cpu().numpy().reshape(sc.n_rays, sc.opts.spp, sc.opts.max_bounces))
+    r.close()
+    return res
+
+
+@pytest.mark.parametrize("cfg", ["c2", "area", "mask"])
+def test_persistent_tail_matches_the_wavefront_and_the_oracle(M, orc, torch_cuda, cfg):
+    """The persistent tail (one launch that finishes every path still live,
+    a warp per path) takes the wavefront engine's steps: with an FP32 field
+    the image, records and statistics equal the per-segment engine's bit for
+    bit, and they match the oracle; here it takes over from the second
+    segment on."""
+    torch = torch_cuda
+    if cfg == "c2":
+        sc = S.config2(64, 64)
+    elif cfg == "area":
+        sc = S.config4(32, 32)
+    else:
+        sc = S.config2(48, 48)
+        sc.lights = [S.Light(pos=l.pos, intensity=l.intensity, mask_strength=0.8) for l in sc.lights]
+        sc.opts.shadow_mask = True
+    W = M.MRF_ENGINE_WAVEFRONT
+    plain = _render_tuned(M, sc, M.MRF_PREC_FP32, 0, W)
+    tail = _render_tuned(M, sc, M.MRF_PREC_FP32, 1 << 20, W)
+    assert torch.equal(tail["img"], plain["img"])
+    assert np.array_equal(tail["segments"], plain["segments"]) and np.array_equal(tail["tri"], plain["tri"])
+    for k in ("segments", "surface_hits", "shadow_rays", "samples_evaluated", "shadow_samples_evaluated",
+              "samples_nominal", "bvh_nodes", "bvh_tri_tests", "ended_miss", "ended_tau", "ended_cap"):
+        assert tail["stats"][k] == plain["stats"][k], k
+    ref = orc.render(sc)
+    _compare(tail, ref, max_flag_frac=3e-2 if cfg == "mask" else 1e-3)
+    # the BF16 field through the tail (the tail's samples take the FP32 weights)
+    bf = _render_tuned(M, sc, M.MRF_PREC_BF16, 1 << 20, W)
+    ok = ref["flags"] == 0
+    assert _psnr(bf["rgba"], ref["rgba"], ok) >= 45.0
+    assert np.abs(bf["rgba"][ok, :3] - ref["rgba"][ok, :3]).max() <= 1e-2
+    assert np.array_equal(bf["tri"][ok], ref["tri"][ok])

@@ -148,9 +148,10 @@ def test_adam_step_matches_oracle(env, orc, renderer):
     net.close()
 
 
-def _train(M, renderer, steps=2000, batch=1 << 16, n_train=1 << 22, precision=None):
+def _train(M, renderer, steps=2000, batch=1 << 16, n_train=1 << 22, precision=None, lr_decay=1.0):
     torch = renderer.torch
-    net = M.ShadowNet(renderer, precision=precision if precision is not None else M.MRF_PREC_FP32, seed=7)
+    net = M.ShadowNet(renderer, precision=precision if precision is not None else M.MRF_PREC_FP32, seed=7,
+                      lr_decay=lr_decay)
     train = net.pairs(SEED, 0, n_train)
     held = net.pairs(SEED, 1 << 30, 1 << 16)
     y = held[:, 7]
@@ -207,17 +208,20 @@ def _psnr(a, b):
     return 10 * np.log10(peak * peak / np.mean((a[:, :3] - b[:, :3]) ** 2))
 
 
-def test_network_gain_over_the_march(env, orc, trained):
+def test_network_gain_over_the_march(env, orc, renderer):
     """What the trained network gains over the plain march on the
     area-light scene with BF16 field and network weights: shadow samples
-    removed, frame time, and the image error it costs against the FP64 oracle
-    (the plain method), next to that of the untrained network."""
+    removed and a shorter frame, at the image error the learned form must
+    keep against the FP64 oracle's plain march (>= 45 dB PSNR, <= 1e-2 max
+    abs in linear HDR), next to the untrained network's error."""
     torch, M = env
-    net, _ = trained
+    net, info = _train(M, renderer, steps=6000, n_train=1 << 24, lr_decay=0.9995)   # as the benchmark trains
+    print(f"trained: held-out MSE {info['mse0']:.4g} -> {info['mse']:.4g} in {info['secs']:.2f} s")
     sc = S.config4(192, 192)
     r = M.Renderer(sc, precision=M.MRF_PREC_BF16)
     bf = M.ShadowNet(r, params=net.params().cpu().numpy(), precision=M.MRF_PREC_BF16)
     untrained = M.ShadowNet(r, precision=M.MRF_PREC_BF16, seed=7)
+    r.set_tuning(8, 512, 16)          # the marched shadow rays need a large sample buffer (both arms use it)
     ids = S.strided_pixels(192, 192, 6, offset=2)
     ref = orc.render(sc, ids)
     ok = ref["flags"] == 0
@@ -239,23 +243,28 @@ def test_network_gain_over_the_march(env, orc, trained):
     img_n, st_n, ms_n = frame(bf)
     img_u, _, _ = frame(untrained)
     p_m, p_n, p_u = (_psnr(x[ids][ok], ref["rgba"][ok]) for x in (img_m, img_n, img_u))
+    max_n = float(np.abs(img_n[ids][ok, :3] - ref["rgba"][ok, :3]).max())
     print(f"march: {ms_m:.2f} ms, {st_m['shadow_samples_evaluated']} shadow samples, PSNR {p_m:.1f} dB | "
-          f"network: {ms_n:.2f} ms, {st_n['shadow_net_evals']} network shadow rays, PSNR {p_n:.1f} dB | "
-          f"untrained network PSNR {p_u:.1f} dB")
+          f"network: {ms_n:.2f} ms, {st_n['shadow_net_evals']} network shadow rays, PSNR {p_n:.1f} dB, "
+          f"max abs {max_n:.3g} | untrained network PSNR {p_u:.1f} dB")
     # every shading point of this scene lies in the field box: no shadow ray is marched
     assert st_n["shadow_samples_evaluated"] == 0 and st_m["shadow_samples_evaluated"] > 1000
     assert st_n["shadow_net_evals"] > 0
     assert p_n > p_u + 10.0           # training is what makes the network usable
-    assert p_n >= 40.0
+    assert p_n >= 45.0 and max_n <= 1e-2
+    assert ms_n < 0.5 * ms_m          # the gain: the network frame takes less than half the marched one
     bf.close()
     untrained.close()
+    net.close()
     r.close()
 
 
 def test_checkpoint_resume(env, renderer, tmp_path):
     """Training stopped at a checkpoint and resumed in a fresh network ends
-    where uninterrupted training ends (up to the order of the FP32 gradient
-    atomics); loading restores the parameters bit for bit."""
+    bit for bit where uninterrupted training ends: loading restores the
+    parameters, Adam moments, step count and pair cursor exactly, and the
+    gradient of a batch is summed in fixed point, independent of the order in
+    which the GPU threads add their parts."""
     torch, M = env
     a = M.ShadowNet(renderer, seed=3, lr_decay=0.999)
     pairs = a.pairs(SEED, 0, 1 << 18)
@@ -268,15 +277,11 @@ def test_checkpoint_resume(env, renderer, tmp_path):
     b.load(ck)
     assert torch.equal(b.params(), saved)
     b.train(pairs, 1 << 14, 40)
-    pa, pb = a.params(), b.params()
-    # Adam with eps 1e-15 turns a gradient of rounding size into a full step of
-    # either sign, so a few entries may differ by a step; the rest agree closely
-    close = (pa - pb).abs() <= 1e-5 * float(pa.abs().max())
-    assert float(close.float().mean()) >= 0.99
-    held = a.pairs(SEED, 1 << 28, 1 << 14)
-    ea = float(((a.eval(held) - held[:, 7]) ** 2).mean())
-    eb = float(((b.eval(held) - held[:, 7]) ** 2).mean())
-    assert abs(ea - eb) <= 0.05 * ea
+    assert torch.equal(a.params(), b.params())
+    # and the same batch twice gives the same gradient bit for bit
+    g1, _ = a.grad(pairs[: 1 << 14])
+    g2, _ = a.grad(pairs[: 1 << 14])
+    assert torch.equal(g1, g2)
     # a checkpoint of another shape is refused
     c = M.ShadowNet(renderer, log2_table=12)
     with pytest.raises(M.MrfError):

@@ -449,3 +449,89 @@ def test_view_dependent_field_pose_uses_the_field_frame(orc):
     peak = np.abs(b[:, :3]).max()
     assert peak > 0.05
     assert np.abs(a - b).max() <= 2e-4 * peak + 1e-7
+
+
+def _mirror_margin_recurrence(t_first, t_next, n):
+    """Edge margins the oracle's FP32 error bounds give the n segments of a ray
+    bouncing at normal incidence between two parallel mirrors (base 2e-7;
+    camera ray: 2.4e-7 lateral, 4e-7 rad; per mirror bounce +2.4e-7 lateral
+    and +4e-7 rad; lateral error grows by t times the angular one)."""
+    lat, ang, out = 2.4e-7, 4e-7, []
+    for j in range(n):
+        t = t_first if j == 0 else t_next
+        out.append(2e-7 + lat + t * ang)
+        lat, ang = lat + t * ang + 2.4e-7, ang + 4e-7
+    return out
+
+
+@pytest.mark.parametrize("delta,expect", [(5e-6, None), (1e-4, 0)])
+def test_edge_margin_grows_along_a_mirror_path(orc, delta, expect):
+    # A ray along z between the z+ and z- walls of a mirror box hits both
+    # walls at the same point, delta from the diagonal edge of their
+    # triangles.  The camera segment is clear of the margin; the first flagged
+    # segment is the one whose accumulated FP32 error bound reaches delta, and
+    # every hit before it is the wall the closed form names.
+    sc = _const_scene(0.0, [0.0, 0.0, 0.0], steps_per_segment=4)
+    sc.mesh = S.box_mesh([0, 0, 0], 0.4, 0, inward=True)
+    sc.materials = [S.Material(S.MAT_MIRROR, (1.0, 1.0, 1.0))]
+    sc.opts.max_bounces = 9
+    x0, z0 = np.float32(0.1), np.float32(0.1)
+    y0 = np.float32(np.float64(x0) - delta * math.sqrt(2.0))
+    d_edge = abs(np.float64(x0) - np.float64(y0)) / math.sqrt(2.0)     # exact distance to the line y = x
+    res = orc.render(S.explicit_rays(sc, [[x0, y0, z0]], [[0.0, 0.0, 1.0]]))
+    margins = _mirror_margin_recurrence(F(0.4) - np.float64(z0), 2 * F(0.4), 9)
+    first = next((j + 1 for j, m in enumerate(margins) if m >= d_edge), 0)
+    if expect is None:
+        assert 1 < first <= 9
+    else:
+        assert first == expect
+    assert res["first_flag"][0, 0] == first
+    k = (first - 1) if first else 9
+    walls = [int(t) // 2 for t in res["tri"][0, 0, :k]]
+    assert walls == [1 if j % 2 == 0 else 0 for j in range(k)]
+
+
+def test_fp32_error_bounds_cover_a_float32_mirror_path():
+    # The error bounds behind the flags, checked against an actual FP32
+    # computation: rays bouncing 16 times inside a rotated mirror box, once in
+    # float32 (every operation rounded) and once in float64 from the same FP32
+    # start and the same FP32 wall normals.  Every float32 hit point lies
+    # within the bound on the hit point's in-plane error.
+    rng = np.random.default_rng(3)
+    q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    n32 = np.concatenate([q, -q]).astype(np.float32)          # six walls n . x = 0.4, normals pointing out
+    n64 = n32.astype(np.float64)
+    n64 /= np.linalg.norm(n64, axis=1, keepdims=True)
+    n32 = n64.astype(np.float32)
+    worst = 0.0
+    for _ in range(300):
+        o = rng.uniform(-0.25, 0.25, 3).astype(np.float32)
+        d = rng.normal(size=3)
+        d = (d / np.linalg.norm(d)).astype(np.float32)
+        p64, d64, p32, d32 = o.astype(np.float64), d.astype(np.float64), o.copy(), d.copy()
+        lat, ang = 2.4e-7, 4e-7
+        for _j in range(16):
+            den64 = n64 @ d64
+            t64 = np.where(den64 > 1e-9, (0.4 - n64 @ p64) / np.where(den64 > 1e-9, den64, 1.0), np.inf)
+            k = int(np.argmin(t64))
+            den32 = (n32 @ d32).astype(np.float32)
+            t32 = np.where(den32 > np.float32(1e-9),
+                           (np.float32(0.4) - (n32 @ p32).astype(np.float32)) / np.where(den32 > 0, den32,
+                                                                                          np.float32(1)),
+                           np.float32(np.inf)).astype(np.float32)
+            if int(np.argmin(t32)) != k:
+                break                               # near a corner: the walls differ, the path ends here
+            cos = max(float(den64[k]), 0.01)
+            h64 = p64 + t64[k] * d64
+            h32 = (p32 + t32[k] * d32).astype(np.float32)
+            bound = (lat + t64[k] * ang) / cos + 2.4e-7
+            err = float(np.linalg.norm(h32.astype(np.float64) - h64))
+            worst = max(worst, err / bound)
+            assert err <= bound, (err, bound)
+            lat, ang = lat + t64[k] * ang + 2.4e-7, ang + 4e-7
+            d64 = d64 - 2 * (d64 @ n64[k]) * n64[k]
+            d64 /= np.linalg.norm(d64)
+            r32 = (d32 - np.float32(2) * np.float32(d32 @ n32[k]) * n32[k]).astype(np.float32)
+            d32 = (r32 / np.float32(np.linalg.norm(r32))).astype(np.float32)
+            p64, p32 = h64, h32
+    assert worst > 1e-3    # the bound is not vacuous
