@@ -21,6 +21,11 @@
  *    stream).  Device work is enqueued on it and the call returns without
  *    waiting, except where noted (host output buffers, statistics).
  *  - Asynchronous device faults surface as MRF_ERR_CUDA from the next call.
+ *    A kernel that gives up after its iteration budget sets the context's
+ *    status word; a render call reports it as MRF_ERR_TIMEOUT without blocking
+ *    the host (each call ends by copying the word to pinned host memory on its
+ *    stream, and the next call reads that copy once it has landed), so the
+ *    report may come one call late.  mrf_sync_status waits and reports at once.
  */
 #ifndef MRF_H
 #define MRF_H
@@ -58,6 +63,12 @@ void mrf_context_destroy(mrf_context *ctx);
 const char *mrf_last_error(void);
 /* Library version as "major.minor.patch". */
 const char *mrf_version(void);
+/* The library's error channel (the paper has no counterpart).  Waits for all
+ * work on the context's device (cudaDeviceSynchronize), then reads and clears
+ * the context's status word.  MRF_ERR_CUDA for an asynchronous
+ * CUDA error, MRF_ERR_TIMEOUT if a kernel gave up since the last report (its
+ * bits in *status_word, nullable), else MRF_OK. */
+mrf_status mrf_sync_status(mrf_context *ctx, uint32_t *status_word);
 
 /* ------------------------------------------------------------------ field */
 /* The radiance field: density sigma(p) and linear-HDR radiance r(p) on the
@@ -264,7 +275,8 @@ enum { MRF_ENGINE_AUTO = 0, MRF_ENGINE_MEGAKERNEL = 1, MRF_ENGINE_WAVEFRONT = 2 
 enum {
     MRF_KERNEL_MEGAKERNEL = 0, MRF_KERNEL_CAST_GEN = 1, MRF_KERNEL_FIELD = 2, MRF_KERNEL_SHADE = 3,
     MRF_KERNEL_FINALIZE = 4, MRF_KERNEL_GEN = 5, MRF_KERNEL_COMPOSITE = 6, MRF_KERNEL_SHADOW_NET = 7,
-    MRF_KERNEL_SHADOW_VIS = 8, MRF_KERNEL_OVERFLOW = 9, MRF_KERNEL_MASK = 10, MRF_KERNEL_COUNT = 11
+    MRF_KERNEL_SHADOW_VIS = 8, MRF_KERNEL_OVERFLOW = 9, MRF_KERNEL_MASK = 10, MRF_KERNEL_TAIL = 11,
+    MRF_KERNEL_COUNT = 12
 };
 
 typedef struct mrf_render_opts {
@@ -336,15 +348,22 @@ mrf_status mrf_tonemap(mrf_context *ctx, const float *in, uint32_t n, float expo
  * an allocation may cause.  It runs the wavefront engine out of a file-scope
  * device arena of 64 MiB that every GPU loading the library holds until the
  * process exits, and it allocates no device or pinned memory itself.
- *  - Limits: rays->count * rays->spp <= 131072 paths and at most 8 shadow rays per hit;
- *    larger requests return MRF_ERR_INVALID_ARG (use mrf_render).  Samples that
- *    do not fit the arena's sample buffer are marched in place, so results do
- *    not depend on the arena size.
+ *  - Limits: rays->count * rays->spp <= 131072 paths, at most 8 shadow rays per
+ *    hit (K), and the per-path state, about (172 + 48 max(K, 1)) bytes a path,
+ *    must leave the arena room for at least one 128-sample tile: at K = 8 that
+ *    allows about 120,000 paths, at K <= 7 the full 131072.  Larger requests
+ *    return MRF_ERR_INVALID_ARG naming the limit (use mrf_render).
+ *  - Samples that do not fit the arena's sample buffer are left for the next
+ *    generation round (mrf_tuning.rounds); with enough rounds the image is
+ *    mrf_render's bit for bit.  Jobs still pending after the last round are
+ *    marched in place on the CUDA cores in FP32, so at FP16/BF16 their pixels
+ *    differ from mrf_render's by up to the reduced-precision error.
  *  - out_hdr, explicit rays and records must be device memory; per-kernel
  *    timing (kernel_ms, kernel_launches) is rejected.
- *  - The first call on a device resolves the arena's address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *  - The arena's device address is resolved (cudaGetSymbolAddress) once per
+ *    context, by mrf_context_create with the context's device current.
+ *  - Without `stats` the call does not block the host: a kernel that gave up
+ *    is reported by a later call or by mrf_sync_status.
  *  - All calls share the arena, which keeps the last call's contents; the
  *    engine clears its counters at the start of every call.  Calls that overlap
  *    on the GPU (for example on two streams) race on the arena.
@@ -364,6 +383,11 @@ typedef struct mrf_tuning {
     uint32_t rounds;             /* sample-generation rounds per segment, 1..16, default 1: the paths whose
                                     samples did not fit the buffer go to the next round; those left after
                                     the last round are marched in place on the CUDA cores in FP32 */
+    uint32_t tail_paths;         /* persistent tail, 0..2^20, default 0 (off): once at most this many paths
+                                    are live at the start of a segment (from the second on), one persistent
+                                    kernel finishes all of them, a warp per path, instead of the per-segment
+                                    launches; its field samples run on the CUDA cores with the FP32 weights
+                                    (for an FP32 field the image is the same bit for bit) */
 } mrf_tuning;
 mrf_status mrf_tuning_get(const mrf_context *ctx, mrf_tuning *out);
 mrf_status mrf_tuning_set(mrf_context *ctx, const mrf_tuning *t);
@@ -479,17 +503,29 @@ mrf_status mrf_shadow_net_load(mrf_shadow_net *net, const char *path);
  * the device array out (n values), with the rendering weights. */
 mrf_status mrf_shadow_net_eval(mrf_shadow_net *net, const float *pairs, uint32_t n, float *out, void *stream);
 
+/* ----------------------------------------------------------- diagnostics
+ * The paper has no counterpart.  mrf_l2_read_bandwidth measures the L2 read
+ * bandwidth the field kernel's table gathers are compared with: it fills
+ * `bytes` of the context's scratch memory (a multiple of 16 in [1 MiB,
+ * 256 MiB]; allocated or grown if needed), reads it once to make it resident,
+ * then times `reps` (1..1000) passes of 16-byte loads that bypass L1 with
+ * CUDA events on `stream`, waits, and stores bytes * reps / time in GB/s in
+ * *gbs.  A buffer larger than the L2 measures DRAM instead. */
+mrf_status mrf_l2_read_bandwidth(mrf_context *ctx, uint64_t bytes, uint32_t reps, void *stream, double *gbs);
+
 /* ------------------------------------------------------------ self tests
  * Failure paths exercised without faulting the GPU.  Every wait of the
  * library's kernels (mbarrier waits on tensor-core work) is bounded; a wait
  * that gives up sets a bit of the context's status word and its kernel
  * returns, and the next call reports MRF_ERR_TIMEOUT.
  * mrf_selftest_timeout runs one such wait on a barrier that nothing arrives
- * at, with a budget of `cycles` SM cycles (at most 2^32): it returns
- * MRF_ERR_TIMEOUT, clears the status word, and leaves the context usable.
+ * at, with a budget of `cycles` SM cycles (at most 2^32).  With `wait` it
+ * waits for the device, returns MRF_ERR_TIMEOUT and clears the status word;
+ * without, it returns MRF_OK at once and the give-up is reported like any
+ * other: by the next render call or mrf_sync_status.  The context stays usable.
  * mrf_debug_fail_allocations makes the library's next n device allocations
  * fail as if the device were out of memory (MRF_ERR_OOM); 0 turns it off. */
-mrf_status mrf_selftest_timeout(mrf_context *ctx, uint64_t cycles);
+mrf_status mrf_selftest_timeout(mrf_context *ctx, uint64_t cycles, int32_t wait);
 void mrf_debug_fail_allocations(uint32_t n);
 
 #ifdef __cplusplus

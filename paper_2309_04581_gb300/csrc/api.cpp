@@ -21,7 +21,8 @@ cudaError_t launch_render_wavefront(const RenderParams &P, void *scratch, size_t
                                     KernelTimer *timer);
 size_t wavefront_scratch_bytes(const RenderParams &P);
 bool wavefront_available();
-cudaError_t static_arena(int device, void **ptr, size_t *bytes);
+cudaError_t static_arena(void **ptr, size_t *bytes);
+uint32_t static_arena_paths_that_fit(int n_shadow);
 cudaError_t launch_render_wavefront_arena(const RenderParams &P, void *arena, size_t arena_bytes, cudaStream_t s);
 uint32_t static_arena_max_paths();
 int static_arena_max_lights();
@@ -62,10 +63,16 @@ struct mrf_context {
     int n_shadow = 0;   // shadow rays per diffuse hit over all lights
     unsigned long long *stats = nullptr;
     unsigned *status = nullptr;  // device status word: non-zero after a kernel gave up
+    unsigned *status_host = nullptr;   // pinned copy of the status word, written at the end of render calls
+    cudaEvent_t status_ev = nullptr;   // completes when that copy has landed
+    bool status_pending = false;       // a copy was enqueued and not read yet
+    void *arena = nullptr;             // device address of the allocation-free render arena
+    size_t arena_bytes = 0;
+    cudaError_t arena_err = cudaSuccess;
     KernelTimer *timer = nullptr;
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
-    mrf_tuning tuning{8, 96, 1};
+    mrf_tuning tuning{8, 96, 1, 0};
 };
 
 struct mrf_field {
@@ -90,7 +97,8 @@ struct mrf_bvh {
 struct mrf_shadow_net {
     mrf_context *ctx = nullptr;
     ShadowNetDev dev{};
-    float *params = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr, *mlp_inf = nullptr;
+    float *params = nullptr, *m = nullptr, *v = nullptr, *mlp_inf = nullptr;
+    unsigned long long *grad = nullptr;   // gradient sums in 64-bit fixed point (order-independent)
     uint8_t *lp = nullptr;   // BF16 tensor-core weights (BF16 networks)
     uint64_t n_params = 0;
     uint32_t t = 0;          // Adam steps taken
@@ -204,6 +212,17 @@ mrf_status mrf_context_create(int device, mrf_context **out) {
     }
     cudaMemset(c->stats, 0, sizeof(unsigned long long) * ST_COUNT);
     cudaMemset(c->status, 0, sizeof(unsigned));
+    cudaError_t e2 = cudaHostAlloc((void **)&c->status_host, sizeof(unsigned), cudaHostAllocDefault);
+    if (e2 == cudaSuccess) e2 = cudaEventCreateWithFlags(&c->status_ev, cudaEventDisableTiming);
+    if (e2 != cudaSuccess) {
+        mrf_context_destroy(c);
+        return cuda_fail(e2, "mrf_context_create: status mirror");
+    }
+    *c->status_host = 0;
+    // the allocation-free entry point's arena: its device address is resolved
+    // here, once per context, with the context's device current
+    c->arena_err = static_arena(&c->arena, &c->arena_bytes);
+    if (c->arena_err != cudaSuccess) cudaGetLastError();
     *out = c;
     return MRF_OK;
 }
@@ -215,6 +234,8 @@ void mrf_context_destroy(mrf_context *c) {
     cudaFree(c->stats);
     cudaFree(c->status);
     cudaFree(c->scratch);
+    if (c->status_host) cudaFreeHost(c->status_host);
+    if (c->status_ev) cudaEventDestroy(c->status_ev);
     if (c->timer) {
         for (auto &e : c->timer->ev) cudaEventDestroy(e);
         delete c->timer;
@@ -969,6 +990,7 @@ static mrf_status plan_render(mrf_context *ctx, const mrf_field *field, const mr
     P.tc_groups = (int)ctx->tuning.field_groups;
     P.cap_per_path = ctx->tuning.samples_per_path;
     P.max_rounds = (int)ctx->tuning.rounds;
+    P.tail_paths = ctx->tuning.tail_paths;
     if (opts->shadow_net) {
         if (opts->shadow_net->ctx != ctx) return fail(MRF_ERR_INVALID_ARG, "shadow_net belongs to another context");
         P.has_snet = 1;
@@ -1039,6 +1061,76 @@ static void stats_from(const unsigned long long *h, unsigned st_word, mrf_stats 
     stats->status = st_word;
 }
 
+// Status of kernels that gave up, reported without blocking the host: every
+// render call ends by copying the device status word to the context's pinned
+// mirror on its stream (post_status); the next call reads the mirror if that
+// copy has landed (poll_status) and otherwise goes on, so the report may come
+// one call later.  mrf_sync_status waits for the device and reads the word.
+static bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+static mrf_status poll_status(mrf_context *ctx, cudaStream_t s, const char *who) {
+    if (!ctx->status_pending || capturing(s)) return MRF_OK;
+    const cudaError_t q = cudaEventQuery(ctx->status_ev);
+    if (q == cudaErrorNotReady) {
+        if (cudaPeekAtLastError() == cudaErrorNotReady) cudaGetLastError();
+        return MRF_OK;
+    }
+    if (q != cudaSuccess) return cuda_fail(q, who);
+    ctx->status_pending = false;
+    const unsigned w = *ctx->status_host;
+    if (w) {
+        *ctx->status_host = 0;
+        CUDA_TRY(cudaMemsetAsync(ctx->status, 0, sizeof(unsigned), s), who);
+        return fail(MRF_ERR_TIMEOUT, "%s: an earlier kernel gave up (status 0x%x)", who, w);
+    }
+    return MRF_OK;
+}
+
+static mrf_status post_status(mrf_context *ctx, cudaStream_t s, const char *who) {
+    if (capturing(s)) return MRF_OK;
+    CUDA_TRY(cudaMemcpyAsync(ctx->status_host, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s), who);
+    CUDA_TRY(cudaEventRecord(ctx->status_ev, s), who);
+    ctx->status_pending = true;
+    return MRF_OK;
+}
+
+// After a call that waited for its stream: the status word as of that point.
+static mrf_status read_status_after_sync(mrf_context *ctx, cudaStream_t s, unsigned &w, const char *who) {
+    CUDA_TRY(cudaMemcpyAsync(ctx->status_host, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s), who);
+    CUDA_TRY(cudaStreamSynchronize(s), who);
+    w = *ctx->status_host;
+    ctx->status_pending = false;
+    if (w) {
+        *ctx->status_host = 0;
+        CUDA_TRY(cudaMemsetAsync(ctx->status, 0, sizeof(unsigned), s), who);
+    }
+    return MRF_OK;
+}
+
+mrf_status mrf_sync_status(mrf_context *ctx, uint32_t *status_word) {
+    if (status_word) *status_word = 0;
+    if (!ctx) return fail(MRF_ERR_INVALID_ARG, "mrf_sync_status: NULL context");
+    CUDA_TRY(cudaSetDevice(ctx->device), "mrf_sync_status: cudaSetDevice");
+    CUDA_TRY(cudaDeviceSynchronize(), "mrf_sync_status: asynchronous error");
+    unsigned w = 0;
+    CUDA_TRY(cudaMemcpy(&w, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost), "mrf_sync_status: status read");
+    ctx->status_pending = false;
+    *ctx->status_host = 0;
+    if (status_word) *status_word = w;
+    if (w) {
+        CUDA_TRY(cudaMemset(ctx->status, 0, sizeof(unsigned)), "mrf_sync_status: status clear");
+        return fail(MRF_ERR_TIMEOUT, "mrf_sync_status: a kernel gave up (status 0x%x)", w);
+    }
+    return MRF_OK;
+}
+
 mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *bvh, const mrf_rays *rays,
                       uint32_t max_bounces, const mrf_render_opts *opts, float *out_hdr, void *stream,
                       mrf_stats *stats) {
@@ -1051,14 +1143,7 @@ mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *b
         if (pending != cudaSuccess) return cuda_fail(pending, "mrf_render: earlier asynchronous error");
     }
     cudaStream_t s = (cudaStream_t)stream;
-    {
-        unsigned st_word = 0;
-        CUDA_TRY(cudaMemcpy(&st_word, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost), "mrf_render: status read");
-        if (st_word) {
-            cudaMemset(ctx->status, 0, sizeof(unsigned));
-            return fail(MRF_ERR_TIMEOUT, "mrf_render: an earlier kernel gave up (status 0x%x)", st_word);
-        }
-    }
+    if ((st = poll_status(ctx, s, "mrf_render"))) return st;
     if (R.scratch_need && (st = ensure_scratch(ctx, R.scratch_need))) return st;
     place_render(ctx, R, out_hdr);
     if (R.n_views)
@@ -1110,17 +1195,14 @@ mrf_status mrf_render(mrf_context *ctx, const mrf_field *field, const mrf_bvh *b
     if (stats) {
         unsigned long long h[ST_COUNT];
         CUDA_TRY(cudaMemcpyAsync(h, ctx->stats, sizeof(h), cudaMemcpyDeviceToHost, s), "stats download");
-        CUDA_TRY(cudaStreamSynchronize(s), "mrf_render: synchronize");
         unsigned st_word = 0;
-        CUDA_TRY(cudaMemcpy(&st_word, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost), "mrf_render: status read");
+        if ((st = read_status_after_sync(ctx, s, st_word, "mrf_render: status read"))) return st;
         stats_from(h, st_word, stats);
-        if (st_word) {
-            cudaMemset(ctx->status, 0, sizeof(unsigned));
-            return fail(MRF_ERR_TIMEOUT, "mrf_render: a kernel gave up (status 0x%x)", st_word);
-        }
-    } else if (R.host_out) {
-        CUDA_TRY(cudaStreamSynchronize(s), "mrf_render: synchronize");
+        if (st_word) return fail(MRF_ERR_TIMEOUT, "mrf_render: a kernel gave up (status 0x%x)", st_word);
+        return MRF_OK;
     }
+    if ((st = post_status(ctx, s, "mrf_render: status copy"))) return st;
+    if (R.host_out) CUDA_TRY(cudaStreamSynchronize(s), "mrf_render: synchronize");
     return MRF_OK;
 }
 
@@ -1134,8 +1216,9 @@ mrf_status mrf_tuning_get(const mrf_context *ctx, mrf_tuning *out) {
 mrf_status mrf_tuning_set(mrf_context *ctx, const mrf_tuning *t) {
     if (!ctx || !t) return fail(MRF_ERR_INVALID_ARG, "mrf_tuning_set: NULL argument");
     if ((t->field_groups != 4 && t->field_groups != 8) || t->samples_per_path < 16 || t->samples_per_path > 4096 ||
-        t->rounds < 1 || t->rounds > 16)
-        return fail(MRF_ERR_INVALID_ARG, "mrf_tuning_set: field_groups 4 or 8, samples_per_path 16..4096, rounds 1..16");
+        t->rounds < 1 || t->rounds > 16 || t->tail_paths > (1u << 20))
+        return fail(MRF_ERR_INVALID_ARG, "mrf_tuning_set: field_groups 4 or 8, samples_per_path 16..4096, rounds 1..16, "
+                                         "tail_paths 0..2^20");
     ctx->tuning = *t;
     return MRF_OK;
 }
@@ -1164,7 +1247,7 @@ mrf_status mrf_autotune(mrf_context *ctx, const mrf_field *field, const mrf_bvh 
     for (uint32_t g : groups) {
         for (uint32_t cap : caps)
         for (uint32_t rr : rounds) {
-            ctx->tuning = mrf_tuning{g, cap, rr};
+            ctx->tuning = mrf_tuning{g, cap, rr, keep.tail_paths};
             float t = INFINITY;
             if ((st = mrf_render(ctx, field, bvh, rays, max_bounces, opts, out_hdr, stream, nullptr))) break;
             cudaEventRecord(e0, s);
@@ -1302,8 +1385,9 @@ mrf_status mrf_frame_stats(mrf_frame *f, void *stream, mrf_stats *stats) {
 }
 
 // Allocation-free render: the wavefront engine on the library's static device
-// arena (render_wavefront.cu).  Nothing here allocates device or pinned memory;
-// the first call on a device resolves the arena's address.
+// arena (render_wavefront.cu), whose device address the context resolved when
+// it was created.  Nothing here allocates device or pinned memory, and nothing
+// blocks the host unless statistics are asked for.
 mrf_status mrf_render_static(mrf_context *ctx, const mrf_field *field, const mrf_bvh *bvh, const mrf_rays *rays,
                              uint32_t max_bounces, const mrf_render_opts *opts, float *out_hdr, void *stream,
                              mrf_stats *stats) {
@@ -1334,15 +1418,6 @@ mrf_status mrf_render_static(mrf_context *ctx, const mrf_field *field, const mrf
         if (pending != cudaSuccess) return cuda_fail(pending, "mrf_render_static: earlier asynchronous error");
     }
     cudaStream_t s = (cudaStream_t)stream;
-    {
-        unsigned st_word = 0;
-        CUDA_TRY(cudaMemcpy(&st_word, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost),
-                 "mrf_render_static: status read");
-        if (st_word) {
-            cudaMemset(ctx->status, 0, sizeof(unsigned));
-            return fail(MRF_ERR_TIMEOUT, "mrf_render_static: an earlier kernel gave up (status 0x%x)", st_word);
-        }
-    }
     RenderParams P{};
     P.F = field->dev;
     P.B = bvh->dev;
@@ -1405,6 +1480,12 @@ mrf_status mrf_render_static(mrf_context *ctx, const mrf_field *field, const mrf
         return fail(MRF_ERR_INVALID_ARG,
                     "mrf_render_static: %llu paths (rays x spp) exceed the static arena limit of %u; use mrf_render",
                     (unsigned long long)paths, static_arena_max_paths());
+    const uint32_t fit = static_arena_paths_that_fit(ctx->n_shadow);
+    if (paths > fit)
+        return fail(MRF_ERR_INVALID_ARG,
+                    "mrf_render_static: %llu paths with %d shadow rays per hit do not fit the static arena "
+                    "(at most %u paths at that light count); use mrf_render",
+                    (unsigned long long)paths, ctx->n_shadow, fit);
     P.count = count;
     P.spp = rays->spp;
     P.max_bounces = max_bounces;
@@ -1418,6 +1499,7 @@ mrf_status mrf_render_static(mrf_context *ctx, const mrf_field *field, const mrf
     P.rec_t = opts->rec_t;
     P.tc_groups = (int)ctx->tuning.field_groups;
     P.max_rounds = (int)ctx->tuning.rounds;
+    P.tail_paths = ctx->tuning.tail_paths;
     P.shadow_mask = opts->shadow_mask ? 1 : 0;
     if (opts->shadow_net) {
         if (opts->shadow_net->ctx != ctx) return fail(MRF_ERR_INVALID_ARG, "shadow_net belongs to another context");
@@ -1426,28 +1508,26 @@ mrf_status mrf_render_static(mrf_context *ctx, const mrf_field *field, const mrf
     }
     P.out = out_hdr;
     P.status = ctx->status;
-    void *arena = nullptr;
-    size_t arena_bytes = 0;
-    CUDA_TRY(static_arena(ctx->device, &arena, &arena_bytes), "mrf_render_static: arena address (cudaGetSymbolAddress)");
+    if (ctx->arena_err != cudaSuccess || !ctx->arena)
+        return cuda_fail(ctx->arena_err != cudaSuccess ? ctx->arena_err : cudaErrorInvalidSymbol,
+                         "mrf_render_static: arena address (cudaGetSymbolAddress at context creation)");
+    mrf_status pst = poll_status(ctx, s, "mrf_render_static");
+    if (pst) return pst;
     if (stats) {
         CUDA_TRY(cudaMemsetAsync(ctx->stats, 0, sizeof(unsigned long long) * ST_COUNT, s), "stats reset");
         P.stats = ctx->stats;
     }
-    CUDA_TRY(launch_render_wavefront_arena(P, arena, arena_bytes, s), "mrf_render_static: launch");
+    CUDA_TRY(launch_render_wavefront_arena(P, ctx->arena, ctx->arena_bytes, s), "mrf_render_static: launch");
     if (stats) {
         unsigned long long h[ST_COUNT];
         CUDA_TRY(cudaMemcpyAsync(h, ctx->stats, sizeof(h), cudaMemcpyDeviceToHost, s), "stats download");
-        CUDA_TRY(cudaStreamSynchronize(s), "mrf_render_static: synchronize");
         unsigned st_word = 0;
-        CUDA_TRY(cudaMemcpy(&st_word, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost),
-                 "mrf_render_static: status read");
+        if ((pst = read_status_after_sync(ctx, s, st_word, "mrf_render_static: status read"))) return pst;
         stats_from(h, st_word, stats);
-        if (st_word) {
-            cudaMemset(ctx->status, 0, sizeof(unsigned));
-            return fail(MRF_ERR_TIMEOUT, "mrf_render_static: a kernel gave up (status 0x%x)", st_word);
-        }
+        if (st_word) return fail(MRF_ERR_TIMEOUT, "mrf_render_static: a kernel gave up (status 0x%x)", st_word);
+        return MRF_OK;
     }
-    return MRF_OK;
+    return post_status(ctx, s, "mrf_render_static: status copy");
 }
 
 mrf_status mrf_tonemap(mrf_context *ctx, const float *in, uint32_t n, float exposure, float *out, void *stream) {
@@ -1571,7 +1651,7 @@ mrf_status mrf_shadow_net_create(mrf_context *ctx, const mrf_field *field, const
     }
     if (cudaMemset(n->m, 0, n->n_params * sizeof(float)) != cudaSuccess ||
         cudaMemset(n->v, 0, n->n_params * sizeof(float)) != cudaSuccess ||
-        cudaMemset(n->grad, 0, n->n_params * sizeof(float)) != cudaSuccess || (st = snet_refresh(n, 0)) ||
+        cudaMemset(n->grad, 0, n->n_params * sizeof(unsigned long long)) != cudaSuccess || (st = snet_refresh(n, 0)) ||
         cudaDeviceSynchronize() != cudaSuccess) {
         mrf_shadow_net_destroy(n);
         return st ? st : fail(MRF_ERR_CUDA, "mrf_shadow_net_create: initialisation");
@@ -1645,9 +1725,9 @@ mrf_status mrf_shadow_net_grad(mrf_shadow_net *n, const float *pairs, uint32_t c
         return fail(MRF_ERR_INVALID_ARG, "mrf_shadow_net_grad: arrays must be device memory");
     CUDA_TRY(cudaSetDevice(n->ctx->device), "cudaSetDevice");
     cudaStream_t s = (cudaStream_t)stream;
-    CUDA_TRY(cudaMemsetAsync(grad, 0, n->n_params * sizeof(float), s), "grad clear");
     CUDA_TRY(cudaMemsetAsync(loss, 0, sizeof(float), s), "loss clear");
-    CUDA_TRY(launch_snet_grad(n->dev, n->params, grad, pairs, count, 0, count, loss, s), "mrf_shadow_net_grad");
+    CUDA_TRY(launch_snet_grad(n->dev, n->params, n->grad, pairs, count, 0, count, loss, s), "mrf_shadow_net_grad");
+    CUDA_TRY(launch_snet_grad_out(n->grad, grad, n->n_params, s), "mrf_shadow_net_grad: output");
     return MRF_OK;
 }
 
@@ -1684,14 +1764,46 @@ mrf_status mrf_shadow_net_eval(mrf_shadow_net *n, const float *pairs, uint32_t c
 }
 
 
+// ------------------------------------------------------------ diagnostics
+mrf_status mrf_l2_read_bandwidth(mrf_context *ctx, uint64_t bytes, uint32_t reps, void *stream, double *gbs) {
+    if (!ctx || !gbs) return fail(MRF_ERR_INVALID_ARG, "mrf_l2_read_bandwidth: NULL argument");
+    if (bytes < (1u << 20) || bytes > (256ull << 20) || bytes % 16 || reps == 0 || reps > 1000)
+        return fail(MRF_ERR_INVALID_ARG, "mrf_l2_read_bandwidth: bytes must be a multiple of 16 in [1 MiB, 256 MiB], "
+                                         "reps in [1, 1000]");
+    CUDA_TRY(cudaSetDevice(ctx->device), "mrf_l2_read_bandwidth: cudaSetDevice");
+    mrf_status st = ensure_scratch(ctx, bytes + 256);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    float *sink = reinterpret_cast<float *>(static_cast<char *>(ctx->scratch) + bytes);
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0), "mrf_l2_read_bandwidth: event");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(cudaGetLastError(), "mrf_l2_read_bandwidth: event");
+    }
+    float ms = 0.f;
+    cudaError_t e = launch_l2_fill(ctx->scratch, bytes, sink, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = launch_l2_read(ctx->scratch, bytes, (int)reps, sink, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "mrf_l2_read_bandwidth");
+    *gbs = (double)bytes * reps / ((double)ms * 1e-3) / 1e9;
+    return MRF_OK;
+}
+
 // ------------------------------------------------------------ self tests
 void mrf_debug_fail_allocations(uint32_t n) { g_fail_allocs.store(n); }
 
-mrf_status mrf_selftest_timeout(mrf_context *ctx, uint64_t cycles) {
+mrf_status mrf_selftest_timeout(mrf_context *ctx, uint64_t cycles, int32_t wait) {
     if (!ctx) return fail(MRF_ERR_INVALID_ARG, "mrf_selftest_timeout: NULL context");
     if (cycles > (1ull << 32)) return fail(MRF_ERR_INVALID_ARG, "mrf_selftest_timeout: budget above 2^32 cycles");
     CUDA_TRY(cudaSetDevice(ctx->device), "mrf_selftest_timeout: cudaSetDevice");
     CUDA_TRY(launch_selftest_timeout((long long)cycles, ctx->status, 0), "mrf_selftest_timeout: launch");
+    if (!wait) return post_status(ctx, 0, "mrf_selftest_timeout: status copy");
     CUDA_TRY(cudaDeviceSynchronize(), "mrf_selftest_timeout: synchronize");
     unsigned st_word = 0;
     CUDA_TRY(cudaMemcpy(&st_word, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost), "mrf_selftest_timeout: status");

@@ -190,6 +190,7 @@ struct RenderParams {
     int tc_groups;               // tuning: tile groups per CTA of the tensor-core field kernel (4 or 8)
     uint32_t cap_per_path;       // tuning: sample-buffer capacity per path
     int max_rounds;              // tuning: sample-generation rounds per segment
+    uint32_t tail_paths;         // tuning: live paths at which the persistent tail takes over (0: never)
     int has_snet;                // shadow rays from inside the field box use the network
     ShadowNetDev snet;
 };
@@ -234,14 +235,18 @@ cudaError_t launch_cast(const BvhDev &B, const float *o, const float *d, const u
                         float *out_t, uint32_t *out_tri, unsigned long long *stats, cudaStream_t s);
 cudaError_t launch_tonemap(const float4 *in, uint32_t n, float exposure, float4 *out, cudaStream_t s);
 cudaError_t launch_selftest_timeout(long long cycles, unsigned *status, cudaStream_t s);
+// the L2 read-bandwidth kernels: fill and warm the buffer, then `reps` passes of reads
+cudaError_t launch_l2_fill(void *buf, size_t bytes, float *sink, cudaStream_t s);
+cudaError_t launch_l2_read(const void *buf, size_t bytes, int reps, float *sink, cudaStream_t s);
 // shadow_net.cu
 size_t snet_train_smem();
 cudaError_t launch_snet_pairs(const RenderParams &P, uint64_t seed, uint64_t first, uint32_t n, float *out,
                               cudaStream_t s);
-cudaError_t launch_snet_grad(const ShadowNetDev &N, const float *params, float *grad, const float *pairs,
+cudaError_t launch_snet_grad(const ShadowNetDev &N, const float *params, unsigned long long *gacc, const float *pairs,
                              uint64_t n_pairs, uint64_t b0, uint32_t B, float *loss, cudaStream_t s);
-cudaError_t launch_snet_adam(float *p, float *m, float *v, float *g, uint64_t n, float lr, float b1, float b2,
-                             float eps, double c1, double c2, cudaStream_t s);
+cudaError_t launch_snet_adam(float *p, float *m, float *v, unsigned long long *g, uint64_t n, float lr, float b1,
+                             float b2, float eps, double c1, double c2, cudaStream_t s);
+cudaError_t launch_snet_grad_out(unsigned long long *g, float *out, uint64_t n, cudaStream_t s);
 cudaError_t launch_snet_refresh(const float *mlp, float *out, bool bf16, cudaStream_t s);
 cudaError_t launch_snet_eval(const ShadowNetDev &N, const float *pairs, uint32_t n, float *out, cudaStream_t s);
 size_t snet_lp_bytes();

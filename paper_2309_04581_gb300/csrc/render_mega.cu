@@ -193,6 +193,46 @@ cudaError_t launch_selftest_timeout(long long cycles, unsigned *status, cudaStre
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------- L2 bandwidth
+// Reads an L2-resident buffer `reps` times with 16-byte loads that bypass L1
+// (ld.global.cg), every thread grid-striding over it; the sum only keeps the
+// loads alive.  The bandwidth the table gathers of the field kernel are
+// compared with.
+__global__ void __launch_bounds__(256) l2_read_kernel(const float4 *__restrict__ buf, size_t n4, int reps,
+                                                      float *__restrict__ sink) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (int r = 0; r < reps; ++r) {
+#pragma unroll 4
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+            const float4 v = __ldcg(buf + i);
+            acc.x += v.x;
+            acc.y += v.y;
+            acc.z += v.z;
+            acc.w += v.w;
+        }
+    }
+    const float t = (acc.x + acc.y) + (acc.z + acc.w);
+    if (t == 1.25e-30f) *sink = t;   // practically never: the loads cannot be dropped
+}
+
+__global__ void l2_fill_kernel(float4 *__restrict__ buf, size_t n4) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x)
+        buf[i] = make_float4(1e-3f, 2e-3f, 3e-3f, (float)(i & 255) * 1e-6f);
+}
+
+cudaError_t launch_l2_fill(void *buf, size_t bytes, float *sink, cudaStream_t s) {
+    const size_t n4 = bytes / 16;
+    l2_fill_kernel<<<152 * 8, 256, 0, s>>>(reinterpret_cast<float4 *>(buf), n4);
+    l2_read_kernel<<<152 * 8, 256, 0, s>>>(reinterpret_cast<const float4 *>(buf), n4, 1, sink);   // warm
+    return cudaGetLastError();
+}
+
+cudaError_t launch_l2_read(const void *buf, size_t bytes, int reps, float *sink, cudaStream_t s) {
+    l2_read_kernel<<<152 * 8, 256, 0, s>>>(reinterpret_cast<const float4 *>(buf), bytes / 16, reps, sink);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------- tone map
 // psi: sRGB transfer function (IEC 61966-2-1) of the clamped, exposed radiance
 __global__ void __launch_bounds__(256) tonemap_kernel(const float4 *__restrict__ in, uint32_t n, float exposure,

@@ -15,7 +15,6 @@
 // the same FP32 formulas as the megakernel.  Jobs whose samples do not fit the
 // sample buffer are marched in place by wf_shade on the CUDA cores.
 #include <algorithm>
-#include <mutex>
 
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
@@ -99,8 +98,14 @@ __device__ __forceinline__ uint32_t next_chunk(uint32_t *work, int S, int lane) 
 // [2] generated samples, [3] network shadow rays, then per generation round r
 // a block of four: slots left pending, and the work counters of wf_gen,
 // wf_mask and wf_composite.  One memset per segment clears [2, 4 + 4 * rounds).
+// Then the persistent tail's words: the segment it took over at (0: none),
+// the paths live then, and its work counter; cleared once per frame.
 __device__ __forceinline__ uint32_t *pending_ctr(const WfParams &W, int r) { return W.ctr + 4 + 4 * r; }
 __device__ __forceinline__ uint32_t *work_ctr(const WfParams &W, int r, int k) { return W.ctr + 5 + 4 * r + k; }
+constexpr int kTailWord = 4 + 4 * kMaxRounds;
+constexpr int kCtrWords = kTailWord + 3;
+// true once the persistent tail (wf_tail) has taken over the remaining segments
+__device__ __forceinline__ bool tail_taken(const WfParams &W) { return W.ctr[kTailWord] != 0u; }
 
 // Shared-memory copies used by the sample walk: coarse occupancy bits and the
 // density-support spheres.
@@ -332,25 +337,31 @@ __device__ __noinline__ uint2 warp_walk(const RenderParams &P, const WalkCtx &X,
     return make_uint2(k, (uint32_t)S.n);
 }
 
-// Writes a job's samples from its recorded runs (lane-parallel over the run's
-// intervals, positions by the same FP32 formulas as the walk).
+// Writes samples [first, first + limit) of a job from its recorded runs into
+// out[0, limit) (lane-parallel over the run's intervals, positions by the same
+// FP32 formulas as the walk).
 __device__ void write_runs(const RenderParams &P, V3 o, V3 d, float a, float b, const RunList &R, float4 *out,
-                           uint32_t limit, int lane) {
+                           uint32_t limit, int lane, uint32_t first = 0) {
     Segment S;
     to_field_frame(P.F, o, d);
     if (!segment_of(P, o, d, a, b, S)) return;
     uint32_t k = 0;
     for (int r = 0; r < R.n; ++r) {
         const int2 run = R.r[r];
-        for (int i = run.x + lane; i < run.y; i += 32) {
-            const float lo = fmaf((float)i, S.h, S.t0);
-            const float hi = P.steps ? fmaf((float)(i + 1), S.h, S.t0) : fminf(lo + S.h, S.t1);
-            const float tm = 0.5f * (lo + hi), delta = hi - lo;
-            const V3 p = fma3(d, tm, o);
-            const uint32_t slot = k + (uint32_t)(i - run.x);
-            if (slot < limit) out[slot] = make_float4(p.x, p.y, p.z, delta);
+        const uint32_t len = (uint32_t)(run.y - run.x);
+        if (k + len > first) {
+            const int i_first = run.x + (int)(first > k ? first - k : 0u);
+            for (int i = i_first + lane; i < run.y; i += 32) {
+                const float lo = fmaf((float)i, S.h, S.t0);
+                const float hi = P.steps ? fmaf((float)(i + 1), S.h, S.t0) : fminf(lo + S.h, S.t1);
+                const float tm = 0.5f * (lo + hi), delta = hi - lo;
+                const V3 p = fma3(d, tm, o);
+                const uint32_t slot = k + (uint32_t)(i - run.x) - first;
+                if (slot < limit) out[slot] = make_float4(p.x, p.y, p.z, delta);
+            }
         }
-        k += (uint32_t)(run.y - run.x);
+        k += len;
+        if (k >= first + limit) break;
     }
 }
 
@@ -369,6 +380,16 @@ __global__ void __launch_bounds__(kThreads, 5) wf_cast(const WfParams W, uint32_
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t live = j == 1 ? W.paths : W.ctr[cur];
     const int K = P.n_shadow;
+    if (j > 1) {
+        if (tail_taken(W)) return;
+        if (live <= P.tail_paths) {   // few paths left: the persistent tail finishes them
+            if (tid == 0) {
+                W.ctr[kTailWord + 1] = live;
+                W.ctr[kTailWord] = j;
+            }
+            return;
+        }
+    }
     Counters C = {};
     if (j == 1 && tid == 0) W.ctr[cur] = W.paths;  // every path is live in segment 1
     uint64_t nmask = 0;   // shadow rays of this slot answered by the network
@@ -472,6 +493,7 @@ __global__ void __launch_bounds__(kThreads, 5) wf_cast(const WfParams W, uint32_
 // later kernels look at each ray's sw.w.
 __global__ void __launch_bounds__(kThreads, 5) wf_vis(const WfParams W, int cur) {
     const RenderParams &P = W.R;
+    if (tail_taken(W)) return;
     const uint32_t K = (uint32_t)P.n_shadow;
     const uint64_t total = (uint64_t)W.ctr[cur] * K;
     Counters C = {};
@@ -514,6 +536,7 @@ __global__ void __launch_bounds__(kThreads, 5) wf_vis(const WfParams W, int cur)
 __global__ void __launch_bounds__(128) wf_shadow_net(const WfParams W) {
     __shared__ __align__(16) float wsm[kSnetMlp + 3];
     const RenderParams &P = W.R;
+    if (tail_taken(W)) return;
     for (int i = threadIdx.x; i < kSnetMlp; i += blockDim.x) wsm[i] = P.snet.mlp[i];
     __syncthreads();
     const uint32_t n = W.ctr[3], K = (uint32_t)P.n_shadow;
@@ -536,7 +559,7 @@ __global__ void __launch_bounds__(kThreads, 6) wf_gen(const WfParams W, uint32_t
     __shared__ WalkSmem wsm;
     __shared__ RunList runs_sm[kThreads / 32][32][2];   // per warp, per slot: segment job, first shadow job
     const RenderParams &P = W.R;
-    if (round > 0 && *pending_ctr(W, round - 1) == 0) return;   // nothing pending: the whole grid leaves
+    if (tail_taken(W) || (round > 0 && *pending_ctr(W, round - 1) == 0)) return;   // nothing to do: the grid leaves
     const WalkCtx X = stage_walk(P.F, wsm);
     const int lane = threadIdx.x & 31;
     const uint32_t live = j == 1 ? W.paths : W.ctr[cur];
@@ -651,12 +674,12 @@ __global__ void __launch_bounds__(kThreads, 6) wf_gen(const WfParams W, uint32_t
 // Stops after the sample at which max(T) falls below tau.  Each lane returns
 // its partial sums of L; `depth` (the job's optical depth up to the stop) and
 // `stop` are the same in every lane.
-__device__ __forceinline__ void warp_composite(const WfParams &W, uint32_t start, uint32_t count, float tmax0,
-                                               float tau, int lane, float &lr, float &lg, float &lb, float &depth,
-                                               bool &stop) {
-    lr = lg = lb = 0.f;
-    depth = 0.f;
-    stop = false;
+// warp_composite_from continues a job from the lane partial sums, depth and
+// stop of its earlier samples: a job split at multiples of 32 samples gives the
+// same results as one call.
+__device__ __forceinline__ void warp_composite_from(const WfParams &W, uint32_t start, uint32_t count, float tmax0,
+                                                    float tau, int lane, float &lr, float &lg, float &lb,
+                                                    float &depth, bool &stop) {
     // eight 32-sample chunks are loaded before the first is composited, so that a
     // job costs one memory round trip per 256 samples (loads past the stop are
     // inside the job's range and harmless)
@@ -699,6 +722,15 @@ __device__ __forceinline__ void warp_composite(const WfParams &W, uint32_t start
     }
 }
 
+__device__ __forceinline__ void warp_composite(const WfParams &W, uint32_t start, uint32_t count, float tmax0,
+                                               float tau, int lane, float &lr, float &lg, float &lb, float &depth,
+                                               bool &stop) {
+    lr = lg = lb = 0.f;
+    depth = 0.f;
+    stop = false;
+    warp_composite_from(W, start, count, tmax0, tau, lane, lr, lg, lb, depth, stop);
+}
+
 __device__ __forceinline__ float warp_sum(float x) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
@@ -713,7 +745,7 @@ __device__ __forceinline__ float warp_sum(float x) {
 // composited slots are marked done so that later rounds pass them by.
 __global__ void __launch_bounds__(kThreads, 8) wf_composite(const WfParams W, int cur, int round) {
     const RenderParams &P = W.R;
-    if (round > 0 && *pending_ctr(W, round - 1) == 0) return;
+    if (tail_taken(W) || (round > 0 && *pending_ctr(W, round - 1) == 0)) return;
     const int lane = threadIdx.x & 31;
     const uint32_t live = W.ctr[cur];
     const int S = chunk_slots(live);
@@ -770,7 +802,7 @@ __global__ void __launch_bounds__(kThreads, 8) wf_composite(const WfParams W, in
 // the samples of each of its slots' jobs.
 __global__ void __launch_bounds__(kThreads) wf_mask(const WfParams W, int cur, int round) {
     const RenderParams &P = W.R;
-    if (round > 0 && *pending_ctr(W, round - 1) == 0) return;
+    if (tail_taken(W) || (round > 0 && *pending_ctr(W, round - 1) == 0)) return;
     const int lane = threadIdx.x & 31;
     const uint32_t live = W.ctr[cur];
     const int S = chunk_slots(live);
@@ -808,7 +840,7 @@ __global__ void __launch_bounds__(kThreads) wf_mask(const WfParams W, int cur, i
 __global__ void __launch_bounds__(kThreads) wf_overflow(const WfParams W, int cur) {
     const RenderParams &P = W.R;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= W.ctr[cur]) return;
+    if (tail_taken(W) || tid >= W.ctr[cur]) return;
     const int K = P.n_shadow;
     const bool rad = W.rcount[tid] == kOverflow;
     const float4 h4 = W.hp[tid];
@@ -849,6 +881,7 @@ __global__ void __launch_bounds__(kThreads) wf_overflow(const WfParams W, int cu
 // terms, sample the BSDF (Eqs. 12-13), test termination and push survivors.
 __global__ void __launch_bounds__(kThreads) wf_shade(const WfParams W, uint32_t j, int cur, int nxt) {
     const RenderParams &P = W.R;
+    if (tail_taken(W)) return;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t live = W.ctr[cur];
     const int K = P.n_shadow;
@@ -951,6 +984,312 @@ __global__ void __launch_bounds__(kThreads) wf_shade(const WfParams W, uint32_t 
     flush_counters(P.stats, C);
 }
 
+// ---------------------------------------------------------------------------
+// Persistent tail.  When at most the tuning's tail_paths paths are live at the
+// start of a segment, wf_cast records that segment and every kernel of the
+// remaining segments leaves at once; wf_tail, launched once after them, then
+// finishes the remaining paths: each warp pops a path from the live queue and
+// runs all of its remaining segments, with the wavefront's own steps and
+// formulas (closest hit, shadow rays, the sample walk of wf_gen, compositing
+// by warp_composite, the surface event of wf_shade).  Paths then wait only on
+// their own chain of dependent traversals instead of the slowest path of every
+// segment.  The few samples of the tail are evaluated on the CUDA cores with
+// the FP32 weights (also for FP16/BF16 fields, as the overflow march does); an
+// FP32 field gives the wavefront engine's result bit for bit.
+constexpr int kTailWarps = 8;   // warps per tail block
+
+// The steps of the tail that need many registers, kept out of its main loop:
+// one field sample as the FP32 field kernel and wf_mask evaluate it,
+__device__ __noinline__ float4 tail_sample(const RenderParams &P, const float *wts, float4 rec, V3 dl, bool radiance) {
+    const V3 p = v3(rec.x, rec.y, rec.z);
+    float rgb[3] = {0.f, 0.f, 0.f}, sigma = 0.f;
+    if (inside_field_box(P.F, p)) {
+        bool ev;
+        sigma = field_at<true>(P.F, wts, p, dl, rgb, ev);
+    }
+    float4 f = make_float4(sigma * rec.w, rgb[0], rgb[1], rgb[2]);
+    if (radiance && P.shadow_mask && f.x > 0.f) {
+        const float m = sample_mask(P, field_to_world(P.F, p));
+        if (m != 1.f) {
+            f.y *= m;
+            f.z *= m;
+            f.w *= m;
+        }
+    }
+    return f;
+}
+
+// a segment whose samples do not fit the warp's slice, marched in place as wf_overflow does,
+__device__ __noinline__ float4 tail_march(const RenderParams &P, V3 o, V3 d, float t_hit, const float T[3]) {
+    float Tm[3] = {T[0], T[1], T[2]}, Lm[3] = {0.f, 0.f, 0.f};
+    bool stop = false;
+    Counters dummy = {};
+    march<true>(P, P.F.mlp, o, d, 0.f, t_hit, Tm, Lm, stop, dummy);
+    const int c = (T[0] >= T[1] && T[0] >= T[2]) ? 0 : (T[1] >= T[2] ? 1 : 2);
+    const float dep = T[c] > 0.f ? logf(T[c] / fmaxf(Tm[c], 1e-38f)) : 0.f;
+    return make_float4(T[0] > 0.f ? Lm[0] / T[0] : 0.f, T[1] > 0.f ? Lm[1] / T[1] : 0.f, T[2] > 0.f ? Lm[2] / T[2] : 0.f,
+                       stop ? -dep - 1.f : dep);
+}
+
+// the optical depth of a shadow ray marched in place,
+__device__ __noinline__ float tail_shadow_depth(const RenderParams &P, V3 p, V3 w, float D) {
+    Counters dummy = {};
+    bool dstop = false;
+    return march<false>(P, P.F.mlp, p, w, 0.f, D, nullptr, nullptr, dstop, dummy);
+}
+
+// the compositing of a window of a segment's samples (warp_composite, continued),
+__device__ __noinline__ void tail_composite(const WfParams &W, uint32_t start, uint32_t n, float tmax0, int lane,
+                                            float &lr, float &lg, float &lb, float &dep, bool &stp) {
+    warp_composite_from(W, start, n, tmax0, W.R.tau, lane, lr, lg, lb, dep, stp);
+}
+
+// the network's transmittance of a shadow ray,
+__device__ __noinline__ float tail_net(const RenderParams &P, V3 p, V3 w) { return snet_eval(P.snet, P.snet.mlp, p, w); }
+
+// the closest hit of a path's segment (with its traversal statistics),
+__device__ __noinline__ Hit tail_cast(const RenderParams &P, V3 o, V3 d, uint32_t prev, uint32_t path, Counters &C) {
+    Hit h;
+    unsigned rt = 0;
+    bool fault = false;
+    const unsigned nodes0 = C.nodes;
+    bvh_trace<false>(P.B, o, d, prev, P.tmin, INFINITY, h, rt, C.nodes, C.tris, fault);
+    note_traversal(C, C.nodes - nodes0, path);
+    C.retests += rt;
+    if (fault) C.fault |= 1;
+    return h;
+}
+
+// and the visibility of a shadow ray (true: a mesh blocks it).
+__device__ __noinline__ bool tail_blocked(const RenderParams &P, V3 p, V3 w, uint32_t skip, float D, Counters &C) {
+    Hit hs;
+    unsigned rs = 0;
+    bool f2 = false;
+    const bool blocked = bvh_trace<true>(P.B, p, w, skip, P.tmin, D, hs, rs, C.nodes, C.tris, f2);
+    C.retests += rs;
+    if (f2) C.fault |= 1;
+    return blocked;
+}
+
+__global__ void __launch_bounds__(32 * kTailWarps, 1) wf_tail(const WfParams W) {
+    extern __shared__ float tail_w[];     // FP32 field weights (hash grid)
+    __shared__ WalkSmem wsm;
+    __shared__ RunList runs_sm[kTailWarps];
+    const RenderParams &P = W.R;
+    const uint32_t j0 = W.ctr[kTailWord];
+    if (j0 == 0u) return;
+    const WalkCtx X = stage_walk(P.F, wsm);
+    const float *wts = P.F.mlp;
+    if (P.F.kind == MRF_FIELD_HASHGRID) {
+        const int nw = field_mlp_floats(P.F);
+        for (int i = threadIdx.x; i < nw; i += blockDim.x) tail_w[i] = P.F.mlp[i];
+        __syncthreads();
+        wts = tail_w;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t live = W.ctr[kTailWord + 1];
+    const int qi = (int)((j0 - 1u) & 1u);
+    const int K = P.n_shadow;
+    // this warp's slice of the (otherwise idle) sample buffer
+    const uint32_t n_warps = gridDim.x * kTailWarps, gw = blockIdx.x * kTailWarps + wid;
+    // windows of up to 1024 samples (a multiple of 32), whatever the buffer size, so
+    // that every buffer gives the same result
+    const uint32_t slice = min(W.cap / n_warps, 1024u) & ~31u, sbase = gw * slice;
+    RunList &rl = runs_sm[wid];
+    Counters C = {};
+    for (uint32_t slot; (slot = next_chunk(W.ctr + kTailWord + 2, 1, lane)) < live;) {
+        const uint32_t path = W.qpath[qi][slot];
+        const float4 qo = W.qo[qi][slot], qd = W.qd[qi][slot], qT = W.qT[qi][slot];
+        V3 o = v3(qo.x, qo.y, qo.z), d = v3(qd.x, qd.y, qd.z);
+        uint32_t prev = __float_as_uint(qo.w);
+        float T[3] = {qT.x, qT.y, qT.z};
+        float4 acc = W.acc[path];
+        float L[3] = {acc.x, acc.y, acc.z};
+        const uint32_t ray = path / P.spp, sp = path % P.spp;
+        const uint64_t rbase = (uint64_t)path * P.max_bounces;
+        for (uint32_t j = j0; j <= P.max_bounces; ++j) {
+            // closest hit (Eq. 3), traced by lane 0
+            Hit h;
+            h.t = INFINITY;
+            h.slot = -1;
+            h.id = kNoHit;
+            if (lane == 0) h = tail_cast(P, o, d, prev, path, C);
+            h.t = __shfl_sync(0xffffffffu, h.t, 0);
+            h.slot = __shfl_sync(0xffffffffu, h.slot, 0);
+            h.id = __shfl_sync(0xffffffffu, h.id, 0);
+            SurfaceHit S;
+            bool diffuse = false;
+            if (h.id != kNoHit) {
+                S = surface_at(P, o, d, h);
+                diffuse = S.mat.kind == MRF_MAT_DIFFUSE;
+            }
+            // shadow rays at a diffuse hit: lane l holds rays l and l + 32
+            V3 pl = diffuse ? S.p : v3(0.f, 0.f, 0.f), wdummy = v3(0.f, 0.f, 1.f);
+            if (diffuse && P.has_snet) snet_to_local(P.snet, pl, wdummy);
+            const bool net = diffuse && P.has_snet && snet_inside(P.snet, pl);
+            float sw_w[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, s_tf[2] = {0.f, 0.f};
+            bool s_on[2] = {false, false};   // unblocked (weight applies)
+            V3 s_dir[2] = {v3(0.f, 0.f, 1.f), v3(0.f, 0.f, 1.f)};
+            float s_D[2] = {0.f, 0.f};
+            // the value of ray q, held by lane q % 32 in entry q / 32, in every lane
+            auto from = [&](const float (&v)[2], int q) {
+                return __shfl_sync(0xffffffffu, q < 32 ? v[0] : v[1], q & 31);
+            };
+            if (diffuse) {
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int qq = lane + 32 * h2;
+                    if (qq >= K) continue;
+                    int l = 0;
+                    while (l + 1 < P.n_lights && (int)P.lights[l + 1].slot0 <= qq) ++l;
+                    const uint32_t k = (uint32_t)qq - P.lights[l].slot0;
+                    V3 wl;
+                    float D, w3[3];
+                    if (!shadow_ray(P, S, l, k, ray, sp, j, wl, D, w3)) continue;
+                    ++C.shadow;
+                    if (tail_blocked(P, S.p, wl, S.id, D, C)) continue;
+                    s_on[h2] = true;
+                    s_dir[h2] = wl;
+                    s_D[h2] = D;
+                    sw_w[h2][0] = w3[0];
+                    sw_w[h2][1] = w3[1];
+                    sw_w[h2][2] = w3[2];
+                    if (net) {
+                        s_tf[h2] = tail_net(P, S.p, wl);
+                        ++C.net;
+                    }
+                }
+            }
+            // marches: job -1 the segment [0, t_hit], job q >= 0 shadow ray q (marched ones)
+            float4 comp = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float tmax0 = fmaxf(T[0], fmaxf(T[1], T[2]));
+            for (int q = -1; q < (diffuse && !net ? K : 0); ++q) {
+                V3 jo = o, jd = d;
+                float jb = h.t;
+                if (q >= 0) {
+                    if (!__shfl_sync(0xffffffffu, (int)(q < 32 ? s_on[0] : s_on[1]), q & 31)) continue;
+                    jo = S.p;
+                    jd = shfl3(q < 32 ? s_dir[0] : s_dir[1], q & 31);
+                    jb = from(s_D, q);
+                }
+                const uint2 wr = warp_walk(P, X, jo, jd, 0.f, jb, nullptr, 0, lane, &rl);
+                const uint32_t n = wr.x;
+                if (lane == 0) {
+                    C.nominal += wr.y;
+                    if (q < 0) C.evaluated += n;
+                    else C.shadow_eval += n;
+                }
+                __syncwarp();
+                float res = 0.f;   // shadow: optical depth
+                const bool replay = rl.n <= kRunsPerJob;
+                if (slice > 0 && (replay || n <= slice)) {
+                    // the job's samples in windows of the slice (a multiple of 32 samples):
+                    // written, evaluated, then composited from the carried sums
+                    float lr = 0.f, lg = 0.f, lb = 0.f, dep = 0.f;
+                    bool stp = false;
+                    V3 ol = jo, dl = jd;
+                    to_field_frame(P.F, ol, dl);
+                    for (uint32_t c0 = 0; c0 < n && !stp; c0 += slice) {
+                        const uint32_t cn = min(slice, n - c0);
+                        if (replay)
+                            write_runs(P, jo, jd, 0.f, jb, rl, W.samp + sbase, cn, lane, c0);
+                        else   // more runs than recorded (then n <= slice): the walk writes them
+                            warp_walk(P, X, jo, jd, 0.f, jb, W.samp + sbase, cn, lane, nullptr);
+                        __syncwarp();
+                        for (uint32_t i = lane; i < cn; i += 32)
+                            W.fout[sbase + i] = tail_sample(P, wts, W.samp[sbase + i], dl, q < 0);
+                        __syncwarp();
+                        if (q < 0) {
+                            tail_composite(W, sbase, cn, tmax0, lane, lr, lg, lb, dep, stp);
+                        } else {
+#pragma unroll 4
+                            for (uint32_t i0 = lane; i0 < cn; i0 += 32) dep += W.fout[sbase + i0].x;
+                        }
+                        __syncwarp();
+                    }
+                    if (q < 0) comp = make_float4(warp_sum(lr), warp_sum(lg), warp_sum(lb), stp ? -dep - 1.f : dep);
+                    else res = warp_sum(dep);
+                } else if (q < 0) {
+                    // no room at all: marched in place, as wf_overflow does
+                    comp = tail_march(P, o, d, h.t, T);
+                } else {
+                    res = tail_shadow_depth(P, S.p, jd, jb);
+                }
+                if (q >= 0 && lane == (q & 31)) {
+                    if (q < 32) s_tf[0] = res;
+                    else s_tf[1] = res;
+                }
+            }
+            // the surface event (all lanes take the same steps; lane 0 records)
+            bool stop = comp.w < 0.f;
+            {
+                const float att = expf(-(stop ? -comp.w - 1.f : comp.w));
+                L[0] = fmaf(T[0], comp.x, L[0]);
+                L[1] = fmaf(T[1], comp.y, L[1]);
+                L[2] = fmaf(T[2], comp.z, L[2]);
+                T[0] *= att;
+                T[1] *= att;
+                T[2] *= att;
+            }
+            if (lane == 0) {
+                ++C.seg;
+                if (P.rec_tri) {
+                    P.rec_tri[rbase + (j - 1)] = h.id;
+                    P.rec_t[rbase + (j - 1)] = h.t;
+                }
+            }
+            bool end = stop || h.id == kNoHit;
+            int cause = stop ? 2 : (h.id == kNoHit ? 1 : 0);
+            if (!end) {
+                if (lane == 0) ++C.hits;
+                float u[3];
+                surface_uniforms(P, ray, sp, j, u);
+                if (diffuse) {
+                    for (int q = 0; q < K; ++q) {
+                        if (!__shfl_sync(0xffffffffu, (int)(q < 32 ? s_on[0] : s_on[1]), q & 31)) continue;
+                        const float tq = from(s_tf, q);
+                        const float Tf = net ? tq : expf(-tq);
+                        const float w0 = __shfl_sync(0xffffffffu, q < 32 ? sw_w[0][0] : sw_w[1][0], q & 31);
+                        const float w1 = __shfl_sync(0xffffffffu, q < 32 ? sw_w[0][1] : sw_w[1][1], q & 31);
+                        const float w2 = __shfl_sync(0xffffffffu, q < 32 ? sw_w[0][2] : sw_w[1][2], q & 31);
+                        L[0] = fmaf(T[0] * Tf, w0, L[0]);
+                        L[1] = fmaf(T[1] * Tf, w1, L[1]);
+                        L[2] = fmaf(T[2] * Tf, w2, L[2]);
+                    }
+                }
+                const V3 nd = bsdf_sample(S, d, u, T);
+                d = normalize(nd);
+                o = S.p;
+                prev = S.id;
+                if (P.tau > 0.f && fmaxf(T[0], fmaxf(T[1], T[2])) < P.tau) {
+                    end = true;
+                    cause = 2;
+                } else if (j == P.max_bounces) {
+                    end = true;
+                    cause = 3;
+                }
+            }
+            if (end) {
+                if (lane == 0) {
+                    C.end_miss += cause == 1;
+                    C.end_tau += cause == 2;
+                    C.end_cap += cause == 3;
+                    if (P.rec_seg) P.rec_seg[path] = j;
+                    if (P.rec_tri)
+                        for (uint32_t q = j; q < P.max_bounces; ++q) {
+                            P.rec_tri[rbase + q] = kNoHit;
+                            P.rec_t[rbase + q] = INFINITY;
+                        }
+                }
+                break;
+            }
+        }
+        if (lane == 0) W.acc[path] = make_float4(L[0], L[1], L[2], acc.w);
+    }
+    flush_counters(P.stats, C);
+    if (C.fault && P.status) atomicOr(P.status, C.fault);
+}
+
 __global__ void __launch_bounds__(kThreads) wf_finalize(const float4 *__restrict__ acc, uint32_t count, uint32_t spp,
                                                         float4 *__restrict__ out) {
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1000,7 +1339,7 @@ Layout layout(uint32_t paths, int n_shadow, uint32_t cap_per_path = 96, bool vie
     L.comp = take(16 * P);
     L.sdepth = take(4 * P * nl);
     L.squeue = take(4 * P * nl);
-    L.ctr = take(4 * (4 + 4 * kMaxRounds));
+    L.ctr = take(4 * kCtrWords);
     // sample capacity: cap_per_path samples per path plus 4M (overflowing jobs are marched in place)
     const uint64_t cap = std::min<uint64_t>((uint64_t)P * (cap_per_path ? cap_per_path : 96) + (4u << 20),
                                             0x7FFFFFFFull);
@@ -1022,7 +1361,7 @@ cudaError_t enqueue_frame(const WfParams &W, const RenderParams &P, uint32_t pat
     const int field_grid = tc ? 152 * field_tc_blocks_per_sm(groups) : 152 * 8;
     const int rounds = std::min(std::max(P.max_rounds, 1), kMaxRounds);
     // counters left over from the previous call
-    cudaError_t e = cudaMemsetAsync(W.ctr, 0, 4 * (4 + 4 * kMaxRounds), s);
+    cudaError_t e = cudaMemsetAsync(W.ctr, 0, 4 * kCtrWords, s);
     if (e != cudaSuccess) return e;
     // NVTX ranges mark the host-side enqueue of the frame and of each segment
     struct Range {
@@ -1099,6 +1438,22 @@ cudaError_t enqueue_frame(const WfParams &W, const RenderParams &P, uint32_t pat
         timer_end(timer, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    if (P.tail_paths > 0 && P.max_bounces > 1) {
+        // the persistent tail: one launch, as many blocks as are resident at once
+        const size_t tsmem = F.kind == MRF_FIELD_HASHGRID ? (size_t)field_mlp_floats(F) * sizeof(float) : 0;
+        static int tail_blocks_per_sm[2] = {0, 0};   // [0]: no dynamic shared memory, [1]: with
+        int &bps = tail_blocks_per_sm[tsmem ? 1 : 0];
+        if (tsmem > 48 * 1024 &&
+            (e = cudaFuncSetAttribute(wf_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem)) != cudaSuccess)
+            return e;
+        if (bps == 0 &&
+            (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, wf_tail, 32 * kTailWarps, tsmem)) != cudaSuccess)
+            return e;
+        timer_begin(timer, MRF_KERNEL_TAIL, s);
+        wf_tail<<<152 * std::max(bps, 1), 32 * kTailWarps, tsmem, s>>>(W);
+        timer_end(timer, s);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     timer_begin(timer, MRF_KERNEL_FINALIZE, s);
     wf_finalize<<<(P.count + kThreads - 1) / kThreads, kThreads, 0, s>>>(W.acc, P.count, P.spp,
                                                                           reinterpret_cast<float4 *>(P.out));
@@ -1163,17 +1518,15 @@ cudaError_t launch_render_wavefront(const RenderParams &P, void *scratch, size_t
 constexpr size_t kStaticArenaBytes = (size_t)64 << 20;   // 64 MiB
 constexpr uint32_t kStaticMaxPaths = 1u << 17;           // count * spp limit
 constexpr int kStaticMaxLights = 8;   // shadow rays per diffuse hit
+constexpr size_t kStaticMinSampleBytes = 2 * 16 * 128 + 512;   // one 128-sample tile in and out, plus slack
 static __device__ __align__(256) unsigned char g_static_arena[kStaticArenaBytes];
 
 namespace {
-std::mutex g_arena_mu;
-void *g_arena_addr[64] = {};
-
 // per-path state of the wavefront engine plus a sample buffer filling the rest
 Layout layout_in(uint32_t paths, int n_shadow, size_t bytes, bool &fits) {
     Layout L = layout(paths, n_shadow);
     const size_t state = L.samp;   // everything before the sample buffers
-    fits = bytes > state + 2 * 16 * 128 + 512;
+    fits = bytes > state + kStaticMinSampleBytes;
     if (!fits) return L;
     const uint64_t cap = std::min<uint64_t>((bytes - state - 512) / 32, 0x7FFFFFFFull);
     L.cap = (uint32_t)cap;
@@ -1187,18 +1540,30 @@ Layout layout_in(uint32_t paths, int n_shadow, size_t bytes, bool &fits) {
 uint32_t static_arena_max_paths() { return kStaticMaxPaths; }
 int static_arena_max_lights() { return kStaticMaxLights; }
 
-// Resolves the device address of the arena on the current device, once per
-// device (the first call on a device therefore runs cudaGetSymbolAddress).
-cudaError_t static_arena(int device, void **ptr, size_t *bytes) {
-    std::lock_guard<std::mutex> lk(g_arena_mu);
-    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
-    if (!g_arena_addr[device]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_arena);
-        if (e != cudaSuccess) return e;
-        g_arena_addr[device] = p;
+// Largest path count whose per-path state, with n_shadow shadow rays per hit,
+// leaves the arena a sample buffer of at least one tile (at most the fixed
+// path limit).  The state grows by about 172 + 48 * max(n_shadow, 1) bytes per path.
+uint32_t static_arena_paths_that_fit(int n_shadow) {
+    uint32_t lo = 0, hi = kStaticMaxPaths;
+    while (lo < hi) {
+        const uint32_t mid = lo + (hi - lo + 1) / 2;
+        bool fits = false;
+        layout_in(mid, n_shadow, kStaticArenaBytes, fits);
+        if (fits) lo = mid;
+        else hi = mid - 1;
     }
-    *ptr = g_arena_addr[device];
+    return lo;
+}
+
+// Device address of the arena on the current device.  The host-side name
+// g_static_arena is only a stand-in for the symbol, so host code must not pass
+// it to a kernel; cudaGetSymbolAddress gives the device address.  Called once
+// per context, at its creation, with the context's device current.
+cudaError_t static_arena(void **ptr, size_t *bytes) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_arena);
+    if (e != cudaSuccess) return e;
+    *ptr = p;
     *bytes = kStaticArenaBytes;
     return cudaSuccess;
 }

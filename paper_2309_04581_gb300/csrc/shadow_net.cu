@@ -140,16 +140,30 @@ __device__ __forceinline__ float row_sum(const float *row) {
     return s;
 }
 
+// Gradients are summed in 64-bit fixed point with 2^-40 units: integer
+// addition is associative, so the sum of a batch does not depend on the order
+// in which blocks and threads add their parts, and training reruns and resumes
+// bit for bit.  |part| < 2^23 and |sum| < 2^23 hold with a wide margin (the
+// loss is a mean of squared errors of a sigmoid, per-pair parts carry 1/B).
+constexpr float kGradUnit = 1099511627776.0f;   // 2^40
+__device__ __forceinline__ void grad_add(unsigned long long *acc, float x) {
+    atomicAdd(acc, (unsigned long long)__float2ll_rn(x * kGradUnit));
+}
+__device__ __forceinline__ float grad_value(unsigned long long v) {
+    return (float)((double)(long long)v * (1.0 / 1099511627776.0));
+}
+
 // One pass over pairs [b0, b0 + B) (cyclic in n_pairs) accumulating the loss
-// and the gradient of every parameter into grad (which the caller cleared).
+// and the gradient of every parameter into the fixed-point sums gacc (which
+// the caller cleared).
 __global__ void __launch_bounds__(kTT, 1)
-snet_train_kernel(const ShadowNetDev N, const float *__restrict__ params, float *__restrict__ grad,
+snet_train_kernel(const ShadowNetDev N, const float *__restrict__ params, unsigned long long *__restrict__ gacc,
                   const float *__restrict__ pairs, uint64_t n_pairs, uint64_t b0, uint32_t B, float *loss) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TrainSmem &S = *reinterpret_cast<TrainSmem *>(smem_raw);
     const int tid = threadIdx.x, mg = tid >> 4, ng = tid & 15;
     const float *mlp = params + ((size_t)kSnetLevels << N.log2T) * 2;
-    float *gmlp = grad + ((size_t)kSnetLevels << N.log2T) * 2;
+    unsigned long long *gmlp = gacc + ((size_t)kSnetLevels << N.log2T) * 2;
     // weights, in both orientations
     for (int i = tid; i < kSnetW * kSnetIn; i += kTT) {
         const int u = i / kSnetIn, k = i % kSnetIn;
@@ -329,7 +343,8 @@ snet_train_kernel(const ShadowNetDev N, const float *__restrict__ params, float 
                 const uint32_t i = snet_index(N, l, c[0] + (v & 1), c[1] + ((v >> 1) & 1), c[2] + ((v >> 2) & 1));
                 const float wt = ((v & 1) ? f[0] : 1.f - f[0]) * (((v >> 1) & 1) ? f[1] : 1.f - f[1]) *
                                  (((v >> 2) & 1) ? f[2] : 1.f - f[2]);
-                atomicAdd(reinterpret_cast<float2 *>(grad) + i, make_float2(wt * g0, wt * g1));
+                grad_add(gacc + 2 * (size_t)i, wt * g0);
+                grad_add(gacc + 2 * (size_t)i + 1, wt * g1);
             }
         }
         __syncthreads();
@@ -340,19 +355,19 @@ snet_train_kernel(const ShadowNetDev N, const float *__restrict__ params, float 
         const int u = 4 * mg + i;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            atomicAdd(gmlp + kSnetOffW2 + u * kSnetW + ng + 16 * j, gW2[i][j]);
-            atomicAdd(gmlp + kSnetOffW3 + u * kSnetW + ng + 16 * j, gW3[i][j]);
+            grad_add(gmlp + kSnetOffW2 + u * kSnetW + ng + 16 * j, gW2[i][j]);
+            grad_add(gmlp + kSnetOffW3 + u * kSnetW + ng + 16 * j, gW3[i][j]);
         }
 #pragma unroll
-        for (int j = 0; j < 2; ++j) atomicAdd(gmlp + u * kSnetIn + ng + 16 * j, gW1[i][j]);
+        for (int j = 0; j < 2; ++j) grad_add(gmlp + u * kSnetIn + ng + 16 * j, gW1[i][j]);
     }
     if (tid < kSnetW) {
-        atomicAdd(gmlp + kSnetOffB1 + tid, gb1);
-        atomicAdd(gmlp + kSnetOffB2 + tid, gb2);
-        atomicAdd(gmlp + kSnetOffB3 + tid, gb3);
-        atomicAdd(gmlp + kSnetOffW4 + tid, gW4);
+        grad_add(gmlp + kSnetOffB1 + tid, gb1);
+        grad_add(gmlp + kSnetOffB2 + tid, gb2);
+        grad_add(gmlp + kSnetOffB3 + tid, gb3);
+        grad_add(gmlp + kSnetOffW4 + tid, gW4);
     }
-    if (tid == 0) atomicAdd(gmlp + kSnetOffB4, gb4);
+    if (tid == 0) grad_add(gmlp + kSnetOffB4, gb4);
     if (loss && tid < kTile) {   // two full warps hold the per-pair losses
         float x = lsum;
         for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
@@ -361,18 +376,26 @@ snet_train_kernel(const ShadowNetDev N, const float *__restrict__ params, float 
 }
 
 // Adam (Kingma and Ba) with bias correction c1 = 1 - b1^t, c2 = 1 - b2^t;
-// clears the gradient.
+// clears the gradient sums.
 __global__ void snet_adam_kernel(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
-                                 float *__restrict__ g, uint64_t n, float lr, float b1, float b2, float eps, float c1,
-                                 float c2) {
+                                 unsigned long long *__restrict__ g, uint64_t n, float lr, float b1, float b2,
+                                 float eps, float c1, float c2) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        const float gi = g[i];
+        const float gi = grad_value(g[i]);
         const float mi = fmaf(b1, m[i], (1.f - b1) * gi);
         const float vi = fmaf(b2, v[i], (1.f - b2) * gi * gi);
         m[i] = mi;
         v[i] = vi;
         p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-        g[i] = 0.f;
+        g[i] = 0ull;
+    }
+}
+
+// The gradient as FP32 values; clears the sums.
+__global__ void snet_grad_out_kernel(unsigned long long *__restrict__ g, float *__restrict__ out, uint64_t n) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        out[i] = grad_value(g[i]);
+        g[i] = 0ull;
     }
 }
 
@@ -661,7 +684,7 @@ cudaError_t launch_snet_pairs(const RenderParams &P, uint64_t seed, uint64_t fir
     return cudaGetLastError();
 }
 
-cudaError_t launch_snet_grad(const ShadowNetDev &N, const float *params, float *grad, const float *pairs,
+cudaError_t launch_snet_grad(const ShadowNetDev &N, const float *params, unsigned long long *gacc, const float *pairs,
                              uint64_t n_pairs, uint64_t b0, uint32_t B, float *loss, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
@@ -672,13 +695,18 @@ cudaError_t launch_snet_grad(const ShadowNetDev &N, const float *params, float *
     }
     const uint32_t tiles = (B + kTile - 1) / kTile;
     const int grid = (int)std::min<uint32_t>(tiles, 152u);
-    snet_train_kernel<<<grid, kTT, sizeof(TrainSmem), s>>>(N, params, grad, pairs, n_pairs, b0, B, loss);
+    snet_train_kernel<<<grid, kTT, sizeof(TrainSmem), s>>>(N, params, gacc, pairs, n_pairs, b0, B, loss);
     return cudaGetLastError();
 }
 
-cudaError_t launch_snet_adam(float *p, float *m, float *v, float *g, uint64_t n, float lr, float b1, float b2,
-                             float eps, double c1, double c2, cudaStream_t s) {
+cudaError_t launch_snet_adam(float *p, float *m, float *v, unsigned long long *g, uint64_t n, float lr, float b1,
+                             float b2, float eps, double c1, double c2, cudaStream_t s) {
     snet_adam_kernel<<<152 * 8, 256, 0, s>>>(p, m, v, g, n, lr, b1, b2, eps, (float)c1, (float)c2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_snet_grad_out(unsigned long long *g, float *out, uint64_t n, cudaStream_t s) {
+    snet_grad_out_kernel<<<152 * 8, 256, 0, s>>>(g, out, n);
     return cudaGetLastError();
 }
 

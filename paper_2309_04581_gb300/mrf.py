@@ -30,7 +30,7 @@ MRF_MAT_MIRROR, MRF_MAT_GLASS, MRF_MAT_DIFFUSE = 0, 1, 2
 MRF_LIGHT_POINT, MRF_LIGHT_AREA = 0, 1
 MRF_ENGINE_AUTO, MRF_ENGINE_MEGAKERNEL, MRF_ENGINE_WAVEFRONT = 0, 1, 2
 KERNEL_NAMES = ("render_megakernel", "wf_cast", "field", "wf_shade", "wf_finalize", "wf_gen", "wf_composite",
-                "wf_shadow_net", "wf_vis", "wf_overflow", "wf_mask")
+                "wf_shadow_net", "wf_vis", "wf_overflow", "wf_mask", "wf_tail")
 NO_HIT = 0xFFFFFFFF
 
 # every entry point declared in include/mrf.h
@@ -41,7 +41,8 @@ EXPORTS = ("mrf_context_create", "mrf_context_destroy", "mrf_last_error", "mrf_v
            "mrf_shadow_net_get_params", "mrf_shadow_net_set_params", "mrf_shadow_pairs", "mrf_shadow_net_grad",
            "mrf_shadow_net_train", "mrf_shadow_net_eval", "mrf_frame_capture", "mrf_frame_replay", "mrf_frame_stats",
            "mrf_frame_destroy", "mrf_tuning_get", "mrf_tuning_set", "mrf_autotune", "mrf_selftest_timeout",
-           "mrf_debug_fail_allocations", "mrf_shadow_net_save", "mrf_shadow_net_load")
+           "mrf_debug_fail_allocations", "mrf_shadow_net_save", "mrf_shadow_net_load", "mrf_sync_status",
+           "mrf_l2_read_bandwidth")
 
 _fp = C.POINTER(C.c_float)
 _u32p = C.POINTER(C.c_uint32)
@@ -98,7 +99,8 @@ class mrf_shadow_net_desc(C.Structure):
 
 
 class mrf_tuning(C.Structure):
-    _fields_ = [("field_groups", C.c_uint32), ("samples_per_path", C.c_uint32), ("rounds", C.c_uint32)]
+    _fields_ = [("field_groups", C.c_uint32), ("samples_per_path", C.c_uint32), ("rounds", C.c_uint32),
+                ("tail_paths", C.c_uint32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -139,7 +141,9 @@ def lib():
             for name in ("mrf_context_destroy", "mrf_field_destroy", "mrf_bvh_destroy", "mrf_shadow_net_destroy",
                          "mrf_frame_destroy", "mrf_debug_fail_allocations"):
                 getattr(L, name).restype = None
-            L.mrf_selftest_timeout.argtypes = [_vp, C.c_uint64]
+            L.mrf_selftest_timeout.argtypes = [_vp, C.c_uint64, C.c_int32]
+            L.mrf_sync_status.argtypes = [_vp, C.POINTER(C.c_uint32)]
+            L.mrf_l2_read_bandwidth.argtypes = [_vp, C.c_uint64, C.c_uint32, _vp, C.POINTER(C.c_double)]
             L.mrf_shadow_net_save.argtypes = [_vp, C.c_char_p]
             L.mrf_shadow_net_load.argtypes = [_vp, C.c_char_p]
             L.mrf_debug_fail_allocations.argtypes = [C.c_uint32]
@@ -362,8 +366,8 @@ class Renderer:
         check(lib().mrf_tuning_get(self.ctx, C.byref(t)))
         return t.as_dict()
 
-    def set_tuning(self, field_groups: int, samples_per_path: int, rounds: int = 1):
-        t = mrf_tuning(field_groups, samples_per_path, rounds)
+    def set_tuning(self, field_groups: int, samples_per_path: int, rounds: int = 1, tail_paths: int = 0):
+        t = mrf_tuning(field_groups, samples_per_path, rounds, tail_paths)
         check(lib().mrf_tuning_set(self.ctx, C.byref(t)))
 
     def autotune(self, out=None, reps: int = 2, engine=MRF_ENGINE_AUTO, shadow_net=None):
@@ -500,6 +504,13 @@ class Frame:
         if getattr(self, "handle", None):
             lib().mrf_frame_destroy(self.handle)
             self.handle = None
+
+
+def mrf_l2_read_bandwidth(ctx: int, nbytes: int, reps: int, stream: int = 0) -> float:
+    """L2 read bandwidth in GB/s over an L2-resident buffer of nbytes (see include/mrf.h)."""
+    g = C.c_double()
+    check(lib().mrf_l2_read_bandwidth(ctx, nbytes, reps, stream, C.byref(g)))
+    return g.value
 
 
 def mrf_tonemap(ctx: int, in_ptr: int, n: int, exposure: float, out_ptr: int, stream: int = 0):

@@ -139,3 +139,32 @@ def test_static_arena_rounds_match_mrf_render_exactly(env):
         torch.cuda.synchronize()
         assert torch.equal(out, ref)
         r.close()
+
+
+def _eight_lights(sc):
+    l0 = sc.lights[0]
+    sc.lights = [S.Light(pos=(l0.pos[0] + 0.05 * (k - 3.5), l0.pos[1], l0.pos[2]),
+                         intensity=tuple(x / 8 for x in l0.intensity)) for k in range(8)]
+    return sc
+
+
+def test_static_arena_limit_depends_on_the_light_count(env):
+    # eight point lights make the per-path state 556 B: 125,316 paths no longer
+    # fit the 64 MiB arena (a clear MRF_ERR_INVALID_ARG, not a launch failure),
+    # while 90,000 paths still render and match mrf_render
+    torch, M = env
+    sc = _eight_lights(S.config2(354, 354))
+    r = M.Renderer(sc)
+    out = torch.empty((sc.n_rays, 4), dtype=torch.float32, device="cuda")
+    st = M.lib().mrf_render_static(r.ctx, r.field, r.bvh, C.byref(r.rays_struct()), 8, C.byref(r.opts_struct()),
+                                   out.data_ptr(), None, None)
+    assert st == M.MRF_ERR_INVALID_ARG
+    assert b"do not fit the static arena" in M.lib().mrf_last_error()
+    r.close()
+    sc = _eight_lights(S.config2(300, 300))
+    r, ref, rec_ref, outs = _render_both(torch, M, sc, M.MRF_PREC_FP32, calls=1)
+    img, rec, st = outs[0]
+    assert _close(img, ref) <= RTOL_PIX
+    assert torch.equal(rec["segments"], rec_ref["segments"])
+    assert st["shadow_rays"] > 0
+    r.close()
