@@ -1,23 +1,35 @@
 """Benchmark of the hybrid light-transport loop (one step = one full render).
 
-Workload: the hash-grid scene at 800x800 (1 spp, up to 8 segments per path):
-16-level hash grid with 2^19 FP16 entries per level (resolutions 16..2048), MLP
-32-64-64-4 with exp density and softplus radiance, 128^3 occupancy, a
-10,240-triangle glass sphere, a mirror cube, a diffuse floor and one point
-light, fixed step sqrt(3)/1024.  Inputs are synthetic and seeded.
+Workload (the metric's configuration): the hash-grid scene at 1920x1080, 1 spp,
+up to 8 segments per path: 16-level hash grid with 2^19 FP16 entries per level
+(resolutions 16..2048), MLP 32-64-64-4 with exp density and softplus radiance,
+128^3 occupancy, a 10,240-triangle glass sphere, a mirror cube, a diffuse
+floor and one point light, fixed step sqrt(3)/1024.  Inputs are synthetic and
+seeded.
 
 The headline runs the mixed-precision renderer (wavefront engine, BF16 MLP on
-the tensor cores, FP32 everywhere else); the same line carries the FP32 GPU
-path (megakernel, and the FP32 wavefront engine) and the FP16 tensor-core form
-measured the same way, the same scene at 1920x1080 (BF16 and FP32, same
-protocol) under "at_1920x1080", the render time at 200^2, 400^2 and 800^2
-pixels, the view-dependent field on the same scene, the BVH traversal counts,
-the image error of the headline against the FP64 oracle on the CPU-baseline
-pixel sample, the per-kernel timings and the dominant kernel's roofline.
+the tensor cores, FP32 everywhere else).  The same line carries:
+  - roofline: the dominant kernel (the tensor-core field kernel) against the
+    measured HBM copy bandwidth, the L2 bandwidth measured here and the
+    measured BF16 tensor peak;
+  - fp32_gpu: the FP32 GPU path (megakernel, and the FP32 wavefront engine);
+    fp16_tensor_cores: the FP16 tensor-core form; each with its image error;
+  - image_error_vs_oracle, cpu_baseline: the FP64 oracle on every 8th row and
+    column of the same frame (all host cores, and one core on a sparser sample);
+  - e2e: the same frame through the C ABI into pinned host memory;
+  - at_800x800, time_vs_pixels, view_dependent_field, bvh_traversal, kernels;
+  - area_lights: 4 area lights x 16 shadow rays per diffuse hit at 1920x1080,
+    the shadow transmittance from the learned network (trained here on the
+    GPU) against the marched shadows (BF16 and FP32 field), with image errors
+    against the oracle's plain march and a clock record;
+  - dynamic: a deforming-mesh sequence (refit per frame, GPU rebuild every 30
+    frames, learned shadows, 4 spp) with p50/p99 frame latency, its FP32 GPU
+    arm, an oracle check of one frame and a clock record.
 Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp16|fp32]
     python bench.py --impl reference    # the FP64 CPU oracle on the host cores
+    python bench.py --workload area|dynamic|views   # one extra workload alone
 
 Under torchrun (N > 1) every rank renders its own copy of the workload
 (replicas: pixels are independent, there is no data exchange); rank 0 prints.
@@ -44,6 +56,7 @@ MLP_FLOP_PER_SAMPLE = 2 * (32 * 64 + 64 * 64 + 64 * 4)   # 12,800
 GATHER_BYTES_PER_SAMPLE = 16 * 8 * 4                       # 16 levels x 8 corners x (2 x FP16)
 SAMPLE_IO_BYTES = 16 + 16                                  # sample record in, (sigma, rgb) out
 SM_COUNT, FP32_LANES_PER_SM = 152, 128
+WIDTH, HEIGHT = 1920, 1080
 
 
 def parse():
@@ -54,18 +67,19 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--engine", default="auto", choices=["auto", "megakernel", "wavefront"])
-    ap.add_argument("--width", type=int, default=800)
-    ap.add_argument("--height", type=int, default=800)
-    ap.add_argument("--cpu-stride", type=int, default=4, help="oracle sample: every n-th row and column")
+    ap.add_argument("--width", type=int, default=WIDTH)
+    ap.add_argument("--height", type=int, default=HEIGHT)
+    ap.add_argument("--cpu-stride", type=int, default=8, help="oracle sample: every n-th row and column")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 comparison run")
-    ap.add_argument("--no-1080p", action="store_true",
-                    help="skip the extra measurements: the scene at 1920x1080, time against pixel count and the "
-                         "view-dependent field")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 and FP16 comparison runs")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other frame sizes, time against pixel count and the view-dependent field")
+    ap.add_argument("--no-area", action="store_true", help="skip the area-light / learned-shadow extra")
+    ap.add_argument("--no-dynamic", action="store_true", help="skip the dynamic-sequence extra")
     ap.add_argument("--workload", default="hashgrid", choices=["hashgrid", "dynamic", "area", "views"],
-                    help="dynamic: the deforming-mesh sequence (per-frame refit, rebuild every --rebuild frames); "
-                         "area: 4 area lights x 16 shadow rays, marched against the learned transmittance")
-    ap.add_argument("--frames", type=int, default=300)
+                    help="dynamic: the deforming-mesh sequence alone; area: the area-light workload alone; "
+                         "views: the 32-view batch")
+    ap.add_argument("--frames", type=int, default=30, help="dynamic: frames timed")
     ap.add_argument("--rebuild", type=int, default=30)
     ap.add_argument("--spp", type=int, default=4)
     ap.add_argument("--train-steps", type=int, default=6000, help="area: Adam steps of the shadow network")
@@ -159,6 +173,7 @@ def source_hash(files) -> str:
 
 
 FIELD_TC_SOURCES = ("paper_2309_04581_gb300/csrc/field_tc.cu", "paper_2309_04581_gb300/csrc/tc.cuh")
+TRAFFIC_SUMMARY = "field_tc_dram_traffic_hashgrid_1920x1080_bf16.md"
 
 
 def measured_traffic(kernel_files, summary: str):
@@ -177,13 +192,19 @@ def measured_traffic(kernel_files, summary: str):
     return int(v.group(1))
 
 
-def workload(args):
-    from paper_2309_04581_gb300 import scenes as S
-    sc = S.config2(args.width, args.height)
-    name = (f"hash-grid field (16 levels, 2^19 FP16 entries, MLP 32-64-64-4, 128^3 occupancy) + "
+def workload_name(w: int, h: int) -> str:
+    return (f"hash-grid field (16 levels, 2^19 FP16 entries, MLP 32-64-64-4, 128^3 occupancy) + "
             f"10,240-triangle glass sphere, mirror cube, diffuse floor, 1 point light; "
-            f"{args.width}x{args.height}, 1 spp, up to 8 segments per path")
-    return sc, name
+            f"{w}x{h}, 1 spp, up to 8 segments per path")
+
+
+def psnr_maxabs(img, ref_rgba, ok):
+    """PSNR (peak = the oracle image's largest channel) and max abs error in linear HDR."""
+    a, b = img[ok, :3], ref_rgba[ok, :3]
+    peak = float(np.abs(b).max())
+    mse = float(np.mean((a - b) ** 2))
+    return {"psnr_db": (10 * np.log10(peak * peak / mse)) if mse > 0 else None,
+            "max_abs": float(np.abs(a - b).max()), "peak": peak, "pixels": int(ok.sum())}
 
 
 def cpu_baseline(sc, stride: int, single_core_stride: int = 0):
@@ -218,44 +239,23 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    sc, name = workload(args)
-    stride = max(args.cpu_stride, 8)
+    from paper_2309_04581_gb300 import scenes as S
+    sc = S.config2(args.width, args.height)
+    vals, cb = [], None
     for _ in range(args.warmup):
         pass  # the oracle has no warm-up state
-    vals, cb = [], None
     for _ in range(max(1, args.steps)):
-        cb, _, _ = cpu_baseline(sc, stride)
+        cb, _, _ = cpu_baseline(sc, args.cpu_stride)
         vals.append(cb["value"])
     v = statistics.mean(vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": name, "precision": "fp64", "l2": "host oracle"},
+            "config": {"workload": workload_name(args.width, args.height), "precision": "fp64", "l2": "host oracle"},
             "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"], "value": v,
                              "unit": METRIC},
             "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
-
-
-def time_steps(torch, r, engine, out, stream, steps, warmup, flush, sampler=None):
-    """W untimed steps, then K steps each bracketed by CUDA events on the render
-    stream, with a >L2 buffer written before every step.  Returns per-step ms."""
-    for _ in range(warmup):
-        r.render(out=out, engine=engine, stream=stream.cuda_stream)
-    stream.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    torch.cuda.synchronize()
-    ctx = sampler if sampler is not None else _Null()
-    with ctx:
-        with torch.cuda.stream(stream):
-            for k in range(steps):
-                flush.fill_(float(k))
-                evs[k][0].record(stream)
-                r.render(out=out, engine=engine, stream=stream.cuda_stream)
-                evs[k][1].record(stream)
-        stream.synchronize()
-    torch.cuda.synchronize()
-    return [a.elapsed_time(b) for a, b in evs]
 
 
 class _Null:
@@ -266,10 +266,79 @@ class _Null:
         return False
 
 
+def time_steps(torch, r, engine, out, stream, steps, warmup, flush, sampler=None, shadow_net=None):
+    """W untimed steps, then K steps each bracketed by CUDA events on the render
+    stream, with a >L2 buffer written before every step.  Returns per-step ms."""
+    for _ in range(warmup):
+        r.render(out=out, engine=engine, stream=stream.cuda_stream, shadow_net=shadow_net)
+    stream.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    with (sampler if sampler is not None else _Null()):
+        with torch.cuda.stream(stream):
+            for k in range(steps):
+                flush.fill_(float(k))
+                evs[k][0].record(stream)
+                r.render(out=out, engine=engine, stream=stream.cuda_stream, shadow_net=shadow_net)
+                evs[k][1].record(stream)
+        stream.synchronize()
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def kernel_times(torch, r, engine, out, stream, flush, reps, shadow_net=None):
+    """Per-kernel CUDA-event milliseconds per frame (mean over reps frames)."""
+    acc = {}
+    for k in range(reps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        tim = {}
+        r.render(out=out, engine=engine, stream=stream.cuda_stream, timing=tim, shadow_net=shadow_net)
+        for name_k, (kms, cnt) in tim.items():
+            a = acc.setdefault(name_k, [0.0, 0])
+            a[0] += kms / reps
+            a[1] = cnt
+    return {k: {"ms_per_step": v[0], "launches_per_step": v[1]} for k, v in acc.items() if v[1]}
+
+
+def measure_l2_bandwidth(M, ctx, stream):
+    """L2 read bandwidth measured here through the library (mrf_l2_read_bandwidth):
+    16-byte loads that bypass L1 over a 32 MiB buffer (the size of the hash
+    table) made resident in L2 first, 200 passes timed with CUDA events, best
+    of 3."""
+    best = max(M.mrf_l2_read_bandwidth(ctx, 32 << 20, 200, stream) for _ in range(3))
+    return {"gbs": best, "how": "mrf_l2_read_bandwidth: ld.global.cg 16-byte reads of a 32 MiB L2-resident buffer, "
+                                "200 passes, CUDA events, best of 3"}
+
+
+def field_roofline(kernels, samples, pk, pk_kind, l2, traffic, dom):
+    f_ms = kernels["field"]["ms_per_step"]
+    launches = kernels["field"]["launches_per_step"]
+    nbytes = (GATHER_BYTES_PER_SAMPLE + SAMPLE_IO_BYTES) * samples
+    ach = nbytes / (f_ms / 1e3) / 1e9
+    gather = GATHER_BYTES_PER_SAMPLE * samples / (f_ms / 1e3) / 1e9
+    tfl = MLP_FLOP_PER_SAMPLE * samples / (f_ms / 1e3) / 1e12
+    return {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
+            "traffic": traffic, "kernel": "field_tc_kernel",
+            "algorithmic_bytes_per_launch": nbytes / launches,
+            "algorithmic": f"{GATHER_BYTES_PER_SAMPLE + SAMPLE_IO_BYTES} B per evaluated sample "
+                           f"(512 B gathered + 32 B I/O) x {samples} samples in {launches} launches",
+            "peak_kind": f"{pk_kind} hbm_gbs",
+            "l2": {"achieved_gather_gbs": gather, "peak_gbs": l2["gbs"], "frac": gather / l2["gbs"],
+                   "peak_kind": "measured here: " + l2["how"]},
+            "l2_frac": gather / l2["gbs"],
+            "tensor": {"achieved_tflops": tfl, "peak_tflops": pk["bf16_tflops"], "frac": tfl / pk["bf16_tflops"],
+                       "peak_kind": f"{pk_kind} bf16_tflops"},
+            "limiter": "L1 load data pipe (random table gathers), instruction issue and integer ALU pipe "
+                       "(ncu summaries in profiles/); the table gathers are served by L2",
+            "dominant_kernel": dom, "is_dominant": dom == "field"}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
     from paper_2309_04581_gb300 import build as cuda_build
+    from paper_2309_04581_gb300 import scenes as S
     import paper_2309_04581_gb300.mrf as M
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -282,7 +351,9 @@ def run_ours(args):
         cuda_build.build()
     if world > 1:
         dist.barrier()
-    sc, name = workload(args)
+    W, H = args.width, args.height
+    sc = S.config2(W, H)
+    name = workload_name(W, H)
     prec_id = {"fp32": M.MRF_PREC_FP32, "fp16": M.MRF_PREC_FP16, "bf16": M.MRF_PREC_BF16}
     engine = {"auto": M.MRF_ENGINE_AUTO, "megakernel": M.MRF_ENGINE_MEGAKERNEL,
               "wavefront": M.MRF_ENGINE_WAVEFRONT}[args.engine]
@@ -309,70 +380,59 @@ def run_ours(args):
     samples = st["samples_evaluated"] + st["shadow_samples_evaluated"]
     value = job_throughput(segs, world, ms)
     # per-kernel CUDA-event timing over the same protocol (separate pass: it waits per call)
-    ktimes = {}
-    nk = max(3, args.steps // 2)
-    for k in range(nk):
-        flush.fill_(float(k))
-        torch.cuda.synchronize()
-        tim = {}
-        r.render(out=out, engine=engine, stream=stream.cuda_stream, timing=tim)
-        for name_k, (kms, cnt) in tim.items():
-            a = ktimes.setdefault(name_k, [0.0, 0])
-            a[0] += kms / nk
-            a[1] = cnt
-    kernels = {k: {"ms_per_step": v[0], "launches_per_step": v[1], "share": v[0] / max(ms, 1e-9)}
-               for k, v in ktimes.items() if v[1]}
+    kernels = kernel_times(torch, r, engine, out, stream, flush, max(3, args.steps // 2))
+    for v in kernels.values():
+        v["share"] = v["ms_per_step"] / max(ms, 1e-9)
     launches = sum(v["launches_per_step"] for v in kernels.values())
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
     pk, pk_kind = peaks()
+    l2 = measure_l2_bandwidth(M, r.ctx, stream.cuda_stream)
     if "field" in kernels and args.precision != "fp32":
-        # the tensor-core field kernel: bytes model against the measured HBM copy bandwidth
-        f_ms = kernels["field"]["ms_per_step"]
-        nbytes = (GATHER_BYTES_PER_SAMPLE + SAMPLE_IO_BYTES) * samples
-        ach = nbytes / (f_ms / 1e3) / 1e9
-        traffic = measured_traffic(FIELD_TC_SOURCES,
-                                   "field_tc_dram_traffic_hashgrid_800x800_bf16.md") \
-            if (args.width, args.height, args.precision) == (800, 800, "bf16") else None
-        tfl = MLP_FLOP_PER_SAMPLE * samples / (f_ms / 1e3) / 1e12
-        roof = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
-                "traffic": traffic, "kernel": "field_tc_kernel",
-                "algorithmic_bytes_per_launch": nbytes / kernels["field"]["launches_per_step"],
-                "algorithmic": f"{GATHER_BYTES_PER_SAMPLE + SAMPLE_IO_BYTES} B per evaluated sample "
-                               f"(512 B gathered + 32 B I/O) x {samples} samples",
-                "limiter": "L1 load data pipe (81 % of peak in ncu); the table gathers are served by L2",
-                "peak_kind": f"{pk_kind} hbm_gbs",
-                "tensor": {"achieved_tflops": tfl, "peak_tflops": pk["bf16_tflops"],
-                           "frac": tfl / pk["bf16_tflops"], "peak_kind": f"{pk_kind} bf16_tflops"},
-                "dominant_kernel": dom, "is_dominant": dom == "field"}
+        traffic = measured_traffic(FIELD_TC_SOURCES, TRAFFIC_SUMMARY) \
+            if (W, H, args.precision) == (WIDTH, HEIGHT, "bf16") else None
+        roof = field_roofline(kernels, samples, pk, pk_kind, l2, traffic, dom)
     else:
         # FP32 MLP on the CUDA cores (megakernel or FP32 field kernel)
-        name = "render_megakernel" if "render_megakernel" in kernels else "field"
-        k_ms = kernels[name]["ms_per_step"]
+        kname = "render_megakernel" if "render_megakernel" in kernels else "field"
+        k_ms = kernels[kname]["ms_per_step"]
         flop = MLP_FLOP_PER_SAMPLE * samples
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         ach = flop / (k_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "kernel": {"field": "field_simt_kernel"}.get(name, name),
+                "traffic": None, "kernel": {"field": "field_simt_kernel"}.get(kname, kname),
                 "algorithmic": f"{MLP_FLOP_PER_SAMPLE} FP32 FLOP per evaluated sample x {samples}",
                 "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock",
-                "dominant_kernel": dom, "is_dominant": dom == name}
+                "dominant_kernel": dom, "is_dominant": dom == kname}
+    short = max(3, args.steps // 4)
+    images = {}
     # FP32 GPU path on the same GPU, same protocol (the comparison the metric names)
     fp32 = None
     if not args.no_fp32 and args.precision != "fp32":
         r32 = M.Renderer(sc, device=local, precision=M.MRF_PREC_FP32)
         o32 = torch.empty_like(out)
-        ms32 = time_steps(torch, r32, M.MRF_ENGINE_MEGAKERNEL, o32, stream, max(3, args.steps // 2), args.warmup,
-                          flush)
-        m32 = sum(ms32) / len(ms32)
-        fp32 = {"value": world * segs / (m32 / 1e3), "ms_per_step": m32, "engine": "megakernel",
+        ms32 = time_steps(torch, r32, M.MRF_ENGINE_MEGAKERNEL, o32, stream, short, 1, flush)
+        m32 = max_over_ranks(sum(ms32) / len(ms32), dev)
+        images["fp32_megakernel"] = o32.cpu().numpy().astype(np.float64)
+        fp32 = {"value": job_throughput(segs, world, m32), "ms_per_step": m32, "engine": "megakernel",
                 "speedup_of_headline": m32 / ms}
         # the same FP32 arithmetic through the wavefront engine (FP32 field on the CUDA cores)
-        ms32w = time_steps(torch, r32, M.MRF_ENGINE_WAVEFRONT, o32, stream, max(3, args.steps // 2), args.warmup,
-                           flush)
-        m32w = sum(ms32w) / len(ms32w)
-        fp32["wavefront"] = {"value": world * segs / (m32w / 1e3), "ms_per_step": m32w,
+        ms32w = time_steps(torch, r32, M.MRF_ENGINE_WAVEFRONT, o32, stream, short, 1, flush)
+        m32w = max_over_ranks(sum(ms32w) / len(ms32w), dev)
+        fp32["wavefront"] = {"value": job_throughput(segs, world, m32w), "ms_per_step": m32w,
                              "speedup_of_headline": m32w / ms}
         r32.close()
+        del o32
+    # the other tensor-core form (FP16 operands when the headline is BF16), same protocol
+    other = None
+    if not args.no_fp32 and args.precision == "bf16":
+        r16 = M.Renderer(sc, device=local, precision=M.MRF_PREC_FP16)
+        o16 = torch.empty_like(out)
+        ms16 = time_steps(torch, r16, engine, o16, stream, short, args.warmup, flush)
+        m16 = max_over_ranks(sum(ms16) / len(ms16), dev)
+        images["fp16"] = o16.cpu().numpy().astype(np.float64)
+        other = {"precision": "fp16", "value": job_throughput(segs, world, m16), "ms_per_step": m16}
+        r16.close()
+        del o16
     # BVH traversal of the cast kernel: nodes (64 B) and triangles (48 B) fetched
     cast = None
     if "wf_cast" in kernels:
@@ -381,78 +441,46 @@ def run_ours(args):
         cast = {"kernel": "wf_cast", "bvh_nodes": st["bvh_nodes"], "tri_tests": st["bvh_tri_tests"],
                 "worst_traversal_nodes": st["bvh_worst_nodes"],
                 "rays": segs + st["shadow_rays"], "algorithmic_bytes": cb_bytes,
-                "achieved_gbs": cb_bytes / (c_ms / 1e3) / 1e9, "ms_per_step": c_ms,
+                "achieved_gbs": cb_bytes / (c_ms / 1e3) / 1e9, "l2_frac": cb_bytes / (c_ms / 1e3) / 1e9 / l2["gbs"],
+                "ms_per_step": c_ms,
                 "note": "64 B per node visited + 48 B per triangle tested; the BVH is on-chip (L1/L2) resident, "
-                        "so this is not DRAM traffic"}
-    # render time against pixel count (the same scene at 200^2, 400^2, 800^2)
-    scaling = None
-    if not args.no_1080p and (args.width, args.height) == (800, 800):
-        from paper_2309_04581_gb300 import scenes as S
+                        "so this is not DRAM traffic; l2_frac against the L2 bandwidth measured here"}
+    # other frame sizes, render time against pixel count, view-dependent field
+    scaling, hd800, vd, img_vd = None, None, None, None
+    if not args.no_extras:
         scaling = []
-        for n_px in (200, 400):
-            sc_s = S.config2(n_px, n_px)
+        for (w_s, h_s) in ((200, 200), (400, 400), (800, 800)):
+            sc_s = S.config2(w_s, h_s)
             r_s = M.Renderer(sc_s, device=local, precision=prec_id[args.precision])
             o_s = torch.empty((sc_s.n_rays, 4), dtype=torch.float32, device=dev)
+            _, st_s = r_s.render(out=o_s, engine=engine, stats=True, stream=stream.cuda_stream)
             ms_s = time_steps(torch, r_s, engine, o_s, stream, 5, args.warmup, flush)
-            scaling.append({"pixels": n_px * n_px, "ms_per_step": statistics.median(ms_s)})
+            m_s = statistics.median(ms_s)
+            scaling.append({"pixels": w_s * h_s, "ms_per_step": m_s})
+            if (w_s, h_s) == (800, 800):
+                hd800 = {"value": job_throughput(st_s["segments"], world, m_s), "unit": METRIC, "ms_per_step": m_s,
+                         "field_samples_per_s": world * (st_s["samples_evaluated"] +
+                                                         st_s["shadow_samples_evaluated"]) / (m_s / 1e3)}
             r_s.close()
-        scaling.append({"pixels": 640000, "ms_per_step": statistics.median(step_ms)})
+        scaling.append({"pixels": W * H, "ms_per_step": statistics.median(step_ms)})
         for e in scaling:
             e["ns_per_pixel"] = e["ms_per_step"] * 1e6 / e["pixels"]
-    # the same scene at 1920x1080, same protocol (the metric's frame size)
-    hd = None
-    if not args.no_1080p and (args.width, args.height) != (1920, 1080):
-        from paper_2309_04581_gb300 import scenes as S
-        sc_hd = S.config2(1920, 1080)
-        r_hd = M.Renderer(sc_hd, device=local, precision=prec_id[args.precision])
-        o_hd = torch.empty((sc_hd.n_rays, 4), dtype=torch.float32, device=dev)
-        _, st_hd = r_hd.render(out=o_hd, engine=engine, stats=True, stream=stream.cuda_stream)
-        ms_hd = time_steps(torch, r_hd, engine, o_hd, stream, max(3, args.steps // 2), args.warmup, flush)
-        m_hd = max_over_ranks(sum(ms_hd) / len(ms_hd), dev)
-        s_hd = st_hd["samples_evaluated"] + st_hd["shadow_samples_evaluated"]
-        hd = {"value": job_throughput(st_hd["segments"], world, m_hd), "unit": METRIC, "ms_per_step": m_hd,
-              "field_samples_per_s": world * s_hd / (m_hd / 1e3), "segments": st_hd["segments"],
-              "samples_evaluated": s_hd, "steps": len(ms_hd)}
-        if not args.no_fp32 and args.precision != "fp32":
-            r32 = M.Renderer(sc_hd, device=local, precision=M.MRF_PREC_FP32)
-            ms32 = time_steps(torch, r32, M.MRF_ENGINE_MEGAKERNEL, o_hd, stream, 3, 1, flush)
-            m32 = max_over_ranks(sum(ms32) / len(ms32), dev)
-            hd["fp32_gpu"] = {"value": job_throughput(st_hd["segments"], world, m32), "ms_per_step": m32,
-                              "engine": "megakernel", "speedup_of_bf16": m32 / m_hd}
-            r32.close()
-        r_hd.close()
-        del o_hd
-    # the other tensor-core form (FP16 operands when the headline is BF16), same protocol
-    other = None
-    img_other = None
-    if not args.no_fp32 and args.precision == "bf16":
-        r16 = M.Renderer(sc, device=local, precision=M.MRF_PREC_FP16)
-        o16 = torch.empty_like(out)
-        ms16 = time_steps(torch, r16, engine, o16, stream, max(3, args.steps // 2), args.warmup, flush)
-        m16 = max_over_ranks(sum(ms16) / len(ms16), dev)
-        r16.render(out=o16, engine=engine, stream=stream.cuda_stream)
-        stream.synchronize()
-        img_other = o16.cpu().numpy().astype(np.float64)
-        other = {"precision": "fp16", "value": job_throughput(segs, world, m16), "ms_per_step": m16}
-        r16.close()
-    # view-dependent radiance (Instant-NGP layout: density head + colour network of
-    # the view direction's SH) on the same scene: five tensor-core layers per sample
-    vd = None
-    img_vd = None
-    if not args.no_1080p and args.precision != "fp32":
-        from paper_2309_04581_gb300 import scenes as S
-        sc_vd = S.config2_view(args.width, args.height)
-        r_vd = M.Renderer(sc_vd, device=local, precision=prec_id[args.precision])
-        o_vd = torch.empty_like(out)
-        _, st_vd = r_vd.render(out=o_vd, engine=engine, stats=True, stream=stream.cuda_stream)
-        stream.synchronize()
-        img_vd = o_vd.cpu().numpy().astype(np.float64)
-        ms_vd = time_steps(torch, r_vd, engine, o_vd, stream, max(3, args.steps // 2), args.warmup, flush)
-        m_vd = max_over_ranks(sum(ms_vd) / len(ms_vd), dev)
-        vd = {"value": job_throughput(st_vd["segments"], world, m_vd), "unit": METRIC, "ms_per_step": m_vd,
-              "field_samples_per_s": world * (st_vd["samples_evaluated"] + st_vd["shadow_samples_evaluated"]) /
-              (m_vd / 1e3), "scene": sc_vd}
-        r_vd.close()
+        # view-dependent radiance (Instant-NGP layout: density head + colour network of
+        # the view direction's SH) on the same scene: five tensor-core layers per sample
+        if args.precision != "fp32":
+            sc_vd = S.config2_view(W, H)
+            r_vd = M.Renderer(sc_vd, device=local, precision=prec_id[args.precision])
+            o_vd = torch.empty_like(out)
+            _, st_vd = r_vd.render(out=o_vd, engine=engine, stats=True, stream=stream.cuda_stream)
+            stream.synchronize()
+            img_vd = o_vd.cpu().numpy().astype(np.float64)
+            ms_vd = time_steps(torch, r_vd, engine, o_vd, stream, short, args.warmup, flush)
+            m_vd = max_over_ranks(sum(ms_vd) / len(ms_vd), dev)
+            vd = {"value": job_throughput(st_vd["segments"], world, m_vd), "unit": METRIC, "ms_per_step": m_vd,
+                  "field_samples_per_s": world * (st_vd["samples_evaluated"] + st_vd["shadow_samples_evaluated"]) /
+                  (m_vd / 1e3), "_scene": sc_vd}
+            r_vd.close()
+            del o_vd
     # end to end through the C ABI: host output buffer, device->host copy inside the call
     host_out = torch.empty((sc.n_rays, 4), dtype=torch.float32).pin_memory()
     e2e_ms = []
@@ -482,8 +510,8 @@ def run_ours(args):
             "roofline": roof,
             "fp32_gpu": fp32,
             "fp16_tensor_cores": other,
+            "at_800x800": hd800,
             "view_dependent_field": vd,
-            "at_1920x1080": hd,
             "bvh_traversal": cast,
             "time_vs_pixels": scaling,
             "e2e": {"value": e2e, "unit": METRIC, "h2d_bytes_per_step": 48,
@@ -491,117 +519,60 @@ def run_ours(args):
                     "note": "camera record passed by value; image copied to pinned host memory inside mrf_render"},
             "gpu_launches": launches * args.steps,
             "clocks": sampler.summary()}
+    del host_out
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
         cb, ids, ref = cpu_baseline(sc, args.cpu_stride, 4 * args.cpu_stride)
         line["cpu_baseline"] = cb
         ok = ref["flags"] == 0
-        g, o = image[ids][ok, :3], ref["rgba"][ok, :3]
-        peak = float(np.abs(o).max())
-        mse = float(np.mean((g - o) ** 2))
-        line["image_error_vs_oracle"] = {
-            "pixels": int(ok.sum()), "psnr_db": (10 * np.log10(peak * peak / mse)) if mse > 0 else None,
-            "max_abs": float(np.abs(g - o).max()), "ambiguous_pixels_excluded": int((~ok).sum()),
-            "peak": peak}
+        line["image_error_vs_oracle"] = dict(psnr_maxabs(image[ids], ref["rgba"], ok),
+                                             ambiguous_pixels_excluded=int((~ok).sum()),
+                                             sample=f"every {args.cpu_stride}th row and column")
+        if fp32 is not None:
+            fp32["image_error_vs_oracle"] = psnr_maxabs(images["fp32_megakernel"][ids], ref["rgba"], ok)
+        if other is not None:
+            other["image_error_vs_oracle"] = psnr_maxabs(images["fp16"][ids], ref["rgba"], ok)
         if vd is not None:
-            # the oracle on a sparser sample of the view-dependent scene
-            import oracle
-            from paper_2309_04581_gb300 import scenes as S
-            ids_vd = S.strided_pixels(sc.camera.width, sc.camera.height, 4 * args.cpu_stride)
-            ref_vd = oracle.render(vd["scene"], ids_vd, records=False)
-            okv = ref_vd["flags"] == 0
-            gv, ov = img_vd[ids_vd][okv, :3], ref_vd["rgba"][okv, :3]
-            pv = float(np.abs(ov).max())
-            msev = float(np.mean((gv - ov) ** 2))
-            vd["image_error_vs_oracle"] = {"pixels": int(okv.sum()),
-                                           "psnr_db": (10 * np.log10(pv * pv / msev)) if msev > 0 else None,
-                                           "max_abs": float(np.abs(gv - ov).max())}
-        if img_other is not None:
-            g16 = img_other[ids][ok, :3]
-            mse16 = float(np.mean((g16 - o) ** 2))
-            other["image_error_vs_oracle"] = {"psnr_db": (10 * np.log10(peak * peak / mse16)) if mse16 > 0 else None,
-                                              "max_abs": float(np.abs(g16 - o).max())}
+            ids_vd = S.strided_pixels(W, H, 2 * args.cpu_stride)
+            ref_vd = oracle.render(vd["_scene"], ids_vd, records=False)
+            vd["image_error_vs_oracle"] = dict(psnr_maxabs(img_vd[ids_vd], ref_vd["rgba"], ref_vd["flags"] == 0),
+                                               sample=f"every {2 * args.cpu_stride}th row and column")
     if vd is not None:
-        vd.pop("scene", None)
+        vd.pop("_scene", None)
+    r.close()
+    del out, flush
+    torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and not args.no_area:
+        line["area_lights"] = area_workload(args, local)
+    if rank == 0 and world == 1 and not args.no_dynamic:
+        line["dynamic"] = dynamic_workload(args, local)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    r.close()
     if world > 1:
         dist.destroy_process_group()
 
 
-def run_dynamic(args):
-    """Dynamic sequence: a 256x256 cloth grid with sinusoid-plus-noise motion and
-    64 rigid 2,048-triangle bodies with seeded rigid motion in the hash-grid
-    scene (BF16 field), 4 point lights whose shadow rays take the learned
-    transmittance, `--frames` frames at --width x --height, --spp paths per
-    pixel.  Every frame uploads its vertices and refits the BVH, every
-    `--rebuild`-th frame rebuilds it on the GPU instead; the frame latency is
-    the host wall time from the vertex upload to the finished image.  Prints one
-    JSON line with the p50/p99 latency beside the throughput."""
-    import torch
-    from paper_2309_04581_gb300 import scenes as S
-    import paper_2309_04581_gb300.mrf as M
-    W = args.width if args.width != 800 else 1920
-    H = args.height if args.height != 800 else 1080
-    seq = S.DynamicSequence(W, H, spp=args.spp)
-    r = M.Renderer(seq.scene, precision=M.MRF_PREC_BF16)
-    net = M.ShadowNet(r, precision=M.MRF_PREC_BF16, seed=7, lr_decay=0.9995)
-    pairs = net.pairs(11, 0, 1 << 22)
-    net.train(pairs, 1 << 16, 3000)
-    del pairs
-    out = torch.empty((seq.scene.n_rays, 4), dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream().cuda_stream
-    verts = [seq.vertices(k) for k in range(min(args.frames, 30))]   # host motion is not the renderer's work
-    lat, segs = [], 0
-    st = None
-    for k in range(-args.warmup, args.frames):
-        v = verts[k % len(verts)] if k >= 0 else verts[0]
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        r.set_vertices(v, rebuild="gpu" if (k > 0 and k % args.rebuild == 0) else False, stream=stream)
-        _, st = r.render(out=out, stats=True, shadow_net=net)
-        t1 = time.perf_counter()
-        if k >= 0:
-            lat.append((t1 - t0) * 1e3)
-            segs += st["segments"]
-    lat_s = sorted(lat)
-    p = lambda q: lat_s[min(len(lat_s) - 1, int(round(q * (len(lat_s) - 1))))]
-    line = {
-        "metric": METRIC, "value": segs / (sum(lat) / 1e3), "unit": METRIC, "n_gpus": 1, "frames": len(lat),
-        "latency_ms": {"p50": p(0.5), "p99": p(0.99), "max": lat_s[-1], "mean": sum(lat) / len(lat)},
-        "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": f"dynamic sequence: {seq.n_tris} triangles ({seq.n_bodies} rigid bodies, cloth "
-                               f"{seq.cloth.tris.shape[0]} triangles), {W}x{H}, {args.spp} spp, 8 segments, "
-                               f"4 point lights with learned shadow transmittance, refit per frame, GPU rebuild "
-                               f"every {args.rebuild}", "engine": "wavefront"},
-        "last_frame": st,
-    }
-    print(json.dumps(line))
-    net.close()
-    r.close()
-
-
-def run_area(args):
-    """Area-light workload: the hash-grid scene lit by 4 seeded triangle lights
-    with 16 shadow rays each per diffuse hit, 1 spp, --width x --height
-    (default 1920x1080), BF16 field.  Times the frame with the shadow rays
-    marched (512 samples per path, up to 16 generation rounds) and with the learned
-    transmittance (BF16 weights on the tensor cores, trained here on 2^24
-    pairs), and the image
-    error of both against the FP64 oracle on every 32nd row and column."""
+def area_workload(args, local: int = 0, steps: int = 5):
+    """Area-light workload (4 area lights x 16 shadow rays per diffuse hit at
+    1920x1080, 1 spp, 8 segments): the frame with the shadow transmittance from
+    the learned network (BF16 weights on the tensor cores; trained here on 2^24
+    pairs labelled by the FP32 march), against the marched shadows with the BF16
+    field and with the FP32 field (the plain FP32 GPU path), and the image error
+    of each against the FP64 oracle's plain march on every 32nd row and column."""
     import torch
     from paper_2309_04581_gb300 import scenes as S
     import paper_2309_04581_gb300.mrf as M
     import oracle
-    W = args.width if args.width != 800 else 1920
-    H = args.height if args.height != 800 else 1080
-    sc = S.config4(W, H)
-    r = M.Renderer(sc, precision=M.MRF_PREC_BF16)
-    out = torch.empty((sc.n_rays, 4), dtype=torch.float32, device="cuda")
+    Wa, Ha = WIDTH, HEIGHT
+    sc = S.config4(Wa, Ha)
+    dev = f"cuda:{local}"
+    stream = torch.cuda.Stream(local)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    r = M.Renderer(sc, device=local, precision=M.MRF_PREC_BF16)
+    out = torch.empty((sc.n_rays, 4), dtype=torch.float32, device=dev)
     # the marched shadow rays need ~3,000 samples per diffuse hit: a large sample
     # buffer evaluated in up to 16 rounds per segment
     r.set_tuning(8, 512, 16)
-    best = r.tuning()
     net = M.ShadowNet(r, seed=7, lr_decay=0.9995)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -614,53 +585,154 @@ def run_area(args):
     t_train = time.perf_counter() - t0
     del pairs
     bf = M.ShadowNet(r, params=net.params().cpu().numpy(), precision=M.MRF_PREC_BF16)
-    stream = torch.cuda.current_stream().cuda_stream
+    eng = M.MRF_ENGINE_WAVEFRONT
 
-    def frames(shadow_net):
-        for _ in range(args.warmup):
-            r.render(out=out, shadow_net=shadow_net)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record()
-        for _ in range(args.steps):
-            r.render(out=out, shadow_net=shadow_net)
-        e1.record()
-        torch.cuda.synchronize()
-        timing = {}
-        _, st = r.render(out=out, stats=True, shadow_net=shadow_net, timing=timing)
+    def arm(renderer, shadow_net, n_steps, sampler=None):
+        _, st = renderer.render(out=out, engine=eng, stats=True, shadow_net=shadow_net, stream=stream.cuda_stream)
+        stream.synchronize()
         img = out.cpu().numpy().astype(np.float64)
-        return e0.elapsed_time(e1) / args.steps, st, img, {k: v[0] for k, v in timing.items() if v[1]}
+        ms = time_steps(torch, renderer, eng, out, stream, n_steps, 1, flush, sampler, shadow_net)
+        return sum(ms) / len(ms), st, img
 
-    ms_m, st_m, img_m, k_m = frames(None)
-    ms_n, st_n, img_n, k_n = frames(bf)
-    ids = S.strided_pixels(W, H, 32, offset=5)
+    sampler = ClockSampler(local)
+    ms_n, st_n, img_n = arm(r, bf, steps, sampler)
+    k_n = {k: v["ms_per_step"] for k, v in kernel_times(torch, r, eng, out, stream, flush, 2, bf).items()}
+    ms_m, st_m, img_m = arm(r, None, 3)
+    k_m = {k: v["ms_per_step"] for k, v in kernel_times(torch, r, eng, out, stream, flush, 1).items()}
+    r32 = M.Renderer(sc, device=local, precision=M.MRF_PREC_FP32)
+    r32.set_tuning(8, 512, 16)
+    ms_f, st_f, img_f = arm(r32, None, 2)
+    r32.close()
+    ids = S.strided_pixels(Wa, Ha, 32, offset=5)
+    t0 = time.perf_counter()
     ref = oracle.render(sc, ids, records=False)
+    t_orc = time.perf_counter() - t0
     ok = ref["flags"] == 0
-
-    def err(img):
-        a, b = img[ids][ok, :3], ref["rgba"][ok, :3]
-        peak = np.abs(b).max()
-        return {"psnr_db": float(10 * np.log10(peak * peak / np.mean((a - b) ** 2))),
-                "max_abs": float(np.abs(a - b).max())}
-
-    line = {
-        "metric": METRIC, "value": st_n["segments"] / (ms_n / 1e3), "unit": METRIC, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_n, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": f"hash-grid scene, 4 area lights x 16 shadow rays per diffuse hit, {W}x{H}, 1 spp, "
-                               "8 segments, BF16 field; shadow transmittance from the learned network (BF16 weights)",
-                   "tuning": best},
-        "march": {"ms_per_step": ms_m, "value": st_m["segments"] / (ms_m / 1e3), "kernels_ms": k_m,
-                  "shadow_samples_evaluated": st_m["shadow_samples_evaluated"], "image_error_vs_oracle": err(img_m)},
+    res = {
+        "metric": METRIC, "value": st_n["segments"] / (ms_n / 1e3), "unit": METRIC, "ms_per_step": ms_n,
+        "steps": steps, "dtype": "bf16",
+        "config": {"workload": f"hash-grid scene, 4 area lights x 16 shadow rays per diffuse hit, {Wa}x{Ha}, 1 spp, "
+                               "8 segments, BF16 field; shadow transmittance from the learned network (BF16 weights "
+                               "on the tensor cores)", "tuning": r.tuning(),
+                   "l2": "256 MB buffer written before every timed step"},
+        "clocks": sampler.summary(),
         "network": {"ms_per_step": ms_n, "kernels_ms": k_n, "shadow_net_evals": st_n["shadow_net_evals"],
-                    "image_error_vs_oracle": err(img_n), "pairs_s": t_pairs, "train_s": t_train,
+                    "image_error_vs_oracle": psnr_maxabs(img_n[ids], ref["rgba"], ok), "pairs_s": t_pairs,
+                    "train_s": t_train,
                     "train": f"2^{args.train_pairs_log2} pairs (FP32 march labels), {args.train_steps} Adam steps "
                              "of 65536, lr 1e-2 x 0.9995^t"},
-        "speedup_vs_march": ms_m / ms_n, "oracle_pixels": int(ok.sum()),
+        "march_bf16": {"ms_per_step": ms_m, "value": st_m["segments"] / (ms_m / 1e3), "kernels_ms": k_m,
+                       "shadow_samples_evaluated": st_m["shadow_samples_evaluated"],
+                       "image_error_vs_oracle": psnr_maxabs(img_m[ids], ref["rgba"], ok)},
+        "march_fp32": {"ms_per_step": ms_f, "value": st_f["segments"] / (ms_f / 1e3),
+                       "image_error_vs_oracle": psnr_maxabs(img_f[ids], ref["rgba"], ok)},
+        "speedup_vs_march_bf16": ms_m / ms_n, "speedup_vs_march_fp32": ms_f / ms_n,
+        "oracle": {"pixels": int(ok.sum()), "ambiguous_pixels_excluded": int((~ok).sum()),
+                   "sample": "every 32nd row and column, the plain method (marched shadows)", "seconds": t_orc},
     }
-    print(json.dumps(line))
     bf.close()
     net.close()
     r.close()
+    del out, flush
+    torch.cuda.empty_cache()
+    return res
+
+
+def dynamic_workload(args, local: int = 0):
+    """Dynamic sequence: a 256x256 cloth grid with sinusoid-plus-noise motion and
+    64 rigid 2,048-triangle bodies with seeded rigid motion in the hash-grid
+    scene (BF16 field), 4 point lights whose shadow rays take the learned
+    transmittance, 1920x1080, --spp paths per pixel, --frames frames.  Every
+    frame uploads its vertices and refits the BVH; every --rebuild-th frame
+    rebuilds it on the GPU instead.  The frame latency is the host wall time from
+    the vertex upload to the finished image.  Beside it: the plain FP32 GPU path
+    (megakernel, marched shadows) on the last frame, and the image error of the
+    last frame against the FP64 oracle's plain method on every 128th row and
+    column."""
+    import torch
+    from paper_2309_04581_gb300 import scenes as S
+    import paper_2309_04581_gb300.mrf as M
+    import oracle
+    seq = S.DynamicSequence(WIDTH, HEIGHT, spp=args.spp)
+    dev = f"cuda:{local}"
+    r = M.Renderer(seq.scene, device=local, precision=M.MRF_PREC_BF16)
+    net = M.ShadowNet(r, precision=M.MRF_PREC_BF16, seed=7, lr_decay=0.9995)
+    t0 = time.perf_counter()
+    pairs = net.pairs(11, 0, 1 << 22)
+    net.train(pairs, 1 << 16, 3000)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del pairs
+    out = torch.empty((seq.scene.n_rays, 4), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(local).cuda_stream
+    n_frames = args.frames
+    verts = [seq.vertices(k) for k in range(min(n_frames, 30))]   # host motion is not the renderer's work
+    lat, segs, st = [], 0, None
+    sampler = ClockSampler(local)
+    for k in range(-args.warmup, 0):
+        r.set_vertices(verts[0], stream=stream)
+        r.render(out=out, shadow_net=net)
+    torch.cuda.synchronize()
+    with sampler:
+        for k in range(n_frames):
+            v = verts[k % len(verts)]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r.set_vertices(v, rebuild="gpu" if (k > 0 and k % args.rebuild == 0) else False, stream=stream)
+            _, st = r.render(out=out, stats=True, shadow_net=net)
+            lat.append((time.perf_counter() - t0) * 1e3)
+            segs += st["segments"]
+    last = (n_frames - 1) % len(verts)
+    img = out.cpu().numpy().astype(np.float64)
+    lat_s = sorted(lat)
+    p = lambda q: lat_s[min(len(lat_s) - 1, int(round(q * (len(lat_s) - 1))))]
+    # the plain FP32 GPU path on the same (last) frame: FP32 field, marched shadows
+    r32 = M.Renderer(seq.scene, device=local, precision=M.MRF_PREC_FP32)
+    r32.set_vertices(verts[last], stream=stream)
+    o32 = torch.empty_like(out)
+    _, st32 = r32.render(out=o32, engine=M.MRF_ENGINE_MEGAKERNEL, stats=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    r32.render(out=o32, engine=M.MRF_ENGINE_MEGAKERNEL)
+    e1.record()
+    torch.cuda.synchronize()
+    ms32 = e0.elapsed_time(e1)
+    img32 = o32.cpu().numpy().astype(np.float64)
+    r32.close()
+    del o32
+    sc_last = S.Scene(name="dynamic_last", camera=seq.scene.camera, field=seq.scene.field,
+                      mesh=S.Mesh(verts[last], seq.tris, seq.mat), materials=seq.scene.materials,
+                      lights=seq.scene.lights, opts=seq.scene.opts)
+    ids = S.strided_pixels(WIDTH, HEIGHT, 128, offset=37)
+    t0 = time.perf_counter()
+    ref = oracle.render(sc_last, ids, records=False)
+    t_orc = time.perf_counter() - t0
+    ok = ref["flags"] == 0
+    res = {
+        "metric": METRIC, "value": segs / (sum(lat) / 1e3), "unit": METRIC, "frames": len(lat),
+        "latency_ms": {"p50": p(0.5), "p99": p(0.99), "max": lat_s[-1], "mean": sum(lat) / len(lat)},
+        "dtype": "bf16", "clocks": sampler.summary(),
+        "config": {"workload": f"dynamic sequence: {seq.n_tris} triangles ({seq.n_bodies} rigid bodies, cloth "
+                               f"{seq.cloth.tris.shape[0]} triangles), {WIDTH}x{HEIGHT}, {args.spp} spp, 8 segments, "
+                               f"4 point lights with learned shadow transmittance (BF16), refit per frame, GPU "
+                               f"rebuild every {args.rebuild}", "engine": "wavefront"},
+        "latency_note": "host wall time per frame: vertex upload + refit or GPU rebuild + render + statistics read",
+        "train_s": t_train,
+        "last_frame": {"segments": st["segments"], "shadow_net_evals": st["shadow_net_evals"],
+                       "image_error_vs_oracle": psnr_maxabs(img[ids], ref["rgba"], ok)},
+        "fp32_gpu": {"engine": "megakernel, marched shadows", "ms_per_frame": ms32,
+                     "value": st32["segments"] / (ms32 / 1e3),
+                     "image_error_vs_oracle": psnr_maxabs(img32[ids], ref["rgba"], ok)},
+        "oracle": {"pixels": int(ok.sum()), "ambiguous_pixels_excluded": int((~ok).sum()),
+                   "sample": "every 128th row and column of the last frame, the plain method (marched shadows)",
+                   "seconds": t_orc},
+    }
+    net.close()
+    r.close()
+    del out
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_views(args):
@@ -668,9 +740,9 @@ def run_views(args):
     one render call, a mirror room around the hash-grid field (BF16), 13
     noise-displaced spheres and a 128x128 cloth grid (99,340 triangles), up to
     16 segments per path, 1 spp.  Launch shapes and queue size come from the
-    autotuner, run on the same frame; the frame
-    is captured once into a CUDA graph and replayed, the cloth refitted before
-    every frame.  Times --steps frames (refit + replay) with CUDA events."""
+    autotuner, run on the same frame; the frame is captured once into a CUDA
+    graph and replayed, the cloth refitted before every frame.  Times --steps
+    frames (refit + replay) with CUDA events."""
     import torch
     from paper_2309_04581_gb300 import scenes as S
     import paper_2309_04581_gb300.mrf as M
@@ -696,12 +768,14 @@ def run_views(args):
         r.set_vertices(verts[k], stream=stream)
         frame.replay()
     torch.cuda.synchronize()
-    e0.record()
-    for k in range(args.warmup, args.warmup + args.steps):
-        r.set_vertices(verts[k], stream=stream)
-        frame.replay()
-    e1.record()
-    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    with sampler:
+        e0.record()
+        for k in range(args.warmup, args.warmup + args.steps):
+            r.set_vertices(verts[k], stream=stream)
+            frame.replay()
+        e1.record()
+        torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     st = frame.stats()
     line = {
@@ -713,6 +787,7 @@ def run_views(args):
                    "tuning": best, "graph": "frame captured once (mrf_frame_capture), replayed per step"},
         "work_per_step": st, "plain_render_ms": ms_plain, "autotune_ms": tune_ms,
         "field_samples_per_s": (st["samples_evaluated"] + st["shadow_samples_evaluated"]) / (ms / 1e3),
+        "clocks": sampler.summary(),
     }
     print(json.dumps(line))
     frame.close()
@@ -724,9 +799,9 @@ def main():
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "dynamic":
-        run_dynamic(args)
+        print(json.dumps(dynamic_workload(args)))
     elif args.workload == "area":
-        run_area(args)
+        print(json.dumps(area_workload(args)))
     elif args.workload == "views":
         run_views(args)
     else:
