@@ -75,10 +75,10 @@ __device__ __forceinline__ void load_pair(const uint32_t *__restrict__ tab, uint
     e1 = ((i1 & ~3u) == c0) ? pick4(q, i1 & 3u) : __ldg(tab + i1);
 }
 
-__device__ __forceinline__ float2 encode_level_pairs(const FieldDev &F, int l, V3 p) {
+// The corner entries (FP16 pairs) of level l around p and the trilinear weights.
+__device__ __forceinline__ void level_corners(const FieldDev &F, int l, V3 p, uint32_t (&e)[8], float (&w)[3]) {
     const uint32_t N = F.res[l];
     int c[3];
-    float w[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         // p lies in the field box (callers encode only samples with support,
@@ -116,11 +116,17 @@ __device__ __forceinline__ float2 encode_level_pairs(const FieldDev &F, int l, V
         idx[7] = (x1 ^ a11) & mask;
     }
     const uint32_t *tab = F.table + ((size_t)l << F.log2T);
-    uint32_t e[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) idx[k] = checked_index(idx[k], 1ull << F.log2T, F.status);
 #pragma unroll
     for (int k = 0; k < 4; ++k) load_pair(tab, idx[2 * k], idx[2 * k + 1], e[2 * k], e[2 * k + 1]);
+}
+
+// Level l of the encoding at p, interpolated in FP32 (FP16 kernels).
+__device__ __forceinline__ float2 encode_level_pairs(const FieldDev &F, int l, V3 p) {
+    uint32_t e[8];
+    float w[3];
+    level_corners(F, l, p, e, w);
     float2 v[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) v[k] = __half22float2(*reinterpret_cast<const __half2 *>(&e[k]));
@@ -132,6 +138,26 @@ __device__ __forceinline__ float2 encode_level_pairs(const FieldDev &F, int l, V
     const float2 b0 = make_float2(fmaf(w[1], a[1].x - a[0].x, a[0].x), fmaf(w[1], a[1].y - a[0].y, a[0].y));
     const float2 b1 = make_float2(fmaf(w[1], a[3].x - a[2].x, a[2].x), fmaf(w[1], a[3].y - a[2].y, a[2].y));
     return make_float2(fmaf(w[2], b1.x - b0.x, b0.x), fmaf(w[2], b1.y - b0.y, b0.y));
+}
+
+// The same level in packed FP16 arithmetic (BF16 kernels): the corner pairs are
+// FP16 already and the trilinear weights are rounded to FP16 once, so the seven
+// interpolations are a subtraction and a fused multiply-add of a pair each.
+// Their rounding (2^-11) stays below the BF16 rounding of the result (2^-8).
+__device__ __forceinline__ __half2 encode_level_h2(const FieldDev &F, int l, V3 p) {
+    uint32_t e[8];
+    float w[3];
+    level_corners(F, l, p, e, w);
+    __half2 v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = *reinterpret_cast<const __half2 *>(&e[k]);
+    const __half2 wx = __float2half2_rn(w[0]), wy = __float2half2_rn(w[1]), wz = __float2half2_rn(w[2]);
+    __half2 a[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a[k] = __hfma2(wx, __hsub2(v[2 * k + 1], v[2 * k]), v[2 * k]);
+    const __half2 b0 = __hfma2(wy, __hsub2(a[1], a[0]), a[0]);
+    const __half2 b1 = __hfma2(wy, __hsub2(a[3], a[2]), a[2]);
+    return __hfma2(wz, __hsub2(b1, b0), b0);
 }
 
 // G tile groups of 128 threads per CTA; group g owns TMEM columns [64g, 64g + 64),
@@ -231,8 +257,13 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
             if (s > 0.f) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const float2 f = encode_level_pairs(F, 4 * c + q, p);
-                    w[q] = pack2<kBF16>(f.x, f.y);
+                    if (kBF16) {
+                        const float2 f = __half22float2(encode_level_h2(F, 4 * c + q, p));
+                        w[q] = pack2<kBF16>(f.x, f.y);
+                    } else {
+                        const float2 f = encode_level_pairs(F, 4 * c + q, p);
+                        w[q] = pack2<kBF16>(f.x, f.y);
+                    }
                 }
             }
             store_chunk(sA, gt, c, sbo_in, make_uint4(w[0], w[1], w[2], w[3]));
@@ -427,8 +458,13 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
             if (s > 0.f) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const float2 f = encode_level_pairs(F, 4 * c + q, p);
-                    w[q] = pack2<kBF16>(f.x, f.y);
+                    if (kBF16) {
+                        const float2 f = __half22float2(encode_level_h2(F, 4 * c + q, p));
+                        w[q] = pack2<kBF16>(f.x, f.y);
+                    } else {
+                        const float2 f = encode_level_pairs(F, 4 * c + q, p);
+                        w[q] = pack2<kBF16>(f.x, f.y);
+                    }
                 }
             }
             store_chunk(sA, gt, c, 512, make_uint4(w[0], w[1], w[2], w[3]));
