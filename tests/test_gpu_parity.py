@@ -267,12 +267,15 @@ def test_traversal_counts_agree_between_engines(M, torch_cuda):
     assert 1 <= a["bvh_worst_nodes"] <= a["bvh_nodes"] and a["bvh_worst_path"] < a["paths"]
 
 
-def test_config2_full_size_sampled_pixels(M, orc, torch_cuda):
-    # the 800x800 benchmark workload, rendered whole on the GPU in the bench's
-    # launch configuration; every 16th row and column is recomputed by the oracle
-    sc = S.config2(800, 800)
+@pytest.mark.parametrize("size", [(800, 800), (1920, 1080)])
+def test_config2_full_size_sampled_pixels(M, orc, torch_cuda, size):
+    # the benchmark's scene at 800x800 and at the headline's 1920x1080, rendered
+    # whole on the GPU (FP32 megakernel); every 16th row and column is
+    # recomputed by the oracle
+    w, h = size
+    sc = S.config2(w, h)
     gpu = _render(M, sc)
-    ids = S.strided_pixels(800, 800, 16, offset=5)
+    ids = S.strided_pixels(w, h, 16, offset=5)
     ref = orc.render(sc, ids)
     _compare(gpu, ref, ids)
 
@@ -498,18 +501,28 @@ def test_wavefront_tensor_core_image_quality(M, orc, torch_cuda, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
-def test_wavefront_tensor_core_full_size_sampled(M, orc, torch_cuda, prec):
-    # the 800x800 workload in the benchmark's configuration, oracle on every 16th row/column
-    sc = S.config2(800, 800)
-    gpu = _render_prec(M, sc, prec, records=False)
-    ids = S.strided_pixels(800, 800, 16, offset=3)
+@pytest.mark.parametrize("size", [(800, 800), (1920, 1080)])
+def test_wavefront_tensor_core_full_size_sampled(M, orc, torch_cuda, prec, size):
+    # the benchmark's workload in its launch configuration (the 1920x1080 frame
+    # is the headline), oracle on every 16th row and column: image error, and
+    # the hit ids and segment counts of every sampled path whose course no
+    # flagged decision touches
+    w, h = size
+    sc = S.config2(w, h)
+    gpu = _render_prec(M, sc, prec, records=True)
+    ids = S.strided_pixels(w, h, 16, offset=3)
     ref = orc.render(sc, ids)
     ok = ref["flags"] == 0
     img = gpu["rgba"][ids]
     psnr = _psnr(img, ref["rgba"], ok)
     maxabs = np.abs(img[ok, :3] - ref["rgba"][ok, :3]).max()
-    print(f"{prec} 800x800 sampled: PSNR {psnr:.1f} dB, max abs {maxabs:.3g}")
+    print(f"{prec} {w}x{h} sampled: PSNR {psnr:.1f} dB, max abs {maxabs:.3g}, {(~ok).mean():.3%} flagged")
     assert psnr >= 45.0 and maxabs <= 1e-2
+    assert (~ok).mean() <= 1e-3
+    tr = _trusted(ref)
+    assert np.array_equal(np.where(tr, gpu["tri"][ids], 0), np.where(tr, ref["tri"], 0))
+    clear = ref["first_flag"] == 0
+    assert np.array_equal(gpu["segments"][ids][clear], ref["segments"][clear])
 
 
 # ----------------------------------------------------------------- field pose and tone map
