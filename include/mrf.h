@@ -314,7 +314,10 @@ typedef struct mrf_stats {
     uint64_t samples_evaluated;    /* samples in occupied cells (field network run) */
     uint64_t shadow_samples_evaluated;
     uint64_t fp64_retests;         /* near-edge triangle tests redone in FP64 */
-    uint64_t status;               /* device status word (0 = ok) */
+    uint64_t status;               /* device status word (0 = ok); bits: 1 BVH traversal stack overflow,
+                                      2 a segment of more than 2^24 samples, 4 a tensor-core wait gave
+                                      up, 8 the self-test wait gave up, 0x100 a bad index (bounds-checked
+                                      build) */
     uint64_t shadow_net_evals;     /* shadow rays answered by the shadow network */
     uint64_t ended_miss, ended_tau, ended_cap;   /* paths that left the scene, fell below tau, hit the bounce cap */
     uint64_t bvh_nodes;            /* BVH nodes visited (closest-hit, shadow and mask rays) */
