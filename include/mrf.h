@@ -381,7 +381,9 @@ mrf_status mrf_render_static(mrf_context *ctx, const mrf_field *field, const mrf
  * such parameters; results do not depend on them (only speed and memory). */
 typedef struct mrf_tuning {
     uint32_t field_groups;       /* 128-sample tiles in flight per CTA of the tensor-core field kernel:
-                                    8 (one CTA per SM, all TMEM) or 4 (two CTAs per SM); default 8 */
+                                    8 (one CTA per SM, all TMEM) or 4 (two CTAs per SM), the layers' A
+                                    operands in shared memory; or 5 (one CTA per SM) with every A operand
+                                    in tensor memory (view-dependent fields then use 8); default 8 */
     uint32_t samples_per_path;   /* sample-buffer capacity per path (plus 4 Mi samples); 16..4096, default 96 */
     uint32_t rounds;             /* sample-generation rounds per segment, 1..16, default 1: the paths whose
                                     samples did not fit the buffer go to the next round; those left after

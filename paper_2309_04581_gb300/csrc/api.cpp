@@ -1215,10 +1215,10 @@ mrf_status mrf_tuning_get(const mrf_context *ctx, mrf_tuning *out) {
 
 mrf_status mrf_tuning_set(mrf_context *ctx, const mrf_tuning *t) {
     if (!ctx || !t) return fail(MRF_ERR_INVALID_ARG, "mrf_tuning_set: NULL argument");
-    if ((t->field_groups != 4 && t->field_groups != 8) || t->samples_per_path < 16 || t->samples_per_path > 4096 ||
-        t->rounds < 1 || t->rounds > 16 || t->tail_paths > (1u << 20))
-        return fail(MRF_ERR_INVALID_ARG, "mrf_tuning_set: field_groups 4 or 8, samples_per_path 16..4096, rounds 1..16, "
-                                         "tail_paths 0..2^20");
+    if ((t->field_groups != 4 && t->field_groups != 5 && t->field_groups != 8) || t->samples_per_path < 16 ||
+        t->samples_per_path > 4096 || t->rounds < 1 || t->rounds > 16 || t->tail_paths > (1u << 20))
+        return fail(MRF_ERR_INVALID_ARG, "mrf_tuning_set: field_groups 4, 5 or 8, samples_per_path 16..4096, "
+                                         "rounds 1..16, tail_paths 0..2^20");
     ctx->tuning = *t;
     return MRF_OK;
 }

@@ -340,6 +340,219 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
 }
 
 // ---------------------------------------------------------------------------
+// The same field with every layer's A operand in tensor memory: the thread of
+// a row writes the row's encoding (K = 32) and, after each hidden layer, its
+// 64 activations (K = 64) with tcgen05.st, and the MMAs read A from tensor
+// memory.  No A operand goes through shared memory, whose stores share the L1
+// data pipe with the table gathers.  A group needs 64 accumulator and 32
+// operand columns: five groups (640 threads) per SM, 480 of the 512 columns.
+// A in tensor memory: row r of the tile in lane r, K along the columns, two
+// 16-bit elements per 32-bit column (the low half first), so a K = 16 step is 8
+// columns.
+constexpr int kTmGroups = 5;
+constexpr uint32_t kTmGroupCols = 96;   // accumulator [0, 64), A operand [64, 96)
+constexpr int kTmBars = kSmemBars;
+constexpr int kTmSlot = kTmBars + 8 * kTmGroups;
+constexpr int kTmBytes = kTmSlot + 16;
+
+__device__ __forceinline__ void tmem_st_x16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]) : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// kind::f16 MMA with A read from tensor memory at a_tmem
+__device__ __forceinline__ void mma_f16_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                               uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// bias (kernel-parameter constant bank) and ReLU of 32 accumulator columns, packed in pairs
+template <bool kBF16, int kOff>
+__device__ __forceinline__ void relu_bias_pack(const uint32_t (&r)[32], const FieldDev &F, uint32_t (&w)[16]) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+        w[q] = pack2_relu<kBF16>(__uint_as_float(r[2 * q]) + F.bias_c[kOff + 2 * q],
+                                 __uint_as_float(r[2 * q + 1]) + F.bias_c[kOff + 2 * q + 1]);
+}
+
+template <bool kBF16>
+__global__ void __launch_bounds__(128 * kTmGroups, 1)
+    field_tc_tmem_kernel(const FieldDev F, const float *__restrict__ pts, int stride,
+                         const uint32_t *__restrict__ n_dev, uint32_t n_host, float4 *__restrict__ out,
+                         unsigned *__restrict__ status) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint32_t *sTmem = reinterpret_cast<uint32_t *>(smem + kTmSlot);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int g = tid >> 7, gt = tid & 127, gw = gt >> 5;
+    const int n_in = F.n_in, kin = n_in / 16, sbo_in = (n_in / 8) * 128;
+    constexpr int kThreadsCta = 128 * kTmGroups;
+    {
+        const int w1_bytes = 64 * n_in * 2;
+        const uint8_t *src = reinterpret_cast<const uint8_t *>(F.mlp_lp) + (kBF16 ? w1_bytes + 10240 : 0);
+        for (int o = tid * 16; o < w1_bytes; o += kThreadsCta * 16)
+            *reinterpret_cast<uint4 *>(smem + kSmemW1 + o) = __ldg(reinterpret_cast<const uint4 *>(src + o));
+        for (int o = tid * 16; o < 10240; o += kThreadsCta * 16)
+            *reinterpret_cast<uint4 *>(smem + kSmemW2 + o) = __ldg(reinterpret_cast<const uint4 *>(src + w1_bytes + o));
+    }
+    float4 *sSup = reinterpret_cast<float4 *>(smem + kSmemSupport);
+    const bool sup_smem = F.n_support <= kSupportMax;
+    if (sup_smem)
+        for (int k = tid; k < F.n_support; k += kThreadsCta) sSup[k] = __ldg(F.support + k);
+    const float4 *sup = sup_smem ? sSup : F.support;
+    const uint32_t bar = smem_u32(smem + kTmBars + 8 * g);
+    if (gt == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(sTmem)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *sTmem;
+    const uint32_t t_acc = tmem + kTmGroupCols * (uint32_t)g;           // this group's accumulator columns
+    const uint32_t t_a = t_acc + 64u;                                   // and its A operand
+    const uint32_t lanes = (uint32_t)(gw * 32) << 16;                   // this warp's lanes
+    const uint32_t aW1 = smem_u32(smem + kSmemW1), aW2 = smem_u32(smem + kSmemW2), aW3 = smem_u32(smem + kSmemW3);
+    constexpr uint32_t id64 = instr_desc(kBF16, 128, 64), id16 = instr_desc(kBF16, 128, 16);
+    const uint32_t n = n_dev ? min(*n_dev, n_host) : n_host;
+    const int bar_id = 1 + g;
+    uint32_t phase = 0;
+    bool ok = true;
+
+    auto wait_mma = [&]() -> bool {
+        if (gw == 0) ok &= mbar_wait(bar, phase);
+        phase ^= 1;
+        fence_before_sync();
+        const bool bad = group_sync_or(bar_id, !ok);
+        fence_after_sync();
+        return !bad;
+    };
+    // the operand written by this group's threads is complete: the MMAs of a layer may read it
+    auto operand_ready = [&]() -> bool {
+        tmem_st_wait();
+        fence_before_sync();
+        return !group_sync_or(bar_id, !ok);
+    };
+    for (uint32_t tile = blockIdx.x * kTmGroups + g; tile * 128u < n; tile += gridDim.x * kTmGroups) {
+        const uint32_t i = tile * 128u + gt;
+        const bool valid = i < n;
+        V3 p = v3(0.f, 0.f, 0.f);
+        float s = 0.f, dl = 1.f;   // support, interval length (stride 4)
+        if (valid) {
+            if (stride == 4) {
+                const float4 q = reinterpret_cast<const float4 *>(pts)[i];
+                p = v3(q.x, q.y, q.z);
+                dl = q.w;
+            } else {
+                p = v3(pts[(size_t)stride * i], pts[(size_t)stride * i + 1], pts[(size_t)stride * i + 2]);
+            }
+            if (F.n_support) {
+                for (int k = 0; k < F.n_support; ++k) {
+                    const float4 c = sup[k];
+                    const float dx = p.x - c.x, dy = p.y - c.y, dz = p.z - c.z;
+                    s = fmaxf(s, 1.0f - (dx * dx + dy * dy + dz * dz) * c.w);
+                }
+            } else {
+                s = 1.f;
+            }
+            if (!inside_field_box(F, p)) s = 0.f;
+        }
+        // hash encoding -> A (K = n_in = 32: 16 columns)
+        {
+            uint32_t w[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                w[q] = 0u;
+                if (s > 0.f) {
+                    if (kBF16) {
+                        const float2 f = __half22float2(encode_level_h2(F, q, p));
+                        w[q] = pack2<kBF16>(f.x, f.y);
+                    } else {
+                        const float2 f = encode_level_pairs(F, q, p);
+                        w[q] = pack2<kBF16>(f.x, f.y);
+                    }
+                }
+            }
+            tmem_st_x16(t_a + lanes, w);
+        }
+        if (!operand_ready()) break;
+        if (gt == 0) {
+            fence_after_sync();
+            for (int k = 0; k < kin; ++k)
+                mma_f16_tmem_a(t_acc, t_a + 8u * (uint32_t)k, smem_desc(aW1 + 256 * k, 128, sbo_in), id64, k);
+            mma_commit(bar);
+        }
+        if (!wait_mma()) break;
+        // layer 1 epilogue -> A (K = 64: 32 columns)
+        {
+            uint32_t r[32], w[16];
+            tmem_ld_x32(t_acc + lanes, r);
+            relu_bias_pack<kBF16, 0>(r, F, w);
+            tmem_st_x16(t_a + lanes, w);
+            tmem_ld_x32(t_acc + lanes + 32, r);
+            relu_bias_pack<kBF16, 32>(r, F, w);
+            tmem_st_x16(t_a + lanes + 16, w);
+        }
+        if (!operand_ready()) break;
+        if (gt == 0) {
+            fence_after_sync();
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                mma_f16_tmem_a(t_acc, t_a + 8u * (uint32_t)k, smem_desc(aW2 + 256 * k, 128, 1024), id64, k);
+            mma_commit(bar);
+        }
+        if (!wait_mma()) break;
+        // layer 2 epilogue -> A (K = 64)
+        {
+            uint32_t r[32], w[16];
+            tmem_ld_x32(t_acc + lanes, r);
+            relu_bias_pack<kBF16, 64>(r, F, w);
+            tmem_st_x16(t_a + lanes, w);
+            tmem_ld_x32(t_acc + lanes + 32, r);
+            relu_bias_pack<kBF16, 96>(r, F, w);
+            tmem_st_x16(t_a + lanes + 16, w);
+        }
+        if (!operand_ready()) break;
+        if (gt == 0) {
+            fence_after_sync();
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                mma_f16_tmem_a(t_acc, t_a + 8u * (uint32_t)k, smem_desc(aW3 + 256 * k, 128, 1024), id16, k);
+            mma_commit(bar);
+        }
+        if (!wait_mma()) break;
+        {
+            uint32_t r[16];
+            tmem_ld_x16(t_acc + lanes, r);
+            const float o0 = __uint_as_float(r[0]) + F.bias_c[128], o1 = __uint_as_float(r[1]) + F.bias_c[129],
+                        o2 = __uint_as_float(r[2]) + F.bias_c[130], o3 = __uint_as_float(r[3]) + F.bias_c[131];
+            if (valid) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (s > 0.f)
+                    v = make_float4(s * expf(fminf(o0, 15.f)) * dl, softplusf(o1), softplusf(o2), softplusf(o3));
+                out[i] = v;
+            }
+        }
+        fence_before_sync();
+    }
+    if (!ok && gt == 0 && status) atomicOr(status, 4u);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // View-dependent fields: five chained MMAs per 128-sample tile.  Layer 1
 // (in -> 64), the density head (64 -> 16, N = 16), then the colour network on
 // [head outputs | sh16(view direction)] (32 -> 64 -> 64 -> 3, the last padded
@@ -539,7 +752,7 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
 
 // CTAs per SM of the persistent launch: 8 groups take all 512 TMEM columns
 // (one CTA), 4 groups half of them (two CTAs)
-int field_tc_blocks_per_sm(int groups) { return groups == 4 ? 2 : 1; }
+int field_tc_blocks_per_sm(int groups) { return groups == 4 ? 2 : 1; }   // 5 and 8 groups: one CTA per SM
 
 template <int G>
 static cudaError_t launch_groups(bool bf16, const FieldDev &F, const float *pts, int stride, const uint32_t *n_dev,
@@ -575,6 +788,13 @@ cudaError_t launch_field_tc_view(const FieldDev &F, bool bf16, const float *pts,
 
 cudaError_t launch_field_tc(const FieldDev &F, bool bf16, const float *pts, int stride, const uint32_t *n_dev,
                             uint32_t n_host, float4 *out, unsigned *status, int grid, cudaStream_t s, int groups) {
+    if (groups == kTmGroups && F.n_in == 32) {   // A operands in tensor memory (one CTA of five groups per SM)
+        auto kern = bf16 ? field_tc_tmem_kernel<true> : field_tc_tmem_kernel<false>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmBytes);
+        if (e != cudaSuccess) return e;
+        kern<<<grid <= 0 ? 1 : grid, 128 * kTmGroups, kTmBytes, s>>>(F, pts, stride, n_dev, n_host, out, status);
+        return cudaGetLastError();
+    }
     if (groups == 4) return launch_groups<4>(bf16, F, pts, stride, n_dev, n_host, out, status, grid, s);
     return launch_groups<kGroups>(bf16, F, pts, stride, n_dev, n_host, out, status, grid, s);
 }

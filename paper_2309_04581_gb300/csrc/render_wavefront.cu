@@ -837,10 +837,11 @@ __global__ void __launch_bounds__(kThreads) wf_mask(const WfParams W, int cur, i
 // Jobs whose samples did not fit the sample buffer are marched in place here,
 // on the CUDA cores in FP32, producing the same per-slot results as
 // wf_composite (comp, sdepth).  Nothing to do when no job overflowed.
-__global__ void __launch_bounds__(kThreads) wf_overflow(const WfParams W, int cur) {
+__global__ void __launch_bounds__(kThreads) wf_overflow(const WfParams W, int cur, int last_round) {
     const RenderParams &P = W.R;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (tail_taken(W) || tid >= W.ctr[cur]) return;
+    // nothing left pending after the last generation round: the whole grid leaves
+    if (tail_taken(W) || *pending_ctr(W, last_round) == 0 || tid >= W.ctr[cur]) return;
     const int K = P.n_shadow;
     const bool rad = W.rcount[tid] == kOverflow;
     const float4 h4 = W.hp[tid];
@@ -1357,7 +1358,7 @@ cudaError_t enqueue_frame(const WfParams &W, const RenderParams &P, uint32_t pat
     const unsigned grid = (paths + kThreads - 1) / kThreads;
     const FieldDev &F = P.F;
     const bool tc = F.kind == MRF_FIELD_HASHGRID && F.precision != MRF_PREC_FP32;
-    const int groups = P.tc_groups == 4 ? 4 : 8;
+    const int groups = P.tc_groups == 4 || P.tc_groups == 5 ? P.tc_groups : 8;
     const int field_grid = tc ? 152 * field_tc_blocks_per_sm(groups) : 152 * 8;
     const int rounds = std::min(std::max(P.max_rounds, 1), kMaxRounds);
     // counters left over from the previous call
@@ -1430,7 +1431,7 @@ cudaError_t enqueue_frame(const WfParams &W, const RenderParams &P, uint32_t pat
         }
         if ((e = cudaMemsetAsync(W.ctr + nxt, 0, 4, s)) != cudaSuccess) return e;
         timer_begin(timer, MRF_KERNEL_OVERFLOW, s);
-        wf_overflow<<<grid, kThreads, 0, s>>>(W, cur);
+        wf_overflow<<<grid, kThreads, 0, s>>>(W, cur, rounds - 1);
         timer_end(timer, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         timer_begin(timer, MRF_KERNEL_SHADE, s);

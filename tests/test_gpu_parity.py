@@ -771,3 +771,23 @@ def test_persistent_tail_matches_the_wavefront_and_the_oracle(M, orc, torch_cuda
     assert _psnr(bf["rgba"], ref["rgba"], ok) >= 45.0
     assert np.abs(bf["rgba"][ok, :3] - ref["rgba"][ok, :3]).max() <= 1e-2
     assert np.array_equal(bf["tri"][ok], ref["tri"][ok])
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_field_operands_in_tensor_memory_give_the_same_image(M, torch_cuda, prec):
+    """field_groups = 5 keeps every layer's A operand in tensor memory (the
+    MMAs read A from TMEM) instead of shared memory: the same operands and the
+    same accumulation, so the image is the same bit for bit (a ragged frame
+    whose last tiles are partial)."""
+    torch = torch_cuda
+    sc = S.config2(97, 61)
+    r = M.Renderer(sc, precision={"fp16": M.MRF_PREC_FP16, "bf16": M.MRF_PREC_BF16}[prec])
+    a, st_a = r.render(stats=True)
+    a = a.clone()
+    r.set_tuning(5, 96, 1)
+    b, st_b = r.render(stats=True)
+    torch.cuda.synchronize()
+    assert st_a["status"] == 0 and st_b["status"] == 0
+    assert torch.equal(a, b)
+    assert st_a["samples_evaluated"] == st_b["samples_evaluated"]
+    r.close()
