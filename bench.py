@@ -18,6 +18,7 @@ the tensor cores, FP32 everywhere else).  The same line carries:
     column of the same frame (all host cores, and one core on a sparser sample);
   - e2e: the same frame through the C ABI into pinned host memory;
   - at_800x800, time_vs_pixels, view_dependent_field, bvh_traversal, kernels;
+  - captured_frame: the headline frame replayed as one CUDA graph;
   - area_lights: 4 area lights x 16 shadow rays per diffuse hit at 1920x1080,
     the shadow transmittance from the learned network (trained here on the
     GPU) against the marched shadows (BF16 and FP32 field), with image errors
@@ -286,6 +287,23 @@ def time_steps(torch, r, engine, out, stream, steps, warmup, flush, sampler=None
     return [a.elapsed_time(b) for a, b in evs]
 
 
+def time_replays(torch, frame, stream, steps, warmup, flush):
+    """The same protocol for a captured frame (mrf_frame_replay: the whole launch
+    sequence as one CUDA graph)."""
+    for _ in range(warmup):
+        frame.replay(stream.cuda_stream)
+    stream.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            flush.fill_(float(k))
+            evs[k][0].record(stream)
+            frame.replay(stream.cuda_stream)
+            evs[k][1].record(stream)
+    stream.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
 def kernel_times(torch, r, engine, out, stream, flush, reps, shadow_net=None):
     """Per-kernel CUDA-event milliseconds per frame (mean over reps frames)."""
     acc = {}
@@ -446,7 +464,7 @@ def run_ours(args):
                 "note": "64 B per node visited + 48 B per triangle tested; the BVH is on-chip (L1/L2) resident, "
                         "so this is not DRAM traffic; l2_frac against the L2 bandwidth measured here"}
     # other frame sizes, render time against pixel count, view-dependent field
-    scaling, hd800, vd, img_vd = None, None, None, None
+    scaling, hd800, vd, img_vd, captured = None, None, None, None, None
     if not args.no_extras:
         scaling = []
         for (w_s, h_s) in ((200, 200), (400, 400), (800, 800)):
@@ -456,13 +474,23 @@ def run_ours(args):
             _, st_s = r_s.render(out=o_s, engine=engine, stats=True, stream=stream.cuda_stream)
             ms_s = time_steps(torch, r_s, engine, o_s, stream, 5, args.warmup, flush)
             m_s = statistics.median(ms_s)
-            scaling.append({"pixels": w_s * h_s, "ms_per_step": m_s})
+            f_s = M.Frame(r_s, o_s, engine=engine)
+            rep_s = statistics.median(time_replays(torch, f_s, stream, 5, args.warmup, flush))
+            f_s.close()
+            scaling.append({"pixels": w_s * h_s, "ms_per_step": m_s, "captured_frame_ms": rep_s})
             if (w_s, h_s) == (800, 800):
                 hd800 = {"value": job_throughput(st_s["segments"], world, m_s), "unit": METRIC, "ms_per_step": m_s,
                          "field_samples_per_s": world * (st_s["samples_evaluated"] +
                                                          st_s["shadow_samples_evaluated"]) / (m_s / 1e3)}
             r_s.close()
-        scaling.append({"pixels": W * H, "ms_per_step": statistics.median(step_ms)})
+        f_hd = M.Frame(r, out, engine=engine)
+        rep_hd = time_replays(torch, f_hd, stream, max(3, args.steps // 2), args.warmup, flush)
+        f_hd.close()
+        captured = {"ms_per_step": statistics.median(rep_hd), "unit": METRIC,
+                    "value": job_throughput(segs, world, statistics.median(rep_hd)),
+                    "note": "the headline frame captured once (mrf_frame_capture) and replayed as one CUDA graph"}
+        scaling.append({"pixels": W * H, "ms_per_step": statistics.median(step_ms),
+                        "captured_frame_ms": captured["ms_per_step"]})
         for e in scaling:
             e["ns_per_pixel"] = e["ms_per_step"] * 1e6 / e["pixels"]
         # view-dependent radiance (Instant-NGP layout: density head + colour network of
@@ -514,6 +542,7 @@ def run_ours(args):
             "view_dependent_field": vd,
             "bvh_traversal": cast,
             "time_vs_pixels": scaling,
+            "captured_frame": captured,
             "e2e": {"value": e2e, "unit": METRIC, "h2d_bytes_per_step": 48,
                     "d2h_bytes_per_step": sc.n_rays * 16, "ms_per_step": statistics.median(e2e_ms),
                     "note": "camera record passed by value; image copied to pinned host memory inside mrf_render"},

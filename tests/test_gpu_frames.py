@@ -107,7 +107,7 @@ def test_autotuner_picks_a_candidate_and_keeps_results(env):
             assert torch.equal(img, before), (g, c)
             assert st["samples_evaluated"] == st0["samples_evaluated"]
     with pytest.raises(M.MrfError):
-        r.set_tuning(5, 96)
+        r.set_tuning(6, 96)
     r.close()
 
 
