@@ -60,19 +60,23 @@ struct Layout {
 };
 constexpr int kGroups = 8;   // 128-sample tiles in flight per CTA (one CTA per SM, all 512 TMEM columns)
 
-// Loads the FP16 pair of corner i0 and of its x-neighbour i1 with one 16-byte
-// load of the aligned 4-entry chunk holding i0; i1 shares that chunk for 3 of 4
-// cells (dense: i1 = i0 + 1; hashed: i1 = i0 ^ 1 or ^ 3 unless x = 3 mod 4) and
-// is otherwise fetched on its own.  Halves the load requests of the gather.
-__device__ __forceinline__ uint32_t pick4(const uint4 &q, uint32_t k) {
-    return (k & 2u) ? ((k & 1u) ? q.w : q.z) : ((k & 1u) ? q.y : q.x);
-}
+// Table loads.  The gathers hold the L1 load data pipe near its peak, and
+// what it spends per warp request grows with the bytes each lane asks for as
+// well as with the number of lanes: on the 1920x1080 frame the field kernel
+// took 14.47 ms with 16-byte chunk loads for every level, 13.21 ms with the
+// 8-byte pairs below for every level, 13.39 ms with one 4-byte load per
+// corner, and 12.93 ms with 4-byte loads on the dense levels and 8-byte pairs
+// on the hashed ones (the form used).
+//
+// Hashed level: corner i0 = x0 ^ a and its x-neighbour i1 = (x0 + 1) ^ a share
+// the aligned 8-byte pair holding i0 whenever x0 is even (then i1 = i0 ^ 1);
+// one 8-byte load serves both there and i1 is fetched on its own otherwise.
 __device__ __forceinline__ void load_pair(const uint32_t *__restrict__ tab, uint32_t i0, uint32_t i1, uint32_t &e0,
                                           uint32_t &e1) {
-    const uint32_t c0 = i0 & ~3u;
-    const uint4 q = __ldg(reinterpret_cast<const uint4 *>(tab + c0));
-    e0 = pick4(q, i0 & 3u);
-    e1 = ((i1 & ~3u) == c0) ? pick4(q, i1 & 3u) : __ldg(tab + i1);
+    const uint32_t c0 = i0 & ~1u;
+    const uint2 q = __ldg(reinterpret_cast<const uint2 *>(tab + c0));
+    e0 = (i0 & 1u) ? q.y : q.x;
+    e1 = ((i1 & ~1u) == c0) ? ((i1 & 1u) ? q.y : q.x) : __ldg(tab + i1);
 }
 
 // The corner entries (FP16 pairs) of level l around p and the trilinear weights.
@@ -118,8 +122,13 @@ __device__ __forceinline__ void level_corners(const FieldDev &F, int l, V3 p, ui
     const uint32_t *tab = F.table + ((size_t)l << F.log2T);
 #pragma unroll
     for (int k = 0; k < 8; ++k) idx[k] = checked_index(idx[k], 1ull << F.log2T, F.status);
+    if ((F.dense_mask >> l) & 1u) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) load_pair(tab, idx[2 * k], idx[2 * k + 1], e[2 * k], e[2 * k + 1]);
+        for (int k = 0; k < 8; ++k) e[k] = __ldg(tab + idx[k]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) load_pair(tab, idx[2 * k], idx[2 * k + 1], e[2 * k], e[2 * k + 1]);
+    }
 }
 
 // Level l of the encoding at p, interpolated in FP32 (FP16 kernels).
