@@ -249,14 +249,11 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
             } else {
                 p = v3(pts[(size_t)stride * i], pts[(size_t)stride * i + 1], pts[(size_t)stride * i + 2]);
             }
-            if (F.n_support) {
-                for (int k = 0; k < F.n_support; ++k) {
-                    const float4 c = sup[k];
-                    const float dx = p.x - c.x, dy = p.y - c.y, dz = p.z - c.z;
-                    s = fmaxf(s, 1.0f - (dx * dx + dy * dy + dz * dz) * c.w);
-                }
-            } else {
-                s = 1.f;
+            // support(p): max over the spheres, clamped at 0 (no sphere: no density)
+            for (int k = 0; k < F.n_support; ++k) {
+                const float4 c = sup[k];
+                const float dx = p.x - c.x, dy = p.y - c.y, dz = p.z - c.z;
+                s = fmaxf(s, 1.0f - (dx * dx + dy * dy + dz * dz) * c.w);
             }
             if (!inside_field_box(F, p)) s = 0.f;
         }
@@ -464,14 +461,11 @@ __global__ void __launch_bounds__(128 * kTmGroups, 1)
             } else {
                 p = v3(pts[(size_t)stride * i], pts[(size_t)stride * i + 1], pts[(size_t)stride * i + 2]);
             }
-            if (F.n_support) {
-                for (int k = 0; k < F.n_support; ++k) {
-                    const float4 c = sup[k];
-                    const float dx = p.x - c.x, dy = p.y - c.y, dz = p.z - c.z;
-                    s = fmaxf(s, 1.0f - (dx * dx + dy * dy + dz * dz) * c.w);
-                }
-            } else {
-                s = 1.f;
+            // support(p): max over the spheres, clamped at 0 (no sphere: no density)
+            for (int k = 0; k < F.n_support; ++k) {
+                const float4 c = sup[k];
+                const float dx = p.x - c.x, dy = p.y - c.y, dz = p.z - c.z;
+                s = fmaxf(s, 1.0f - (dx * dx + dy * dy + dz * dz) * c.w);
             }
             if (!inside_field_box(F, p)) s = 0.f;
         }
@@ -664,14 +658,11 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
                 const float4 q = dirs[i];
                 dv = v3(q.x, q.y, q.z);
             }
-            if (F.n_support) {
-                for (int k = 0; k < F.n_support; ++k) {
-                    const float4 c = sup[k];
-                    const float dx = p.x - c.x, dy = p.y - c.y, dz = p.z - c.z;
-                    s = fmaxf(s, 1.0f - (dx * dx + dy * dy + dz * dz) * c.w);
-                }
-            } else {
-                s = 1.f;
+            // support(p): max over the spheres, clamped at 0 (no sphere: no density)
+            for (int k = 0; k < F.n_support; ++k) {
+                const float4 c = sup[k];
+                const float dx = p.x - c.x, dy = p.y - c.y, dz = p.z - c.z;
+                s = fmaxf(s, 1.0f - (dx * dx + dy * dy + dz * dz) * c.w);
             }
             if (!inside_field_box(F, p)) s = 0.f;
         }

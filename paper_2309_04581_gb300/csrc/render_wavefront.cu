@@ -173,23 +173,83 @@ __device__ __forceinline__ bool segment_of(const RenderParams &P, V3 o, V3 d, fl
     return true;
 }
 
-// Support spheres a job's ray can enter: lane k tests sphere k (k < 32) against
-// the segment [t0, t1] with a small relative margin; spheres left out have
-// 1 - |p - c|^2 / r^2 < 0 at every point of the segment, so the support (a max
-// clamped at 0) is the same over the kept spheres.  More than 32 spheres: all kept.
-__device__ __forceinline__ uint32_t job_spheres(const FieldDev &F, const WalkCtx &X, V3 o, V3 d, float t0, float t1,
-                                                int lane) {
-    if (F.n_support > 32) return 0xffffffffu;
-    bool hit = false;
-    if (lane < F.n_support) {
-        const float4 c = X.support[lane];
-        const V3 oc = v3(c.x - o.x, c.y - o.y, c.z - o.z);
-        const float dd = dot(d, d), b = dot(oc, d) / dd;   // parameter of the closest approach
-        const float tc = fminf(fmaxf(b, t0), t1);          // clamped to the segment
-        const V3 q = v3(o.x + d.x * tc - c.x, o.y + d.y * tc - c.y, o.z + d.z * tc - c.z);
-        hit = dot(q, q) * c.w < 1.0f + 1e-3f;
+// Support sphere c's part in one job (o, d in the field's frame, S its
+// intervals): whether the ray passes within the sphere (a small relative
+// margin on r^2) over [S.t0, S.t1], and, with `ranges`, the interval-index
+// range [jb, je) the ray can spend inside it, conservative by two intervals
+// (none: jb = INT_MAX, je = -1).  A sphere the ray misses has
+// 1 - |p - c|^2 / r^2 < 0 at every point of the segment, and every sample
+// outside all ranges lies outside every sphere, so neither changes the support
+// (a max clamped at 0) of any sample the walk tests.
+__device__ __forceinline__ bool sphere_range(const float4 c, V3 o, V3 d, const Segment &S, float inv_h, bool ranges,
+                                             int &jb, int &je) {
+    const V3 oc = v3(c.x - o.x, c.y - o.y, c.z - o.z);
+    const float dd = dot(d, d), b = dot(oc, d) / dd;   // parameter of the closest approach
+    const float tc = fminf(fmaxf(b, S.t0), S.t1);      // clamped to the segment
+    const V3 q = v3(o.x + d.x * tc - c.x, o.y + d.y * tc - c.y, o.z + d.z * tc - c.z);
+    const bool hit = dot(q, q) * c.w < 1.0f + 1e-3f;
+    jb = 0x7fffffff;
+    je = -1;
+    if (ranges && hit) {
+        const V3 e = v3(o.x + d.x * b - c.x, o.y + d.y * b - c.y, o.z + d.z * b - c.z);
+        const float disc = ((1.0f + 1e-3f) / c.w - dot(e, e)) / dd;
+        if (disc > 0.f) {
+            const float w = sqrtf(disc);
+            jb = max((int)floorf((b - w - S.t0) * inv_h - 0.5f) - 2, 0);
+            je = min((int)ceilf((b + w - S.t0) * inv_h - 0.5f) + 2, S.n);
+        }
     }
-    return __ballot_sync(0xffffffffu, hit);
+    return hit;
+}
+
+// What the walk of one job tests: the support spheres its ray can enter
+// (smask, hash fields with 1..32 spheres) and the interval indices [cb, ce)
+// that cover every range of theirs; the walk starts at cb and stops at ce.
+// Other fields: every interval, no sphere mask.  A hash field without support
+// spheres has no density: an empty cover.
+struct Cover {
+    uint32_t smask;
+    int cb, ce;
+};
+__device__ __forceinline__ bool cover_jumps(const FieldDev &F) {
+    return F.kind == MRF_FIELD_HASHGRID && F.n_support > 0 && F.n_support <= 32;
+}
+
+// The cover computed by one thread (loop over the spheres).
+__device__ __forceinline__ Cover job_cover(const FieldDev &F, const WalkCtx &X, V3 o, V3 d, const Segment &S) {
+    Cover cv{0u, 0, S.n};
+    if (F.kind == MRF_FIELD_HASHGRID && F.n_support == 0) cv.ce = 0;
+    if (!cover_jumps(F)) return cv;
+    const float inv_h = 1.0f / S.h;
+    cv.cb = 0x7fffffff;
+    cv.ce = -1;
+    for (int k = 0; k < F.n_support; ++k) {
+        int jb, je;
+        if (sphere_range(X.support[k], o, d, S, inv_h, true, jb, je)) cv.smask |= 1u << k;
+        cv.cb = min(cv.cb, jb);
+        cv.ce = max(cv.ce, je);
+    }
+    return cv;
+}
+
+// The same cover computed by a warp (lane k takes sphere k); equal to job_cover's.
+__device__ __forceinline__ Cover job_cover_warp(const FieldDev &F, const WalkCtx &X, V3 o, V3 d, const Segment &S,
+                                                int lane) {
+    Cover cv{0u, 0, S.n};
+    if (F.kind == MRF_FIELD_HASHGRID && F.n_support == 0) cv.ce = 0;
+    if (!cover_jumps(F)) return cv;
+    int jb = 0x7fffffff, je = -1;
+    bool hit = false;
+    if (lane < F.n_support) hit = sphere_range(X.support[lane], o, d, S, 1.0f / S.h, true, jb, je);
+    cv.smask = __ballot_sync(0xffffffffu, hit);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        jb = min(jb, __shfl_xor_sync(0xffffffffu, jb, off));
+        je = max(je, __shfl_xor_sync(0xffffffffu, je, off));
+    }
+    cv.cb = jb;
+    cv.ce = je;
+    return cv;
 }
 
 __device__ __forceinline__ float support_masked(const float4 *sup, uint32_t mask, V3 p) {
@@ -204,6 +264,16 @@ __device__ __forceinline__ float support_masked(const float4 *sup, uint32_t mask
     return s;
 }
 
+__device__ __forceinline__ float support_all(const float4 *sup, int n, V3 p) {
+    float s = 0.f;
+    for (int k = 0; k < n; ++k) {
+        const float4 c = sup[k];
+        const float dx = p.x - c.x, dy = p.y - c.y, dz = p.z - c.z;
+        s = fmaxf(s, 1.0f - (dx * dx + dy * dy + dz * dz) * c.w);
+    }
+    return s;
+}
+
 constexpr int kRunsPerJob = 8;
 struct RunList {
     int n;                 // runs recorded; kRunsPerJob + 1 = more than fit (write pass walks again)
@@ -211,60 +281,38 @@ struct RunList {
 };
 
 // Warp-cooperative walk over the quadrature intervals of one job (every lane
-// holds the same job): lane l takes interval i0 + l of each 32-interval chunk,
-// tests the density support and the occupancy grid, taking the decisions
-// march() takes, and the warp advances by 32, to the exit of an empty cell
-// that holds the chunk's last interval, or to the next support sphere's range.
-// Returns the number of samples whose density can be non-zero (x) and the
-// job's nominal interval count (y); records the samples as runs of consecutive
-// intervals in `runs` (lane 0 writes; may be nullptr) and, if `out` is
-// non-NULL, writes them in order, never more than `limit`.  One compiled copy
-// (noinline) serves the counting and the writing walk, so both take
-// bit-identical decisions; the counts come back in registers (a reference
+// holds the same job; o and d in the field's frame, S its intervals, cv its
+// cover): from the cover's first interval, lane l takes interval i0 + l of
+// each 32-interval chunk, tests the density support and the occupancy grid,
+// taking the decisions march() takes, and the warp advances by 32 or to the
+// exit of an empty cell that holds the chunk's last interval, until the end of
+// the cover.  Returns the number of samples whose density can be non-zero (x)
+// and the job's nominal interval count (y); records the samples as runs of
+// consecutive intervals in `runs` (lane 0 writes; may be nullptr) and, if
+// `out` is non-NULL, writes them in order, never more than `limit`.  One
+// compiled copy (noinline) serves the counting and the writing walk, so both
+// take bit-identical decisions; the counts come back in registers (a reference
 // argument would put the caller's counters in local memory).
-__device__ __noinline__ uint2 warp_walk(const RenderParams &P, const WalkCtx &X, V3 o, V3 d, float a, float b,
-                                        float4 *out, uint32_t limit, int lane, RunList *runs) {
-    Segment S;
+__device__ __noinline__ uint2 warp_walk_in(const RenderParams &P, const WalkCtx &X, V3 o, V3 d, const Segment S,
+                                           const Cover cv, float4 *out, uint32_t limit, int lane, RunList *runs) {
     if (runs && lane == 0) runs->n = 0;
-    to_field_frame(P.F, o, d);
-    if (!segment_of(P, o, d, a, b, S)) return make_uint2(0u, 0u);
     const FieldDev &F = P.F;
-    const V3 inv = v3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
     const bool hash = F.kind == MRF_FIELD_HASHGRID;
+    const bool jump = cover_jumps(F);
     const bool use_occ0 = hash && F.occ != nullptr;
-    const bool use_coarse = use_occ0 && X.coarse != nullptr;
+    // With the sphere cover the support test (arithmetic only) goes first and
+    // the coarse grid is left out: the fine grid alone takes the same decisions,
+    // and the coarse one only sped up skipping, which the cover now does.  When
+    // the grid covers the support it can no longer reject anything either.
+    const bool use_coarse = use_occ0 && X.coarse != nullptr && !jump;
+    const bool use_occ = use_occ0 && !(jump && F.occ_covers_support);
     const int Rc = F.occ_coarse_res;
     const float inv_h = 1.0f / S.h;
-    const uint32_t smask = hash ? job_spheres(F, X, o, d, S.t0, S.t1, lane) : 0u;
-    // Interval-index range of this lane's support sphere along the job: only
-    // samples inside some sphere can have non-zero density, so the walk jumps
-    // over the gaps between the ranges (conservative by two intervals).
-    const bool jump = hash && F.n_support > 0 && F.n_support <= 32;
-    // with range jumps the support test comes first; when the grid covers the
-    // support it can no longer reject anything, and is left out
-    const bool use_occ = use_occ0 && !(jump && F.occ_covers_support);
-    int jb = 0x7fffffff, je = -1;
-    if (jump && ((smask >> lane) & 1u)) {
-        const float4 c = X.support[lane];
-        const V3 oc = v3(c.x - o.x, c.y - o.y, c.z - o.z);
-        const float dd = dot(d, d), tcl = dot(oc, d) / dd;
-        const V3 q = v3(o.x + d.x * tcl - c.x, o.y + d.y * tcl - c.y, o.z + d.z * tcl - c.z);
-        const float disc = ((1.0f + 1e-3f) / c.w - dot(q, q)) / dd;
-        if (disc > 0.f) {
-            const float w = sqrtf(disc);
-            jb = max((int)floorf((tcl - w - S.t0) * inv_h - 0.5f) - 2, 0);
-            je = min((int)ceilf((tcl + w - S.t0) * inv_h - 0.5f) + 2, S.n);
-        }
-    }
-    auto next_start = [&](int from) {
-        int v = je > from ? max(jb, from) : 0x7fffffff;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, off));
-        return v;
-    };
+    V3 inv = v3(0.f, 0.f, 0.f);
+    if (use_coarse || use_occ) inv = v3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
     int nrun = 0, run_end = -1;
     uint32_t k = 0;
-    for (int i0 = jump ? next_start(0) : 0; i0 < S.n;) {
+    for (int i0 = cv.cb; i0 < cv.ce;) {
         const int i = i0 + lane;
         bool emit = false;
         int skip_to = i + 1;
@@ -274,12 +322,8 @@ __device__ __noinline__ uint2 warp_walk(const RenderParams &P, const WalkCtx &X,
             const float hi = P.steps ? fmaf((float)(i + 1), S.h, S.t0) : fminf(lo + S.h, S.t1);
             const float tm = 0.5f * (lo + hi), delta = hi - lo;
             const V3 p = fma3(d, tm, o);
-            // With the range jumps the support test (arithmetic only) goes first
-            // and the coarse grid is left out: the fine grid alone takes the same
-            // decisions, and the coarse one only sped up skipping, which the
-            // jumps between sphere ranges now do.
-            bool empty = jump && !(support_masked(X.support, smask, p) > 0.f);
-            if (!empty && use_coarse && !jump) {
+            bool empty = jump && !(support_masked(X.support, cv.smask, p) > 0.f);
+            if (!empty && use_coarse) {
                 int c[3];
 #pragma unroll
                 for (int q = 0; q < 3; ++q)
@@ -299,7 +343,7 @@ __device__ __noinline__ uint2 warp_walk(const RenderParams &P, const WalkCtx &X,
                     empty = true;
                 }
             }
-            if (!empty) emit = !hash || jump || support_masked(X.support, smask, p) > 0.f;
+            if (!empty) emit = !hash || jump || support_all(X.support, F.n_support, p) > 0.f;
             rec = make_float4(p.x, p.y, p.z, delta);
         } else {
             skip_to = S.n;
@@ -331,20 +375,29 @@ __device__ __noinline__ uint2 warp_walk(const RenderParams &P, const WalkCtx &X,
         }
         const int last_skip = __shfl_sync(0xffffffffu, skip_to, 31);
         i0 = max(i0 + 32, last_skip);
-        if (jump) i0 = next_start(i0);
     }
     if (runs && lane == 0) runs->n = nrun;
     return make_uint2(k, (uint32_t)S.n);
 }
 
-// Writes samples [first, first + limit) of a job from its recorded runs into
-// out[0, limit) (lane-parallel over the run's intervals, positions by the same
-// FP32 formulas as the walk).
-__device__ void write_runs(const RenderParams &P, V3 o, V3 d, float a, float b, const RunList &R, float4 *out,
-                           uint32_t limit, int lane, uint32_t first = 0) {
+// The same walk for a world-space job on [a, b].
+__device__ __forceinline__ uint2 warp_walk(const RenderParams &P, const WalkCtx &X, V3 o, V3 d, float a, float b,
+                                           float4 *out, uint32_t limit, int lane, RunList *runs) {
     Segment S;
     to_field_frame(P.F, o, d);
-    if (!segment_of(P, o, d, a, b, S)) return;
+    if (!segment_of(P, o, d, a, b, S)) {
+        if (runs && lane == 0) runs->n = 0;
+        return make_uint2(0u, 0u);
+    }
+    return warp_walk_in(P, X, o, d, S, job_cover_warp(P.F, X, o, d, S, lane), out, limit, lane, runs);
+}
+
+// Writes samples [first, first + limit) of a job from its recorded runs into
+// out[0, limit) (lane-parallel over the run's intervals, positions by the same
+// FP32 formulas as the walk); o and d in the field's frame, S the job's
+// intervals.
+__device__ void write_runs_in(const RenderParams &P, V3 o, V3 d, const Segment &S, const RunList &R, float4 *out,
+                              uint32_t limit, int lane, uint32_t first = 0) {
     uint32_t k = 0;
     for (int r = 0; r < R.n; ++r) {
         const int2 run = R.r[r];
@@ -363,6 +416,15 @@ __device__ void write_runs(const RenderParams &P, V3 o, V3 d, float a, float b, 
         k += len;
         if (k >= first + limit) break;
     }
+}
+
+// The same for a world-space job on [a, b].
+__device__ __forceinline__ void write_runs(const RenderParams &P, V3 o, V3 d, float a, float b, const RunList &R,
+                                           float4 *out, uint32_t limit, int lane, uint32_t first = 0) {
+    Segment S;
+    to_field_frame(P.F, o, d);
+    if (!segment_of(P, o, d, a, b, S)) return;
+    write_runs_in(P, o, d, S, R, out, limit, lane, first);
 }
 
 __device__ __forceinline__ V3 shfl3(V3 v, int src) {
@@ -555,9 +617,19 @@ __global__ void __launch_bounds__(128) wf_shadow_net(const WfParams W) {
 // ranges with one atomic per warp, and writes them in order.
 // Round r > 0 regenerates only the slots that round r - 1 left pending (their
 // samples did not fit the buffer), into the emptied buffer.
+// The per-job set-up of the segment jobs (the ray in the field's frame and its
+// quadrature intervals, with their divisions) runs lane-parallel, each lane for
+// its own slot, before the warp walks the jobs one after another.
+struct JobSm {
+    float o[3], d[3];
+    Segment S;   // S.n = 0: no interval
+    Cover cv;
+};
+
 __global__ void __launch_bounds__(kThreads, 6) wf_gen(const WfParams W, uint32_t j, int cur, int round) {
     __shared__ WalkSmem wsm;
     __shared__ RunList runs_sm[kThreads / 32][32][2];   // per warp, per slot: segment job, first shadow job
+    __shared__ JobSm jobs_sm[kThreads / 32][32];
     const RenderParams &P = W.R;
     if (tail_taken(W) || (round > 0 && *pending_ctr(W, round - 1) == 0)) return;   // nothing to do: the grid leaves
     const WalkCtx X = stage_walk(P.F, wsm);
@@ -565,30 +637,46 @@ __global__ void __launch_bounds__(kThreads, 6) wf_gen(const WfParams W, uint32_t
     const uint32_t live = j == 1 ? W.paths : W.ctr[cur];
     const int S = chunk_slots(live);
     const int K = P.n_shadow;
+    JobSm(&jobs)[32] = jobs_sm[threadIdx.x >> 5];
     Counters C = {};
     for (uint32_t wbase; (wbase = next_chunk(work_ctr(W, round, 0), S, lane)) < live;) {
         const uint32_t tid = wbase + (uint32_t)lane;   // this lane's slot (lane < S)
         const bool active = lane < S && tid < live && (round == 0 || W.rcount[tid] == kOverflow);
-        V3 o = v3(0.f, 0.f, 0.f), d = v3(0.f, 0.f, 1.f), hp = v3(0.f, 0.f, 0.f);
-        float th = 0.f;
+        V3 hp = v3(0.f, 0.f, 0.f);
         uint32_t vis = 0;   // unblocked shadow rays of the slot
         if (active) {
             const float4 qo = W.qo[cur][tid], qd = W.qd[cur][tid], h4 = W.hp[tid];
-            o = v3(qo.x, qo.y, qo.z);
-            d = v3(qd.x, qd.y, qd.z);
-            th = W.hit_t[tid];
+            V3 o = v3(qo.x, qo.y, qo.z), d = v3(qd.x, qd.y, qd.z);
             hp = v3(h4.x, h4.y, h4.z);
             vis = __float_as_uint(h4.w);
+            to_field_frame(P.F, o, d);
+            Segment sg;
+            JobSm &J = jobs[lane];
+            if (segment_of(P, o, d, 0.f, W.hit_t[tid], sg)) {
+                J.cv = job_cover(P.F, X, o, d, sg);
+            } else {
+                sg.n = 0;
+                J.cv = Cover{0u, 0, 0};
+            }
+            J.o[0] = o.x, J.o[1] = o.y, J.o[2] = o.z;
+            J.d[0] = d.x, J.d[1] = d.y, J.d[2] = d.z;
+            J.S = sg;
         }
+        __syncwarp();
         uint32_t my_nr = 0, my_total = 0;
         for (int src = 0; src < S; ++src) {
             if (!__shfl_sync(0xffffffffu, (int)active, src)) continue;
-            const V3 so = shfl3(o, src), sd = shfl3(d, src), sp = shfl3(hp, src);
-            const float st = __shfl_sync(0xffffffffu, th, src);
+            const V3 sp = shfl3(hp, src);
             const uint32_t svis = __shfl_sync(0xffffffffu, vis, src);
             const uint32_t src_tid = wbase + src;
             RunList(&rl)[2] = runs_sm[threadIdx.x >> 5][src];
-            const uint2 wr = warp_walk(P, X, so, sd, 0.f, st, nullptr, 0, lane, &rl[0]);
+            const JobSm &J = jobs[src];
+            uint2 wr = make_uint2(0u, 0u);
+            if (J.S.n > 0)
+                wr = warp_walk_in(P, X, v3(J.o[0], J.o[1], J.o[2]), v3(J.d[0], J.d[1], J.d[2]), J.S, J.cv, nullptr, 0,
+                                  lane, &rl[0]);
+            else if (lane == 0)
+                rl[0].n = 0;
             const uint32_t n_r = wr.x;
             if (lane == 0) C.nominal += wr.y;
             uint32_t n_s = 0;
@@ -631,20 +719,20 @@ __global__ void __launch_bounds__(kThreads, 6) wf_gen(const WfParams W, uint32_t
                 }
                 continue;
             }
-            const V3 so = shfl3(o, src), sd = shfl3(d, src), sp = shfl3(hp, src);
-            const float st = __shfl_sync(0xffffffffu, th, src);
+            const V3 sp = shfl3(hp, src);
             uint32_t k = sbase;
             const uint32_t nr = __shfl_sync(0xffffffffu, my_nr, src);
             const RunList(&rl)[2] = runs_sm[threadIdx.x >> 5][src];
-            if (rl[0].n <= kRunsPerJob)
-                write_runs(P, so, sd, 0.f, st, rl[0], W.samp + k, nr, lane);
-            else
-                warp_walk(P, X, so, sd, 0.f, st, W.samp + k, nr, lane, nullptr);
-            if (P.F.view_dep) {   // the colour network needs each radiance sample's view direction
-                V3 ol = so, dl = sd;
-                to_field_frame(P.F, ol, dl);
-                for (uint32_t i = lane; i < nr; i += 32) W.sview[k + i] = make_float4(dl.x, dl.y, dl.z, 0.f);
+            const JobSm &J = jobs[src];
+            const V3 jo = v3(J.o[0], J.o[1], J.o[2]), jd = v3(J.d[0], J.d[1], J.d[2]);
+            if (nr > 0) {
+                if (rl[0].n <= kRunsPerJob)
+                    write_runs_in(P, jo, jd, J.S, rl[0], W.samp + k, nr, lane);
+                else
+                    warp_walk_in(P, X, jo, jd, J.S, J.cv, W.samp + k, nr, lane, nullptr);
             }
+            if (P.F.view_dep)   // the colour network needs each radiance sample's view direction (field frame)
+                for (uint32_t i = lane; i < nr; i += 32) W.sview[k + i] = make_float4(jd.x, jd.y, jd.z, 0.f);
             k += nr;
             if (lane == src) W.rstart[tid] = sbase;
             bool first = true;
@@ -662,7 +750,7 @@ __global__ void __launch_bounds__(kThreads, 6) wf_gen(const WfParams W, uint32_t
                 k += ns;
             }
         }
-        __syncwarp();   // runs_sm is rewritten by the next chunk
+        __syncwarp();   // runs_sm and jobs_sm are rewritten by the next chunk
     }
     if (round > 0) C.evaluated = C.shadow_eval = 0, C.nominal = 0;   // counted by round 0
     flush_counters(P.stats, C);

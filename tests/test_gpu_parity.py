@@ -791,3 +791,49 @@ def test_field_operands_in_tensor_memory_give_the_same_image(M, torch_cuda, prec
     assert torch.equal(a, b)
     assert st_a["samples_evaluated"] == st_b["samples_evaluated"]
     r.close()
+
+
+@pytest.mark.parametrize("n_support", [0, 40, 70])
+def test_support_sphere_counts(M, orc, torch_cuda, n_support):
+    """Hash fields without a support sphere (support(p) is a max over an empty
+    set, so no density anywhere), with more spheres than a warp has lanes (the
+    sample walk then tests every sphere at every interval) and with more than
+    the shared-memory copy holds: both FP32 engines match the oracle element by
+    element, the BF16 wavefront reaches >= 45 dB, and the field queries return
+    zero density wherever the support is zero."""
+    torch = torch_cuda
+    sc = S.config2(48, 48)
+    sc.field = S.hash_field(2, n_support=n_support, support_r=(0.05, 0.12))
+    ref = orc.render(sc)
+    for engine in (M.MRF_ENGINE_MEGAKERNEL, M.MRF_ENGINE_WAVEFRONT):
+        gpu = _render(M, sc, engine=engine)
+        _compare(gpu, ref)
+        if n_support == 0:
+            assert gpu["stats"]["samples_evaluated"] == 0
+        else:
+            assert gpu["stats"]["samples_evaluated"] > 0
+    low = _render_prec(M, sc, "bf16")
+    ok = ref["flags"] == 0
+    assert np.array_equal(low["segments"][ok], ref["segments"][ok])
+    diff = np.abs(low["rgba"][ok, :3] - ref["rgba"][ok, :3])
+    assert diff.max() <= 1e-2
+    if diff.max() > 0:
+        assert _psnr(low["rgba"], ref["rgba"], ok) >= 45.0
+    # field queries: points spread over the whole box
+    rng = np.random.default_rng(5)
+    pts = rng.uniform(-0.5, 0.5, (4096, 3)).astype(np.float32)
+    osc = orc.OracleScene(sc)
+    ref_sig = np.array([orc.field_eval(osc, p)[0] for p in pts.astype(np.float64)])
+    ctx = M.mrf_context_create(0)
+    for prec in (M.MRF_PREC_FP32, M.MRF_PREC_BF16):
+        desc, keep = M.field_desc(sc.field, prec)
+        fh = M.mrf_field_create(ctx, desc)
+        dp = torch.from_numpy(pts).cuda()
+        out = torch.full((len(pts), 4), float("nan"), dtype=torch.float32, device="cuda")
+        M.mrf_field_query(ctx, fh, dp.data_ptr(), len(pts), out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        sig = out.cpu().numpy()[:, 0]
+        M.mrf_field_destroy(fh)
+        assert np.all(np.isfinite(sig))
+        assert np.all(sig[ref_sig == 0] == 0)
+        assert np.all(sig[ref_sig > 0] > 0) or prec != M.MRF_PREC_FP32
+    M.mrf_context_destroy(ctx)
