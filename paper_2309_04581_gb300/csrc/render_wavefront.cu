@@ -16,6 +16,7 @@
 // sample buffer are marched in place by wf_shade on the CUDA cores.
 #include <algorithm>
 
+#include <atomic>
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
@@ -927,41 +928,43 @@ __global__ void __launch_bounds__(kThreads) wf_mask(const WfParams W, int cur, i
 // wf_composite (comp, sdepth).  Nothing to do when no job overflowed.
 __global__ void __launch_bounds__(kThreads) wf_overflow(const WfParams W, int cur, int last_round) {
     const RenderParams &P = W.R;
-    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     // nothing left pending after the last generation round: the whole grid leaves
-    if (tail_taken(W) || *pending_ctr(W, last_round) == 0 || tid >= W.ctr[cur]) return;
+    if (tail_taken(W) || *pending_ctr(W, last_round) == 0) return;
+    const uint32_t live = W.ctr[cur];
     const int K = P.n_shadow;
-    const bool rad = W.rcount[tid] == kOverflow;
-    const float4 h4 = W.hp[tid];
-    bool any_shadow = false;
-    if (__float_as_uint(h4.w) != 0u)   // unblocked shadow rays (only their counts are current)
-        for (int q = 0; q < K; ++q)
-            any_shadow |= W.sw[(size_t)tid * K + q].w == 1.f && W.scount[(size_t)tid * K + q] == kOverflow;
-    if (!rad && !any_shadow) return;
-    const float4 qo = W.qo[cur][tid], qd = W.qd[cur][tid], qT = W.qT[cur][tid];
-    const V3 o = v3(qo.x, qo.y, qo.z), d = v3(qd.x, qd.y, qd.z);
-    if (rad) {
-        // march with the path's own throughput so that the tau test is the same
-        float T[3] = {qT.x, qT.y, qT.z}, L[3] = {0.f, 0.f, 0.f};
-        bool stop = false;
-        Counters dummy = {};
-        march<true>(P, P.F.mlp, o, d, 0.f, W.hit_t[tid], T, L, stop, dummy);
-        const int c = (qT.x >= qT.y && qT.x >= qT.z) ? 0 : (qT.y >= qT.z ? 1 : 2);
-        const float T0[3] = {qT.x, qT.y, qT.z};
-        const float dep = T0[c] > 0.f ? logf(T0[c] / fmaxf(T[c], 1e-38f)) : 0.f;
-        W.comp[tid] = make_float4(T0[0] > 0.f ? L[0] / T0[0] : 0.f, T0[1] > 0.f ? L[1] / T0[1] : 0.f,
-                                  T0[2] > 0.f ? L[2] / T0[2] : 0.f, stop ? -dep - 1.f : dep);
-    }
-    if (any_shadow) {
-        const V3 hp = v3(h4.x, h4.y, h4.z);
-        for (int q = 0; q < K; ++q) {
-            const size_t idx = (size_t)tid * K + q;
-            if (W.sw[idx].w != 1.f || W.scount[idx] != kOverflow) continue;
-            const float4 sh = W.sdir[idx];
+    for (uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x; tid < live; tid += gridDim.x * blockDim.x) {
+        const bool rad = W.rcount[tid] == kOverflow;
+        const float4 h4 = W.hp[tid];
+        bool any_shadow = false;
+        if (__float_as_uint(h4.w) != 0u)   // unblocked shadow rays (only their counts are current)
+            for (int q = 0; q < K; ++q)
+                any_shadow |= W.sw[(size_t)tid * K + q].w == 1.f && W.scount[(size_t)tid * K + q] == kOverflow;
+        if (!rad && !any_shadow) continue;
+        const float4 qo = W.qo[cur][tid], qd = W.qd[cur][tid], qT = W.qT[cur][tid];
+        const V3 o = v3(qo.x, qo.y, qo.z), d = v3(qd.x, qd.y, qd.z);
+        if (rad) {
+            // march with the path's own throughput so that the tau test is the same
+            float T[3] = {qT.x, qT.y, qT.z}, L[3] = {0.f, 0.f, 0.f};
+            bool stop = false;
             Counters dummy = {};
-            bool dstop = false;
-            W.sdepth[idx] = march<false>(P, P.F.mlp, hp, v3(sh.x, sh.y, sh.z), 0.f, sh.w, nullptr, nullptr, dstop,
-                                         dummy);
+            march<true>(P, P.F.mlp, o, d, 0.f, W.hit_t[tid], T, L, stop, dummy);
+            const int c = (qT.x >= qT.y && qT.x >= qT.z) ? 0 : (qT.y >= qT.z ? 1 : 2);
+            const float T0[3] = {qT.x, qT.y, qT.z};
+            const float dep = T0[c] > 0.f ? logf(T0[c] / fmaxf(T[c], 1e-38f)) : 0.f;
+            W.comp[tid] = make_float4(T0[0] > 0.f ? L[0] / T0[0] : 0.f, T0[1] > 0.f ? L[1] / T0[1] : 0.f,
+                                      T0[2] > 0.f ? L[2] / T0[2] : 0.f, stop ? -dep - 1.f : dep);
+        }
+        if (any_shadow) {
+            const V3 hp = v3(h4.x, h4.y, h4.z);
+            for (int q = 0; q < K; ++q) {
+                const size_t idx = (size_t)tid * K + q;
+                if (W.sw[idx].w != 1.f || W.scount[idx] != kOverflow) continue;
+                const float4 sh = W.sdir[idx];
+                Counters dummy = {};
+                bool dstop = false;
+                W.sdepth[idx] = march<false>(P, P.F.mlp, hp, v3(sh.x, sh.y, sh.z), 0.f, sh.w, nullptr, nullptr, dstop,
+                                             dummy);
+            }
         }
     }
 }
@@ -971,104 +974,106 @@ __global__ void __launch_bounds__(kThreads) wf_overflow(const WfParams W, int cu
 __global__ void __launch_bounds__(kThreads) wf_shade(const WfParams W, uint32_t j, int cur, int nxt) {
     const RenderParams &P = W.R;
     if (tail_taken(W)) return;
-    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t live = W.ctr[cur];
     const int K = P.n_shadow;
     Counters C = {};
-    bool push = false;
-    uint32_t path = 0, prev = kNoHit;
-    V3 o = v3(0.f, 0.f, 0.f), d = v3(0.f, 0.f, 1.f);
-    float T[3] = {1.f, 1.f, 1.f};
-    if (tid < live) {
-        path = W.qpath[cur][tid];
-        const uint32_t ray = path / P.spp, s = path % P.spp;
-        const float4 qo = W.qo[cur][tid], qd = W.qd[cur][tid], qT = W.qT[cur][tid];
-        o = v3(qo.x, qo.y, qo.z);
-        d = v3(qd.x, qd.y, qd.z);
-        T[0] = qT.x;
-        T[1] = qT.y;
-        T[2] = qT.z;
-        Hit h;
-        h.t = W.hit_t[tid];
-        h.slot = W.hit_slot[tid];
-        h.id = W.hit_id[tid];
-        float4 acc = j == 1 ? make_float4(0.f, 0.f, 0.f, 0.f) : W.acc[path];
-        float L[3] = {acc.x, acc.y, acc.z};
-        const float T0 = T[0];
-        bool stop = false;
-        {
-            // L += T(p_j) * sum_i T_i alpha_i r_i, T' = T(p_j) exp(-depth)
-            const float4 cp = W.comp[tid];
-            stop = cp.w < 0.f;
-            const float att = expf(-(stop ? -cp.w - 1.f : cp.w));
-            L[0] = fmaf(T[0], cp.x, L[0]);
-            L[1] = fmaf(T[1], cp.y, L[1]);
-            L[2] = fmaf(T[2], cp.z, L[2]);
-            T[0] *= att;
-            T[1] *= att;
-            T[2] *= att;
-        }
-        if (j == 1) acc.w = T0 > 0.f ? 1.f - T[0] / T0 : 0.f;
-        ++C.seg;
-        const uint64_t rbase = (uint64_t)path * P.max_bounces;
-        if (P.rec_tri) {
-            P.rec_tri[rbase + (j - 1)] = h.id;
-            P.rec_t[rbase + (j - 1)] = h.t;
-        }
-        bool end = stop || h.id == kNoHit;
-        int cause = stop ? 2 : (h.id == kNoHit ? 1 : 0);   // 1 left the scene, 2 throughput below tau, 3 bounce cap
-        if (!end) {
-            ++C.hits;
-            const SurfaceHit S = surface_at(P, o, d, h);
-            float u[3];
-            surface_uniforms(P, ray, s, j, u);
-            if (S.mat.kind == MRF_MAT_DIFFUSE && __float_as_uint(W.hp[tid].w) != 0u) {
-                for (int q = 0; q < K; ++q) {
-                    const size_t idx = (size_t)tid * K + q;
-                    const float4 wgt = W.sw[idx];
-                    if (wgt.w == 0.f) continue;
-                    const float Tf = wgt.w == 2.f ? W.sdepth[idx] : expf(-W.sdepth[idx]);
-                    L[0] = fmaf(T[0] * Tf, wgt.x, L[0]);
-                    L[1] = fmaf(T[1] * Tf, wgt.y, L[1]);
-                    L[2] = fmaf(T[2] * Tf, wgt.z, L[2]);
+    for (uint32_t base = blockIdx.x * blockDim.x; base < live; base += gridDim.x * blockDim.x) {
+        const uint32_t tid = base + threadIdx.x;
+        bool push = false;
+        uint32_t path = 0, prev = kNoHit;
+        V3 o = v3(0.f, 0.f, 0.f), d = v3(0.f, 0.f, 1.f);
+        float T[3] = {1.f, 1.f, 1.f};
+        if (tid < live) {
+            path = W.qpath[cur][tid];
+            const uint32_t ray = path / P.spp, s = path % P.spp;
+            const float4 qo = W.qo[cur][tid], qd = W.qd[cur][tid], qT = W.qT[cur][tid];
+            o = v3(qo.x, qo.y, qo.z);
+            d = v3(qd.x, qd.y, qd.z);
+            T[0] = qT.x;
+            T[1] = qT.y;
+            T[2] = qT.z;
+            Hit h;
+            h.t = W.hit_t[tid];
+            h.slot = W.hit_slot[tid];
+            h.id = W.hit_id[tid];
+            float4 acc = j == 1 ? make_float4(0.f, 0.f, 0.f, 0.f) : W.acc[path];
+            float L[3] = {acc.x, acc.y, acc.z};
+            const float T0 = T[0];
+            bool stop = false;
+            {
+                // L += T(p_j) * sum_i T_i alpha_i r_i, T' = T(p_j) exp(-depth)
+                const float4 cp = W.comp[tid];
+                stop = cp.w < 0.f;
+                const float att = expf(-(stop ? -cp.w - 1.f : cp.w));
+                L[0] = fmaf(T[0], cp.x, L[0]);
+                L[1] = fmaf(T[1], cp.y, L[1]);
+                L[2] = fmaf(T[2], cp.z, L[2]);
+                T[0] *= att;
+                T[1] *= att;
+                T[2] *= att;
+            }
+            if (j == 1) acc.w = T0 > 0.f ? 1.f - T[0] / T0 : 0.f;
+            ++C.seg;
+            const uint64_t rbase = (uint64_t)path * P.max_bounces;
+            if (P.rec_tri) {
+                P.rec_tri[rbase + (j - 1)] = h.id;
+                P.rec_t[rbase + (j - 1)] = h.t;
+            }
+            bool end = stop || h.id == kNoHit;
+            int cause = stop ? 2 : (h.id == kNoHit ? 1 : 0);   // 1 left the scene, 2 throughput below tau, 3 bounce cap
+            if (!end) {
+                ++C.hits;
+                const SurfaceHit S = surface_at(P, o, d, h);
+                float u[3];
+                surface_uniforms(P, ray, s, j, u);
+                if (S.mat.kind == MRF_MAT_DIFFUSE && __float_as_uint(W.hp[tid].w) != 0u) {
+                    for (int q = 0; q < K; ++q) {
+                        const size_t idx = (size_t)tid * K + q;
+                        const float4 wgt = W.sw[idx];
+                        if (wgt.w == 0.f) continue;
+                        const float Tf = wgt.w == 2.f ? W.sdepth[idx] : expf(-W.sdepth[idx]);
+                        L[0] = fmaf(T[0] * Tf, wgt.x, L[0]);
+                        L[1] = fmaf(T[1] * Tf, wgt.y, L[1]);
+                        L[2] = fmaf(T[2] * Tf, wgt.z, L[2]);
+                    }
+                }
+                const V3 nd = bsdf_sample(S, d, u, T);
+                d = normalize(nd);
+                o = S.p;
+                prev = S.id;
+                if (P.tau > 0.f && fmaxf(T[0], fmaxf(T[1], T[2])) < P.tau) {
+                    end = true;
+                    cause = 2;
+                } else if (j == P.max_bounces) {
+                    end = true;
+                    cause = 3;
                 }
             }
-            const V3 nd = bsdf_sample(S, d, u, T);
-            d = normalize(nd);
-            o = S.p;
-            prev = S.id;
-            if (P.tau > 0.f && fmaxf(T[0], fmaxf(T[1], T[2])) < P.tau) {
-                end = true;
-                cause = 2;
-            } else if (j == P.max_bounces) {
-                end = true;
-                cause = 3;
+            acc.x = L[0];
+            acc.y = L[1];
+            acc.z = L[2];
+            W.acc[path] = acc;
+            if (end) {
+                C.end_miss += cause == 1;
+                C.end_tau += cause == 2;
+                C.end_cap += cause == 3;
+                if (P.rec_seg) P.rec_seg[path] = j;
+                if (P.rec_tri)
+                    for (uint32_t q = j; q < P.max_bounces; ++q) {
+                        P.rec_tri[rbase + q] = kNoHit;
+                        P.rec_t[rbase + q] = INFINITY;
+                    }
             }
+            push = !end;
         }
-        acc.x = L[0];
-        acc.y = L[1];
-        acc.z = L[2];
-        W.acc[path] = acc;
-        if (end) {
-            C.end_miss += cause == 1;
-            C.end_tau += cause == 2;
-            C.end_cap += cause == 3;
-            if (P.rec_seg) P.rec_seg[path] = j;
-            if (P.rec_tri)
-                for (uint32_t q = j; q < P.max_bounces; ++q) {
-                    P.rec_tri[rbase + q] = kNoHit;
-                    P.rec_t[rbase + q] = INFINITY;
-                }
+        uint32_t slot = warp_alloc(&W.ctr[nxt], push ? 1u : 0u);
+        if (push) {
+            slot = checked_index(slot, W.paths, P.status);
+            W.qpath[nxt][slot] = path;
+            W.qo[nxt][slot] = make_float4(o.x, o.y, o.z, __uint_as_float(prev));
+            W.qd[nxt][slot] = make_float4(d.x, d.y, d.z, 0.f);
+            W.qT[nxt][slot] = make_float4(T[0], T[1], T[2], 0.f);
         }
-        push = !end;
-    }
-    uint32_t slot = warp_alloc(&W.ctr[nxt], push ? 1u : 0u);
-    if (push) {
-        slot = checked_index(slot, W.paths, P.status);
-        W.qpath[nxt][slot] = path;
-        W.qo[nxt][slot] = make_float4(o.x, o.y, o.z, __uint_as_float(prev));
-        W.qd[nxt][slot] = make_float4(d.x, d.y, d.z, 0.f);
-        W.qT[nxt][slot] = make_float4(T[0], T[1], T[2], 0.f);
     }
     flush_counters(P.stats, C);
 }
@@ -1440,10 +1445,39 @@ Layout layout(uint32_t paths, int n_shadow, uint32_t cap_per_path = 96, bool vie
     return L;
 }
 
+// Blocks of `kernel` resident on one SM at kThreads threads (queried once).
+template <typename Kern>
+unsigned resident_blocks(Kern kernel, std::atomic<int> &cache) {
+    int b = cache.load(std::memory_order_relaxed);
+    if (b == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kThreads, 0) != cudaSuccess || b < 1) b = 1;
+        cache.store(b, std::memory_order_relaxed);
+    }
+    return (unsigned)b;
+}
+
+// Grids of the per-segment kernels.  The slot kernels loop over the live slots
+// (grid-stride) and the warp-cooperative ones take chunks of slots from work
+// counters, so they need no more blocks than are resident at once (four waves
+// for the slot kernels).  A grid sized for every path launched tens of
+// thousands of blocks in the late segments, where few paths are left, and each
+// of them only found that it had no work.  wf_cast keeps one thread per path
+// and a block per 128 paths: its rays differ most in cost, and a grid-stride
+// loop (more registers spilled around the traversal) took 1.03 ms per
+// 1920x1080 frame with one resident wave and 0.97 with four, against 0.87.
+constexpr unsigned kSlotWaves = 4;
+
 // Every launch of one frame, in stream order, with no host synchronisation.
 cudaError_t enqueue_frame(const WfParams &W, const RenderParams &P, uint32_t paths, cudaStream_t s,
                           KernelTimer *timer) {
     const unsigned grid = (paths + kThreads - 1) / kThreads;
+    static std::atomic<int> occ[5] = {{0}, {0}, {0}, {0}, {0}};   // resident blocks per SM, queried once
+    const unsigned g_cast = grid;
+    const unsigned g_shade = std::min(grid, kSlotWaves * 152u * resident_blocks(wf_shade, occ[0]));
+    const unsigned g_over = std::min(grid, kSlotWaves * 152u * resident_blocks(wf_overflow, occ[1]));
+    const unsigned g_gen = std::min(grid, 152u * resident_blocks(wf_gen, occ[2]));
+    const unsigned g_mask = std::min(grid, 152u * resident_blocks(wf_mask, occ[3]));
+    const unsigned g_comp = std::min(grid, 152u * resident_blocks(wf_composite, occ[4]));
     const FieldDev &F = P.F;
     const bool tc = F.kind == MRF_FIELD_HASHGRID && F.precision != MRF_PREC_FP32;
     const int groups = P.tc_groups == 4 || P.tc_groups == 5 ? P.tc_groups : 8;
@@ -1462,7 +1496,7 @@ cudaError_t enqueue_frame(const WfParams &W, const RenderParams &P, uint32_t pat
         Range seg_range("mrf segment");
         if ((e = cudaMemsetAsync(W.ctr + 2, 0, 4 * (2 + 4 * rounds), s)) != cudaSuccess) return e;
         timer_begin(timer, MRF_KERNEL_CAST_GEN, s);
-        wf_cast<<<grid, kThreads, 0, s>>>(W, j, cur);
+        wf_cast<<<g_cast, kThreads, 0, s>>>(W, j, cur);
         timer_end(timer, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (P.n_shadow > 1) {
@@ -1491,7 +1525,7 @@ cudaError_t enqueue_frame(const WfParams &W, const RenderParams &P, uint32_t pat
         for (int r = 0; r < rounds; ++r) {
             if (r > 0 && (e = cudaMemsetAsync(W.ctr + 2, 0, 4, s)) != cudaSuccess) return e;
             timer_begin(timer, MRF_KERNEL_GEN, s);
-            wf_gen<<<grid, kThreads, 0, s>>>(W, j, cur, r);
+            wf_gen<<<g_gen, kThreads, 0, s>>>(W, j, cur, r);
             timer_end(timer, s);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             timer_begin(timer, MRF_KERNEL_FIELD, s);
@@ -1508,22 +1542,22 @@ cudaError_t enqueue_frame(const WfParams &W, const RenderParams &P, uint32_t pat
             if (e != cudaSuccess) return e;
             if (P.shadow_mask) {
                 timer_begin(timer, MRF_KERNEL_MASK, s);
-                wf_mask<<<grid, kThreads, 0, s>>>(W, cur, r);
+                wf_mask<<<g_mask, kThreads, 0, s>>>(W, cur, r);
                 timer_end(timer, s);
                 if ((e = cudaGetLastError()) != cudaSuccess) return e;
             }
             timer_begin(timer, MRF_KERNEL_COMPOSITE, s);
-            wf_composite<<<grid, kThreads, 0, s>>>(W, cur, r);
+            wf_composite<<<g_comp, kThreads, 0, s>>>(W, cur, r);
             timer_end(timer, s);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
         if ((e = cudaMemsetAsync(W.ctr + nxt, 0, 4, s)) != cudaSuccess) return e;
         timer_begin(timer, MRF_KERNEL_OVERFLOW, s);
-        wf_overflow<<<grid, kThreads, 0, s>>>(W, cur, rounds - 1);
+        wf_overflow<<<g_over, kThreads, 0, s>>>(W, cur, rounds - 1);
         timer_end(timer, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         timer_begin(timer, MRF_KERNEL_SHADE, s);
-        wf_shade<<<grid, kThreads, 0, s>>>(W, j, cur, nxt);
+        wf_shade<<<g_shade, kThreads, 0, s>>>(W, j, cur, nxt);
         timer_end(timer, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
