@@ -627,7 +627,7 @@ struct JobSm {
     Cover cv;
 };
 
-__global__ void __launch_bounds__(kThreads, 6) wf_gen(const WfParams W, uint32_t j, int cur, int round) {
+__global__ void __launch_bounds__(kThreads, 5) wf_gen(const WfParams W, uint32_t j, int cur, int round) {
     __shared__ WalkSmem wsm;
     __shared__ RunList runs_sm[kThreads / 32][32][2];   // per warp, per slot: segment job, first shadow job
     __shared__ JobSm jobs_sm[kThreads / 32][32];
