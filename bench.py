@@ -455,13 +455,13 @@ def run_ours(args):
     cast = None
     if "wf_cast" in kernels:
         c_ms = kernels["wf_cast"]["ms_per_step"]
-        cb_bytes = 64 * st["bvh_nodes"] + 48 * st["bvh_tri_tests"]
+        cb_bytes = 128 * st["bvh_nodes"] + 48 * st["bvh_tri_tests"]
         cast = {"kernel": "wf_cast", "bvh_nodes": st["bvh_nodes"], "tri_tests": st["bvh_tri_tests"],
                 "worst_traversal_nodes": st["bvh_worst_nodes"],
                 "rays": segs + st["shadow_rays"], "algorithmic_bytes": cb_bytes,
                 "achieved_gbs": cb_bytes / (c_ms / 1e3) / 1e9, "l2_frac": cb_bytes / (c_ms / 1e3) / 1e9 / l2["gbs"],
                 "ms_per_step": c_ms,
-                "note": "64 B per node visited + 48 B per triangle tested; the BVH is on-chip (L1/L2) resident, "
+                "note": "128 B per (four-child) node visited + 48 B per triangle tested; the BVH is on-chip (L1/L2) resident, "
                         "so this is not DRAM traffic; l2_frac against the L2 bandwidth measured here"}
     # other frame sizes, render time against pixel count, view-dependent field
     scaling, hd800, vd, img_vd, captured = None, None, None, None, None

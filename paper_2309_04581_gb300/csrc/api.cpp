@@ -85,6 +85,7 @@ struct mrf_bvh {
     mrf_context *ctx = nullptr;
     BvhDev dev{};
     float4 *nodes = nullptr, *tris = nullptr;
+    float4 *wide = nullptr;              // four-child copy the traversals walk (8 float4 per node)
     uint32_t *order = nullptr, *tri_idx = nullptr;
     float *verts = nullptr;
     int *parent = nullptr, *counters = nullptr;
@@ -627,7 +628,8 @@ mrf_status mrf_bvh_build(mrf_context *ctx, const float *verts, uint32_t n_verts,
         mrf_bvh_destroy(b);
         return s2;
     };
-    if ((st = dev_alloc(&b->nodes, 4 * (size_t)b->n_nodes, "bvh nodes")) || (st = dev_alloc(&b->tris, tv.size(), "bvh tris")) ||
+    if ((st = dev_alloc(&b->nodes, 4 * (size_t)b->n_nodes, "bvh nodes")) ||
+        (st = dev_alloc(&b->wide, 8 * (size_t)b->n_nodes, "bvh wide nodes")) || (st = dev_alloc(&b->tris, tv.size(), "bvh tris")) ||
         (st = dev_alloc(&b->order, n_tris, "bvh order")) || (st = dev_alloc(&b->tri_idx, 3 * (size_t)n_tris, "bvh indices")) ||
         (st = dev_alloc(&b->verts, 3 * (size_t)n_verts, "bvh verts")) || (st = dev_alloc(&b->parent, (size_t)b->n_nodes, "bvh parents")) ||
         (st = dev_alloc(&b->counters, (size_t)b->n_nodes, "bvh counters")) ||
@@ -647,7 +649,11 @@ mrf_status mrf_bvh_build(mrf_context *ctx, const float *verts, uint32_t n_verts,
         if (e == cudaSuccess) e = cudaMemcpy(b->mat, hm.data(), hm.size() * 4, cudaMemcpyHostToDevice);
     }
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "mrf_bvh_build: upload"));
+    // the wide copy, finished before the call returns (renders may run on any stream)
+    if ((e = launch_bvh_widen(b->nodes, b->n_nodes, b->wide, 0)) == cudaSuccess) e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "mrf_bvh_build: wide nodes"));
     b->dev.nodes = b->nodes;
+    b->dev.wide = b->wide;
     b->dev.tris = b->tris;
     b->dev.n_nodes = b->n_nodes;
     b->dev.n_tris = (int)n_tris;
@@ -667,35 +673,40 @@ mrf_status mrf_bvh_rebuild(mrf_bvh *b, const float *verts, uint32_t n_verts, voi
     if (b->node_cap < need || !b->rebuild_scratch) {
         // first rebuild: room for n - 1 internal nodes and the sort buffers
         CUDA_TRY(cudaStreamSynchronize(s), "mrf_bvh_rebuild: synchronize");
-        float4 *nodes = nullptr;
+        float4 *nodes = nullptr, *wide = nullptr;
         int *parent = nullptr, *counters = nullptr;
         uint32_t *scr = nullptr;
         mrf_status st;
-        if ((st = dev_alloc(&nodes, 4 * (size_t)need, "bvh nodes")) || (st = dev_alloc(&parent, (size_t)need, "bvh parents")) ||
-            (st = dev_alloc(&counters, (size_t)need, "bvh counters")) ||
+        if ((st = dev_alloc(&nodes, 4 * (size_t)need, "bvh nodes")) || (st = dev_alloc(&wide, 8 * (size_t)need, "bvh wide nodes")) ||
+            (st = dev_alloc(&parent, (size_t)need, "bvh parents")) || (st = dev_alloc(&counters, (size_t)need, "bvh counters")) ||
             (st = dev_alloc(&scr, bvh_rebuild_scratch_words(b->n_tris), "bvh rebuild scratch"))) {
             cudaFree(nodes);
+            cudaFree(wide);
             cudaFree(parent);
             cudaFree(counters);
             cudaFree(scr);
             return st;
         }
         cudaFree(b->nodes);
+        cudaFree(b->wide);
         cudaFree(b->parent);
         cudaFree(b->counters);
         cudaFree(b->rebuild_scratch);
         b->nodes = nodes;
+        b->wide = wide;
         b->parent = parent;
         b->counters = counters;
         b->rebuild_scratch = scr;
         b->node_cap = need;
         b->dev.nodes = b->nodes;
+        b->dev.wide = b->wide;
     }
     CUDA_TRY(cudaMemcpyAsync(b->verts, verts, 3 * sizeof(float) * (size_t)n_verts, cudaMemcpyDefault, s),
              "mrf_bvh_rebuild: vertex upload");
     CUDA_TRY(launch_bvh_rebuild(b->nodes, b->parent, b->counters, b->tris, b->order, b->tri_idx, b->mat, b->verts,
                                 b->n_tris, b->rebuild_scratch, s),
              "mrf_bvh_rebuild");
+    CUDA_TRY(launch_bvh_widen(b->nodes, need, b->wide, s), "mrf_bvh_rebuild: wide nodes");
     b->n_nodes = need;
     b->dev.n_nodes = need;
     if (!is_device_ptr(verts)) CUDA_TRY(cudaStreamSynchronize(s), "mrf_bvh_rebuild: synchronize");
@@ -713,12 +724,14 @@ mrf_status mrf_bvh_refit(mrf_bvh *b, const float *verts, uint32_t n_verts, void 
     CUDA_TRY(launch_bvh_refit(b->nodes, b->n_nodes, b->tris, (int)b->n_tris, b->order, b->tri_idx, b->verts, b->parent,
                               b->counters, nullptr, s),
              "mrf_bvh_refit: launch");
+    CUDA_TRY(launch_bvh_widen(b->nodes, b->n_nodes, b->wide, s), "mrf_bvh_refit: wide nodes");
     return MRF_OK;
 }
 
 void mrf_bvh_destroy(mrf_bvh *b) {
     if (!b) return;
     cudaFree(b->nodes);
+    cudaFree(b->wide);
     cudaFree(b->tris);
     cudaFree(b->order);
     cudaFree(b->tri_idx);

@@ -1,4 +1,5 @@
-// BVH refit for moved vertices (same topology), bottom-up in one launch.
+// BVH refit for moved vertices (same topology), bottom-up in one launch, and
+// the four-child copy of the binary BVH that the traversals walk.
 //
 // One thread per internal node rewrites the triangles of its leaf children and
 // their boxes, then "arrives" at its node.  A node is complete after
@@ -86,6 +87,66 @@ cudaError_t launch_bvh_refit(float4 *nodes, int n_nodes, float4 *tris, int n_tri
     if (e != cudaSuccess) return e;
     bvh_refit_kernel<<<(n_nodes + 127) / 128, 128, 0, s>>>(nodes, n_nodes, tris, tri_order, tri_idx, verts, parent,
                                                            counters);
+    return cudaGetLastError();
+}
+
+// Wide (four-child) copy of the BVH, the one every traversal walks.  Wide
+// node k stands for binary node k and holds k's grandchildren, or k's children
+// where those are leaves, so one traversal step tests four boxes after one
+// memory round trip and a ray takes about half as many dependent steps.  Every
+// binary node gets its wide copy (those at odd depth are never reached from
+// the root, which spares computing depths after a rebuild); one thread per
+// node, after every build, refit and rebuild.  Layout, 8 float4 per node:
+// [0..5] lo.x, lo.y, lo.z, hi.x, hi.y, hi.z of the four children (one float4
+// per coordinate), [6] child index (inner: node, leaf: first triangle slot),
+// [7] triangle count (> 0 leaf, 0 inner node, -1 no child: empty box).
+struct WideKid {
+    float lo[3], hi[3];
+    int index, count;
+};
+
+__device__ __forceinline__ WideKid kid_of(const float4 *nodes, int k, int s) {
+    WideKid r;
+    box_of_child(nodes, k, s, r.lo, r.hi);
+    const int4 m = __ldcg(reinterpret_cast<const int4 *>(nodes + 4 * k + 3));
+    const int ci = s ? m.y : m.x, cc = s ? m.w : m.z;
+    r.index = ci;
+    r.count = cc > 0 ? cc : ((cc == 0 && ci >= 0) ? 0 : -1);
+    return r;
+}
+
+__global__ void bvh_widen_kernel(const float4 *nodes, int n_nodes, float4 *wide) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_nodes) return;
+    WideKid out[4];
+    int n = 0;
+    for (int s = 0; s < 2; ++s) {
+        const WideKid a = kid_of(nodes, k, s);
+        if (a.count > 0) {
+            out[n++] = a;
+        } else if (a.count == 0) {
+            for (int t = 0; t < 2; ++t) {
+                const WideKid g = kid_of(nodes, a.index, t);
+                if (g.count >= 0) out[n++] = g;
+            }
+        }
+    }
+    float f[8][4];
+    for (int c = 0; c < 4; ++c) {
+        const bool v = c < n;
+        for (int a = 0; a < 3; ++a) {
+            f[a][c] = v ? out[c].lo[a] : INFINITY;
+            f[3 + a][c] = v ? out[c].hi[a] : -INFINITY;
+        }
+        f[6][c] = __int_as_float(v ? out[c].index : -1);
+        f[7][c] = __int_as_float(v ? out[c].count : -1);
+    }
+    for (int u = 0; u < 8; ++u) wide[8 * (size_t)k + u] = make_float4(f[u][0], f[u][1], f[u][2], f[u][3]);
+}
+
+cudaError_t launch_bvh_widen(const float4 *nodes, int n_nodes, float4 *wide, cudaStream_t s) {
+    if (n_nodes <= 0) return cudaSuccess;
+    bvh_widen_kernel<<<(n_nodes + 127) / 128, 128, 0, s>>>(nodes, n_nodes, wide);
     return cudaGetLastError();
 }
 

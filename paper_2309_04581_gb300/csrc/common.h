@@ -14,7 +14,7 @@ constexpr int kMaxLevels = 32;
 constexpr int kMlpWidth = 64;
 constexpr int kMaxIn = 64;
 constexpr int kMaxBounces = 64;
-constexpr int kStackSize = 64;
+constexpr int kWideStackSize = 96;   // traversal stack of the wide BVH (up to three pushes per step)
 
 // Packed FP32 MLP weights (floats):  W1T[in][64] | b1[64] | W2[64][64] | b2[64] | W3T[64][4] | b3[4]
 __host__ __device__ constexpr int mlp_floats(int n_in) { return n_in * 64 + 64 + 64 * 64 + 64 + 64 * 4 + 4; }
@@ -70,6 +70,7 @@ struct FieldDev {
 // count > 0: leaf child whose triangles are [index, index + count) of `tris`.
 struct BvhDev {
     const float4 *nodes;
+    const float4 *wide;         // four-child copy (8 float4 per node), what the traversals walk
     const float4 *tris;         // 3 x float4 per triangle: (v0, id) (v1, material) (v2, 0)
     int n_nodes;
     int n_tris;
@@ -263,5 +264,7 @@ cudaError_t launch_bvh_rebuild(float4 *nodes, int *parent, int *counters, float4
 cudaError_t launch_bvh_refit(float4 *nodes, int n_nodes, float4 *tris, int n_tris, const uint32_t *tri_order,
                              const uint32_t *tri_idx, const float *verts, const int *parent, int *counters,
                              const int *leaf_parent_of_tri, cudaStream_t s);
+// the wide copy of the BVH that traversals walk (8 float4 per binary node), from the binary nodes
+cudaError_t launch_bvh_widen(const float4 *nodes, int n_nodes, float4 *wide, cudaStream_t s);
 
 }  // namespace mrf

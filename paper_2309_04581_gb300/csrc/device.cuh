@@ -446,15 +446,29 @@ __device__ __forceinline__ bool child_hit(float lx, float ly, float lz, float hx
     return a <= b;
 }
 
+__device__ __forceinline__ void cswap(float &ka, int &va, float &kb, int &vb) {
+    if (kb < ka) {
+        const float k = ka;
+        ka = kb;
+        kb = k;
+        const int v = va;
+        va = vb;
+        vb = v;
+    }
+}
+
 // Closest hit (any_hit = false) or first hit in (tmin, tmax) (any_hit = true),
-// skipping the triangle with original id `skip`.  A leaf's triangles are
-// loaded in batches of kTriBatch before they are tested.  4 (the host SAH
-// builder's largest leaf) makes a leaf one memory round trip, which shortens a
-// lone slow ray's chain of dependent loads, but the extra registers cost more
-// occupancy than that gains wherever many rays are in flight, so every caller
-// uses 1.  Adds the nodes visited to
-// `visits` and the ray-triangle tests made to `tests`.  Returns false and sets
-// `fault` if the traversal stack overflows.
+// skipping the triangle with original id `skip`, over the wide (four-child)
+// BVH: a step loads one node (8 x 16 bytes, one memory round trip), tests its
+// four child boxes, tests the triangles of the leaf children, visits the
+// nearest inner child and pushes the others far to near.  The closest hit does
+// not depend on the order of the steps: the closest triangle's boxes all
+// contain its hit point, so it is always tested, and ties go to the lower id.
+// A leaf's triangles are loaded in batches of kTriBatch before they are
+// tested; every caller uses 1 (a batch of 4 shortens a lone slow ray's chain of
+// dependent loads, but its registers cost more occupancy than that gains).
+// Adds the nodes visited to `visits` and the ray-triangle tests made to
+// `tests`.  Returns false and sets `fault` if the traversal stack overflows.
 template <bool any_hit, int kTriBatch = 1>
 __device__ bool bvh_trace(const BvhDev &B, V3 o, V3 d, uint32_t skip, float tmin, float tmax, Hit &h,
                           unsigned &retests, unsigned &visits, unsigned &tests, bool &fault) {
@@ -463,8 +477,8 @@ __device__ bool bvh_trace(const BvhDev &B, V3 o, V3 d, uint32_t skip, float tmin
     h.slot = -1;
     if (B.n_tris == 0) return false;
     V3 inv = v3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
-    int stack[kStackSize];
-    float stack_t[kStackSize];
+    int stack[kWideStackSize];
+    float stack_t[kWideStackSize];
     int sp = 0;
     int node = 0;
     bool found = false;
@@ -472,67 +486,78 @@ __device__ bool bvh_trace(const BvhDev &B, V3 o, V3 d, uint32_t skip, float tmin
     while (true) {
         if (--guard < 0) { fault = true; return found; }
         ++visits;
-        const float4 *nd = B.nodes + 4 * checked_index((uint32_t)node, (uint64_t)B.n_nodes, B.status);
-        float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
-        int ci[2] = {__float_as_int(n3.x), __float_as_int(n3.y)};
-        int cc[2] = {__float_as_int(n3.z), __float_as_int(n3.w)};
-        float tl, tr;
-        bool hl = child_hit(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, o, inv, h.t, tl);
-        bool hr = child_hit(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, o, inv, h.t, tr);
-        int next[2];
-        float nt[2];
-        int nn = 0;
+        const float4 *nd = B.wide + 8 * (size_t)checked_index((uint32_t)node, (uint64_t)B.n_nodes, B.status);
+        float4 q[8];
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            bool hs = s == 0 ? hl : hr;
-            if (!hs) continue;
-            if (cc[s] > 0) {
-                for (int k0 = ci[s]; k0 < ci[s] + cc[s]; k0 += kTriBatch) {
-                    const int nb = min(kTriBatch, ci[s] + cc[s] - k0);
-                    float4 tv[kTriBatch][3];
+        for (int u = 0; u < 8; ++u) q[u] = __ldg(nd + u);
+        const int ci[4] = {__float_as_int(q[6].x), __float_as_int(q[6].y), __float_as_int(q[6].z),
+                           __float_as_int(q[6].w)};
+        const int cc[4] = {__float_as_int(q[7].x), __float_as_int(q[7].y), __float_as_int(q[7].z),
+                           __float_as_int(q[7].w)};
+        float tn[4];
+        bool hit[4];
+        hit[0] = child_hit(q[0].x, q[1].x, q[2].x, q[3].x, q[4].x, q[5].x, o, inv, h.t, tn[0]);
+        hit[1] = child_hit(q[0].y, q[1].y, q[2].y, q[3].y, q[4].y, q[5].y, o, inv, h.t, tn[1]);
+        hit[2] = child_hit(q[0].z, q[1].z, q[2].z, q[3].z, q[4].z, q[5].z, o, inv, h.t, tn[2]);
+        hit[3] = child_hit(q[0].w, q[1].w, q[2].w, q[3].w, q[4].w, q[5].w, o, inv, h.t, tn[3]);
 #pragma unroll
-                    for (int q = 0; q < kTriBatch; ++q)
-                        if (q < nb) {
-                            const float4 *tp =
-                                B.tris + 3 * checked_index((uint32_t)(k0 + q), (uint64_t)B.n_tris, B.status);
-                            tv[q][0] = __ldg(tp);
-                            tv[q][1] = __ldg(tp + 1);
-                            tv[q][2] = __ldg(tp + 2);
-                        }
+        for (int c = 0; c < 4; ++c) {
+            if (!hit[c] || cc[c] <= 0) continue;
+            for (int k0 = ci[c]; k0 < ci[c] + cc[c]; k0 += kTriBatch) {
+                const int nb = min(kTriBatch, ci[c] + cc[c] - k0);
+                float4 tv[kTriBatch][3];
 #pragma unroll
-                    for (int q = 0; q < kTriBatch; ++q) {
-                        if (q >= nb) break;
-                        const uint32_t id = __float_as_uint(tv[q][0].w);
-                        if (id == skip) continue;
-                        ++tests;
-                        float t;
-                        const V3 a = v3(tv[q][0].x, tv[q][0].y, tv[q][0].z), b = v3(tv[q][1].x, tv[q][1].y, tv[q][1].z),
-                                 c = v3(tv[q][2].x, tv[q][2].y, tv[q][2].z);
-                        if (tri_test(o, d, a, b, c, tmin, h.t, t, retests)) {
-                            if (t < h.t || (t == h.t && id < h.id)) {
-                                h.t = t;
-                                h.id = id;
-                                h.slot = k0 + q;
-                                found = true;
-                                if (any_hit) return true;
-                            }
+                for (int qq = 0; qq < kTriBatch; ++qq)
+                    if (qq < nb) {
+                        const float4 *tp = B.tris + 3 * checked_index((uint32_t)(k0 + qq), (uint64_t)B.n_tris, B.status);
+                        tv[qq][0] = __ldg(tp);
+                        tv[qq][1] = __ldg(tp + 1);
+                        tv[qq][2] = __ldg(tp + 2);
+                    }
+#pragma unroll
+                for (int qq = 0; qq < kTriBatch; ++qq) {
+                    if (qq >= nb) break;
+                    const uint32_t id = __float_as_uint(tv[qq][0].w);
+                    if (id == skip) continue;
+                    ++tests;
+                    float t;
+                    const V3 a = v3(tv[qq][0].x, tv[qq][0].y, tv[qq][0].z), b = v3(tv[qq][1].x, tv[qq][1].y, tv[qq][1].z),
+                             c3 = v3(tv[qq][2].x, tv[qq][2].y, tv[qq][2].z);
+                    if (tri_test(o, d, a, b, c3, tmin, h.t, t, retests)) {
+                        if (t < h.t || (t == h.t && id < h.id)) {
+                            h.t = t;
+                            h.id = id;
+                            h.slot = k0 + qq;
+                            found = true;
+                            if (any_hit) return true;
                         }
                     }
                 }
-            } else if (cc[s] == 0 && ci[s] >= 0) {
-                next[nn] = ci[s];
-                nt[nn] = s == 0 ? tl : tr;
-                ++nn;
             }
         }
-        if (nn == 2) {
-            int nearc = nt[0] <= nt[1] ? 0 : 1;
-            if (sp >= kStackSize) { fault = true; return found; }
-            stack_t[sp] = nt[1 - nearc];
-            stack[sp++] = next[1 - nearc];
-            node = next[nearc];
-        } else if (nn == 1) {
-            node = next[0];
+        // inner children, nearest first (absent ones sort last)
+        float key[4];
+        int val[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const bool inner = hit[c] && cc[c] == 0;
+            key[c] = inner ? fminf(tn[c], 3.0e38f) : INFINITY;
+            val[c] = inner ? ci[c] : -1;
+        }
+        cswap(key[0], val[0], key[1], val[1]);
+        cswap(key[2], val[2], key[3], val[3]);
+        cswap(key[0], val[0], key[2], val[2]);
+        cswap(key[1], val[1], key[3], val[3]);
+        cswap(key[1], val[1], key[2], val[2]);
+        if (val[0] >= 0) {
+            if (sp + 3 > kWideStackSize) { fault = true; return found; }
+#pragma unroll
+            for (int c = 3; c >= 1; --c)
+                if (val[c] >= 0) {
+                    stack_t[sp] = key[c];
+                    stack[sp++] = val[c];
+                }
+            node = val[0];
         } else {
             // pop the next subtree whose box still starts before the best hit
             bool got = false;
