@@ -618,19 +618,21 @@ __global__ void __launch_bounds__(128) wf_shadow_net(const WfParams W) {
 // ranges with one atomic per warp, and writes them in order.
 // Round r > 0 regenerates only the slots that round r - 1 left pending (their
 // samples did not fit the buffer), into the emptied buffer.
-// The per-job set-up of the segment jobs (the ray in the field's frame and its
-// quadrature intervals, with their divisions) runs lane-parallel, each lane for
-// its own slot, before the warp walks the jobs one after another.
+// The per-job set-up of the segment job and of the first marched shadow ray of
+// each slot (the ray in the field's frame, its quadrature intervals with their
+// divisions, its sphere cover, and the loads it needs) runs lane-parallel, each
+// lane for its own slot, before the warp walks the jobs one after another.
 struct JobSm {
     float o[3], d[3];
     Segment S;   // S.n = 0: no interval
     Cover cv;
 };
 
-__global__ void __launch_bounds__(kThreads, 5) wf_gen(const WfParams W, uint32_t j, int cur, int round) {
+__global__ void __launch_bounds__(kThreads, 4) wf_gen(const WfParams W, uint32_t j, int cur, int round) {
     __shared__ WalkSmem wsm;
     __shared__ RunList runs_sm[kThreads / 32][32][2];   // per warp, per slot: segment job, first shadow job
     __shared__ JobSm jobs_sm[kThreads / 32][32];
+    __shared__ JobSm shjobs_sm[kThreads / 32][32];   // per slot: its first marched shadow ray
     const RenderParams &P = W.R;
     if (tail_taken(W) || (round > 0 && *pending_ctr(W, round - 1) == 0)) return;   // nothing to do: the grid leaves
     const WalkCtx X = stage_walk(P.F, wsm);
@@ -639,12 +641,14 @@ __global__ void __launch_bounds__(kThreads, 5) wf_gen(const WfParams W, uint32_t
     const int S = chunk_slots(live);
     const int K = P.n_shadow;
     JobSm(&jobs)[32] = jobs_sm[threadIdx.x >> 5];
+    JobSm(&shjobs)[32] = shjobs_sm[threadIdx.x >> 5];
     Counters C = {};
     for (uint32_t wbase; (wbase = next_chunk(work_ctr(W, round, 0), S, lane)) < live;) {
         const uint32_t tid = wbase + (uint32_t)lane;   // this lane's slot (lane < S)
         const bool active = lane < S && tid < live && (round == 0 || W.rcount[tid] == kOverflow);
         V3 hp = v3(0.f, 0.f, 0.f);
         uint32_t vis = 0;   // unblocked shadow rays of the slot
+        int sq = -1;        // the slot's first marched shadow ray
         if (active) {
             const float4 qo = W.qo[cur][tid], qd = W.qd[cur][tid], h4 = W.hp[tid];
             V3 o = v3(qo.x, qo.y, qo.z), d = v3(qd.x, qd.y, qd.z);
@@ -662,13 +666,34 @@ __global__ void __launch_bounds__(kThreads, 5) wf_gen(const WfParams W, uint32_t
             J.o[0] = o.x, J.o[1] = o.y, J.o[2] = o.z;
             J.d[0] = d.x, J.d[1] = d.y, J.d[2] = d.z;
             J.S = sg;
+            for (int q = 0; vis && q < K; ++q)
+                if (W.sw[(size_t)tid * K + q].w == 1.f) {   // marched shadow rays only
+                    sq = q;
+                    break;
+                }
+            if (sq >= 0) {
+                const float4 sh = W.sdir[(size_t)tid * K + sq];
+                V3 so = hp, sd = v3(sh.x, sh.y, sh.z);
+                to_field_frame(P.F, so, sd);
+                Segment ss;
+                JobSm &J2 = shjobs[lane];
+                if (segment_of(P, so, sd, 0.f, sh.w, ss)) {
+                    J2.cv = job_cover(P.F, X, so, sd, ss);
+                } else {
+                    ss.n = 0;
+                    J2.cv = Cover{0u, 0, 0};
+                }
+                J2.o[0] = so.x, J2.o[1] = so.y, J2.o[2] = so.z;
+                J2.d[0] = sd.x, J2.d[1] = sd.y, J2.d[2] = sd.z;
+                J2.S = ss;
+            }
         }
         __syncwarp();
-        uint32_t my_nr = 0, my_total = 0;
+        uint32_t my_nr = 0, my_ns0 = 0, my_total = 0;
         for (int src = 0; src < S; ++src) {
             if (!__shfl_sync(0xffffffffu, (int)active, src)) continue;
             const V3 sp = shfl3(hp, src);
-            const uint32_t svis = __shfl_sync(0xffffffffu, vis, src);
+            const int ssq = __shfl_sync(0xffffffffu, sq, src);
             const uint32_t src_tid = wbase + src;
             RunList(&rl)[2] = runs_sm[threadIdx.x >> 5][src];
             const JobSm &J = jobs[src];
@@ -680,23 +705,34 @@ __global__ void __launch_bounds__(kThreads, 5) wf_gen(const WfParams W, uint32_t
                 rl[0].n = 0;
             const uint32_t n_r = wr.x;
             if (lane == 0) C.nominal += wr.y;
-            uint32_t n_s = 0;
-            bool first = true;   // the first unblocked shadow ray records its runs
-            for (int q = 0; svis && q < K; ++q) {
-                const size_t idx = (size_t)src_tid * K + q;
-                if (W.sw[idx].w != 1.f) continue;   // marched shadow rays only
-                const float4 sh = W.sdir[idx];
-                const uint2 ws = warp_walk(P, X, sp, v3(sh.x, sh.y, sh.z), 0.f, sh.w, nullptr, 0, lane,
-                                           first ? &rl[1] : nullptr);
-                const uint32_t ns = ws.x;
+            uint32_t n_s = 0, ns0 = 0;
+            if (ssq >= 0) {
+                // the first marched shadow ray (set up above) records its runs; the others walk from scratch
+                const JobSm &J2 = shjobs[src];
+                uint2 ws = make_uint2(0u, 0u);
+                if (J2.S.n > 0)
+                    ws = warp_walk_in(P, X, v3(J2.o[0], J2.o[1], J2.o[2]), v3(J2.d[0], J2.d[1], J2.d[2]), J2.S, J2.cv,
+                                      nullptr, 0, lane, &rl[1]);
+                else if (lane == 0)
+                    rl[1].n = 0;
+                ns0 = ws.x;
                 if (lane == 0) C.nominal += ws.y;
-                first = false;
-                if (lane == src) W.scount[idx] = ns;
-                n_s += ns;
+                if (lane == src) W.scount[(size_t)src_tid * K + ssq] = ns0;
+                n_s = ns0;
+                for (int q = ssq + 1; q < K; ++q) {
+                    const size_t idx = (size_t)src_tid * K + q;
+                    if (W.sw[idx].w != 1.f) continue;   // marched shadow rays only
+                    const float4 sh = W.sdir[idx];
+                    const uint2 wq = warp_walk(P, X, sp, v3(sh.x, sh.y, sh.z), 0.f, sh.w, nullptr, 0, lane, nullptr);
+                    if (lane == 0) C.nominal += wq.y;
+                    if (lane == src) W.scount[idx] = wq.x;
+                    n_s += wq.x;
+                }
             }
             if (lane == src) {
                 W.rcount[tid] = n_r;
                 my_nr = n_r;
+                my_ns0 = ns0;
                 my_total = n_r + n_s;
                 C.evaluated += n_r;
                 C.shadow_eval += n_s;
@@ -709,7 +745,7 @@ __global__ void __launch_bounds__(kThreads, 5) wf_gen(const WfParams W, uint32_t
             if (!__shfl_sync(0xffffffffu, (int)active, src)) continue;
             const bool sfits = __shfl_sync(0xffffffffu, (int)fits, src);
             const uint32_t sbase = __shfl_sync(0xffffffffu, base, src);
-            const uint32_t svis = __shfl_sync(0xffffffffu, vis, src);
+            const int ssq = __shfl_sync(0xffffffffu, sq, src);
             const uint32_t src_tid = wbase + src;
             if (!sfits) {
                 if (lane == src) {
@@ -736,22 +772,30 @@ __global__ void __launch_bounds__(kThreads, 5) wf_gen(const WfParams W, uint32_t
                 for (uint32_t i = lane; i < nr; i += 32) W.sview[k + i] = make_float4(jd.x, jd.y, jd.z, 0.f);
             k += nr;
             if (lane == src) W.rstart[tid] = sbase;
-            bool first = true;
-            for (int q = 0; svis && q < K; ++q) {
-                const size_t idx = (size_t)src_tid * K + q;
-                if (W.sw[idx].w != 1.f) continue;
-                const float4 sh = W.sdir[idx];
-                const uint32_t ns = W.scount[idx];
-                if (lane == src) W.sstart[idx] = k;
-                if (first && rl[1].n <= kRunsPerJob)
-                    write_runs(P, sp, v3(sh.x, sh.y, sh.z), 0.f, sh.w, rl[1], W.samp + k, ns, lane);
-                else
+            if (ssq >= 0) {
+                const JobSm &J2 = shjobs[src];
+                const uint32_t ns0 = __shfl_sync(0xffffffffu, my_ns0, src);
+                if (lane == src) W.sstart[(size_t)src_tid * K + ssq] = k;
+                if (ns0 > 0) {
+                    const V3 so = v3(J2.o[0], J2.o[1], J2.o[2]), sd = v3(J2.d[0], J2.d[1], J2.d[2]);
+                    if (rl[1].n <= kRunsPerJob)
+                        write_runs_in(P, so, sd, J2.S, rl[1], W.samp + k, ns0, lane);
+                    else
+                        warp_walk_in(P, X, so, sd, J2.S, J2.cv, W.samp + k, ns0, lane, nullptr);
+                }
+                k += ns0;
+                for (int q = ssq + 1; q < K; ++q) {
+                    const size_t idx = (size_t)src_tid * K + q;
+                    if (W.sw[idx].w != 1.f) continue;
+                    const float4 sh = W.sdir[idx];
+                    const uint32_t ns = W.scount[idx];
+                    if (lane == src) W.sstart[idx] = k;
                     warp_walk(P, X, sp, v3(sh.x, sh.y, sh.z), 0.f, sh.w, W.samp + k, ns, lane, nullptr);
-                first = false;
-                k += ns;
+                    k += ns;
+                }
             }
         }
-        __syncwarp();   // runs_sm and jobs_sm are rewritten by the next chunk
+        __syncwarp();   // runs_sm, jobs_sm and shjobs_sm are rewritten by the next chunk
     }
     if (round > 0) C.evaluated = C.shadow_eval = 0, C.nominal = 0;   // counted by round 0
     flush_counters(P.stats, C);
