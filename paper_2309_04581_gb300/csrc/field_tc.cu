@@ -236,7 +236,8 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
         fence_after_sync();
         return !bad;
     };
-    for (uint32_t tile = blockIdx.x * G + g; tile * 128u < n; tile += gridDim.x * G) {
+    const TileLoop tl = cta_tiles(n, G, g);
+    for (uint32_t tile = tl.first; tile < tl.end; tile += tl.step) {
         const uint32_t i = tile * 128u + gt;
         const bool valid = i < n;
         V3 p = v3(0.f, 0.f, 0.f);
@@ -448,7 +449,8 @@ __global__ void __launch_bounds__(128 * kTmGroups, 1)
         fence_before_sync();
         return !group_sync_or(bar_id, !ok);
     };
-    for (uint32_t tile = blockIdx.x * kTmGroups + g; tile * 128u < n; tile += gridDim.x * kTmGroups) {
+    const TileLoop tl = cta_tiles(n, kTmGroups, g);
+    for (uint32_t tile = tl.first; tile < tl.end; tile += tl.step) {
         const uint32_t i = tile * 128u + gt;
         const bool valid = i < n;
         V3 p = v3(0.f, 0.f, 0.f);
@@ -641,7 +643,8 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
         return true;
     };
 
-    for (uint32_t tile = blockIdx.x * G + g; tile * 128u < n; tile += gridDim.x * G) {
+    const TileLoop tl = cta_tiles(n, G, g);
+    for (uint32_t tile = tl.first; tile < tl.end; tile += tl.step) {
         const uint32_t i = tile * 128u + gt;
         const bool valid = i < n;
         V3 p = v3(0.f, 0.f, 0.f), dv = v3(0.f, 0.f, 1.f);

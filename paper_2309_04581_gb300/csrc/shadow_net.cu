@@ -542,7 +542,8 @@ __global__ void __launch_bounds__(128 * kTcGroups, 2)
     const int bar_id = 1 + g;
     uint32_t phase = 0, evals = 0;
     bool ok = true;
-    for (uint32_t tile = blockIdx.x * kTcGroups + g; tile * 128u < n; tile += gridDim.x * kTcGroups) {
+    const tc::TileLoop tl = tc::cta_tiles(n, kTcGroups, g);
+    for (uint32_t tile = tl.first; tile < tl.end; tile += tl.step) {
         const uint32_t i = tile * 128u + gt;
         const bool valid = i < n;
         uint32_t dst = i;

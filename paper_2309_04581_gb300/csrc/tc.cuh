@@ -147,5 +147,25 @@ __device__ __forceinline__ void relu_bias_store(const uint32_t (&r)[32], const f
 }
 
 
+// The 128-sample tiles of an n-sample launch that group g (of G) of this CTA
+// takes: tiles first, first + step, ... below end.  With at least one tile
+// per group of the grid, CTA b's groups take tiles b*G .. b*G + G - 1 of each
+// round (neighbouring tiles, that is neighbouring rays, share an SM's L1).
+// With fewer, every CTA takes a run of ceil(tiles / gridDim.x) <= G tiles, one
+// per group, so that every SM gets work: handing consecutive tiles to the
+// groups of one CTA queued them behind one SM's L1 data pipe and made a launch
+// of a few hundred tiles 2.5 times slower (a run per CTA for every launch cost
+// the large ones 1 %).
+struct TileLoop {
+    uint32_t first, end, step;
+};
+__device__ __forceinline__ TileLoop cta_tiles(uint32_t n, int G, int g) {
+    const uint32_t tiles = (n + 127u) / 128u;
+    if (tiles >= gridDim.x * (uint32_t)G) return TileLoop{blockIdx.x * G + g, tiles, gridDim.x * G};
+    const uint32_t per = (tiles + gridDim.x - 1u) / gridDim.x;
+    const uint32_t b = min(blockIdx.x * per, tiles);
+    return TileLoop{b + g, min(b + per, tiles), (uint32_t)G};
+}
+
 }  // namespace tc
 }  // namespace mrf
