@@ -162,7 +162,10 @@ mrf_status mrf_field_query(mrf_context *ctx, const mrf_field *field, const float
 /* Builds a bounding-volume hierarchy over a triangle mesh for the ray-casting
  * function t(p, w) of Eq. 3 (the paper does not name its acceleration
  * structure; this one is a binned-SAH binary BVH built on the host, 64-byte
- * nodes holding both children's boxes, leaves of at most 4 triangles).
+ * nodes holding both children's boxes, leaves of at most 4 triangles).  The
+ * traversals walk a four-child copy of it (128-byte nodes holding a node's
+ * grandchildren), which build, refit and rebuild rewrite on the GPU; the
+ * statistics count the four-child nodes visited.
  * verts: n_verts x 3 FP32; tris: n_tris x 3 vertex indices; mat_id: n_tris
  * material indices into the table of mrf_materials_set.  Triangle ids reported
  * by the renderer are indices into `tris`.  n_tris may be 0 (no meshes).
@@ -171,7 +174,8 @@ mrf_status mrf_bvh_build(mrf_context *ctx, const float *verts, uint32_t n_verts,
                          const uint32_t *mat_id, uint32_t n_tris, mrf_bvh **out);
 /* Refits the BVH boxes to moved vertices (same topology; the dynamic meshes of
  * Sec. 3.2 change their vertices every simulation step).  verts: n_verts x 3,
- * n_verts must equal the build's (else MRF_ERR_INVALID_ARG).  Runs on `stream`. */
+ * n_verts must equal the build's (else MRF_ERR_INVALID_ARG).  Runs on `stream`
+ * (the boxes, then the four-child copy). */
 mrf_status mrf_bvh_refit(mrf_bvh *bvh, const float *verts, uint32_t n_verts, void *stream);
 /* Rebuild of the hierarchy on the GPU for new vertex positions (same
  * triangles, n_verts as at build; host or device array): a linear BVH over the
@@ -320,7 +324,7 @@ typedef struct mrf_stats {
                                       build) */
     uint64_t shadow_net_evals;     /* shadow rays answered by the shadow network */
     uint64_t ended_miss, ended_tau, ended_cap;   /* paths that left the scene, fell below tau, hit the bounce cap */
-    uint64_t bvh_nodes;            /* BVH nodes visited (closest-hit, shadow and mask rays) */
+    uint64_t bvh_nodes;            /* four-child BVH nodes visited (closest-hit, shadow and mask rays) */
     uint64_t bvh_tri_tests;        /* ray-triangle tests made by those traversals */
     uint64_t bvh_worst_nodes;      /* nodes visited by the longest closest-hit traversal */
     uint64_t bvh_worst_path;       /* the path (ray * spp + sample) that made it */
