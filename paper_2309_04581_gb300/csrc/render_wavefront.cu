@@ -649,6 +649,7 @@ __global__ void __launch_bounds__(kThreads, 4) wf_gen(const WfParams W, uint32_t
         V3 hp = v3(0.f, 0.f, 0.f);
         uint32_t vis = 0;   // unblocked shadow rays of the slot
         int sq = -1;        // the slot's first marched shadow ray
+        bool walk = false;  // some job of the slot has intervals to walk
         if (active) {
             const float4 qo = W.qo[cur][tid], qd = W.qd[cur][tid], h4 = W.hp[tid];
             V3 o = v3(qo.x, qo.y, qo.z), d = v3(qd.x, qd.y, qd.z);
@@ -687,11 +688,19 @@ __global__ void __launch_bounds__(kThreads, 4) wf_gen(const WfParams W, uint32_t
                 J2.d[0] = sd.x, J2.d[1] = sd.y, J2.d[2] = sd.z;
                 J2.S = ss;
             }
+            // a segment whose cover is empty has no sample: without a marched
+            // shadow ray the slot is done here and the warp does not visit it
+            walk = (sg.n > 0 && J.cv.cb < J.cv.ce) || sq >= 0;
+            if (!walk) {
+                W.rcount[tid] = 0;
+                C.nominal += (uint32_t)sg.n;
+            }
         }
         __syncwarp();
         uint32_t my_nr = 0, my_ns0 = 0, my_total = 0;
-        for (int src = 0; src < S; ++src) {
-            if (!__shfl_sync(0xffffffffu, (int)active, src)) continue;
+        const unsigned walkers = __ballot_sync(0xffffffffu, walk);
+        for (unsigned wm = walkers; wm; wm &= wm - 1u) {
+            const int src = __ffs(wm) - 1;
             const V3 sp = shfl3(hp, src);
             const int ssq = __shfl_sync(0xffffffffu, sq, src);
             const uint32_t src_tid = wbase + src;
@@ -740,9 +749,10 @@ __global__ void __launch_bounds__(kThreads, 4) wf_gen(const WfParams W, uint32_t
         }
         const uint32_t base = warp_alloc(&W.ctr[2], my_total);
         const bool fits = (uint64_t)base + my_total <= (uint64_t)W.cap;
+        if (active && !walk) W.rstart[tid] = base;
         __syncwarp();
-        for (int src = 0; src < S; ++src) {
-            if (!__shfl_sync(0xffffffffu, (int)active, src)) continue;
+        for (unsigned wm = walkers; wm; wm &= wm - 1u) {
+            const int src = __ffs(wm) - 1;
             const bool sfits = __shfl_sync(0xffffffffu, (int)fits, src);
             const uint32_t sbase = __shfl_sync(0xffffffffu, base, src);
             const int ssq = __shfl_sync(0xffffffffu, sq, src);
