@@ -907,9 +907,13 @@ __global__ void __launch_bounds__(kThreads, 8) wf_composite(const WfParams W, in
             tmax = fmaxf(qT.x, fmaxf(qT.y, qT.z));
             diffuse = __float_as_uint(W.hp[tid].w) != 0u;   // some unblocked shadow ray from a diffuse hit
             if (active) W.rcount[tid] = kDone;   // read below from the registers only
+            if (active && rc == 0 && !diffuse) {   // no sample and no shadow depth: done here
+                W.comp[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+                active = false;
+            }
         }
-        for (int src = 0; src < S; ++src) {
-            if (!__shfl_sync(0xffffffffu, (int)active, src)) continue;
+        for (unsigned am = __ballot_sync(0xffffffffu, active); am; am &= am - 1u) {
+            const int src = __ffs(am) - 1;
             const uint32_t src_rc = __shfl_sync(0xffffffffu, rc, src);
             const uint32_t src_tid = wbase + src;
             {
