@@ -212,7 +212,7 @@ struct Cover {
     uint32_t smask;
     int cb, ce;
 };
-__device__ __forceinline__ bool cover_jumps(const FieldDev &F) {
+__device__ __forceinline__ bool has_sphere_cover(const FieldDev &F) {
     return F.kind == MRF_FIELD_HASHGRID && F.n_support > 0 && F.n_support <= 32;
 }
 
@@ -220,7 +220,7 @@ __device__ __forceinline__ bool cover_jumps(const FieldDev &F) {
 __device__ __forceinline__ Cover job_cover(const FieldDev &F, const WalkCtx &X, V3 o, V3 d, const Segment &S) {
     Cover cv{0u, 0, S.n};
     if (F.kind == MRF_FIELD_HASHGRID && F.n_support == 0) cv.ce = 0;
-    if (!cover_jumps(F)) return cv;
+    if (!has_sphere_cover(F)) return cv;
     const float inv_h = 1.0f / S.h;
     cv.cb = 0x7fffffff;
     cv.ce = -1;
@@ -238,7 +238,7 @@ __device__ __forceinline__ Cover job_cover_warp(const FieldDev &F, const WalkCtx
                                                 int lane) {
     Cover cv{0u, 0, S.n};
     if (F.kind == MRF_FIELD_HASHGRID && F.n_support == 0) cv.ce = 0;
-    if (!cover_jumps(F)) return cv;
+    if (!has_sphere_cover(F)) return cv;
     int jb = 0x7fffffff, je = -1;
     bool hit = false;
     if (lane < F.n_support) hit = sphere_range(X.support[lane], o, d, S, 1.0f / S.h, true, jb, je);
@@ -299,14 +299,14 @@ __device__ __noinline__ uint2 warp_walk_in(const RenderParams &P, const WalkCtx 
     if (runs && lane == 0) runs->n = 0;
     const FieldDev &F = P.F;
     const bool hash = F.kind == MRF_FIELD_HASHGRID;
-    const bool jump = cover_jumps(F);
+    const bool covered = has_sphere_cover(F);
     const bool use_occ0 = hash && F.occ != nullptr;
     // With the sphere cover the support test (arithmetic only) goes first and
     // the coarse grid is left out: the fine grid alone takes the same decisions,
     // and the coarse one only sped up skipping, which the cover now does.  When
     // the grid covers the support it can no longer reject anything either.
-    const bool use_coarse = use_occ0 && X.coarse != nullptr && !jump;
-    const bool use_occ = use_occ0 && !(jump && F.occ_covers_support);
+    const bool use_coarse = use_occ0 && X.coarse != nullptr && !covered;
+    const bool use_occ = use_occ0 && !(covered && F.occ_covers_support);
     const int Rc = F.occ_coarse_res;
     const float inv_h = 1.0f / S.h;
     V3 inv = v3(0.f, 0.f, 0.f);
@@ -323,7 +323,7 @@ __device__ __noinline__ uint2 warp_walk_in(const RenderParams &P, const WalkCtx 
             const float hi = P.steps ? fmaf((float)(i + 1), S.h, S.t0) : fminf(lo + S.h, S.t1);
             const float tm = 0.5f * (lo + hi), delta = hi - lo;
             const V3 p = fma3(d, tm, o);
-            bool empty = jump && !(support_masked(X.support, cv.smask, p) > 0.f);
+            bool empty = covered && !(support_masked(X.support, cv.smask, p) > 0.f);
             if (!empty && use_coarse) {
                 int c[3];
 #pragma unroll
@@ -344,7 +344,7 @@ __device__ __noinline__ uint2 warp_walk_in(const RenderParams &P, const WalkCtx 
                     empty = true;
                 }
             }
-            if (!empty) emit = !hash || jump || support_all(X.support, F.n_support, p) > 0.f;
+            if (!empty) emit = !hash || covered || support_all(X.support, F.n_support, p) > 0.f;
             rec = make_float4(p.x, p.y, p.z, delta);
         } else {
             skip_to = S.n;
