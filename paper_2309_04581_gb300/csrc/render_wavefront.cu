@@ -667,10 +667,14 @@ __global__ void __launch_bounds__(kThreads, 4) wf_gen(const WfParams W, uint32_t
             J.o[0] = o.x, J.o[1] = o.y, J.o[2] = o.z;
             J.d[0] = d.x, J.d[1] = d.y, J.d[2] = d.z;
             J.S = sg;
+            bool more = false;   // a second marched shadow ray
             for (int q = 0; vis && q < K; ++q)
                 if (W.sw[(size_t)tid * K + q].w == 1.f) {   // marched shadow rays only
+                    if (sq >= 0) {
+                        more = true;
+                        break;
+                    }
                     sq = q;
-                    break;
                 }
             if (sq >= 0) {
                 const float4 sh = W.sdir[(size_t)tid * K + sq];
@@ -688,12 +692,17 @@ __global__ void __launch_bounds__(kThreads, 4) wf_gen(const WfParams W, uint32_t
                 J2.d[0] = sd.x, J2.d[1] = sd.y, J2.d[2] = sd.z;
                 J2.S = ss;
             }
-            // a segment whose cover is empty has no sample: without a marched
-            // shadow ray the slot is done here and the warp does not visit it
-            walk = (sg.n > 0 && J.cv.cb < J.cv.ce) || sq >= 0;
+            // a job whose cover is empty has no sample: a slot with nothing else
+            // to walk is done here and the warp does not visit it
+            const bool sh_walk = sq >= 0 && (more || (shjobs[lane].S.n > 0 && shjobs[lane].cv.cb < shjobs[lane].cv.ce));
+            walk = (sg.n > 0 && J.cv.cb < J.cv.ce) || sh_walk;
             if (!walk) {
                 W.rcount[tid] = 0;
                 C.nominal += (uint32_t)sg.n;
+                if (sq >= 0) {
+                    W.scount[(size_t)tid * K + sq] = 0;
+                    C.nominal += (uint32_t)shjobs[lane].S.n;
+                }
             }
         }
         __syncwarp();
@@ -706,8 +715,8 @@ __global__ void __launch_bounds__(kThreads, 4) wf_gen(const WfParams W, uint32_t
             const uint32_t src_tid = wbase + src;
             RunList(&rl)[2] = runs_sm[threadIdx.x >> 5][src];
             const JobSm &J = jobs[src];
-            uint2 wr = make_uint2(0u, 0u);
-            if (J.S.n > 0)
+            uint2 wr = make_uint2(0u, (uint32_t)J.S.n);   // an empty cover: no sample
+            if (J.S.n > 0 && J.cv.cb < J.cv.ce)
                 wr = warp_walk_in(P, X, v3(J.o[0], J.o[1], J.o[2]), v3(J.d[0], J.d[1], J.d[2]), J.S, J.cv, nullptr, 0,
                                   lane, &rl[0]);
             else if (lane == 0)
@@ -718,8 +727,8 @@ __global__ void __launch_bounds__(kThreads, 4) wf_gen(const WfParams W, uint32_t
             if (ssq >= 0) {
                 // the first marched shadow ray (set up above) records its runs; the others walk from scratch
                 const JobSm &J2 = shjobs[src];
-                uint2 ws = make_uint2(0u, 0u);
-                if (J2.S.n > 0)
+                uint2 ws = make_uint2(0u, (uint32_t)J2.S.n);
+                if (J2.S.n > 0 && J2.cv.cb < J2.cv.ce)
                     ws = warp_walk_in(P, X, v3(J2.o[0], J2.o[1], J2.o[2]), v3(J2.d[0], J2.d[1], J2.d[2]), J2.S, J2.cv,
                                       nullptr, 0, lane, &rl[1]);
                 else if (lane == 0)
