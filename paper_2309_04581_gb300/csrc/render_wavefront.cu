@@ -78,14 +78,14 @@ __device__ __forceinline__ uint32_t warp_alloc(uint32_t *ctr, uint32_t n) {
 // wf_composite): a warp takes a chunk of S consecutive slots from a per-round
 // work counter, walks their jobs one after another (lane l < S holds slot
 // base + l) and takes the next chunk until none is left.  S is a power of two,
-// at most 32, sized for about four chunks per resident warp: job lengths vary
+// at most 32, sized for at least four chunks per resident warp: job lengths vary
 // by orders of magnitude (a ray through the field against one that hits the
 // floor at once), and a static split left SMs idle for half of the first
 // segment and waiting on a few warps with 32 long jobs in the late ones.
 __device__ __forceinline__ int chunk_slots(uint32_t live) {
     const uint32_t warps = min(gridDim.x * (blockDim.x >> 5), 152u * 32u);
-    const uint32_t need = (live + 4u * warps - 1u) / (4u * warps);
-    return need <= 1 ? 1 : (int)min(32u, 1u << (32 - __clz(need - 1)));
+    const uint32_t need = live / (4u * warps);   // rounded down: at least four chunks per warp
+    return need <= 1 ? 1 : (int)min(32u, 1u << (31 - __clz(need)));
 }
 
 // First slot of the warp's next chunk (>= live: no work left).
